@@ -1,0 +1,62 @@
+"""The synthetic pencil-beam inputs have the structure the paper describes.
+
+Sec. II-A/II-B: rows = voxels, columns = spots, rows far outnumber columns,
+most rows are empty (about 70 % in Fig. 2) and row lengths are very uneven;
+the non-zero ratio of the paper's matrices is 0.6-2 %.
+"""
+import numpy as np
+
+import dosegen
+
+
+def test_tiny_beam_shape_and_nnz_target():
+    A = dosegen.generate(dosegen.TINY)
+    assert (A.nrows, A.ncols) == (20480, 500)
+    assert abs(A.nnz - dosegen.NNZ_TARGETS["tiny"]) <= 0.05 * dosegen.NNZ_TARGETS["tiny"]
+    assert 0.015 <= A.nnz / (A.nrows * A.ncols) <= 0.025       # ~2 % density
+    rp = A.row_ptr.astype(np.int64)
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and rp[-1] == A.nnz
+    for i in range(A.nrows):
+        c = A.col[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(c.astype(np.int64)) > 0)         # ascending, unique
+    assert A.col.max() < A.ncols
+    assert A.val.min() >= dosegen.TINY.tau and A.val.max() <= 1.0
+
+
+def test_clinical_beam_counts_and_row_length_profile():
+    n, rl = dosegen.count_nnz(dosegen.CLINICAL, row_lengths=True)
+    assert rl.size == 256 * 256 * 160
+    assert abs(n - dosegen.NNZ_TARGETS["clinical"]) <= 0.05 * dosegen.NNZ_TARGETS["clinical"]
+    empty = np.mean(rl == 0)
+    assert 0.7 <= empty <= 0.95                                 # mostly empty rows
+    assert 200 <= rl.max() <= 450                               # 0 to ~400 entries per row
+    assert rl.size / dosegen.CLINICAL.ncols > 40                # rows >> columns
+
+
+def test_generation_is_deterministic():
+    a = dosegen.generate(dosegen.TINY)
+    b = dosegen.generate(dosegen.TINY)
+    assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)
+    assert np.array_equal(a.val, b.val)
+    x1 = dosegen.spot_weights(500, 123)
+    x2 = dosegen.spot_weights(500, 123)
+    assert x1.dtype == np.float32 and np.array_equal(x1, x2)
+    assert x1.min() >= 0.0 and x1.max() < 1.0
+    assert not np.array_equal(x1, dosegen.spot_weights(500, 124))
+
+
+def test_batched_scenarios_are_shifted_beams():
+    beams = dosegen.batched_beams()
+    assert len(beams) == 27
+    assert len({b.shift for b in beams}) == 9
+    assert sorted({b.ncols for b in beams}) == [1000, 2500, 4000]
+    for b in beams:
+        assert 2_000_000 <= b.nrows <= 8_000_000
+
+
+def test_ellipsoid_target():
+    p, w = dosegen.ellipsoid_target(dosegen.TINY)
+    inside = p == 60.0
+    assert inside.sum() > 0 and np.all(w[inside] == 10.0) and np.all(w[~inside] == 1.0)
+    # semi-axes (8, 8, 4): volume ~ 4/3 pi 256 voxels
+    assert abs(inside.sum() - 4.0 / 3.0 * np.pi * 256) < 0.15 * 4.0 / 3.0 * np.pi * 256

@@ -1,0 +1,330 @@
+"""Pins of the FP64 oracle against facts fixed outside it.
+
+Each test checks the oracle against something other than itself: brute-force
+dense products, library routines (scipy.sparse, torch dtype conversions),
+closed forms, algebraic identities, or values the paper prints (Table I and the
+Sec. V operational intensity, stored under tests/golden/).  Chosen so that a
+dropped term, a wrong index, a transposed operand or a wrong rounding rule in
+the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import dosegen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dense(csr_or_enc, a=None):
+    nr, nc = csr_or_enc.nrows, csr_or_enc.ncols
+    vals = csr_or_enc.val if a is None else a
+    M = np.zeros((nr, nc))
+    rp = csr_or_enc.row_ptr.astype(np.int64)
+    for i in range(nr):
+        for k in range(rp[i], rp[i + 1]):
+            M[i, csr_or_enc.col[k]] += vals[k]
+    return M
+
+
+def _tiny_cases():
+    out = [dosegen.random_csr(37, 23, seed=s, density=0.3) for s in range(4)]
+    out.append(dosegen.random_csr(5, 7, seed=9, lengths=[0, 7, 1, 0, 3]))
+    out.append(dosegen.random_csr(1, 1, seed=10, lengths=[1]))
+    out.append(dosegen.random_csr(6, 4, seed=11, lengths=[0] * 6))
+    return out
+
+
+# ------------------------------------------------------------ SpMV: d = A x
+
+@pytest.mark.parametrize("case", range(7))
+def test_spmv_matches_dense_brute_force(case):
+    A = _tiny_cases()[case]
+    x = np.random.default_rng(case).uniform(0, 1, A.ncols)
+    d = oracle.spmv(A.nrows, A.row_ptr, A.col, A.val, x)
+    # Pure-Python loop over the dense matrix in ascending column order: the same
+    # order as CSR storage (columns ascending), so the sums agree exactly.
+    M = _dense(A)
+    ref = np.array([sum(M[i, j] * x[j] for j in range(A.ncols) if M[i, j] != 0.0)
+                    for i in range(A.nrows)], dtype=np.float64)
+    assert np.array_equal(d, ref)
+    assert np.allclose(d, M @ x, rtol=1e-14, atol=0)
+
+
+def test_spmv_matches_scipy_and_rows_sampling():
+    A = dosegen.random_csr(300, 120, seed=3, density=0.05)
+    x = np.random.default_rng(1).uniform(0, 1, A.ncols)
+    d = oracle.spmv(A.nrows, A.row_ptr, A.col, A.val, x)
+    S = sp.csr_matrix((A.val, A.col.astype(np.int64), A.row_ptr.astype(np.int64)),
+                      shape=(A.nrows, A.ncols))
+    np.testing.assert_allclose(d, S @ x, rtol=1e-13, atol=0)
+    rows = np.array([0, 5, 299, 17, 5], dtype=np.uint32)
+    assert np.array_equal(oracle.spmv_rows(rows, A.row_ptr, A.col, A.val, x), d[rows])
+
+
+def test_spmv_linearity():
+    A = dosegen.random_csr(200, 60, seed=5, density=0.2)
+    rng = np.random.default_rng(2)
+    x, y = rng.uniform(0, 1, A.ncols), rng.uniform(0, 1, A.ncols)
+    al, be = 0.37, -1.9
+    lhs = oracle.spmv(A.nrows, A.row_ptr, A.col, A.val, al * x + be * y)
+    rhs = al * oracle.spmv(A.nrows, A.row_ptr, A.col, A.val, x) + \
+        be * oracle.spmv(A.nrows, A.row_ptr, A.col, A.val, y)
+    scale = oracle.spmv(A.nrows, A.row_ptr, A.col, np.abs(A.val), np.abs(al * x) + np.abs(be * y))
+    assert np.all(np.abs(lhs - rhs) <= 1e-14 * scale + 1e-300)
+
+
+def test_spmv_unit_vectors_reproduce_columns_exactly():
+    A = dosegen.random_csr(50, 12, seed=6, density=0.4)
+    M = _dense(A)
+    for j in range(A.ncols):
+        e = np.zeros(A.ncols)
+        e[j] = 1.0
+        assert np.array_equal(oracle.spmv(A.nrows, A.row_ptr, A.col, A.val, e), M[:, j])
+
+
+def test_spmv_special_cases():
+    n = 9
+    ident = dosegen.CSR(n, n, np.arange(n + 1, dtype=np.uint32), np.arange(n, dtype=np.uint32),
+                        np.ones(n))
+    x = np.random.default_rng(3).uniform(0, 1, n)
+    assert np.array_equal(oracle.spmv(n, ident.row_ptr, ident.col, ident.val, x), x)
+    A = dosegen.random_csr(40, 10, seed=7, density=0.5)
+    rs = oracle.spmv(A.nrows, A.row_ptr, A.col, A.val, np.ones(A.ncols))
+    ref = np.array([math.fsum(A.val[A.row_ptr[i]:A.row_ptr[i + 1]]) for i in range(A.nrows)])
+    np.testing.assert_allclose(rs, ref, rtol=1e-15, atol=0)
+    Z = dosegen.random_csr(8, 5, seed=8, lengths=[0] * 8)
+    assert np.array_equal(oracle.spmv(8, Z.row_ptr, Z.col, Z.val, np.ones(5)), np.zeros(8))
+
+
+def test_spmm_equals_columnwise_dense():
+    A = dosegen.random_csr(64, 20, seed=12, density=0.3)
+    X = np.random.default_rng(4).uniform(0, 1, (A.ncols, 5))
+    D = oracle.spmm(A.nrows, A.row_ptr, A.col, A.val, X)
+    np.testing.assert_allclose(D, _dense(A) @ X, rtol=1e-14, atol=0)
+
+
+# ------------------------------------------------------------ adjoint: A^T r
+
+def test_adjoint_identity_and_transpose():
+    A = dosegen.random_csr(150, 40, seed=13, density=0.2)
+    rng = np.random.default_rng(5)
+    x, y = rng.uniform(0, 1, A.ncols), rng.normal(size=A.nrows)
+    Ax = oracle.spmv(A.nrows, A.row_ptr, A.col, A.val, x)
+    ATy = oracle.spmv_t(A.nrows, A.ncols, A.row_ptr, A.col, A.val, y)
+    scale = np.dot(oracle.spmv(A.nrows, A.row_ptr, A.col, A.val, np.abs(x)), np.abs(y))
+    assert abs(np.dot(Ax, y) - np.dot(x, ATy)) <= 1e-13 * scale
+    # A^T of the explicitly transposed CSR (scipy) matches the scatter form.
+    S = sp.csr_matrix((A.val, A.col.astype(np.int64), A.row_ptr.astype(np.int64)),
+                      shape=(A.nrows, A.ncols))
+    T = S.T.tocsr()
+    g_t = oracle.spmv(A.ncols, T.indptr.astype(np.uint32), T.indices.astype(np.uint32), T.data, y)
+    np.testing.assert_allclose(ATy, g_t, rtol=1e-13, atol=1e-13 * np.abs(y).sum())
+    np.testing.assert_allclose(ATy, _dense(A).T @ y, rtol=1e-12, atol=1e-13 * np.abs(y).sum())
+    absg = oracle.abs_spmv_t(A.nrows, A.ncols, A.row_ptr, A.col, A.val, y)
+    np.testing.assert_allclose(absg, np.abs(_dense(A)).T @ np.abs(y), rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------- objective and gradient
+
+def test_objective_closed_form():
+    d = np.array([1.0, 2.0, 0.0, 5.0])
+    p = np.array([0.0, 2.0, 60.0, 1.0])
+    w = np.array([1.0, 10.0, 10.0, 1.0])
+    f, r = oracle.objective(d, p, w)
+    assert f == 1.0 + 0.0 + 36000.0 + 16.0
+    assert np.array_equal(r, [2.0, 0.0, -1200.0, 8.0])
+
+
+def test_gradient_central_differences_exact_for_quadratic():
+    beam = dosegen.TINY
+    A = dosegen.generate(beam)
+    p, w = dosegen.ellipsoid_target(beam)
+    x = dosegen.spot_weights(A.ncols, dosegen.weight_seed(beam)).astype(np.float64)
+    f0, g = oracle.fgrad(A.nrows, A.ncols, A.row_ptr, A.col, A.val, x, p, w)
+    h = 0.5
+    spots = np.random.default_rng(6).choice(A.ncols, 20, replace=False)
+    for j in spots:
+        xp, xm = x.copy(), x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fp, _ = oracle.fgrad(A.nrows, A.ncols, A.row_ptr, A.col, A.val, xp, p, w)
+        fm, _ = oracle.fgrad(A.nrows, A.ncols, A.row_ptr, A.col, A.val, xm, p, w)
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-9 * max(abs(g[j]), 1e-6 * f0)
+
+
+def test_pg_closed_form_on_diagonal_and_monotone_on_beam():
+    n = 16
+    rng = np.random.default_rng(7)
+    a = rng.uniform(0.5, 2.0, n)
+    diag = dosegen.CSR(n, n, np.arange(n + 1, dtype=np.uint32), np.arange(n, dtype=np.uint32), a)
+    p = rng.uniform(0, 3, n)
+    w = rng.choice([1.0, 10.0], n)
+    x0 = rng.uniform(0, 1, n)
+    eta = 0.01
+    x1, fh = oracle.pg(n, n, diag.row_ptr, diag.col, diag.val, x0, p, w, eta, 1)
+    ref = np.maximum(0.0, x0 - eta * 2 * w * a * (a * x0 - p))
+    np.testing.assert_allclose(x1, ref, rtol=1e-15, atol=1e-15)
+    assert fh[0] == pytest.approx(np.sum(w * (a * x0 - p) ** 2), rel=1e-15)
+    # lambda_max(A^T A) of a diagonal matrix is max a^2.
+    lam = oracle.norm2_sq(n, n, diag.row_ptr, diag.col, diag.val, iters=2000)
+    assert lam == pytest.approx(np.max(a) ** 2, rel=1e-6)
+
+    beam = dosegen.TINY
+    A = dosegen.generate(beam)
+    enc = oracle.encode(A, oracle.U16_SCALE)
+    pt, wt = dosegen.ellipsoid_target(beam)
+    eta = oracle.pg_step_size(A.nrows, A.ncols, enc.row_ptr, enc.col, enc.decoded, wt)
+    xs = dosegen.spot_weights(A.ncols, dosegen.weight_seed(beam))
+    xf, fh = oracle.pg(A.nrows, A.ncols, enc.row_ptr, enc.col, enc.decoded, xs, pt, wt, eta, 30)
+    assert np.all(xf >= 0)
+    assert np.all(np.diff(fh) <= 1e-12 * fh[0])
+    assert fh[-1] < fh[0]
+
+
+# ------------------------------------------------------------------ formats
+
+def test_fp8_e4m3_code_table():
+    vals = np.array([oracle.fp8_e4m3_value(c) for c in range(256)])
+    assert vals[0x7E] == 448.0 and vals[0xFE] == -448.0           # largest finite
+    assert vals[0x38] == 1.0 and vals[0x08] == 2.0 ** -6           # one, smallest normal
+    assert vals[0x01] == 2.0 ** -9 and vals[0x07] == 7 * 2.0 ** -9  # subnormals
+    assert math.isnan(vals[0x7F]) and math.isnan(vals[0xFF])        # the only NaNs
+    assert np.sum(np.isnan(vals)) == 2 and not np.any(np.isinf(vals))
+    assert np.all(np.diff(vals[:0x7F]) > 0)                         # monotone in the code
+    # Library routine: torch's float8_e4m3fn has the same 254 finite values.
+    codes = torch.arange(256, dtype=torch.int32).to(torch.uint8)
+    tv = codes.view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    fin = ~np.isnan(vals)
+    assert np.array_equal(tv[fin], vals[fin]) and np.all(np.isnan(tv[~fin]))
+
+
+def test_fp8_nearest_matches_torch_rne():
+    rng = np.random.default_rng(8)
+    t = np.concatenate([rng.uniform(0, 448, 4000), rng.uniform(0, 0.02, 1000),
+                        [0.0, 448.0, 2.0 ** -10, 3 * 2.0 ** -11, 1.0625, 1.1875, 17.0, 19.0]])
+    t = t.astype(np.float32)   # exactly representable: one rounding on both sides
+    ours = np.array([oracle.fp8_e4m3_nearest(float(v)) for v in t], dtype=np.uint8)
+    ref = torch.from_numpy(t).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(ours, ref)
+    assert oracle.fp8_e4m3_nearest(1e6) == 0x7E            # saturates at 448
+
+
+def test_bf16_round_matches_torch_and_neighbour_search():
+    rng = np.random.default_rng(9)
+    f32 = np.concatenate([rng.uniform(0, 1, 3000), rng.uniform(0, 1e-3, 500),
+                          [1.0, 1.00390625, 1.01171875, 2.0 ** -130]]).astype(np.float32)
+    ours = np.array([oracle.bf16_round(float(v)) for v in f32], dtype=np.uint16)
+    ref = torch.from_numpy(f32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(ours, ref)
+    # FP64 inputs (no exact FP32 form): the code is a nearest bf16, ties to even.
+    for v in rng.uniform(1e-3, 1.0, 500):
+        c = oracle.bf16_round(float(v))
+        err = abs(oracle.bf16_value(c) - v)
+        for nb in (c - 1, c + 1):
+            e2 = abs(oracle.bf16_value(nb) - v)
+            assert err < e2 or (err == e2 and c % 2 == 0)
+
+
+def test_u16_encoding_nearest_code():
+    A = dosegen.random_csr(100, 50, seed=14, density=0.3)
+    enc = oracle.encode(A, oracle.U16_SCALE)
+    s = float(enc.scales[0])
+    assert s == float(np.float32(A.val.max() / 65535.0))
+    t = A.val / s
+    q = enc.values.astype(np.float64)
+    assert np.all(np.abs(q - np.minimum(t, 65535.0)) <= 0.5)
+    ties = np.abs(q - t) == 0.5
+    assert np.all(q[ties] % 2 == 0)
+    assert np.array_equal(enc.decoded, s * q)
+    # Exact ties and the clamp, constructed by hand.
+    B = dosegen.CSR(1, 4, np.array([0, 4], dtype=np.uint32), np.arange(4, dtype=np.uint32),
+                    np.array([65535.0, 2.5, 3.5, 65534.5]) * 2.0 ** -10)
+    eb = oracle.encode(B, oracle.U16_SCALE)
+    assert eb.scales[0] == np.float32(2.0 ** -10)
+    assert list(eb.values) == [65535, 2, 4, 65534]
+
+
+def test_fp8_rowscale_encoding():
+    A = dosegen.random_csr(60, 30, seed=15, density=0.3, empty_frac=0.2)
+    enc = oracle.encode(A, oracle.FP8E4M3_ROWSCALE)
+    L = A.row_lengths()
+    for i in range(A.nrows):
+        k0, k1 = A.row_ptr[i], A.row_ptr[i + 1]
+        if L[i] == 0:
+            assert enc.scales[i] == 1.0
+            continue
+        s = enc.scales[i]
+        assert s == np.float32(A.val[k0:k1].max() / 448.0)
+        t = (A.val[k0:k1] / float(s)).astype(np.float32)
+        ref = torch.from_numpy(t).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+        exact32 = A.val[k0:k1] / float(s) == t.astype(np.float64)
+        assert np.array_equal(enc.values[k0:k1][exact32], ref[exact32])
+        # relative error of a normal E4M3 code is at most 2^-4
+        dec = enc.decoded[k0:k1]
+        normal = dec >= float(s) * 2.0 ** -6
+        assert np.all(np.abs(dec - A.val[k0:k1])[normal] <= 2.0 ** -4 * A.val[k0:k1][normal])
+
+
+def test_bf16_encoding_error_bound():
+    A = dosegen.random_csr(60, 30, seed=16, density=0.3)
+    enc = oracle.encode(A, oracle.BF16)
+    # 8 significant bits: unit roundoff 2^-8
+    assert np.all(np.abs(enc.decoded - A.val) <= 2.0 ** -8 * A.val)
+
+
+# ---------------------------------------------- printed values of the paper
+
+def _table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_dimensions.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, nr, nc, nnz, ratio, size = line.split()
+            rows.append((name, float(nr), float(nc), float(nnz), ratio, size))
+    return rows
+
+
+def _interval(printed: str):
+    """Rounding interval of a printed decimal (e.g. '8.880' -> [8.8795, 8.8805])."""
+    mant = printed.lower().split("e")[0]
+    dec = len(mant.split(".")[1]) if "." in mant else 0
+    exp = int(printed.lower().split("e")[1]) if "e" in printed.lower() else 0
+    half = 0.5 * 10.0 ** (exp - dec)
+    v = float(printed)
+    return v - half, v + half
+
+
+def test_operational_intensity_liver1_is_0332():
+    with open(os.path.join(GOLDEN, "operational_intensity.txt")) as f:
+        line = [ln for ln in f if not ln.startswith("#") and ln.strip()][0]
+    name, printed, digits = line.split()
+    t1 = {r[0]: r for r in _table1()}
+    _, nr, nc, nnz, _, _ = t1[name]
+    oi = oracle.paper_operational_intensity(nnz, nr, nc)
+    assert round(oi, int(digits)) == float(printed)
+    # A dropped row term or a 4-byte value width moves the third digit.
+    assert round(2 * nnz / (6 * nnz + 8 * nc), 3) != float(printed)
+    assert round(2 * nnz / (8 * nnz + 12 * nr + 8 * nc), 3) != float(printed)
+
+
+def test_table1_sizes_and_ratios_follow_csr_widths():
+    for name, nr, nc, nnz, ratio, size in _table1():
+        # printed nnz is rounded to 3 digits: the size must fall inside the model's range
+        n_lo, n_hi = _interval(f"{nnz:.2e}")
+        s_lo, s_hi = _interval(size)
+        m_lo = oracle.csr_storage_bytes(n_lo, nr) / 1e9
+        m_hi = oracle.csr_storage_bytes(n_hi, nr) / 1e9
+        assert m_lo <= s_hi and m_hi >= s_lo, name
+        # 4-byte values (FP32) would not fit any row
+        assert oracle.csr_storage_bytes(n_lo, nr, value_bytes=4) / 1e9 > s_hi, name
+        r_lo, r_hi = _interval(ratio)
+        dens = 100.0 * nnz / (nr * nc)
+        assert r_lo * 0.995 <= dens <= r_hi * 1.005, name
