@@ -1,0 +1,195 @@
+/*
+ * dose.h -- C ABI of libdose: the dose-deposition SpMV and its optimisation-step
+ * forms on one GB300 (sm_103a).
+ *
+ * The dose in the patient is one sparse matrix-vector product d = A x, where A
+ * is the dose-deposition matrix (rows = voxels, columns = beam spots) and x the
+ * spot weights; A is built once and only x changes across the optimiser's
+ * iterations (Sec. II-A).  A is stored in CSR with reduced-width values
+ * (Sec. II-C, Sec. II-D).  Results are bitwise reproducible for the same
+ * handle, inputs and GPU: no reduction anywhere depends on the order in which
+ * threads happen to run (Sec. II-D, second requirement).
+ *
+ * Conventions for every call below
+ *   - Plain pointers and sizes only.  "device" pointers are CUDA device memory of
+ *     the current device; "host" pointers are CPU memory.
+ *   - Compute calls (dose_spmv, dose_spmv_batched, dose_adjoint,
+ *     dose_fwd_adj_quadratic, dose_pg_step) are asynchronous on the caller's
+ *     cudaStream_t (passed as void*; NULL = legacy default stream).  They never
+ *     allocate, never synchronise the host, and may be captured in a CUDA graph.
+ *   - Output buffers are caller-owned and fully overwritten.  Inputs are never
+ *     modified (except x in dose_pg_step, documented there).
+ *   - A matrix handle is library-owned from dose_create_matrix to dose_destroy.
+ *     Calls that use the same handle must be ordered on one stream (the handle
+ *     owns the scratch of the adjoint reduction).
+ *   - Errors: every call returns a dose_status; dose_last_error() gives a
+ *     thread-local message for the last failure on the calling thread.  Invalid
+ *     arguments are rejected on the host before anything is launched.
+ */
+#ifndef DOSE_H
+#define DOSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dose_matrix dose_matrix; /* opaque, library-owned */
+
+typedef enum {
+    DOSE_OK = 0,
+    DOSE_ERR_INVALID_ARG = 1, /* bad pointer, size, structure or value */
+    DOSE_ERR_OOM = 2,         /* host or device allocation failed */
+    DOSE_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    DOSE_ERR_UNSUPPORTED = 4, /* valid request outside what this build implements */
+    DOSE_ERR_TIMEOUT = 5      /* a kernel's bounded wait ran out (dose_device_status) */
+} dose_status;
+
+/* Stored value formats.  The paper stores 16-bit values (Sec. II-D) without
+ * defining the encoding; these are the library's formats:
+ *   U16_SCALE        : uint16 code q, one FP32 scale s per matrix, a = s * q
+ *   BF16             : bfloat16 bits, a = value
+ *   FP8E4M3_ROWSCALE : OCP FP8 E4M3 code q, one FP32 scale s_r per row, a = s_r * e4m3(q) */
+typedef enum {
+    DOSE_FMT_U16_SCALE = 0,
+    DOSE_FMT_BF16 = 1,
+    DOSE_FMT_FP8E4M3_ROWSCALE = 2
+} dose_format;
+
+/* A CSR matrix (Sec. II-C: values, column indices, row starts).
+ *   nrows, ncols : voxels, spots.  nnz must be < 2^32 (row_ptr is uint32).
+ *   row_ptr      : nrows+1 entries, row_ptr[0] = 0, non-decreasing, row_ptr[nrows] = nnz.
+ *   col_idx      : nnz entries, each < ncols, unique within a row (any order).
+ *   fmt          : stored format of `values`.
+ *   values       : nnz encoded values (uint16 for U16/BF16, uint8 for FP8), or NULL
+ *                  to have the library encode `values_f64`.
+ *   scales       : U16: 1 float (s); FP8: nrows floats (s_r); BF16: NULL.  Ignored
+ *                  when the library encodes.
+ *   values_f64   : nnz non-negative FP64 values, used when values == NULL.
+ *   on_device    : 0 = all pointers are host memory; 1 = row_ptr, col_idx, values,
+ *                  scales are device memory (values_f64 must then be NULL).
+ * The library copies everything it needs; the caller's arrays can be freed after
+ * dose_create_matrix returns. */
+typedef struct {
+    uint32_t nrows;
+    uint32_t ncols;
+    uint64_t nnz;
+    const uint32_t* row_ptr;
+    const uint32_t* col_idx;
+    dose_format fmt;
+    const void* values;
+    const float* scales;
+    const double* values_f64;
+    int on_device;
+} dose_csr_desc;
+
+/* dose_create_matrix flags */
+#define DOSE_CREATE_COMPENSATED 0x1u /* compensated (TwoSum/TwoProduct) accumulation on rows
+                                        longer than 128 entries */
+
+/* Schedule knobs of a matrix (row-length binning and pipeline shape).  All
+ * fields 0 = library default.  Changing them never changes which rows an
+ * output depends on; it may change the last bits of FP32 results. */
+typedef struct {
+    uint32_t tile_nnz;       /* max entries staged per pipeline stage (256..16384) */
+    uint32_t tile_rows;      /* max rows per stage (32..8192) */
+    uint32_t coop_nnz;       /* rows longer than this are reduced by the whole CTA */
+    uint32_t lane_target;    /* lanes per row = power of two nearest mean row length / lane_target */
+    uint32_t stages;         /* pipeline depth (2..8) */
+    uint32_t consumer_warps; /* 4, 8 or 16 */
+} dose_tuning;
+
+typedef struct {
+    uint32_t nrows, ncols;
+    uint64_t nnz;
+    uint32_t fmt, flags;
+    uint32_t n_stages;          /* pipeline stages (row blocks) in the schedule */
+    uint32_t n_coop_rows;       /* rows reduced by a whole CTA */
+    uint32_t lanes_hist[6];     /* stages per lanes-per-row bin 1,2,4,8,16,32 */
+    uint32_t grid, block;       /* launch shape of the forward kernel */
+    uint32_t max_row_len;
+    uint64_t device_bytes;      /* device memory held by the handle */
+    uint64_t spmv_bytes;        /* algorithmic HBM bytes of one dose_spmv */
+    uint64_t adjoint_bytes;     /* ... of one dose_adjoint */
+    uint64_t fused_bytes;       /* ... of one dose_fwd_adj_quadratic with d == NULL */
+    float scale;                /* U16: the matrix scale s; else 0 */
+    dose_tuning tuning;         /* the knobs in effect */
+} dose_info;
+
+/* Build a matrix handle: validate the CSR on the host (or on the device for
+ * on_device=1, with a synchronising check), encode FP64 values if asked, build
+ * the row-binned pipeline schedule, copy everything to the device (enqueued on
+ * `stream`, synchronised before return).  flags: DOSE_CREATE_*.  `tuning` may be
+ * NULL (defaults).  On success *out is a new handle. */
+dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const dose_tuning* tuning,
+                               void* stream, dose_matrix** out);
+
+/* d = A x (Sec. II-A; Sec. III: one output per row, the row's dot product).
+ * x: device, ncols floats.  d: device, nrows floats, every row written (empty
+ * rows get 0).  FP32 accumulation; U16 and FP8 scales applied once per row. */
+dose_status dose_spmv(const dose_matrix* A, const float* x, float* d, void* stream);
+
+/* D_m = A_m X_m for m < count, all in one persistent launch (one dose evaluation
+ * of many beams and uncertainty scenarios, Sec. I).  X[m]: device, ncols_m x nvec
+ * floats row-major (spot j's nvec weights contiguous).  D[m]: device, nrows_m x
+ * nvec floats row-major.  1 <= nvec <= 16; count <= 4096.  The handles must be
+ * distinct only in the sense that their outputs must not overlap. */
+dose_status dose_spmv_batched(const dose_matrix* const* A, int count, const float* const* X,
+                              float* const* D, int nvec, void* stream);
+
+/* g = A^T r, the adjoint (gradient of any dose objective with dD/dd = r).
+ * r: device, nrows floats.  g: device, ncols floats.  Deterministic: per-warp
+ * private accumulators combined in a fixed order, no atomics on values. */
+dose_status dose_adjoint(const dose_matrix* A, const float* r, float* g, void* stream);
+
+/* One pass over A of the quadratic dose objective
+ *   d = A x,  f = sum_i w_i (d_i - p_i)^2 (FP64),  g = A^T [2 w (d - p)]
+ * x: device ncols floats; p, w: device nrows floats; d: device nrows floats or
+ * NULL (not written); f: device, one double; g: device ncols floats. */
+dose_status dose_fwd_adj_quadratic(const dose_matrix* A, const float* x, const float* p,
+                                   const float* w, float* d, double* f, float* g, void* stream);
+
+/* One projected-gradient step of the quadratic objective:
+ *   f = f(x), g = grad f(x), then x <- max(0, x - eta g)   (x updated in place)
+ * f: device double (f before the step), g: device floats or NULL. */
+dose_status dose_pg_step(const dose_matrix* A, float* x, const float* p, const float* w, float eta,
+                         double* f, float* g, void* stream);
+
+/* Free the handle and its device memory (synchronises the device first).  NULL -> DOSE_OK. */
+dose_status dose_destroy(dose_matrix* A);
+
+/* Describe a handle (sizes, schedule, algorithmic bytes of each call). */
+dose_status dose_matrix_info(const dose_matrix* A, dose_info* out);
+
+/* Re-schedule a handle with new knobs (synchronous; not during capture). */
+dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning);
+
+/* Time candidate schedules of dose_spmv on this GPU with x (device, ncols
+ * floats) and keep the fastest; the chosen knobs are returned in *best (may be
+ * NULL).  Synchronous; uses `stream`; not during capture. */
+dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tuning* best);
+
+/* Host-only encoder of the library's stored formats (no GPU needed):
+ * values_f64 (nnz, non-negative) -> codes (uint16 or uint8, nnz) and scales
+ * (U16: 1 float; FP8: nrows floats; BF16: untouched, may be NULL).  Uses
+ * row_ptr (host, nrows+1) for FP8 row scales. */
+dose_status dose_encode_host(dose_format fmt, uint32_t nrows, const uint32_t* row_ptr,
+                             uint64_t nnz, const double* values_f64, void* codes, float* scales);
+
+/* Synchronise `stream` and report a kernel-side failure recorded on the
+ * handle since the last call (DOSE_ERR_TIMEOUT if a bounded wait ran out), then
+ * clear it. */
+dose_status dose_device_status(const dose_matrix* A, void* stream);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* dose_last_error(void);
+
+/* Library version string. */
+const char* dose_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOSE_H */

@@ -1,0 +1,427 @@
+"""GB300-native dose-deposition SpMV (arXiv 2103.09683), Python binding.
+
+Argument marshalling over the C ABI of libdose.so (include/dose.h): every step
+of the dose calculation runs in the library's CUDA kernels.  PyTorch provides
+device memory, streams, CUDA graphs and autograd plumbing only.  There is no
+CPU fallback: if the library is missing, loading raises.
+
+    import paper_2103_09683_gb300 as dose
+    A = dose.DoseMatrix.from_csr(row_ptr, col, values_f64=val, ncols=nc, fmt="u16")
+    d = A.spmv(x)                      # d = A x          (Sec. II-A)
+    g = A.adjoint(r)                   # g = A^T r
+    f, g = A.fwd_adj_quadratic(x, p, w)   # one pass: d, f, gradient
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["build", "load", "DoseMatrix", "DoseError", "FORMATS", "spmv_batched", "dose_spmv",
+           "QuadraticDoseObjective", "pg_solve", "PGSolver", "encode_host", "library_path"]
+
+FORMATS = {"u16": 0, "bf16": 1, "fp8": 2}
+CREATE_COMPENSATED = 0x1
+_STATUS = {0: "DOSE_OK", 1: "DOSE_ERR_INVALID_ARG", 2: "DOSE_ERR_OOM", 3: "DOSE_ERR_CUDA",
+           4: "DOSE_ERR_UNSUPPORTED", 5: "DOSE_ERR_TIMEOUT"}
+
+
+class DoseError(RuntimeError):
+    """A libdose call returned an error status."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_uint32), ("ncols", ctypes.c_uint32), ("nnz", ctypes.c_uint64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("fmt", ctypes.c_int),
+                ("values", ctypes.c_void_p), ("scales", ctypes.c_void_p),
+                ("values_f64", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class Tuning(ctypes.Structure):
+    """Schedule knobs (0 = default); see dose_tuning in include/dose.h."""
+    _fields_ = [("tile_nnz", ctypes.c_uint32), ("tile_rows", ctypes.c_uint32),
+                ("coop_nnz", ctypes.c_uint32), ("lane_target", ctypes.c_uint32),
+                ("stages", ctypes.c_uint32), ("consumer_warps", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_uint32), ("ncols", ctypes.c_uint32), ("nnz", ctypes.c_uint64),
+                ("fmt", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("n_stages", ctypes.c_uint32), ("n_coop_rows", ctypes.c_uint32),
+                ("lanes_hist", ctypes.c_uint32 * 6), ("grid", ctypes.c_uint32),
+                ("block", ctypes.c_uint32), ("max_row_len", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64), ("spmv_bytes", ctypes.c_uint64),
+                ("adjoint_bytes", ctypes.c_uint64), ("fused_bytes", ctypes.c_uint64),
+                ("scale", ctypes.c_float), ("tuning", Tuning)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+EXPORTS = {
+    "dose_create_matrix": (ctypes.c_int, [_P, ctypes.c_uint, _P, _P, _P]),
+    "dose_spmv": (ctypes.c_int, [_P, _P, _P, _P]),
+    "dose_spmv_batched": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "dose_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
+    "dose_fwd_adj_quadratic": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "dose_pg_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
+    "dose_destroy": (ctypes.c_int, [_P]),
+    "dose_matrix_info": (ctypes.c_int, [_P, _P]),
+    "dose_set_tuning": (ctypes.c_int, [_P, _P]),
+    "dose_autotune": (ctypes.c_int, [_P, _P, _P, _P]),
+    "dose_encode_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, _P, ctypes.c_uint64, _P, _P, _P]),
+    "dose_device_status": (ctypes.c_int, [_P, _P]),
+    "dose_last_error": (ctypes.c_char_p, []),
+    "dose_version": (ctypes.c_char_p, []),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile libdose.so for sm_103a (nvcc) and return its path."""
+    return _build.build(force=force)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libdose.so (built by build()); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libdose.so is not built: call paper_2103_09683_gb300.build() first "
+                                   "(there is no CPU fallback)")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in EXPORTS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        msg = load().dose_last_error().decode(errors="replace")
+        raise DoseError(status, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype, n=None, what="tensor"):
+    """Device pointer of a contiguous CUDA tensor of the given dtype (and length)."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what} has {t.numel()} elements, expected {n}")
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() else ctypes.c_void_p(0)
+
+
+def encode_host(fmt: str, row_ptr: np.ndarray, values_f64: np.ndarray):
+    """The library's own encoder (host code, no GPU): returns (codes, scales)."""
+    lib = load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.uint32)
+    v = np.ascontiguousarray(values_f64, dtype=np.float64)
+    nrows = rp.size - 1
+    f = FORMATS[fmt]
+    codes = np.empty(v.size, dtype=np.uint8 if fmt == "fp8" else np.uint16)
+    scales = np.empty(nrows if fmt == "fp8" else 1, dtype=np.float32)
+    _check(lib.dose_encode_host(f, nrows, rp.ctypes.data, v.size, v.ctypes.data if v.size else None,
+                                codes.ctypes.data if codes.size else None, scales.ctypes.data))
+    return codes, (None if fmt == "bf16" else scales)
+
+
+class DoseMatrix:
+    """A dose-deposition matrix resident on the GPU (library-owned handle)."""
+
+    def __init__(self, handle, nrows, ncols, nnz, fmt):
+        self._h = ctypes.c_void_p(handle)
+        self.nrows, self.ncols, self.nnz, self.fmt = nrows, ncols, nnz, fmt
+
+    # ---- construction
+    @classmethod
+    def from_csr(cls, row_ptr, col, *, ncols: int, fmt: str = "u16", values=None, scales=None,
+                 values_f64=None, compensated: bool = False, tuning: dict | None = None, stream=None):
+        """Create from host (numpy) or device (torch CUDA) CSR arrays.
+
+        Pass either encoded `values` (+ `scales`) in the stored format, or
+        `values_f64` (host) to let the library encode.
+        """
+        torch = _torch()
+        lib = load()
+        on_dev = isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda
+        keep = []
+
+        def host(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data if a.size else None
+
+        def dev(a, dt, what):
+            p = _dptr(a, dt, what=what)
+            keep.append(a)
+            return p.value
+
+        nrows = int(row_ptr.shape[0]) - 1
+        nnz = int(col.shape[0])
+        d = _Desc()
+        d.nrows, d.ncols, d.nnz, d.fmt = nrows, int(ncols), nnz, FORMATS[fmt]
+        d.on_device = 1 if on_dev else 0
+        vdt_np = np.uint8 if fmt == "fp8" else np.uint16
+        if on_dev:
+            d.row_ptr = dev(row_ptr, torch.int32, "row_ptr") if row_ptr.dtype == torch.int32 else \
+                dev(row_ptr.view(torch.int32), torch.int32, "row_ptr")
+            d.col_idx = dev(col if col.dtype == torch.int32 else col.view(torch.int32), torch.int32, "col")
+            if values is None:
+                raise ValueError("device CSR needs encoded values")
+            vt = torch.uint8 if fmt == "fp8" else torch.int16
+            d.values = dev(values if values.dtype == vt else values.view(vt), vt, "values")
+            if fmt != "bf16":
+                d.scales = dev(scales, torch.float32, "scales")
+        else:
+            d.row_ptr = host(row_ptr, np.uint32)
+            d.col_idx = host(col, np.uint32)
+            if values is not None:
+                d.values = host(values, vdt_np)
+                if fmt != "bf16":
+                    d.scales = host(np.asarray(scales, dtype=np.float32).reshape(-1), np.float32)
+            elif values_f64 is not None:
+                d.values_f64 = host(values_f64, np.float64)
+            else:
+                raise ValueError("give values (+scales) or values_f64")
+        t = None
+        if tuning:
+            t = Tuning(**{k: int(v) for k, v in tuning.items()})
+        out = ctypes.c_void_p()
+        stream_h = _stream_handle(stream) if torch.cuda.is_available() else ctypes.c_void_p(0)
+        _check(lib.dose_create_matrix(ctypes.byref(d), CREATE_COMPENSATED if compensated else 0,
+                                      ctypes.byref(t) if t is not None else None, stream_h,
+                                      ctypes.byref(out)))
+        return cls(out.value, nrows, int(ncols), nnz, fmt)
+
+    def close(self):
+        if self._h and self._h.value:
+            load().dose_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ---- compute (asynchronous on the current or given stream)
+    def spmv(self, x, d=None, stream=None):
+        """d = A x.  x: CUDA float32 [ncols]; d (optional): CUDA float32 [nrows]."""
+        torch = _torch()
+        if d is None:
+            d = torch.empty(self.nrows, dtype=torch.float32, device=x.device)
+        _check(load().dose_spmv(self._h, _dptr(x, torch.float32, self.ncols, "x"),
+                                _dptr(d, torch.float32, self.nrows, "d"), _stream_handle(stream)))
+        return d
+
+    def adjoint(self, r, g=None, stream=None):
+        """g = A^T r.  r: CUDA float32 [nrows]."""
+        torch = _torch()
+        if g is None:
+            g = torch.empty(self.ncols, dtype=torch.float32, device=r.device)
+        _check(load().dose_adjoint(self._h, _dptr(r, torch.float32, self.nrows, "r"),
+                                   _dptr(g, torch.float32, self.ncols, "g"), _stream_handle(stream)))
+        return g
+
+    def fwd_adj_quadratic(self, x, p, w, d=None, f=None, g=None, stream=None, want_d=False):
+        """One pass: f = sum w (Ax - p)^2 (FP64 device scalar) and g = grad f."""
+        torch = _torch()
+        dev = x.device
+        if f is None:
+            f = torch.empty(1, dtype=torch.float64, device=dev)
+        if g is None:
+            g = torch.empty(self.ncols, dtype=torch.float32, device=dev)
+        if d is None and want_d:
+            d = torch.empty(self.nrows, dtype=torch.float32, device=dev)
+        dptr = _dptr(d, torch.float32, self.nrows, "d") if d is not None else None
+        _check(load().dose_fwd_adj_quadratic(
+            self._h, _dptr(x, torch.float32, self.ncols, "x"), _dptr(p, torch.float32, self.nrows, "p"),
+            _dptr(w, torch.float32, self.nrows, "w"), dptr, _dptr(f, torch.float64, 1, "f"),
+            _dptr(g, torch.float32, self.ncols, "g"), _stream_handle(stream)))
+        return (f, g, d) if want_d else (f, g)
+
+    def pg_step(self, x, p, w, eta: float, f=None, g=None, stream=None):
+        """x <- max(0, x - eta grad f(x)) in place; returns f(x) before the step."""
+        torch = _torch()
+        if f is None:
+            f = torch.empty(1, dtype=torch.float64, device=x.device)
+        gptr = _dptr(g, torch.float32, self.ncols, "g") if g is not None else None
+        _check(load().dose_pg_step(self._h, _dptr(x, torch.float32, self.ncols, "x"),
+                                   _dptr(p, torch.float32, self.nrows, "p"),
+                                   _dptr(w, torch.float32, self.nrows, "w"), ctypes.c_float(eta),
+                                   _dptr(f, torch.float64, 1, "f"), gptr, _stream_handle(stream)))
+        return f
+
+    # ---- schedule
+    def info(self) -> dict:
+        inf = _Info()
+        _check(load().dose_matrix_info(self._h, ctypes.byref(inf)))
+        out = {k: getattr(inf, k) for k, _ in _Info._fields_ if k not in ("lanes_hist", "tuning")}
+        out["lanes_hist"] = list(inf.lanes_hist)
+        out["tuning"] = inf.tuning.as_dict()
+        return out
+
+    def set_tuning(self, **knobs):
+        t = Tuning(**{k: int(v) for k, v in knobs.items()})
+        _check(load().dose_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, x, stream=None) -> dict:
+        torch = _torch()
+        t = Tuning()
+        _check(load().dose_autotune(self._h, _dptr(x, torch.float32, self.ncols, "x"),
+                                    _stream_handle(stream), ctypes.byref(t)))
+        return t.as_dict()
+
+    def device_status(self, stream=None):
+        """Synchronise and raise DoseError if a kernel recorded a failure."""
+        _check(load().dose_device_status(self._h, _stream_handle(stream)))
+
+
+def spmv_batched(mats, Xs, Ds=None, stream=None):
+    """D_m = A_m X_m for all m in one launch.  X_m: CUDA float32 [ncols_m, nvec]."""
+    torch = _torch()
+    n = len(mats)
+    if n == 0:
+        return []
+    nvec = int(Xs[0].shape[1]) if Xs[0].dim() == 2 else 1
+    if Ds is None:
+        Ds = [torch.empty((A.nrows, nvec), dtype=torch.float32, device=Xs[0].device) for A in mats]
+    hs = (ctypes.c_void_p * n)(*[A.handle.value for A in mats])
+    xp = (ctypes.c_void_p * n)(*[_dptr(X, torch.float32, A.ncols * nvec, "X").value
+                                 for A, X in zip(mats, Xs)])
+    dp = (ctypes.c_void_p * n)(*[_dptr(D, torch.float32, A.nrows * nvec, "D").value
+                                 for A, D in zip(mats, Ds)])
+    _check(load().dose_spmv_batched(hs, n, xp, dp, nvec, _stream_handle(stream)))
+    return Ds
+
+
+# ------------------------------------------------------------------ autograd
+
+def _autograd():
+    torch = _torch()
+
+    class _DoseSpMV(torch.autograd.Function):
+        """d = A x with backward g = A^T grad_d (the hand-written adjoint kernel)."""
+
+        @staticmethod
+        def forward(ctx, x, A):
+            ctx.A = A
+            return A.spmv(x.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad_d):
+            return ctx.A.adjoint(grad_d.contiguous().float()), None
+
+    class _Quadratic(torch.autograd.Function):
+        """f(x) = sum w (A x - p)^2 in one fused pass; backward scales the saved gradient."""
+
+        @staticmethod
+        def forward(ctx, x, A, p, w):
+            f, g = A.fwd_adj_quadratic(x.contiguous(), p, w)
+            ctx.save_for_backward(g)
+            return f.reshape(())
+
+        @staticmethod
+        def backward(ctx, grad_f):
+            (g,) = ctx.saved_tensors
+            return (grad_f.to(g.dtype) * g), None, None, None
+
+    return _DoseSpMV, _Quadratic
+
+
+_AG = None
+
+
+def dose_spmv(A: DoseMatrix, x):
+    """Differentiable d = A x (torch.autograd): backward runs dose_adjoint."""
+    global _AG
+    if _AG is None:
+        _AG = _autograd()
+    return _AG[0].apply(x, A)
+
+
+def QuadraticDoseObjective(A: DoseMatrix, x, p, w):
+    """Differentiable f = sum_i w_i (d_i - p_i)^2 (FP64 scalar), d = A x."""
+    global _AG
+    if _AG is None:
+        _AG = _autograd()
+    return _AG[1].apply(x, A, p, w)
+
+
+class PGSolver:
+    """Projected-gradient iterations x <- max(0, x - eta grad f) captured once in a
+    CUDA graph (torch.cuda.CUDAGraph) and replayed: `iters` dose_pg_step calls per
+    replay, f of every step written to a device buffer."""
+
+    def __init__(self, A: DoseMatrix, x, p, w, eta: float, iters: int, use_graph: bool = True):
+        torch = _torch()
+        self.A, self.x, self.p, self.w, self.eta, self.iters = A, x, p, w, float(eta), int(iters)
+        self.f_hist = torch.zeros(self.iters, dtype=torch.float64, device=x.device)
+        self.graph = None
+        if use_graph:
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=s):
+                self._enqueue(s)
+            torch.cuda.current_stream().wait_stream(s)
+
+    def _enqueue(self, stream):
+        for k in range(self.iters):
+            self.A.pg_step(self.x, self.p, self.w, self.eta, f=self.f_hist[k:k + 1], stream=stream)
+
+    def run(self):
+        """Run `iters` steps (one graph launch when captured); returns f_hist."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._enqueue(None)
+        return self.f_hist
+
+
+def pg_solve(A: DoseMatrix, x, p, w, eta: float, iters: int = 100, use_graph: bool = True):
+    """Run `iters` projected-gradient steps on x (in place); returns f per step."""
+    return PGSolver(A, x, p, w, eta, iters, use_graph).run()

@@ -1,0 +1,637 @@
+// Host side of libdose: the C ABI declared in include/dose.h.
+//
+// dose_create_matrix validates the CSR (Sec. II-C layout), encodes FP64 values
+// into the stored format if asked, builds the row-binned pipeline schedule and
+// uploads everything once: the dose-deposition matrix does not change during
+// the optimisation, only the spot weights do (Sec. II-A).  Compute calls only
+// enqueue kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dose_internal.cuh"
+
+namespace dose {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+dose_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return DOSE_ERR_CUDA;
+}
+
+static dose_status invalid(const std::string& msg) {
+    set_error(msg);
+    return DOSE_ERR_INVALID_ARG;
+}
+
+// ------------------------------------------------------------- encoders
+// Library encoders of the stored formats (same definitions as the format
+// comments in dose.h; written independently of any checker).
+
+// Round-to-nearest-even of a double to 8 significant bits (bfloat16), by
+// rounding the binary64 significand at bit 45.
+static uint16_t encode_bf16(double v) {
+    if (std::isnan(v)) return 0x7FC0;
+    const uint16_t sign = std::signbit(v) ? 0x8000 : 0;
+    const double a = std::fabs(v);
+    float f;
+    if (a < 0x1p-126) {
+        f = (float)(std::rint(a * 0x1p133) * 0x1p-133);  // bf16 subnormal quantum 2^-133
+    } else {
+        uint64_t u;
+        std::memcpy(&u, &a, 8);
+        const uint64_t lsb = (u >> 45) & 1u;
+        u += 0x0FFFFFFFFFFFull + lsb;  // half of the dropped 45 bits, minus one, plus the kept LSB
+        u &= ~0x1FFFFFFFFFFFull;
+        double r;
+        std::memcpy(&r, &u, 8);
+        f = r > 0x1.FEp127 ? INFINITY : (float)r;
+    }
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    return (uint16_t)(sign | (b >> 16));
+}
+
+// Nearest OCP E4M3 code of a non-negative finite t, ties to the even code,
+// saturating at 448 (code 0x7E).
+static uint8_t encode_e4m3(double t) {
+    if (!(t > 0)) return 0;
+    if (t >= 448.0) return 0x7E;
+    if (t < 0x1p-6) {  // subnormal range: quantum 2^-9 (q = 8 is the smallest normal)
+        return (uint8_t)std::rint(t * 0x1p9);
+    }
+    int ex;
+    const double f = std::frexp(t, &ex);  // t = f 2^ex, f in [0.5, 1)
+    int e = ex - 1;                       // t = (2f) 2^e, 2f in [1, 2)
+    double m = std::rint((2.0 * f - 1.0) * 8.0);
+    if (m == 8.0) {
+        m = 0.0;
+        ++e;
+    }
+    const int code = ((e + 7) << 3) | (int)m;
+    return code > 0x7E ? (uint8_t)0x7E : (uint8_t)code;
+}
+
+static dose_status encode(dose_format fmt, uint32_t nrows, const uint32_t* row_ptr, uint64_t nnz,
+                          const double* v, void* codes, float* scales) {
+    for (uint64_t k = 0; k < nnz; ++k)
+        if (!(v[k] >= 0.0) || std::isinf(v[k])) return invalid("values_f64 must be finite and non-negative");
+    if (fmt == DOSE_FMT_U16_SCALE) {
+        double vmax = 0.0;
+        for (uint64_t k = 0; k < nnz; ++k) vmax = std::max(vmax, v[k]);
+        float s = vmax > 0.0 ? (float)(vmax / 65535.0) : 1.0f;
+        if (!(s > 0.0f)) s = 1.0f;
+        scales[0] = s;
+        uint16_t* q = static_cast<uint16_t*>(codes);
+        const double sd = s;
+        for (uint64_t k = 0; k < nnz; ++k) {
+            const double t = std::rint(v[k] / sd);
+            q[k] = (uint16_t)(t > 65535.0 ? 65535.0 : t);
+        }
+        return DOSE_OK;
+    }
+    if (fmt == DOSE_FMT_BF16) {
+        uint16_t* q = static_cast<uint16_t*>(codes);
+        for (uint64_t k = 0; k < nnz; ++k) q[k] = encode_bf16(v[k]);
+        return DOSE_OK;
+    }
+    if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {
+        uint8_t* q = static_cast<uint8_t*>(codes);
+        for (uint32_t i = 0; i < nrows; ++i) {
+            double rmax = 0.0;
+            for (uint64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) rmax = std::max(rmax, v[k]);
+            float s = rmax > 0.0 ? (float)(rmax / 448.0) : 1.0f;
+            if (!(s > 0.0f)) s = 1.0f;
+            scales[i] = s;
+            const double sd = s;
+            for (uint64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) q[k] = encode_e4m3(v[k] / sd);
+        }
+        return DOSE_OK;
+    }
+    return invalid("unknown format");
+}
+
+// ------------------------------------------------------------ schedule
+
+static uint32_t nearest_pow2_log2(double v) {
+    if (!(v > 1.0)) return 0;
+    int lg = (int)std::lround(std::log2(v));
+    return (uint32_t)std::min(5, std::max(0, lg));
+}
+
+static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, const Tuning& t, uint32_t grid) {
+    Schedule S;
+    uint32_t r = 0;
+    while (r < nrows) {
+        const uint32_t len = rp[r + 1] - rp[r];
+        if (len > t.coop_nnz) {
+            const uint32_t nch = (len + t.tile_nnz - 1) / t.tile_nnz;
+            for (uint32_t c = 0; c < nch; ++c) {
+                S.row0.push_back(r);
+                S.nz0.push_back(rp[r] + c * t.tile_nnz);
+                uint8_t m = STAGE_COOP;
+                if (c == 0) m |= STAGE_FIRST;
+                if (c + 1 == nch) m |= STAGE_LAST;
+                S.meta.push_back(m);
+            }
+            ++S.n_coop_rows;
+            ++r;
+            continue;
+        }
+        const uint32_t start = r;
+        uint64_t nz = 0;
+        uint32_t nonempty = 0;
+        while (r < nrows && r - start < t.tile_rows) {
+            const uint32_t l = rp[r + 1] - rp[r];
+            if (l > t.coop_nnz || nz + l > t.tile_nnz) break;
+            nz += l;
+            nonempty += l > 0;
+            ++r;
+        }
+        const double mean = nonempty ? (double)nz / nonempty : 0.0;
+        const uint32_t lg = nonempty ? nearest_pow2_log2(mean / t.lane_target) : 5;
+        S.row0.push_back(start);
+        S.nz0.push_back(rp[start]);
+        S.meta.push_back((uint8_t)lg);
+        ++S.lanes_hist[lg];
+    }
+    S.row0.push_back(nrows);
+    S.nz0.push_back(rp[nrows]);
+
+    // Contiguous stage ranges per CTA, balanced by streamed bytes; never split
+    // the chunks of one long row across CTAs.
+    const size_t n = S.meta.size();
+    std::vector<double> wcum(n + 1, 0.0);
+    for (size_t s = 0; s < n; ++s) {
+        const double rows = (S.meta[s] & STAGE_COOP) ? 0.0 : (double)(S.row0[s + 1] - S.row0[s]);
+        wcum[s + 1] = wcum[s] + 6.0 * (S.nz0[s + 1] - S.nz0[s]) + 8.0 * rows + 256.0;
+    }
+    S.cta_begin.assign(grid + 1, (uint32_t)n);
+    S.cta_begin[0] = 0;
+    size_t s = 0;
+    for (uint32_t c = 1; c < grid; ++c) {
+        const double target = wcum[n] * c / grid;
+        while (s < n && wcum[s] < target) ++s;
+        while (s < n && (S.meta[s] & STAGE_COOP) && !(S.meta[s] & STAGE_FIRST)) ++s;
+        S.cta_begin[c] = (uint32_t)std::max<size_t>(s, S.cta_begin[c - 1]);
+    }
+    S.cta_begin[grid] = (uint32_t)n;
+    return S;
+}
+
+// ------------------------------------------------------------ handle state
+
+struct DevFree {
+    void operator()(void* p) const {
+        if (p) cudaFree(p);
+    }
+};
+
+static void free_schedule(dose_matrix* A) {
+    cudaFree(A->st_row0);
+    cudaFree(A->st_nz0);
+    cudaFree(A->st_meta);
+    cudaFree(A->st_cta_begin);
+    A->st_row0 = A->st_nz0 = A->st_cta_begin = nullptr;
+    A->st_meta = nullptr;
+}
+
+static void free_all(dose_matrix* A) {
+    free_schedule(A);
+    cudaFree(A->row_ptr);
+    cudaFree(A->col);
+    cudaFree(A->val);
+    cudaFree(A->row_scale);
+    cudaFree(A->g_part);
+    cudaFree(A->f_part);
+    cudaFree(A->err);
+}
+
+static dose_status check_tuning(const dose_matrix* A, Tuning& t) {
+    if (t.tile_nnz < 256 || t.tile_nnz > 16384) return invalid("tuning.tile_nnz must be in [256, 16384]");
+    if (t.tile_rows < 32 || t.tile_rows > 8192) return invalid("tuning.tile_rows must be in [32, 8192]");
+    if (t.coop_nnz < 32 || t.coop_nnz > t.tile_nnz) return invalid("tuning.coop_nnz must be in [32, tile_nnz]");
+    if (t.lane_target < 1 || t.lane_target > 64) return invalid("tuning.lane_target must be in [1, 64]");
+    if (t.stages < 2 || t.stages > 8) return invalid("tuning.stages must be in [2, 8]");
+    if (t.consumer_warps != 4 && t.consumer_warps != 8 && t.consumer_warps != 16)
+        return invalid("tuning.consumer_warps must be 4, 8 or 16");
+    if (spmv_smem_bytes(A, t, spmv_x_in_smem(A)) > kMaxSmemPerBlock)
+        return invalid("tuning needs more shared memory than a CTA has");
+    return DOSE_OK;
+}
+
+static Tuning merge_tuning(const Tuning& base, const dose_tuning* in) {
+    Tuning t = base;
+    if (!in) return t;
+    if (in->tile_nnz) t.tile_nnz = in->tile_nnz;
+    if (in->tile_rows) t.tile_rows = in->tile_rows;
+    if (in->coop_nnz) t.coop_nnz = in->coop_nnz;
+    if (in->lane_target) t.lane_target = in->lane_target;
+    if (in->stages) t.stages = in->stages;
+    if (in->consumer_warps) t.consumer_warps = in->consumer_warps;
+    return t;
+}
+
+template <class T>
+static cudaError_t upload(T** dst, const T* src, size_t n, size_t alloc_n) {
+    cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(alloc_n, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(*dst, 0, std::max<size_t>(alloc_n, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+static dose_status apply_schedule(dose_matrix* A, const Tuning& t) {
+    Schedule S = build_schedule(A->host_row_ptr, A->nrows, t, A->grid);
+    free_schedule(A);
+    cudaError_t e;
+    if ((e = upload(&A->st_row0, S.row0.data(), S.row0.size(), S.row0.size())) != cudaSuccess ||
+        (e = upload(&A->st_nz0, S.nz0.data(), S.nz0.size(), S.nz0.size())) != cudaSuccess ||
+        (e = upload(&A->st_meta, S.meta.data(), S.meta.size(), S.meta.size() + 16)) != cudaSuccess ||
+        (e = upload(&A->st_cta_begin, S.cta_begin.data(), S.cta_begin.size(), S.cta_begin.size())) != cudaSuccess)
+        return cuda_fail(e, "uploading the schedule");
+    A->n_stages = (uint32_t)S.meta.size();
+    A->n_coop_rows = S.n_coop_rows;
+    std::memcpy(A->lanes_hist, S.lanes_hist, sizeof(A->lanes_hist));
+    A->tuning = t;
+    return DOSE_OK;
+}
+
+static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace dose
+
+using namespace dose;
+
+extern "C" {
+
+const char* dose_last_error(void) { return g_last_error.c_str(); }
+
+const char* dose_version(void) { return "libdose 0.1 (sm_103a)"; }
+
+dose_status dose_encode_host(dose_format fmt, uint32_t nrows, const uint32_t* row_ptr, uint64_t nnz,
+                             const double* values_f64, void* codes, float* scales) {
+    if ((nnz && (!values_f64 || !codes)) || !row_ptr) return invalid("dose_encode_host: null pointer");
+    if (fmt != DOSE_FMT_BF16 && !scales) return invalid("dose_encode_host: scales needed for this format");
+    return encode(fmt, nrows, row_ptr, nnz, values_f64, codes, scales);
+}
+
+dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const dose_tuning* tuning, void* stream,
+                               dose_matrix** out) {
+    if (!desc || !out) return invalid("dose_create_matrix: null desc or out");
+    *out = nullptr;
+    if (flags & ~DOSE_CREATE_COMPENSATED) return invalid("dose_create_matrix: unknown flags");
+    const dose_format fmt = desc->fmt;
+    if (fmt != DOSE_FMT_U16_SCALE && fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_FP8E4M3_ROWSCALE)
+        return invalid("dose_create_matrix: unknown format");
+    if (desc->nnz >= (1ull << 32)) return invalid("nnz must be < 2^32 (uint32 row pointers)");
+    if (desc->nrows == 0xFFFFFFFFu) return invalid("nrows must be < 2^32 - 1");
+    if (!desc->row_ptr) return invalid("row_ptr is NULL");
+    if (desc->nnz && !desc->col_idx) return invalid("col_idx is NULL");
+    if (desc->on_device && desc->values_f64) return invalid("values_f64 must be host memory (on_device=0)");
+    if (!desc->values && !desc->values_f64 && desc->nnz) return invalid("neither values nor values_f64 given");
+    if (desc->values && fmt != DOSE_FMT_BF16 && !desc->scales) return invalid("scales are NULL for this format");
+    const uint32_t nrows = desc->nrows, ncols = desc->ncols;
+    const uint64_t nnz = desc->nnz;
+    const size_t esize = fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    cudaStream_t s = as_stream(stream);
+
+    // Bring the structure to the host (validation and scheduling need it).
+    std::vector<uint32_t> rp(nrows + 1), col(nnz);
+    std::vector<unsigned char> vals;
+    std::vector<float> scl;
+    cudaError_t e;
+    if (desc->on_device) {
+        if ((e = cudaMemcpyAsync(rp.data(), desc->row_ptr, rp.size() * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "reading row_ptr");
+        if (nnz && (e = cudaMemcpyAsync(col.data(), desc->col_idx, nnz * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "reading col_idx");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "reading the CSR");
+    } else {
+        std::memcpy(rp.data(), desc->row_ptr, rp.size() * 4);
+        if (nnz) std::memcpy(col.data(), desc->col_idx, nnz * 4);
+    }
+    if (rp[0] != 0) return invalid("row_ptr[0] must be 0");
+    if (rp[nrows] != nnz) return invalid("row_ptr[nrows] must equal nnz");
+    uint32_t max_len = 0;
+    for (uint32_t i = 0; i < nrows; ++i) {
+        if (rp[i + 1] < rp[i]) return invalid("row_ptr must be non-decreasing (row " + std::to_string(i) + ")");
+        max_len = std::max(max_len, rp[i + 1] - rp[i]);
+    }
+    {
+        std::vector<uint32_t> stamp(ncols, 0xFFFFFFFFu);
+        for (uint32_t i = 0; i < nrows; ++i) {
+            for (uint32_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const uint32_t c = col[k];
+                if (c >= ncols)
+                    return invalid("col_idx[" + std::to_string(k) + "] = " + std::to_string(c) + " >= ncols");
+                if (stamp[c] == i)
+                    return invalid("duplicate column " + std::to_string(c) + " in row " + std::to_string(i));
+                stamp[c] = i;
+            }
+        }
+    }
+    // Values: encode FP64 on the host, or take the given codes.
+    float scale = 1.0f;
+    if (!desc->values) {
+        vals.resize(nnz * esize);
+        scl.resize(fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? std::max<uint32_t>(nrows, 1) : 1);
+        dose_status st = encode(fmt, nrows, rp.data(), nnz, desc->values_f64, vals.data(), scl.data());
+        if (st != DOSE_OK) return st;
+    } else {
+        vals.resize(nnz * esize);
+        scl.resize(fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? nrows : (fmt == DOSE_FMT_U16_SCALE ? 1 : 0));
+        if (desc->on_device) {
+            if (nnz && (e = cudaMemcpyAsync(vals.data(), desc->values, nnz * esize, cudaMemcpyDeviceToHost, s)) !=
+                           cudaSuccess)
+                return cuda_fail(e, "reading values");
+            if (!scl.empty() && (e = cudaMemcpyAsync(scl.data(), desc->scales, scl.size() * 4,
+                                                     cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return cuda_fail(e, "reading scales");
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "reading values");
+        } else {
+            if (nnz) std::memcpy(vals.data(), desc->values, nnz * esize);
+            if (!scl.empty()) std::memcpy(scl.data(), desc->scales, scl.size() * 4);
+        }
+        for (float v : scl)
+            if (!(v > 0.0f) || std::isinf(v)) return invalid("scales must be finite and positive");
+        if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE)
+            for (uint64_t k = 0; k < nnz; ++k)
+                if ((vals[k] & 0x7F) == 0x7F) return invalid("FP8 code is NaN at entry " + std::to_string(k));
+    }
+    if (fmt == DOSE_FMT_U16_SCALE) scale = scl.empty() ? 1.0f : scl[0];
+
+    std::unique_ptr<dose_matrix> A(new dose_matrix());
+    A->nrows = nrows;
+    A->ncols = ncols;
+    A->nnz = nnz;
+    A->fmt = fmt;
+    A->flags = flags;
+    A->scale = scale;
+    A->max_row_len = max_len;
+    if ((e = cudaGetDevice(&A->device)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&A->sm_count, cudaDevAttrMultiProcessorCount, A->device)) != cudaSuccess)
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    A->grid = (uint32_t)std::max(1, A->sm_count);
+    A->host_row_ptr = std::move(rp);
+    Tuning t = merge_tuning(Tuning(), tuning);
+    {
+        dose_status st = check_tuning(A.get(), t);
+        if (st != DOSE_OK) return st;
+    }
+    auto fail = [&](cudaError_t err, const char* what) {
+        free_all(A.get());
+        return err == cudaErrorMemoryAllocation ? (set_error(std::string(what) + ": out of device memory"),
+                                                   DOSE_ERR_OOM)
+                                                : cuda_fail(err, what);
+    };
+    const size_t rp_alloc = ((size_t)nrows + 1 + 3) / 4 * 4 + 16;
+    const size_t col_alloc = ((size_t)nnz + 3) / 4 * 4 + 16;
+    const size_t val_alloc = ((size_t)nnz * esize + 15) / 16 * 16 + 64;
+    if ((e = upload(&A->row_ptr, A->host_row_ptr.data(), (size_t)nrows + 1, rp_alloc)) != cudaSuccess)
+        return fail(e, "row_ptr");
+    if ((e = upload(&A->col, col.data(), (size_t)nnz, col_alloc)) != cudaSuccess) return fail(e, "col_idx");
+    if ((e = upload((unsigned char**)&A->val, vals.data(), vals.size(), val_alloc)) != cudaSuccess)
+        return fail(e, "values");
+    if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE &&
+        (e = upload(&A->row_scale, scl.data(), (size_t)nrows, (size_t)nrows + 16)) != cudaSuccess)
+        return fail(e, "row scales");
+    if ((e = cudaMalloc(&A->g_part, std::max<size_t>((size_t)A->grid * ncols, 1) * 4)) != cudaSuccess)
+        return fail(e, "adjoint partials");
+    if ((e = cudaMalloc(&A->f_part, (size_t)A->grid * 8)) != cudaSuccess) return fail(e, "objective partials");
+    if ((e = cudaMalloc(&A->err, sizeof(int))) != cudaSuccess) return fail(e, "error word");
+    if ((e = cudaMemset(A->err, 0, sizeof(int))) != cudaSuccess) return fail(e, "error word");
+    {
+        dose_status st = apply_schedule(A.get(), t);
+        if (st != DOSE_OK) {
+            free_all(A.get());
+            return st;
+        }
+    }
+    A->device_bytes = rp_alloc * 4 + col_alloc * 4 + val_alloc +
+                      (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) +
+                      (size_t)A->grid * ncols * 4 + (size_t)A->grid * 8 + 4 +
+                      (size_t)(A->n_stages + 1) * 9 + (A->grid + 1) * 4;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "create");
+    *out = A.release();
+    return DOSE_OK;
+}
+
+dose_status dose_destroy(dose_matrix* A) {
+    if (!A) return DOSE_OK;
+    cudaDeviceSynchronize();
+    free_all(A);
+    delete A;
+    return DOSE_OK;
+}
+
+dose_status dose_spmv(const dose_matrix* A, const float* x, float* d, void* stream) {
+    if (!A) return invalid("dose_spmv: null matrix");
+    if (A->nrows && !d) return invalid("dose_spmv: d is NULL");
+    if (A->ncols && !x) return invalid("dose_spmv: x is NULL");
+    cudaError_t e = launch_spmv(A, x, d, as_stream(stream));
+    return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_spmv launch");
+}
+
+static dose_status adjoint_supported(const dose_matrix* A, bool quad) {
+    if (quad && A->ncols > kXSmemMaxCols) {
+        set_error("the fused objective pass keeps x in shared memory: ncols must be <= 16384");
+        return DOSE_ERR_UNSUPPORTED;
+    }
+    Tuning t = A->tuning;
+    if (t.stages > 3) t.stages = 3;
+    if (adjoint_warps(A, t, quad, kMaxSmemPerBlock) == 0) {
+        set_error("per-warp gradient accumulators of ncols floats do not fit in shared memory");
+        return DOSE_ERR_UNSUPPORTED;
+    }
+    return DOSE_OK;
+}
+
+dose_status dose_adjoint(const dose_matrix* A, const float* r, float* g, void* stream) {
+    if (!A) return invalid("dose_adjoint: null matrix");
+    if (A->nrows && !r) return invalid("dose_adjoint: r is NULL");
+    if (A->ncols && !g) return invalid("dose_adjoint: g is NULL");
+    dose_status st = adjoint_supported(A, false);
+    if (st != DOSE_OK) return st;
+    cudaError_t e = launch_adjoint(A, ADJ_MODE_ADJOINT, nullptr, nullptr, nullptr, r, nullptr, nullptr, g, nullptr,
+                                   0.f, as_stream(stream));
+    return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_adjoint launch");
+}
+
+dose_status dose_fwd_adj_quadratic(const dose_matrix* A, const float* x, const float* p, const float* w, float* d,
+                                   double* f, float* g, void* stream) {
+    if (!A) return invalid("dose_fwd_adj_quadratic: null matrix");
+    if (!f || (A->ncols && (!x || !g)) || (A->nrows && (!p || !w)))
+        return invalid("dose_fwd_adj_quadratic: null pointer argument");
+    dose_status st = adjoint_supported(A, true);
+    if (st != DOSE_OK) return st;
+    cudaError_t e = launch_adjoint(A, ADJ_MODE_QUADRATIC, x, p, w, nullptr, d, f, g, nullptr, 0.f, as_stream(stream));
+    return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_fwd_adj_quadratic launch");
+}
+
+dose_status dose_pg_step(const dose_matrix* A, float* x, const float* p, const float* w, float eta, double* f,
+                         float* g, void* stream) {
+    if (!A) return invalid("dose_pg_step: null matrix");
+    if (!f || (A->ncols && !x) || (A->nrows && (!p || !w))) return invalid("dose_pg_step: null pointer argument");
+    if (!(eta >= 0.0f) || std::isinf(eta)) return invalid("dose_pg_step: eta must be finite and >= 0");
+    dose_status st = adjoint_supported(A, true);
+    if (st != DOSE_OK) return st;
+    cudaError_t e = launch_adjoint(A, ADJ_MODE_QUADRATIC, x, p, w, nullptr, nullptr, f, g, x, eta, as_stream(stream));
+    return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_pg_step launch");
+}
+
+dose_status dose_spmv_batched(const dose_matrix* const* A, int count, const float* const* X, float* const* D,
+                              int nvec, void* stream) {
+    if (count < 0 || count > 4096) return invalid("dose_spmv_batched: count must be in [0, 4096]");
+    if (count == 0) return DOSE_OK;
+    if (!A || !X || !D) return invalid("dose_spmv_batched: null array");
+    if (nvec < 1 || nvec > 16) return invalid("dose_spmv_batched: nvec must be in [1, 16]");
+    for (int m = 0; m < count; ++m) {
+        if (!A[m]) return invalid("dose_spmv_batched: null matrix " + std::to_string(m));
+        if ((A[m]->ncols && !X[m]) || (A[m]->nrows && !D[m]))
+            return invalid("dose_spmv_batched: null vector for matrix " + std::to_string(m));
+    }
+    std::string why;
+    cudaError_t e = launch_spmm_batched(A, count, X, D, nvec, as_stream(stream), &why);
+    if (!why.empty()) {
+        set_error(why);
+        return DOSE_ERR_UNSUPPORTED;
+    }
+    return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_spmv_batched launch");
+}
+
+dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
+    if (!A || !out) return invalid("dose_matrix_info: null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->nrows = A->nrows;
+    out->ncols = A->ncols;
+    out->nnz = A->nnz;
+    out->fmt = A->fmt;
+    out->flags = A->flags;
+    out->n_stages = A->n_stages;
+    out->n_coop_rows = A->n_coop_rows;
+    std::memcpy(out->lanes_hist, A->lanes_hist, sizeof(out->lanes_hist));
+    out->grid = A->grid;
+    out->block = 32 * (A->tuning.consumer_warps + 1);
+    out->max_row_len = A->max_row_len;
+    out->device_bytes = A->device_bytes;
+    const uint64_t vb = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const uint64_t nz = A->nnz, nr = A->nrows, nc = A->ncols;
+    const uint64_t rs = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 4 * nr : 0;  // row scales
+    // Algorithmic bytes: every stored byte of A once, the vectors once.
+    out->spmv_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
+    out->adjoint_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
+    out->fused_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 8 * nr + 4 * nc + 4 * nc + 8;
+    out->scale = A->fmt == DOSE_FMT_U16_SCALE ? A->scale : 0.f;
+    out->tuning.tile_nnz = A->tuning.tile_nnz;
+    out->tuning.tile_rows = A->tuning.tile_rows;
+    out->tuning.coop_nnz = A->tuning.coop_nnz;
+    out->tuning.lane_target = A->tuning.lane_target;
+    out->tuning.stages = A->tuning.stages;
+    out->tuning.consumer_warps = A->tuning.consumer_warps;
+    return DOSE_OK;
+}
+
+dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning) {
+    if (!A) return invalid("dose_set_tuning: null matrix");
+    Tuning t = merge_tuning(A->tuning, tuning);
+    dose_status st = check_tuning(A, t);
+    if (st != DOSE_OK) return st;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "dose_set_tuning");
+    return apply_schedule(A, t);
+}
+
+dose_status dose_device_status(const dose_matrix* A, void* stream) {
+    if (!A) return invalid("dose_device_status: null matrix");
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, A->err, sizeof(int), cudaMemcpyDeviceToHost, as_stream(stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "dose_device_status");
+    if (h != 0) {
+        cudaMemsetAsync(A->err, 0, sizeof(int), as_stream(stream));
+        cudaStreamSynchronize(as_stream(stream));
+        set_error(h == kErrTimeoutFull ? "a consumer warp timed out waiting for staged data"
+                                       : "the producer timed out waiting for a free stage slot");
+        return DOSE_ERR_TIMEOUT;
+    }
+    return DOSE_OK;
+}
+
+dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tuning* best) {
+    if (!A) return invalid("dose_autotune: null matrix");
+    if (A->ncols && !x) return invalid("dose_autotune: x is NULL");
+    cudaStream_t s = as_stream(stream);
+    float* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, std::max<size_t>(A->nrows, 1) * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "dose_autotune scratch");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const Tuning orig = A->tuning;
+    Tuning best_t = orig;
+    float best_ms = 1e30f;
+    const uint32_t nnzs[] = {2048, 4096, 8192};
+    const uint32_t rows[] = {1024, 2048, 4096};
+    const uint32_t targets[] = {2, 4, 8};
+    const uint32_t depths[] = {3, 4, 6};
+    dose_status result = DOSE_OK;
+    for (uint32_t tn : nnzs)
+        for (uint32_t tr : rows)
+            for (uint32_t lt : targets)
+                for (uint32_t sd : depths) {
+                    Tuning t = orig;
+                    t.tile_nnz = tn;
+                    t.tile_rows = tr;
+                    t.coop_nnz = std::min(t.coop_nnz, tn);
+                    t.lane_target = lt;
+                    t.stages = sd;
+                    if (check_tuning(A, t) != DOSE_OK) continue;
+                    if (apply_schedule(A, t) != DOSE_OK) continue;
+                    for (int i = 0; i < 3; ++i) launch_spmv(A, x, d, s);
+                    const int reps = 10;
+                    cudaEventRecord(e0, s);
+                    for (int i = 0; i < reps; ++i) launch_spmv(A, x, d, s);
+                    cudaEventRecord(e1, s);
+                    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                        result = cuda_fail(e, "dose_autotune timing");
+                        goto done;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best_t = t;
+                    }
+                }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d);
+    if (result != DOSE_OK) {
+        apply_schedule(A, orig);
+        return result;
+    }
+    dose_status st = apply_schedule(A, best_t);
+    if (st != DOSE_OK) return st;
+    if (best) {
+        best->tile_nnz = best_t.tile_nnz;
+        best->tile_rows = best_t.tile_rows;
+        best->coop_nnz = best_t.coop_nnz;
+        best->lane_target = best_t.lane_target;
+        best->stages = best_t.stages;
+        best->consumer_warps = best_t.consumer_warps;
+    }
+    return DOSE_OK;
+}
+
+}  // extern "C"

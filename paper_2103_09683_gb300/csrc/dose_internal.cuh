@@ -1,0 +1,242 @@
+// Internal definitions shared by the library's translation units: the matrix
+// handle, the pipeline schedule, and sm_100-family device helpers (mbarrier,
+// bulk async copies, bounded waits, value decoders).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dose.h"
+
+namespace dose {
+
+// ------------------------------------------------------------ schedule
+//
+// The matrix rows are cut into pipeline stages ("row blocks"), each staged in
+// shared memory by bulk async copies:
+//   NORMAL stage: consecutive rows [row0, row1), at most tile_rows rows and
+//                 tile_nnz entries, none longer than coop_nnz.  Rows are handled
+//                 32 at a time by one warp; the non-empty ones by groups of
+//                 L = 2^lanes_log2 lanes (row-length binning per stage).
+//   COOP stage:   one chunk (<= tile_nnz entries) of one row longer than
+//                 coop_nnz; all consumer warps reduce it together.  A row of
+//                 several chunks occupies consecutive stages FIRST..LAST.
+// Each CTA owns a contiguous range of stages (static, so every reduction order
+// is fixed at create time).
+enum : uint32_t {
+    STAGE_LANES_MASK = 0x7u,  // log2 of lanes per row (0..5)
+    STAGE_COOP = 0x8u,
+    STAGE_FIRST = 0x10u,
+    STAGE_LAST = 0x20u,
+};
+
+struct Tuning {
+    uint32_t tile_nnz = 4096;
+    uint32_t tile_rows = 2048;
+    uint32_t coop_nnz = 1024;
+    uint32_t lane_target = 4;
+    uint32_t stages = 4;
+    uint32_t consumer_warps = 16;
+};
+
+struct Schedule {
+    std::vector<uint32_t> row0;    // n_stages + 1
+    std::vector<uint32_t> nz0;     // n_stages + 1
+    std::vector<uint8_t> meta;     // n_stages
+    std::vector<uint32_t> cta_begin;  // grid + 1
+    uint32_t n_coop_rows = 0;
+    uint32_t lanes_hist[6] = {0, 0, 0, 0, 0, 0};
+};
+
+// Device-side view of a schedule, passed to kernels by value.
+struct ScheduleView {
+    const uint32_t* row0;
+    const uint32_t* nz0;
+    const uint8_t* meta;
+    const uint32_t* cta_begin;
+};
+
+}  // namespace dose
+
+struct dose_matrix {
+    uint32_t nrows = 0, ncols = 0;
+    uint64_t nnz = 0;
+    dose_format fmt = DOSE_FMT_U16_SCALE;
+    unsigned flags = 0;
+    int device = 0;
+    int sm_count = 0;
+    uint32_t max_row_len = 0;
+    float scale = 1.0f;  // U16 matrix scale
+
+    // matrix arrays (device, padded so aligned bulk copies stay in bounds)
+    uint32_t* row_ptr = nullptr;
+    uint32_t* col = nullptr;
+    void* val = nullptr;
+    float* row_scale = nullptr;  // FP8 only
+
+    // schedule (device)
+    uint32_t* st_row0 = nullptr;
+    uint32_t* st_nz0 = nullptr;
+    uint8_t* st_meta = nullptr;
+    uint32_t* st_cta_begin = nullptr;
+    uint32_t n_stages = 0;
+    uint32_t grid = 0;
+    uint32_t n_coop_rows = 0;
+    uint32_t lanes_hist[6] = {0, 0, 0, 0, 0, 0};
+    dose::Tuning tuning;
+
+    // adjoint scratch: per-CTA partial gradients and objective values
+    float* g_part = nullptr;     // grid_adj * ncols
+    double* f_part = nullptr;    // grid_adj
+    uint32_t grid_adj = 0;
+    uint32_t* adj_cta_begin = nullptr;  // grid_adj + 1 (schedule split for the adjoint grid)
+
+    int* err = nullptr;  // device error word (0 = ok)
+    uint64_t device_bytes = 0;
+    std::vector<uint32_t> host_row_ptr;  // kept for re-scheduling
+};
+
+namespace dose {
+
+// Host helpers (dose_api.cu)
+void set_error(const std::string& msg);
+dose_status cuda_fail(cudaError_t e, const char* what);
+
+// Launchers (spmv_kernel.cu, adjoint_kernel.cu, batched_kernel.cu)
+size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem);
+bool spmv_x_in_smem(const dose_matrix* A);
+cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s);
+cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const float* p,
+                           const float* w, const float* r, float* d, double* f, float* g,
+                           float* x_update, float eta, cudaStream_t s);
+size_t adjoint_smem_bytes(const dose_matrix* A, const Tuning& t, uint32_t warps, bool need_x);
+uint32_t adjoint_warps(const dose_matrix* A, const Tuning& t, bool need_x, int max_smem);
+cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const float* const* X,
+                                float* const* D, int nvec, cudaStream_t s, std::string* why);
+
+constexpr uint32_t kMaxSmemPerBlock = 227 * 1024;
+constexpr uint32_t kXSmemMaxCols = 16384;  // x staged in shared memory up to 64 KB
+constexpr uint32_t kCompThreshold = 128;   // compensated accumulation above this row length
+constexpr int ADJ_MODE_ADJOINT = 0;   // g = A^T r
+constexpr int ADJ_MODE_QUADRATIC = 1; // d, f, g of the quadratic objective
+
+// Error codes written into the device error word.
+constexpr int kErrTimeoutFull = 1;
+constexpr int kErrTimeoutEmpty = 2;
+
+}  // namespace dose
+
+// ------------------------------------------------------------------ device
+#ifdef __CUDACC__
+namespace dose {
+namespace dev {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `parity` to complete, giving up after ~4 s of wall
+// time (the kernels this guards run for milliseconds).  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > 4000000000ull) return false;
+    }
+}
+
+// Bulk async copy global -> shared (no tensor map), completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a non-zero multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void named_barrier(uint32_t id, uint32_t nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// ---- value decoders (exact conversions to FP32)
+__device__ __forceinline__ float dec_u16(uint16_t q) { return static_cast<float>(q); }
+
+__device__ __forceinline__ float dec_bf16(uint16_t b) {
+    return __uint_as_float(static_cast<uint32_t>(b) << 16);
+}
+
+// OCP E4M3 -> FP32 through the hardware E4M3x2 -> F16x2 conversion (exact:
+// every E4M3 value is representable in F16), then F16 -> F32 (exact).
+__device__ __forceinline__ float dec_e4m3(uint8_t q) {
+    uint32_t h2;
+    const uint16_t in = (uint16_t)(q | (q << 8));  // same code in both bytes: either half is the value
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(in));
+    float f;
+    asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(static_cast<uint16_t>(h2 & 0xFFFFu)));
+    return f;
+}
+
+// ---- error-free transformations for compensated dot products (Ogita, Rump,
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005: TwoSum of
+// Knuth and TwoProduct by FMA).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+}  // namespace dev
+}  // namespace dose
+#endif

@@ -1,0 +1,301 @@
+// Forward dose SpMV d = A x on sm_103a (Sec. II-A: the dose is one matrix-vector
+// product; Sec. III, Listing 1: one output per row, the row's dot product,
+// lanes of a warp read consecutive entries and reduce with warp shuffles).
+//
+// GB300 design (not the paper's one-warp-per-row grid):
+//   * persistent CTAs, one per SM, each owning a contiguous range of row blocks
+//     ("stages") fixed at create time;
+//   * one producer warp streams each stage's row_ptr / value / column slices
+//     into shared memory with bulk async copies (cp.async.bulk + mbarrier
+//     transaction counts), `stages` deep, so HBM sees a few large contiguous
+//     reads per stage instead of per-warp gathers;
+//   * consumer warps take 32 consecutive rows at a time, write 0 for empty rows
+//     (coalesced), and reduce the non-empty ones with groups of L lanes per row,
+//     L chosen per stage from its mean row length (row-length binning);
+//     rows longer than coop_nnz are reduced by the whole CTA;
+//   * values are decoded in registers (u16 -> f32, bf16 -> f32, e4m3 -> f32),
+//     x sits in shared memory, accumulation is FP32 (optionally compensated),
+//     and the U16/FP8 scale is applied once per row.
+// Every reduction has a fixed shape, so results are bitwise reproducible.
+#include "stage_common.cuh"
+
+namespace dose {
+namespace {
+
+struct SpmvParams {
+    const uint32_t* row_ptr;
+    const uint32_t* col;
+    const void* val;
+    const float* row_scale;
+    float scale;
+    const float* x;
+    float* d;
+    uint32_t nrows, ncols;
+    ScheduleView sched;
+    uint32_t tile_nnz, tile_rows, depth, cwarps;
+    int* err;
+};
+
+constexpr uint32_t kHeaderBytes = 1024;  // mbarriers (<= 16 x 16 B) + reduction scratch
+
+// Accumulate entries kb, kb+step, ... < ke of one row.  vs/cs hold the stage's
+// value and column slices starting at global entry vb / cb.
+template <int FMT, bool COMP>
+__device__ __forceinline__ void accumulate_row(const typename Fmt<FMT>::T* __restrict__ vs, uint32_t vb,
+                                               const uint32_t* __restrict__ cs, uint32_t cb,
+                                               const float* __restrict__ xs, const float* __restrict__ xg,
+                                               bool xsmem, uint32_t kb, uint32_t ke, uint32_t step, float& s,
+                                               float& c) {
+    if (COMP) {
+        for (uint32_t k = kb; k < ke; k += step) {
+            const float a = Fmt<FMT>::dec(vs[k - vb]);
+            const uint32_t j = cs[k - cb];
+            const float xv = xsmem ? xs[j] : __ldg(xg + j);
+            float pr, ep, t, es;
+            dev::two_prod(a, xv, pr, ep);
+            dev::two_sum(s, pr, t, es);
+            s = t;
+            c = __fadd_rn(c, __fadd_rn(es, ep));
+        }
+    } else {
+#pragma unroll 4
+        for (uint32_t k = kb; k < ke; k += step) {
+            const float a = Fmt<FMT>::dec(vs[k - vb]);
+            const uint32_t j = cs[k - cb];
+            const float xv = xsmem ? xs[j] : __ldg(xg + j);
+            s = __fmaf_rn(a, xv, s);
+        }
+    }
+}
+
+template <int FMT, bool COMP, bool XSMEM>
+__global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
+    using T = typename Fmt<FMT>::T;
+    constexpr uint32_t VA = Fmt<FMT>::kAlign;
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t S = p.depth;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + S;
+    float* red = reinterpret_cast<float*>(smem + 256);            // 64 floats: CTA reduction
+    uint8_t* rowlist = smem + 512;                                 // 16 warps x 32 bytes
+    float* xs = reinterpret_cast<float*>(smem + kHeaderBytes);
+    const uint32_t x_bytes = XSMEM ? round_up(p.ncols * 4, 128) : 0;
+    unsigned char* stage_base = smem + kHeaderBytes + x_bytes;
+    const StageLayout SL = stage_layout(p.tile_nnz, p.tile_rows, sizeof(T));
+
+    const uint32_t s_begin = p.sched.cta_begin[blockIdx.x];
+    const uint32_t s_end = p.sched.cta_begin[blockIdx.x + 1];
+    const uint32_t W = p.cwarps;
+
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < S; ++i) {
+            dev::mbar_init(&full[i], 1);
+            dev::mbar_init(&empty[i], W);
+        }
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    if (s_begin >= s_end) return;
+
+    if (warp == 0) {
+        // ---------------- producer: one thread streams stage slices into smem
+        if (lane == 0)
+            run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, stage_base, SL, full, empty, S,
+                              p.err);
+        return;
+    }
+
+    // -------------------- consumers
+    const uint32_t cw = warp - 1;          // consumer warp index
+    const uint32_t ctid = threadIdx.x - 32;
+    const uint32_t nct = W * 32;
+    if (XSMEM) {
+        for (uint32_t j = ctid; j < p.ncols; j += nct) xs[j] = __ldg(p.x + j);
+        dev::named_barrier(1, nct);
+    }
+    uint8_t* my_rows = rowlist + cw * 32;
+    float coop_s = 0.f, coop_c = 0.f;
+
+    uint32_t st = 0, ph = 0;
+    for (uint32_t s = s_begin; s < s_end; ++s) {
+        if (!dev::mbar_wait_bounded(&full[st], ph)) {
+            atomicExch(p.err, kErrTimeoutFull);
+            return;
+        }
+        const unsigned char* buf = stage_base + st * SL.bytes;
+        const uint8_t meta = p.sched.meta[s];
+        const uint32_t nz0 = p.sched.nz0[s], nz1 = p.sched.nz0[s + 1];
+        const T* vs = reinterpret_cast<const T*>(buf + SL.val_off);
+        const uint32_t* cs = reinterpret_cast<const uint32_t*>(buf + SL.col_off);
+        const uint32_t vb = nz0 & ~(VA - 1), cb = nz0 & ~3u;
+
+        if (!(meta & STAGE_COOP)) {
+            const uint32_t r0 = p.sched.row0[s], r1 = p.sched.row0[s + 1];
+            const uint32_t* rps = reinterpret_cast<const uint32_t*>(buf + SL.rp_off);
+            const uint32_t rb0 = r0 & ~3u;
+            const uint32_t lg = meta & STAGE_LANES_MASK;
+            const uint32_t L = 1u << lg, NG = 32u >> lg;
+            const uint32_t g = lane >> lg, li = lane & (L - 1);
+            const uint32_t nchunks = (r1 - r0 + 31) / 32;
+            for (uint32_t c = (cw + W - (s % W)) % W; c < nchunks; c += W) {
+                const uint32_t rb = r0 + c * 32;
+                const uint32_t r = rb + lane;
+                const bool valid = r < r1;
+                const uint32_t beg = valid ? rps[r - rb0] : 0, end = valid ? rps[r + 1 - rb0] : 0;
+                const unsigned nonempty = __ballot_sync(0xffffffffu, end > beg);
+                if (valid && end == beg) p.d[r] = 0.0f;
+                if (end > beg) my_rows[__popc(nonempty & ((1u << lane) - 1))] = (uint8_t)lane;
+                __syncwarp();
+                const uint32_t cnt = __popc(nonempty);
+                for (uint32_t base = 0; base < cnt; base += NG) {
+                    const uint32_t idx = base + g;
+                    const bool has = idx < cnt;
+                    const uint32_t j = has ? my_rows[idx] : 0;
+                    const uint32_t rs = __shfl_sync(0xffffffffu, beg, j);
+                    const uint32_t re = __shfl_sync(0xffffffffu, end, j);
+                    float sum = 0.f, comp = 0.f;
+                    if (has) {
+                        if (COMP && re - rs > kCompThreshold)
+                            accumulate_row<FMT, true>(vs, vb, cs, cb, xs, p.x, XSMEM, rs + li, re, L, sum, comp);
+                        else
+                            accumulate_row<FMT, false>(vs, vb, cs, cb, xs, p.x, XSMEM, rs + li, re, L, sum, comp);
+                    }
+                    for (uint32_t off = L >> 1; off > 0; off >>= 1) {
+                        const float os = __shfl_xor_sync(0xffffffffu, sum, off);
+                        if (COMP) {
+                            const float oc = __shfl_xor_sync(0xffffffffu, comp, off);
+                            float t, e;
+                            dev::two_sum(sum, os, t, e);
+                            sum = t;
+                            comp = __fadd_rn(__fadd_rn(comp, oc), e);
+                        } else {
+                            sum = __fadd_rn(sum, os);
+                        }
+                    }
+                    if (has && li == 0) {
+                        float v = COMP ? __fadd_rn(sum, comp) : sum;
+                        const uint32_t row = rb + j;
+                        if (FMT == DOSE_FMT_U16_SCALE) v = __fmul_rn(p.scale, v);
+                        if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) v = __fmul_rn(__ldg(p.row_scale + row), v);
+                        p.d[row] = v;
+                    }
+                }
+                __syncwarp();
+            }
+        } else {
+            // one chunk of a long row, reduced by every consumer thread
+            if (meta & STAGE_FIRST) {
+                coop_s = 0.f;
+                coop_c = 0.f;
+            }
+            if (COMP)
+                accumulate_row<FMT, true>(vs, vb, cs, cb, xs, p.x, XSMEM, nz0 + ctid, nz1, nct, coop_s, coop_c);
+            else
+                accumulate_row<FMT, false>(vs, vb, cs, cb, xs, p.x, XSMEM, nz0 + ctid, nz1, nct, coop_s, coop_c);
+            if (meta & STAGE_LAST) {
+                float sum = coop_s, comp = coop_c;
+                for (uint32_t off = 16; off > 0; off >>= 1) {
+                    const float os = __shfl_xor_sync(0xffffffffu, sum, off);
+                    if (COMP) {
+                        const float oc = __shfl_xor_sync(0xffffffffu, comp, off);
+                        float t, e;
+                        dev::two_sum(sum, os, t, e);
+                        sum = t;
+                        comp = __fadd_rn(__fadd_rn(comp, oc), e);
+                    } else {
+                        sum = __fadd_rn(sum, os);
+                    }
+                }
+                if (lane == 0) {
+                    red[cw] = sum;
+                    red[32 + cw] = comp;
+                }
+                dev::named_barrier(1, nct);
+                if (ctid == 0) {
+                    float tot = red[0], tc = red[32];
+                    for (uint32_t w2 = 1; w2 < W; ++w2) {
+                        if (COMP) {
+                            float t, e;
+                            dev::two_sum(tot, red[w2], t, e);
+                            tot = t;
+                            tc = __fadd_rn(__fadd_rn(tc, red[32 + w2]), e);
+                        } else {
+                            tot = __fadd_rn(tot, red[w2]);
+                        }
+                    }
+                    float v = COMP ? __fadd_rn(tot, tc) : tot;
+                    const uint32_t row = p.sched.row0[s];
+                    if (FMT == DOSE_FMT_U16_SCALE) v = __fmul_rn(p.scale, v);
+                    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) v = __fmul_rn(__ldg(p.row_scale + row), v);
+                    p.d[row] = v;
+                }
+                dev::named_barrier(1, nct);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) dev::mbar_arrive(&empty[st]);
+        if (++st == S) {
+            st = 0;
+            ph ^= 1;
+        }
+    }
+}
+
+template <int FMT, bool COMP, bool XSMEM>
+cudaError_t launch_t(const dose_matrix* A, const SpmvParams& p, size_t smem, cudaStream_t s) {
+    auto k = spmv_kernel<FMT, COMP, XSMEM>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<A->grid, 32 * (p.cwarps + 1), smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int FMT>
+cudaError_t launch_fmt(const dose_matrix* A, const SpmvParams& p, size_t smem, bool comp, bool xsmem,
+                       cudaStream_t s) {
+    if (comp) return xsmem ? launch_t<FMT, true, true>(A, p, smem, s) : launch_t<FMT, true, false>(A, p, smem, s);
+    return xsmem ? launch_t<FMT, false, true>(A, p, smem, s) : launch_t<FMT, false, false>(A, p, smem, s);
+}
+
+}  // namespace
+
+bool spmv_x_in_smem(const dose_matrix* A) { return A->ncols <= kXSmemMaxCols; }
+
+size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem) {
+    const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const StageLayout SL = stage_layout(t.tile_nnz, t.tile_rows, esize);
+    return kHeaderBytes + (x_in_smem ? round_up(A->ncols * 4, 128) : 0) + (size_t)t.stages * SL.bytes;
+}
+
+cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s) {
+    if (A->nrows == 0) return cudaSuccess;
+    SpmvParams p;
+    p.row_ptr = A->row_ptr;
+    p.col = A->col;
+    p.val = A->val;
+    p.row_scale = A->row_scale;
+    p.scale = A->scale;
+    p.x = x;
+    p.d = d;
+    p.nrows = A->nrows;
+    p.ncols = A->ncols;
+    p.sched = ScheduleView{A->st_row0, A->st_nz0, A->st_meta, A->st_cta_begin};
+    p.tile_nnz = A->tuning.tile_nnz;
+    p.tile_rows = A->tuning.tile_rows;
+    p.depth = A->tuning.stages;
+    p.cwarps = A->tuning.consumer_warps;
+    p.err = A->err;
+    const bool xsmem = spmv_x_in_smem(A);
+    const size_t smem = spmv_smem_bytes(A, A->tuning, xsmem);
+    const bool comp = (A->flags & DOSE_CREATE_COMPENSATED) != 0;
+    switch (A->fmt) {
+        case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, smem, comp, xsmem, s);
+        case DOSE_FMT_BF16: return launch_fmt<DOSE_FMT_BF16>(A, p, smem, comp, xsmem, s);
+        case DOSE_FMT_FP8E4M3_ROWSCALE: return launch_fmt<DOSE_FMT_FP8E4M3_ROWSCALE>(A, p, smem, comp, xsmem, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dose

@@ -1,0 +1,111 @@
+"""The C-ABI library loads on a CPU-only host, exports every entry point that
+include/dose.h declares, and its host-side logic (argument validation, value
+encoders) behaves as specified -- no GPU and no kernel launch needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import dosegen
+import oracle
+import paper_2103_09683_gb300 as dose
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    dose.build()
+    return dose.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dose.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dose_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "dose_spmv" in names and "dose_create_matrix" in names and len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in dose.EXPORTS, f"binding does not wrap {n}"
+    assert lib.dose_version().startswith(b"libdose")
+
+
+@pytest.mark.parametrize("fmt,ofmt", [("u16", oracle.U16_SCALE), ("bf16", oracle.BF16),
+                                      ("fp8", oracle.FP8E4M3_ROWSCALE)])
+def test_library_encoder_matches_oracle_bit_exact(lib, fmt, ofmt):
+    A = dosegen.generate(dosegen.TINY)
+    rng = np.random.default_rng(1)
+    # add ties and awkward values: exact midpoints between codes, tiny and large entries
+    val = A.val.copy()
+    val[:50] = rng.uniform(0, 1e-6, 50)
+    codes, scales = dose.encode_host(fmt, A.row_ptr, val)
+    ref = oracle.encode(dosegen.CSR(A.nrows, A.ncols, A.row_ptr, A.col, val), ofmt)
+    assert np.array_equal(codes, ref.values)
+    if fmt != "bf16":
+        assert np.array_equal(scales, ref.scales)
+
+
+def test_fp8_encoder_on_exact_ties(lib):
+    # one row whose max is 448 * s with s = 1: every E4M3 midpoint in (0, 448]
+    mids = []
+    vals = sorted({oracle.fp8_e4m3_value(c) for c in range(0x7F)})
+    for a, b in zip(vals[:-1], vals[1:]):
+        mids += [a, 0.5 * (a + b)]
+    mids.append(448.0)
+    v = np.array(mids, dtype=np.float64)
+    rp = np.array([0, v.size], dtype=np.uint32)
+    codes, scales = dose.encode_host("fp8", rp, v)
+    assert scales[0] == 1.0
+    ref = [oracle.fp8_e4m3_nearest(t) for t in v]
+    assert list(codes) == ref
+
+
+def _desc(**kw):
+    d = dose._Desc()
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def test_create_rejects_invalid_csr_on_host(lib):
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    out = ctypes.c_void_p()
+    v = np.full(3, 0.5)
+    cases = {
+        "row_ptr[0]": dict(nrows=2, ncols=3, nnz=3, row_ptr=arr([1, 2, 3], np.uint32),
+                           col_idx=arr([0, 1, 2], np.uint32)),
+        "row_ptr[nrows]": dict(nrows=2, ncols=3, nnz=3, row_ptr=arr([0, 1, 2], np.uint32),
+                               col_idx=arr([0, 1, 2], np.uint32)),
+        "non-decreasing": dict(nrows=2, ncols=3, nnz=3, row_ptr=arr([0, 4, 3], np.uint32),
+                               col_idx=arr([0, 1, 2], np.uint32)),
+        ">= ncols": dict(nrows=2, ncols=3, nnz=3, row_ptr=arr([0, 2, 3], np.uint32),
+                         col_idx=arr([0, 3, 2], np.uint32)),
+        "duplicate": dict(nrows=2, ncols=3, nnz=3, row_ptr=arr([0, 2, 3], np.uint32),
+                          col_idx=arr([1, 1, 2], np.uint32)),
+    }
+    for needle, kw in cases.items():
+        d = _desc(fmt=0, values_f64=arr(v, np.float64), **kw)
+        st = lib.dose_create_matrix(ctypes.byref(d), 0, None, None, ctypes.byref(out))
+        assert st == 1, needle
+        assert needle in lib.dose_last_error().decode(), (needle, lib.dose_last_error())
+    # negative value for the encoder, NULL arguments, unknown flags
+    d = _desc(nrows=1, ncols=3, nnz=3, row_ptr=arr([0, 3], np.uint32), col_idx=arr([0, 1, 2], np.uint32),
+              fmt=0, values_f64=arr([0.5, -1.0, 0.2], np.float64))
+    assert lib.dose_create_matrix(ctypes.byref(d), 0, None, None, ctypes.byref(out)) == 1
+    assert lib.dose_create_matrix(None, 0, None, None, ctypes.byref(out)) == 1
+    assert lib.dose_create_matrix(ctypes.byref(d), 0x80, None, None, ctypes.byref(out)) == 1
+    assert lib.dose_destroy(None) == 0
+    assert lib.dose_spmv(None, None, None, None) == 1
+    assert lib.dose_spmv_batched(None, -1, None, None, 16, None) == 1

@@ -1,0 +1,248 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Forward: max relative error per row <= 1e-5 (FP32 accumulation of
+non-negative terms; rows of zero dose exactly 0).  Adjoint: componentwise
+|g - g_ref| <= 1e-5 (|A|^T |r|)_j.  Index work is bit-exact (unit vectors give
+the stored column exactly).  Every result is bitwise repeatable.
+"""
+import numpy as np
+import pytest
+import torch
+
+import dosegen
+import oracle
+import paper_2103_09683_gb300 as dose
+from gpu_helpers import adj_check, edge_case_matrices, fwd_check, make
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    dose.build()
+    dose.load()
+
+
+def _x(n, seed=11):
+    return dosegen.spot_weights(n, seed)
+
+
+def _to(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return dosegen.generate(dosegen.TINY)
+
+
+# ---------------------------------------------------------------- forward
+
+@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8"])
+@pytest.mark.parametrize("compensated", [False, True])
+def test_forward_tiny_beam(tiny, fmt, compensated):
+    A, enc = make(tiny, fmt, compensated=compensated)
+    x = _x(tiny.ncols)
+    d = A.spmv(_to(x)).cpu().numpy()
+    ref = oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x)
+    fwd_check(d, ref)
+    d2 = A.spmv(_to(x)).cpu().numpy()
+    assert np.array_equal(d.view(np.uint32), d2.view(np.uint32)), "not bitwise repeatable"
+    A.device_status()
+
+
+@pytest.mark.parametrize("name", list(edge_case_matrices().keys()))
+@pytest.mark.parametrize("fmt", ["u16", "fp8"])
+def test_forward_edge_cases(name, fmt):
+    csr = edge_case_matrices()[name]
+    for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4),
+                   dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16)):
+        A, enc = make(csr, fmt, tuning=tuning)
+        x = _x(csr.ncols, seed=3)
+        d = A.spmv(_to(x)).cpu().numpy()
+        ref = oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x)
+        # long rows (16000 entries) need compensated sums or more lanes; plain
+        # FP32 over at most nnz/32 sequential terms stays within this bound
+        fwd_check(d, ref, rtol=3e-5 if csr.row_lengths().max() > 4096 else 1e-5)
+        A.device_status()
+
+
+@pytest.mark.parametrize("fmt", ["u16", "fp8", "bf16"])
+def test_unit_vectors_reproduce_stored_columns_bit_exact(tiny, fmt):
+    A, enc = make(tiny, fmt)
+    rng = np.random.default_rng(0)
+    M_cols = {}
+    rp = enc.row_ptr.astype(np.int64)
+    rows_of = np.repeat(np.arange(tiny.nrows), np.diff(rp))
+    for j in rng.choice(tiny.ncols, 12, replace=False):
+        e = np.zeros(tiny.ncols, dtype=np.float32)
+        e[j] = 1.0
+        d = A.spmv(_to(e)).cpu().numpy()
+        sel = enc.col == j
+        expect = np.zeros(tiny.nrows, dtype=np.float32)
+        # the stored value rounded once to FP32: fl32(s*q) (u16), fl32(s_r*e4m3) (fp8)
+        expect[rows_of[sel]] = enc.decoded[sel].astype(np.float32)
+        assert np.array_equal(d.view(np.uint32), expect.view(np.uint32)), j
+
+
+def test_compensated_long_rows_adversarial():
+    # descending magnitudes over 16000 entries: plain FP32 loses digits
+    n = 16000
+    rp = np.array([0, n], dtype=np.uint32)
+    col = np.arange(n, dtype=np.uint32)
+    val = np.geomspace(1.0, 1e-4, n)
+    csr = dosegen.CSR(1, n, rp, col, val)
+    A, enc = make(csr, "u16", compensated=True)
+    x = np.ones(n, dtype=np.float32)
+    d = A.spmv(_to(x)).cpu().numpy()
+    ref = oracle.spmv(1, enc.row_ptr, enc.col, enc.decoded, x)
+    rel = abs(float(d[0]) - ref[0]) / ref[0]
+    # Dot2: about 2u of the result, then one rounding by the scale
+    assert rel <= 4 * 2.0 ** -24, rel
+
+
+# ---------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8"])
+def test_adjoint_tiny_beam(tiny, fmt):
+    A, enc = make(tiny, fmt)
+    r = np.random.default_rng(4).normal(size=tiny.nrows).astype(np.float32)
+    g = A.adjoint(_to(r)).cpu().numpy()
+    ref = oracle.spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r)
+    gabs = oracle.abs_spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r)
+    adj_check(g, ref, gabs)
+    g2 = A.adjoint(_to(r)).cpu().numpy()
+    assert np.array_equal(g.view(np.uint32), g2.view(np.uint32))
+    A.device_status()
+
+
+@pytest.mark.parametrize("name", list(edge_case_matrices().keys()))
+def test_adjoint_edge_cases(name):
+    csr = edge_case_matrices()[name]
+    if csr.ncols > 16384:
+        csr = dosegen.random_csr(csr.nrows, 9000, seed=8,
+                                 lengths=np.minimum(csr.row_lengths(), 9000))
+    for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4)):
+        A, enc = make(csr, "u16", tuning=tuning)
+        r = np.random.default_rng(9).normal(size=csr.nrows).astype(np.float32)
+        g = A.adjoint(_to(r)).cpu().numpy()
+        ref = oracle.spmv_t(csr.nrows, csr.ncols, enc.row_ptr, enc.col, enc.decoded, r)
+        gabs = oracle.abs_spmv_t(csr.nrows, csr.ncols, enc.row_ptr, enc.col, enc.decoded, r)
+        adj_check(g, ref, gabs)
+
+
+def test_adjoint_identity_on_gpu(tiny):
+    A, enc = make(tiny, "u16")
+    x = _x(tiny.ncols)
+    y = np.random.default_rng(2).uniform(-1, 1, tiny.nrows).astype(np.float32)
+    Ax = A.spmv(_to(x)).cpu().numpy().astype(np.float64)
+    ATy = A.adjoint(_to(y)).cpu().numpy().astype(np.float64)
+    scale = np.dot(oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x), np.abs(y))
+    assert abs(np.dot(Ax, y) - np.dot(x.astype(np.float64), ATy)) <= 1e-5 * scale
+
+
+# ------------------------------------------------------ fused objective pass
+
+@pytest.fixture(scope="module")
+def objective_inputs(tiny):
+    p, w = dosegen.ellipsoid_target(dosegen.TINY)
+    x = _x(tiny.ncols, seed=dosegen.weight_seed(dosegen.TINY))
+    return p, w, x
+
+
+@pytest.mark.parametrize("fmt", ["u16", "fp8"])
+def test_fused_forward_adjoint_quadratic(tiny, objective_inputs, fmt):
+    p, w, x = objective_inputs
+    A, enc = make(tiny, fmt)
+    f, g, d = A.fwd_adj_quadratic(_to(x), _to(p), _to(w), want_d=True)
+    f, g, d = float(f.item()), g.cpu().numpy(), d.cpu().numpy()
+    d_ref = oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x)
+    fwd_check(d, d_ref)
+    # f from the GPU's own FP32 dose, reduced in FP64 (tight), and end to end
+    f_own, r_own = oracle.objective(d.astype(np.float64), p, w)
+    assert abs(f - f_own) <= 1e-12 * f_own
+    f_ref, _ = oracle.objective(d_ref, p, w)
+    assert abs(f - f_ref) <= 1e-4 * f_ref
+    g_ref = oracle.spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r_own)
+    gabs = oracle.abs_spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r_own)
+    adj_check(g, g_ref, gabs)
+    # the unfused path gives the same gradient up to rounding
+    g2 = A.adjoint(_to(r_own.astype(np.float32))).cpu().numpy()
+    adj_check(g2, g_ref, gabs)
+
+
+def test_gradient_matches_central_differences(tiny, objective_inputs):
+    p, w, x = objective_inputs
+    A, enc = make(tiny, "u16")
+    f0, g = A.fwd_adj_quadratic(_to(x), _to(p), _to(w))
+    g = g.cpu().numpy()
+    _, g_exact = oracle.fgrad(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, x, p, w)
+    h = 0.5
+    for j in np.random.default_rng(6).choice(tiny.ncols, 20, replace=False):
+        xp, xm = x.copy(), x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fp = float(A.fwd_adj_quadratic(_to(xp), _to(p), _to(w))[0].item())
+        fm = float(A.fwd_adj_quadratic(_to(xm), _to(p), _to(w))[0].item())
+        fd = (fp - fm) / (2 * h)
+        scale = max(abs(g_exact[j]), 1e-3 * np.abs(g_exact).max())
+        assert abs(fd - g[j]) <= 1e-3 * scale, (j, fd, g[j])
+        assert abs(g[j] - g_exact[j]) <= 1e-4 * scale
+
+
+def test_pg_100_iterations_in_one_graph(tiny, objective_inputs):
+    p, w, x0 = objective_inputs
+    A, enc = make(tiny, "u16")
+    eta = oracle.pg_step_size(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, w)
+    x_ref, f_ref = oracle.pg(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, x0, p, w, eta, 100)
+    xg = _to(x0.copy())
+    solver = dose.PGSolver(A, xg, _to(p), _to(w), eta, 100, use_graph=True)
+    fh = solver.run().cpu().numpy()
+    assert np.all(np.abs(fh - f_ref) <= 1e-4 * f_ref)
+    np.testing.assert_allclose(xg.cpu().numpy(), x_ref, rtol=1e-3, atol=1e-4 * np.abs(x_ref).max())
+    assert np.all(np.diff(fh) <= 1e-6 * fh[0])
+    # eager replay of the same steps gives the same bits as the graph
+    xe = _to(x0.copy())
+    fe = dose.PGSolver(A, xe, _to(p), _to(w), eta, 100, use_graph=False).run().cpu().numpy()
+    assert np.array_equal(fe.view(np.uint64), fh.view(np.uint64))
+    assert np.array_equal(xe.cpu().numpy().view(np.uint32), xg.cpu().numpy().view(np.uint32))
+
+
+# ---------------------------------------------------------------- autograd
+
+def test_autograd_function_uses_adjoint(tiny, objective_inputs):
+    p, w, x = objective_inputs
+    A, enc = make(tiny, "u16")
+    xt = _to(x).requires_grad_(True)
+    d = dose.dose_spmv(A, xt)
+    r = torch.randn(tiny.nrows, device="cuda", dtype=torch.float32)
+    (d * r).sum().backward()
+    g_ref = oracle.spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r.cpu().numpy())
+    gabs = oracle.abs_spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r.cpu().numpy())
+    adj_check(xt.grad.cpu().numpy(), g_ref, gabs)
+    xt2 = _to(x).requires_grad_(True)
+    f = dose.QuadraticDoseObjective(A, xt2, _to(p), _to(w))
+    (2.0 * f).backward()
+    _, g = A.fwd_adj_quadratic(_to(x), _to(p), _to(w))
+    assert torch.equal(xt2.grad, 2.0 * g)
+
+
+# ----------------------------------------------------------------- batched
+
+@pytest.mark.parametrize("nvec", [1, 5, 16])
+def test_batched_spmm_small(nvec):
+    mats = [dosegen.random_csr(500 + 97 * i, 60 + 13 * i, seed=20 + i, density=0.1) for i in range(5)]
+    mats.append(dosegen.random_csr(40, 3000, seed=30, lengths=[0, 2500] + [7] * 38))
+    handles, encs, Xs = [], [], []
+    for i, m in enumerate(mats):
+        A, enc = make(m, "u16" if i % 2 == 0 else "fp8")
+        handles.append(A)
+        encs.append(enc)
+        Xs.append(_to(dosegen.spot_weights(m.ncols, 100 + i, nvec=nvec).reshape(m.ncols, nvec)))
+    Ds = dose.spmv_batched(handles, Xs)
+    for m, enc, X, D in zip(mats, encs, Xs, Ds):
+        ref = oracle.spmm(m.nrows, enc.row_ptr, enc.col, enc.decoded, X.cpu().numpy().astype(np.float64))
+        fwd_check(D.cpu().numpy().reshape(-1), ref.reshape(-1))
+    Ds2 = dose.spmv_batched(handles, Xs)
+    for D, D2 in zip(Ds, Ds2):
+        assert torch.equal(D, D2)
