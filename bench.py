@@ -1,0 +1,370 @@
+"""Benchmark of the dose calculation hot path on GB300.
+
+One step = one dose evaluation d = A x (dose_spmv) plus one dose+gradient
+evaluation of the quadratic objective (dose_pg_step: fused d, f, A^T r and the
+projected-gradient update) on the clinical-size pencil-beam matrix
+(256x256x160 voxels x 4000 spots, ~1.5e8 entries, uint16 values + one FP32
+scale, uint32 indices).  Inputs are resident in HBM when the timed region
+starts; A (~1 GB) is larger than the 129 MB L2, so every step streams it from
+HBM.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on the same workload and metric.  Under torchrun (N > 1) every rank
+runs an independent replica on its own GPU (weak scaling; no collective on the
+data path) and rank 0 reports the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import dosegen  # noqa: E402
+
+METRIC = "dose SpMV effective HBM GB/s (% of GB300 peak) and ms per dose+gradient eval"
+WORKLOAD = ("clinical pencil beam: 256x256x160 voxels (10,485,760 rows) x 4000 spots, "
+            "sigma 4 voxels, ~1.5e8 entries; u16 values + FP32 scale, u32 indices, FP32 x/d; "
+            "step = dose eval (d = A x) + dose+gradient eval (fused d, FP64 f, A^T[2w(d-p)], "
+            "projected-gradient update)")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this build."""
+    try:
+        import paper_2103_09683_gb300._build as b
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tab = json.load(f)
+        ent = tab.get(kernel)
+        if ent and ent.get("inputs_sha256") == b._inputs_digest():
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def setup_workload(device):
+    """Clinical beam on the device: handle, x, p, w and the PG step size."""
+    import torch
+
+    import paper_2103_09683_gb300 as dose
+
+    beam = dosegen.CLINICAL
+    csr = dosegen.generate(beam)
+    A = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="u16", values_f64=csr.val)
+    p, w = dosegen.ellipsoid_target(beam, semi_axes=(30.0, 20.0, 16.0))
+    x = dosegen.spot_weights(csr.ncols, dosegen.weight_seed(beam))
+    # step size 1/L with L = 2 max(w) ||A||_1 ||A||_inf >= the gradient's Lipschitz constant
+    cs = np.concatenate([[0.0], np.cumsum(csr.val)])
+    rp = csr.row_ptr.astype(np.int64)
+    absrow = cs[rp[1:]] - cs[rp[:-1]]
+    del cs
+    abscol = np.bincount(csr.col, weights=csr.val, minlength=csr.ncols)
+    eta = 1.0 / (2.0 * float(w.max()) * float(absrow.max()) * float(abscol.max()))
+    t = lambda a: torch.from_numpy(a).to(device)
+    return csr, A, t(x), t(p), t(w), eta
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2103_09683_gb300 as dose
+
+    ws, rank, local = _dist()
+    dose.build()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=device)
+    csr, A, x, p, w, eta = setup_workload(device)
+    info = A.info()
+    stream = torch.cuda.current_stream()
+    d = torch.empty(A.nrows, dtype=torch.float32, device=device)
+    f = torch.empty(1, dtype=torch.float64, device=device)
+    x0 = x.clone()
+
+    def step():
+        A.spmv(x, d)
+        A.pg_step(x, p, w, eta, f=f)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    x.copy_(x0)
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e_start.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        A.spmv(x, d)
+        ev[k][1].record(stream)
+        A.pg_step(x, p, w, eta, f=f)
+        ev[k][2].record(stream)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    time.sleep(0.2)
+    clk = clocks.stop()
+    total_ms = e_start.elapsed_time(e_end)
+    spmv_ms = sum(ev[k][0].elapsed_time(ev[k][1]) for k in range(K)) / K
+    grad_ms = sum(ev[k][1].elapsed_time(ev[k][2]) for k in range(K)) / K
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    A.device_status()
+
+    # end to end through the public API with host buffers: H2D x, both calls, D2H d and f
+    xh = x0.cpu().pin_memory()
+    dh = torch.empty(A.nrows, dtype=torch.float32).pin_memory()
+    fh = torch.empty(1, dtype=torch.float64).pin_memory()
+    ke = max(3, min(K, 50))
+    for _ in range(2):
+        x.copy_(xh, non_blocking=True)
+        step()
+        dh.copy_(d, non_blocking=True)
+        fh.copy_(f, non_blocking=True)
+    torch.cuda.synchronize()
+    e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e2[0].record(stream)
+    for _ in range(ke):
+        x.copy_(xh, non_blocking=True)
+        step()
+        dh.copy_(d, non_blocking=True)
+        fh.copy_(f, non_blocking=True)
+    e2[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2[0].elapsed_time(e2[1]) / ke
+
+    step_bytes = info["spmv_bytes"] + info["fused_bytes"]
+    value = ws * step_bytes * K / (total_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    spmv_gbs = info["spmv_bytes"] / (spmv_ms * 1e-3) / 1e9
+    grad_gbs = info["fused_bytes"] / (grad_ms * 1e-3) / 1e9
+    kernels = {
+        "spmv_kernel": {"ms": round(spmv_ms, 5), "bytes": info["spmv_bytes"],
+                        "achieved_gbs": round(spmv_gbs, 1), "frac": round(spmv_gbs / peak, 4),
+                        "traffic": _traffic("spmv_kernel")},
+        "adjoint_kernel+finalize": {"ms": round(grad_ms, 5), "bytes": info["fused_bytes"],
+                                    "achieved_gbs": round(grad_gbs, 1), "frac": round(grad_gbs / peak, 4),
+                                    "traffic": _traffic("adjoint_kernel")},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": peak,
+            "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+            else "fallback 6.8 TB/s", "unit": "GB/s", "frac": kernels[dom]["frac"],
+            "traffic": kernels[dom]["traffic"]}
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / K, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nrows": A.nrows, "ncols": A.ncols, "nnz": A.nnz,
+                   "format": "u16+scale", "bytes_per_step": step_bytes,
+                   "l2": "inputs larger than L2 (A streams ~1 GB per call; L2 129 MB)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "ms_per_dose_eval": round(spmv_ms, 5),
+        "ms_per_dose_grad_eval": round(grad_ms, 5),
+        "pct_of_nominal_8tbs": round(100 * spmv_gbs / 8000.0, 1),
+        "kernels": kernels,
+        "roofline": roof,
+        "e2e": {"value": round(step_bytes / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": 4 * A.ncols,
+                "d2h_bytes_per_step": 4 * A.nrows + 8},
+        "gpu_launches": 3 * K,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(csr, x0.cpu().numpy(), p.cpu().numpy(), w.cpu().numpy())
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def _oracle_block(csr, enc, frac):
+    """Contiguous block of rows from the middle of the matrix holding about
+    frac of its entries, as a standalone CSR (rebased row pointers)."""
+    rp = enc.row_ptr.astype(np.int64)
+    nnz = int(rp[-1])
+    want = max(1, int(frac * nnz))
+    mid = int(np.searchsorted(rp, nnz // 2))
+    r0 = int(np.searchsorted(rp, max(0, int(rp[mid]) - want // 2)))
+    r1 = int(np.searchsorted(rp, min(nnz, int(rp[r0]) + want)))
+    r1 = max(r1, r0 + 1)
+    k0, k1 = int(rp[r0]), int(rp[r1])
+    sub_rp = (rp[r0:r1 + 1] - k0).astype(np.uint32)
+    return r0, r1, sub_rp, enc.col[k0:k1], enc.decoded[k0:k1]
+
+
+def oracle_step(csr, enc, x, p, w, frac):
+    """One oracle step (FP64 SpMV + f and A^T r) on a row block holding frac of
+    the entries: returns (algorithmic bytes of that block, seconds)."""
+    import oracle
+
+    r0, r1, rp, col, a = _oracle_block(csr, enc, frac)
+    nr, nc, nz = r1 - r0, csr.ncols, int(rp[-1])
+    t0 = time.perf_counter()
+    oracle.spmv(nr, rp, col, a, x)
+    oracle.fgrad(nr, nc, rp, col, a, x, p[r0:r1], w[r0:r1])
+    dt = time.perf_counter() - t0
+    bytes_ = (6 * nz + 4 * (nr + 1) + 4 * nr + 4 * nc) + (6 * nz + 4 * (nr + 1) + 8 * nr + 8 * nc + 8)
+    return bytes_, dt
+
+
+def cpu_baseline(csr, x, p, w, budget_s=10.0):
+    """The FP64 oracle, as it stands, on one host core: full-matrix steps
+    (dose evaluation + dose+gradient evaluation) repeated for about budget_s."""
+    import oracle
+
+    enc = oracle.encode(csr, oracle.U16_SCALE)
+    tot_b, tot_t, reps = 0, 0.0, 0
+    while tot_t < budget_s and reps < 50:
+        b, t = oracle_step(csr, enc, x, p, w, 1.0)
+        tot_b, tot_t, reps = tot_b + b, tot_t + t, reps + 1
+    return {"value": round(tot_b / tot_t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "ms_per_step": round(1e3 * tot_t / reps, 1),
+            "sample": f"{reps} full-matrix step(s) of the clinical beam ({csr.nnz} entries): "
+                      f"FP64 SpMV + f and A^T r, single thread"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+
+    beam = dosegen.CLINICAL
+    csr = dosegen.generate(beam)
+    enc = oracle.encode(csr, oracle.U16_SCALE)
+    p, w = dosegen.ellipsoid_target(beam, semi_axes=(30.0, 20.0, 16.0))
+    x = dosegen.spot_weights(csr.ncols, dosegen.weight_seed(beam))
+    # size each step's row block so that warmup + steps take about two minutes
+    _, t_full = oracle_step(csr, enc, x, p, w, 1.0)
+    frac = min(1.0, 120.0 / max(args.steps + args.warmup, 1) / max(t_full, 1e-6))
+    for _ in range(args.warmup):
+        oracle_step(csr, enc, x, p, w, frac)
+    tot_b, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        b, t = oracle_step(csr, enc, x, p, w, frac)
+        tot_b, tot_t = tot_b + b, tot_t + t
+    v = round(tot_b / tot_t / 1e9, 3)
+    sample = (f"each step: a contiguous row block with {frac:.3%} of the clinical matrix's entries "
+              f"(FP64 SpMV + f and A^T r), single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot_t / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "nrows": csr.nrows, "ncols": csr.ncols,
+                                           "nnz": csr.nnz},
+           "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -191,10 +191,9 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
                     const float dv = end > beg ? my_d[lane] : 0.f;
                     if (valid) {
                         if (p.d) p.d[r] = dv;
-                        const float e = __fsub_rn(dv, pv);
-                        const double ed = (double)e;
+                        const double ed = (double)dv - (double)pv;  // residual in FP64
                         f_lane += (double)wv * ed * ed;
-                        rv = __fmul_rn(__fmul_rn(2.0f, wv), e);
+                        rv = (float)(2.0 * (double)wv * ed);
                     }
                 } else {
                     rv = valid ? __ldg(p.r + r) : 0.f;
@@ -229,12 +228,12 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
                     for (uint32_t w2 = 1; w2 < W; ++w2) tot = __fadd_rn(tot, red[w2]);
                     const float dv = finish_dot<FMT>(p, row, tot);
                     const float pv = __ldg(p.p + row), wv = __ldg(p.w + row);
-                    const float e = __fsub_rn(dv, pv);
+                    const double ed = (double)dv - (double)pv;
                     if (ctid == 0) {
                         if (p.d) p.d[row] = dv;
-                        f_lane += (double)wv * (double)e * (double)e;
+                        f_lane += (double)wv * ed * ed;
                     }
-                    const float rj = __fmul_rn(__fmul_rn(__fmul_rn(2.0f, wv), e), row_factor<FMT>(p, row));
+                    const float rj = __fmul_rn((float)(2.0 * (double)wv * ed), row_factor<FMT>(p, row));
                     const uint32_t kb = p.row_ptr[row], ke = p.row_ptr[row + 1];
                     // warp cw scatters entries kb + 32*(cw + W*t) + lane into its own accumulator
                     for (uint32_t k0 = kb + cw * 32; k0 < ke; k0 += nct) {
