@@ -93,22 +93,32 @@ typedef struct {
  * fields 0 = library default.  Changing them never changes which rows an
  * output depends on; it may change the last bits of FP32 results. */
 typedef struct {
+    /* forward SpMV (dose_spmv, dose_spmv_batched) */
     uint32_t tile_nnz;       /* max entries staged per pipeline stage (256..16384) */
     uint32_t tile_rows;      /* max rows per stage (32..8192) */
     uint32_t coop_nnz;       /* rows longer than this are reduced by the whole CTA */
     uint32_t lane_target;    /* lanes per row = power of two nearest mean row length / lane_target */
     uint32_t stages;         /* pipeline depth (2..8) */
     uint32_t consumer_warps; /* 4, 8 or 16 */
+    /* adjoint and fused objective pass (dose_adjoint, dose_fwd_adj_quadratic, dose_pg_step) */
+    uint32_t adj_tile_nnz;      /* (256..16384) */
+    uint32_t adj_tile_rows;     /* (32..8192) */
+    uint32_t adj_stages;        /* (2..8) */
+    uint32_t adj_forward_warps; /* warps computing d, f, r in the fused pass (1..15) */
+    uint32_t adj_scatter_warps; /* warps owning gradient accumulators (0 = as many as fit) */
 } dose_tuning;
 
 typedef struct {
     uint32_t nrows, ncols;
     uint64_t nnz;
     uint32_t fmt, flags;
-    uint32_t n_stages;          /* pipeline stages (row blocks) in the schedule */
+    uint32_t n_stages;          /* pipeline stages (row blocks) of the forward schedule */
     uint32_t n_coop_rows;       /* rows reduced by a whole CTA */
-    uint32_t lanes_hist[6];     /* stages per lanes-per-row bin 1,2,4,8,16,32 */
+    uint32_t lanes_hist[6];     /* forward stages per lanes-per-row bin 1,2,4,8,16,32 */
     uint32_t grid, block;       /* launch shape of the forward kernel */
+    uint32_t adj_n_stages;      /* stages of the adjoint schedule */
+    uint32_t adj_block_fused;   /* threads per CTA of the fused pass (0 if it does not fit) */
+    uint32_t adj_block_adjoint; /* threads per CTA of the adjoint (0 if it does not fit) */
     uint32_t max_row_len;
     uint64_t device_bytes;      /* device memory held by the handle */
     uint64_t spmv_bytes;        /* algorithmic HBM bytes of one dose_spmv */
@@ -140,13 +150,13 @@ dose_status dose_spmv_batched(const dose_matrix* const* A, int count, const floa
                               float* const* D, int nvec, void* stream);
 
 /* g = A^T r, the adjoint (gradient of any dose objective with dD/dd = r).
- * r: device, nrows floats.  g: device, ncols floats.  Deterministic: per-warp
+ * r: device, nrows floats, 16-byte aligned.  g: device, ncols floats.  Deterministic: per-warp
  * private accumulators combined in a fixed order, no atomics on values. */
 dose_status dose_adjoint(const dose_matrix* A, const float* r, float* g, void* stream);
 
 /* One pass over A of the quadratic dose objective
  *   d = A x,  f = sum_i w_i (d_i - p_i)^2 (FP64),  g = A^T [2 w (d - p)]
- * x: device ncols floats; p, w: device nrows floats; d: device nrows floats or
+ * x: device ncols floats; p, w: device nrows floats, 16-byte aligned; d: device nrows floats or
  * NULL (not written); f: device, one double; g: device ncols floats. */
 dose_status dose_fwd_adj_quadratic(const dose_matrix* A, const float* x, const float* p,
                                    const float* w, float* d, double* f, float* g, void* stream);

@@ -49,7 +49,10 @@ class Tuning(ctypes.Structure):
     """Schedule knobs (0 = default); see dose_tuning in include/dose.h."""
     _fields_ = [("tile_nnz", ctypes.c_uint32), ("tile_rows", ctypes.c_uint32),
                 ("coop_nnz", ctypes.c_uint32), ("lane_target", ctypes.c_uint32),
-                ("stages", ctypes.c_uint32), ("consumer_warps", ctypes.c_uint32)]
+                ("stages", ctypes.c_uint32), ("consumer_warps", ctypes.c_uint32),
+                ("adj_tile_nnz", ctypes.c_uint32), ("adj_tile_rows", ctypes.c_uint32),
+                ("adj_stages", ctypes.c_uint32), ("adj_forward_warps", ctypes.c_uint32),
+                ("adj_scatter_warps", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -60,7 +63,9 @@ class _Info(ctypes.Structure):
                 ("fmt", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("n_stages", ctypes.c_uint32), ("n_coop_rows", ctypes.c_uint32),
                 ("lanes_hist", ctypes.c_uint32 * 6), ("grid", ctypes.c_uint32),
-                ("block", ctypes.c_uint32), ("max_row_len", ctypes.c_uint32),
+                ("block", ctypes.c_uint32), ("adj_n_stages", ctypes.c_uint32),
+                ("adj_block_fused", ctypes.c_uint32), ("adj_block_adjoint", ctypes.c_uint32),
+                ("max_row_len", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64), ("spmv_bytes", ctypes.c_uint64),
                 ("adjoint_bytes", ctypes.c_uint64), ("fused_bytes", ctypes.c_uint64),
                 ("scale", ctypes.c_float), ("tuning", Tuning)]

@@ -4,15 +4,22 @@
 // optimiser the paper motivates needs every iteration (Sec. I: function values
 // and gradients of the beam variables; Sec. II-A: A fixed, x changing).
 //
+// Warp specialisation (one persistent CTA per SM, shared-memory ring filled by
+// bulk async copies as in the forward kernel):
+//   warp 0            producer: row_ptr / non-empty list / values / columns /
+//                     per-row vectors (p, w or r) of each stage;
+//   forward warps     (fused pass only) d for the stage's rows, the FP64
+//                     objective terms, and r_i = 2 w_i (d_i - p_i) per non-empty
+//                     row into the slot; then signal `fwd_done`;
+//   scatter warps     each owns a private shared-memory accumulator of all
+//                     ncols gradient entries and scatters a_ij r_i for its share
+//                     of the stage's non-empty rows, one row at a time.
 // Determinism (Sec. II-D: no reductions whose order is not fixed, so no float
-// atomics): every consumer warp owns a private shared-memory accumulator of all
-// ncols gradient entries.  A warp scatters one row at a time; the entries of a
-// row have distinct columns, so the 32 lanes never update the same word in one
-// instruction, and rows follow a fixed order per warp.  At the end each CTA
-// sums its warps' accumulators in warp order into a per-CTA partial, and a
-// second kernel sums the partials in CTA order (and applies an optional
-// projected-gradient update x <- max(0, x - eta g)).  The stage pipeline is the
-// one of the forward kernel (bulk async copies into a shared-memory ring).
+// atomics): the entries of a row have distinct columns, so the lanes of a
+// scatter warp never update the same word in one instruction; each warp's rows
+// follow a fixed order; at the end each CTA sums its warps' accumulators in
+// warp order into a per-CTA partial, and a second kernel sums the partials in
+// CTA order (and applies an optional projected-gradient step x <- max(0, x - eta g)).
 #include "stage_common.cuh"
 
 namespace dose {
@@ -22,51 +29,40 @@ struct AdjParams {
     const uint32_t* row_ptr;
     const uint32_t* col;
     const void* val;
-    const float* row_scale;
     float scale;
     const float* x;   // QUADRATIC
-    const float* p;   // QUADRATIC
-    const float* w;   // QUADRATIC
-    const float* r;   // ADJOINT
     float* d;         // QUADRATIC, may be null
     float* g_part;    // grid x ncols
     double* f_part;   // grid
     uint32_t nrows, ncols;
     ScheduleView sched;
-    uint32_t tile_nnz, tile_rows, depth, cwarps;
+    VecSet vecs;      // QUADRATIC: p, w [, row scale]; ADJOINT: r [, row scale]
+    uint32_t tile_nnz, tile_rows, depth, fwarps, swarps;
     int* err;
 };
 
-constexpr uint32_t kAdjHeader = 4096;  // barriers, warp reduction scratch, row lists (512 B), row results (2 KB)
+constexpr uint32_t kAdjHeader = 1024;  // 3 x 8 mbarriers, CTA reduction scratch
 
 template <int FMT>
-__device__ __forceinline__ float row_factor(const AdjParams& p, uint32_t row) {
-    // Per-row factor folded into r for the scatter (FP8 row scale); the U16
-    // matrix scale is applied once per column in the finalize kernel.
-    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) return __ldg(p.row_scale + row);
-    return 1.0f;
-}
-
-template <int FMT>
-__device__ __forceinline__ float finish_dot(const AdjParams& p, uint32_t row, float acc) {
+__device__ __forceinline__ float finish_dot(const AdjParams& p, float rs, float acc) {
     if (FMT == DOSE_FMT_U16_SCALE) return __fmul_rn(p.scale, acc);
-    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) return __fmul_rn(__ldg(p.row_scale + row), acc);
+    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) return __fmul_rn(rs, acc);
     return acc;
 }
 
-// gw[col_k] += a_k * rj for the entries k in [kb, ke) of one row, lanes strided
-// by 32 (columns in a row are distinct: the four loads precede the four stores).
+// gw[col_k] += a_k * rj for the entries k = kb, kb + step, ... < ke of one row
+// (columns in a row are distinct: the four loads precede the four stores).
 template <int FMT>
-__device__ __forceinline__ void scatter_row(float* __restrict__ gw, const typename Fmt<FMT>::T* __restrict__ vs,
-                                            uint32_t vb, const uint32_t* __restrict__ cs, uint32_t cb,
-                                            uint32_t kb, uint32_t ke, uint32_t lane, float rj) {
-    for (uint32_t k0 = kb + lane; k0 < ke; k0 += 128) {
+__device__ __forceinline__ void scatter_entries(float* __restrict__ gw, const typename Fmt<FMT>::T* __restrict__ vs,
+                                                uint32_t vb, const uint32_t* __restrict__ cs, uint32_t cb,
+                                                uint32_t kb, uint32_t ke, uint32_t step, float rj) {
+    for (uint32_t k0 = kb; k0 < ke; k0 += 4 * step) {
         uint32_t c[4];
         float a[4], gv[4];
         bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint32_t k = k0 + 32u * u;
+            const uint32_t k = k0 + step * u;
             ok[u] = k < ke;
             c[u] = ok[u] ? cs[k - cb] : 0;
             a[u] = ok[u] ? Fmt<FMT>::dec(vs[k - vb]) : 0.f;
@@ -84,30 +80,32 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     using T = typename Fmt<FMT>::T;
     constexpr uint32_t VA = Fmt<FMT>::kAlign;
     constexpr bool QUAD = MODE == ADJ_MODE_QUADRATIC;
+    constexpr uint32_t kRowScaleVec = QUAD ? 2 : 1;  // index of the FP8 row scales in vecs
     extern __shared__ __align__(128) unsigned char smem[];
 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t S = p.depth, W = p.cwarps;
+    const uint32_t S = p.depth, Wf = QUAD ? p.fwarps : 0, Ws = p.swarps;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* empty = full + S;
-    float* red = reinterpret_cast<float*>(smem + 256);          // 32 floats
-    double* fred = reinterpret_cast<double*>(smem + 384);       // 16 doubles
-    uint8_t* rowlist = smem + 512;                               // 16 x 32 bytes
-    float* dres = reinterpret_cast<float*>(smem + 1024);        // 16 x 32 floats
-    const uint32_t gw_bytes = round_up(p.ncols * 4, 128);
-    float* gacc = reinterpret_cast<float*>(smem + kAdjHeader);   // W x ncols
-    float* xs = reinterpret_cast<float*>(smem + kAdjHeader + W * gw_bytes);
+    uint64_t* empty = full + 8;
+    uint64_t* fwd_done = full + 16;
+    float* red = reinterpret_cast<float*>(smem + 256);      // 32 floats: long-row partials
+    double* fred = reinterpret_cast<double*>(smem + 512);   // 32 doubles: per-warp objective
+    const uint32_t gw_floats = round_up(p.ncols * 4, 128) / 4;
+    float* gacc = reinterpret_cast<float*>(smem + kAdjHeader);  // Ws x gw_floats
+    float* xs = gacc + Ws * gw_floats;
     const uint32_t x_bytes = QUAD ? round_up(p.ncols * 4, 128) : 0;
-    unsigned char* stage_base = smem + kAdjHeader + W * gw_bytes + x_bytes;
-    const StageLayout SL = stage_layout(p.tile_nnz, p.tile_rows, sizeof(T));
+    unsigned char* slot_base = reinterpret_cast<unsigned char*>(xs) + x_bytes;
+    const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, sizeof(T), p.vecs.n, QUAD);
 
     const uint32_t s_begin = p.sched.cta_begin[blockIdx.x];
     const uint32_t s_end = p.sched.cta_begin[blockIdx.x + 1];
+    const uint32_t ncons = (Wf + Ws) * 32;
 
     if (threadIdx.x == 0) {
         for (uint32_t i = 0; i < S; ++i) {
             dev::mbar_init(&full[i], 1);
-            dev::mbar_init(&empty[i], W);
+            dev::mbar_init(&empty[i], Ws);
+            if (QUAD) dev::mbar_init(&fwd_done[i], Wf);
         }
         dev::fence_mbar_init();
     }
@@ -115,196 +113,230 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
 
     if (warp == 0) {
         if (lane == 0)
-            run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, stage_base, SL, full, empty, S,
-                              p.err);
+            run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, p.vecs, slot_base, SL, full,
+                              empty, S, p.err);
         return;
     }
 
-    const uint32_t cw = warp - 1;
     const uint32_t ctid = threadIdx.x - 32;
-    const uint32_t nct = W * 32;
-    for (uint32_t j = ctid; j < W * (gw_bytes / 4); j += nct) gacc[j] = 0.f;
+    for (uint32_t j = ctid; j < Ws * gw_floats; j += ncons) gacc[j] = 0.f;
     if (QUAD)
-        for (uint32_t j = ctid; j < p.ncols; j += nct) xs[j] = __ldg(p.x + j);
-    dev::named_barrier(1, nct);
+        for (uint32_t j = ctid; j < p.ncols; j += ncons) xs[j] = __ldg(p.x + j);
+    dev::named_barrier(1, ncons);
 
-    float* gw = gacc + cw * (gw_bytes / 4);
-    uint8_t* my_rows = rowlist + cw * 32;
-    float* my_d = dres + cw * 32;
-    double f_lane = 0.0;
-    float coop_s = 0.f;
+    const bool is_fwd = QUAD && warp <= Wf;
     bool failed = false;
+    double f_lane = 0.0;
 
-    uint32_t st = 0, ph = 0;
-    for (uint32_t s = s_begin; s < s_end; ++s) {
-        if (!dev::mbar_wait_bounded(&full[st], ph)) {
-            atomicExch(p.err, kErrTimeoutFull);
-            failed = true;
-            break;
-        }
-        const unsigned char* buf = stage_base + st * SL.bytes;
-        const uint8_t meta = p.sched.meta[s];
-        const uint32_t nz0 = p.sched.nz0[s], nz1 = p.sched.nz0[s + 1];
-        const T* vs = reinterpret_cast<const T*>(buf + SL.val_off);
-        const uint32_t* cs = reinterpret_cast<const uint32_t*>(buf + SL.col_off);
-        const uint32_t vb = nz0 & ~(VA - 1), cb = nz0 & ~3u;
-
-        if (!(meta & STAGE_COOP)) {
-            const uint32_t r0 = p.sched.row0[s], r1 = p.sched.row0[s + 1];
-            const uint32_t* rps = reinterpret_cast<const uint32_t*>(buf + SL.rp_off);
-            const uint32_t rb0 = r0 & ~3u;
-            const uint32_t lg = meta & STAGE_LANES_MASK;
-            const uint32_t L = 1u << lg, NG = 32u >> lg;
-            const uint32_t g = lane >> lg, li = lane & (L - 1);
-            const uint32_t nchunks = (r1 - r0 + 31) / 32;
-            for (uint32_t c = (cw + W - (s % W)) % W; c < nchunks; c += W) {
-                const uint32_t rb = r0 + c * 32;
-                const uint32_t r = rb + lane;
-                const bool valid = r < r1;
-                const uint32_t beg = valid ? rps[r - rb0] : 0, end = valid ? rps[r + 1 - rb0] : 0;
-                const unsigned nonempty = __ballot_sync(0xffffffffu, end > beg);
-                const uint32_t cnt = __popc(nonempty);
-                float rv = 0.f;
-                if (QUAD) {
-                    const float pv = valid ? __ldg(p.p + r) : 0.f;
-                    const float wv = valid ? __ldg(p.w + r) : 0.f;
-                    if (end > beg) my_rows[__popc(nonempty & ((1u << lane) - 1))] = (uint8_t)lane;
-                    __syncwarp();
-                    // forward: d for the non-empty rows, L lanes per row
-                    for (uint32_t base = 0; base < cnt; base += NG) {
-                        const uint32_t idx = base + g;
-                        const bool has = idx < cnt;
-                        const uint32_t j = has ? my_rows[idx] : 0;
-                        const uint32_t rs = __shfl_sync(0xffffffffu, beg, j);
-                        const uint32_t re = __shfl_sync(0xffffffffu, end, j);
-                        float sum = 0.f;
-                        if (has) {
-#pragma unroll 4
-                            for (uint32_t k = rs + li; k < re; k += L)
-                                sum = __fmaf_rn(Fmt<FMT>::dec(vs[k - vb]), xs[cs[k - cb]], sum);
-                        }
-                        for (uint32_t off = L >> 1; off > 0; off >>= 1)
-                            sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
-                        if (has && li == 0) my_d[j] = finish_dot<FMT>(p, rb + j, sum);
-                    }
-                    __syncwarp();
-                    const float dv = end > beg ? my_d[lane] : 0.f;
-                    if (valid) {
-                        if (p.d) p.d[r] = dv;
-                        const double ed = (double)dv - (double)pv;  // residual in FP64
-                        f_lane += (double)wv * ed * ed;
-                        rv = (float)(2.0 * (double)wv * ed);
-                    }
-                } else {
-                    rv = valid ? __ldg(p.r + r) : 0.f;
-                }
-                if (valid && end > beg) rv = __fmul_rn(rv, row_factor<FMT>(p, r));
-                // scatter the non-empty rows one at a time, in row order
-                unsigned m = nonempty;
-                while (m) {
-                    const uint32_t j = __ffs(m) - 1;
-                    m &= m - 1;
-                    const uint32_t rs = __shfl_sync(0xffffffffu, beg, j);
-                    const uint32_t re = __shfl_sync(0xffffffffu, end, j);
-                    const float rj = __shfl_sync(0xffffffffu, rv, j);
-                    scatter_row<FMT>(gw, vs, vb, cs, cb, rs, re, lane, rj);
-                    __syncwarp();
-                }
+    if (is_fwd) {
+        // ------------------------------------------------ forward warps
+        const uint32_t fw = warp - 1, ftid = fw * 32 + lane, nft = Wf * 32;
+        float coop_s = 0.f;
+        uint32_t st = 0, ph = 0;
+        for (uint32_t s = s_begin; s < s_end; ++s) {
+            if (!dev::mbar_wait_bounded(&full[st], ph)) {
+                atomicExch(p.err, kErrTimeoutFull);
+                failed = true;
+                break;
             }
-        } else {
-            // one chunk of a long row: every consumer thread takes part
-            const uint32_t row = p.sched.row0[s];
-            if (QUAD) {
-                if (meta & STAGE_FIRST) coop_s = 0.f;
-                for (uint32_t k = nz0 + ctid; k < nz1; k += nct)
+            unsigned char* buf = slot_base + st * SL.bytes;
+            const StageDesc D = *reinterpret_cast<const StageDesc*>(buf + SL.hdr_off);
+            const T* vs = reinterpret_cast<const T*>(buf + SL.val_off);
+            const uint32_t* cs = reinterpret_cast<const uint32_t*>(buf + SL.col_off);
+            const uint32_t vb = D.nz0 & ~(VA - 1), cb = D.nz0 & ~3u;
+            if (!(D.meta & STAGE_COOP)) {
+                const uint32_t* rps = reinterpret_cast<const uint32_t*>(buf + SL.rp_off);
+                const uint16_t* nes = reinterpret_cast<const uint16_t*>(buf + SL.ne_off) + (D.ne0 & 7u);
+                float* rl = reinterpret_cast<float*>(buf + SL.rl_off);
+                const uint32_t rb0 = D.row0 & ~3u;
+                for (uint32_t r = D.row0 + ftid; r < D.row1; r += nft) {
+                    if (rps[r - rb0] == rps[r + 1 - rb0]) {
+                        if (p.d) p.d[r] = 0.0f;
+                        const double pv = slot_vec(buf, SL, p.vecs, 0, D.row0, r);
+                        f_lane += (double)slot_vec(buf, SL, p.vecs, 1, D.row0, r) * pv * pv;
+                    }
+                }
+                const uint32_t lg = D.meta & STAGE_LANES_MASK;
+                const uint32_t L = 1u << lg;
+                const uint32_t gid = ftid >> lg, li = lane & (L - 1), G = nft >> lg;
+                const uint32_t n_ne = D.ne1 - D.ne0;
+                for (uint32_t base = 0; base < n_ne; base += G) {
+                    const uint32_t i = base + gid;
+                    const bool has = i < n_ne;
+                    float sum = 0.f;
+                    uint32_t row = 0;
+                    if (has) {
+                        row = D.row0 + nes[i];
+                        const uint32_t re = rps[row + 1 - rb0];
+#pragma unroll 4
+                        for (uint32_t k = rps[row - rb0] + li; k < re; k += L)
+                            sum = __fmaf_rn(Fmt<FMT>::dec(vs[k - vb]), xs[cs[k - cb]], sum);
+                    }
+                    for (uint32_t off = L >> 1; off > 0; off >>= 1)
+                        sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
+                    if (has && li == 0) {
+                        const float rsc =
+                            FMT == DOSE_FMT_FP8E4M3_ROWSCALE ? slot_vec(buf, SL, p.vecs, kRowScaleVec, D.row0, row) : 1.f;
+                        const float dv = finish_dot<FMT>(p, rsc, sum);
+                        if (p.d) p.d[row] = dv;
+                        const double wv = slot_vec(buf, SL, p.vecs, 1, D.row0, row);
+                        const double ed = (double)dv - (double)slot_vec(buf, SL, p.vecs, 0, D.row0, row);
+                        f_lane += wv * ed * ed;
+                        rl[i] = __fmul_rn((float)(2.0 * wv * ed), rsc);
+                    }
+                }
+            } else {
+                // one chunk of a long row: every forward thread takes part
+                if (D.meta & STAGE_FIRST) coop_s = 0.f;
+#pragma unroll 4
+                for (uint32_t k = D.nz0 + ftid; k < D.nz1; k += nft)
                     coop_s = __fmaf_rn(Fmt<FMT>::dec(vs[k - vb]), xs[cs[k - cb]], coop_s);
-                if (meta & STAGE_LAST) {
+                if (D.meta & STAGE_LAST) {
                     float sum = coop_s;
                     for (uint32_t off = 16; off > 0; off >>= 1)
                         sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
-                    if (lane == 0) red[cw] = sum;
-                    dev::named_barrier(1, nct);
-                    float tot = red[0];
-                    for (uint32_t w2 = 1; w2 < W; ++w2) tot = __fadd_rn(tot, red[w2]);
-                    const float dv = finish_dot<FMT>(p, row, tot);
-                    const float pv = __ldg(p.p + row), wv = __ldg(p.w + row);
-                    const double ed = (double)dv - (double)pv;
-                    if (ctid == 0) {
-                        if (p.d) p.d[row] = dv;
-                        f_lane += (double)wv * ed * ed;
+                    if (lane == 0) red[fw] = sum;
+                    dev::named_barrier(2, nft);
+                    if (ftid == 0) {
+                        float tot = red[0];
+                        for (uint32_t w2 = 1; w2 < Wf; ++w2) tot = __fadd_rn(tot, red[w2]);
+                        const float rsc = FMT == DOSE_FMT_FP8E4M3_ROWSCALE
+                                              ? slot_vec(buf, SL, p.vecs, kRowScaleVec, D.row0, D.row0)
+                                              : 1.f;
+                        const float dv = finish_dot<FMT>(p, rsc, tot);
+                        if (p.d) p.d[D.row0] = dv;
+                        const double wv = slot_vec(buf, SL, p.vecs, 1, D.row0, D.row0);
+                        const double ed = (double)dv - (double)slot_vec(buf, SL, p.vecs, 0, D.row0, D.row0);
+                        f_lane += wv * ed * ed;
+                        reinterpret_cast<float*>(buf + SL.hdr_off + 32)[0] = __fmul_rn((float)(2.0 * wv * ed), rsc);
                     }
-                    const float rj = __fmul_rn((float)(2.0 * (double)wv * ed), row_factor<FMT>(p, row));
-                    const uint32_t kb = p.row_ptr[row], ke = p.row_ptr[row + 1];
-                    // warp cw scatters entries kb + 32*(cw + W*t) + lane into its own accumulator
-                    for (uint32_t k0 = kb + cw * 32; k0 < ke; k0 += nct) {
-                        const uint32_t k = k0 + lane;
-                        if (k < ke) {
-                            const uint32_t cc = __ldg(p.col + k);
-                            gw[cc] = __fmaf_rn(Fmt<FMT>::dec(static_cast<const T*>(p.val)[k]), rj, gw[cc]);
-                        }
-                    }
-                    dev::named_barrier(1, nct);
-                }
-            } else {
-                const float rj = __fmul_rn(__ldg(p.r + row), row_factor<FMT>(p, row));
-                for (uint32_t k0 = nz0 + cw * 32; k0 < nz1; k0 += nct) {
-                    const uint32_t k = k0 + lane;
-                    if (k < nz1) {
-                        const uint32_t cc = cs[k - cb];
-                        gw[cc] = __fmaf_rn(Fmt<FMT>::dec(vs[k - vb]), rj, gw[cc]);
-                    }
+                    dev::named_barrier(2, nft);
                 }
             }
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&fwd_done[st]);
+            if (++st == S) {
+                st = 0;
+                ph ^= 1;
+            }
         }
-        __syncwarp();
-        if (lane == 0) dev::mbar_arrive(&empty[st]);
-        if (++st == S) {
-            st = 0;
-            ph ^= 1;
+    } else {
+        // ------------------------------------------------ scatter warps
+        const uint32_t sw = warp - 1 - Wf;
+        float* gw = gacc + sw * gw_floats;
+        uint32_t st = 0, ph = 0;
+        for (uint32_t s = s_begin; s < s_end; ++s) {
+            if (!dev::mbar_wait_bounded(&full[st], ph) || (QUAD && !dev::mbar_wait_bounded(&fwd_done[st], ph))) {
+                atomicExch(p.err, kErrTimeoutFull);
+                failed = true;
+                break;
+            }
+            const unsigned char* buf = slot_base + st * SL.bytes;
+            const StageDesc D = *reinterpret_cast<const StageDesc*>(buf + SL.hdr_off);
+            const T* vs = reinterpret_cast<const T*>(buf + SL.val_off);
+            const uint32_t* cs = reinterpret_cast<const uint32_t*>(buf + SL.col_off);
+            const uint32_t vb = D.nz0 & ~(VA - 1), cb = D.nz0 & ~3u;
+            if (!(D.meta & STAGE_COOP)) {
+                const uint32_t* rps = reinterpret_cast<const uint32_t*>(buf + SL.rp_off);
+                const uint16_t* nes = reinterpret_cast<const uint16_t*>(buf + SL.ne_off) + (D.ne0 & 7u);
+                const float* rl = reinterpret_cast<const float*>(buf + SL.rl_off);
+                const uint32_t rb0 = D.row0 & ~3u;
+                const uint32_t n_ne = D.ne1 - D.ne0;
+                for (uint32_t i = sw; i < n_ne; i += Ws) {
+                    const uint32_t row = D.row0 + nes[i];
+                    float rj;
+                    if (QUAD) {
+                        rj = rl[i];
+                    } else {
+                        rj = slot_vec(buf, SL, p.vecs, 0, D.row0, row);
+                        if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE)
+                            rj = __fmul_rn(rj, slot_vec(buf, SL, p.vecs, kRowScaleVec, D.row0, row));
+                    }
+                    scatter_entries<FMT>(gw, vs, vb, cs, cb, rps[row - rb0] + lane, rps[row + 1 - rb0], 32, rj);
+                    __syncwarp();
+                }
+            } else if (QUAD) {
+                if (D.meta & STAGE_LAST) {
+                    // the whole long row, from global memory (its earlier chunks left the ring)
+                    const float rj = reinterpret_cast<const float*>(buf + SL.hdr_off + 32)[0];
+                    const uint32_t kb = __ldg(p.row_ptr + D.row0), ke = __ldg(p.row_ptr + D.row0 + 1);
+                    const T* v = static_cast<const T*>(p.val);
+                    for (uint32_t k = kb + sw * 32 + lane; k < ke; k += Ws * 32) {
+                        const uint32_t c = __ldg(p.col + k);
+                        gw[c] = __fmaf_rn(Fmt<FMT>::dec(v[k]), rj, gw[c]);
+                    }
+                }
+            } else {
+                float rj = slot_vec(buf, SL, p.vecs, 0, D.row0, D.row0);
+                if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE)
+                    rj = __fmul_rn(rj, slot_vec(buf, SL, p.vecs, kRowScaleVec, D.row0, D.row0));
+                scatter_entries<FMT>(gw, vs, vb, cs, cb, D.nz0 + sw * 32 + lane, D.nz1, Ws * 32, rj);
+            }
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&empty[st]);
+            if (++st == S) {
+                st = 0;
+                ph ^= 1;
+            }
         }
     }
-    if (failed) return;  // every consumer times out on the same phase: no one is left at a barrier
+    // Timeouts are consistent across warps (all wait on the same phases), so a
+    // failed warp leaves no one waiting at the barriers below.
+    if (failed) return;
 
-    // CTA partials: warp accumulators summed in warp order; f in a fixed tree.
-    if (QUAD) {
+    // CTA partials: accumulators summed in warp order; f in a fixed tree.
+    if (is_fwd) {
         for (uint32_t off = 16; off > 0; off >>= 1) f_lane += __shfl_xor_sync(0xffffffffu, f_lane, off);
-        if (lane == 0) fred[cw] = f_lane;
+        if (lane == 0) fred[warp - 1] = f_lane;
     }
-    dev::named_barrier(1, nct);
-    const uint32_t gstride = gw_bytes / 4;
-    for (uint32_t j = ctid; j < p.ncols; j += nct) {
+    dev::named_barrier(1, ncons);
+    for (uint32_t j = ctid; j < p.ncols; j += ncons) {
         float t = gacc[j];
-        for (uint32_t w2 = 1; w2 < W; ++w2) t = __fadd_rn(t, gacc[w2 * gstride + j]);
+        for (uint32_t w2 = 1; w2 < Ws; ++w2) t = __fadd_rn(t, gacc[w2 * gw_floats + j]);
         p.g_part[(size_t)blockIdx.x * p.ncols + j] = t;
     }
     if (ctid == 0) {
         double t = 0.0;
-        if (QUAD)
-            for (uint32_t w2 = 0; w2 < W; ++w2) t += fred[w2];
+        for (uint32_t w2 = 0; w2 < Wf; ++w2) t += fred[w2];
         p.f_part[blockIdx.x] = t;
     }
 }
 
-// g_j = s * sum_c g_part[c][j] (CTA order), f = sum_c f_part[c]; optional
-// projected-gradient update of x.
-__global__ void adjoint_finalize(const float* __restrict__ g_part, const double* __restrict__ f_part,
-                                 uint32_t nparts, uint32_t ncols, float scale, float* g, double* f,
-                                 float* x_update, float eta) {
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < ncols) {
-        float t = 0.f;
-        for (uint32_t c = 0; c < nparts; ++c) t = __fadd_rn(t, g_part[(size_t)c * ncols + j]);
-        t = __fmul_rn(scale, t);
-        if (g) g[j] = t;
+// g_j = s * sum_c g_part[c][j] and f = sum_c f_part[c], both in a fixed order;
+// optional projected-gradient step on x.  Block: 256 threads = 8 warps x 32
+// columns; warp w sums the partials c = w, w + 8, ...; warp 0 adds the eight.
+__global__ void __launch_bounds__(256) adjoint_finalize(const float* __restrict__ g_part,
+                                                        const double* __restrict__ f_part, uint32_t nparts,
+                                                        uint32_t ncols, float scale, float* g, double* f,
+                                                        float* x_update, float eta) {
+    __shared__ float part[8][33];
+    __shared__ double fpart[256];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t j = blockIdx.x * 32 + lane;
+    float t = 0.f;
+    if (j < ncols)
+        for (uint32_t c = w; c < nparts; c += 8) t = __fadd_rn(t, g_part[(size_t)c * ncols + j]);
+    part[w][lane] = t;
+    if (f && blockIdx.x == 0) {
+        double ft = 0.0;
+        for (uint32_t c = threadIdx.x; c < nparts; c += 256) ft += f_part[c];
+        fpart[threadIdx.x] = ft;
+    }
+    __syncthreads();
+    if (w == 0 && j < ncols) {
+        float tot = part[0][lane];
+        for (uint32_t k = 1; k < 8; ++k) tot = __fadd_rn(tot, part[k][lane]);
+        tot = __fmul_rn(scale, tot);
+        if (g) g[j] = tot;
         if (x_update) {
-            const float xn = __fsub_rn(x_update[j], __fmul_rn(eta, t));
+            const float xn = __fsub_rn(x_update[j], __fmul_rn(eta, tot));
             x_update[j] = xn > 0.f ? xn : 0.f;
         }
     }
     if (f && blockIdx.x == 0 && threadIdx.x == 0) {
-        double t = 0.0;
-        for (uint32_t c = 0; c < nparts; ++c) t += f_part[c];
-        *f = t;
+        double ft = 0.0;
+        for (uint32_t k = 0; k < 256; ++k) ft += fpart[k];
+        *f = ft;
     }
 }
 
@@ -313,64 +345,90 @@ cudaError_t launch_adj_t(const dose_matrix* A, const AdjParams& p, size_t smem, 
     auto k = adjoint_kernel<FMT, MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<A->grid, 32 * (p.cwarps + 1), smem, s>>>(p);
+    const uint32_t warps = 1 + (MODE == ADJ_MODE_QUADRATIC ? p.fwarps : 0) + p.swarps;
+    k<<<A->adj.grid, 32 * warps, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+size_t adj_smem(const dose_matrix* A, const AdjTuning& t, bool quad, uint32_t ws) {
+    const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const uint32_t nvec = (quad ? 2 : 1) + (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
+    const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, quad);
+    const size_t col_bytes = round_up(A->ncols * 4, 128);
+    return kAdjHeader + ws * col_bytes + (quad ? col_bytes : 0) + (size_t)t.stages * SL.bytes;
 }
 
 }  // namespace
 
-size_t adjoint_smem_bytes(const dose_matrix* A, const Tuning& t, uint32_t warps, bool need_x) {
-    const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
-    const StageLayout SL = stage_layout(t.tile_nnz, t.tile_rows, esize);
-    const size_t col_bytes = round_up(A->ncols * 4, 128);
-    return kAdjHeader + warps * col_bytes + (need_x ? col_bytes : 0) + (size_t)t.stages * SL.bytes;
-}
-
-// Consumer warps that fit in shared memory next to the stage ring (0 = none).
-uint32_t adjoint_warps(const dose_matrix* A, const Tuning& t, bool need_x, int max_smem) {
-    for (uint32_t w = 16; w >= 1; --w)
-        if (adjoint_smem_bytes(A, t, w, need_x) <= (size_t)max_smem) return w;
-    return 0;
-}
-
-// Pipeline shape of the adjoint kernels: the forward schedule with at most 3
-// ring slots, leaving shared memory for the per-warp accumulators.
-static Tuning adjoint_tuning(const dose_matrix* A) {
-    Tuning t = A->tuning;
-    if (t.stages > 3) t.stages = 3;
-    return t;
+bool adjoint_shape(const dose_matrix* A, const AdjTuning& in, bool quad, AdjTuning* out, size_t* smem) {
+    AdjTuning t = in;
+    t.forward_warps = quad ? (in.forward_warps ? in.forward_warps : 8) : 0;
+    if (t.forward_warps > 15) t.forward_warps = 15;
+    if (t.stages < 2 || t.stages > 8) return false;
+    const uint32_t max_ws = 16 - t.forward_warps;
+    uint32_t ws = 0;
+    if (in.scatter_warps) {
+        ws = in.scatter_warps <= max_ws && adj_smem(A, t, quad, in.scatter_warps) <= kMaxSmemPerBlock
+                 ? in.scatter_warps
+                 : 0;
+    } else {
+        for (uint32_t w = max_ws; w >= 1; --w)
+            if (adj_smem(A, t, quad, w) <= kMaxSmemPerBlock) {
+                ws = w;
+                break;
+            }
+    }
+    if (ws == 0) return false;
+    t.scatter_warps = ws;
+    if (out) *out = t;
+    if (smem) *smem = adj_smem(A, t, quad, ws);
+    return true;
 }
 
 cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const float* p, const float* w,
                            const float* r, float* d, double* f, float* g, float* x_update, float eta,
                            cudaStream_t s) {
     const bool quad = mode == ADJ_MODE_QUADRATIC;
-    const Tuning t = adjoint_tuning(A);
-    const uint32_t W = adjoint_warps(A, t, quad, kMaxSmemPerBlock);
-    if (W == 0) return cudaErrorInvalidConfiguration;
+    AdjTuning t;
+    size_t smem = 0;
+    if (!adjoint_shape(A, A->adj_tuning, quad, &t, &smem)) return cudaErrorInvalidConfiguration;
     if (A->nrows > 0) {
         AdjParams prm;
         prm.row_ptr = A->row_ptr;
         prm.col = A->col;
         prm.val = A->val;
-        prm.row_scale = A->row_scale;
         prm.scale = A->scale;
         prm.x = x;
-        prm.p = p;
-        prm.w = w;
-        prm.r = r;
         prm.d = d;
         prm.g_part = A->g_part;
         prm.f_part = A->f_part;
         prm.nrows = A->nrows;
         prm.ncols = A->ncols;
-        prm.sched = ScheduleView{A->st_row0, A->st_nz0, A->st_meta, A->st_cta_begin};
+        prm.sched = ScheduleView{A->adj.desc, A->adj.ne, A->adj.cta_begin};
+        const uint32_t user_lim = A->nrows & ~3u;  // caller arrays: whole 16-byte pieces only
+        prm.vecs.n = 0;
+        if (quad) {
+            prm.vecs.ptr[0] = p;
+            prm.vecs.lim[0] = user_lim;
+            prm.vecs.ptr[1] = w;
+            prm.vecs.lim[1] = user_lim;
+            prm.vecs.n = 2;
+        } else {
+            prm.vecs.ptr[0] = r;
+            prm.vecs.lim[0] = user_lim;
+            prm.vecs.n = 1;
+        }
+        if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {
+            prm.vecs.ptr[prm.vecs.n] = A->row_scale;
+            prm.vecs.lim[prm.vecs.n] = round_up(A->nrows, 4);
+            prm.vecs.n++;
+        }
         prm.tile_nnz = t.tile_nnz;
         prm.tile_rows = t.tile_rows;
         prm.depth = t.stages;
-        prm.cwarps = W;
+        prm.fwarps = t.forward_warps;
+        prm.swarps = t.scatter_warps;
         prm.err = A->err;
-        const size_t smem = adjoint_smem_bytes(A, t, W, quad);
         cudaError_t e = cudaSuccess;
         switch (A->fmt) {
             case DOSE_FMT_U16_SCALE:
@@ -388,9 +446,9 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
         }
         if (e != cudaSuccess) return e;
     }
-    const uint32_t nparts = A->nrows > 0 ? A->grid : 0;
+    const uint32_t nparts = A->nrows > 0 ? A->adj.grid : 0;
     const float scale = A->fmt == DOSE_FMT_U16_SCALE ? A->scale : 1.0f;
-    const uint32_t blocks = A->ncols ? (A->ncols + 255) / 256 : 1;
+    const uint32_t blocks = A->ncols ? (A->ncols + 31) / 32 : 1;
     adjoint_finalize<<<blocks, 256, 0, s>>>(A->g_part, A->f_part, nparts, A->ncols, scale, g, quad ? f : nullptr,
                                             x_update, eta);
     return cudaGetLastError();

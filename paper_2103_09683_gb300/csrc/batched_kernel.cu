@@ -25,8 +25,7 @@ struct BatchItem {
     const float* row_scale;
     const float* X;
     float* D;
-    const uint32_t* st_row0;
-    const uint8_t* st_meta;
+    const StageDesc* desc;
     float scale;
     uint32_t nrows, n_stages;
     uint32_t unit_begin;  // first global unit of this matrix
@@ -72,8 +71,9 @@ __global__ void __launch_bounds__(256) spmm_batched_kernel(const __grid_constant
         while (m + 1 < p.count && p.item[m + 1].unit_begin <= u) ++m;
         const BatchItem& it = p.item[m];
         const uint32_t s = u - it.unit_begin;
-        const uint8_t meta = it.st_meta[s];
-        uint32_t r0 = it.st_row0[s], r1 = it.st_row0[s + 1];
+        const StageDesc D = it.desc[s];
+        const uint32_t meta = D.meta;
+        uint32_t r0 = D.row0, r1 = D.row1;
         if (meta & STAGE_COOP) {
             if (!(meta & STAGE_FIRST)) continue;  // a long row is reduced once, at its first chunk
             r1 = r0 + 1;
@@ -113,14 +113,13 @@ cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const fl
             it.row_scale = M->row_scale;
             it.X = X[base + i];
             it.D = D[base + i];
-            it.st_row0 = M->st_row0;
-            it.st_meta = M->st_meta;
+            it.desc = M->fwd.desc;
             it.scale = M->scale;
             it.nrows = M->nrows;
-            it.n_stages = M->n_stages;
+            it.n_stages = M->fwd.n_stages;
             it.unit_begin = units;
             it.fmt = M->fmt;
-            units += M->n_stages;
+            units += M->fwd.n_stages;
         }
         p.total_units = units;
         if (units == 0) continue;

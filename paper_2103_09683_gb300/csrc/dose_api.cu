@@ -134,45 +134,52 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
         const uint32_t len = rp[r + 1] - rp[r];
         if (len > t.coop_nnz) {
             const uint32_t nch = (len + t.tile_nnz - 1) / t.tile_nnz;
+            const uint32_t ne = (uint32_t)S.ne.size();
             for (uint32_t c = 0; c < nch; ++c) {
-                S.row0.push_back(r);
-                S.nz0.push_back(rp[r] + c * t.tile_nnz);
-                uint8_t m = STAGE_COOP;
-                if (c == 0) m |= STAGE_FIRST;
-                if (c + 1 == nch) m |= STAGE_LAST;
-                S.meta.push_back(m);
+                StageDesc D{};
+                D.row0 = r;
+                D.row1 = r + 1;
+                D.nz0 = rp[r] + c * t.tile_nnz;
+                D.nz1 = std::min(rp[r + 1], D.nz0 + t.tile_nnz);
+                D.ne0 = D.ne1 = ne;
+                D.meta = STAGE_COOP | (c == 0 ? STAGE_FIRST : 0u) | (c + 1 == nch ? STAGE_LAST : 0u);
+                S.desc.push_back(D);
             }
             ++S.n_coop_rows;
             ++r;
             continue;
         }
-        const uint32_t start = r;
+        StageDesc D{};
+        D.row0 = r;
+        D.nz0 = rp[r];
+        D.ne0 = (uint32_t)S.ne.size();
         uint64_t nz = 0;
-        uint32_t nonempty = 0;
-        while (r < nrows && r - start < t.tile_rows) {
+        while (r < nrows && r - D.row0 < t.tile_rows) {
             const uint32_t l = rp[r + 1] - rp[r];
             if (l > t.coop_nnz || nz + l > t.tile_nnz) break;
             nz += l;
-            nonempty += l > 0;
+            if (l) S.ne.push_back((uint16_t)(r - D.row0));
             ++r;
         }
+        D.row1 = r;
+        D.nz1 = rp[r];
+        D.ne1 = (uint32_t)S.ne.size();
+        const uint32_t nonempty = D.ne1 - D.ne0;
         const double mean = nonempty ? (double)nz / nonempty : 0.0;
         const uint32_t lg = nonempty ? nearest_pow2_log2(mean / t.lane_target) : 5;
-        S.row0.push_back(start);
-        S.nz0.push_back(rp[start]);
-        S.meta.push_back((uint8_t)lg);
+        D.meta = lg;
+        S.desc.push_back(D);
         ++S.lanes_hist[lg];
     }
-    S.row0.push_back(nrows);
-    S.nz0.push_back(rp[nrows]);
 
     // Contiguous stage ranges per CTA, balanced by streamed bytes; never split
     // the chunks of one long row across CTAs.
-    const size_t n = S.meta.size();
+    const size_t n = S.desc.size();
     std::vector<double> wcum(n + 1, 0.0);
     for (size_t s = 0; s < n; ++s) {
-        const double rows = (S.meta[s] & STAGE_COOP) ? 0.0 : (double)(S.row0[s + 1] - S.row0[s]);
-        wcum[s + 1] = wcum[s] + 6.0 * (S.nz0[s + 1] - S.nz0[s]) + 8.0 * rows + 256.0;
+        const StageDesc& D = S.desc[s];
+        const double rows = (D.meta & STAGE_COOP) ? 0.0 : (double)(D.row1 - D.row0);
+        wcum[s + 1] = wcum[s] + 6.0 * (D.nz1 - D.nz0) + 8.0 * rows + 2.0 * (D.ne1 - D.ne0) + 256.0;
     }
     S.cta_begin.assign(grid + 1, (uint32_t)n);
     S.cta_begin[0] = 0;
@@ -180,7 +187,7 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
     for (uint32_t c = 1; c < grid; ++c) {
         const double target = wcum[n] * c / grid;
         while (s < n && wcum[s] < target) ++s;
-        while (s < n && (S.meta[s] & STAGE_COOP) && !(S.meta[s] & STAGE_FIRST)) ++s;
+        while (s < n && (S.desc[s].meta & STAGE_COOP) && !(S.desc[s].meta & STAGE_FIRST)) ++s;
         S.cta_begin[c] = (uint32_t)std::max<size_t>(s, S.cta_begin[c - 1]);
     }
     S.cta_begin[grid] = (uint32_t)n;
@@ -189,23 +196,19 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
 
 // ------------------------------------------------------------ handle state
 
-struct DevFree {
-    void operator()(void* p) const {
-        if (p) cudaFree(p);
-    }
-};
-
-static void free_schedule(dose_matrix* A) {
-    cudaFree(A->st_row0);
-    cudaFree(A->st_nz0);
-    cudaFree(A->st_meta);
-    cudaFree(A->st_cta_begin);
-    A->st_row0 = A->st_nz0 = A->st_cta_begin = nullptr;
-    A->st_meta = nullptr;
+static void free_dev_schedule(DevSchedule& D) {
+    cudaFree(D.desc);
+    cudaFree(D.ne);
+    cudaFree(D.cta_begin);
+    D.desc = nullptr;
+    D.ne = nullptr;
+    D.cta_begin = nullptr;
+    D.n_stages = 0;
 }
 
 static void free_all(dose_matrix* A) {
-    free_schedule(A);
+    free_dev_schedule(A->fwd);
+    free_dev_schedule(A->adj);
     cudaFree(A->row_ptr);
     cudaFree(A->col);
     cudaFree(A->val);
@@ -228,16 +231,42 @@ static dose_status check_tuning(const dose_matrix* A, Tuning& t) {
     return DOSE_OK;
 }
 
-static Tuning merge_tuning(const Tuning& base, const dose_tuning* in) {
-    Tuning t = base;
-    if (!in) return t;
+static dose_status check_adj_tuning(const AdjTuning& t) {
+    if (t.tile_nnz < 256 || t.tile_nnz > 16384) return invalid("tuning.adj_tile_nnz must be in [256, 16384]");
+    if (t.tile_rows < 32 || t.tile_rows > 8192) return invalid("tuning.adj_tile_rows must be in [32, 8192]");
+    if (t.stages < 2 || t.stages > 8) return invalid("tuning.adj_stages must be in [2, 8]");
+    if (t.forward_warps < 1 || t.forward_warps > 15) return invalid("tuning.adj_forward_warps must be in [1, 15]");
+    if (t.scatter_warps > 15) return invalid("tuning.adj_scatter_warps must be in [0, 15]");
+    return DOSE_OK;
+}
+
+static void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
+    if (!in) return;
     if (in->tile_nnz) t.tile_nnz = in->tile_nnz;
     if (in->tile_rows) t.tile_rows = in->tile_rows;
     if (in->coop_nnz) t.coop_nnz = in->coop_nnz;
     if (in->lane_target) t.lane_target = in->lane_target;
     if (in->stages) t.stages = in->stages;
     if (in->consumer_warps) t.consumer_warps = in->consumer_warps;
-    return t;
+    if (in->adj_tile_nnz) a.tile_nnz = in->adj_tile_nnz;
+    if (in->adj_tile_rows) a.tile_rows = in->adj_tile_rows;
+    if (in->adj_stages) a.stages = in->adj_stages;
+    if (in->adj_forward_warps) a.forward_warps = in->adj_forward_warps;
+    if (in->adj_scatter_warps) a.scatter_warps = in->adj_scatter_warps;
+}
+
+static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out) {
+    out->tile_nnz = t.tile_nnz;
+    out->tile_rows = t.tile_rows;
+    out->coop_nnz = t.coop_nnz;
+    out->lane_target = t.lane_target;
+    out->stages = t.stages;
+    out->consumer_warps = t.consumer_warps;
+    out->adj_tile_nnz = a.tile_nnz;
+    out->adj_tile_rows = a.tile_rows;
+    out->adj_stages = a.stages;
+    out->adj_forward_warps = a.forward_warps;
+    out->adj_scatter_warps = a.scatter_warps;
 }
 
 template <class T>
@@ -250,20 +279,34 @@ static cudaError_t upload(T** dst, const T* src, size_t n, size_t alloc_n) {
     return e;
 }
 
-static dose_status apply_schedule(dose_matrix* A, const Tuning& t) {
-    Schedule S = build_schedule(A->host_row_ptr, A->nrows, t, A->grid);
-    free_schedule(A);
+// Build one schedule on the host and replace `D` with its device copy.
+static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& t) {
+    Schedule S = build_schedule(A->host_row_ptr, A->nrows, t, D.grid);
+    free_dev_schedule(D);
     cudaError_t e;
-    if ((e = upload(&A->st_row0, S.row0.data(), S.row0.size(), S.row0.size())) != cudaSuccess ||
-        (e = upload(&A->st_nz0, S.nz0.data(), S.nz0.size(), S.nz0.size())) != cudaSuccess ||
-        (e = upload(&A->st_meta, S.meta.data(), S.meta.size(), S.meta.size() + 16)) != cudaSuccess ||
-        (e = upload(&A->st_cta_begin, S.cta_begin.data(), S.cta_begin.size(), S.cta_begin.size())) != cudaSuccess)
+    if ((e = upload(&D.desc, S.desc.data(), S.desc.size(), S.desc.size() + 1)) != cudaSuccess ||
+        (e = upload(&D.ne, S.ne.data(), S.ne.size(), (S.ne.size() + 7) / 8 * 8 + 16)) != cudaSuccess ||
+        (e = upload(&D.cta_begin, S.cta_begin.data(), S.cta_begin.size(), S.cta_begin.size())) != cudaSuccess)
         return cuda_fail(e, "uploading the schedule");
-    A->n_stages = (uint32_t)S.meta.size();
-    A->n_coop_rows = S.n_coop_rows;
-    std::memcpy(A->lanes_hist, S.lanes_hist, sizeof(A->lanes_hist));
-    A->tuning = t;
+    D.n_stages = (uint32_t)S.desc.size();
+    D.n_coop_rows = S.n_coop_rows;
+    std::memcpy(D.lanes_hist, S.lanes_hist, sizeof(D.lanes_hist));
+    D.tuning = t;
     return DOSE_OK;
+}
+
+// The adjoint schedule: its own tile sizes, the forward's lane binning.
+static Tuning adj_schedule_tuning(const Tuning& fwd, const AdjTuning& a) {
+    Tuning t = fwd;
+    t.tile_nnz = a.tile_nnz;
+    t.tile_rows = a.tile_rows;
+    t.coop_nnz = std::min(fwd.coop_nnz, a.tile_nnz);
+    t.stages = a.stages;
+    return t;
+}
+
+static uint64_t schedule_bytes(const DevSchedule& D) {
+    return (uint64_t)(D.n_stages + 1) * sizeof(StageDesc) + (D.grid + 1) * 4;
 }
 
 static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
@@ -381,13 +424,17 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if ((e = cudaGetDevice(&A->device)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if ((e = cudaDeviceGetAttribute(&A->sm_count, cudaDevAttrMultiProcessorCount, A->device)) != cudaSuccess)
         return cuda_fail(e, "cudaDeviceGetAttribute");
-    A->grid = (uint32_t)std::max(1, A->sm_count);
+    A->fwd.grid = A->adj.grid = (uint32_t)std::max(1, A->sm_count);
     A->host_row_ptr = std::move(rp);
-    Tuning t = merge_tuning(Tuning(), tuning);
+    Tuning t;
+    AdjTuning at;
+    merge_tuning(t, at, tuning);
     {
         dose_status st = check_tuning(A.get(), t);
+        if (st == DOSE_OK) st = check_adj_tuning(at);
         if (st != DOSE_OK) return st;
     }
+    A->adj_tuning = at;
     auto fail = [&](cudaError_t err, const char* what) {
         free_all(A.get());
         return err == cudaErrorMemoryAllocation ? (set_error(std::string(what) + ": out of device memory"),
@@ -405,13 +452,14 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE &&
         (e = upload(&A->row_scale, scl.data(), (size_t)nrows, (size_t)nrows + 16)) != cudaSuccess)
         return fail(e, "row scales");
-    if ((e = cudaMalloc(&A->g_part, std::max<size_t>((size_t)A->grid * ncols, 1) * 4)) != cudaSuccess)
+    if ((e = cudaMalloc(&A->g_part, std::max<size_t>((size_t)A->adj.grid * ncols, 1) * 4)) != cudaSuccess)
         return fail(e, "adjoint partials");
-    if ((e = cudaMalloc(&A->f_part, (size_t)A->grid * 8)) != cudaSuccess) return fail(e, "objective partials");
+    if ((e = cudaMalloc(&A->f_part, (size_t)A->adj.grid * 8)) != cudaSuccess) return fail(e, "objective partials");
     if ((e = cudaMalloc(&A->err, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     if ((e = cudaMemset(A->err, 0, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     {
-        dose_status st = apply_schedule(A.get(), t);
+        dose_status st = apply_schedule(A.get(), A->fwd, t);
+        if (st == DOSE_OK) st = apply_schedule(A.get(), A->adj, adj_schedule_tuning(t, at));
         if (st != DOSE_OK) {
             free_all(A.get());
             return st;
@@ -419,8 +467,8 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     }
     A->device_bytes = rp_alloc * 4 + col_alloc * 4 + val_alloc +
                       (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) +
-                      (size_t)A->grid * ncols * 4 + (size_t)A->grid * 8 + 4 +
-                      (size_t)(A->n_stages + 1) * 9 + (A->grid + 1) * 4;
+                      (size_t)A->adj.grid * ncols * 4 + (size_t)A->adj.grid * 8 + 4 + schedule_bytes(A->fwd) +
+                      schedule_bytes(A->adj);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "create");
     *out = A.release();
     return DOSE_OK;
@@ -442,17 +490,18 @@ dose_status dose_spmv(const dose_matrix* A, const float* x, float* d, void* stre
     return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_spmv launch");
 }
 
-static dose_status adjoint_supported(const dose_matrix* A, bool quad) {
+static dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* const* vecs, int nvec) {
     if (quad && A->ncols > kXSmemMaxCols) {
         set_error("the fused objective pass keeps x in shared memory: ncols must be <= 16384");
         return DOSE_ERR_UNSUPPORTED;
     }
-    Tuning t = A->tuning;
-    if (t.stages > 3) t.stages = 3;
-    if (adjoint_warps(A, t, quad, kMaxSmemPerBlock) == 0) {
+    if (!adjoint_shape(A, A->adj_tuning, quad, nullptr, nullptr)) {
         set_error("per-warp gradient accumulators of ncols floats do not fit in shared memory");
         return DOSE_ERR_UNSUPPORTED;
     }
+    for (int k = 0; k < nvec; ++k)
+        if (vecs[k] && (reinterpret_cast<uintptr_t>(vecs[k]) & 15u))
+            return invalid("per-row vectors (p, w, r) must be 16-byte aligned");
     return DOSE_OK;
 }
 
@@ -460,7 +509,8 @@ dose_status dose_adjoint(const dose_matrix* A, const float* r, float* g, void* s
     if (!A) return invalid("dose_adjoint: null matrix");
     if (A->nrows && !r) return invalid("dose_adjoint: r is NULL");
     if (A->ncols && !g) return invalid("dose_adjoint: g is NULL");
-    dose_status st = adjoint_supported(A, false);
+    const float* vv[1] = {r};
+    dose_status st = adjoint_supported(A, false, vv, 1);
     if (st != DOSE_OK) return st;
     cudaError_t e = launch_adjoint(A, ADJ_MODE_ADJOINT, nullptr, nullptr, nullptr, r, nullptr, nullptr, g, nullptr,
                                    0.f, as_stream(stream));
@@ -472,7 +522,8 @@ dose_status dose_fwd_adj_quadratic(const dose_matrix* A, const float* x, const f
     if (!A) return invalid("dose_fwd_adj_quadratic: null matrix");
     if (!f || (A->ncols && (!x || !g)) || (A->nrows && (!p || !w)))
         return invalid("dose_fwd_adj_quadratic: null pointer argument");
-    dose_status st = adjoint_supported(A, true);
+    const float* vv[2] = {p, w};
+    dose_status st = adjoint_supported(A, true, vv, 2);
     if (st != DOSE_OK) return st;
     cudaError_t e = launch_adjoint(A, ADJ_MODE_QUADRATIC, x, p, w, nullptr, d, f, g, nullptr, 0.f, as_stream(stream));
     return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_fwd_adj_quadratic launch");
@@ -483,7 +534,8 @@ dose_status dose_pg_step(const dose_matrix* A, float* x, const float* p, const f
     if (!A) return invalid("dose_pg_step: null matrix");
     if (!f || (A->ncols && !x) || (A->nrows && (!p || !w))) return invalid("dose_pg_step: null pointer argument");
     if (!(eta >= 0.0f) || std::isinf(eta)) return invalid("dose_pg_step: eta must be finite and >= 0");
-    dose_status st = adjoint_supported(A, true);
+    const float* vv[2] = {p, w};
+    dose_status st = adjoint_supported(A, true, vv, 2);
     if (st != DOSE_OK) return st;
     cudaError_t e = launch_adjoint(A, ADJ_MODE_QUADRATIC, x, p, w, nullptr, nullptr, f, g, x, eta, as_stream(stream));
     return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_pg_step launch");
@@ -517,11 +569,16 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     out->nnz = A->nnz;
     out->fmt = A->fmt;
     out->flags = A->flags;
-    out->n_stages = A->n_stages;
-    out->n_coop_rows = A->n_coop_rows;
-    std::memcpy(out->lanes_hist, A->lanes_hist, sizeof(out->lanes_hist));
-    out->grid = A->grid;
-    out->block = 32 * (A->tuning.consumer_warps + 1);
+    out->n_stages = A->fwd.n_stages;
+    out->n_coop_rows = A->fwd.n_coop_rows;
+    std::memcpy(out->lanes_hist, A->fwd.lanes_hist, sizeof(out->lanes_hist));
+    out->grid = A->fwd.grid;
+    out->block = 32 * (A->fwd.tuning.consumer_warps + 1);
+    out->adj_n_stages = A->adj.n_stages;
+    AdjTuning sh;
+    if (adjoint_shape(A, A->adj_tuning, true, &sh, nullptr) && A->ncols <= kXSmemMaxCols)
+        out->adj_block_fused = 32 * (1 + sh.forward_warps + sh.scatter_warps);
+    if (adjoint_shape(A, A->adj_tuning, false, &sh, nullptr)) out->adj_block_adjoint = 32 * (1 + sh.scatter_warps);
     out->max_row_len = A->max_row_len;
     out->device_bytes = A->device_bytes;
     const uint64_t vb = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
@@ -532,23 +589,24 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     out->adjoint_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
     out->fused_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 8 * nr + 4 * nc + 4 * nc + 8;
     out->scale = A->fmt == DOSE_FMT_U16_SCALE ? A->scale : 0.f;
-    out->tuning.tile_nnz = A->tuning.tile_nnz;
-    out->tuning.tile_rows = A->tuning.tile_rows;
-    out->tuning.coop_nnz = A->tuning.coop_nnz;
-    out->tuning.lane_target = A->tuning.lane_target;
-    out->tuning.stages = A->tuning.stages;
-    out->tuning.consumer_warps = A->tuning.consumer_warps;
+    export_tuning(A->fwd.tuning, A->adj_tuning, &out->tuning);
     return DOSE_OK;
 }
 
 dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning) {
     if (!A) return invalid("dose_set_tuning: null matrix");
-    Tuning t = merge_tuning(A->tuning, tuning);
+    Tuning t = A->fwd.tuning;
+    AdjTuning at = A->adj_tuning;
+    merge_tuning(t, at, tuning);
     dose_status st = check_tuning(A, t);
+    if (st == DOSE_OK) st = check_adj_tuning(at);
     if (st != DOSE_OK) return st;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "dose_set_tuning");
-    return apply_schedule(A, t);
+    st = apply_schedule(A, A->fwd, t);
+    if (st != DOSE_OK) return st;
+    A->adj_tuning = at;
+    return apply_schedule(A, A->adj, adj_schedule_tuning(t, at));
 }
 
 dose_status dose_device_status(const dose_matrix* A, void* stream) {
@@ -577,7 +635,7 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const Tuning orig = A->tuning;
+    const Tuning orig = A->fwd.tuning;
     Tuning best_t = orig;
     float best_ms = 1e30f;
     const uint32_t nnzs[] = {2048, 4096, 8192};
@@ -596,7 +654,7 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
                     t.lane_target = lt;
                     t.stages = sd;
                     if (check_tuning(A, t) != DOSE_OK) continue;
-                    if (apply_schedule(A, t) != DOSE_OK) continue;
+                    if (apply_schedule(A, A->fwd, t) != DOSE_OK) continue;
                     for (int i = 0; i < 3; ++i) launch_spmv(A, x, d, s);
                     const int reps = 10;
                     cudaEventRecord(e0, s);
@@ -618,19 +676,12 @@ done:
     cudaEventDestroy(e1);
     cudaFree(d);
     if (result != DOSE_OK) {
-        apply_schedule(A, orig);
+        apply_schedule(A, A->fwd, orig);
         return result;
     }
-    dose_status st = apply_schedule(A, best_t);
+    dose_status st = apply_schedule(A, A->fwd, best_t);
     if (st != DOSE_OK) return st;
-    if (best) {
-        best->tile_nnz = best_t.tile_nnz;
-        best->tile_rows = best_t.tile_rows;
-        best->coop_nnz = best_t.coop_nnz;
-        best->lane_target = best_t.lane_target;
-        best->stages = best_t.stages;
-        best->consumer_warps = best_t.consumer_warps;
-    }
+    if (best) export_tuning(best_t, A->adj_tuning, best);
     return DOSE_OK;
 }
 

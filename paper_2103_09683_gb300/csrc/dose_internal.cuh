@@ -18,9 +18,11 @@ namespace dose {
 // The matrix rows are cut into pipeline stages ("row blocks"), each staged in
 // shared memory by bulk async copies:
 //   NORMAL stage: consecutive rows [row0, row1), at most tile_rows rows and
-//                 tile_nnz entries, none longer than coop_nnz.  Rows are handled
-//                 32 at a time by one warp; the non-empty ones by groups of
-//                 L = 2^lanes_log2 lanes (row-length binning per stage).
+//                 tile_nnz entries, none longer than coop_nnz.  Its non-empty
+//                 rows are listed (u16 offsets from row0, ne list) so that every
+//                 consumer warp gets an even share of them; they are reduced by
+//                 groups of L = 2^lanes_log2 lanes, L chosen per stage from the
+//                 stage's mean row length (row-length binning).  Empty rows get 0.
 //   COOP stage:   one chunk (<= tile_nnz entries) of one row longer than
 //                 coop_nnz; all consumer warps reduce it together.  A row of
 //                 several chunks occupies consecutive stages FIRST..LAST.
@@ -33,6 +35,15 @@ enum : uint32_t {
     STAGE_LAST = 0x20u,
 };
 
+// One stage, as stored on the device (32 bytes, two 16-byte loads).
+struct StageDesc {
+    uint32_t row0, row1;  // rows [row0, row1) (COOP: row1 = row0 + 1)
+    uint32_t nz0, nz1;    // entries [nz0, nz1) of this stage
+    uint32_t ne0, ne1;    // its slice of the non-empty-row list
+    uint32_t meta;        // STAGE_* bits
+    uint32_t pad;
+};
+
 struct Tuning {
     uint32_t tile_nnz = 4096;
     uint32_t tile_rows = 2048;
@@ -43,20 +54,39 @@ struct Tuning {
 };
 
 struct Schedule {
-    std::vector<uint32_t> row0;    // n_stages + 1
-    std::vector<uint32_t> nz0;     // n_stages + 1
-    std::vector<uint8_t> meta;     // n_stages
+    std::vector<StageDesc> desc;      // n_stages
+    std::vector<uint16_t> ne;         // non-empty rows of NORMAL stages (offset from row0)
     std::vector<uint32_t> cta_begin;  // grid + 1
     uint32_t n_coop_rows = 0;
     uint32_t lanes_hist[6] = {0, 0, 0, 0, 0, 0};
 };
 
-// Device-side view of a schedule, passed to kernels by value.
+// Device copy of a schedule.
+struct DevSchedule {
+    StageDesc* desc = nullptr;
+    uint16_t* ne = nullptr;
+    uint32_t* cta_begin = nullptr;
+    uint32_t n_stages = 0;
+    uint32_t grid = 0;
+    uint32_t n_coop_rows = 0;
+    uint32_t lanes_hist[6] = {0, 0, 0, 0, 0, 0};
+    Tuning tuning;
+};
+
+// Kernel-side view of a schedule, passed by value.
 struct ScheduleView {
-    const uint32_t* row0;
-    const uint32_t* nz0;
-    const uint8_t* meta;
+    const StageDesc* desc;
+    const uint16_t* ne;
     const uint32_t* cta_begin;
+};
+
+// Shape of the adjoint / fused kernels (warp specialisation and pipeline).
+struct AdjTuning {
+    uint32_t tile_nnz = 2048;
+    uint32_t tile_rows = 1024;
+    uint32_t stages = 3;
+    uint32_t forward_warps = 8;   // fused pass: warps computing d, f and r
+    uint32_t scatter_warps = 0;   // warps owning gradient accumulators (0 = as many as fit)
 };
 
 }  // namespace dose
@@ -77,22 +107,13 @@ struct dose_matrix {
     void* val = nullptr;
     float* row_scale = nullptr;  // FP8 only
 
-    // schedule (device)
-    uint32_t* st_row0 = nullptr;
-    uint32_t* st_nz0 = nullptr;
-    uint8_t* st_meta = nullptr;
-    uint32_t* st_cta_begin = nullptr;
-    uint32_t n_stages = 0;
-    uint32_t grid = 0;
-    uint32_t n_coop_rows = 0;
-    uint32_t lanes_hist[6] = {0, 0, 0, 0, 0, 0};
-    dose::Tuning tuning;
+    dose::DevSchedule fwd;      // schedule of dose_spmv (and the batched SpMM)
+    dose::DevSchedule adj;      // schedule of the adjoint / fused kernels
+    dose::AdjTuning adj_tuning;
 
     // adjoint scratch: per-CTA partial gradients and objective values
-    float* g_part = nullptr;     // grid_adj * ncols
-    double* f_part = nullptr;    // grid_adj
-    uint32_t grid_adj = 0;
-    uint32_t* adj_cta_begin = nullptr;  // grid_adj + 1 (schedule split for the adjoint grid)
+    float* g_part = nullptr;     // adj.grid * ncols
+    double* f_part = nullptr;    // adj.grid
 
     int* err = nullptr;  // device error word (0 = ok)
     uint64_t device_bytes = 0;
@@ -109,11 +130,11 @@ dose_status cuda_fail(cudaError_t e, const char* what);
 size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem);
 bool spmv_x_in_smem(const dose_matrix* A);
 cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s);
+// Adjoint shape that fits in shared memory: fills forward/scatter warp counts; false if none.
+bool adjoint_shape(const dose_matrix* A, const AdjTuning& in, bool quad, AdjTuning* out, size_t* smem);
 cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const float* p,
                            const float* w, const float* r, float* d, double* f, float* g,
                            float* x_update, float eta, cudaStream_t s);
-size_t adjoint_smem_bytes(const dose_matrix* A, const Tuning& t, uint32_t warps, bool need_x);
-uint32_t adjoint_warps(const dose_matrix* A, const Tuning& t, bool need_x, int max_smem);
 cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const float* const* X,
                                 float* const* D, int nvec, cudaStream_t s, std::string* why);
 

@@ -5,14 +5,14 @@
 // GB300 design (not the paper's one-warp-per-row grid):
 //   * persistent CTAs, one per SM, each owning a contiguous range of row blocks
 //     ("stages") fixed at create time;
-//   * one producer warp streams each stage's row_ptr / value / column slices
-//     into shared memory with bulk async copies (cp.async.bulk + mbarrier
-//     transaction counts), `stages` deep, so HBM sees a few large contiguous
-//     reads per stage instead of per-warp gathers;
-//   * consumer warps take 32 consecutive rows at a time, write 0 for empty rows
-//     (coalesced), and reduce the non-empty ones with groups of L lanes per row,
-//     L chosen per stage from its mean row length (row-length binning);
-//     rows longer than coop_nnz are reduced by the whole CTA;
+//   * one producer warp streams each stage's row_ptr / non-empty-row list /
+//     value / column slices into a shared-memory ring with bulk async copies
+//     (cp.async.bulk + mbarrier transaction counts), so HBM sees a few large
+//     contiguous reads per stage and consumers never wait on global memory;
+//   * consumer warps write 0 for the stage's empty rows (coalesced) and share
+//     its non-empty rows evenly: groups of L lanes per row, L chosen per stage
+//     from its mean row length (row-length binning); rows longer than coop_nnz
+//     are reduced by the whole CTA;
 //   * values are decoded in registers (u16 -> f32, bf16 -> f32, e4m3 -> f32),
 //     x sits in shared memory, accumulation is FP32 (optionally compensated),
 //     and the U16/FP8 scale is applied once per row.
@@ -26,17 +26,17 @@ struct SpmvParams {
     const uint32_t* row_ptr;
     const uint32_t* col;
     const void* val;
-    const float* row_scale;
     float scale;
     const float* x;
     float* d;
     uint32_t nrows, ncols;
     ScheduleView sched;
+    VecSet vecs;  // FP8: the row scales
     uint32_t tile_nnz, tile_rows, depth, cwarps;
     int* err;
 };
 
-constexpr uint32_t kHeaderBytes = 1024;  // mbarriers (<= 16 x 16 B) + reduction scratch
+constexpr uint32_t kHeaderBytes = 1024;  // mbarriers (<= 16 x 8 B) + CTA reduction scratch
 
 // Accumulate entries kb, kb+step, ... < ke of one row.  vs/cs hold the stage's
 // value and column slices starting at global entry vb / cb.
@@ -68,6 +68,31 @@ __device__ __forceinline__ void accumulate_row(const typename Fmt<FMT>::T* __res
     }
 }
 
+// Combine the (sum, compensation) pairs of the `width` lanes of a group.
+template <bool COMP>
+__device__ __forceinline__ void group_reduce(float& sum, float& comp, uint32_t width) {
+    for (uint32_t off = width >> 1; off > 0; off >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, sum, off);
+        if (COMP) {
+            const float oc = __shfl_xor_sync(0xffffffffu, comp, off);
+            float t, e;
+            dev::two_sum(sum, os, t, e);
+            sum = t;
+            comp = __fadd_rn(__fadd_rn(comp, oc), e);
+        } else {
+            sum = __fadd_rn(sum, os);
+        }
+    }
+}
+
+template <int FMT>
+__device__ __forceinline__ float row_result(const SpmvParams& p, const unsigned char* buf, const SlotLayout& SL,
+                                            uint32_t row0, uint32_t row, float v) {
+    if (FMT == DOSE_FMT_U16_SCALE) return __fmul_rn(p.scale, v);
+    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) return __fmul_rn(slot_vec(buf, SL, p.vecs, 0, row0, row), v);
+    return v;
+}
+
 template <int FMT, bool COMP, bool XSMEM>
 __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     using T = typename Fmt<FMT>::T;
@@ -75,19 +100,17 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t S = p.depth;
+    const uint32_t S = p.depth, W = p.cwarps;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + S;
-    float* red = reinterpret_cast<float*>(smem + 256);            // 64 floats: CTA reduction
-    uint8_t* rowlist = smem + 512;                                 // 16 warps x 32 bytes
+    float* red = reinterpret_cast<float*>(smem + 256);  // 64 floats: CTA reduction
     float* xs = reinterpret_cast<float*>(smem + kHeaderBytes);
     const uint32_t x_bytes = XSMEM ? round_up(p.ncols * 4, 128) : 0;
-    unsigned char* stage_base = smem + kHeaderBytes + x_bytes;
-    const StageLayout SL = stage_layout(p.tile_nnz, p.tile_rows, sizeof(T));
+    unsigned char* slot_base = smem + kHeaderBytes + x_bytes;
+    const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, sizeof(T), p.vecs.n, false);
 
     const uint32_t s_begin = p.sched.cta_begin[blockIdx.x];
     const uint32_t s_end = p.sched.cta_begin[blockIdx.x + 1];
-    const uint32_t W = p.cwarps;
 
     if (threadIdx.x == 0) {
         for (uint32_t i = 0; i < S; ++i) {
@@ -100,22 +123,20 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     if (s_begin >= s_end) return;
 
     if (warp == 0) {
-        // ---------------- producer: one thread streams stage slices into smem
         if (lane == 0)
-            run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, stage_base, SL, full, empty, S,
-                              p.err);
+            run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, p.vecs, slot_base, SL, full,
+                              empty, S, p.err);
         return;
     }
 
     // -------------------- consumers
-    const uint32_t cw = warp - 1;          // consumer warp index
+    const uint32_t cw = warp - 1;
     const uint32_t ctid = threadIdx.x - 32;
     const uint32_t nct = W * 32;
     if (XSMEM) {
         for (uint32_t j = ctid; j < p.ncols; j += nct) xs[j] = __ldg(p.x + j);
         dev::named_barrier(1, nct);
     }
-    uint8_t* my_rows = rowlist + cw * 32;
     float coop_s = 0.f, coop_c = 0.f;
 
     uint32_t st = 0, ph = 0;
@@ -124,90 +145,55 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
             atomicExch(p.err, kErrTimeoutFull);
             return;
         }
-        const unsigned char* buf = stage_base + st * SL.bytes;
-        const uint8_t meta = p.sched.meta[s];
-        const uint32_t nz0 = p.sched.nz0[s], nz1 = p.sched.nz0[s + 1];
+        const unsigned char* buf = slot_base + st * SL.bytes;
+        const StageDesc D = *reinterpret_cast<const StageDesc*>(buf + SL.hdr_off);
         const T* vs = reinterpret_cast<const T*>(buf + SL.val_off);
         const uint32_t* cs = reinterpret_cast<const uint32_t*>(buf + SL.col_off);
-        const uint32_t vb = nz0 & ~(VA - 1), cb = nz0 & ~3u;
+        const uint32_t vb = D.nz0 & ~(VA - 1), cb = D.nz0 & ~3u;
 
-        if (!(meta & STAGE_COOP)) {
-            const uint32_t r0 = p.sched.row0[s], r1 = p.sched.row0[s + 1];
+        if (!(D.meta & STAGE_COOP)) {
             const uint32_t* rps = reinterpret_cast<const uint32_t*>(buf + SL.rp_off);
-            const uint32_t rb0 = r0 & ~3u;
-            const uint32_t lg = meta & STAGE_LANES_MASK;
-            const uint32_t L = 1u << lg, NG = 32u >> lg;
-            const uint32_t g = lane >> lg, li = lane & (L - 1);
-            const uint32_t nchunks = (r1 - r0 + 31) / 32;
-            for (uint32_t c = (cw + W - (s % W)) % W; c < nchunks; c += W) {
-                const uint32_t rb = r0 + c * 32;
-                const uint32_t r = rb + lane;
-                const bool valid = r < r1;
-                const uint32_t beg = valid ? rps[r - rb0] : 0, end = valid ? rps[r + 1 - rb0] : 0;
-                const unsigned nonempty = __ballot_sync(0xffffffffu, end > beg);
-                if (valid && end == beg) p.d[r] = 0.0f;
-                if (end > beg) my_rows[__popc(nonempty & ((1u << lane) - 1))] = (uint8_t)lane;
-                __syncwarp();
-                const uint32_t cnt = __popc(nonempty);
-                for (uint32_t base = 0; base < cnt; base += NG) {
-                    const uint32_t idx = base + g;
-                    const bool has = idx < cnt;
-                    const uint32_t j = has ? my_rows[idx] : 0;
-                    const uint32_t rs = __shfl_sync(0xffffffffu, beg, j);
-                    const uint32_t re = __shfl_sync(0xffffffffu, end, j);
-                    float sum = 0.f, comp = 0.f;
-                    if (has) {
-                        if (COMP && re - rs > kCompThreshold)
-                            accumulate_row<FMT, true>(vs, vb, cs, cb, xs, p.x, XSMEM, rs + li, re, L, sum, comp);
-                        else
-                            accumulate_row<FMT, false>(vs, vb, cs, cb, xs, p.x, XSMEM, rs + li, re, L, sum, comp);
-                    }
-                    for (uint32_t off = L >> 1; off > 0; off >>= 1) {
-                        const float os = __shfl_xor_sync(0xffffffffu, sum, off);
-                        if (COMP) {
-                            const float oc = __shfl_xor_sync(0xffffffffu, comp, off);
-                            float t, e;
-                            dev::two_sum(sum, os, t, e);
-                            sum = t;
-                            comp = __fadd_rn(__fadd_rn(comp, oc), e);
-                        } else {
-                            sum = __fadd_rn(sum, os);
-                        }
-                    }
-                    if (has && li == 0) {
-                        float v = COMP ? __fadd_rn(sum, comp) : sum;
-                        const uint32_t row = rb + j;
-                        if (FMT == DOSE_FMT_U16_SCALE) v = __fmul_rn(p.scale, v);
-                        if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) v = __fmul_rn(__ldg(p.row_scale + row), v);
-                        p.d[row] = v;
-                    }
+            const uint16_t* nes = reinterpret_cast<const uint16_t*>(buf + SL.ne_off) + (D.ne0 & 7u);
+            const uint32_t rb0 = D.row0 & ~3u;
+            // empty rows: write 0 (coalesced)
+            for (uint32_t r = D.row0 + ctid; r < D.row1; r += nct)
+                if (rps[r - rb0] == rps[r + 1 - rb0]) p.d[r] = 0.0f;
+            // non-empty rows: groups of L lanes, entries i = gid, gid + G, ...
+            const uint32_t lg = D.meta & STAGE_LANES_MASK;
+            const uint32_t L = 1u << lg;
+            const uint32_t gid = ctid >> lg, li = lane & (L - 1), G = nct >> lg;
+            const uint32_t n_ne = D.ne1 - D.ne0;
+            for (uint32_t base = 0; base < n_ne; base += G) {
+                const uint32_t i = base + gid;
+                const bool has = i < n_ne;
+                float sum = 0.f, comp = 0.f;
+                uint32_t row = 0;
+                if (has) {
+                    row = D.row0 + nes[i];
+                    const uint32_t rs = rps[row - rb0], re = rps[row + 1 - rb0];
+                    if (COMP && re - rs > kCompThreshold)
+                        accumulate_row<FMT, true>(vs, vb, cs, cb, xs, p.x, XSMEM, rs + li, re, L, sum, comp);
+                    else
+                        accumulate_row<FMT, false>(vs, vb, cs, cb, xs, p.x, XSMEM, rs + li, re, L, sum, comp);
                 }
-                __syncwarp();
+                group_reduce<COMP>(sum, comp, L);
+                if (has && li == 0)
+                    p.d[row] = row_result<FMT>(p, buf, SL, D.row0, row, COMP ? __fadd_rn(sum, comp) : sum);
             }
         } else {
             // one chunk of a long row, reduced by every consumer thread
-            if (meta & STAGE_FIRST) {
+            if (D.meta & STAGE_FIRST) {
                 coop_s = 0.f;
                 coop_c = 0.f;
             }
             if (COMP)
-                accumulate_row<FMT, true>(vs, vb, cs, cb, xs, p.x, XSMEM, nz0 + ctid, nz1, nct, coop_s, coop_c);
+                accumulate_row<FMT, true>(vs, vb, cs, cb, xs, p.x, XSMEM, D.nz0 + ctid, D.nz1, nct, coop_s, coop_c);
             else
-                accumulate_row<FMT, false>(vs, vb, cs, cb, xs, p.x, XSMEM, nz0 + ctid, nz1, nct, coop_s, coop_c);
-            if (meta & STAGE_LAST) {
+                accumulate_row<FMT, false>(vs, vb, cs, cb, xs, p.x, XSMEM, D.nz0 + ctid, D.nz1, nct, coop_s,
+                                           coop_c);
+            if (D.meta & STAGE_LAST) {
                 float sum = coop_s, comp = coop_c;
-                for (uint32_t off = 16; off > 0; off >>= 1) {
-                    const float os = __shfl_xor_sync(0xffffffffu, sum, off);
-                    if (COMP) {
-                        const float oc = __shfl_xor_sync(0xffffffffu, comp, off);
-                        float t, e;
-                        dev::two_sum(sum, os, t, e);
-                        sum = t;
-                        comp = __fadd_rn(__fadd_rn(comp, oc), e);
-                    } else {
-                        sum = __fadd_rn(sum, os);
-                    }
-                }
+                group_reduce<COMP>(sum, comp, 32);
                 if (lane == 0) {
                     red[cw] = sum;
                     red[32 + cw] = comp;
@@ -225,11 +211,7 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
                             tot = __fadd_rn(tot, red[w2]);
                         }
                     }
-                    float v = COMP ? __fadd_rn(tot, tc) : tot;
-                    const uint32_t row = p.sched.row0[s];
-                    if (FMT == DOSE_FMT_U16_SCALE) v = __fmul_rn(p.scale, v);
-                    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) v = __fmul_rn(__ldg(p.row_scale + row), v);
-                    p.d[row] = v;
+                    p.d[D.row0] = row_result<FMT>(p, buf, SL, D.row0, D.row0, COMP ? __fadd_rn(tot, tc) : tot);
                 }
                 dev::named_barrier(1, nct);
             }
@@ -248,7 +230,7 @@ cudaError_t launch_t(const dose_matrix* A, const SpmvParams& p, size_t smem, cud
     auto k = spmv_kernel<FMT, COMP, XSMEM>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<A->grid, 32 * (p.cwarps + 1), smem, s>>>(p);
+    k<<<A->fwd.grid, 32 * (p.cwarps + 1), smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -265,7 +247,8 @@ bool spmv_x_in_smem(const dose_matrix* A) { return A->ncols <= kXSmemMaxCols; }
 
 size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem) {
     const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
-    const StageLayout SL = stage_layout(t.tile_nnz, t.tile_rows, esize);
+    const uint32_t nvec = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
+    const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, false);
     return kHeaderBytes + (x_in_smem ? round_up(A->ncols * 4, 128) : 0) + (size_t)t.stages * SL.bytes;
 }
 
@@ -275,20 +258,25 @@ cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStre
     p.row_ptr = A->row_ptr;
     p.col = A->col;
     p.val = A->val;
-    p.row_scale = A->row_scale;
     p.scale = A->scale;
     p.x = x;
     p.d = d;
     p.nrows = A->nrows;
     p.ncols = A->ncols;
-    p.sched = ScheduleView{A->st_row0, A->st_nz0, A->st_meta, A->st_cta_begin};
-    p.tile_nnz = A->tuning.tile_nnz;
-    p.tile_rows = A->tuning.tile_rows;
-    p.depth = A->tuning.stages;
-    p.cwarps = A->tuning.consumer_warps;
+    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin};
+    p.vecs.n = 0;
+    if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {  // library-owned, padded: every row can be copied
+        p.vecs.n = 1;
+        p.vecs.ptr[0] = A->row_scale;
+        p.vecs.lim[0] = round_up(A->nrows, 4);
+    }
+    p.tile_nnz = A->fwd.tuning.tile_nnz;
+    p.tile_rows = A->fwd.tuning.tile_rows;
+    p.depth = A->fwd.tuning.stages;
+    p.cwarps = A->fwd.tuning.consumer_warps;
     p.err = A->err;
     const bool xsmem = spmv_x_in_smem(A);
-    const size_t smem = spmv_smem_bytes(A, A->tuning, xsmem);
+    const size_t smem = spmv_smem_bytes(A, A->fwd.tuning, xsmem);
     const bool comp = (A->flags & DOSE_CREATE_COMPENSATED) != 0;
     switch (A->fmt) {
         case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, smem, comp, xsmem, s);

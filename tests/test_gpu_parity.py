@@ -122,7 +122,9 @@ def test_adjoint_edge_cases(name):
     if csr.ncols > 16384:
         csr = dosegen.random_csr(csr.nrows, 9000, seed=8,
                                  lengths=np.minimum(csr.row_lengths(), 9000))
-    for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4)):
+    for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4,
+                              adj_tile_nnz=256, adj_tile_rows=32, adj_stages=2, adj_forward_warps=2,
+                              adj_scatter_warps=3)):
         A, enc = make(csr, "u16", tuning=tuning)
         r = np.random.default_rng(9).normal(size=csr.nrows).astype(np.float32)
         g = A.adjoint(_to(r)).cpu().numpy()
