@@ -51,34 +51,34 @@ __device__ __forceinline__ float finish_dot(const AdjParams& p, float rs, float 
 }
 
 // gw[col_k] += a_k * rj for the entries k = kb, kb + step, ... < ke of one row
-// (columns in a row are distinct: the four loads precede the four stores).
+// (gw: shared address of a warp's accumulator).  The columns of a row are
+// distinct, so the four loads may precede the four stores.
 template <int FMT>
-__device__ __forceinline__ void scatter_entries(float* __restrict__ gw, const typename Fmt<FMT>::T* __restrict__ vs,
-                                                uint32_t vb, const uint32_t* __restrict__ cs, uint32_t cb,
-                                                uint32_t kb, uint32_t ke, uint32_t step, float rj) {
+__device__ __forceinline__ void scatter_entries(uint32_t gw, const SlotView& v, uint32_t kb, uint32_t ke,
+                                                uint32_t step, float rj) {
+    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
     for (uint32_t k0 = kb; k0 < ke; k0 += 4 * step) {
-        uint32_t c[4];
+        uint32_t ga[4];
         float a[4], gv[4];
         bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t k = k0 + step * u;
             ok[u] = k < ke;
-            c[u] = ok[u] ? cs[k - cb] : 0;
-            a[u] = ok[u] ? Fmt<FMT>::dec(vs[k - vb]) : 0.f;
+            ga[u] = gw + 4 * (ok[u] ? dev::lds_u32(v.col + 4 * k) : 0u);
+            a[u] = ok[u] ? Fmt<FMT>::lds(v.val + ES * k) : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) gv[u] = ok[u] ? gw[c[u]] : 0.f;
+        for (int u = 0; u < 4; ++u) gv[u] = ok[u] ? dev::lds_f32(ga[u]) : 0.f;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (ok[u]) gw[c[u]] = __fmaf_rn(a[u], rj, gv[u]);
+            if (ok[u]) dev::sts_f32(ga[u], __fmaf_rn(a[u], rj, gv[u]));
     }
 }
 
 template <int FMT, int MODE>
 __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     using T = typename Fmt<FMT>::T;
-    constexpr uint32_t VA = Fmt<FMT>::kAlign;
     constexpr bool QUAD = MODE == ADJ_MODE_QUADRATIC;
     constexpr uint32_t kRowScaleVec = QUAD ? 2 : 1;  // index of the FP8 row scales in vecs
     extern __shared__ __align__(128) unsigned char smem[];
@@ -124,6 +124,8 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
         for (uint32_t j = ctid; j < p.ncols; j += ncons) xs[j] = __ldg(p.x + j);
     dev::named_barrier(1, ncons);
 
+    const uint32_t xs_a = dev::smem_u32(xs);
+    const uint32_t slot0 = dev::smem_u32(slot_base);
     const bool is_fwd = QUAD && warp <= Wf;
     bool failed = false;
     double f_lane = 0.0;
@@ -139,58 +141,51 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
                 failed = true;
                 break;
             }
-            unsigned char* buf = slot_base + st * SL.bytes;
-            const StageDesc D = *reinterpret_cast<const StageDesc*>(buf + SL.hdr_off);
-            const T* vs = reinterpret_cast<const T*>(buf + SL.val_off);
-            const uint32_t* cs = reinterpret_cast<const uint32_t*>(buf + SL.col_off);
-            const uint32_t vb = D.nz0 & ~(VA - 1), cb = D.nz0 & ~3u;
+            const uint32_t slot = slot0 + st * SL.bytes;
+            const StageDesc D = slot_desc(slot);
+            const SlotView v = slot_view<FMT>(slot, SL, D);
             if (!(D.meta & STAGE_COOP)) {
-                const uint32_t* rps = reinterpret_cast<const uint32_t*>(buf + SL.rp_off);
-                const uint16_t* nes = reinterpret_cast<const uint16_t*>(buf + SL.ne_off) + (D.ne0 & 7u);
-                float* rl = reinterpret_cast<float*>(buf + SL.rl_off);
-                const uint32_t rb0 = D.row0 & ~3u;
                 for (uint32_t r = D.row0 + ftid; r < D.row1; r += nft) {
-                    if (rps[r - rb0] == rps[r + 1 - rb0]) {
+                    if (dev::lds_u32(v.rp + 4 * r) == dev::lds_u32(v.rp + 4 * r + 4)) {
                         if (p.d) p.d[r] = 0.0f;
-                        const double pv = slot_vec(buf, SL, p.vecs, 0, D.row0, r);
-                        f_lane += (double)slot_vec(buf, SL, p.vecs, 1, D.row0, r) * pv * pv;
+                        const double pv = slot_vec(slot, SL, p.vecs, 0, D.row0, r);
+                        f_lane += (double)slot_vec(slot, SL, p.vecs, 1, D.row0, r) * pv * pv;
                     }
                 }
                 const uint32_t lg = D.meta & STAGE_LANES_MASK;
                 const uint32_t L = 1u << lg;
                 const uint32_t gid = ftid >> lg, li = lane & (L - 1), G = nft >> lg;
+                const uint32_t rot = ((s % Wf) << (5 - lg)) % G;
+                const uint32_t j0 = (gid + G - rot) % G;
                 const uint32_t n_ne = D.ne1 - D.ne0;
+                const uint32_t rl = slot + SL.rl_off;
                 for (uint32_t base = 0; base < n_ne; base += G) {
-                    const uint32_t i = base + gid;
+                    const uint32_t i = base + j0;
                     const bool has = i < n_ne;
                     float sum = 0.f;
                     uint32_t row = 0;
                     if (has) {
-                        row = D.row0 + nes[i];
-                        const uint32_t re = rps[row + 1 - rb0];
-#pragma unroll 4
-                        for (uint32_t k = rps[row - rb0] + li; k < re; k += L)
-                            sum = __fmaf_rn(Fmt<FMT>::dec(vs[k - vb]), xs[cs[k - cb]], sum);
+                        row = D.row0 + dev::lds_u16(v.ne + 2 * i);
+                        sum = dot_strided<FMT>(v, xs_a, dev::lds_u32(v.rp + 4 * row) + li,
+                                               dev::lds_u32(v.rp + 4 * row + 4), L);
                     }
                     for (uint32_t off = L >> 1; off > 0; off >>= 1)
                         sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
                     if (has && li == 0) {
                         const float rsc =
-                            FMT == DOSE_FMT_FP8E4M3_ROWSCALE ? slot_vec(buf, SL, p.vecs, kRowScaleVec, D.row0, row) : 1.f;
+                            FMT == DOSE_FMT_FP8E4M3_ROWSCALE ? slot_vec(slot, SL, p.vecs, kRowScaleVec, D.row0, row) : 1.f;
                         const float dv = finish_dot<FMT>(p, rsc, sum);
                         if (p.d) p.d[row] = dv;
-                        const double wv = slot_vec(buf, SL, p.vecs, 1, D.row0, row);
-                        const double ed = (double)dv - (double)slot_vec(buf, SL, p.vecs, 0, D.row0, row);
+                        const double wv = slot_vec(slot, SL, p.vecs, 1, D.row0, row);
+                        const double ed = (double)dv - (double)slot_vec(slot, SL, p.vecs, 0, D.row0, row);
                         f_lane += wv * ed * ed;
-                        rl[i] = __fmul_rn((float)(2.0 * wv * ed), rsc);
+                        dev::sts_f32(rl + 4 * i, __fmul_rn((float)(2.0 * wv * ed), rsc));
                     }
                 }
             } else {
                 // one chunk of a long row: every forward thread takes part
                 if (D.meta & STAGE_FIRST) coop_s = 0.f;
-#pragma unroll 4
-                for (uint32_t k = D.nz0 + ftid; k < D.nz1; k += nft)
-                    coop_s = __fmaf_rn(Fmt<FMT>::dec(vs[k - vb]), xs[cs[k - cb]], coop_s);
+                coop_s = __fadd_rn(coop_s, dot_strided<FMT>(v, xs_a, D.nz0 + ftid, D.nz1, nft));
                 if (D.meta & STAGE_LAST) {
                     float sum = coop_s;
                     for (uint32_t off = 16; off > 0; off >>= 1)
@@ -201,14 +196,14 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
                         float tot = red[0];
                         for (uint32_t w2 = 1; w2 < Wf; ++w2) tot = __fadd_rn(tot, red[w2]);
                         const float rsc = FMT == DOSE_FMT_FP8E4M3_ROWSCALE
-                                              ? slot_vec(buf, SL, p.vecs, kRowScaleVec, D.row0, D.row0)
+                                              ? slot_vec(slot, SL, p.vecs, kRowScaleVec, D.row0, D.row0)
                                               : 1.f;
                         const float dv = finish_dot<FMT>(p, rsc, tot);
                         if (p.d) p.d[D.row0] = dv;
-                        const double wv = slot_vec(buf, SL, p.vecs, 1, D.row0, D.row0);
-                        const double ed = (double)dv - (double)slot_vec(buf, SL, p.vecs, 0, D.row0, D.row0);
+                        const double wv = slot_vec(slot, SL, p.vecs, 1, D.row0, D.row0);
+                        const double ed = (double)dv - (double)slot_vec(slot, SL, p.vecs, 0, D.row0, D.row0);
                         f_lane += wv * ed * ed;
-                        reinterpret_cast<float*>(buf + SL.hdr_off + 32)[0] = __fmul_rn((float)(2.0 * wv * ed), rsc);
+                        dev::sts_f32(slot + SL.hdr_off + 32, __fmul_rn((float)(2.0 * wv * ed), rsc));
                     }
                     dev::named_barrier(2, nft);
                 }
@@ -223,7 +218,7 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     } else {
         // ------------------------------------------------ scatter warps
         const uint32_t sw = warp - 1 - Wf;
-        float* gw = gacc + sw * gw_floats;
+        const uint32_t gw = dev::smem_u32(gacc + sw * gw_floats);
         uint32_t st = 0, ph = 0;
         for (uint32_t s = s_begin; s < s_end; ++s) {
             if (!dev::mbar_wait_bounded(&full[st], ph) || (QUAD && !dev::mbar_wait_bounded(&fwd_done[st], ph))) {
@@ -231,46 +226,42 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
                 failed = true;
                 break;
             }
-            const unsigned char* buf = slot_base + st * SL.bytes;
-            const StageDesc D = *reinterpret_cast<const StageDesc*>(buf + SL.hdr_off);
-            const T* vs = reinterpret_cast<const T*>(buf + SL.val_off);
-            const uint32_t* cs = reinterpret_cast<const uint32_t*>(buf + SL.col_off);
-            const uint32_t vb = D.nz0 & ~(VA - 1), cb = D.nz0 & ~3u;
+            const uint32_t slot = slot0 + st * SL.bytes;
+            const StageDesc D = slot_desc(slot);
+            const SlotView v = slot_view<FMT>(slot, SL, D);
             if (!(D.meta & STAGE_COOP)) {
-                const uint32_t* rps = reinterpret_cast<const uint32_t*>(buf + SL.rp_off);
-                const uint16_t* nes = reinterpret_cast<const uint16_t*>(buf + SL.ne_off) + (D.ne0 & 7u);
-                const float* rl = reinterpret_cast<const float*>(buf + SL.rl_off);
-                const uint32_t rb0 = D.row0 & ~3u;
+                const uint32_t rl = slot + SL.rl_off;
                 const uint32_t n_ne = D.ne1 - D.ne0;
-                for (uint32_t i = sw; i < n_ne; i += Ws) {
-                    const uint32_t row = D.row0 + nes[i];
+                for (uint32_t i = (sw + s) % Ws; i < n_ne; i += Ws) {
+                    const uint32_t row = D.row0 + dev::lds_u16(v.ne + 2 * i);
                     float rj;
                     if (QUAD) {
-                        rj = rl[i];
+                        rj = dev::lds_f32(rl + 4 * i);
                     } else {
-                        rj = slot_vec(buf, SL, p.vecs, 0, D.row0, row);
+                        rj = slot_vec(slot, SL, p.vecs, 0, D.row0, row);
                         if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE)
-                            rj = __fmul_rn(rj, slot_vec(buf, SL, p.vecs, kRowScaleVec, D.row0, row));
+                            rj = __fmul_rn(rj, slot_vec(slot, SL, p.vecs, kRowScaleVec, D.row0, row));
                     }
-                    scatter_entries<FMT>(gw, vs, vb, cs, cb, rps[row - rb0] + lane, rps[row + 1 - rb0], 32, rj);
+                    scatter_entries<FMT>(gw, v, dev::lds_u32(v.rp + 4 * row) + lane, dev::lds_u32(v.rp + 4 * row + 4),
+                                         32, rj);
                     __syncwarp();
                 }
             } else if (QUAD) {
                 if (D.meta & STAGE_LAST) {
                     // the whole long row, from global memory (its earlier chunks left the ring)
-                    const float rj = reinterpret_cast<const float*>(buf + SL.hdr_off + 32)[0];
+                    const float rj = dev::lds_f32(slot + SL.hdr_off + 32);
                     const uint32_t kb = __ldg(p.row_ptr + D.row0), ke = __ldg(p.row_ptr + D.row0 + 1);
-                    const T* v = static_cast<const T*>(p.val);
+                    const T* vg = static_cast<const T*>(p.val);
                     for (uint32_t k = kb + sw * 32 + lane; k < ke; k += Ws * 32) {
-                        const uint32_t c = __ldg(p.col + k);
-                        gw[c] = __fmaf_rn(Fmt<FMT>::dec(v[k]), rj, gw[c]);
+                        const uint32_t ga = gw + 4 * __ldg(p.col + k);
+                        dev::sts_f32(ga, __fmaf_rn(Fmt<FMT>::dec(vg[k]), rj, dev::lds_f32(ga)));
                     }
                 }
             } else {
-                float rj = slot_vec(buf, SL, p.vecs, 0, D.row0, D.row0);
+                float rj = slot_vec(slot, SL, p.vecs, 0, D.row0, D.row0);
                 if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE)
-                    rj = __fmul_rn(rj, slot_vec(buf, SL, p.vecs, kRowScaleVec, D.row0, D.row0));
-                scatter_entries<FMT>(gw, vs, vb, cs, cb, D.nz0 + sw * 32 + lane, D.nz1, Ws * 32, rj);
+                    rj = __fmul_rn(rj, slot_vec(slot, SL, p.vecs, kRowScaleVec, D.row0, D.row0));
+                scatter_entries<FMT>(gw, v, D.nz0 + sw * 32 + lane, D.nz1, Ws * 32, rj);
             }
             __syncwarp();
             if (lane == 0) dev::mbar_arrive(&empty[st]);

@@ -640,7 +640,7 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
     float best_ms = 1e30f;
     const uint32_t nnzs[] = {2048, 4096, 8192};
     const uint32_t rows[] = {1024, 2048, 4096};
-    const uint32_t targets[] = {2, 4, 8};
+    const uint32_t targets[] = {4, 8, 12, 16, 24};
     const uint32_t depths[] = {3, 4, 6};
     dose_status result = DOSE_OK;
     for (uint32_t tn : nnzs)

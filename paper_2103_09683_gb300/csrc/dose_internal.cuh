@@ -48,7 +48,7 @@ struct Tuning {
     uint32_t tile_nnz = 4096;
     uint32_t tile_rows = 2048;
     uint32_t coop_nnz = 1024;
-    uint32_t lane_target = 4;
+    uint32_t lane_target = 12;  // entries per lane: 4 per unrolled step, about 3 steps
     uint32_t stages = 4;
     uint32_t consumer_warps = 16;
 };
@@ -220,6 +220,33 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Explicit shared-memory accesses on 32-bit shared addresses (the staged data
+// is written by the async proxy between mbarrier waits, so these are volatile:
+// never moved across a wait).
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u8(uint32_t a) {
+    uint16_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_f32(uint32_t a, float v) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
 
 __device__ __forceinline__ void named_barrier(uint32_t id, uint32_t nthreads) {

@@ -38,36 +38,6 @@ struct SpmvParams {
 
 constexpr uint32_t kHeaderBytes = 1024;  // mbarriers (<= 16 x 8 B) + CTA reduction scratch
 
-// Accumulate entries kb, kb+step, ... < ke of one row.  vs/cs hold the stage's
-// value and column slices starting at global entry vb / cb.
-template <int FMT, bool COMP>
-__device__ __forceinline__ void accumulate_row(const typename Fmt<FMT>::T* __restrict__ vs, uint32_t vb,
-                                               const uint32_t* __restrict__ cs, uint32_t cb,
-                                               const float* __restrict__ xs, const float* __restrict__ xg,
-                                               bool xsmem, uint32_t kb, uint32_t ke, uint32_t step, float& s,
-                                               float& c) {
-    if (COMP) {
-        for (uint32_t k = kb; k < ke; k += step) {
-            const float a = Fmt<FMT>::dec(vs[k - vb]);
-            const uint32_t j = cs[k - cb];
-            const float xv = xsmem ? xs[j] : __ldg(xg + j);
-            float pr, ep, t, es;
-            dev::two_prod(a, xv, pr, ep);
-            dev::two_sum(s, pr, t, es);
-            s = t;
-            c = __fadd_rn(c, __fadd_rn(es, ep));
-        }
-    } else {
-#pragma unroll 4
-        for (uint32_t k = kb; k < ke; k += step) {
-            const float a = Fmt<FMT>::dec(vs[k - vb]);
-            const uint32_t j = cs[k - cb];
-            const float xv = xsmem ? xs[j] : __ldg(xg + j);
-            s = __fmaf_rn(a, xv, s);
-        }
-    }
-}
-
 // Combine the (sum, compensation) pairs of the `width` lanes of a group.
 template <bool COMP>
 __device__ __forceinline__ void group_reduce(float& sum, float& comp, uint32_t width) {
@@ -86,17 +56,35 @@ __device__ __forceinline__ void group_reduce(float& sum, float& comp, uint32_t w
 }
 
 template <int FMT>
-__device__ __forceinline__ float row_result(const SpmvParams& p, const unsigned char* buf, const SlotLayout& SL,
-                                            uint32_t row0, uint32_t row, float v) {
+__device__ __forceinline__ float row_result(const SpmvParams& p, uint32_t slot, const SlotLayout& SL, uint32_t row0,
+                                            uint32_t row, float v) {
     if (FMT == DOSE_FMT_U16_SCALE) return __fmul_rn(p.scale, v);
-    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) return __fmul_rn(slot_vec(buf, SL, p.vecs, 0, row0, row), v);
+    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) return __fmul_rn(slot_vec(slot, SL, p.vecs, 0, row0, row), v);
     return v;
+}
+
+// Sum over the entries kb, kb + step, ... < ke (plain or compensated).
+template <int FMT, bool COMP, bool XSMEM>
+__device__ __forceinline__ void row_dot(const SlotView& v, uint32_t xs, const float* __restrict__ xg, uint32_t kb,
+                                        uint32_t ke, uint32_t step, bool comp_row, float& sum, float& comp) {
+    if (COMP && comp_row) {
+        dot_strided_comp<FMT>(v, xs, xg, XSMEM, kb, ke, step, sum, comp);
+    } else {
+        const float t = XSMEM ? dot_strided<FMT>(v, xs, kb, ke, step) : dot_strided_gx<FMT>(v, xg, kb, ke, step);
+        if (COMP) {
+            float u, e;
+            dev::two_sum(sum, t, u, e);
+            sum = u;
+            comp = __fadd_rn(comp, e);
+        } else {
+            sum = __fadd_rn(sum, t);
+        }
+    }
 }
 
 template <int FMT, bool COMP, bool XSMEM>
 __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     using T = typename Fmt<FMT>::T;
-    constexpr uint32_t VA = Fmt<FMT>::kAlign;
     extern __shared__ __align__(128) unsigned char smem[];
 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -137,6 +125,8 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
         for (uint32_t j = ctid; j < p.ncols; j += nct) xs[j] = __ldg(p.x + j);
         dev::named_barrier(1, nct);
     }
+    const uint32_t xs_a = dev::smem_u32(xs);
+    const uint32_t slot0 = dev::smem_u32(slot_base);
     float coop_s = 0.f, coop_c = 0.f;
 
     uint32_t st = 0, ph = 0;
@@ -145,40 +135,35 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
             atomicExch(p.err, kErrTimeoutFull);
             return;
         }
-        const unsigned char* buf = slot_base + st * SL.bytes;
-        const StageDesc D = *reinterpret_cast<const StageDesc*>(buf + SL.hdr_off);
-        const T* vs = reinterpret_cast<const T*>(buf + SL.val_off);
-        const uint32_t* cs = reinterpret_cast<const uint32_t*>(buf + SL.col_off);
-        const uint32_t vb = D.nz0 & ~(VA - 1), cb = D.nz0 & ~3u;
+        const uint32_t slot = slot0 + st * SL.bytes;
+        const StageDesc D = slot_desc(slot);
+        const SlotView v = slot_view<FMT>(slot, SL, D);
 
         if (!(D.meta & STAGE_COOP)) {
-            const uint32_t* rps = reinterpret_cast<const uint32_t*>(buf + SL.rp_off);
-            const uint16_t* nes = reinterpret_cast<const uint16_t*>(buf + SL.ne_off) + (D.ne0 & 7u);
-            const uint32_t rb0 = D.row0 & ~3u;
             // empty rows: write 0 (coalesced)
             for (uint32_t r = D.row0 + ctid; r < D.row1; r += nct)
-                if (rps[r - rb0] == rps[r + 1 - rb0]) p.d[r] = 0.0f;
-            // non-empty rows: groups of L lanes, entries i = gid, gid + G, ...
+                if (dev::lds_u32(v.rp + 4 * r) == dev::lds_u32(v.rp + 4 * r + 4)) p.d[r] = 0.0f;
+            // non-empty rows: groups of L lanes; the list is dealt round-robin to
+            // the groups, starting one warp further on at every stage
             const uint32_t lg = D.meta & STAGE_LANES_MASK;
             const uint32_t L = 1u << lg;
             const uint32_t gid = ctid >> lg, li = lane & (L - 1), G = nct >> lg;
+            const uint32_t rot = ((s % W) << (5 - lg)) % G;
+            const uint32_t j0 = (gid + G - rot) % G;
             const uint32_t n_ne = D.ne1 - D.ne0;
             for (uint32_t base = 0; base < n_ne; base += G) {
-                const uint32_t i = base + gid;
+                const uint32_t i = base + j0;
                 const bool has = i < n_ne;
                 float sum = 0.f, comp = 0.f;
                 uint32_t row = 0;
                 if (has) {
-                    row = D.row0 + nes[i];
-                    const uint32_t rs = rps[row - rb0], re = rps[row + 1 - rb0];
-                    if (COMP && re - rs > kCompThreshold)
-                        accumulate_row<FMT, true>(vs, vb, cs, cb, xs, p.x, XSMEM, rs + li, re, L, sum, comp);
-                    else
-                        accumulate_row<FMT, false>(vs, vb, cs, cb, xs, p.x, XSMEM, rs + li, re, L, sum, comp);
+                    row = D.row0 + dev::lds_u16(v.ne + 2 * i);
+                    const uint32_t rs = dev::lds_u32(v.rp + 4 * row), re = dev::lds_u32(v.rp + 4 * row + 4);
+                    row_dot<FMT, COMP, XSMEM>(v, xs_a, p.x, rs + li, re, L, re - rs > kCompThreshold, sum, comp);
                 }
                 group_reduce<COMP>(sum, comp, L);
                 if (has && li == 0)
-                    p.d[row] = row_result<FMT>(p, buf, SL, D.row0, row, COMP ? __fadd_rn(sum, comp) : sum);
+                    p.d[row] = row_result<FMT>(p, slot, SL, D.row0, row, COMP ? __fadd_rn(sum, comp) : sum);
             }
         } else {
             // one chunk of a long row, reduced by every consumer thread
@@ -186,11 +171,7 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
                 coop_s = 0.f;
                 coop_c = 0.f;
             }
-            if (COMP)
-                accumulate_row<FMT, true>(vs, vb, cs, cb, xs, p.x, XSMEM, D.nz0 + ctid, D.nz1, nct, coop_s, coop_c);
-            else
-                accumulate_row<FMT, false>(vs, vb, cs, cb, xs, p.x, XSMEM, D.nz0 + ctid, D.nz1, nct, coop_s,
-                                           coop_c);
+            row_dot<FMT, COMP, XSMEM>(v, xs_a, p.x, D.nz0 + ctid, D.nz1, nct, true, coop_s, coop_c);
             if (D.meta & STAGE_LAST) {
                 float sum = coop_s, comp = coop_c;
                 group_reduce<COMP>(sum, comp, 32);
@@ -211,7 +192,7 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
                             tot = __fadd_rn(tot, red[w2]);
                         }
                     }
-                    p.d[D.row0] = row_result<FMT>(p, buf, SL, D.row0, D.row0, COMP ? __fadd_rn(tot, tc) : tot);
+                    p.d[D.row0] = row_result<FMT>(p, slot, SL, D.row0, D.row0, COMP ? __fadd_rn(tot, tc) : tot);
                 }
                 dev::named_barrier(1, nct);
             }

@@ -15,6 +15,8 @@ struct Fmt<DOSE_FMT_U16_SCALE> {
     static constexpr uint32_t kAlign = 8;  // elements per 16 bytes
 #ifdef __CUDACC__
     __device__ static float dec(T v) { return dev::dec_u16(v); }
+    // decoded value of the stored entry at shared address a
+    __device__ static float lds(uint32_t a) { return (float)dev::lds_u16(a); }
 #endif
 };
 template <>
@@ -23,6 +25,7 @@ struct Fmt<DOSE_FMT_BF16> {
     static constexpr uint32_t kAlign = 8;
 #ifdef __CUDACC__
     __device__ static float dec(T v) { return dev::dec_bf16(v); }
+    __device__ static float lds(uint32_t a) { return __uint_as_float(dev::lds_u16(a) << 16); }
 #endif
 };
 template <>
@@ -31,6 +34,7 @@ struct Fmt<DOSE_FMT_FP8E4M3_ROWSCALE> {
     static constexpr uint32_t kAlign = 16;
 #ifdef __CUDACC__
     __device__ static float dec(T v) { return dev::dec_e4m3(v); }
+    __device__ static float lds(uint32_t a) { return dev::dec_e4m3((uint8_t)dev::lds_u8(a)); }
 #endif
 };
 
@@ -137,12 +141,111 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
     }
 }
 
-// Value of staged vector k for row r of the slot whose stage starts at row0.
-__device__ __forceinline__ float slot_vec(const unsigned char* buf, const SlotLayout& SL, const VecSet& vecs,
-                                          uint32_t k, uint32_t row0, uint32_t r) {
-    if (r < vecs.lim[k])
-        return reinterpret_cast<const float*>(buf + SL.vec_off + k * SL.vec_stride)[r - (row0 & ~3u)];
+// Value of staged vector k for row r; `slot` is the slot's shared address and
+// row0 the stage's first row.
+__device__ __forceinline__ float slot_vec(uint32_t slot, const SlotLayout& SL, const VecSet& vecs, uint32_t k,
+                                          uint32_t row0, uint32_t r) {
+    if (r < vecs.lim[k]) return dev::lds_f32(slot + SL.vec_off + k * SL.vec_stride + (r - (row0 & ~3u)) * 4);
     return __ldg(vecs.ptr[k] + r);
+}
+
+// Read the stage descriptor from a slot header.
+__device__ __forceinline__ StageDesc slot_desc(uint32_t slot) {
+    StageDesc D;
+    D.row0 = dev::lds_u32(slot + 0);
+    D.row1 = dev::lds_u32(slot + 4);
+    D.nz0 = dev::lds_u32(slot + 8);
+    D.nz1 = dev::lds_u32(slot + 12);
+    D.ne0 = dev::lds_u32(slot + 16);
+    D.ne1 = dev::lds_u32(slot + 20);
+    D.meta = dev::lds_u32(slot + 24);
+    D.pad = 0;
+    return D;
+}
+
+// Shared addresses of a slot's slices, rebased so that global indices can be
+// used directly (32-bit wrap-around arithmetic: only the sums are addresses).
+struct SlotView {
+    uint32_t rp;   // + 4 * row
+    uint32_t col;  // + 4 * k
+    uint32_t val;  // + esize * k
+    uint32_t ne;   // + 2 * i, i = position in the stage's list
+};
+
+template <int FMT>
+__device__ __forceinline__ SlotView slot_view(uint32_t slot, const SlotLayout& SL, const StageDesc& D) {
+    constexpr uint32_t VA = Fmt<FMT>::kAlign;
+    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
+    SlotView v;
+    v.rp = slot + SL.rp_off - (D.row0 & ~3u) * 4u;
+    v.col = slot + SL.col_off - (D.nz0 & ~3u) * 4u;
+    v.val = slot + SL.val_off - (D.nz0 & ~(VA - 1)) * ES;
+    v.ne = slot + SL.ne_off + (D.ne0 & 7u) * 2u;
+    return v;
+}
+
+// Sum of a[k] * x[col[k]] over k = kb, kb + step, ... < ke with four
+// independent FP32 accumulators (combined as (a0 + a1) + (a2 + a3)).
+template <int FMT>
+__device__ __forceinline__ float dot_strided(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke,
+                                             uint32_t step) {
+    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    uint32_t k = kb;
+    for (; k + 3 * step < ke; k += 4 * step) {
+        const uint32_t k1 = k + step, k2 = k + 2 * step, k3 = k + 3 * step;
+        const uint32_t c0 = dev::lds_u32(v.col + 4 * k), c1 = dev::lds_u32(v.col + 4 * k1);
+        const uint32_t c2 = dev::lds_u32(v.col + 4 * k2), c3 = dev::lds_u32(v.col + 4 * k3);
+        const float w0 = Fmt<FMT>::lds(v.val + ES * k), w1 = Fmt<FMT>::lds(v.val + ES * k1);
+        const float w2 = Fmt<FMT>::lds(v.val + ES * k2), w3 = Fmt<FMT>::lds(v.val + ES * k3);
+        a0 = __fmaf_rn(w0, dev::lds_f32(xs + 4 * c0), a0);
+        a1 = __fmaf_rn(w1, dev::lds_f32(xs + 4 * c1), a1);
+        a2 = __fmaf_rn(w2, dev::lds_f32(xs + 4 * c2), a2);
+        a3 = __fmaf_rn(w3, dev::lds_f32(xs + 4 * c3), a3);
+    }
+    if (k < ke) a0 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * dev::lds_u32(v.col + 4 * k)), a0);
+    k += step;
+    if (k < ke) a1 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * dev::lds_u32(v.col + 4 * k)), a1);
+    k += step;
+    if (k < ke) a2 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * dev::lds_u32(v.col + 4 * k)), a2);
+    return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
+}
+
+// Compensated version (Dot2 of Ogita, Rump and Oishi, 2005): returns (s, c)
+// with s + c the dot product to about twice the working precision.
+template <int FMT>
+__device__ __forceinline__ void dot_strided_comp(const SlotView& v, uint32_t xs, const float* __restrict__ xg,
+                                                 bool xsmem, uint32_t kb, uint32_t ke, uint32_t step, float& s,
+                                                 float& c) {
+    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
+    for (uint32_t k = kb; k < ke; k += step) {
+        const float a = Fmt<FMT>::lds(v.val + ES * k);
+        const uint32_t j = dev::lds_u32(v.col + 4 * k);
+        const float xv = xsmem ? dev::lds_f32(xs + 4 * j) : __ldg(xg + j);
+        float pr, ep, t, es;
+        dev::two_prod(a, xv, pr, ep);
+        dev::two_sum(s, pr, t, es);
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(es, ep));
+    }
+}
+
+// Plain sum with x read from global memory (x too large for shared memory).
+template <int FMT>
+__device__ __forceinline__ float dot_strided_gx(const SlotView& v, const float* __restrict__ xg, uint32_t kb,
+                                                uint32_t ke, uint32_t step) {
+    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
+    float a0 = 0.f, a1 = 0.f;
+    uint32_t k = kb;
+    for (; k + step < ke; k += 2 * step) {
+        const uint32_t k1 = k + step;
+        const uint32_t c0 = dev::lds_u32(v.col + 4 * k), c1 = dev::lds_u32(v.col + 4 * k1);
+        const float w0 = Fmt<FMT>::lds(v.val + ES * k), w1 = Fmt<FMT>::lds(v.val + ES * k1);
+        a0 = __fmaf_rn(w0, __ldg(xg + c0), a0);
+        a1 = __fmaf_rn(w1, __ldg(xg + c1), a1);
+    }
+    if (k < ke) a0 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), __ldg(xg + dev::lds_u32(v.col + 4 * k)), a0);
+    return __fadd_rn(a0, a1);
 }
 
 #endif
