@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     const uint32_t slot0 = dev::smem_u32(slot_base);
     const bool is_fwd = QUAD && warp <= Wf;
     bool failed = false;
-    double f_lane = 0.0;
+    float f_hi = 0.f, f_lo = 0.f;  // this lane's objective terms, double-float
 
     if (is_fwd) {
         // ------------------------------------------------ forward warps
@@ -148,8 +148,8 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
                 for (uint32_t r = D.row0 + ftid; r < D.row1; r += nft) {
                     if (dev::lds_u32(v.rp + 4 * r) == dev::lds_u32(v.rp + 4 * r + 4)) {
                         if (p.d) p.d[r] = 0.0f;
-                        const double pv = slot_vec(slot, SL, p.vecs, 0, D.row0, r);
-                        f_lane += (double)slot_vec(slot, SL, p.vecs, 1, D.row0, r) * pv * pv;
+                        dev::df_add_wsq(f_hi, f_lo, slot_vec(slot, SL, p.vecs, 1, D.row0, r), 0.0f,
+                                        slot_vec(slot, SL, p.vecs, 0, D.row0, r));
                     }
                 }
                 const uint32_t lg = D.meta & STAGE_LANES_MASK;
@@ -176,10 +176,9 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
                             FMT == DOSE_FMT_FP8E4M3_ROWSCALE ? slot_vec(slot, SL, p.vecs, kRowScaleVec, D.row0, row) : 1.f;
                         const float dv = finish_dot<FMT>(p, rsc, sum);
                         if (p.d) p.d[row] = dv;
-                        const double wv = slot_vec(slot, SL, p.vecs, 1, D.row0, row);
-                        const double ed = (double)dv - (double)slot_vec(slot, SL, p.vecs, 0, D.row0, row);
-                        f_lane += wv * ed * ed;
-                        dev::sts_f32(rl + 4 * i, __fmul_rn((float)(2.0 * wv * ed), rsc));
+                        const float wv = slot_vec(slot, SL, p.vecs, 1, D.row0, row);
+                        const float e = dev::df_add_wsq(f_hi, f_lo, wv, dv, slot_vec(slot, SL, p.vecs, 0, D.row0, row));
+                        dev::sts_f32(rl + 4 * i, __fmul_rn(__fmul_rn(__fmul_rn(2.0f, wv), e), rsc));
                     }
                 }
             } else {
@@ -200,10 +199,10 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
                                               : 1.f;
                         const float dv = finish_dot<FMT>(p, rsc, tot);
                         if (p.d) p.d[D.row0] = dv;
-                        const double wv = slot_vec(slot, SL, p.vecs, 1, D.row0, D.row0);
-                        const double ed = (double)dv - (double)slot_vec(slot, SL, p.vecs, 0, D.row0, D.row0);
-                        f_lane += wv * ed * ed;
-                        dev::sts_f32(slot + SL.hdr_off + 32, __fmul_rn((float)(2.0 * wv * ed), rsc));
+                        const float wv = slot_vec(slot, SL, p.vecs, 1, D.row0, D.row0);
+                        const float e =
+                            dev::df_add_wsq(f_hi, f_lo, wv, dv, slot_vec(slot, SL, p.vecs, 0, D.row0, D.row0));
+                        dev::sts_f32(slot + SL.hdr_off + 32, __fmul_rn(__fmul_rn(__fmul_rn(2.0f, wv), e), rsc));
                     }
                     dev::named_barrier(2, nft);
                 }
@@ -277,6 +276,7 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
 
     // CTA partials: accumulators summed in warp order; f in a fixed tree.
     if (is_fwd) {
+        double f_lane = (double)f_hi + (double)f_lo;
         for (uint32_t off = 16; off > 0; off >>= 1) f_lane += __shfl_xor_sync(0xffffffffu, f_lane, off);
         if (lane == 0) fred[warp - 1] = f_lane;
     }
@@ -395,7 +395,7 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
         prm.f_part = A->f_part;
         prm.nrows = A->nrows;
         prm.ncols = A->ncols;
-        prm.sched = ScheduleView{A->adj.desc, A->adj.ne, A->adj.cta_begin};
+        prm.sched = ScheduleView{A->adj.desc, A->adj.ne, A->adj.order, A->adj.cta_begin};
         const uint32_t user_lim = A->nrows & ~3u;  // caller arrays: whole 16-byte pieces only
         prm.vecs.n = 0;
         if (quad) {

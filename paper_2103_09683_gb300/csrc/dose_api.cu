@@ -172,25 +172,27 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
         ++S.lanes_hist[lg];
     }
 
-    // Contiguous stage ranges per CTA, balanced by streamed bytes; never split
-    // the chunks of one long row across CTAs.
-    const size_t n = S.desc.size();
-    std::vector<double> wcum(n + 1, 0.0);
-    for (size_t s = 0; s < n; ++s) {
-        const StageDesc& D = S.desc[s];
-        const double rows = (D.meta & STAGE_COOP) ? 0.0 : (double)(D.row1 - D.row0);
-        wcum[s + 1] = wcum[s] + 6.0 * (D.nz1 - D.nz0) + 8.0 * rows + 2.0 * (D.ne1 - D.ne0) + 256.0;
+    // Deal work items (a NORMAL stage, or the consecutive chunks of one long
+    // row) to the CTAs round-robin, in matrix order.
+    const uint32_t n = (uint32_t)S.desc.size();
+    std::vector<std::vector<uint32_t>> per(grid);
+    uint32_t item = 0;
+    for (uint32_t s = 0; s < n;) {
+        uint32_t e = s + 1;
+        if (S.desc[s].meta & STAGE_COOP)
+            while (e < n && (S.desc[e].meta & STAGE_COOP) && !(S.desc[e].meta & STAGE_FIRST)) ++e;
+        std::vector<uint32_t>& dst = per[item % grid];
+        for (uint32_t k = s; k < e; ++k) dst.push_back(k);
+        ++item;
+        s = e;
     }
-    S.cta_begin.assign(grid + 1, (uint32_t)n);
-    S.cta_begin[0] = 0;
-    size_t s = 0;
-    for (uint32_t c = 1; c < grid; ++c) {
-        const double target = wcum[n] * c / grid;
-        while (s < n && wcum[s] < target) ++s;
-        while (s < n && (S.desc[s].meta & STAGE_COOP) && !(S.desc[s].meta & STAGE_FIRST)) ++s;
-        S.cta_begin[c] = (uint32_t)std::max<size_t>(s, S.cta_begin[c - 1]);
+    S.cta_begin.assign(grid + 1, 0);
+    S.order.reserve(n);
+    for (uint32_t c = 0; c < grid; ++c) {
+        S.cta_begin[c] = (uint32_t)S.order.size();
+        S.order.insert(S.order.end(), per[c].begin(), per[c].end());
     }
-    S.cta_begin[grid] = (uint32_t)n;
+    S.cta_begin[grid] = (uint32_t)S.order.size();
     return S;
 }
 
@@ -199,9 +201,11 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
 static void free_dev_schedule(DevSchedule& D) {
     cudaFree(D.desc);
     cudaFree(D.ne);
+    cudaFree(D.order);
     cudaFree(D.cta_begin);
     D.desc = nullptr;
     D.ne = nullptr;
+    D.order = nullptr;
     D.cta_begin = nullptr;
     D.n_stages = 0;
 }
@@ -286,6 +290,7 @@ static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& 
     cudaError_t e;
     if ((e = upload(&D.desc, S.desc.data(), S.desc.size(), S.desc.size() + 1)) != cudaSuccess ||
         (e = upload(&D.ne, S.ne.data(), S.ne.size(), (S.ne.size() + 7) / 8 * 8 + 16)) != cudaSuccess ||
+        (e = upload(&D.order, S.order.data(), S.order.size(), S.order.size() + 1)) != cudaSuccess ||
         (e = upload(&D.cta_begin, S.cta_begin.data(), S.cta_begin.size(), S.cta_begin.size())) != cudaSuccess)
         return cuda_fail(e, "uploading the schedule");
     D.n_stages = (uint32_t)S.desc.size();
@@ -306,7 +311,7 @@ static Tuning adj_schedule_tuning(const Tuning& fwd, const AdjTuning& a) {
 }
 
 static uint64_t schedule_bytes(const DevSchedule& D) {
-    return (uint64_t)(D.n_stages + 1) * sizeof(StageDesc) + (D.grid + 1) * 4;
+    return (uint64_t)(D.n_stages + 1) * (sizeof(StageDesc) + 4) + (D.grid + 1) * 4;
 }
 
 static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }

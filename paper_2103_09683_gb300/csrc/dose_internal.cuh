@@ -26,8 +26,10 @@ namespace dose {
 //   COOP stage:   one chunk (<= tile_nnz entries) of one row longer than
 //                 coop_nnz; all consumer warps reduce it together.  A row of
 //                 several chunks occupies consecutive stages FIRST..LAST.
-// Each CTA owns a contiguous range of stages (static, so every reduction order
-// is fixed at create time).
+// Work items (a NORMAL stage, or all chunks of one long row) are dealt to the
+// CTAs round-robin, so every CTA gets a similar mix of empty and dense row
+// blocks; the assignment is static, so every reduction order is fixed at
+// create time.
 enum : uint32_t {
     STAGE_LANES_MASK = 0x7u,  // log2 of lanes per row (0..5)
     STAGE_COOP = 0x8u,
@@ -56,7 +58,8 @@ struct Tuning {
 struct Schedule {
     std::vector<StageDesc> desc;      // n_stages
     std::vector<uint16_t> ne;         // non-empty rows of NORMAL stages (offset from row0)
-    std::vector<uint32_t> cta_begin;  // grid + 1
+    std::vector<uint32_t> order;      // stage indices, CTA by CTA
+    std::vector<uint32_t> cta_begin;  // grid + 1: CTA c runs order[cta_begin[c] .. cta_begin[c+1])
     uint32_t n_coop_rows = 0;
     uint32_t lanes_hist[6] = {0, 0, 0, 0, 0, 0};
 };
@@ -65,6 +68,7 @@ struct Schedule {
 struct DevSchedule {
     StageDesc* desc = nullptr;
     uint16_t* ne = nullptr;
+    uint32_t* order = nullptr;
     uint32_t* cta_begin = nullptr;
     uint32_t n_stages = 0;
     uint32_t grid = 0;
@@ -77,6 +81,7 @@ struct DevSchedule {
 struct ScheduleView {
     const StageDesc* desc;
     const uint16_t* ne;
+    const uint32_t* order;
     const uint32_t* cta_begin;
 };
 
@@ -283,6 +288,26 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
     p = __fmul_rn(a, b);
     e = __fmaf_rn(a, b, -p);
+}
+
+// Double-float accumulation (hi + lo, |lo| <= ulp(hi)/2 after each step) of the
+// objective term w (d - p)^2 from FP32 operands, using only FP32 arithmetic:
+// e = d - p exactly (TwoSum), e^2 and w e^2 by TwoProduct with the first-order
+// cross terms, then a TwoSum into the accumulator and a renormalisation.  Each
+// term and each step carries a relative error of a few u^2 (u = 2^-24), so the
+// per-lane sum matches FP64 accumulation without using the FP64 pipe.
+__device__ __forceinline__ float df_add_wsq(float& hi, float& lo, float w, float d, float p) {
+    float eh, el, qh, ql, th, tl, sh, se;
+    two_sum(d, -p, eh, el);
+    two_prod(eh, eh, qh, ql);
+    ql = __fmaf_rn(__fmul_rn(2.0f, eh), el, ql);
+    two_prod(w, qh, th, tl);
+    tl = __fmaf_rn(w, ql, tl);
+    two_sum(hi, th, sh, se);
+    const float l = __fadd_rn(lo, __fadd_rn(se, tl));
+    hi = __fadd_rn(sh, l);                  // renormalise (fast TwoSum: |sh| >= |l|)
+    lo = __fsub_rn(l, __fsub_rn(hi, sh));
+    return eh;                              // e rounded to FP32 (exact difference's leading part)
 }
 
 }  // namespace dev

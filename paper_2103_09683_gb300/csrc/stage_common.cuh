@@ -91,10 +91,10 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
     constexpr uint32_t VA = Fmt<FMT>::kAlign;
     uint32_t st = 0, ph = 0, issued = 0;
     StageDesc nxt;
-    if (s_begin < s_end) nxt = sched.desc[s_begin];
+    if (s_begin < s_end) nxt = sched.desc[sched.order[s_begin]];
     for (uint32_t s = s_begin; s < s_end; ++s) {
         const StageDesc D = nxt;
-        if (s + 1 < s_end) nxt = sched.desc[s + 1];  // in flight while this stage is issued
+        if (s + 1 < s_end) nxt = sched.desc[sched.order[s + 1]];  // in flight while this stage is issued
         if (!dev::mbar_wait_bounded(&empty[st], ph ^ 1)) {
             atomicExch(err, kErrTimeoutEmpty);
             break;
