@@ -76,6 +76,41 @@ __device__ __forceinline__ void scatter_entries(uint32_t gw, const SlotView& v, 
     }
 }
 
+// Forward part of the fused pass for the non-empty rows of a NORMAL stage,
+// 2^LG lanes per row: d, the objective terms, and r_i = 2 w_i (d_i - p_i) (FP8:
+// times the row scale) into the slot's r list.
+template <int FMT, uint32_t LG, uint32_t kRowScaleVec>
+__device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D, const SlotView& v, uint32_t slot,
+                                         const SlotLayout& SL, uint32_t xs_a, uint32_t ftid, uint32_t lane,
+                                         uint32_t nft, uint32_t rotw, float& f_hi, float& f_lo) {
+    constexpr uint32_t L = 1u << LG;
+    const uint32_t gid = ftid >> LG, li = lane & (L - 1), G = nft >> LG;
+    const uint32_t j0 = (gid + G - ((rotw << (5 - LG)) & (G - 1))) & (G - 1);
+    const uint32_t n_ne = D.ne1 - D.ne0;
+    const uint32_t rl = slot + SL.rl_off;
+    for (uint32_t base = 0; base < n_ne; base += G) {
+        const uint32_t i = base + j0;
+        const bool has = i < n_ne;
+        float sum = 0.f;
+        uint32_t row = 0;
+        if (has) {
+            row = D.row0 + dev::lds_u16(v.ne + 2 * i);
+            sum = dot_fixed<FMT, L>(v, xs_a, dev::lds_u32(v.rp + 4 * row) + li, dev::lds_u32(v.rp + 4 * row + 4));
+        }
+#pragma unroll
+        for (uint32_t off = L >> 1; off > 0; off >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
+        if (has && li == 0) {
+            const float rsc =
+                FMT == DOSE_FMT_FP8E4M3_ROWSCALE ? slot_vec(slot, SL, p.vecs, kRowScaleVec, D.row0, row) : 1.f;
+            const float dv = finish_dot<FMT>(p, rsc, sum);
+            if (p.d) p.d[row] = dv;
+            const float wv = slot_vec(slot, SL, p.vecs, 1, D.row0, row);
+            const float e = dev::df_add_wsq(f_hi, f_lo, wv, dv, slot_vec(slot, SL, p.vecs, 0, D.row0, row));
+            dev::sts_f32(rl + 4 * i, __fmul_rn(__fmul_rn(__fmul_rn(2.0f, wv), e), rsc));
+        }
+    }
+}
+
 template <int FMT, int MODE>
 __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     using T = typename Fmt<FMT>::T;
@@ -132,10 +167,11 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
 
     if (is_fwd) {
         // ------------------------------------------------ forward warps
-        const uint32_t fw = warp - 1, ftid = fw * 32 + lane, nft = Wf * 32;
+        const uint32_t fw = warp - 1, ftid = fw * 32 + lane, nft = Wf * 32;  // Wf is a power of two
         float coop_s = 0.f;
         uint32_t st = 0, ph = 0;
         for (uint32_t s = s_begin; s < s_end; ++s) {
+            const uint32_t rotw = s & (Wf - 1);
             if (!dev::mbar_wait_bounded(&full[st], ph)) {
                 atomicExch(p.err, kErrTimeoutFull);
                 failed = true;
@@ -152,34 +188,13 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
                                         slot_vec(slot, SL, p.vecs, 0, D.row0, r));
                     }
                 }
-                const uint32_t lg = D.meta & STAGE_LANES_MASK;
-                const uint32_t L = 1u << lg;
-                const uint32_t gid = ftid >> lg, li = lane & (L - 1), G = nft >> lg;
-                const uint32_t rot = ((s % Wf) << (5 - lg)) % G;
-                const uint32_t j0 = (gid + G - rot) % G;
-                const uint32_t n_ne = D.ne1 - D.ne0;
-                const uint32_t rl = slot + SL.rl_off;
-                for (uint32_t base = 0; base < n_ne; base += G) {
-                    const uint32_t i = base + j0;
-                    const bool has = i < n_ne;
-                    float sum = 0.f;
-                    uint32_t row = 0;
-                    if (has) {
-                        row = D.row0 + dev::lds_u16(v.ne + 2 * i);
-                        sum = dot_strided<FMT>(v, xs_a, dev::lds_u32(v.rp + 4 * row) + li,
-                                               dev::lds_u32(v.rp + 4 * row + 4), L);
-                    }
-                    for (uint32_t off = L >> 1; off > 0; off >>= 1)
-                        sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
-                    if (has && li == 0) {
-                        const float rsc =
-                            FMT == DOSE_FMT_FP8E4M3_ROWSCALE ? slot_vec(slot, SL, p.vecs, kRowScaleVec, D.row0, row) : 1.f;
-                        const float dv = finish_dot<FMT>(p, rsc, sum);
-                        if (p.d) p.d[row] = dv;
-                        const float wv = slot_vec(slot, SL, p.vecs, 1, D.row0, row);
-                        const float e = dev::df_add_wsq(f_hi, f_lo, wv, dv, slot_vec(slot, SL, p.vecs, 0, D.row0, row));
-                        dev::sts_f32(rl + 4 * i, __fmul_rn(__fmul_rn(__fmul_rn(2.0f, wv), e), rsc));
-                    }
+                switch (D.meta & STAGE_LANES_MASK) {
+                    case 0: fwd_rows<FMT, 0, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    case 1: fwd_rows<FMT, 1, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    case 2: fwd_rows<FMT, 2, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    case 3: fwd_rows<FMT, 3, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    case 4: fwd_rows<FMT, 4, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    default: fwd_rows<FMT, 5, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
                 }
             } else {
                 // one chunk of a long row: every forward thread takes part
@@ -218,8 +233,8 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
         // ------------------------------------------------ scatter warps
         const uint32_t sw = warp - 1 - Wf;
         const uint32_t gw = dev::smem_u32(gacc + sw * gw_floats);
-        uint32_t st = 0, ph = 0;
-        for (uint32_t s = s_begin; s < s_end; ++s) {
+        uint32_t st = 0, ph = 0, first = sw;  // first list entry of this warp, rotating per stage
+        for (uint32_t s = s_begin; s < s_end; ++s, first = first + 1 == Ws ? 0 : first + 1) {
             if (!dev::mbar_wait_bounded(&full[st], ph) || (QUAD && !dev::mbar_wait_bounded(&fwd_done[st], ph))) {
                 atomicExch(p.err, kErrTimeoutFull);
                 failed = true;
@@ -231,7 +246,7 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
             if (!(D.meta & STAGE_COOP)) {
                 const uint32_t rl = slot + SL.rl_off;
                 const uint32_t n_ne = D.ne1 - D.ne0;
-                for (uint32_t i = (sw + s) % Ws; i < n_ne; i += Ws) {
+                for (uint32_t i = first; i < n_ne; i += Ws) {
                     const uint32_t row = D.row0 + dev::lds_u16(v.ne + 2 * i);
                     float rj;
                     if (QUAD) {
@@ -353,8 +368,10 @@ size_t adj_smem(const dose_matrix* A, const AdjTuning& t, bool quad, uint32_t ws
 
 bool adjoint_shape(const dose_matrix* A, const AdjTuning& in, bool quad, AdjTuning* out, size_t* smem) {
     AdjTuning t = in;
-    t.forward_warps = quad ? (in.forward_warps ? in.forward_warps : 8) : 0;
-    if (t.forward_warps > 15) t.forward_warps = 15;
+    uint32_t fwq = in.forward_warps ? in.forward_warps : 8;
+    if (fwq > 8) fwq = 8;
+    while (fwq & (fwq - 1)) fwq &= fwq - 1;  // a power of two: 1, 2, 4 or 8
+    t.forward_warps = quad ? fwq : 0;
     if (t.stages < 2 || t.stages > 8) return false;
     const uint32_t max_ws = 16 - t.forward_warps;
     uint32_t ws = 0;

@@ -82,6 +82,34 @@ __device__ __forceinline__ void row_dot(const SlotView& v, uint32_t xs, const fl
     }
 }
 
+// The non-empty rows of a NORMAL stage, 2^LG lanes per row.  The stage's list
+// is dealt round-robin to the CTA's G groups, starting `rotw` warps further on.
+template <int FMT, bool COMP, bool XSMEM, uint32_t LG>
+__device__ __forceinline__ void normal_rows(const SpmvParams& p, const StageDesc& D, const SlotView& v,
+                                            uint32_t slot, const SlotLayout& SL, uint32_t xs_a, uint32_t ctid,
+                                            uint32_t lane, uint32_t nct, uint32_t rotw) {
+    constexpr uint32_t L = 1u << LG;
+    const uint32_t gid = ctid >> LG, li = lane & (L - 1), G = nct >> LG;
+    const uint32_t j0 = (gid + G - ((rotw << (5 - LG)) & (G - 1))) & (G - 1);
+    const uint32_t n_ne = D.ne1 - D.ne0;
+    for (uint32_t base = 0; base < n_ne; base += G) {
+        const uint32_t i = base + j0;
+        const bool has = i < n_ne;
+        float sum = 0.f, comp = 0.f;
+        uint32_t row = 0;
+        if (has) {
+            row = D.row0 + dev::lds_u16(v.ne + 2 * i);
+            const uint32_t rs = dev::lds_u32(v.rp + 4 * row), re = dev::lds_u32(v.rp + 4 * row + 4);
+            if (COMP && re - rs > kCompThreshold)
+                dot_strided_comp<FMT>(v, xs_a, p.x, XSMEM, rs + li, re, L, sum, comp);
+            else
+                sum = XSMEM ? dot_fixed<FMT, L>(v, xs_a, rs + li, re) : dot_strided_gx<FMT>(v, p.x, rs + li, re, L);
+        }
+        group_reduce<COMP>(sum, comp, L);
+        if (has && li == 0) p.d[row] = row_result<FMT>(p, slot, SL, D.row0, row, COMP ? __fadd_rn(sum, comp) : sum);
+    }
+}
+
 template <int FMT, bool COMP, bool XSMEM>
 __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     using T = typename Fmt<FMT>::T;
@@ -143,27 +171,15 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
             // empty rows: write 0 (coalesced)
             for (uint32_t r = D.row0 + ctid; r < D.row1; r += nct)
                 if (dev::lds_u32(v.rp + 4 * r) == dev::lds_u32(v.rp + 4 * r + 4)) p.d[r] = 0.0f;
-            // non-empty rows: groups of L lanes; the list is dealt round-robin to
-            // the groups, starting one warp further on at every stage
-            const uint32_t lg = D.meta & STAGE_LANES_MASK;
-            const uint32_t L = 1u << lg;
-            const uint32_t gid = ctid >> lg, li = lane & (L - 1), G = nct >> lg;
-            const uint32_t rot = ((s % W) << (5 - lg)) % G;
-            const uint32_t j0 = (gid + G - rot) % G;
-            const uint32_t n_ne = D.ne1 - D.ne0;
-            for (uint32_t base = 0; base < n_ne; base += G) {
-                const uint32_t i = base + j0;
-                const bool has = i < n_ne;
-                float sum = 0.f, comp = 0.f;
-                uint32_t row = 0;
-                if (has) {
-                    row = D.row0 + dev::lds_u16(v.ne + 2 * i);
-                    const uint32_t rs = dev::lds_u32(v.rp + 4 * row), re = dev::lds_u32(v.rp + 4 * row + 4);
-                    row_dot<FMT, COMP, XSMEM>(v, xs_a, p.x, rs + li, re, L, re - rs > kCompThreshold, sum, comp);
-                }
-                group_reduce<COMP>(sum, comp, L);
-                if (has && li == 0)
-                    p.d[row] = row_result<FMT>(p, slot, SL, D.row0, row, COMP ? __fadd_rn(sum, comp) : sum);
+            // non-empty rows: groups of L lanes (L chosen per stage)
+            const uint32_t rotw = s & (W - 1);
+            switch (D.meta & STAGE_LANES_MASK) {
+                case 0: normal_rows<FMT, COMP, XSMEM, 0>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
+                case 1: normal_rows<FMT, COMP, XSMEM, 1>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
+                case 2: normal_rows<FMT, COMP, XSMEM, 2>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
+                case 3: normal_rows<FMT, COMP, XSMEM, 3>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
+                case 4: normal_rows<FMT, COMP, XSMEM, 4>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
+                default: normal_rows<FMT, COMP, XSMEM, 5>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
             }
         } else {
             // one chunk of a long row, reduced by every consumer thread

@@ -184,8 +184,38 @@ __device__ __forceinline__ SlotView slot_view(uint32_t slot, const SlotLayout& S
     return v;
 }
 
-// Sum of a[k] * x[col[k]] over k = kb, kb + step, ... < ke with four
-// independent FP32 accumulators (combined as (a0 + a1) + (a2 + a3)).
+// Sum of a[k] * x[col[k]] over k = kb, kb + STEP, ... < ke with four
+// independent FP32 accumulators (combined as (a0 + a1) + (a2 + a3)).  STEP is a
+// compile-time power of two, so successive entries are immediate offsets from
+// two walking shared addresses.
+template <int FMT, uint32_t STEP>
+__device__ __forceinline__ float dot_fixed(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke) {
+    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (kb < ke) {
+        uint32_t n = (ke - kb + STEP - 1) / STEP;  // entries of this lane
+        uint32_t ca = v.col + 4 * kb, va = v.val + ES * kb;
+        for (; n >= 4; n -= 4) {
+            const uint32_t c0 = dev::lds_u32(ca), c1 = dev::lds_u32(ca + 4 * STEP);
+            const uint32_t c2 = dev::lds_u32(ca + 8 * STEP), c3 = dev::lds_u32(ca + 12 * STEP);
+            const float w0 = Fmt<FMT>::lds(va), w1 = Fmt<FMT>::lds(va + ES * STEP);
+            const float w2 = Fmt<FMT>::lds(va + 2 * ES * STEP), w3 = Fmt<FMT>::lds(va + 3 * ES * STEP);
+            a0 = __fmaf_rn(w0, dev::lds_f32(xs + 4 * c0), a0);
+            a1 = __fmaf_rn(w1, dev::lds_f32(xs + 4 * c1), a1);
+            a2 = __fmaf_rn(w2, dev::lds_f32(xs + 4 * c2), a2);
+            a3 = __fmaf_rn(w3, dev::lds_f32(xs + 4 * c3), a3);
+            ca += 16 * STEP;
+            va += 4 * ES * STEP;
+        }
+        if (n > 0) a0 = __fmaf_rn(Fmt<FMT>::lds(va), dev::lds_f32(xs + 4 * dev::lds_u32(ca)), a0);
+        if (n > 1) a1 = __fmaf_rn(Fmt<FMT>::lds(va + ES * STEP), dev::lds_f32(xs + 4 * dev::lds_u32(ca + 4 * STEP)), a1);
+        if (n > 2)
+            a2 = __fmaf_rn(Fmt<FMT>::lds(va + 2 * ES * STEP), dev::lds_f32(xs + 4 * dev::lds_u32(ca + 8 * STEP)), a2);
+    }
+    return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
+}
+
+// Same with a run-time stride (the whole-CTA reduction of long rows).
 template <int FMT>
 __device__ __forceinline__ float dot_strided(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke,
                                              uint32_t step) {
