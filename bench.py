@@ -161,6 +161,7 @@ def run_gpu(args):
         import torch.distributed as td
         td.init_process_group("nccl", device_id=device)
     csr, A, x, p, w, eta = setup_workload(device)
+    tuned = A.autotune(x) if args.autotune else None
     info = A.info()
     stream = torch.cuda.current_stream()
     d = torch.empty(A.nrows, dtype=torch.float32, device=device)
@@ -262,6 +263,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 4 * A.nrows + 8},
         "gpu_launches": 3 * K,
         "clocks": clk,
+        "tuning": info["tuning"],
+        "autotuned": bool(tuned),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(csr, x0.cpu().numpy(), p.cpu().numpy(), w.cpu().numpy())
@@ -357,6 +360,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="time candidate schedules first (dose_autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -320,6 +320,25 @@ static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 using namespace dose;
 
+namespace {
+// Time `reps` launches of fn after 3 warm-up launches; returns ms per launch or
+// a negative value on error.
+template <class F>
+static float time_launches(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& fn) {
+    for (int i = 0; i < 3; ++i)
+        if (fn() != cudaSuccess) return -1.f;
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps; ++i)
+        if (fn() != cudaSuccess) return -1.f;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / reps;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* dose_last_error(void) { return g_last_error.c_str(); }
@@ -634,12 +653,28 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
     if (!A) return invalid("dose_autotune: null matrix");
     if (A->ncols && !x) return invalid("dose_autotune: x is NULL");
     cudaStream_t s = as_stream(stream);
-    float* d = nullptr;
-    cudaError_t e = cudaMalloc(&d, std::max<size_t>(A->nrows, 1) * 4);
-    if (e != cudaSuccess) return cuda_fail(e, "dose_autotune scratch");
+    float *d = nullptr, *pw = nullptr, *g = nullptr;
+    double* f = nullptr;
+    const size_t nr = std::max<size_t>(A->nrows, 1), nrp = (nr + 3) / 4 * 4;
+    cudaError_t e = cudaMalloc(&d, nr * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&pw, 2 * nrp * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g, std::max<size_t>(A->ncols, 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&f, 8);
+    if (e == cudaSuccess) e = cudaMemset(pw, 0, 2 * nrp * 4);  // p = 0, w = 0: timing only
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        cudaFree(pw);
+        cudaFree(g);
+        cudaFree(f);
+        return cuda_fail(e, "dose_autotune scratch");
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    const int reps = 10;
+    dose_status result = DOSE_OK;
+
+    // 1. forward: tile sizes, lanes-per-row target, pipeline depth
     const Tuning orig = A->fwd.tuning;
     Tuning best_t = orig;
     float best_ms = 1e30f;
@@ -647,7 +682,6 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
     const uint32_t rows[] = {1024, 2048, 4096};
     const uint32_t targets[] = {4, 8, 12, 16, 24};
     const uint32_t depths[] = {3, 4, 6};
-    dose_status result = DOSE_OK;
     for (uint32_t tn : nnzs)
         for (uint32_t tr : rows)
             for (uint32_t lt : targets)
@@ -660,33 +694,65 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
                     t.stages = sd;
                     if (check_tuning(A, t) != DOSE_OK) continue;
                     if (apply_schedule(A, A->fwd, t) != DOSE_OK) continue;
-                    for (int i = 0; i < 3; ++i) launch_spmv(A, x, d, s);
-                    const int reps = 10;
-                    cudaEventRecord(e0, s);
-                    for (int i = 0; i < reps; ++i) launch_spmv(A, x, d, s);
-                    cudaEventRecord(e1, s);
-                    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
-                        result = cuda_fail(e, "dose_autotune timing");
-                        goto done;
+                    const float ms = time_launches(s, e0, e1, reps, [&] { return launch_spmv(A, x, d, s); });
+                    if (ms < 0.f) {
+                        result = cuda_fail(cudaGetLastError(), "dose_autotune forward timing");
+                        break;
                     }
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
                     if (ms < best_ms) {
                         best_ms = ms;
                         best_t = t;
                     }
                 }
-done:
+    if (result == DOSE_OK) result = apply_schedule(A, A->fwd, best_t);
+
+    // 2. fused objective pass: adjoint tile sizes, depth, forward warps (scatter warps: all that fit)
+    const AdjTuning orig_a = A->adj_tuning;
+    AdjTuning best_a = orig_a;
+    if (result == DOSE_OK && A->ncols <= kXSmemMaxCols) {
+        float best_a_ms = 1e30f;
+        const uint32_t anz[] = {1024, 2048, 4096};
+        const uint32_t arows[] = {512, 1024, 2048};
+        const uint32_t adepth[] = {2, 3, 4};
+        const uint32_t afw[] = {4, 8};
+        for (uint32_t tn : anz)
+            for (uint32_t tr : arows)
+                for (uint32_t sd : adepth)
+                    for (uint32_t fw : afw) {
+                        AdjTuning a = orig_a;
+                        a.tile_nnz = tn;
+                        a.tile_rows = tr;
+                        a.stages = sd;
+                        a.forward_warps = fw;
+                        a.scatter_warps = 0;
+                        if (!adjoint_shape(A, a, true, nullptr, nullptr)) continue;
+                        A->adj_tuning = a;
+                        if (apply_schedule(A, A->adj, adj_schedule_tuning(A->fwd.tuning, a)) != DOSE_OK) continue;
+                        const float ms = time_launches(s, e0, e1, reps, [&] {
+                            return launch_adjoint(A, ADJ_MODE_QUADRATIC, x, pw, pw + nrp, nullptr, nullptr, f, g,
+                                                  nullptr, 0.f, s);
+                        });
+                        if (ms < 0.f) {
+                            result = cuda_fail(cudaGetLastError(), "dose_autotune fused timing");
+                            break;
+                        }
+                        if (ms < best_a_ms) {
+                            best_a_ms = ms;
+                            best_a = a;
+                        }
+                    }
+        A->adj_tuning = best_a;
+        dose_status st = apply_schedule(A, A->adj, adj_schedule_tuning(A->fwd.tuning, best_a));
+        if (result == DOSE_OK) result = st;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(d);
-    if (result != DOSE_OK) {
-        apply_schedule(A, A->fwd, orig);
-        return result;
-    }
-    dose_status st = apply_schedule(A, A->fwd, best_t);
-    if (st != DOSE_OK) return st;
-    if (best) export_tuning(best_t, A->adj_tuning, best);
+    cudaFree(pw);
+    cudaFree(g);
+    cudaFree(f);
+    if (result != DOSE_OK) return result;
+    if (best) export_tuning(A->fwd.tuning, A->adj_tuning, best);
     return DOSE_OK;
 }
 

@@ -248,3 +248,20 @@ def test_batched_spmm_small(nvec):
     Ds2 = dose.spmv_batched(handles, Xs)
     for D, D2 in zip(Ds, Ds2):
         assert torch.equal(D, D2)
+
+
+def test_autotune_keeps_parity(tiny, objective_inputs):
+    p, w, x = objective_inputs
+    A, enc = make(tiny, "u16")
+    best = A.autotune(_to(x))
+    assert best["tile_nnz"] in (2048, 4096, 8192) and best["adj_tile_nnz"] in (1024, 2048, 4096)
+    assert A.info()["tuning"] == best
+    d = A.spmv(_to(x)).cpu().numpy()
+    fwd_check(d, oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x))
+    f, g = A.fwd_adj_quadratic(_to(x), _to(p), _to(w))
+    f_ref, g_ref = oracle.fgrad(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, x, p, w)
+    assert abs(float(f.item()) - f_ref) <= 1e-4 * f_ref
+    _, r = oracle.objective(oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x), p, w)
+    gabs = oracle.abs_spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r)
+    adj_check(g.cpu().numpy(), g_ref, gabs, rtol=1e-4)
+    A.device_status()
