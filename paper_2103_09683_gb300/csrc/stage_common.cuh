@@ -65,9 +65,9 @@ __host__ __device__ inline SlotLayout slot_layout(uint32_t tile_nnz, uint32_t ti
 }
 
 // Per-row float vectors staged next to the matrix slices.  Rows below `lim`
-// are copied with the slot; rows at or above it (the ragged tail of a caller's
-// array, which cannot be read in whole 16-byte pieces) are read from global
-// memory by whoever needs them.
+// are bulk-copied with the slot; rows at or above it (the ragged tail of a
+// caller's array, which cannot be read in whole 16-byte pieces) are copied by
+// the producer thread with plain loads.
 struct VecSet {
     const float* ptr[kMaxVec];
     uint32_t lim[kMaxVec];
@@ -113,6 +113,16 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
             const uint32_t e = min(round_up(D.row1, 4), vecs.lim[k]);
             vn[k] = e > r_a ? e - r_a : 0;
             bytes += vn[k] * 4;
+            // The ragged tail of a caller's array (< 4 rows) is read with plain
+            // loads and stored before the arrive below, which releases it.
+            float* dst = reinterpret_cast<float*>(buf + SL.vec_off + k * SL.vec_stride);
+            bool tail = false;
+            for (uint32_t r = max(vecs.lim[k], r_a + vn[k]); r < D.row1; ++r) {
+                dst[r - r_a] = __ldg(vecs.ptr[k] + r);
+                tail = true;
+            }
+            // later fills of this slot write the same words through the async proxy
+            if (tail) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         dev::mbar_arrive_expect_tx(&full[st], bytes);
         if (rp_n) dev::bulk_g2s(buf + SL.rp_off, row_ptr + rp_a, rp_n * 4, &full[st]);
@@ -122,7 +132,8 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
                           &full[st]);
         if (c_n) dev::bulk_g2s(buf + SL.col_off, col + c_a, c_n * 4, &full[st]);
         for (uint32_t k = 0; k < vecs.n; ++k)
-            if (vn[k]) dev::bulk_g2s(buf + SL.vec_off + k * SL.vec_stride, vecs.ptr[k] + r_a, vn[k] * 4, &full[st]);
+            if (vn[k])
+                dev::bulk_g2s(buf + SL.vec_off + k * SL.vec_stride, vecs.ptr[k] + r_a, vn[k] * 4, &full[st]);
         ++issued;
         if (++st == S) {
             st = 0;
@@ -145,8 +156,8 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
 // row0 the stage's first row.
 __device__ __forceinline__ float slot_vec(uint32_t slot, const SlotLayout& SL, const VecSet& vecs, uint32_t k,
                                           uint32_t row0, uint32_t r) {
-    if (r < vecs.lim[k]) return dev::lds_f32(slot + SL.vec_off + k * SL.vec_stride + (r - (row0 & ~3u)) * 4);
-    return __ldg(vecs.ptr[k] + r);
+    (void)vecs;
+    return dev::lds_f32(slot + SL.vec_off + k * SL.vec_stride + (r - (row0 & ~3u)) * 4);
 }
 
 // Read the stage descriptor from a slot header.
