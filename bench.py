@@ -161,6 +161,8 @@ def run_gpu(args):
         import torch.distributed as td
         td.init_process_group("nccl", device_id=device)
     csr, A, x, p, w, eta = setup_workload(device)
+    if args.tuning:
+        A.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
     tuned = A.autotune(x) if args.autotune else None
     info = A.info()
     stream = torch.cuda.current_stream()
@@ -361,6 +363,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="time candidate schedules first (dose_autotune)")
+    ap.add_argument("--tuning", default="", help="schedule knobs, e.g. tile_nnz=8192,adj_scatter_warps=4")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -711,20 +711,22 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
     AdjTuning best_a = orig_a;
     if (result == DOSE_OK && A->ncols <= kXSmemMaxCols) {
         float best_a_ms = 1e30f;
-        const uint32_t anz[] = {1024, 2048, 4096};
+        const uint32_t anz[] = {2048, 4096, 8192};
         const uint32_t arows[] = {512, 1024, 2048};
-        const uint32_t adepth[] = {2, 3, 4};
+        const uint32_t adepth[] = {2, 3, 4, 6};
         const uint32_t afw[] = {4, 8};
+        const uint32_t asw[] = {3, 4, 6, 0};
         for (uint32_t tn : anz)
             for (uint32_t tr : arows)
                 for (uint32_t sd : adepth)
-                    for (uint32_t fw : afw) {
+                    for (uint32_t fw : afw)
+                        for (uint32_t sw : asw) {
                         AdjTuning a = orig_a;
                         a.tile_nnz = tn;
                         a.tile_rows = tr;
                         a.stages = sd;
                         a.forward_warps = fw;
-                        a.scatter_warps = 0;
+                        a.scatter_warps = sw;
                         if (!adjoint_shape(A, a, true, nullptr, nullptr)) continue;
                         A->adj_tuning = a;
                         if (apply_schedule(A, A->adj, adj_schedule_tuning(A->fwd.tuning, a)) != DOSE_OK) continue;
