@@ -79,6 +79,65 @@ __device__ __forceinline__ void scatter_entries(uint32_t gw, const SlotView& v, 
 // Forward part of the fused pass for the non-empty rows of a NORMAL stage,
 // 2^LG lanes per row: d, the objective terms, and r_i = 2 w_i (d_i - p_i) (FP8:
 // times the row scale) into the slot's r list.
+// Scatter of a NORMAL stage's non-empty rows i = first, first + Ws, ... by one
+// warp, software-pipelined: the next row's list entry, row pointers and r are
+// loaded while the current row's accumulator updates are in flight.  Rows are
+// still applied strictly in order (the LSU keeps each warp's shared-memory
+// accesses in program order), so the result does not change.
+template <int FMT, bool QUAD, uint32_t kRowScaleVec>
+__device__ __forceinline__ void scatter_rows(uint32_t gw, const SlotView& v, uint32_t slot, const SlotLayout& SL,
+                                             const VecSet& vecs, const StageDesc& D, uint32_t first, uint32_t Ws,
+                                             uint32_t lane) {
+    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
+    const uint32_t n_ne = D.ne1 - D.ne0;
+    const uint32_t rl = slot + SL.rl_off;
+    auto meta = [&](uint32_t i, uint32_t& kb, uint32_t& ke, float& rj) {
+        const uint32_t row = D.row0 + dev::lds_u16(v.ne + 2 * i);
+        kb = dev::lds_u32(v.rp + 4 * row);
+        ke = dev::lds_u32(v.rp + 4 * row + 4);
+        if (QUAD) {
+            rj = dev::lds_f32(rl + 4 * i);
+        } else {
+            rj = slot_vec(slot, SL, vecs, 0, D.row0, row);
+            if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) rj = __fmul_rn(rj, slot_vec(slot, SL, vecs, kRowScaleVec, D.row0, row));
+        }
+    };
+    uint32_t i = first;
+    if (i >= n_ne) return;
+    uint32_t kb, ke;
+    float rj;
+    meta(i, kb, ke, rj);
+    while (true) {
+        const uint32_t k0 = kb + lane, kend = ke;
+        const float r = rj;
+        // this row's first 128 entries: 4 per lane
+        uint32_t ga[4];
+        float a[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t k = k0 + 32u * u;
+            ok[u] = k < kend;
+            ga[u] = gw + 4 * (ok[u] ? dev::lds_u32(v.col + 4 * k) : 0u);
+            a[u] = ok[u] ? Fmt<FMT>::lds(v.val + ES * k) : 0.f;
+        }
+        // next row's metadata, independent of this row's updates
+        i += Ws;
+        const bool more = i < n_ne;
+        if (more) meta(i, kb, ke, rj);
+        float gv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) gv[u] = ok[u] ? dev::lds_f32(ga[u]) : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (ok[u]) dev::sts_f32(ga[u], __fmaf_rn(a[u], r, gv[u]));
+        // entries beyond the first 128 (rows longer than 128)
+        if (k0 + 128 < kend) scatter_entries<FMT>(gw, v, k0 + 128, kend, 32, r);
+        __syncwarp();  // all lanes' updates of this row precede the next row's loads
+        if (!more) break;
+    }
+}
+
 template <int FMT, uint32_t LG, uint32_t kRowScaleVec>
 __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D, const SlotView& v, uint32_t slot,
                                          const SlotLayout& SL, uint32_t xs_a, uint32_t ftid, uint32_t lane,
@@ -244,22 +303,7 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
             const StageDesc D = slot_desc(slot);
             const SlotView v = slot_view<FMT>(slot, SL, D);
             if (!(D.meta & STAGE_COOP)) {
-                const uint32_t rl = slot + SL.rl_off;
-                const uint32_t n_ne = D.ne1 - D.ne0;
-                for (uint32_t i = first; i < n_ne; i += Ws) {
-                    const uint32_t row = D.row0 + dev::lds_u16(v.ne + 2 * i);
-                    float rj;
-                    if (QUAD) {
-                        rj = dev::lds_f32(rl + 4 * i);
-                    } else {
-                        rj = slot_vec(slot, SL, p.vecs, 0, D.row0, row);
-                        if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE)
-                            rj = __fmul_rn(rj, slot_vec(slot, SL, p.vecs, kRowScaleVec, D.row0, row));
-                    }
-                    scatter_entries<FMT>(gw, v, dev::lds_u32(v.rp + 4 * row) + lane, dev::lds_u32(v.rp + 4 * row + 4),
-                                         32, rj);
-                    __syncwarp();
-                }
+                scatter_rows<FMT, QUAD, kRowScaleVec>(gw, v, slot, SL, p.vecs, D, first, Ws, lane);
             } else if (QUAD) {
                 if (D.meta & STAGE_LAST) {
                     // the whole long row, from global memory (its earlier chunks left the ring)
