@@ -41,7 +41,7 @@ struct AdjParams {
     int* err;
 };
 
-constexpr uint32_t kAdjHeader = 1024;  // 3 x 8 mbarriers, CTA reduction scratch
+constexpr uint32_t kAdjHeader = 3072;  // mbarriers, CTA reduction scratch, 2 KB of stage descriptors
 
 template <int FMT>
 __device__ __forceinline__ float finish_dot(const AdjParams& p, float rs, float acc) {
@@ -182,6 +182,8 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + 8;
     uint64_t* fwd_done = full + 16;
+    uint64_t* dbar = full + 24;                              // 2 descriptor-window barriers
+    StageDesc* dwin = reinterpret_cast<StageDesc*>(smem + 1024);  // 2 x kDescWin descriptors
     float* red = reinterpret_cast<float*>(smem + 256);      // 32 floats: long-row partials
     double* fred = reinterpret_cast<double*>(smem + 512);   // 32 doubles: per-warp objective
     const uint32_t gw_floats = round_up(p.ncols * 4, 128) / 4;
@@ -201,6 +203,8 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
             dev::mbar_init(&empty[i], Ws);
             if (QUAD) dev::mbar_init(&fwd_done[i], Wf);
         }
+        dev::mbar_init(&dbar[0], 1);
+        dev::mbar_init(&dbar[1], 1);
         dev::fence_mbar_init();
     }
     __syncthreads();
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     if (warp == 0) {
         if (lane == 0)
             run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, p.vecs, slot_base, SL, full,
-                              empty, S, p.err);
+                              empty, S, dwin, dbar, p.err);
         return;
     }
 
@@ -456,7 +460,7 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
         prm.f_part = A->f_part;
         prm.nrows = A->nrows;
         prm.ncols = A->ncols;
-        prm.sched = ScheduleView{A->adj.desc, A->adj.ne, A->adj.order, A->adj.cta_begin};
+        prm.sched = ScheduleView{A->adj.desc, A->adj.ne, A->adj.cta_begin};
         const uint32_t user_lim = A->nrows & ~3u;  // caller arrays: whole 16-byte pieces only
         prm.vecs.n = 0;
         if (quad) {

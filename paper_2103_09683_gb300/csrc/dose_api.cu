@@ -186,13 +186,16 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
         ++item;
         s = e;
     }
+    // Store the descriptors CTA by CTA, so each CTA reads one contiguous range.
+    std::vector<StageDesc> sorted;
+    sorted.reserve(n);
     S.cta_begin.assign(grid + 1, 0);
-    S.order.reserve(n);
     for (uint32_t c = 0; c < grid; ++c) {
-        S.cta_begin[c] = (uint32_t)S.order.size();
-        S.order.insert(S.order.end(), per[c].begin(), per[c].end());
+        S.cta_begin[c] = (uint32_t)sorted.size();
+        for (uint32_t k : per[c]) sorted.push_back(S.desc[k]);
     }
-    S.cta_begin[grid] = (uint32_t)S.order.size();
+    S.cta_begin[grid] = (uint32_t)sorted.size();
+    S.desc.swap(sorted);
     return S;
 }
 
@@ -201,11 +204,9 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
 static void free_dev_schedule(DevSchedule& D) {
     cudaFree(D.desc);
     cudaFree(D.ne);
-    cudaFree(D.order);
     cudaFree(D.cta_begin);
     D.desc = nullptr;
     D.ne = nullptr;
-    D.order = nullptr;
     D.cta_begin = nullptr;
     D.n_stages = 0;
 }
@@ -290,7 +291,6 @@ static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& 
     cudaError_t e;
     if ((e = upload(&D.desc, S.desc.data(), S.desc.size(), S.desc.size() + 1)) != cudaSuccess ||
         (e = upload(&D.ne, S.ne.data(), S.ne.size(), (S.ne.size() + 7) / 8 * 8 + 16)) != cudaSuccess ||
-        (e = upload(&D.order, S.order.data(), S.order.size(), S.order.size() + 1)) != cudaSuccess ||
         (e = upload(&D.cta_begin, S.cta_begin.data(), S.cta_begin.size(), S.cta_begin.size())) != cudaSuccess)
         return cuda_fail(e, "uploading the schedule");
     D.n_stages = (uint32_t)S.desc.size();
@@ -311,7 +311,7 @@ static Tuning adj_schedule_tuning(const Tuning& fwd, const AdjTuning& a) {
 }
 
 static uint64_t schedule_bytes(const DevSchedule& D) {
-    return (uint64_t)(D.n_stages + 1) * (sizeof(StageDesc) + 4) + (D.grid + 1) * 4;
+    return (uint64_t)(D.n_stages + 1) * sizeof(StageDesc) + (D.grid + 1) * 4;
 }
 
 static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }

@@ -56,10 +56,9 @@ struct Tuning {
 };
 
 struct Schedule {
-    std::vector<StageDesc> desc;      // n_stages
+    std::vector<StageDesc> desc;      // n_stages, stored CTA by CTA
     std::vector<uint16_t> ne;         // non-empty rows of NORMAL stages (offset from row0)
-    std::vector<uint32_t> order;      // stage indices, CTA by CTA
-    std::vector<uint32_t> cta_begin;  // grid + 1: CTA c runs order[cta_begin[c] .. cta_begin[c+1])
+    std::vector<uint32_t> cta_begin;  // grid + 1: CTA c runs desc[cta_begin[c] .. cta_begin[c+1])
     uint32_t n_coop_rows = 0;
     uint32_t lanes_hist[6] = {0, 0, 0, 0, 0, 0};
 };
@@ -68,7 +67,6 @@ struct Schedule {
 struct DevSchedule {
     StageDesc* desc = nullptr;
     uint16_t* ne = nullptr;
-    uint32_t* order = nullptr;
     uint32_t* cta_begin = nullptr;
     uint32_t n_stages = 0;
     uint32_t grid = 0;
@@ -81,7 +79,6 @@ struct DevSchedule {
 struct ScheduleView {
     const StageDesc* desc;
     const uint16_t* ne;
-    const uint32_t* order;
     const uint32_t* cta_begin;
 };
 

@@ -36,7 +36,7 @@ struct SpmvParams {
     int* err;
 };
 
-constexpr uint32_t kHeaderBytes = 1024;  // mbarriers (<= 16 x 8 B) + CTA reduction scratch
+constexpr uint32_t kHeaderBytes = 3072;  // mbarriers, CTA reduction scratch, 2 KB of stage descriptors
 
 // Combine the (sum, compensation) pairs of the `width` lanes of a group.
 template <bool COMP>
@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     const uint32_t S = p.depth, W = p.cwarps;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + S;
+    uint64_t* dbar = full + 16;                         // 2 descriptor-window barriers
     float* red = reinterpret_cast<float*>(smem + 256);  // 64 floats: CTA reduction
+    StageDesc* dwin = reinterpret_cast<StageDesc*>(smem + 1024);  // 2 x kDescWin descriptors
     float* xs = reinterpret_cast<float*>(smem + kHeaderBytes);
     const uint32_t x_bytes = XSMEM ? round_up(p.ncols * 4, 128) : 0;
     unsigned char* slot_base = smem + kHeaderBytes + x_bytes;
@@ -133,6 +135,8 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
             dev::mbar_init(&full[i], 1);
             dev::mbar_init(&empty[i], W);
         }
+        dev::mbar_init(&dbar[0], 1);
+        dev::mbar_init(&dbar[1], 1);
         dev::fence_mbar_init();
     }
     __syncthreads();
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     if (warp == 0) {
         if (lane == 0)
             run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, p.vecs, slot_base, SL, full,
-                              empty, S, p.err);
+                              empty, S, dwin, dbar, p.err);
         return;
     }
 
@@ -260,7 +264,7 @@ cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStre
     p.d = d;
     p.nrows = A->nrows;
     p.ncols = A->ncols;
-    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.order, A->fwd.cta_begin};
+    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin};
     p.vecs.n = 0;
     if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {  // library-owned, padded: every row can be copied
         p.vecs.n = 1;

@@ -76,25 +76,54 @@ struct VecSet {
 
 #ifdef __CUDACC__
 
+constexpr uint32_t kDescWin = 32;  // stage descriptors per shared-memory window (1 KB)
+
 // Producer loop (one thread): for each stage of [s_begin, s_end) wait until its
 // ring slot is free, copy the stage descriptor into the slot header, then
 // bulk-copy the row_ptr / non-empty-list / value / column / vector slices and
-// let the slot's `full` barrier count the bytes.  Before returning, wait until
-// every copy it issued has landed, so the CTA never exits with copies into its
-// shared memory in flight.  All waits are bounded.
+// let the slot's `full` barrier count the bytes.  The CTA's descriptors are
+// contiguous in global memory and arrive in double-buffered windows of 32
+// (`dwin`, completion on `dbar[2]`), so the loop never waits on a global load.
+// Before returning, wait until every copy it issued has landed, so the CTA
+// never exits with copies into its shared memory in flight.  All waits are
+// bounded.
 template <int FMT>
 __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32_t s_end,
                              const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
                              const void* __restrict__ val, const VecSet& vecs, unsigned char* slot_base,
-                             const SlotLayout& SL, uint64_t* full, uint64_t* empty, uint32_t S, int* err) {
+                             const SlotLayout& SL, uint64_t* full, uint64_t* empty, uint32_t S, StageDesc* dwin,
+                             uint64_t* dbar, int* err) {
     using T = typename Fmt<FMT>::T;
     constexpr uint32_t VA = Fmt<FMT>::kAlign;
     uint32_t st = 0, ph = 0, issued = 0;
-    StageDesc nxt;
-    if (s_begin < s_end) nxt = sched.desc[sched.order[s_begin]];
+    auto load_window = [&](uint32_t w) {
+        const uint32_t first = s_begin + w * kDescWin;
+        if (first >= s_end) return;
+        const uint32_t n = min(kDescWin, s_end - first);
+        dev::mbar_arrive_expect_tx(&dbar[w & 1], n * (uint32_t)sizeof(StageDesc));
+        dev::bulk_g2s(dwin + (w & 1) * kDescWin, sched.desc + first, n * (uint32_t)sizeof(StageDesc), &dbar[w & 1]);
+    };
+    const uint32_t nwin = (s_end - s_begin + kDescWin - 1) / kDescWin;
+    uint32_t w_issued = 0, w_waited = 0;  // descriptor windows issued / waited for
+    load_window(0);
+    load_window(1);
+    w_issued = min(nwin, 2u);
     for (uint32_t s = s_begin; s < s_end; ++s) {
-        const StageDesc D = nxt;
-        if (s + 1 < s_end) nxt = sched.desc[sched.order[s + 1]];  // in flight while this stage is issued
+        const uint32_t j = s - s_begin, w = j / kDescWin, jw = j % kDescWin;
+        if (jw == 0) {
+            if (!dev::mbar_wait_bounded(&dbar[w & 1], (w >> 1) & 1)) {
+                atomicExch(err, kErrTimeoutEmpty);
+                break;
+            }
+            w_waited = w + 1;
+        }
+        const StageDesc D = dwin[(w & 1) * kDescWin + jw];
+        if (jw == kDescWin - 1 && w + 2 < nwin) {
+            // the window's last descriptor is in registers: refill its buffer
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            load_window(w + 2);
+            w_issued = w + 3;
+        }
         if (!dev::mbar_wait_bounded(&empty[st], ph ^ 1)) {
             atomicExch(err, kErrTimeoutEmpty);
             break;
@@ -140,6 +169,8 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
             ph ^= 1;
         }
     }
+    // Descriptor windows issued but not waited for (only after a timeout).
+    for (uint32_t w = w_waited; w < w_issued; ++w) dev::mbar_wait_bounded(&dbar[w & 1], (w >> 1) & 1);
     uint32_t n = issued < S ? issued : S;
     for (uint32_t i = 0; i < n; ++i) {
         if (st == 0) {
