@@ -108,18 +108,17 @@ __device__ __forceinline__ void scatter_rows(uint32_t gw, const SlotView& v, uin
     float rj;
     meta(i, kb, ke, rj);
     while (true) {
-        const uint32_t k0 = kb + lane, kend = ke;
+        const uint32_t kend = ke;
         const float r = rj;
-        // this row's first 128 entries: 4 per lane
+        uint32_t k = kb + lane;
+        // this row's first 128 entries, 4 per lane, predicated (no branches)
         uint32_t ga[4];
         float a[4];
-        bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint32_t k = k0 + 32u * u;
-            ok[u] = k < kend;
-            ga[u] = gw + 4 * (ok[u] ? dev::lds_u32(v.col + 4 * k) : 0u);
-            a[u] = ok[u] ? Fmt<FMT>::lds(v.val + ES * k) : 0.f;
+            const uint32_t ku = k + 32u * u;
+            ga[u] = gw + 4 * dev::lds_u32_lt(ku, kend, v.col + 4 * ku);
+            a[u] = Fmt<FMT>::lds_lt(ku, kend, v.val + ES * ku);
         }
         // next row's metadata, independent of this row's updates
         i += Ws;
@@ -127,12 +126,22 @@ __device__ __forceinline__ void scatter_rows(uint32_t gw, const SlotView& v, uin
         if (more) meta(i, kb, ke, rj);
         float gv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) gv[u] = ok[u] ? dev::lds_f32(ga[u]) : 0.f;
+        for (int u = 0; u < 4; ++u) gv[u] = dev::lds_f32_lt(k + 32u * u, kend, ga[u]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (ok[u]) dev::sts_f32(ga[u], __fmaf_rn(a[u], r, gv[u]));
+        for (int u = 0; u < 4; ++u) dev::sts_f32_lt(k + 32u * u, kend, ga[u], __fmaf_rn(a[u], r, gv[u]));
         // entries beyond the first 128 (rows longer than 128)
-        if (k0 + 128 < kend) scatter_entries<FMT>(gw, v, k0 + 128, kend, 32, r);
+        for (k += 128; k < kend; k += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t ku = k + 32u * u;
+                ga[u] = gw + 4 * dev::lds_u32_lt(ku, kend, v.col + 4 * ku);
+                a[u] = Fmt<FMT>::lds_lt(ku, kend, v.val + ES * ku);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) gv[u] = dev::lds_f32_lt(k + 32u * u, kend, ga[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dev::sts_f32_lt(k + 32u * u, kend, ga[u], __fmaf_rn(a[u], r, gv[u]));
+        }
         __syncwarp();  // all lanes' updates of this row precede the next row's loads
         if (!more) break;
     }
@@ -150,12 +159,14 @@ __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D,
     for (uint32_t base = 0; base < n_ne; base += G) {
         const uint32_t i = base + j0;
         const bool has = i < n_ne;
-        float sum = 0.f;
-        uint32_t row = 0;
+        uint32_t row = 0, rs = 0, re = 0;
         if (has) {
             row = D.row0 + dev::lds_u16(v.ne + 2 * i);
-            sum = dot_fixed<FMT, L>(v, xs_a, dev::lds_u32(v.rp + 4 * row) + li, dev::lds_u32(v.rp + 4 * row + 4));
+            rs = dev::lds_u32(v.rp + 4 * row);
+            re = dev::lds_u32(v.rp + 4 * row + 4);
         }
+        const uint32_t iters = __reduce_max_sync(0xffffffffu, (re - rs + 4 * L - 1) / (4 * L));
+        float sum = dot_uniform<FMT, L>(v, xs_a, rs + li, re, iters);
 #pragma unroll
         for (uint32_t off = L >> 1; off > 0; off >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
         if (has && li == 0) {

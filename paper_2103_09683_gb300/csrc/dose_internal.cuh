@@ -265,6 +265,36 @@ __device__ __forceinline__ void sts_f32(uint32_t a, float v) {
     asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
 
+// Predicated forms: access only when k < ke (no branch); loads give 0 otherwise.
+__device__ __forceinline__ uint32_t lds_u32_lt(uint32_t k, uint32_t ke, uint32_t a) {
+    uint32_t v = 0;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %1, %2;\n\t@q ld.shared.u32 %0, [%3];\n\t}"
+                 : "+r"(v) : "r"(k), "r"(ke), "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u16_lt(uint32_t k, uint32_t ke, uint32_t a) {
+    uint16_t v = 0;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %1, %2;\n\t@q ld.shared.u16 %0, [%3];\n\t}"
+                 : "+h"(v) : "r"(k), "r"(ke), "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u8_lt(uint32_t k, uint32_t ke, uint32_t a) {
+    uint16_t v = 0;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %1, %2;\n\t@q ld.shared.u8 %0, [%3];\n\t}"
+                 : "+h"(v) : "r"(k), "r"(ke), "r"(a));
+    return v;
+}
+__device__ __forceinline__ float lds_f32_lt(uint32_t k, uint32_t ke, uint32_t a) {
+    float v = 0.f;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %1, %2;\n\t@q ld.shared.f32 %0, [%3];\n\t}"
+                 : "+f"(v) : "r"(k), "r"(ke), "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_f32_lt(uint32_t k, uint32_t ke, uint32_t a, float v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %0, %1;\n\t@q st.shared.f32 [%2], %3;\n\t}"
+                 ::"r"(k), "r"(ke), "r"(a), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ void named_barrier(uint32_t id, uint32_t nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }

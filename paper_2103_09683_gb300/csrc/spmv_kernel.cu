@@ -96,10 +96,17 @@ __device__ __forceinline__ void normal_rows(const SpmvParams& p, const StageDesc
         const uint32_t i = base + j0;
         const bool has = i < n_ne;
         float sum = 0.f, comp = 0.f;
-        uint32_t row = 0;
+        uint32_t row = 0, rs = 0, re = 0;
         if (has) {
             row = D.row0 + dev::lds_u16(v.ne + 2 * i);
-            const uint32_t rs = dev::lds_u32(v.rp + 4 * row), re = dev::lds_u32(v.rp + 4 * row + 4);
+            rs = dev::lds_u32(v.rp + 4 * row);
+            re = dev::lds_u32(v.rp + 4 * row + 4);
+        }
+        if (XSMEM && !COMP) {
+            // one trip count for the whole warp: no divergent loop tails
+            const uint32_t iters = __reduce_max_sync(0xffffffffu, (re - rs + 4 * L - 1) / (4 * L));
+            sum = dot_uniform<FMT, L>(v, xs_a, rs + li, re, iters);
+        } else if (has) {
             if (COMP && re - rs > kCompThreshold)
                 dot_strided_comp<FMT>(v, xs_a, p.x, XSMEM, rs + li, re, L, sum, comp);
             else

@@ -15,8 +15,9 @@ struct Fmt<DOSE_FMT_U16_SCALE> {
     static constexpr uint32_t kAlign = 8;  // elements per 16 bytes
 #ifdef __CUDACC__
     __device__ static float dec(T v) { return dev::dec_u16(v); }
-    // decoded value of the stored entry at shared address a
+    // decoded value of the stored entry at shared address a (0 unless k < ke)
     __device__ static float lds(uint32_t a) { return (float)dev::lds_u16(a); }
+    __device__ static float lds_lt(uint32_t k, uint32_t ke, uint32_t a) { return (float)dev::lds_u16_lt(k, ke, a); }
 #endif
 };
 template <>
@@ -26,6 +27,9 @@ struct Fmt<DOSE_FMT_BF16> {
 #ifdef __CUDACC__
     __device__ static float dec(T v) { return dev::dec_bf16(v); }
     __device__ static float lds(uint32_t a) { return __uint_as_float(dev::lds_u16(a) << 16); }
+    __device__ static float lds_lt(uint32_t k, uint32_t ke, uint32_t a) {
+        return __uint_as_float(dev::lds_u16_lt(k, ke, a) << 16);
+    }
 #endif
 };
 template <>
@@ -35,6 +39,9 @@ struct Fmt<DOSE_FMT_FP8E4M3_ROWSCALE> {
 #ifdef __CUDACC__
     __device__ static float dec(T v) { return dev::dec_e4m3(v); }
     __device__ static float lds(uint32_t a) { return dev::dec_e4m3((uint8_t)dev::lds_u8(a)); }
+    __device__ static float lds_lt(uint32_t k, uint32_t ke, uint32_t a) {
+        return dev::dec_e4m3((uint8_t)dev::lds_u8_lt(k, ke, a));
+    }
 #endif
 };
 
@@ -253,6 +260,33 @@ __device__ __forceinline__ float dot_fixed(const SlotView& v, uint32_t xs, uint3
         if (n > 1) a1 = __fmaf_rn(Fmt<FMT>::lds(va + ES * STEP), dev::lds_f32(xs + 4 * dev::lds_u32(ca + 4 * STEP)), a1);
         if (n > 2)
             a2 = __fmaf_rn(Fmt<FMT>::lds(va + 2 * ES * STEP), dev::lds_f32(xs + 4 * dev::lds_u32(ca + 8 * STEP)), a2);
+    }
+    return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
+}
+
+// Branch-free form of dot_fixed: `iters` (equal for the whole warp) unrolled
+// steps of four entries per lane; entries at or beyond ke are masked by
+// predicated loads that give a = 0 and x = 0, so they add exactly nothing.
+template <int FMT, uint32_t STEP>
+__device__ __forceinline__ float dot_uniform(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke,
+                                             uint32_t iters) {
+    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    uint32_t k = kb, ca = v.col + 4 * kb, va = v.val + ES * kb;
+    for (uint32_t it = 0; it < iters; ++it) {
+        const uint32_t k1 = k + STEP, k2 = k + 2 * STEP, k3 = k + 3 * STEP;
+        const uint32_t c0 = dev::lds_u32_lt(k, ke, ca), c1 = dev::lds_u32_lt(k1, ke, ca + 4 * STEP);
+        const uint32_t c2 = dev::lds_u32_lt(k2, ke, ca + 8 * STEP), c3 = dev::lds_u32_lt(k3, ke, ca + 12 * STEP);
+        const float w0 = Fmt<FMT>::lds_lt(k, ke, va), w1 = Fmt<FMT>::lds_lt(k1, ke, va + ES * STEP);
+        const float w2 = Fmt<FMT>::lds_lt(k2, ke, va + 2 * ES * STEP);
+        const float w3 = Fmt<FMT>::lds_lt(k3, ke, va + 3 * ES * STEP);
+        a0 = __fmaf_rn(w0, dev::lds_f32_lt(k, ke, xs + 4 * c0), a0);
+        a1 = __fmaf_rn(w1, dev::lds_f32_lt(k1, ke, xs + 4 * c1), a1);
+        a2 = __fmaf_rn(w2, dev::lds_f32_lt(k2, ke, xs + 4 * c2), a2);
+        a3 = __fmaf_rn(w3, dev::lds_f32_lt(k3, ke, xs + 4 * c3), a3);
+        k += 4 * STEP;
+        ca += 16 * STEP;
+        va += 4 * ES * STEP;
     }
     return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
 }
