@@ -100,12 +100,15 @@ typedef struct {
     uint32_t lane_target;    /* lanes per row = power of two nearest mean row length / lane_target */
     uint32_t stages;         /* pipeline depth (2..8) */
     uint32_t consumer_warps; /* 4, 8 or 16 */
+    uint32_t l2_prefetch;    /* stages prefetched into L2 ahead of the shared-memory ring (0..31);
+                                set 32 to mean "off" */
     /* adjoint and fused objective pass (dose_adjoint, dose_fwd_adj_quadratic, dose_pg_step) */
     uint32_t adj_tile_nnz;      /* (256..16384) */
     uint32_t adj_tile_rows;     /* (32..8192) */
     uint32_t adj_stages;        /* (2..8) */
     uint32_t adj_forward_warps; /* warps computing d, f, r in the fused pass (1..15) */
     uint32_t adj_scatter_warps; /* warps owning gradient accumulators (0 = as many as fit) */
+    uint32_t adj_l2_prefetch;   /* as l2_prefetch, for these passes (32 = off) */
 } dose_tuning;
 
 typedef struct {

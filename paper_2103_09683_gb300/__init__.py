@@ -50,9 +50,10 @@ class Tuning(ctypes.Structure):
     _fields_ = [("tile_nnz", ctypes.c_uint32), ("tile_rows", ctypes.c_uint32),
                 ("coop_nnz", ctypes.c_uint32), ("lane_target", ctypes.c_uint32),
                 ("stages", ctypes.c_uint32), ("consumer_warps", ctypes.c_uint32),
+                ("l2_prefetch", ctypes.c_uint32),
                 ("adj_tile_nnz", ctypes.c_uint32), ("adj_tile_rows", ctypes.c_uint32),
                 ("adj_stages", ctypes.c_uint32), ("adj_forward_warps", ctypes.c_uint32),
-                ("adj_scatter_warps", ctypes.c_uint32)]
+                ("adj_scatter_warps", ctypes.c_uint32), ("adj_l2_prefetch", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

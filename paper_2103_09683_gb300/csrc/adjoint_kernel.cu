@@ -37,7 +37,7 @@ struct AdjParams {
     uint32_t nrows, ncols;
     ScheduleView sched;
     VecSet vecs;      // QUADRATIC: p, w [, row scale]; ADJOINT: r [, row scale]
-    uint32_t tile_nnz, tile_rows, depth, fwarps, swarps;
+    uint32_t tile_nnz, tile_rows, depth, fwarps, swarps, l2pf;
     int* err;
 };
 
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     if (warp == 0) {
         if (lane == 0)
             run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, p.vecs, slot_base, SL, full,
-                              empty, S, dwin, dbar, p.err);
+                              empty, S, dwin, dbar, p.l2pf, p.err);
         return;
     }
 
@@ -495,6 +495,7 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
         prm.depth = t.stages;
         prm.fwarps = t.forward_warps;
         prm.swarps = t.scatter_warps;
+        prm.l2pf = t.l2_prefetch;
         prm.err = A->err;
         cudaError_t e = cudaSuccess;
         switch (A->fmt) {

@@ -253,11 +253,13 @@ static void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
     if (in->lane_target) t.lane_target = in->lane_target;
     if (in->stages) t.stages = in->stages;
     if (in->consumer_warps) t.consumer_warps = in->consumer_warps;
+    if (in->l2_prefetch) t.l2_prefetch = in->l2_prefetch >= 32 ? 0 : in->l2_prefetch;
     if (in->adj_tile_nnz) a.tile_nnz = in->adj_tile_nnz;
     if (in->adj_tile_rows) a.tile_rows = in->adj_tile_rows;
     if (in->adj_stages) a.stages = in->adj_stages;
     if (in->adj_forward_warps) a.forward_warps = in->adj_forward_warps;
     if (in->adj_scatter_warps) a.scatter_warps = in->adj_scatter_warps;
+    if (in->adj_l2_prefetch) a.l2_prefetch = in->adj_l2_prefetch >= 32 ? 0 : in->adj_l2_prefetch;
 }
 
 static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out) {
@@ -267,11 +269,13 @@ static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out)
     out->lane_target = t.lane_target;
     out->stages = t.stages;
     out->consumer_warps = t.consumer_warps;
+    out->l2_prefetch = t.l2_prefetch ? t.l2_prefetch : 32;
     out->adj_tile_nnz = a.tile_nnz;
     out->adj_tile_rows = a.tile_rows;
     out->adj_stages = a.stages;
     out->adj_forward_warps = a.forward_warps;
     out->adj_scatter_warps = a.scatter_warps;
+    out->adj_l2_prefetch = a.l2_prefetch ? a.l2_prefetch : 32;
 }
 
 template <class T>

@@ -53,6 +53,7 @@ struct Tuning {
     uint32_t lane_target = 12;  // entries per lane: 4 per unrolled step, about 3 steps
     uint32_t stages = 4;
     uint32_t consumer_warps = 16;
+    uint32_t l2_prefetch = 0;   // stages prefetched into L2 ahead of the shared-memory ring
 };
 
 struct Schedule {
@@ -89,6 +90,7 @@ struct AdjTuning {
     uint32_t stages = 3;
     uint32_t forward_warps = 8;   // fused pass: warps computing d, f and r
     uint32_t scatter_warps = 0;   // warps owning gradient accumulators (0 = as many as fit)
+    uint32_t l2_prefetch = 8;     // stages prefetched into L2 ahead of the shared-memory ring
 };
 
 }  // namespace dose
@@ -293,6 +295,12 @@ __device__ __forceinline__ float lds_f32_lt(uint32_t k, uint32_t ke, uint32_t a)
 __device__ __forceinline__ void sts_f32_lt(uint32_t k, uint32_t ke, uint32_t a, float v) {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %0, %1;\n\t@q st.shared.f32 [%2], %3;\n\t}"
                  ::"r"(k), "r"(ke), "r"(a), "f"(v) : "memory");
+}
+
+// Bulk prefetch global -> L2 (no shared memory, no completion): addr 16-byte
+// aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void named_barrier(uint32_t id, uint32_t nthreads) {

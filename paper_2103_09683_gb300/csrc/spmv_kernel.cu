@@ -32,7 +32,7 @@ struct SpmvParams {
     uint32_t nrows, ncols;
     ScheduleView sched;
     VecSet vecs;  // FP8: the row scales
-    uint32_t tile_nnz, tile_rows, depth, cwarps;
+    uint32_t tile_nnz, tile_rows, depth, cwarps, l2pf;
     int* err;
 };
 
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     if (warp == 0) {
         if (lane == 0)
             run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, p.vecs, slot_base, SL, full,
-                              empty, S, dwin, dbar, p.err);
+                              empty, S, dwin, dbar, p.l2pf, p.err);
         return;
     }
 
@@ -282,6 +282,7 @@ cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStre
     p.tile_rows = A->fwd.tuning.tile_rows;
     p.depth = A->fwd.tuning.stages;
     p.cwarps = A->fwd.tuning.consumer_warps;
+    p.l2pf = A->fwd.tuning.l2_prefetch;
     p.err = A->err;
     const bool xsmem = spmv_x_in_smem(A);
     const size_t smem = spmv_smem_bytes(A, A->fwd.tuning, xsmem);

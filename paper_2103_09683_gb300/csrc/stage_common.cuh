@@ -99,7 +99,7 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
                              const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
                              const void* __restrict__ val, const VecSet& vecs, unsigned char* slot_base,
                              const SlotLayout& SL, uint64_t* full, uint64_t* empty, uint32_t S, StageDesc* dwin,
-                             uint64_t* dbar, int* err) {
+                             uint64_t* dbar, uint32_t pf, int* err) {
     using T = typename Fmt<FMT>::T;
     constexpr uint32_t VA = Fmt<FMT>::kAlign;
     uint32_t st = 0, ph = 0, issued = 0;
@@ -110,23 +110,47 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
         dev::mbar_arrive_expect_tx(&dbar[w & 1], n * (uint32_t)sizeof(StageDesc));
         dev::bulk_g2s(dwin + (w & 1) * kDescWin, sched.desc + first, n * (uint32_t)sizeof(StageDesc), &dbar[w & 1]);
     };
-    const uint32_t nwin = (s_end - s_begin + kDescWin - 1) / kDescWin;
+    const uint32_t nst = s_end - s_begin;
+    const uint32_t nwin = (nst + kDescWin - 1) / kDescWin;
     uint32_t w_issued = 0, w_waited = 0;  // descriptor windows issued / waited for
     load_window(0);
     load_window(1);
     w_issued = min(nwin, 2u);
+    // Make window w readable (windows are waited for in order).
+    auto have_window = [&](uint32_t w) -> bool {
+        while (w_waited <= w) {
+            if (!dev::mbar_wait_bounded(&dbar[w_waited & 1], (w_waited >> 1) & 1)) return false;
+            ++w_waited;
+        }
+        return true;
+    };
+    // Ask L2 for stage j's slices (the HBM latency is then paid into L2,
+    // not into the shared-memory ring).
+    auto prefetch = [&](uint32_t j) {
+        const uint32_t w = j / kDescWin;
+        if (w >= w_issued || !have_window(w)) return;
+        const StageDesc P = dwin[(w & 1) * kDescWin + j % kDescWin];
+        const uint32_t v_a = P.nz0 & ~(VA - 1), v_n = round_up(P.nz1, VA) - v_a;
+        const uint32_t c_a = P.nz0 & ~3u, c_n = round_up(P.nz1, 4) - c_a;
+        if (v_n) dev::bulk_prefetch_l2(static_cast<const T*>(val) + v_a, v_n * (uint32_t)sizeof(T));
+        if (c_n) dev::bulk_prefetch_l2(col + c_a, c_n * 4);
+        if (!(P.meta & STAGE_COOP)) {
+            const uint32_t rp_a = P.row0 & ~3u;
+            dev::bulk_prefetch_l2(row_ptr + rp_a, (round_up(P.row1 + 1, 4) - rp_a) * 4);
+        }
+    };
+    for (uint32_t j = 0; j < pf && j < nst; ++j) prefetch(j);
     for (uint32_t s = s_begin; s < s_end; ++s) {
         const uint32_t j = s - s_begin, w = j / kDescWin, jw = j % kDescWin;
-        if (jw == 0) {
-            if (!dev::mbar_wait_bounded(&dbar[w & 1], (w >> 1) & 1)) {
-                atomicExch(err, kErrTimeoutEmpty);
-                break;
-            }
-            w_waited = w + 1;
+        if (pf && j + pf < nst) prefetch(j + pf);
+        if (!have_window(w)) {
+            atomicExch(err, kErrTimeoutEmpty);
+            break;
         }
         const StageDesc D = dwin[(w & 1) * kDescWin + jw];
         if (jw == kDescWin - 1 && w + 2 < nwin) {
-            // the window's last descriptor is in registers: refill its buffer
+            // the window's last descriptor is in registers (and the prefetch
+            // look-ahead, < kDescWin, reads window w + 1): refill its buffer
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             load_window(w + 2);
             w_issued = w + 3;
