@@ -170,6 +170,26 @@ dose_status dose_fwd_adj_quadratic(const dose_matrix* A, const float* x, const f
 dose_status dose_pg_step(const dose_matrix* A, float* x, const float* p, const float* w, float eta,
                          double* f, float* g, void* stream);
 
+/* g = A^T r without any device allocation -- for callers that cannot call
+ * cudaMalloc (device memory owned by another runtime or a fixed arena,
+ * allocation forbidden after start-up, or a frozen capture memory plan); such
+ * callers cannot create a handle, so A is passed as device CSR arrays.  The
+ * paper has no counterpart: this is a deployment variant of dose_adjoint.
+ *   row_ptr (nrows+1), col_idx (nnz), values (nnz, fmt-encoded): device memory,
+ *   a valid CSR (malformed rows are skipped, never read out of bounds);
+ *   row_scales: FP8 only, device nrows floats; scale: U16 matrix scale;
+ *   r: device nrows floats; g: device ncols floats (written).
+ * Scratch is a 4 MiB static __device__ array that every GPU loading the
+ * library holds until exit; all calls on a device share it, so calls that
+ * overlap on the GPU race -- order them.  The first call on a device looks up
+ * the array's address; make it before any stream capture.  ncols beyond the
+ * scratch (2^20 floats) or beyond one shared-memory accumulator is rejected with
+ * DOSE_ERR_INVALID_ARG.  Deterministic, asynchronous on `stream`. */
+dose_status dose_adjoint_noalloc(uint32_t nrows, uint32_t ncols, uint64_t nnz, const uint32_t* row_ptr,
+                                 const uint32_t* col_idx, dose_format fmt, const void* values,
+                                 const float* row_scales, float scale, const float* r, float* g,
+                                 void* stream);
+
 /* Free the handle and its device memory (synchronises the device first).  NULL -> DOSE_OK. */
 dose_status dose_destroy(dose_matrix* A);
 

@@ -21,7 +21,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["build", "load", "DoseMatrix", "DoseError", "FORMATS", "spmv_batched", "dose_spmv",
+__all__ = ["build", "load", "DoseMatrix", "DoseError", "FORMATS", "spmv_batched", "adjoint_noalloc", "dose_spmv",
            "QuadraticDoseObjective", "pg_solve", "PGSolver", "encode_host", "library_path"]
 
 FORMATS = {"u16": 0, "bf16": 1, "fp8": 2}
@@ -88,6 +88,8 @@ EXPORTS = {
     "dose_autotune": (ctypes.c_int, [_P, _P, _P, _P]),
     "dose_encode_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, _P, ctypes.c_uint64, _P, _P, _P]),
     "dose_device_status": (ctypes.c_int, [_P, _P]),
+    "dose_adjoint_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, _P, _P, ctypes.c_int,
+                                            _P, _P, ctypes.c_float, _P, _P, _P]),
     "dose_last_error": (ctypes.c_char_p, []),
     "dose_version": (ctypes.c_char_p, []),
 }
@@ -324,6 +326,26 @@ class DoseMatrix:
     def device_status(self, stream=None):
         """Synchronise and raise DoseError if a kernel recorded a failure."""
         _check(load().dose_device_status(self._h, _stream_handle(stream)))
+
+
+def adjoint_noalloc(row_ptr, col, values, r, *, ncols: int, fmt: str = "u16", scale: float = 1.0,
+                    row_scales=None, g=None, stream=None):
+    """g = A^T r from caller-held device CSR arrays, allocating no device memory
+    in the library (dose_adjoint_noalloc).  All arrays are CUDA tensors: row_ptr
+    and col int32 (bit patterns of uint32), values int16 (u16/bf16 codes) or
+    uint8 (fp8), r float32; g (optional) float32 [ncols]."""
+    torch = _torch()
+    nrows = int(row_ptr.numel()) - 1
+    nnz = int(col.numel())
+    if g is None:
+        g = torch.empty(ncols, dtype=torch.float32, device=r.device)
+    vt = torch.uint8 if fmt == "fp8" else torch.int16
+    rs = _dptr(row_scales, torch.float32, nrows, "row_scales") if fmt == "fp8" else None
+    _check(load().dose_adjoint_noalloc(
+        nrows, int(ncols), nnz, _dptr(row_ptr, torch.int32, nrows + 1, "row_ptr"), _dptr(col, torch.int32, nnz, "col"),
+        FORMATS[fmt], _dptr(values, vt, nnz, "values"), rs, ctypes.c_float(scale),
+        _dptr(r, torch.float32, nrows, "r"), _dptr(g, torch.float32, int(ncols), "g"), _stream_handle(stream)))
+    return g
 
 
 def spmv_batched(mats, Xs, Ds=None, stream=None):
