@@ -108,39 +108,31 @@ __device__ __forceinline__ void scatter_rows(uint32_t gw, const SlotView& v, uin
     float rj;
     meta(i, kb, ke, rj);
     while (true) {
-        const uint32_t kend = ke;
+        const uint32_t kbeg = kb, kend = ke;
         const float r = rj;
-        uint32_t k = kb + lane;
-        // this row's first 128 entries, 4 per lane, predicated (no branches)
-        uint32_t ga[4];
-        float a[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t ku = k + 32u * u;
-            ga[u] = gw + 4 * dev::lds_u32_lt(ku, kend, v.col + 4 * ku);
-            a[u] = Fmt<FMT>::lds_lt(ku, kend, v.val + ES * ku);
-        }
-        // next row's metadata, independent of this row's updates
-        i += Ws;
-        const bool more = i < n_ne;
-        if (more) meta(i, kb, ke, rj);
-        float gv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) gv[u] = dev::lds_f32_lt(k + 32u * u, kend, ga[u]);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) dev::sts_f32_lt(k + 32u * u, kend, ga[u], __fmaf_rn(a[u], r, gv[u]));
-        // entries beyond the first 128 (rows longer than 128)
-        for (k += 128; k < kend; k += 128) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t ku = k + 32u * u;
-                ga[u] = gw + 4 * dev::lds_u32_lt(ku, kend, v.col + 4 * ku);
-                a[u] = Fmt<FMT>::lds_lt(ku, kend, v.val + ES * ku);
+        // next row's metadata is fetched during this row's first chunk
+        bool more = false;
+        uint32_t k = (kbeg & ~3u) + 4 * lane;
+        for (bool first = true; first || (k - 4 * lane) < kend; first = false, k += 128) {
+            // four consecutive entries per lane: one 16-byte column load, one value load
+            const bool in = k < kend;
+            const uint4 c = dev::lds_v4_if(in, v.col + 4 * k);
+            float a[4];
+            Fmt<FMT>::lds4(in, v.val + ES * k, a);
+            const bool m0 = in && k >= kbeg, m1 = in && k + 1 >= kbeg && k + 1 < kend;
+            const bool m2 = in && k + 2 >= kbeg && k + 2 < kend, m3 = in && k + 3 >= kbeg && k + 3 < kend;
+            if (first) {
+                i += Ws;
+                more = i < n_ne;
+                if (more) meta(i, kb, ke, rj);
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) gv[u] = dev::lds_f32_lt(k + 32u * u, kend, ga[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) dev::sts_f32_lt(k + 32u * u, kend, ga[u], __fmaf_rn(a[u], r, gv[u]));
+            const uint32_t g0 = gw + 4 * c.x, g1 = gw + 4 * c.y, g2 = gw + 4 * c.z, g3 = gw + 4 * c.w;
+            const float v0 = dev::lds_f32_if(m0, g0), v1 = dev::lds_f32_if(m1, g1);
+            const float v2 = dev::lds_f32_if(m2, g2), v3 = dev::lds_f32_if(m3, g3);
+            dev::sts_f32_if(m0, g0, __fmaf_rn(a[0], r, v0));
+            dev::sts_f32_if(m1, g1, __fmaf_rn(a[1], r, v1));
+            dev::sts_f32_if(m2, g2, __fmaf_rn(a[2], r, v2));
+            dev::sts_f32_if(m3, g3, __fmaf_rn(a[3], r, v3));
         }
         __syncwarp();  // all lanes' updates of this row precede the next row's loads
         if (!more) break;
@@ -165,8 +157,9 @@ __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D,
             rs = dev::lds_u32(v.rp + 4 * row);
             re = dev::lds_u32(v.rp + 4 * row + 4);
         }
-        const uint32_t iters = __reduce_max_sync(0xffffffffu, (re - rs + 4 * L - 1) / (4 * L));
-        float sum = dot_uniform<FMT, L>(v, xs_a, rs + li, re, iters);
+        const uint32_t span = re > rs ? re - (rs & ~3u) : 0;
+        const uint32_t iters = __reduce_max_sync(0xffffffffu, (span + 4 * L - 1) / (4 * L));
+        float sum = dot_vec<FMT, L>(v, xs_a, rs, re, li, iters);
 #pragma unroll
         for (uint32_t off = L >> 1; off > 0; off >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
         if (has && li == 0) {

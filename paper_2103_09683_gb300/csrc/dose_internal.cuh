@@ -292,6 +292,37 @@ __device__ __forceinline__ float lds_f32_lt(uint32_t k, uint32_t ke, uint32_t a)
                  : "+f"(v) : "r"(k), "r"(ke), "r"(a));
     return v;
 }
+// Predicated on a boolean: load only when p (0 otherwise) / store only when p.
+__device__ __forceinline__ float lds_f32_if(bool p, uint32_t a) {
+    float v = 0.f;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q ld.shared.f32 %0, [%2];\n\t}"
+                 : "+f"(v) : "r"((uint32_t)p), "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_f32_if(bool p, uint32_t a, float v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.shared.f32 [%1], %2;\n\t}"
+                 ::"r"((uint32_t)p), "r"(a), "f"(v) : "memory");
+}
+// Vector loads (a 16- resp. 8- resp. 4-byte aligned), only when p; zeros otherwise.
+__device__ __forceinline__ uint4 lds_v4_if(bool p, uint32_t a) {
+    uint4 v = make_uint4(0, 0, 0, 0);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t@q ld.shared.v4.u32 {%0, %1, %2, %3}, [%5];\n\t}"
+                 : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w) : "r"((uint32_t)p), "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint2 lds_v2_if(bool p, uint32_t a) {
+    uint2 v = make_uint2(0, 0);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.v2.u32 {%0, %1}, [%3];\n\t}"
+                 : "+r"(v.x), "+r"(v.y) : "r"((uint32_t)p), "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u32_if(bool p, uint32_t a) {
+    uint32_t v = 0;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q ld.shared.u32 %0, [%2];\n\t}"
+                 : "+r"(v) : "r"((uint32_t)p), "r"(a));
+    return v;
+}
+
 __device__ __forceinline__ void sts_f32_lt(uint32_t k, uint32_t ke, uint32_t a, float v) {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %0, %1;\n\t@q st.shared.f32 [%2], %3;\n\t}"
                  ::"r"(k), "r"(ke), "r"(a), "f"(v) : "memory");

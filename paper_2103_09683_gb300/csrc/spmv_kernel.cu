@@ -104,8 +104,9 @@ __device__ __forceinline__ void normal_rows(const SpmvParams& p, const StageDesc
         }
         if (XSMEM && !COMP) {
             // one trip count for the whole warp: no divergent loop tails
-            const uint32_t iters = __reduce_max_sync(0xffffffffu, (re - rs + 4 * L - 1) / (4 * L));
-            sum = dot_uniform<FMT, L>(v, xs_a, rs + li, re, iters);
+            const uint32_t span = re > rs ? re - (rs & ~3u) : 0;
+            const uint32_t iters = __reduce_max_sync(0xffffffffu, (span + 4 * L - 1) / (4 * L));
+            sum = dot_vec<FMT, L>(v, xs_a, rs, re, li, iters);
         } else if (has) {
             if (COMP && re - rs > kCompThreshold)
                 dot_strided_comp<FMT>(v, xs_a, p.x, XSMEM, rs + li, re, L, sum, comp);

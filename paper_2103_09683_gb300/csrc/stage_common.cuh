@@ -18,6 +18,14 @@ struct Fmt<DOSE_FMT_U16_SCALE> {
     // decoded value of the stored entry at shared address a (0 unless k < ke)
     __device__ static float lds(uint32_t a) { return (float)dev::lds_u16(a); }
     __device__ static float lds_lt(uint32_t k, uint32_t ke, uint32_t a) { return (float)dev::lds_u16_lt(k, ke, a); }
+    // four consecutive entries (index a multiple of 4) decoded, loaded only when p
+    __device__ static void lds4(bool p, uint32_t a, float* w) {
+        const uint2 q = dev::lds_v2_if(p, a);
+        w[0] = (float)(q.x & 0xFFFFu);
+        w[1] = (float)(q.x >> 16);
+        w[2] = (float)(q.y & 0xFFFFu);
+        w[3] = (float)(q.y >> 16);
+    }
 #endif
 };
 template <>
@@ -30,6 +38,13 @@ struct Fmt<DOSE_FMT_BF16> {
     __device__ static float lds_lt(uint32_t k, uint32_t ke, uint32_t a) {
         return __uint_as_float(dev::lds_u16_lt(k, ke, a) << 16);
     }
+    __device__ static void lds4(bool p, uint32_t a, float* w) {
+        const uint2 q = dev::lds_v2_if(p, a);
+        w[0] = __uint_as_float(q.x << 16);
+        w[1] = __uint_as_float(q.x & 0xFFFF0000u);
+        w[2] = __uint_as_float(q.y << 16);
+        w[3] = __uint_as_float(q.y & 0xFFFF0000u);
+    }
 #endif
 };
 template <>
@@ -41,6 +56,13 @@ struct Fmt<DOSE_FMT_FP8E4M3_ROWSCALE> {
     __device__ static float lds(uint32_t a) { return dev::dec_e4m3((uint8_t)dev::lds_u8(a)); }
     __device__ static float lds_lt(uint32_t k, uint32_t ke, uint32_t a) {
         return dev::dec_e4m3((uint8_t)dev::lds_u8_lt(k, ke, a));
+    }
+    __device__ static void lds4(bool p, uint32_t a, float* w) {
+        const uint32_t q = dev::lds_u32_if(p, a);
+        w[0] = dev::dec_e4m3((uint8_t)(q & 0xFF));
+        w[1] = dev::dec_e4m3((uint8_t)((q >> 8) & 0xFF));
+        w[2] = dev::dec_e4m3((uint8_t)((q >> 16) & 0xFF));
+        w[3] = dev::dec_e4m3((uint8_t)(q >> 24));
     }
 #endif
 };
@@ -311,6 +333,34 @@ __device__ __forceinline__ float dot_uniform(const SlotView& v, uint32_t xs, uin
         k += 4 * STEP;
         ca += 16 * STEP;
         va += 4 * ES * STEP;
+    }
+    return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
+}
+
+// Vectorised form: lane li of an L-lane group takes the aligned chunks of four
+// consecutive entries starting at (kb & ~3) + 4 li, stepping 4L; one 16-byte
+// load brings four column indices and one 8-byte (u16/bf16) or 4-byte (fp8)
+// load their values.  Entries outside [kb, ke) are masked: their x is not
+// loaded and they add nothing.  `iters` is the same for the whole warp.
+// Chunks never leave the slot: [kb & ~3, round_up(ke, 4)) lies inside the
+// stage's copied slices.
+template <int FMT, uint32_t L>
+__device__ __forceinline__ float dot_vec(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke, uint32_t li,
+                                         uint32_t iters) {
+    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    uint32_t k = (kb & ~3u) + 4 * li;
+    for (uint32_t it = 0; it < iters; ++it, k += 4 * L) {
+        const bool in = k < ke;
+        const uint4 c = dev::lds_v4_if(in, v.col + 4 * k);
+        float w[4];
+        Fmt<FMT>::lds4(in, v.val + ES * k, w);
+        const bool m0 = in && k >= kb, m1 = in && k + 1 >= kb && k + 1 < ke;
+        const bool m2 = in && k + 2 >= kb && k + 2 < ke, m3 = in && k + 3 >= kb && k + 3 < ke;
+        a0 = __fmaf_rn(m0 ? w[0] : 0.f, dev::lds_f32_if(m0, xs + 4 * c.x), a0);
+        a1 = __fmaf_rn(m1 ? w[1] : 0.f, dev::lds_f32_if(m1, xs + 4 * c.y), a1);
+        a2 = __fmaf_rn(m2 ? w[2] : 0.f, dev::lds_f32_if(m2, xs + 4 * c.z), a2);
+        a3 = __fmaf_rn(m3 ? w[3] : 0.f, dev::lds_f32_if(m3, xs + 4 * c.w), a3);
     }
     return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
 }
