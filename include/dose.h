@@ -107,7 +107,9 @@ typedef struct {
     uint32_t adj_tile_rows;     /* (32..8192) */
     uint32_t adj_stages;        /* (2..8) */
     uint32_t adj_forward_warps; /* warps computing d, f, r in the fused pass (1..15) */
-    uint32_t adj_scatter_warps; /* warps owning gradient accumulators (0 = as many as fit) */
+    uint32_t adj_scatter_warps; /* warps owning gradient accumulators (0..22): at most this many,
+                                   fewer if their accumulators do not fit (0 = as many as fit;
+                                   never more than 23 - forward warps) */
     uint32_t adj_l2_prefetch;   /* as l2_prefetch, for these passes (32 = off) */
 } dose_tuning;
 
@@ -123,6 +125,8 @@ typedef struct {
     uint32_t adj_block_fused;   /* threads per CTA of the fused pass (0 if it does not fit) */
     uint32_t adj_block_adjoint; /* threads per CTA of the adjoint (0 if it does not fit) */
     uint32_t max_row_len;
+    uint32_t adj_window;        /* columns of each CTA's gradient window in the adjoint schedule */
+    uint32_t reserved0;
     uint64_t device_bytes;      /* device memory held by the handle */
     uint64_t spmv_bytes;        /* algorithmic HBM bytes of one dose_spmv */
     uint64_t adjoint_bytes;     /* ... of one dose_adjoint */

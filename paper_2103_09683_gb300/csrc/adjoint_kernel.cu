@@ -11,9 +11,10 @@
 //   forward warps     (fused pass only) d for the stage's rows, the FP64
 //                     objective terms, and r_i = 2 w_i (d_i - p_i) per non-empty
 //                     row into the slot; then signal `fwd_done`;
-//   scatter warps     each owns a private shared-memory accumulator of all
-//                     ncols gradient entries and scatters a_ij r_i for its share
-//                     of the stage's non-empty rows, one row at a time.
+//   scatter warps     each owns a private shared-memory accumulator of the
+//                     CTA's column window of the gradient and scatters a_ij r_i
+//                     for its share of the stage's non-empty rows, one row at a
+//                     time.
 // Determinism (Sec. II-D: no reductions whose order is not fixed, so no float
 // atomics): the entries of a row have distinct columns, so the lanes of a
 // scatter warp never update the same word in one instruction; each warp's rows
@@ -32,9 +33,10 @@ struct AdjParams {
     float scale;
     const float* x;   // QUADRATIC
     float* d;         // QUADRATIC, may be null
-    float* g_part;    // grid x ncols
+    float* g_part;    // grid x wwidth: CTA c's window of the gradient
     double* f_part;   // grid
     uint32_t nrows, ncols;
+    uint32_t wwidth;  // columns of each CTA's window [wlo, wlo + wwidth), wlo = sched.wlo[cta]
     ScheduleView sched;
     VecSet vecs;      // QUADRATIC: p, w [, row scale]; ADJOINT: r [, row scale]
     uint32_t tile_nnz, tile_rows, depth, fwarps, swarps, l2pf;
@@ -175,7 +177,7 @@ __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D,
 }
 
 template <int FMT, int MODE>
-__global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
+__global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const AdjParams p) {
     using T = typename Fmt<FMT>::T;
     constexpr bool QUAD = MODE == ADJ_MODE_QUADRATIC;
     constexpr uint32_t kRowScaleVec = QUAD ? 2 : 1;  // index of the FP8 row scales in vecs
@@ -190,10 +192,14 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     StageDesc* dwin = reinterpret_cast<StageDesc*>(smem + 1024);  // 2 x kDescWin descriptors
     float* red = reinterpret_cast<float*>(smem + 256);      // 32 floats: long-row partials
     double* fred = reinterpret_cast<double*>(smem + 512);   // 32 doubles: per-warp objective
-    const uint32_t gw_floats = round_up(p.ncols * 4, 128) / 4;
+    // This CTA's entries have columns in [wlo, wlo + wwidth): the accumulators
+    // and x hold that window, addressed by column through a base moved down by
+    // wlo words (shared addresses wrap mod 2^32, so base + 4 c lands in place).
+    const uint32_t wlo = p.sched.wlo[blockIdx.x];
+    const uint32_t gw_floats = round_up(p.wwidth * 4, 128) / 4;
     float* gacc = reinterpret_cast<float*>(smem + kAdjHeader);  // Ws x gw_floats
     float* xs = gacc + Ws * gw_floats;
-    const uint32_t x_bytes = QUAD ? round_up(p.ncols * 4, 128) : 0;
+    const uint32_t x_bytes = QUAD ? round_up(p.wwidth * 4, 128) : 0;
     unsigned char* slot_base = reinterpret_cast<unsigned char*>(xs) + x_bytes;
     const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, sizeof(T), p.vecs.n, QUAD);
 
@@ -223,10 +229,10 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     const uint32_t ctid = threadIdx.x - 32;
     for (uint32_t j = ctid; j < Ws * gw_floats; j += ncons) gacc[j] = 0.f;
     if (QUAD)
-        for (uint32_t j = ctid; j < p.ncols; j += ncons) xs[j] = __ldg(p.x + j);
+        for (uint32_t j = ctid; j < p.wwidth; j += ncons) xs[j] = wlo + j < p.ncols ? __ldg(p.x + wlo + j) : 0.f;
     dev::named_barrier(1, ncons);
 
-    const uint32_t xs_a = dev::smem_u32(xs);
+    const uint32_t xs_a = dev::smem_u32(xs) - 4 * wlo;
     const uint32_t slot0 = dev::smem_u32(slot_base);
     const bool is_fwd = QUAD && warp <= Wf;
     bool failed = false;
@@ -299,7 +305,7 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     } else {
         // ------------------------------------------------ scatter warps
         const uint32_t sw = warp - 1 - Wf;
-        const uint32_t gw = dev::smem_u32(gacc + sw * gw_floats);
+        const uint32_t gw = dev::smem_u32(gacc + sw * gw_floats) - 4 * wlo;
         uint32_t st = 0, ph = 0, first = sw;  // first list entry of this warp, rotating per stage
         for (uint32_t s = s_begin; s < s_end; ++s, first = first + 1 == Ws ? 0 : first + 1) {
             if (!dev::mbar_wait_bounded(&full[st], ph) || (QUAD && !dev::mbar_wait_bounded(&fwd_done[st], ph))) {
@@ -348,10 +354,10 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
         if (lane == 0) fred[warp - 1] = f_lane;
     }
     dev::named_barrier(1, ncons);
-    for (uint32_t j = ctid; j < p.ncols; j += ncons) {
+    for (uint32_t j = ctid; j < p.wwidth; j += ncons) {
         float t = gacc[j];
         for (uint32_t w2 = 1; w2 < Ws; ++w2) t = __fadd_rn(t, gacc[w2 * gw_floats + j]);
-        p.g_part[(size_t)blockIdx.x * p.ncols + j] = t;
+        p.g_part[(size_t)blockIdx.x * p.wwidth + j] = t;
     }
     if (ctid == 0) {
         double t = 0.0;
@@ -360,10 +366,12 @@ __global__ void __launch_bounds__(544, 1) adjoint_kernel(const AdjParams p) {
     }
 }
 
-// g_j = s * sum_c g_part[c][j] and f = sum_c f_part[c], both in a fixed order;
-// optional projected-gradient step on x.  Block: 256 threads = 8 warps x 32
-// columns; warp w sums the partials c = w, w + 8, ...; warp 0 adds the eight.
+// g_j = s * sum_c g_part[c][j - wlo_c] over the CTAs c whose window holds j,
+// and f = sum_c f_part[c], both in a fixed order; optional projected-gradient
+// step on x.  Block: 256 threads = 8 warps x 32 columns; warp w sums the
+// partials c = w, w + 8, ...; warp 0 adds the eight.
 __global__ void __launch_bounds__(256) adjoint_finalize(const float* __restrict__ g_part,
+                                                        const uint32_t* __restrict__ wlo, uint32_t wwidth,
                                                         const double* __restrict__ f_part, uint32_t nparts,
                                                         uint32_t ncols, float scale, float* g, double* f,
                                                         float* x_update, float eta) {
@@ -373,7 +381,10 @@ __global__ void __launch_bounds__(256) adjoint_finalize(const float* __restrict_
     const uint32_t j = blockIdx.x * 32 + lane;
     float t = 0.f;
     if (j < ncols)
-        for (uint32_t c = w; c < nparts; c += 8) t = __fadd_rn(t, g_part[(size_t)c * ncols + j]);
+        for (uint32_t c = w; c < nparts; c += 8) {
+            const uint32_t off = j - __ldg(wlo + c);
+            if (off < wwidth) t = __fadd_rn(t, g_part[(size_t)c * wwidth + off]);
+        }
     part[w][lane] = t;
     if (f && blockIdx.x == 0) {
         double ft = 0.0;
@@ -412,7 +423,7 @@ size_t adj_smem(const dose_matrix* A, const AdjTuning& t, bool quad, uint32_t ws
     const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
     const uint32_t nvec = (quad ? 2 : 1) + (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, quad);
-    const size_t col_bytes = round_up(A->ncols * 4, 128);
+    const size_t col_bytes = round_up(A->adj.wwidth * 4, 128);
     return kAdjHeader + ws * col_bytes + (quad ? col_bytes : 0) + (size_t)t.stages * SL.bytes;
 }
 
@@ -425,19 +436,15 @@ bool adjoint_shape(const dose_matrix* A, const AdjTuning& in, bool quad, AdjTuni
     while (fwq & (fwq - 1)) fwq &= fwq - 1;  // a power of two: 1, 2, 4 or 8
     t.forward_warps = quad ? fwq : 0;
     if (t.stages < 2 || t.stages > 8) return false;
-    const uint32_t max_ws = 16 - t.forward_warps;
+    // scatter warps: as many as fit (at most the requested number, if any)
+    uint32_t max_ws = kMaxAdjWarps - 1 - t.forward_warps;
+    if (in.scatter_warps && in.scatter_warps < max_ws) max_ws = in.scatter_warps;
     uint32_t ws = 0;
-    if (in.scatter_warps) {
-        ws = in.scatter_warps <= max_ws && adj_smem(A, t, quad, in.scatter_warps) <= kMaxSmemPerBlock
-                 ? in.scatter_warps
-                 : 0;
-    } else {
-        for (uint32_t w = max_ws; w >= 1; --w)
-            if (adj_smem(A, t, quad, w) <= kMaxSmemPerBlock) {
-                ws = w;
-                break;
-            }
-    }
+    for (uint32_t w = max_ws; w >= 1; --w)
+        if (adj_smem(A, t, quad, w) <= kMaxSmemPerBlock) {
+            ws = w;
+            break;
+        }
     if (ws == 0) return false;
     t.scatter_warps = ws;
     if (out) *out = t;
@@ -464,7 +471,8 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
         prm.f_part = A->f_part;
         prm.nrows = A->nrows;
         prm.ncols = A->ncols;
-        prm.sched = ScheduleView{A->adj.desc, A->adj.ne, A->adj.cta_begin};
+        prm.wwidth = A->adj.wwidth;
+        prm.sched = ScheduleView{A->adj.desc, A->adj.ne, A->adj.cta_begin, A->adj.wlo};
         const uint32_t user_lim = A->nrows & ~3u;  // caller arrays: whole 16-byte pieces only
         prm.vecs.n = 0;
         if (quad) {
@@ -510,8 +518,8 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
     const uint32_t nparts = A->nrows > 0 ? A->adj.grid : 0;
     const float scale = A->fmt == DOSE_FMT_U16_SCALE ? A->scale : 1.0f;
     const uint32_t blocks = A->ncols ? (A->ncols + 31) / 32 : 1;
-    adjoint_finalize<<<blocks, 256, 0, s>>>(A->g_part, A->f_part, nparts, A->ncols, scale, g, quad ? f : nullptr,
-                                            x_update, eta);
+    adjoint_finalize<<<blocks, 256, 0, s>>>(A->g_part, A->adj.wlo, A->adj.wwidth, A->f_part, nparts, A->ncols,
+                                            scale, g, quad ? f : nullptr, x_update, eta);
     return cudaGetLastError();
 }
 

@@ -127,7 +127,11 @@ static uint32_t nearest_pow2_log2(double v) {
     return (uint32_t)std::min(5, std::max(0, lg));
 }
 
-static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, const Tuning& t, uint32_t grid) {
+// Column windows: rcmin / rcmax give each row's lowest and highest column (null
+// for the forward schedule, which deals round-robin).  vbytes: stored bytes per
+// entry (value + column index), used to balance the CTAs' HBM traffic.
+static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, const Tuning& t, uint32_t grid,
+                               const uint32_t* rcmin, const uint32_t* rcmax, uint32_t ncols, uint32_t vbytes) {
     Schedule S;
     uint32_t r = 0;
     while (r < nrows) {
@@ -172,19 +176,89 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
         ++S.lanes_hist[lg];
     }
 
-    // Deal work items (a NORMAL stage, or the consecutive chunks of one long
-    // row) to the CTAs round-robin, in matrix order.
+    // Work items: a NORMAL stage, or the consecutive chunks of one long row.
     const uint32_t n = (uint32_t)S.desc.size();
-    std::vector<std::vector<uint32_t>> per(grid);
-    uint32_t item = 0;
+    struct Item {
+        uint32_t s, e;       // descriptors [s, e)
+        uint32_t lo, hi;     // column range (lo > hi: no entries)
+        uint64_t cost;       // HBM bytes (entries, row pointers, two per-row vectors)
+                             // + for the adjoint, a share per 128-entry step of each row
+    };
+    std::vector<Item> items;
     for (uint32_t s = 0; s < n;) {
         uint32_t e = s + 1;
         if (S.desc[s].meta & STAGE_COOP)
             while (e < n && (S.desc[e].meta & STAGE_COOP) && !(S.desc[e].meta & STAGE_FIRST)) ++e;
-        std::vector<uint32_t>& dst = per[item % grid];
-        for (uint32_t k = s; k < e; ++k) dst.push_back(k);
-        ++item;
+        Item it{s, e, 0xFFFFFFFFu, 0u, 0};
+        const uint32_t r0 = S.desc[s].row0, r1 = S.desc[e - 1].row1;
+        it.cost = (uint64_t)vbytes * (rp[r1] - rp[r0]) + 12ull * (r1 - r0);
+        if (rcmin)
+            for (uint32_t r = r0; r < r1; ++r)
+                if (rcmin[r] <= rcmax[r]) {
+                    it.lo = std::min(it.lo, rcmin[r]);
+                    it.hi = std::max(it.hi, rcmax[r]);
+                    // a scatter warp takes a row in steps of 128 entries, whatever its length
+                    it.cost += 512ull * ((rp[r + 1] - rp[r] + 2 + 127) / 128);
+                }
+        items.push_back(it);
         s = e;
+    }
+    std::vector<std::vector<uint32_t>> per(grid);
+    S.wlo.assign(grid, 0);
+    const uint32_t ncols_pad = (ncols + 31) / 32 * 32;
+    S.wwidth = ncols_pad;
+    if (!rcmin) {
+        // round-robin, in matrix order
+        for (size_t i = 0; i < items.size(); ++i)
+            for (uint32_t k = items[i].s; k < items[i].e; ++k) per[i % grid].push_back(k);
+    } else {
+        // Items with entries are sorted by lowest column and cut into G groups of
+        // equal estimated cost; group g is dealt round-robin, in matrix order, to
+        // its own grid/G CTAs.  A CTA's window then spans one group's columns
+        // (for a pencil beam: one lateral band plus the spot footprint), while
+        // round-robin inside the group mixes long and short rows as evenly as
+        // dealing over the whole matrix does.  Items without entries (blocks of
+        // empty rows: cheap in bytes, but each costs a ring round trip) are
+        // dealt round-robin over all CTAs.  Each CTA runs its items in matrix
+        // order, so the blocks in flight at any time lie close together in HBM.
+        std::vector<uint32_t> order, empties;
+        for (uint32_t i = 0; i < items.size(); ++i) (items[i].lo <= items[i].hi ? order : empties).push_back(i);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](uint32_t a, uint32_t b) { return items[a].lo < items[b].lo; });
+        uint64_t total = 0;
+        for (uint32_t i : order) total += items[i].cost;
+        const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(kAdjColumnGroups, grid));
+        std::vector<std::vector<uint32_t>> group(G);
+        uint64_t acc = 0;
+        uint32_t gi = 0;
+        for (uint32_t i : order) {
+            while (gi + 1 < G && acc * G >= total * (gi + 1)) ++gi;  // group gi holds its share
+            group[gi].push_back(i);
+            acc += items[i].cost;
+        }
+        std::vector<uint32_t> lo(grid, 0xFFFFFFFFu), hi(grid, 0);
+        std::vector<std::vector<uint32_t>> mine(grid);
+        for (uint32_t g = 0; g < G; ++g) {
+            const uint32_t c0 = (uint32_t)((uint64_t)grid * g / G), c1 = (uint32_t)((uint64_t)grid * (g + 1) / G);
+            std::sort(group[g].begin(), group[g].end());
+            for (size_t k = 0; k < group[g].size(); ++k) {
+                const uint32_t c = c0 + (uint32_t)(k % (c1 - c0)), i = group[g][k];
+                mine[c].push_back(i);
+                lo[c] = std::min(lo[c], items[i].lo);
+                hi[c] = std::max(hi[c], items[i].hi);
+            }
+        }
+        for (size_t k = 0; k < empties.size(); ++k) mine[k % grid].push_back(empties[k]);
+        for (uint32_t k = 0; k < grid; ++k) {
+            std::sort(mine[k].begin(), mine[k].end());
+            for (uint32_t i : mine[k])
+                for (uint32_t d = items[i].s; d < items[i].e; ++d) per[k].push_back(d);
+        }
+        uint32_t width = 0;
+        for (uint32_t k = 0; k < grid; ++k)
+            if (lo[k] <= hi[k]) width = std::max(width, hi[k] - lo[k] + 1);
+        S.wwidth = std::max<uint32_t>(32, std::min(ncols_pad, (width + 31) / 32 * 32));
+        for (uint32_t k = 0; k < grid; ++k) S.wlo[k] = lo[k] <= hi[k] ? lo[k] : 0;
     }
     // Store the descriptors CTA by CTA, so each CTA reads one contiguous range.
     std::vector<StageDesc> sorted;
@@ -205,9 +279,12 @@ static void free_dev_schedule(DevSchedule& D) {
     cudaFree(D.desc);
     cudaFree(D.ne);
     cudaFree(D.cta_begin);
+    cudaFree(D.wlo);
     D.desc = nullptr;
     D.ne = nullptr;
     D.cta_begin = nullptr;
+    D.wlo = nullptr;
+    D.wwidth = 0;
     D.n_stages = 0;
 }
 
@@ -236,12 +313,29 @@ static dose_status check_tuning(const dose_matrix* A, Tuning& t) {
     return DOSE_OK;
 }
 
+// Knobs the caller left at 0 shrink until the forward pipeline fits beside x:
+// first the tile (down to 1024 entries), then the depth (down to 2).
+static void fit_default_tuning(const dose_matrix* A, Tuning& t, const dose_tuning* in) {
+    const bool user_tile = in && in->tile_nnz, user_stages = in && in->stages;
+    while (spmv_smem_bytes(A, t, spmv_x_in_smem(A)) > kMaxSmemPerBlock) {
+        if (!user_tile && t.tile_nnz > 1024) {
+            t.tile_nnz /= 2;
+            if (!(in && in->coop_nnz)) t.coop_nnz = std::min(t.coop_nnz, t.tile_nnz);
+        } else if (!user_stages && t.stages > 2) {
+            --t.stages;
+        } else {
+            break;
+        }
+    }
+}
+
 static dose_status check_adj_tuning(const AdjTuning& t) {
     if (t.tile_nnz < 256 || t.tile_nnz > 16384) return invalid("tuning.adj_tile_nnz must be in [256, 16384]");
     if (t.tile_rows < 32 || t.tile_rows > 8192) return invalid("tuning.adj_tile_rows must be in [32, 8192]");
     if (t.stages < 2 || t.stages > 8) return invalid("tuning.adj_stages must be in [2, 8]");
     if (t.forward_warps < 1 || t.forward_warps > 15) return invalid("tuning.adj_forward_warps must be in [1, 15]");
-    if (t.scatter_warps > 15) return invalid("tuning.adj_scatter_warps must be in [0, 15]");
+    if (t.scatter_warps > kMaxAdjWarps - 2)
+        return invalid("tuning.adj_scatter_warps must be in [0, " + std::to_string(kMaxAdjWarps - 2) + "]");
     return DOSE_OK;
 }
 
@@ -288,15 +382,21 @@ static cudaError_t upload(T** dst, const T* src, size_t n, size_t alloc_n) {
     return e;
 }
 
-// Build one schedule on the host and replace `D` with its device copy.
-static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& t) {
-    Schedule S = build_schedule(A->host_row_ptr, A->nrows, t, D.grid);
+// Build one schedule on the host and replace `D` with its device copy.  The
+// adjoint schedule (`windowed`) gets per-CTA column windows.
+static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& t, bool windowed = false) {
+    const bool win = windowed && !A->host_row_cmin.empty();
+    const uint32_t vbytes = (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2) + 4;
+    Schedule S = build_schedule(A->host_row_ptr, A->nrows, t, D.grid, win ? A->host_row_cmin.data() : nullptr,
+                                win ? A->host_row_cmax.data() : nullptr, A->ncols, vbytes);
     free_dev_schedule(D);
     cudaError_t e;
     if ((e = upload(&D.desc, S.desc.data(), S.desc.size(), S.desc.size() + 1)) != cudaSuccess ||
         (e = upload(&D.ne, S.ne.data(), S.ne.size(), (S.ne.size() + 7) / 8 * 8 + 16)) != cudaSuccess ||
-        (e = upload(&D.cta_begin, S.cta_begin.data(), S.cta_begin.size(), S.cta_begin.size())) != cudaSuccess)
+        (e = upload(&D.cta_begin, S.cta_begin.data(), S.cta_begin.size(), S.cta_begin.size())) != cudaSuccess ||
+        (e = upload(&D.wlo, S.wlo.data(), S.wlo.size(), S.wlo.size())) != cudaSuccess)
         return cuda_fail(e, "uploading the schedule");
+    D.wwidth = S.wwidth;
     D.n_stages = (uint32_t)S.desc.size();
     D.n_coop_rows = S.n_coop_rows;
     std::memcpy(D.lanes_hist, S.lanes_hist, sizeof(D.lanes_hist));
@@ -315,7 +415,7 @@ static Tuning adj_schedule_tuning(const Tuning& fwd, const AdjTuning& a) {
 }
 
 static uint64_t schedule_bytes(const DevSchedule& D) {
-    return (uint64_t)(D.n_stages + 1) * sizeof(StageDesc) + (D.grid + 1) * 4;
+    return (uint64_t)(D.n_stages + 1) * sizeof(StageDesc) + (D.grid + 1) * 4 + D.grid * 4;
 }
 
 static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
@@ -398,9 +498,11 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
         if (rp[i + 1] < rp[i]) return invalid("row_ptr must be non-decreasing (row " + std::to_string(i) + ")");
         max_len = std::max(max_len, rp[i + 1] - rp[i]);
     }
+    std::vector<uint32_t> rcmin(nrows, 0xFFFFFFFFu), rcmax(nrows, 0);
     {
         std::vector<uint32_t> stamp(ncols, 0xFFFFFFFFu);
         for (uint32_t i = 0; i < nrows; ++i) {
+            uint32_t lo = 0xFFFFFFFFu, hi = 0;
             for (uint32_t k = rp[i]; k < rp[i + 1]; ++k) {
                 const uint32_t c = col[k];
                 if (c >= ncols)
@@ -408,7 +510,11 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
                 if (stamp[c] == i)
                     return invalid("duplicate column " + std::to_string(c) + " in row " + std::to_string(i));
                 stamp[c] = i;
+                lo = std::min(lo, c);
+                hi = std::max(hi, c);
             }
+            rcmin[i] = lo;
+            rcmax[i] = hi;
         }
     }
     // Values: encode FP64 on the host, or take the given codes.
@@ -454,9 +560,12 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
         return cuda_fail(e, "cudaDeviceGetAttribute");
     A->fwd.grid = A->adj.grid = (uint32_t)std::max(1, A->sm_count);
     A->host_row_ptr = std::move(rp);
+    A->host_row_cmin = std::move(rcmin);
+    A->host_row_cmax = std::move(rcmax);
     Tuning t;
     AdjTuning at;
     merge_tuning(t, at, tuning);
+    fit_default_tuning(A.get(), t, tuning);
     {
         dose_status st = check_tuning(A.get(), t);
         if (st == DOSE_OK) st = check_adj_tuning(at);
@@ -480,14 +589,15 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE &&
         (e = upload(&A->row_scale, scl.data(), (size_t)nrows, (size_t)nrows + 16)) != cudaSuccess)
         return fail(e, "row scales");
-    if ((e = cudaMalloc(&A->g_part, std::max<size_t>((size_t)A->adj.grid * ncols, 1) * 4)) != cudaSuccess)
+    const size_t ncols_pad = ((size_t)ncols + 31) / 32 * 32;  // a CTA's window is at most this wide
+    if ((e = cudaMalloc(&A->g_part, std::max<size_t>((size_t)A->adj.grid * ncols_pad, 1) * 4)) != cudaSuccess)
         return fail(e, "adjoint partials");
     if ((e = cudaMalloc(&A->f_part, (size_t)A->adj.grid * 8)) != cudaSuccess) return fail(e, "objective partials");
     if ((e = cudaMalloc(&A->err, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     if ((e = cudaMemset(A->err, 0, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     {
         dose_status st = apply_schedule(A.get(), A->fwd, t);
-        if (st == DOSE_OK) st = apply_schedule(A.get(), A->adj, adj_schedule_tuning(t, at));
+        if (st == DOSE_OK) st = apply_schedule(A.get(), A->adj, adj_schedule_tuning(t, at), true);
         if (st != DOSE_OK) {
             free_all(A.get());
             return st;
@@ -495,7 +605,7 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     }
     A->device_bytes = rp_alloc * 4 + col_alloc * 4 + val_alloc +
                       (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) +
-                      (size_t)A->adj.grid * ncols * 4 + (size_t)A->adj.grid * 8 + 4 + schedule_bytes(A->fwd) +
+                      (size_t)A->adj.grid * ncols_pad * 4 + (size_t)A->adj.grid * 8 + 4 + schedule_bytes(A->fwd) +
                       schedule_bytes(A->adj);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "create");
     *out = A.release();
@@ -519,12 +629,14 @@ dose_status dose_spmv(const dose_matrix* A, const float* x, float* d, void* stre
 }
 
 static dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* const* vecs, int nvec) {
-    if (quad && A->ncols > kXSmemMaxCols) {
-        set_error("the fused objective pass keeps x in shared memory: ncols must be <= 16384");
+    if (quad && A->adj.wwidth > kXSmemMaxCols) {
+        set_error("the fused objective pass keeps each CTA's window of x in shared memory: the column window (" +
+                  std::to_string(A->adj.wwidth) + ") must be <= 16384");
         return DOSE_ERR_UNSUPPORTED;
     }
     if (!adjoint_shape(A, A->adj_tuning, quad, nullptr, nullptr)) {
-        set_error("per-warp gradient accumulators of ncols floats do not fit in shared memory");
+        set_error("per-warp gradient accumulators of the column window (" + std::to_string(A->adj.wwidth) +
+                  " floats) do not fit in shared memory");
         return DOSE_ERR_UNSUPPORTED;
     }
     for (int k = 0; k < nvec; ++k)
@@ -604,9 +716,10 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     out->block = 32 * (A->fwd.tuning.consumer_warps + 1);
     out->adj_n_stages = A->adj.n_stages;
     AdjTuning sh;
-    if (adjoint_shape(A, A->adj_tuning, true, &sh, nullptr) && A->ncols <= kXSmemMaxCols)
+    if (adjoint_shape(A, A->adj_tuning, true, &sh, nullptr) && A->adj.wwidth <= kXSmemMaxCols)
         out->adj_block_fused = 32 * (1 + sh.forward_warps + sh.scatter_warps);
     if (adjoint_shape(A, A->adj_tuning, false, &sh, nullptr)) out->adj_block_adjoint = 32 * (1 + sh.scatter_warps);
+    out->adj_window = A->adj.wwidth;
     out->max_row_len = A->max_row_len;
     out->device_bytes = A->device_bytes;
     const uint64_t vb = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
@@ -634,7 +747,7 @@ dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning) {
     st = apply_schedule(A, A->fwd, t);
     if (st != DOSE_OK) return st;
     A->adj_tuning = at;
-    return apply_schedule(A, A->adj, adj_schedule_tuning(t, at));
+    return apply_schedule(A, A->adj, adj_schedule_tuning(t, at), true);
 }
 
 dose_status dose_device_status(const dose_matrix* A, void* stream) {
@@ -713,42 +826,46 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
     // 2. fused objective pass: adjoint tile sizes, depth, forward warps (scatter warps: all that fit)
     const AdjTuning orig_a = A->adj_tuning;
     AdjTuning best_a = orig_a;
-    if (result == DOSE_OK && A->ncols <= kXSmemMaxCols) {
+    if (result == DOSE_OK) {
         float best_a_ms = 1e30f;
         const uint32_t anz[] = {2048, 4096, 8192};
         const uint32_t arows[] = {512, 1024, 2048};
         const uint32_t adepth[] = {2, 3, 4, 6};
         const uint32_t afw[] = {4, 8};
-        const uint32_t asw[] = {3, 4, 6, 0};
+        const uint32_t asw[] = {4, 8, 12, 0};
         for (uint32_t tn : anz)
-            for (uint32_t tr : arows)
+            for (uint32_t tr : arows) {
+                // the schedule (and so the column window) depends on the tile sizes only
+                AdjTuning a = orig_a;
+                a.tile_nnz = tn;
+                a.tile_rows = tr;
+                A->adj_tuning = a;
+                if (apply_schedule(A, A->adj, adj_schedule_tuning(A->fwd.tuning, a), true) != DOSE_OK) continue;
+                if (A->adj.wwidth > kXSmemMaxCols) continue;
                 for (uint32_t sd : adepth)
                     for (uint32_t fw : afw)
                         for (uint32_t sw : asw) {
-                        AdjTuning a = orig_a;
-                        a.tile_nnz = tn;
-                        a.tile_rows = tr;
-                        a.stages = sd;
-                        a.forward_warps = fw;
-                        a.scatter_warps = sw;
-                        if (!adjoint_shape(A, a, true, nullptr, nullptr)) continue;
-                        A->adj_tuning = a;
-                        if (apply_schedule(A, A->adj, adj_schedule_tuning(A->fwd.tuning, a)) != DOSE_OK) continue;
-                        const float ms = time_launches(s, e0, e1, reps, [&] {
-                            return launch_adjoint(A, ADJ_MODE_QUADRATIC, x, pw, pw + nrp, nullptr, nullptr, f, g,
-                                                  nullptr, 0.f, s);
-                        });
-                        if (ms < 0.f) {
-                            result = cuda_fail(cudaGetLastError(), "dose_autotune fused timing");
-                            break;
+                            a.stages = sd;
+                            a.forward_warps = fw;
+                            a.scatter_warps = sw;
+                            if (!adjoint_shape(A, a, true, nullptr, nullptr)) continue;
+                            A->adj_tuning = a;
+                            const float ms = time_launches(s, e0, e1, reps, [&] {
+                                return launch_adjoint(A, ADJ_MODE_QUADRATIC, x, pw, pw + nrp, nullptr, nullptr, f, g,
+                                                      nullptr, 0.f, s);
+                            });
+                            if (ms < 0.f) {
+                                result = cuda_fail(cudaGetLastError(), "dose_autotune fused timing");
+                                break;
+                            }
+                            if (ms < best_a_ms) {
+                                best_a_ms = ms;
+                                best_a = a;
+                            }
                         }
-                        if (ms < best_a_ms) {
-                            best_a_ms = ms;
-                            best_a = a;
-                        }
-                    }
+            }
         A->adj_tuning = best_a;
-        dose_status st = apply_schedule(A, A->adj, adj_schedule_tuning(A->fwd.tuning, best_a));
+        dose_status st = apply_schedule(A, A->adj, adj_schedule_tuning(A->fwd.tuning, best_a), true);
         if (result == DOSE_OK) result = st;
     }
     cudaEventDestroy(e0);

@@ -26,10 +26,17 @@ namespace dose {
 //   COOP stage:   one chunk (<= tile_nnz entries) of one row longer than
 //                 coop_nnz; all consumer warps reduce it together.  A row of
 //                 several chunks occupies consecutive stages FIRST..LAST.
-// Work items (a NORMAL stage, or all chunks of one long row) are dealt to the
-// CTAs round-robin, so every CTA gets a similar mix of empty and dense row
-// blocks; the assignment is static, so every reduction order is fixed at
-// create time.
+// Work items (a NORMAL stage, or all chunks of one long row) are assigned to
+// CTAs statically, so every reduction order is fixed at create time:
+//   forward schedule: dealt round-robin in matrix order, so every CTA gets a
+//                     similar mix of empty and dense row blocks;
+//   adjoint schedule: sorted by their lowest column, cut into a few groups of
+//                     equal estimated cost, each dealt round-robin to its own
+//                     share of the CTAs.  Each CTA then touches a narrow column
+//                     window [wlo, wlo + wwidth) (a pencil beam's row block sees
+//                     only the spots near its voxels), so its per-warp gradient
+//                     accumulators and its copy of x hold wwidth columns instead
+//                     of ncols, and more warps fit.
 enum : uint32_t {
     STAGE_LANES_MASK = 0x7u,  // log2 of lanes per row (0..5)
     STAGE_COOP = 0x8u,
@@ -47,19 +54,21 @@ struct StageDesc {
 };
 
 struct Tuning {
-    uint32_t tile_nnz = 4096;
+    uint32_t tile_nnz = 8192;
     uint32_t tile_rows = 2048;
     uint32_t coop_nnz = 1024;
-    uint32_t lane_target = 12;  // entries per lane: 4 per unrolled step, about 3 steps
-    uint32_t stages = 4;
+    uint32_t lane_target = 24;  // entries per lane: 4 per unrolled step, about 6 steps
+    uint32_t stages = 3;
     uint32_t consumer_warps = 16;
-    uint32_t l2_prefetch = 0;   // stages prefetched into L2 ahead of the shared-memory ring
+    uint32_t l2_prefetch = 2;   // stages prefetched into L2 ahead of the shared-memory ring
 };
 
 struct Schedule {
     std::vector<StageDesc> desc;      // n_stages, stored CTA by CTA
     std::vector<uint16_t> ne;         // non-empty rows of NORMAL stages (offset from row0)
     std::vector<uint32_t> cta_begin;  // grid + 1: CTA c runs desc[cta_begin[c] .. cta_begin[c+1])
+    std::vector<uint32_t> wlo;        // grid: first column of each CTA's window (adjoint schedule)
+    uint32_t wwidth = 0;              // window width in columns, a multiple of 32
     uint32_t n_coop_rows = 0;
     uint32_t lanes_hist[6] = {0, 0, 0, 0, 0, 0};
 };
@@ -69,6 +78,8 @@ struct DevSchedule {
     StageDesc* desc = nullptr;
     uint16_t* ne = nullptr;
     uint32_t* cta_begin = nullptr;
+    uint32_t* wlo = nullptr;
+    uint32_t wwidth = 0;
     uint32_t n_stages = 0;
     uint32_t grid = 0;
     uint32_t n_coop_rows = 0;
@@ -81,15 +92,16 @@ struct ScheduleView {
     const StageDesc* desc;
     const uint16_t* ne;
     const uint32_t* cta_begin;
+    const uint32_t* wlo;  // adjoint schedule only (else null)
 };
 
 // Shape of the adjoint / fused kernels (warp specialisation and pipeline).
 struct AdjTuning {
-    uint32_t tile_nnz = 2048;
-    uint32_t tile_rows = 1024;
-    uint32_t stages = 3;
+    uint32_t tile_nnz = 4096;
+    uint32_t tile_rows = 512;
+    uint32_t stages = 4;
     uint32_t forward_warps = 8;   // fused pass: warps computing d, f and r
-    uint32_t scatter_warps = 0;   // warps owning gradient accumulators (0 = as many as fit)
+    uint32_t scatter_warps = 0;   // warps owning gradient accumulators (0 = as many as fit, up to the cap)
     uint32_t l2_prefetch = 8;     // stages prefetched into L2 ahead of the shared-memory ring
 };
 
@@ -122,6 +134,8 @@ struct dose_matrix {
     int* err = nullptr;  // device error word (0 = ok)
     uint64_t device_bytes = 0;
     std::vector<uint32_t> host_row_ptr;  // kept for re-scheduling
+    std::vector<uint32_t> host_row_cmin;  // lowest / highest column of each row (empty rows:
+    std::vector<uint32_t> host_row_cmax;  // cmin > cmax), for the adjoint's column windows
 };
 
 namespace dose {
@@ -143,6 +157,8 @@ cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const fl
                                 float* const* D, int nvec, cudaStream_t s, std::string* why);
 
 constexpr uint32_t kMaxSmemPerBlock = 227 * 1024;
+constexpr uint32_t kMaxAdjWarps = 24;      // producer + forward + scatter warps of the adjoint kernels
+constexpr uint32_t kAdjColumnGroups = 16;  // column groups of the adjoint schedule (CTAs per group: grid / 16)
 constexpr uint32_t kXSmemMaxCols = 16384;  // x staged in shared memory up to 64 KB
 constexpr uint32_t kCompThreshold = 128;   // compensated accumulation above this row length
 constexpr int ADJ_MODE_ADJOINT = 0;   // g = A^T r

@@ -272,7 +272,7 @@ cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStre
     p.d = d;
     p.nrows = A->nrows;
     p.ncols = A->ncols;
-    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin};
+    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin, nullptr};
     p.vecs.n = 0;
     if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {  // library-owned, padded: every row can be copied
         p.vecs.n = 1;
