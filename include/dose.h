@@ -107,9 +107,9 @@ typedef struct {
     uint32_t adj_tile_rows;     /* (32..8192) */
     uint32_t adj_stages;        /* (2..8) */
     uint32_t adj_forward_warps; /* warps computing d, f, r in the fused pass (1..15) */
-    uint32_t adj_scatter_warps; /* warps owning gradient accumulators (0..22): at most this many,
+    uint32_t adj_scatter_warps; /* warps owning gradient accumulators (0..18): at most this many,
                                    fewer if their accumulators do not fit (0 = as many as fit;
-                                   never more than 23 - forward warps) */
+                                   never more than 19 - forward warps) */
     uint32_t adj_l2_prefetch;   /* as l2_prefetch, for these passes (32 = off) */
 } dose_tuning;
 

@@ -78,9 +78,6 @@ __device__ __forceinline__ void scatter_entries(uint32_t gw, const SlotView& v, 
     }
 }
 
-// Forward part of the fused pass for the non-empty rows of a NORMAL stage,
-// 2^LG lanes per row: d, the objective terms, and r_i = 2 w_i (d_i - p_i) (FP8:
-// times the row scale) into the slot's r list.
 // Scatter of a NORMAL stage's non-empty rows i = first, first + Ws, ... by one
 // warp, software-pipelined: the next row's list entry, row pointers and r are
 // loaded while the current row's accumulator updates are in flight.  Rows are
@@ -109,38 +106,38 @@ __device__ __forceinline__ void scatter_rows(uint32_t gw, const SlotView& v, uin
     uint32_t kb, ke;
     float rj;
     meta(i, kb, ke, rj);
-    while (true) {
-        const uint32_t kbeg = kb, kend = ke;
+    bool more;
+    do {
+        // this row: lane l takes the groups at (kb & ~3) + 4 l + 128 s
+        const int len = (int)(ke - kb);
+        int off = (int)(4 * lane) - (int)(kb & 3u);
+        const uint32_t k0 = (kb & ~3u) + 4 * lane;
+        uint32_t ca = v.col + 4 * k0, va = v.val + ES * k0;
+        const uint32_t steps = (uint32_t)(len + (int)(kb & 3u) + 127) >> 7;  // the same for every lane
         const float r = rj;
-        // next row's metadata is fetched during this row's first chunk
-        bool more = false;
-        uint32_t k = (kbeg & ~3u) + 4 * lane;
-        for (bool first = true; first || (k - 4 * lane) < kend; first = false, k += 128) {
-            // four consecutive entries per lane: one 16-byte column load, one value load
-            const bool in = k < kend;
-            const uint4 c = dev::lds_v4_if(in, v.col + 4 * k);
-            float a[4];
-            Fmt<FMT>::lds4(in, v.val + ES * k, a);
-            const bool m0 = in && k >= kbeg, m1 = in && k + 1 >= kbeg && k + 1 < kend;
-            const bool m2 = in && k + 2 >= kbeg && k + 2 < kend, m3 = in && k + 3 >= kbeg && k + 3 < kend;
-            if (first) {
-                i += Ws;
-                more = i < n_ne;
-                if (more) meta(i, kb, ke, rj);
-            }
-            const uint32_t g0 = gw + 4 * c.x, g1 = gw + 4 * c.y, g2 = gw + 4 * c.z, g3 = gw + 4 * c.w;
-            const float v0 = dev::lds_f32_if(m0, g0), v1 = dev::lds_f32_if(m1, g1);
-            const float v2 = dev::lds_f32_if(m2, g2), v3 = dev::lds_f32_if(m3, g3);
-            dev::sts_f32_if(m0, g0, __fmaf_rn(a[0], r, v0));
-            dev::sts_f32_if(m1, g1, __fmaf_rn(a[1], r, v1));
-            dev::sts_f32_if(m2, g2, __fmaf_rn(a[2], r, v2));
-            dev::sts_f32_if(m3, g3, __fmaf_rn(a[3], r, v3));
+        uint32_t c[4];
+        float a[4];
+        load_group<FMT>(off, len, ca, va, c, a);
+        // the next row's metadata is fetched while this row's first step is in flight
+        i += Ws;
+        more = i < n_ne;
+        if (more) meta(i, kb, ke, rj);
+        scatter_group(off, len, gw, c, a, r);
+#pragma unroll 1
+        for (uint32_t s = 1; s < steps; ++s) {
+            off += 128;
+            ca += 512;
+            va += 128 * ES;
+            load_group<FMT>(off, len, ca, va, c, a);
+            scatter_group(off, len, gw, c, a, r);
         }
         __syncwarp();  // all lanes' updates of this row precede the next row's loads
-        if (!more) break;
-    }
+    } while (more);
 }
 
+// Forward part of the fused pass for the non-empty rows of a NORMAL stage,
+// 2^LG lanes per row: d, the objective terms, and r_i = 2 w_i (d_i - p_i) (FP8:
+// times the row scale) into the slot's r list.
 template <int FMT, uint32_t LG, uint32_t kRowScaleVec>
 __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D, const SlotView& v, uint32_t slot,
                                          const SlotLayout& SL, uint32_t xs_a, uint32_t ftid, uint32_t lane,

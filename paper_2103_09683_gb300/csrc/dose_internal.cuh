@@ -157,7 +157,7 @@ cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const fl
                                 float* const* D, int nvec, cudaStream_t s, std::string* why);
 
 constexpr uint32_t kMaxSmemPerBlock = 227 * 1024;
-constexpr uint32_t kMaxAdjWarps = 24;      // producer + forward + scatter warps of the adjoint kernels
+constexpr uint32_t kMaxAdjWarps = 20;      // producer + forward + scatter warps of the adjoint kernels
 constexpr uint32_t kAdjColumnGroups = 16;  // column groups of the adjoint schedule (CTAs per group: grid / 16)
 constexpr uint32_t kXSmemMaxCols = 16384;  // x staged in shared memory up to 64 KB
 constexpr uint32_t kCompThreshold = 128;   // compensated accumulation above this row length
@@ -359,6 +359,12 @@ __device__ __forceinline__ float dec_u16(uint16_t q) { return static_cast<float>
 
 __device__ __forceinline__ float dec_bf16(uint16_t b) {
     return __uint_as_float(static_cast<uint32_t>(b) << 16);
+}
+
+__device__ __forceinline__ float f16_to_f32(uint16_t h) {
+    float f;
+    asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));
+    return f;
 }
 
 // OCP E4M3 -> FP32 through the hardware E4M3x2 -> F16x2 conversion (exact:

@@ -26,6 +26,13 @@ struct Fmt<DOSE_FMT_U16_SCALE> {
         w[2] = (float)(q.y & 0xFFFFu);
         w[3] = (float)(q.y >> 16);
     }
+    // four stored entries packed in q0 (entries 0, 1) and q1 (2, 3), decoded
+    __device__ static void dec4(uint32_t q0, uint32_t q1, float (&w)[4]) {
+        w[0] = (float)(q0 & 0xFFFFu);
+        w[1] = (float)(q0 >> 16);
+        w[2] = (float)(q1 & 0xFFFFu);
+        w[3] = (float)(q1 >> 16);
+    }
 #endif
 };
 template <>
@@ -45,6 +52,12 @@ struct Fmt<DOSE_FMT_BF16> {
         w[2] = __uint_as_float(q.y << 16);
         w[3] = __uint_as_float(q.y & 0xFFFF0000u);
     }
+    __device__ static void dec4(uint32_t q0, uint32_t q1, float (&w)[4]) {
+        w[0] = __uint_as_float(q0 << 16);
+        w[1] = __uint_as_float(q0 & 0xFFFF0000u);
+        w[2] = __uint_as_float(q1 << 16);
+        w[3] = __uint_as_float(q1 & 0xFFFF0000u);
+    }
 #endif
 };
 template <>
@@ -63,6 +76,16 @@ struct Fmt<DOSE_FMT_FP8E4M3_ROWSCALE> {
         w[1] = dev::dec_e4m3((uint8_t)((q >> 8) & 0xFF));
         w[2] = dev::dec_e4m3((uint8_t)((q >> 16) & 0xFF));
         w[3] = dev::dec_e4m3((uint8_t)(q >> 24));
+    }
+    // four codes in the bytes of q0 (q1 unused): two E4M3x2 -> F16x2 conversions
+    __device__ static void dec4(uint32_t q0, uint32_t, float (&w)[4]) {
+        uint32_t h01, h23;
+        asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h01) : "h"(static_cast<uint16_t>(q0 & 0xFFFFu)));
+        asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h23) : "h"(static_cast<uint16_t>(q0 >> 16)));
+        w[0] = dev::f16_to_f32(static_cast<uint16_t>(h01 & 0xFFFFu));
+        w[1] = dev::f16_to_f32(static_cast<uint16_t>(h01 >> 16));
+        w[2] = dev::f16_to_f32(static_cast<uint16_t>(h23 & 0xFFFFu));
+        w[3] = dev::f16_to_f32(static_cast<uint16_t>(h23 >> 16));
     }
 #endif
 };
@@ -335,6 +358,89 @@ __device__ __forceinline__ float dot_uniform(const SlotView& v, uint32_t xs, uin
         va += 4 * ES * STEP;
     }
     return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
+}
+
+// ---- one step over a group of four consecutive entries of a row
+//
+// A lane's group holds the entries at positions off .. off + 3 of a row of len
+// entries (positions counted from the row's first entry; a row's first group
+// starts at the 4-aligned entry at or below it, so off may be -1..-3 there).
+// An entry takes part iff 0 <= position < len, tested as one unsigned compare;
+// that predicate guards its gather, its FMA and (scatter) its store, so no
+// loaded value needs a default and masked entries cost no select.
+
+// Column indices (one 16-byte load) and stored values (8 bytes, or 4 for FP8)
+// of the group at shared addresses ca / va, loaded only if the group reaches
+// into the row (off < len), decoded to FP32.  Registers of a group that is not
+// loaded hold unspecified values that no guarded access ever uses.
+template <int FMT>
+__device__ __forceinline__ void load_group(int off, int len, uint32_t ca, uint32_t va, uint32_t (&c)[4],
+                                           float (&a)[4]) {
+    uint32_t q0, q1 = 0;
+    if (sizeof(typename Fmt<FMT>::T) == 2) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.lt.s32 p, %6, %7;\n\t"
+            "@p ld.shared.v4.u32 {%0, %1, %2, %3}, [%8];\n\t"
+            "@p ld.shared.v2.u32 {%4, %5}, [%9];\n\t}"
+            : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(q0), "=r"(q1)
+            : "r"(off), "r"(len), "r"(ca), "r"(va));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.lt.s32 p, %5, %6;\n\t"
+            "@p ld.shared.v4.u32 {%0, %1, %2, %3}, [%7];\n\t"
+            "@p ld.shared.u32 %4, [%8];\n\t}"
+            : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(q0)
+            : "r"(off), "r"(len), "r"(ca), "r"(va));
+    }
+    Fmt<FMT>::dec4(q0, q1, a);
+}
+
+// acc[u] += a[u] * x[c[u]] for the group's entries inside the row; x at shared
+// address xs + 4 * column.
+__device__ __forceinline__ void dot_group(int off, int len, uint32_t xs, const uint32_t (&c)[4], const float (&a)[4],
+                                          float (&acc)[4]) {
+    asm volatile(
+        "{\n\t.reg .pred p0, p1, p2, p3;\n\t.reg .b32 t1, t2, t3, g0, g1, g2, g3;\n\t"
+        ".reg .f32 x0, x1, x2, x3;\n\t"
+        "setp.lt.u32 p0, %4, %5;\n\t"
+        "add.s32 t1, %4, 1;\n\tsetp.lt.u32 p1, t1, %5;\n\t"
+        "add.s32 t2, %4, 2;\n\tsetp.lt.u32 p2, t2, %5;\n\t"
+        "add.s32 t3, %4, 3;\n\tsetp.lt.u32 p3, t3, %5;\n\t"
+        "mad.lo.u32 g0, %7, 4, %6;\n\tmad.lo.u32 g1, %8, 4, %6;\n\t"
+        "mad.lo.u32 g2, %9, 4, %6;\n\tmad.lo.u32 g3, %10, 4, %6;\n\t"
+        "@p0 ld.shared.f32 x0, [g0];\n\t@p1 ld.shared.f32 x1, [g1];\n\t"
+        "@p2 ld.shared.f32 x2, [g2];\n\t@p3 ld.shared.f32 x3, [g3];\n\t"
+        "@p0 fma.rn.f32 %0, %11, x0, %0;\n\t@p1 fma.rn.f32 %1, %12, x1, %1;\n\t"
+        "@p2 fma.rn.f32 %2, %13, x2, %2;\n\t@p3 fma.rn.f32 %3, %14, x3, %3;\n\t}"
+        : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3])
+        : "r"(off), "r"(len), "r"(xs), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "f"(a[0]), "f"(a[1]),
+          "f"(a[2]), "f"(a[3]));
+}
+
+// g[c[u]] += a[u] * r for the group's entries inside the row; g at shared
+// address gw + 4 * column.  The columns of a row are distinct, so the four
+// loads may precede the four stores, and no two lanes of the warp touch one
+// word.
+__device__ __forceinline__ void scatter_group(int off, int len, uint32_t gw, const uint32_t (&c)[4],
+                                              const float (&a)[4], float r) {
+    asm volatile(
+        "{\n\t.reg .pred p0, p1, p2, p3;\n\t.reg .b32 t1, t2, t3, g0, g1, g2, g3;\n\t"
+        ".reg .f32 v0, v1, v2, v3;\n\t"
+        "setp.lt.u32 p0, %0, %1;\n\t"
+        "add.s32 t1, %0, 1;\n\tsetp.lt.u32 p1, t1, %1;\n\t"
+        "add.s32 t2, %0, 2;\n\tsetp.lt.u32 p2, t2, %1;\n\t"
+        "add.s32 t3, %0, 3;\n\tsetp.lt.u32 p3, t3, %1;\n\t"
+        "mad.lo.u32 g0, %3, 4, %2;\n\tmad.lo.u32 g1, %4, 4, %2;\n\t"
+        "mad.lo.u32 g2, %5, 4, %2;\n\tmad.lo.u32 g3, %6, 4, %2;\n\t"
+        "@p0 ld.shared.f32 v0, [g0];\n\t@p1 ld.shared.f32 v1, [g1];\n\t"
+        "@p2 ld.shared.f32 v2, [g2];\n\t@p3 ld.shared.f32 v3, [g3];\n\t"
+        "@p0 fma.rn.f32 v0, %7, %11, v0;\n\t@p1 fma.rn.f32 v1, %8, %11, v1;\n\t"
+        "@p2 fma.rn.f32 v2, %9, %11, v2;\n\t@p3 fma.rn.f32 v3, %10, %11, v3;\n\t"
+        "@p0 st.shared.f32 [g0], v0;\n\t@p1 st.shared.f32 [g1], v1;\n\t"
+        "@p2 st.shared.f32 [g2], v2;\n\t@p3 st.shared.f32 [g3], v3;\n\t}"
+        ::"r"(off), "r"(len), "r"(gw), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "f"(a[0]), "f"(a[1]),
+          "f"(a[2]), "f"(a[3]), "f"(r)
+        : "memory");
 }
 
 // Vectorised form: lane li of an L-lane group takes the aligned chunks of four
