@@ -130,41 +130,55 @@ struct VecSet {
 
 constexpr uint32_t kDescWin = 32;  // stage descriptors per shared-memory window (1 KB)
 
+// State of a producer thread's ring, carried across the matrices of a batch:
+// the next slot and its phase, the stages issued so far, and the descriptor
+// windows completed on dbar[0..1] (window g of the whole run uses buffer and
+// barrier g & 1, phase (g >> 1) & 1).
+struct ProducerRing {
+    uint32_t st = 0, ph = 0, issued = 0, wbase = 0;
+    bool ok = true;
+};
+
 // Producer loop (one thread): for each stage of [s_begin, s_end) wait until its
 // ring slot is free, copy the stage descriptor into the slot header, then
 // bulk-copy the row_ptr / non-empty-list / value / column / vector slices and
 // let the slot's `full` barrier count the bytes.  The CTA's descriptors are
 // contiguous in global memory and arrive in double-buffered windows of 32
 // (`dwin`, completion on `dbar[2]`), so the loop never waits on a global load.
-// Before returning, wait until every copy it issued has landed, so the CTA
-// never exits with copies into its shared memory in flight.  All waits are
-// bounded.
+// Slots are `slot_stride` bytes apart (at least SL.bytes).  All waits are
+// bounded; a timeout sets the error word and clears R.ok.
 template <int FMT>
-__device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32_t s_end,
-                             const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
-                             const void* __restrict__ val, const VecSet& vecs, unsigned char* slot_base,
-                             const SlotLayout& SL, uint64_t* full, uint64_t* empty, uint32_t S, StageDesc* dwin,
-                             uint64_t* dbar, uint32_t pf, int* err) {
+__device__ void produce_stages(ProducerRing& R, const ScheduleView& sched, uint32_t s_begin, uint32_t s_end,
+                               const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                               const void* __restrict__ val, const VecSet& vecs, unsigned char* slot_base,
+                               const SlotLayout& SL, uint32_t slot_stride, uint64_t* full, uint64_t* empty,
+                               uint32_t S, StageDesc* dwin, uint64_t* dbar, uint32_t pf, int* err) {
     using T = typename Fmt<FMT>::T;
     constexpr uint32_t VA = Fmt<FMT>::kAlign;
-    uint32_t st = 0, ph = 0, issued = 0;
+    if (!R.ok || s_begin >= s_end) return;
+    uint32_t st = R.st, ph = R.ph, issued = R.issued;
+    const uint32_t wb = R.wbase;
     auto load_window = [&](uint32_t w) {
         const uint32_t first = s_begin + w * kDescWin;
         if (first >= s_end) return;
-        const uint32_t n = min(kDescWin, s_end - first);
-        dev::mbar_arrive_expect_tx(&dbar[w & 1], n * (uint32_t)sizeof(StageDesc));
-        dev::bulk_g2s(dwin + (w & 1) * kDescWin, sched.desc + first, n * (uint32_t)sizeof(StageDesc), &dbar[w & 1]);
+        const uint32_t n = min(kDescWin, s_end - first), g = wb + w;
+        dev::mbar_arrive_expect_tx(&dbar[g & 1], n * (uint32_t)sizeof(StageDesc));
+        dev::bulk_g2s(dwin + (g & 1) * kDescWin, sched.desc + first, n * (uint32_t)sizeof(StageDesc), &dbar[g & 1]);
     };
     const uint32_t nst = s_end - s_begin;
     const uint32_t nwin = (nst + kDescWin - 1) / kDescWin;
     uint32_t w_issued = 0, w_waited = 0;  // descriptor windows issued / waited for
+    // descriptors of earlier calls were read through the generic proxy before
+    // their buffers are refilled by bulk copies
+    if (wb) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     load_window(0);
     load_window(1);
     w_issued = min(nwin, 2u);
     // Make window w readable (windows are waited for in order).
     auto have_window = [&](uint32_t w) -> bool {
         while (w_waited <= w) {
-            if (!dev::mbar_wait_bounded(&dbar[w_waited & 1], (w_waited >> 1) & 1)) return false;
+            const uint32_t g = wb + w_waited;
+            if (!dev::mbar_wait_bounded(&dbar[g & 1], (g >> 1) & 1)) return false;
             ++w_waited;
         }
         return true;
@@ -174,7 +188,7 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
     auto prefetch = [&](uint32_t j) {
         const uint32_t w = j / kDescWin;
         if (w >= w_issued || !have_window(w)) return;
-        const StageDesc P = dwin[(w & 1) * kDescWin + j % kDescWin];
+        const StageDesc P = dwin[((wb + w) & 1) * kDescWin + j % kDescWin];
         const uint32_t v_a = P.nz0 & ~(VA - 1), v_n = round_up(P.nz1, VA) - v_a;
         const uint32_t c_a = P.nz0 & ~3u, c_n = round_up(P.nz1, 4) - c_a;
         if (v_n) dev::bulk_prefetch_l2(static_cast<const T*>(val) + v_a, v_n * (uint32_t)sizeof(T));
@@ -190,9 +204,10 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
         if (pf && j + pf < nst) prefetch(j + pf);
         if (!have_window(w)) {
             atomicExch(err, kErrTimeoutEmpty);
+            R.ok = false;
             break;
         }
-        const StageDesc D = dwin[(w & 1) * kDescWin + jw];
+        const StageDesc D = dwin[((wb + w) & 1) * kDescWin + jw];
         if (jw == kDescWin - 1 && w + 2 < nwin) {
             // the window's last descriptor is in registers (and the prefetch
             // look-ahead, < kDescWin, reads window w + 1): refill its buffer
@@ -202,9 +217,10 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
         }
         if (!dev::mbar_wait_bounded(&empty[st], ph ^ 1)) {
             atomicExch(err, kErrTimeoutEmpty);
+            R.ok = false;
             break;
         }
-        unsigned char* buf = slot_base + st * SL.bytes;
+        unsigned char* buf = slot_base + st * slot_stride;
         *reinterpret_cast<StageDesc*>(buf + SL.hdr_off) = D;
         const bool coop = (D.meta & STAGE_COOP) != 0;
         const uint32_t rp_a = D.row0 & ~3u, rp_n = coop ? 0 : round_up(D.row1 + 1, 4) - rp_a;
@@ -246,8 +262,18 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
         }
     }
     // Descriptor windows issued but not waited for (only after a timeout).
-    for (uint32_t w = w_waited; w < w_issued; ++w) dev::mbar_wait_bounded(&dbar[w & 1], (w >> 1) & 1);
-    uint32_t n = issued < S ? issued : S;
+    for (uint32_t w = w_waited; w < w_issued; ++w) dev::mbar_wait_bounded(&dbar[(wb + w) & 1], ((wb + w) >> 1) & 1);
+    R.st = st;
+    R.ph = ph;
+    R.issued = issued;
+    R.wbase = wb + w_issued;
+}
+
+// Wait until every copy the ring issued has landed, so the CTA never exits with
+// copies into its shared memory in flight (bounded waits).
+__device__ __forceinline__ void producer_drain(const ProducerRing& R, uint64_t* full, uint32_t S) {
+    uint32_t st = R.st, ph = R.ph;
+    const uint32_t n = R.issued < S ? R.issued : S;
     for (uint32_t i = 0; i < n; ++i) {
         if (st == 0) {
             st = S - 1;
@@ -257,6 +283,19 @@ __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32
         }
         dev::mbar_wait_bounded(&full[st], ph);
     }
+}
+
+// The producer of a single-matrix kernel: all of the CTA's stages, then drain.
+template <int FMT>
+__device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32_t s_end,
+                             const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                             const void* __restrict__ val, const VecSet& vecs, unsigned char* slot_base,
+                             const SlotLayout& SL, uint64_t* full, uint64_t* empty, uint32_t S, StageDesc* dwin,
+                             uint64_t* dbar, uint32_t pf, int* err) {
+    ProducerRing R;
+    produce_stages<FMT>(R, sched, s_begin, s_end, row_ptr, col, val, vecs, slot_base, SL, SL.bytes, full, empty, S,
+                        dwin, dbar, pf, err);
+    producer_drain(R, full, S);
 }
 
 // Value of staged vector k for row r; `slot` is the slot's shared address and
