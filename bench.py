@@ -10,6 +10,7 @@ HBM.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
     python bench.py --workload batched [--steps K]   # 27 scenario matrices x 16 vectors
+    python bench.py --workload precision             # u16 / BF16 / FP8, plain and compensated
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on the same workload and metric.  Under torchrun (N > 1) every rank
@@ -113,6 +114,24 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(ms: float, device=None) -> float:
+    """The slowest rank's time (all ranks get it); the value itself with one rank."""
+    import torch
+    import torch.distributed as td
+
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_step: int, steps: int, world_size: int, max_ms: float) -> float:
+    """Whole-job throughput of `world_size` replicas, each doing `steps` steps of
+    `bytes_per_step` algorithmic bytes, timed by the slowest rank."""
+    return world_size * bytes_per_step * steps / (max_ms * 1e-3) / 1e9
+
+
 def _traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it matches this build."""
     try:
@@ -202,10 +221,7 @@ def run_gpu(args):
     total_ms = e_start.elapsed_time(e_end)
     spmv_ms = sum(ev[k][0].elapsed_time(ev[k][1]) for k in range(K)) / K
     grad_ms = sum(ev[k][1].elapsed_time(ev[k][2]) for k in range(K)) / K
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, device)
     A.device_status()
 
     # end to end through the public API with host buffers: H2D x, both calls, D2H d and f
@@ -231,7 +247,7 @@ def run_gpu(args):
     e2e_ms = e2[0].elapsed_time(e2[1]) / ke
 
     step_bytes = info["spmv_bytes"] + info["fused_bytes"]
-    value = ws * step_bytes * K / (total_ms * 1e-3) / 1e9
+    value = whole_job_gbs(step_bytes, K, ws, total_ms)
     peak, peak_kind = _peaks()
     spmv_gbs = info["spmv_bytes"] / (spmv_ms * 1e-3) / 1e9
     grad_gbs = info["fused_bytes"] / (grad_ms * 1e-3) / 1e9
@@ -379,7 +395,10 @@ def run_batched(args):
     nvec = 16
     mats, Xs, nbytes, nnz, nrows = [], [], 0, 0, 0
     sample = None
+    pick = set(range(27)) if not args.matrices else {int(m) for m in args.matrices.split(",")}
     for i, beam in enumerate(dosegen.batched_beams()):
+        if i not in pick:
+            continue
         csr = dosegen.generate(beam)
         mats.append(dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="u16", values_f64=csr.val))
         Xs.append(torch.from_numpy(dosegen.spot_weights(csr.ncols, 300 + i, nvec=nvec).reshape(csr.ncols, nvec))
@@ -387,7 +406,7 @@ def run_batched(args):
         nbytes += 6 * csr.nnz + 4 * (csr.nrows + 1) + 4 * nvec * (csr.nrows + csr.ncols)
         nnz += csr.nnz
         nrows += csr.nrows
-        if i == 13 and rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        if i == max(pick) and rank == 0 and ws == 1 and not args.no_cpu_baseline:
             sample = (csr, Xs[-1].cpu().numpy())
         del csr
     Ds = [torch.empty((A.nrows, nvec), dtype=torch.float32, device=device) for A in mats]
@@ -418,15 +437,11 @@ def run_batched(args):
     torch.cuda.synchronize()
     time.sleep(0.2)
     clk = clocks.stop()
-    total_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(e0.elapsed_time(e1), device)
     for A in mats:
         A.device_status()
     ms = total_ms / K
-    gbs = nbytes / (ms * 1e-3) / 1e9
+    gbs = whole_job_gbs(nbytes, K, 1, total_ms)
     peak, peak_kind = _peaks()
     # end to end: X from pinned host memory in, the graph, all of D out to pinned host memory
     Xh = [X.cpu().pin_memory() for X in Xs]
@@ -450,7 +465,9 @@ def run_batched(args):
         "metric": BATCH_METRIC, "value": round(ws * gbs, 1), "unit": "GB/s", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "matrices": len(mats), "nvec": nvec, "nnz": nnz, "nrows": nrows,
+        "config": {"workload": BATCH_WORKLOAD if len(mats) == 27 else
+                   f"{len(mats)} of the scenario matrices ({sorted(pick)}) x 16 FP32 spot-weight vectors",
+                   "matrices": len(mats), "nvec": nvec, "nnz": nnz, "nrows": nrows,
                    "bytes_per_step": nbytes, "l2": "inputs larger than L2 (A streams ~11 GB per step)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "spmm_staged_kernel", "achieved": round(gbs, 1), "peak": peak,
@@ -470,6 +487,76 @@ def run_batched(args):
         print(json.dumps(out), flush=True)
 
 
+PREC_METRIC = "dose SpMV effective HBM GB/s per stored format, with max / mean relative dose error vs the FP64 oracle"
+
+
+def run_precision(args):
+    """The clinical beam stored as u16 + scale (the baseline), BF16 and FP8-E4M3
+    with per-row scales, each plain and with compensated (Dot2) rows: time per
+    dose evaluation, effective GB/s of the format's own bytes, and the dose
+    error on sampled rows against the FP64 oracle applied to (a) the
+    generator's FP64 values (format + accumulation error) and (b) the same
+    decoded values (accumulation error only)."""
+    import torch
+
+    import oracle
+    import paper_2103_09683_gb300 as dose
+
+    dose.build()
+    torch.cuda.set_device(0)
+    beam = dosegen.CLINICAL
+    csr = dosegen.generate(beam)
+    x = dosegen.spot_weights(csr.ncols, dosegen.weight_seed(beam))
+    xd = torch.from_numpy(x).cuda()
+    rng = np.random.default_rng(7)
+    lens = np.diff(csr.row_ptr.astype(np.int64))
+    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 20000, replace=False))
+    exact = oracle.spmv_rows(rows, csr.row_ptr, csr.col, csr.val, x)  # generator's FP64 values
+    peak, _ = _peaks()
+    K = max(3, min(args.steps, 200))
+    variants = []
+    for fmt in ("u16", "bf16", "fp8"):
+        enc = oracle.encode(csr, {"u16": oracle.U16_SCALE, "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE}[fmt])
+        same = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
+        for comp in (False, True):
+            A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt=fmt, values=enc.values,
+                                         scales=enc.scales, compensated=comp)
+            d = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
+            for _ in range(args.warmup):
+                A.spmv(xd, d)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(K):
+                A.spmv(xd, d)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            A.device_status()
+            dv = d.cpu().numpy()[rows].astype(np.float64)
+            nz = exact != 0
+            rel_fmt = np.abs(dv[nz] - exact[nz]) / np.abs(exact[nz])
+            nz2 = same != 0
+            rel_acc = np.abs(dv[nz2] - same[nz2]) / np.abs(same[nz2])
+            nbytes = A.info()["spmv_bytes"]
+            variants.append({"format": fmt, "compensated": comp, "ms": round(ms, 5),
+                             "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                             "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4), "bytes": nbytes,
+                             "bytes_per_entry": round(nbytes / csr.nnz, 3),
+                             "rel_err_vs_fp64_values": {"max": float(rel_fmt.max()), "mean": float(rel_fmt.mean())},
+                             "rel_err_vs_same_decoded": {"max": float(rel_acc.max()), "mean": float(rel_acc.mean())}})
+            del A, d
+        del enc
+    base = variants[0]
+    out = {"metric": PREC_METRIC, "value": base["achieved_gbs"], "unit": "GB/s", "n_gpus": 1, "steps": K,
+           "warmup": args.warmup, "ms_per_step": base["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD.split("; step")[0] + "; dose eval d = A x per stored format",
+                      "sampled_rows": int(len(rows))},
+           "variants": variants}
+    print(json.dumps(out), flush=True)
+
+
 def batched_cpu_baseline(csr, X, budget_s=10.0):
     """The oracle's FP64 SpMM on row blocks of one scenario matrix (about
     budget_s of single-core work), as GB/s of the same byte model."""
@@ -487,7 +574,7 @@ def batched_cpu_baseline(csr, X, budget_s=10.0):
         nb += 6 * nz + 4 * (r1 - r0 + 1) + 4 * X.shape[1] * ((r1 - r0) + X.shape[0])
         blocks += 1
     return {"value": round(nb / spent / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{blocks} row block(s) of ~5% of scenario matrix 13 ({csr.nnz} entries) x {X.shape[1]} "
+            "sample": f"{blocks} row block(s) of ~5% of one scenario matrix ({csr.nnz} entries) x {X.shape[1]} "
                       f"vectors: FP64 SpMM, single thread, {spent:.1f} s"}
 
 
@@ -500,8 +587,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="time candidate schedules first (dose_autotune)")
     ap.add_argument("--tuning", default="", help="schedule knobs, e.g. tile_nnz=8192,adj_scatter_warps=4")
-    ap.add_argument("--workload", default="clinical", choices=["clinical", "batched"],
-                    help="clinical: the dose + dose-gradient step (default); batched: 27 matrices x 16 vectors")
+    ap.add_argument("--matrices", default="", help="batched: subset of the 27 scenario matrices, e.g. 4,13,22")
+    ap.add_argument("--workload", default="clinical", choices=["clinical", "batched", "precision"],
+                    help="clinical: the dose + dose-gradient step (default); batched: 27 matrices x 16 vectors; "
+                         "precision: dose eval per stored format with its error vs the FP64 oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -509,6 +598,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_gpu(args)
 
