@@ -71,11 +71,12 @@ struct Fmt<DOSE_FMT_FP8E4M3_ROWSCALE> {
         return dev::dec_e4m3((uint8_t)dev::lds_u8_lt(k, ke, a));
     }
     __device__ static void lds4(bool p, uint32_t a, float* w) {
-        const uint32_t q = dev::lds_u32_if(p, a);
-        w[0] = dev::dec_e4m3((uint8_t)(q & 0xFF));
-        w[1] = dev::dec_e4m3((uint8_t)((q >> 8) & 0xFF));
-        w[2] = dev::dec_e4m3((uint8_t)((q >> 16) & 0xFF));
-        w[3] = dev::dec_e4m3((uint8_t)(q >> 24));
+        float v[4];
+        dec4(dev::lds_u32_if(p, a), 0u, v);
+        w[0] = v[0];
+        w[1] = v[1];
+        w[2] = v[2];
+        w[3] = v[3];
     }
     // four codes in the bytes of q0 (q1 unused): two E4M3x2 -> F16x2 conversions
     __device__ static void dec4(uint32_t q0, uint32_t, float (&w)[4]) {
