@@ -220,6 +220,15 @@ dose_status dose_encode_host(dose_format fmt, uint32_t nrows, const uint32_t* ro
  * clear it. */
 dose_status dose_device_status(const dose_matrix* A, void* stream);
 
+/* Self-test of the bounded waits that guard every pipelined kernel: one GPU
+ * thread waits on an mbarrier phase that never completes and gives up after
+ * limit_us microseconds (1..1e6), as the kernels' ring waits do after ~4 s.
+ * Returns DOSE_ERR_TIMEOUT when the wait ran out as designed (the expected
+ * result; the CUDA context stays usable), DOSE_OK if the wait did not run out
+ * (the self-test failed), DOSE_ERR_CUDA on a CUDA error.  Synchronises
+ * `stream`. */
+dose_status dose_selftest_bounded_wait(uint32_t limit_us, void* stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* dose_last_error(void);
 

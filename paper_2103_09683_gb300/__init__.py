@@ -22,7 +22,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["build", "load", "DoseMatrix", "DoseError", "FORMATS", "spmv_batched", "adjoint_noalloc", "dose_spmv",
-           "QuadraticDoseObjective", "pg_solve", "PGSolver", "encode_host", "library_path"]
+           "QuadraticDoseObjective", "pg_solve", "PGSolver", "encode_host", "library_path", "selftest_bounded_wait"]
 
 FORMATS = {"u16": 0, "bf16": 1, "fp8": 2}
 CREATE_COMPENSATED = 0x1
@@ -90,6 +90,7 @@ EXPORTS = {
     "dose_device_status": (ctypes.c_int, [_P, _P]),
     "dose_adjoint_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, _P, _P, ctypes.c_int,
                                             _P, _P, ctypes.c_float, _P, _P, _P]),
+    "dose_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, _P]),
     "dose_last_error": (ctypes.c_char_p, []),
     "dose_version": (ctypes.c_char_p, []),
 }
@@ -150,6 +151,12 @@ def _dptr(t, dtype, n=None, what="tensor"):
     if n is not None and t.numel() != n:
         raise ValueError(f"{what} has {t.numel()} elements, expected {n}")
     return ctypes.c_void_p(t.data_ptr()) if t.numel() else ctypes.c_void_p(0)
+
+
+def selftest_bounded_wait(limit_us: int = 20000, stream=None) -> int:
+    """Run the device self-test of the bounded waits; returns the status code
+    (5 = DOSE_ERR_TIMEOUT, the expected result)."""
+    return int(load().dose_selftest_bounded_wait(ctypes.c_uint32(limit_us), _stream_handle(stream)))
 
 
 def encode_host(fmt: str, row_ptr: np.ndarray, values_f64: np.ndarray):

@@ -254,8 +254,10 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
                 for (uint32_t r = D.row0 + ftid; r < D.row1; r += nft) {
                     if (dev::lds_u32(v.rp + 4 * r) == dev::lds_u32(v.rp + 4 * r + 4)) {
                         if (p.d) p.d[r] = 0.0f;
-                        dev::df_add_wsq(f_hi, f_lo, slot_vec(slot, SL, p.vecs, 1, D.row0, r), 0.0f,
-                                        slot_vec(slot, SL, p.vecs, 0, D.row0, r));
+                        // an empty row with p = 0 adds exactly nothing (d = 0), unless w is not finite
+                        const float pv = slot_vec(slot, SL, p.vecs, 0, D.row0, r);
+                        const float wv = slot_vec(slot, SL, p.vecs, 1, D.row0, r);
+                        if (pv != 0.0f || !(fabsf(wv) < INFINITY)) dev::df_add_wsq(f_hi, f_lo, wv, 0.0f, pv);
                     }
                 }
                 switch (D.meta & STAGE_LANES_MASK) {

@@ -441,9 +441,39 @@ static float time_launches(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int r
     return ms / reps;
 }
 
+// Self-test of the bounded waits: one thread waits on a phase of an mbarrier
+// that nothing arrives at; the wait gives up after limit_ns and the kernel
+// records whether it did, then returns.
+__device__ int g_selftest_timed_out;
+
+__global__ void selftest_wait_kernel(uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    dev::mbar_init(&bar, 1);
+    dev::fence_mbar_init();
+    g_selftest_timed_out = dev::mbar_wait_limit(&bar, 0, limit_ns) ? 0 : 1;
+}
+
 }  // namespace
 
 extern "C" {
+
+dose_status dose_selftest_bounded_wait(uint32_t limit_us, void* stream) {
+    if (limit_us == 0 || limit_us > 1000000u) return invalid("dose_selftest_bounded_wait: limit_us must be in [1, 1e6]");
+    cudaStream_t s = as_stream(stream);
+    selftest_wait_kernel<<<1, 1, 0, s>>>((uint64_t)limit_us * 1000ull);
+    cudaError_t e = cudaGetLastError();
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(&flag, g_selftest_timed_out, sizeof(int), 0,
+                                                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "dose_selftest_bounded_wait");
+    if (!flag) {
+        set_error("dose_selftest_bounded_wait: the wait on a phase that never completes returned as completed");
+        return DOSE_OK;
+    }
+    set_error("dose_selftest_bounded_wait: the bounded wait ran out as designed");
+    return DOSE_ERR_TIMEOUT;
+}
 
 const char* dose_last_error(void) { return g_last_error.c_str(); }
 

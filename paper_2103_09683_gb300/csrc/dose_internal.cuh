@@ -234,16 +234,21 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
     return ok != 0;
 }
 
-// Wait for the phase of `parity` to complete, giving up after ~4 s of wall
-// time (the kernels this guards run for milliseconds).  Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Wait for the phase of `parity` to complete, giving up after limit_ns of wall
+// time.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     while (true) {
         for (int i = 0; i < 16; ++i)
             if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-        if (global_timer_ns() - t0 > 4000000000ull) return false;
+        if (global_timer_ns() - t0 > limit_ns) return false;
     }
+}
+
+// The waits of the pipelined kernels: ~4 s (the kernels run for milliseconds).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    return mbar_wait_limit(bar, parity, 4000000000ull);
 }
 
 // Bulk async copy global -> shared (no tensor map), completion counted on `bar`.

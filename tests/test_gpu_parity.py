@@ -367,3 +367,16 @@ def test_autotune_keeps_parity(tiny, objective_inputs):
     gabs = oracle.abs_spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r)
     adj_check(g.cpu().numpy(), g_ref, gabs, rtol=1e-4)
     A.device_status()
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(tiny):
+    """Failure detection without a fault: a wait on an mbarrier phase that never
+    completes gives up after 20 ms and reports DOSE_ERR_TIMEOUT; the next call
+    on the same context computes correctly."""
+    import time
+    t0 = time.perf_counter()
+    assert dose.selftest_bounded_wait(20000) == 5
+    assert time.perf_counter() - t0 < 5.0
+    A, enc = make(tiny, "u16")
+    x = _x(tiny.ncols)
+    fwd_check(A.spmv(_to(x)).cpu().numpy(), oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x))
