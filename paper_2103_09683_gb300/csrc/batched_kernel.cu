@@ -74,12 +74,18 @@ __device__ __forceinline__ VecSet item_vecs(const StagedItem& it) {
 template <uint32_t NQ>
 __host__ __device__ constexpr uint32_t xrow_bytes() { return NQ * 16u; }
 
+// Window row of X that holds column c (window-relative): rows are swapped in
+// pairs when bit 2 of c is set, so the rows of columns c and c + 4 (read by
+// neighbouring entry slots in one instruction) lie in opposite halves of the
+// banks.  An involution that maps every multiple of 8 to itself, so the
+// window (a multiple of 32 columns) and its zero row keep their places.
+__device__ __forceinline__ uint32_t xrow_swz(uint32_t c) { return c ^ ((c >> 2) & 1u); }
+
 // D rows of one group of L = SLOTS * NQ lanes; lanes (e, q): e = entry slot,
-// q = quad of vectors.  Slot e takes the entries kb + e, kb + e + SLOTS, ...
-// (neighbouring slots read neighbouring columns, whose 64-byte rows of X lie
-// in opposite halves of the banks); `iters` (warp-uniform) steps of four.
-// Plain typed shared-memory loads (the slot's data were released by the
-// mbarrier wait, a compiler barrier), so the compiler may overlap steps.
+// q = quad of vectors.  Slot e takes the groups of four consecutive entries at
+// (kb & ~3) + 4 e + 4 SLOTS s (one 16-byte column load, one value load);
+// `iters` (warp-uniform) steps.  Plain typed shared-memory loads (the slot's
+// data were released by the mbarrier wait, a compiler barrier).
 template <int FMT, uint32_t NQ, uint32_t SLOTS>
 __device__ __forceinline__ void spmm_rows(const StagedItem& it, const StageDesc& D, const uint32_t* __restrict__ colp,
                                           const typename Fmt<FMT>::T* __restrict__ valp,
@@ -87,6 +93,7 @@ __device__ __forceinline__ void spmm_rows(const StagedItem& it, const StageDesc&
                                           const float4* __restrict__ xw4, uint32_t wlo, uint32_t nvec, bool vec4,
                                           float rs_row0, const float* __restrict__ rsp, uint32_t ctid, uint32_t lane,
                                           uint32_t rot) {
+    using T = typename Fmt<FMT>::T;
     constexpr uint32_t L = SLOTS * NQ;  // lanes per row
     constexpr uint32_t G = kSpmmConsumerWarps * 32 / L;
     const uint32_t li = lane & (L - 1), e = li / NQ, q = li % NQ;
@@ -97,36 +104,42 @@ __device__ __forceinline__ void spmm_rows(const StagedItem& it, const StageDesc&
     for (uint32_t base = 0; base < n_ne; base += G) {
         const uint32_t i = base + j0;
         const bool has = i < n_ne;
-        // lanes without a row read the stage's first entry (masked) and write nothing
+        // lanes without a row read the stage's first aligned group (masked) and write nothing
         uint32_t row = 0, kb = D.nz0, ke = D.nz0;
         if (has) {
             row = D.row0 + nep[i];
             kb = rpp[row];
             ke = rpp[row + 1];
         }
-        const uint32_t iters = __reduce_max_sync(0xffffffffu, (ke - kb + 4 * SLOTS - 1) / (4 * SLOTS));
+        const int len = (int)(ke - kb);
+        const uint32_t kb4 = kb & ~3u;
+        const uint32_t span = ke > kb ? ke - kb4 : 0;
+        const uint32_t iters = __reduce_max_sync(0xffffffffu, (span + 4 * SLOTS - 1) / (4 * SLOTS));
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        uint32_t k = kb + e;
-        for (uint32_t s2 = 0; s2 < iters; ++s2, k += 4 * SLOTS) {
-            uint32_t c[4];
-            float a[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t ku = k + u * SLOTS;
-                const bool m = ku < ke;
-                const uint32_t kc = m ? ku : kb;  // an entry of this row either way
-                const uint32_t cv = colp[kc];
-                const float av = Fmt<FMT>::dec(valp[kc]);
-                c[u] = m ? cv - wlo : zrow;
-                a[u] = m ? av : 0.f;
+        int off = (int)(4 * e) - (int)(kb & 3u);
+        uint32_t k4 = kb4 + 4 * e;
+        for (uint32_t s2 = 0; s2 < iters; ++s2, off += 4 * SLOTS, k4 += 4 * SLOTS) {
+            // a group outside the row reads the row's first group instead (always in the slot)
+            const uint32_t kg = off < len ? k4 : kb4;
+            const uint4 cc = *reinterpret_cast<const uint4*>(colp + kg);
+            float av[4];
+            if (sizeof(T) == 2) {
+                const uint2 qv = *reinterpret_cast<const uint2*>(valp + kg);
+                Fmt<FMT>::dec4(qv.x, qv.y, av);
+            } else {
+                Fmt<FMT>::dec4(*reinterpret_cast<const uint32_t*>(valp + kg), 0u, av);
             }
+            const uint32_t cu[4] = {cc.x, cc.y, cc.z, cc.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float4 x = xw4[c[u] * NQ + q];
-                acc.x = __fmaf_rn(a[u], x.x, acc.x);
-                acc.y = __fmaf_rn(a[u], x.y, acc.y);
-                acc.z = __fmaf_rn(a[u], x.z, acc.z);
-                acc.w = __fmaf_rn(a[u], x.w, acc.w);
+                const bool m = (uint32_t)(off + u) < (uint32_t)len;
+                const uint32_t c = m ? xrow_swz(cu[u] - wlo) : zrow;
+                const float a = m ? av[u] : 0.f;
+                const float4 x = xw4[c * NQ + q];
+                acc.x = __fmaf_rn(a, x.x, acc.x);
+                acc.y = __fmaf_rn(a, x.y, acc.y);
+                acc.z = __fmaf_rn(a, x.z, acc.z);
+                acc.w = __fmaf_rn(a, x.w, acc.w);
             }
         }
 #pragma unroll
@@ -204,7 +217,7 @@ __device__ __forceinline__ void spmm_stage(const StagedItem& it, const SlotLayou
         const uint32_t kb = __ldg(it.row_ptr + row), ke = __ldg(it.row_ptr + row + 1);
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (uint32_t k = kb + e; k < ke; k += SL32) {
-            const uint32_t c = __ldg(it.col + k) - wlo;
+            const uint32_t c = xrow_swz(__ldg(it.col + k) - wlo);
             const float a = Fmt<FMT>::dec(val[k]);
             float4 x;
             asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -307,7 +320,7 @@ __global__ void __launch_bounds__(32 * (kSpmmConsumerWarps + 1), 1) spmm_staged_
         dev::named_barrier(1, nct);
         constexpr uint32_t XF = xrow_bytes<NQ>() / 4;  // floats per window row
         for (uint32_t j = ctid; j < (it.wwidth + 1) * XF; j += nct) {  // row wwidth: all zeros
-            const uint32_t jc = j / XF, c = wlo + jc, u = j % XF;
+            const uint32_t jc = xrow_swz(j / XF), c = wlo + jc, u = j % XF;  // window row j holds column jc
             xwin[j] = (jc < it.wwidth && c < it.ncols && u < p.nvec) ? __ldg(it.X + (size_t)c * p.nvec + u) : 0.f;
         }
         dev::named_barrier(1, nct);
