@@ -492,7 +492,8 @@ PREC_METRIC = "dose SpMV effective HBM GB/s per stored format, with max / mean r
 
 def run_precision(args):
     """The clinical beam stored as u16 + scale (the baseline), BF16 and FP8-E4M3
-    with per-row scales, each plain and with compensated (Dot2) rows: time per
+    with per-row scales, each plain, with compensated (Dot2) rows, and with
+    16-bit column indices: time per
     dose evaluation, effective GB/s of the format's own bytes, and the dose
     error on sampled rows against the FP64 oracle applied to (a) the
     generator's FP64 values (format + accumulation error) and (b) the same
@@ -518,9 +519,9 @@ def run_precision(args):
     for fmt in ("u16", "bf16", "fp8"):
         enc = oracle.encode(csr, {"u16": oracle.U16_SCALE, "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE}[fmt])
         same = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
-        for comp in (False, True):
+        for comp, idx16 in ((False, False), (True, False), (False, True)):
             A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt=fmt, values=enc.values,
-                                         scales=enc.scales, compensated=comp)
+                                         scales=enc.scales, compensated=comp, index16=idx16)
             d = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
             for _ in range(args.warmup):
                 A.spmv(xd, d)
@@ -539,7 +540,7 @@ def run_precision(args):
             nz2 = same != 0
             rel_acc = np.abs(dv[nz2] - same[nz2]) / np.abs(same[nz2])
             nbytes = A.info()["spmv_bytes"]
-            variants.append({"format": fmt, "compensated": comp, "ms": round(ms, 5),
+            variants.append({"format": fmt, "compensated": comp, "index_bytes": 2 if idx16 else 4, "ms": round(ms, 5),
                              "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
                              "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4), "bytes": nbytes,
                              "bytes_per_entry": round(nbytes / csr.nnz, 3),

@@ -88,6 +88,12 @@ typedef struct {
 /* dose_create_matrix flags */
 #define DOSE_CREATE_COMPENSATED 0x1u /* compensated (TwoSum/TwoProduct) accumulation on rows
                                         longer than 128 entries */
+#define DOSE_CREATE_U16_INDEX 0x2u   /* dose_spmv reads 16-bit column indices: 2 + value bytes per
+                                        entry instead of 4 + value bytes (the reduced index width the
+                                        paper's Sec. V proposes as future work); needs ncols <= 65536.
+                                        The handle keeps a 16-bit copy of the indices beside the
+                                        32-bit ones (the other kernels use those): +2 B per entry of
+                                        device memory. */
 
 /* Schedule knobs of a matrix (row-length binning and pipeline shape).  All
  * fields 0 = library default.  Changing them never changes which rows an

@@ -26,6 +26,7 @@ __all__ = ["build", "load", "DoseMatrix", "DoseError", "FORMATS", "spmv_batched"
 
 FORMATS = {"u16": 0, "bf16": 1, "fp8": 2}
 CREATE_COMPENSATED = 0x1
+CREATE_U16_INDEX = 0x2
 _STATUS = {0: "DOSE_OK", 1: "DOSE_ERR_INVALID_ARG", 2: "DOSE_ERR_OOM", 3: "DOSE_ERR_CUDA",
            4: "DOSE_ERR_UNSUPPORTED", 5: "DOSE_ERR_TIMEOUT"}
 
@@ -183,11 +184,14 @@ class DoseMatrix:
     # ---- construction
     @classmethod
     def from_csr(cls, row_ptr, col, *, ncols: int, fmt: str = "u16", values=None, scales=None,
-                 values_f64=None, compensated: bool = False, tuning: dict | None = None, stream=None):
+                 values_f64=None, compensated: bool = False, index16: bool = False, tuning: dict | None = None,
+                 stream=None):
         """Create from host (numpy) or device (torch CUDA) CSR arrays.
 
         Pass either encoded `values` (+ `scales`) in the stored format, or
-        `values_f64` (host) to let the library encode.
+        `values_f64` (host) to let the library encode.  `compensated`: Dot2
+        accumulation on rows longer than 128 entries; `index16`: the dose SpMV
+        reads 16-bit column indices (ncols <= 65536).
         """
         torch = _torch()
         lib = load()
@@ -236,7 +240,8 @@ class DoseMatrix:
             t = Tuning(**{k: int(v) for k, v in tuning.items()})
         out = ctypes.c_void_p()
         stream_h = _stream_handle(stream) if torch.cuda.is_available() else ctypes.c_void_p(0)
-        _check(lib.dose_create_matrix(ctypes.byref(d), CREATE_COMPENSATED if compensated else 0,
+        flags = (CREATE_COMPENSATED if compensated else 0) | (CREATE_U16_INDEX if index16 else 0)
+        _check(lib.dose_create_matrix(ctypes.byref(d), flags,
                                       ctypes.byref(t) if t is not None else None, stream_h,
                                       ctypes.byref(out)))
         return cls(out.value, nrows, int(ncols), nnz, fmt)

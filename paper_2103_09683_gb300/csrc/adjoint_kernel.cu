@@ -140,8 +140,9 @@ __device__ __forceinline__ void scatter_rows(uint32_t gw, const SlotView& v, uin
 // times the row scale) into the slot's r list.
 template <int FMT, uint32_t LG, uint32_t kRowScaleVec>
 __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D, const SlotView& v, uint32_t slot,
-                                         const SlotLayout& SL, uint32_t xs_a, uint32_t ftid, uint32_t lane,
-                                         uint32_t nft, uint32_t rotw, float& f_hi, float& f_lo) {
+                                         const SlotLayout& SL, const SlotPtrs<FMT, 4>& sp, const float* xsp,
+                                         uint32_t zc, uint32_t ftid, uint32_t lane, uint32_t nft, uint32_t rotw,
+                                         float& f_hi, float& f_lo) {
     constexpr uint32_t L = 1u << LG;
     const uint32_t gid = ftid >> LG, li = lane & (L - 1), G = nft >> LG;
     const uint32_t j0 = (gid + G - ((rotw << (5 - LG)) & (G - 1))) & (G - 1);
@@ -150,7 +151,8 @@ __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D,
     for (uint32_t base = 0; base < n_ne; base += G) {
         const uint32_t i = base + j0;
         const bool has = i < n_ne;
-        uint32_t row = 0, rs = 0, re = 0;
+        // groups without a row read the stage's first entries (masked) and write nothing
+        uint32_t row = 0, rs = D.nz0, re = D.nz0;
         if (has) {
             row = D.row0 + dev::lds_u16(v.ne + 2 * i);
             rs = dev::lds_u32(v.rp + 4 * row);
@@ -158,7 +160,7 @@ __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D,
         }
         const uint32_t span = re > rs ? re - (rs & ~3u) : 0;
         const uint32_t iters = __reduce_max_sync(0xffffffffu, (span + 4 * L - 1) / (4 * L));
-        float sum = dot_vec<FMT, L>(v, xs_a, rs, re, li, iters);
+        float sum = dot_vec_p<FMT, L, 4>(sp, xsp, zc, rs, re, li, iters);
 #pragma unroll
         for (uint32_t off = L >> 1; off > 0; off >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
         if (has && li == 0) {
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
     const uint32_t gw_floats = round_up(p.wwidth * 4, 128) / 4;
     float* gacc = reinterpret_cast<float*>(smem + kAdjHeader);  // Ws x gw_floats
     float* xs = gacc + Ws * gw_floats;
-    const uint32_t x_bytes = QUAD ? round_up(p.wwidth * 4, 128) : 0;
+    const uint32_t x_bytes = QUAD ? round_up((p.wwidth + 1) * 4, 128) : 0;  // the window of x and a zero
     unsigned char* slot_base = reinterpret_cast<unsigned char*>(xs) + x_bytes;
     const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, sizeof(T), p.vecs.n, QUAD);
 
@@ -226,7 +228,8 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
     const uint32_t ctid = threadIdx.x - 32;
     for (uint32_t j = ctid; j < Ws * gw_floats; j += ncons) gacc[j] = 0.f;
     if (QUAD)
-        for (uint32_t j = ctid; j < p.wwidth; j += ncons) xs[j] = wlo + j < p.ncols ? __ldg(p.x + wlo + j) : 0.f;
+        for (uint32_t j = ctid; j <= p.wwidth; j += ncons)
+            xs[j] = j < p.wwidth && wlo + j < p.ncols ? __ldg(p.x + wlo + j) : 0.f;
     dev::named_barrier(1, ncons);
 
     const uint32_t xs_a = dev::smem_u32(xs) - 4 * wlo;
@@ -238,6 +241,8 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
     if (is_fwd) {
         // ------------------------------------------------ forward warps
         const uint32_t fw = warp - 1, ftid = fw * 32 + lane, nft = Wf * 32;  // Wf is a power of two
+        const float* xsp = xs - wlo;         // x of column c at xsp[c] (c in this CTA's window)
+        const uint32_t zc = wlo + p.wwidth;  // the zero element after the window
         float coop_s = 0.f;
         uint32_t st = 0, ph = 0;
         for (uint32_t s = s_begin; s < s_end; ++s) {
@@ -250,6 +255,7 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
             const uint32_t slot = slot0 + st * SL.bytes;
             const StageDesc D = slot_desc(slot);
             const SlotView v = slot_view<FMT>(slot, SL, D);
+            const SlotPtrs<FMT, 4> sp = slot_ptrs<FMT, 4>(slot_base + st * SL.bytes, SL, D);
             if (!(D.meta & STAGE_COOP)) {
                 for (uint32_t r = D.row0 + ftid; r < D.row1; r += nft) {
                     if (dev::lds_u32(v.rp + 4 * r) == dev::lds_u32(v.rp + 4 * r + 4)) {
@@ -261,12 +267,12 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
                     }
                 }
                 switch (D.meta & STAGE_LANES_MASK) {
-                    case 0: fwd_rows<FMT, 0, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
-                    case 1: fwd_rows<FMT, 1, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
-                    case 2: fwd_rows<FMT, 2, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
-                    case 3: fwd_rows<FMT, 3, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
-                    case 4: fwd_rows<FMT, 4, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
-                    default: fwd_rows<FMT, 5, kRowScaleVec>(p, D, v, slot, SL, xs_a, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    case 0: fwd_rows<FMT, 0, kRowScaleVec>(p, D, v, slot, SL, sp, xsp, zc, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    case 1: fwd_rows<FMT, 1, kRowScaleVec>(p, D, v, slot, SL, sp, xsp, zc, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    case 2: fwd_rows<FMT, 2, kRowScaleVec>(p, D, v, slot, SL, sp, xsp, zc, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    case 3: fwd_rows<FMT, 3, kRowScaleVec>(p, D, v, slot, SL, sp, xsp, zc, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    case 4: fwd_rows<FMT, 4, kRowScaleVec>(p, D, v, slot, SL, sp, xsp, zc, ftid, lane, nft, rotw, f_hi, f_lo); break;
+                    default: fwd_rows<FMT, 5, kRowScaleVec>(p, D, v, slot, SL, sp, xsp, zc, ftid, lane, nft, rotw, f_hi, f_lo); break;
                 }
             } else {
                 // one chunk of a long row: every forward thread takes part
@@ -423,7 +429,8 @@ size_t adj_smem(const dose_matrix* A, const AdjTuning& t, bool quad, uint32_t ws
     const uint32_t nvec = (quad ? 2 : 1) + (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, quad);
     const size_t col_bytes = round_up(A->adj.wwidth * 4, 128);
-    return kAdjHeader + ws * col_bytes + (quad ? col_bytes : 0) + (size_t)t.stages * SL.bytes;
+    const size_t x_bytes = quad ? round_up((A->adj.wwidth + 1) * 4, 128) : 0;  // the window of x and a zero
+    return kAdjHeader + ws * col_bytes + x_bytes + (size_t)t.stages * SL.bytes;
 }
 
 }  // namespace

@@ -293,6 +293,7 @@ static void free_all(dose_matrix* A) {
     free_dev_schedule(A->adj);
     cudaFree(A->row_ptr);
     cudaFree(A->col);
+    cudaFree(A->col16);
     cudaFree(A->val);
     cudaFree(A->row_scale);
     cudaFree(A->g_part);
@@ -490,7 +491,9 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
                                dose_matrix** out) {
     if (!desc || !out) return invalid("dose_create_matrix: null desc or out");
     *out = nullptr;
-    if (flags & ~DOSE_CREATE_COMPENSATED) return invalid("dose_create_matrix: unknown flags");
+    if (flags & ~(DOSE_CREATE_COMPENSATED | DOSE_CREATE_U16_INDEX)) return invalid("dose_create_matrix: unknown flags");
+    if ((flags & DOSE_CREATE_U16_INDEX) && desc->ncols > 65536u)
+        return invalid("DOSE_CREATE_U16_INDEX needs ncols <= 65536 (16-bit column indices)");
     const dose_format fmt = desc->fmt;
     if (fmt != DOSE_FMT_U16_SCALE && fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_FP8E4M3_ROWSCALE)
         return invalid("dose_create_matrix: unknown format");
@@ -614,6 +617,13 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if ((e = upload(&A->row_ptr, A->host_row_ptr.data(), (size_t)nrows + 1, rp_alloc)) != cudaSuccess)
         return fail(e, "row_ptr");
     if ((e = upload(&A->col, col.data(), (size_t)nnz, col_alloc)) != cudaSuccess) return fail(e, "col_idx");
+    const size_t col16_alloc = ((size_t)nnz + 7) / 8 * 8 + 32;  // copy windows reach round_up(nz1, 8)
+    if (flags & DOSE_CREATE_U16_INDEX) {
+        std::vector<uint16_t> c16(nnz);
+        for (uint64_t k = 0; k < nnz; ++k) c16[k] = (uint16_t)col[k];
+        if ((e = upload(&A->col16, c16.data(), (size_t)nnz, col16_alloc)) != cudaSuccess)
+            return fail(e, "16-bit col_idx");
+    }
     if ((e = upload((unsigned char**)&A->val, vals.data(), vals.size(), val_alloc)) != cudaSuccess)
         return fail(e, "values");
     if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE &&
@@ -633,7 +643,7 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
             return st;
         }
     }
-    A->device_bytes = rp_alloc * 4 + col_alloc * 4 + val_alloc +
+    A->device_bytes = rp_alloc * 4 + col_alloc * 4 + ((flags & DOSE_CREATE_U16_INDEX) ? col16_alloc * 2 : 0) + val_alloc +
                       (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) +
                       (size_t)A->adj.grid * ncols_pad * 4 + (size_t)A->adj.grid * 8 + 4 + schedule_bytes(A->fwd) +
                       schedule_bytes(A->adj);
@@ -756,7 +766,8 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     const uint64_t nz = A->nnz, nr = A->nrows, nc = A->ncols;
     const uint64_t rs = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 4 * nr : 0;  // row scales
     // Algorithmic bytes: every stored byte of A once, the vectors once.
-    out->spmv_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
+    const uint64_t ib = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;  // column index bytes read by dose_spmv
+    out->spmv_bytes = (vb + ib) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
     out->adjoint_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
     out->fused_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 8 * nr + 4 * nc + 4 * nc + 8;
     out->scale = A->fmt == DOSE_FMT_U16_SCALE ? A->scale : 0.f;

@@ -120,6 +120,7 @@ struct dose_matrix {
     // matrix arrays (device, padded so aligned bulk copies stay in bounds)
     uint32_t* row_ptr = nullptr;
     uint32_t* col = nullptr;
+    uint16_t* col16 = nullptr;   // DOSE_CREATE_U16_INDEX: 16-bit copy of col for the forward SpMV
     void* val = nullptr;
     float* row_scale = nullptr;  // FP8 only
 

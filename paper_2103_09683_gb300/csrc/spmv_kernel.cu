@@ -24,7 +24,7 @@ namespace {
 
 struct SpmvParams {
     const uint32_t* row_ptr;
-    const uint32_t* col;
+    const void* col;  // column indices of IW bytes
     const void* val;
     float scale;
     const float* x;
@@ -64,13 +64,13 @@ __device__ __forceinline__ float row_result(const SpmvParams& p, uint32_t slot, 
 }
 
 // Sum over the entries kb, kb + step, ... < ke (plain or compensated).
-template <int FMT, bool COMP, bool XSMEM>
+template <int FMT, bool COMP, bool XSMEM, uint32_t IW>
 __device__ __forceinline__ void row_dot(const SlotView& v, uint32_t xs, const float* __restrict__ xg, uint32_t kb,
                                         uint32_t ke, uint32_t step, bool comp_row, float& sum, float& comp) {
     if (COMP && comp_row) {
-        dot_strided_comp<FMT>(v, xs, xg, XSMEM, kb, ke, step, sum, comp);
+        dot_strided_comp<FMT, IW>(v, xs, xg, XSMEM, kb, ke, step, sum, comp);
     } else {
-        const float t = XSMEM ? dot_strided<FMT>(v, xs, kb, ke, step) : dot_strided_gx<FMT>(v, xg, kb, ke, step);
+        const float t = XSMEM ? dot_strided<FMT, IW>(v, xs, kb, ke, step) : dot_strided_gx<FMT, IW>(v, xg, kb, ke, step);
         if (COMP) {
             float u, e;
             dev::two_sum(sum, t, u, e);
@@ -84,9 +84,10 @@ __device__ __forceinline__ void row_dot(const SlotView& v, uint32_t xs, const fl
 
 // The non-empty rows of a NORMAL stage, 2^LG lanes per row.  The stage's list
 // is dealt round-robin to the CTA's G groups, starting `rotw` warps further on.
-template <int FMT, bool COMP, bool XSMEM, uint32_t LG>
+template <int FMT, bool COMP, bool XSMEM, uint32_t IW, uint32_t LG>
 __device__ __forceinline__ void normal_rows(const SpmvParams& p, const StageDesc& D, const SlotView& v,
-                                            uint32_t slot, const SlotLayout& SL, uint32_t xs_a, uint32_t ctid,
+                                            uint32_t slot, const SlotLayout& SL, uint32_t xs_a,
+                                            const SlotPtrs<FMT, IW>& sp, const float* xsp, uint32_t ctid,
                                             uint32_t lane, uint32_t nct, uint32_t rotw) {
     constexpr uint32_t L = 1u << LG;
     const uint32_t gid = ctid >> LG, li = lane & (L - 1), G = nct >> LG;
@@ -96,7 +97,8 @@ __device__ __forceinline__ void normal_rows(const SpmvParams& p, const StageDesc
         const uint32_t i = base + j0;
         const bool has = i < n_ne;
         float sum = 0.f, comp = 0.f;
-        uint32_t row = 0, rs = 0, re = 0;
+        // groups without a row read the stage's first entries (masked) and write nothing
+        uint32_t row = 0, rs = D.nz0, re = D.nz0;
         if (has) {
             row = D.row0 + dev::lds_u16(v.ne + 2 * i);
             rs = dev::lds_u32(v.rp + 4 * row);
@@ -106,19 +108,19 @@ __device__ __forceinline__ void normal_rows(const SpmvParams& p, const StageDesc
             // one trip count for the whole warp: no divergent loop tails
             const uint32_t span = re > rs ? re - (rs & ~3u) : 0;
             const uint32_t iters = __reduce_max_sync(0xffffffffu, (span + 4 * L - 1) / (4 * L));
-            sum = dot_vec<FMT, L>(v, xs_a, rs, re, li, iters);
+            sum = dot_vec_p<FMT, L, IW>(sp, xsp, p.ncols, rs, re, li, iters);
         } else if (has) {
             if (COMP && re - rs > kCompThreshold)
-                dot_strided_comp<FMT>(v, xs_a, p.x, XSMEM, rs + li, re, L, sum, comp);
+                dot_strided_comp<FMT, IW>(v, xs_a, p.x, XSMEM, rs + li, re, L, sum, comp);
             else
-                sum = XSMEM ? dot_fixed<FMT, L>(v, xs_a, rs + li, re) : dot_strided_gx<FMT>(v, p.x, rs + li, re, L);
+                sum = XSMEM ? dot_fixed<FMT, L, IW>(v, xs_a, rs + li, re) : dot_strided_gx<FMT, IW>(v, p.x, rs + li, re, L);
         }
         group_reduce<COMP>(sum, comp, L);
         if (has && li == 0) p.d[row] = row_result<FMT>(p, slot, SL, D.row0, row, COMP ? __fadd_rn(sum, comp) : sum);
     }
 }
 
-template <int FMT, bool COMP, bool XSMEM>
+template <int FMT, bool COMP, bool XSMEM, uint32_t IW>
 __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     using T = typename Fmt<FMT>::T;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -131,9 +133,9 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     float* red = reinterpret_cast<float*>(smem + 256);  // 64 floats: CTA reduction
     StageDesc* dwin = reinterpret_cast<StageDesc*>(smem + 1024);  // 2 x kDescWin descriptors
     float* xs = reinterpret_cast<float*>(smem + kHeaderBytes);
-    const uint32_t x_bytes = XSMEM ? round_up(p.ncols * 4, 128) : 0;
+    const uint32_t x_bytes = XSMEM ? round_up((p.ncols + 1) * 4, 128) : 0;  // x and one zero element
     unsigned char* slot_base = smem + kHeaderBytes + x_bytes;
-    const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, sizeof(T), p.vecs.n, false);
+    const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, sizeof(T), p.vecs.n, false, IW);
 
     const uint32_t s_begin = p.sched.cta_begin[blockIdx.x];
     const uint32_t s_end = p.sched.cta_begin[blockIdx.x + 1];
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
 
     if (warp == 0) {
         if (lane == 0)
-            run_producer<FMT>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, p.vecs, slot_base, SL, full,
+            run_producer<FMT, IW>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, p.vecs, slot_base, SL, full,
                               empty, S, dwin, dbar, p.l2pf, p.err);
         return;
     }
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     const uint32_t ctid = threadIdx.x - 32;
     const uint32_t nct = W * 32;
     if (XSMEM) {
-        for (uint32_t j = ctid; j < p.ncols; j += nct) xs[j] = __ldg(p.x + j);
+        for (uint32_t j = ctid; j <= p.ncols; j += nct) xs[j] = j < p.ncols ? __ldg(p.x + j) : 0.f;
         dev::named_barrier(1, nct);
     }
     const uint32_t xs_a = dev::smem_u32(xs);
@@ -177,7 +179,8 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
         }
         const uint32_t slot = slot0 + st * SL.bytes;
         const StageDesc D = slot_desc(slot);
-        const SlotView v = slot_view<FMT>(slot, SL, D);
+        const SlotView v = slot_view<FMT, IW>(slot, SL, D);
+        const SlotPtrs<FMT, IW> sp = slot_ptrs<FMT, IW>(slot_base + st * SL.bytes, SL, D);
 
         if (!(D.meta & STAGE_COOP)) {
             // empty rows: write 0 (coalesced)
@@ -186,12 +189,12 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
             // non-empty rows: groups of L lanes (L chosen per stage)
             const uint32_t rotw = s & (W - 1);
             switch (D.meta & STAGE_LANES_MASK) {
-                case 0: normal_rows<FMT, COMP, XSMEM, 0>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
-                case 1: normal_rows<FMT, COMP, XSMEM, 1>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
-                case 2: normal_rows<FMT, COMP, XSMEM, 2>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
-                case 3: normal_rows<FMT, COMP, XSMEM, 3>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
-                case 4: normal_rows<FMT, COMP, XSMEM, 4>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
-                default: normal_rows<FMT, COMP, XSMEM, 5>(p, D, v, slot, SL, xs_a, ctid, lane, nct, rotw); break;
+                case 0: normal_rows<FMT, COMP, XSMEM, IW, 0>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
+                case 1: normal_rows<FMT, COMP, XSMEM, IW, 1>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
+                case 2: normal_rows<FMT, COMP, XSMEM, IW, 2>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
+                case 3: normal_rows<FMT, COMP, XSMEM, IW, 3>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
+                case 4: normal_rows<FMT, COMP, XSMEM, IW, 4>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
+                default: normal_rows<FMT, COMP, XSMEM, IW, 5>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
             }
         } else {
             // one chunk of a long row, reduced by every consumer thread
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
                 coop_s = 0.f;
                 coop_c = 0.f;
             }
-            row_dot<FMT, COMP, XSMEM>(v, xs_a, p.x, D.nz0 + ctid, D.nz1, nct, true, coop_s, coop_c);
+            row_dot<FMT, COMP, XSMEM, IW>(v, xs_a, p.x, D.nz0 + ctid, D.nz1, nct, true, coop_s, coop_c);
             if (D.meta & STAGE_LAST) {
                 float sum = coop_s, comp = coop_c;
                 group_reduce<COMP>(sum, comp, 32);
@@ -234,20 +237,27 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     }
 }
 
-template <int FMT, bool COMP, bool XSMEM>
+template <int FMT, bool COMP, bool XSMEM, uint32_t IW>
 cudaError_t launch_t(const dose_matrix* A, const SpmvParams& p, size_t smem, cudaStream_t s) {
-    auto k = spmv_kernel<FMT, COMP, XSMEM>;
+    auto k = spmv_kernel<FMT, COMP, XSMEM, IW>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<A->fwd.grid, 32 * (p.cwarps + 1), smem, s>>>(p);
     return cudaGetLastError();
 }
 
+template <int FMT, uint32_t IW>
+cudaError_t launch_iw(const dose_matrix* A, const SpmvParams& p, size_t smem, bool comp, bool xsmem,
+                      cudaStream_t s) {
+    if (comp)
+        return xsmem ? launch_t<FMT, true, true, IW>(A, p, smem, s) : launch_t<FMT, true, false, IW>(A, p, smem, s);
+    return xsmem ? launch_t<FMT, false, true, IW>(A, p, smem, s) : launch_t<FMT, false, false, IW>(A, p, smem, s);
+}
+
 template <int FMT>
-cudaError_t launch_fmt(const dose_matrix* A, const SpmvParams& p, size_t smem, bool comp, bool xsmem,
+cudaError_t launch_fmt(const dose_matrix* A, const SpmvParams& p, size_t smem, bool comp, bool xsmem, bool idx16,
                        cudaStream_t s) {
-    if (comp) return xsmem ? launch_t<FMT, true, true>(A, p, smem, s) : launch_t<FMT, true, false>(A, p, smem, s);
-    return xsmem ? launch_t<FMT, false, true>(A, p, smem, s) : launch_t<FMT, false, false>(A, p, smem, s);
+    return idx16 ? launch_iw<FMT, 2>(A, p, smem, comp, xsmem, s) : launch_iw<FMT, 4>(A, p, smem, comp, xsmem, s);
 }
 
 }  // namespace
@@ -257,15 +267,17 @@ bool spmv_x_in_smem(const dose_matrix* A) { return A->ncols <= kXSmemMaxCols; }
 size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem) {
     const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
     const uint32_t nvec = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
-    const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, false);
-    return kHeaderBytes + (x_in_smem ? round_up(A->ncols * 4, 128) : 0) + (size_t)t.stages * SL.bytes;
+    const uint32_t iw = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;
+    const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, false, iw);
+    return kHeaderBytes + (x_in_smem ? round_up((A->ncols + 1) * 4, 128) : 0) + (size_t)t.stages * SL.bytes;
 }
 
 cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s) {
     if (A->nrows == 0) return cudaSuccess;
     SpmvParams p;
+    const bool idx16 = (A->flags & DOSE_CREATE_U16_INDEX) != 0;
     p.row_ptr = A->row_ptr;
-    p.col = A->col;
+    p.col = idx16 ? static_cast<const void*>(A->col16) : static_cast<const void*>(A->col);
     p.val = A->val;
     p.scale = A->scale;
     p.x = x;
@@ -289,9 +301,10 @@ cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStre
     const size_t smem = spmv_smem_bytes(A, A->fwd.tuning, xsmem);
     const bool comp = (A->flags & DOSE_CREATE_COMPENSATED) != 0;
     switch (A->fmt) {
-        case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, smem, comp, xsmem, s);
-        case DOSE_FMT_BF16: return launch_fmt<DOSE_FMT_BF16>(A, p, smem, comp, xsmem, s);
-        case DOSE_FMT_FP8E4M3_ROWSCALE: return launch_fmt<DOSE_FMT_FP8E4M3_ROWSCALE>(A, p, smem, comp, xsmem, s);
+        case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, smem, comp, xsmem, idx16, s);
+        case DOSE_FMT_BF16: return launch_fmt<DOSE_FMT_BF16>(A, p, smem, comp, xsmem, idx16, s);
+        case DOSE_FMT_FP8E4M3_ROWSCALE:
+            return launch_fmt<DOSE_FMT_FP8E4M3_ROWSCALE>(A, p, smem, comp, xsmem, idx16, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -103,14 +103,14 @@ struct SlotLayout {
 };
 
 __host__ __device__ inline SlotLayout slot_layout(uint32_t tile_nnz, uint32_t tile_rows, uint32_t esize,
-                                                  uint32_t nvec, bool with_rl) {
+                                                  uint32_t nvec, bool with_rl, uint32_t iw = 4) {
     SlotLayout L;
     L.hdr_off = 0;  // StageDesc copy (32 B) + 32 B of per-stage scalars
     L.rp_off = 128;
     L.ne_off = L.rp_off + round_up((tile_rows + 8) * 4, 128);
     L.val_off = L.ne_off + round_up((tile_rows + 16) * 2, 128);
     L.col_off = L.val_off + round_up((tile_nnz + 32) * esize, 128);
-    L.vec_off = L.col_off + round_up((tile_nnz + 8) * 4, 128);
+    L.vec_off = L.col_off + round_up((tile_nnz + 32 / iw) * iw, 128);  // column indices of iw bytes
     L.vec_stride = round_up((tile_rows + 8) * 4, 128);
     L.rl_off = L.vec_off + nvec * L.vec_stride;
     L.bytes = L.rl_off + (with_rl ? round_up(tile_rows * 4, 128) : 0);
@@ -148,14 +148,16 @@ struct ProducerRing {
 // (`dwin`, completion on `dbar[2]`), so the loop never waits on a global load.
 // Slots are `slot_stride` bytes apart (at least SL.bytes).  All waits are
 // bounded; a timeout sets the error word and clears R.ok.
-template <int FMT>
+template <int FMT, uint32_t IW = 4>
 __device__ void produce_stages(ProducerRing& R, const ScheduleView& sched, uint32_t s_begin, uint32_t s_end,
-                               const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                               const uint32_t* __restrict__ row_ptr, const void* __restrict__ col_v,
                                const void* __restrict__ val, const VecSet& vecs, unsigned char* slot_base,
                                const SlotLayout& SL, uint32_t slot_stride, uint64_t* full, uint64_t* empty,
                                uint32_t S, StageDesc* dwin, uint64_t* dbar, uint32_t pf, int* err) {
     using T = typename Fmt<FMT>::T;
     constexpr uint32_t VA = Fmt<FMT>::kAlign;
+    constexpr uint32_t CA = 16 / IW;  // column indices per 16 bytes
+    const unsigned char* col = static_cast<const unsigned char*>(col_v);  // + IW * k
     if (!R.ok || s_begin >= s_end) return;
     uint32_t st = R.st, ph = R.ph, issued = R.issued;
     const uint32_t wb = R.wbase;
@@ -191,9 +193,9 @@ __device__ void produce_stages(ProducerRing& R, const ScheduleView& sched, uint3
         if (w >= w_issued || !have_window(w)) return;
         const StageDesc P = dwin[((wb + w) & 1) * kDescWin + j % kDescWin];
         const uint32_t v_a = P.nz0 & ~(VA - 1), v_n = round_up(P.nz1, VA) - v_a;
-        const uint32_t c_a = P.nz0 & ~3u, c_n = round_up(P.nz1, 4) - c_a;
+        const uint32_t c_a = P.nz0 & ~(CA - 1), c_n = round_up(P.nz1, CA) - c_a;
         if (v_n) dev::bulk_prefetch_l2(static_cast<const T*>(val) + v_a, v_n * (uint32_t)sizeof(T));
-        if (c_n) dev::bulk_prefetch_l2(col + c_a, c_n * 4);
+        if (c_n) dev::bulk_prefetch_l2(col + (size_t)c_a * IW, c_n * IW);
         if (!(P.meta & STAGE_COOP)) {
             const uint32_t rp_a = P.row0 & ~3u;
             dev::bulk_prefetch_l2(row_ptr + rp_a, (round_up(P.row1 + 1, 4) - rp_a) * 4);
@@ -227,10 +229,10 @@ __device__ void produce_stages(ProducerRing& R, const ScheduleView& sched, uint3
         const uint32_t rp_a = D.row0 & ~3u, rp_n = coop ? 0 : round_up(D.row1 + 1, 4) - rp_a;
         const uint32_t ne_a = D.ne0 & ~7u, ne_n = D.ne1 > D.ne0 ? round_up(D.ne1, 8) - ne_a : 0;
         const uint32_t v_a = D.nz0 & ~(VA - 1), v_n = round_up(D.nz1, VA) - v_a;
-        const uint32_t c_a = D.nz0 & ~3u, c_n = round_up(D.nz1, 4) - c_a;
+        const uint32_t c_a = D.nz0 & ~(CA - 1), c_n = round_up(D.nz1, CA) - c_a;
         const uint32_t r_a = D.row0 & ~3u;
         uint32_t vn[kMaxVec];
-        uint32_t bytes = rp_n * 4 + ne_n * 2 + v_n * (uint32_t)sizeof(T) + c_n * 4;
+        uint32_t bytes = rp_n * 4 + ne_n * 2 + v_n * (uint32_t)sizeof(T) + c_n * IW;
         for (uint32_t k = 0; k < vecs.n; ++k) {
             const uint32_t e = min(round_up(D.row1, 4), vecs.lim[k]);
             vn[k] = e > r_a ? e - r_a : 0;
@@ -252,7 +254,7 @@ __device__ void produce_stages(ProducerRing& R, const ScheduleView& sched, uint3
         if (v_n)
             dev::bulk_g2s(buf + SL.val_off, static_cast<const T*>(val) + v_a, v_n * (uint32_t)sizeof(T),
                           &full[st]);
-        if (c_n) dev::bulk_g2s(buf + SL.col_off, col + c_a, c_n * 4, &full[st]);
+        if (c_n) dev::bulk_g2s(buf + SL.col_off, col + (size_t)c_a * IW, c_n * IW, &full[st]);
         for (uint32_t k = 0; k < vecs.n; ++k)
             if (vn[k])
                 dev::bulk_g2s(buf + SL.vec_off + k * SL.vec_stride, vecs.ptr[k] + r_a, vn[k] * 4, &full[st]);
@@ -287,15 +289,15 @@ __device__ __forceinline__ void producer_drain(const ProducerRing& R, uint64_t* 
 }
 
 // The producer of a single-matrix kernel: all of the CTA's stages, then drain.
-template <int FMT>
+template <int FMT, uint32_t IW = 4>
 __device__ void run_producer(const ScheduleView& sched, uint32_t s_begin, uint32_t s_end,
-                             const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                             const uint32_t* __restrict__ row_ptr, const void* __restrict__ col,
                              const void* __restrict__ val, const VecSet& vecs, unsigned char* slot_base,
                              const SlotLayout& SL, uint64_t* full, uint64_t* empty, uint32_t S, StageDesc* dwin,
                              uint64_t* dbar, uint32_t pf, int* err) {
     ProducerRing R;
-    produce_stages<FMT>(R, sched, s_begin, s_end, row_ptr, col, val, vecs, slot_base, SL, SL.bytes, full, empty, S,
-                        dwin, dbar, pf, err);
+    produce_stages<FMT, IW>(R, sched, s_begin, s_end, row_ptr, col, val, vecs, slot_base, SL, SL.bytes, full, empty,
+                            S, dwin, dbar, pf, err);
     producer_drain(R, full, S);
 }
 
@@ -325,77 +327,72 @@ __device__ __forceinline__ StageDesc slot_desc(uint32_t slot) {
 // used directly (32-bit wrap-around arithmetic: only the sums are addresses).
 struct SlotView {
     uint32_t rp;   // + 4 * row
-    uint32_t col;  // + 4 * k
+    uint32_t col;  // + IW * k (IW: bytes per column index, 4 or 2)
     uint32_t val;  // + esize * k
     uint32_t ne;   // + 2 * i, i = position in the stage's list
 };
 
-template <int FMT>
+template <int FMT, uint32_t IW = 4>
 __device__ __forceinline__ SlotView slot_view(uint32_t slot, const SlotLayout& SL, const StageDesc& D) {
     constexpr uint32_t VA = Fmt<FMT>::kAlign;
     constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
+    constexpr uint32_t CA = 16 / IW;  // column indices per 16 bytes
     SlotView v;
     v.rp = slot + SL.rp_off - (D.row0 & ~3u) * 4u;
-    v.col = slot + SL.col_off - (D.nz0 & ~3u) * 4u;
+    v.col = slot + SL.col_off - (D.nz0 & ~(CA - 1)) * IW;
     v.val = slot + SL.val_off - (D.nz0 & ~(VA - 1)) * ES;
     v.ne = slot + SL.ne_off + (D.ne0 & 7u) * 2u;
     return v;
+}
+
+// Column index of entry k of a slot (IW-byte indices).
+template <uint32_t IW>
+__device__ __forceinline__ uint32_t col_at(const SlotView& v, uint32_t k) {
+    return IW == 4 ? dev::lds_u32(v.col + 4 * k) : dev::lds_u16(v.col + 2 * k);
+}
+template <uint32_t IW>
+__device__ __forceinline__ uint32_t col_at_lt(uint32_t k, uint32_t ke, const SlotView& v) {
+    if (IW == 4) return dev::lds_u32_lt(k, ke, v.col + 4 * k);
+    return dev::lds_u16_lt(k, ke, v.col + 2 * k);
+}
+// Column indices of the four entries k .. k + 3 (k a multiple of 4), loaded
+// only when p (zeros otherwise): one 16-byte or 8-byte load.
+template <uint32_t IW>
+__device__ __forceinline__ uint4 col4_if(bool p, const SlotView& v, uint32_t k) {
+    if (IW == 4) return dev::lds_v4_if(p, v.col + 4 * k);
+    const uint2 q = dev::lds_v2_if(p, v.col + 2 * k);
+    return make_uint4(q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16);
 }
 
 // Sum of a[k] * x[col[k]] over k = kb, kb + STEP, ... < ke with four
 // independent FP32 accumulators (combined as (a0 + a1) + (a2 + a3)).  STEP is a
 // compile-time power of two, so successive entries are immediate offsets from
 // two walking shared addresses.
-template <int FMT, uint32_t STEP>
+template <int FMT, uint32_t STEP, uint32_t IW = 4>
 __device__ __forceinline__ float dot_fixed(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke) {
     constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     if (kb < ke) {
         uint32_t n = (ke - kb + STEP - 1) / STEP;  // entries of this lane
-        uint32_t ca = v.col + 4 * kb, va = v.val + ES * kb;
+        uint32_t ca = v.col + IW * kb, va = v.val + ES * kb;
         for (; n >= 4; n -= 4) {
-            const uint32_t c0 = dev::lds_u32(ca), c1 = dev::lds_u32(ca + 4 * STEP);
-            const uint32_t c2 = dev::lds_u32(ca + 8 * STEP), c3 = dev::lds_u32(ca + 12 * STEP);
+            auto ldc = [](uint32_t a) { return IW == 4 ? dev::lds_u32(a) : dev::lds_u16(a); };
+            const uint32_t c0 = ldc(ca), c1 = ldc(ca + IW * STEP);
+            const uint32_t c2 = ldc(ca + 2 * IW * STEP), c3 = ldc(ca + 3 * IW * STEP);
             const float w0 = Fmt<FMT>::lds(va), w1 = Fmt<FMT>::lds(va + ES * STEP);
             const float w2 = Fmt<FMT>::lds(va + 2 * ES * STEP), w3 = Fmt<FMT>::lds(va + 3 * ES * STEP);
             a0 = __fmaf_rn(w0, dev::lds_f32(xs + 4 * c0), a0);
             a1 = __fmaf_rn(w1, dev::lds_f32(xs + 4 * c1), a1);
             a2 = __fmaf_rn(w2, dev::lds_f32(xs + 4 * c2), a2);
             a3 = __fmaf_rn(w3, dev::lds_f32(xs + 4 * c3), a3);
-            ca += 16 * STEP;
+            ca += 4 * IW * STEP;
             va += 4 * ES * STEP;
         }
-        if (n > 0) a0 = __fmaf_rn(Fmt<FMT>::lds(va), dev::lds_f32(xs + 4 * dev::lds_u32(ca)), a0);
-        if (n > 1) a1 = __fmaf_rn(Fmt<FMT>::lds(va + ES * STEP), dev::lds_f32(xs + 4 * dev::lds_u32(ca + 4 * STEP)), a1);
+        auto ldc = [](uint32_t a) { return IW == 4 ? dev::lds_u32(a) : dev::lds_u16(a); };
+        if (n > 0) a0 = __fmaf_rn(Fmt<FMT>::lds(va), dev::lds_f32(xs + 4 * ldc(ca)), a0);
+        if (n > 1) a1 = __fmaf_rn(Fmt<FMT>::lds(va + ES * STEP), dev::lds_f32(xs + 4 * ldc(ca + IW * STEP)), a1);
         if (n > 2)
-            a2 = __fmaf_rn(Fmt<FMT>::lds(va + 2 * ES * STEP), dev::lds_f32(xs + 4 * dev::lds_u32(ca + 8 * STEP)), a2);
-    }
-    return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
-}
-
-// Branch-free form of dot_fixed: `iters` (equal for the whole warp) unrolled
-// steps of four entries per lane; entries at or beyond ke are masked by
-// predicated loads that give a = 0 and x = 0, so they add exactly nothing.
-template <int FMT, uint32_t STEP>
-__device__ __forceinline__ float dot_uniform(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke,
-                                             uint32_t iters) {
-    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    uint32_t k = kb, ca = v.col + 4 * kb, va = v.val + ES * kb;
-    for (uint32_t it = 0; it < iters; ++it) {
-        const uint32_t k1 = k + STEP, k2 = k + 2 * STEP, k3 = k + 3 * STEP;
-        const uint32_t c0 = dev::lds_u32_lt(k, ke, ca), c1 = dev::lds_u32_lt(k1, ke, ca + 4 * STEP);
-        const uint32_t c2 = dev::lds_u32_lt(k2, ke, ca + 8 * STEP), c3 = dev::lds_u32_lt(k3, ke, ca + 12 * STEP);
-        const float w0 = Fmt<FMT>::lds_lt(k, ke, va), w1 = Fmt<FMT>::lds_lt(k1, ke, va + ES * STEP);
-        const float w2 = Fmt<FMT>::lds_lt(k2, ke, va + 2 * ES * STEP);
-        const float w3 = Fmt<FMT>::lds_lt(k3, ke, va + 3 * ES * STEP);
-        a0 = __fmaf_rn(w0, dev::lds_f32_lt(k, ke, xs + 4 * c0), a0);
-        a1 = __fmaf_rn(w1, dev::lds_f32_lt(k1, ke, xs + 4 * c1), a1);
-        a2 = __fmaf_rn(w2, dev::lds_f32_lt(k2, ke, xs + 4 * c2), a2);
-        a3 = __fmaf_rn(w3, dev::lds_f32_lt(k3, ke, xs + 4 * c3), a3);
-        k += 4 * STEP;
-        ca += 16 * STEP;
-        va += 4 * ES * STEP;
+            a2 = __fmaf_rn(Fmt<FMT>::lds(va + 2 * ES * STEP), dev::lds_f32(xs + 4 * ldc(ca + 2 * IW * STEP)), a2);
     }
     return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
 }
@@ -483,36 +480,69 @@ __device__ __forceinline__ void scatter_group(int off, int len, uint32_t gw, con
         : "memory");
 }
 
-// Vectorised form: lane li of an L-lane group takes the aligned chunks of four
-// consecutive entries starting at (kb & ~3) + 4 li, stepping 4L; one 16-byte
-// load brings four column indices and one 8-byte (u16/bf16) or 4-byte (fp8)
-// load their values.  Entries outside [kb, ke) are masked: their x is not
-// loaded and they add nothing.  `iters` is the same for the whole warp.
-// Chunks never leave the slot: [kb & ~3, round_up(ke, 4)) lies inside the
-// stage's copied slices.
-template <int FMT, uint32_t L>
-__device__ __forceinline__ float dot_vec(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke, uint32_t li,
-                                         uint32_t iters) {
-    constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    uint32_t k = (kb & ~3u) + 4 * li;
-    for (uint32_t it = 0; it < iters; ++it, k += 4 * L) {
-        const bool in = k < ke;
-        const uint4 c = dev::lds_v4_if(in, v.col + 4 * k);
-        float w[4];
-        Fmt<FMT>::lds4(in, v.val + ES * k, w);
-        const bool m0 = in && k >= kb, m1 = in && k + 1 >= kb && k + 1 < ke;
-        const bool m2 = in && k + 2 >= kb && k + 2 < ke, m3 = in && k + 3 >= kb && k + 3 < ke;
-        a0 = __fmaf_rn(m0 ? w[0] : 0.f, dev::lds_f32_if(m0, xs + 4 * c.x), a0);
-        a1 = __fmaf_rn(m1 ? w[1] : 0.f, dev::lds_f32_if(m1, xs + 4 * c.y), a1);
-        a2 = __fmaf_rn(m2 ? w[2] : 0.f, dev::lds_f32_if(m2, xs + 4 * c.z), a2);
-        a3 = __fmaf_rn(m3 ? w[3] : 0.f, dev::lds_f32_if(m3, xs + 4 * c.w), a3);
+// Plain typed pointers to a slot's column indices and values, indexed by the
+// global entry index (the slot holds [nz0 & ~(16/IW - 1), ...) and
+// [nz0 & ~(kAlign - 1), ...)).
+template <int FMT, uint32_t IW>
+struct SlotPtrs {
+    const void* col;
+    const typename Fmt<FMT>::T* val;
+};
+template <int FMT, uint32_t IW>
+__device__ __forceinline__ SlotPtrs<FMT, IW> slot_ptrs(const unsigned char* slotp, const SlotLayout& SL,
+                                                       const StageDesc& D) {
+    using T = typename Fmt<FMT>::T;
+    SlotPtrs<FMT, IW> q;
+    q.col = slotp + SL.col_off - (size_t)(D.nz0 & ~(16 / IW - 1)) * IW;
+    q.val = reinterpret_cast<const T*>(slotp + SL.val_off) - (D.nz0 & ~(Fmt<FMT>::kAlign - 1));
+    return q;
+}
+
+// Lane li of an L-lane group takes the groups of four consecutive entries at
+// (kb & ~3) + 4 li + 4 L s, `iters` steps (the same for the whole warp).  A
+// group is loaded whole (one 16- or 8-byte load of indices, one of values);
+// a group past the row's end loads the row's first group instead (always in
+// the slot), and every entry outside [kb, ke) reads x at the zero element zc
+// with weight 0, so it adds exactly nothing.  Plain typed shared-memory loads
+// (the slot's data were released by an mbarrier wait, a compiler barrier), so
+// the compiler may overlap steps.
+template <int FMT, uint32_t L, uint32_t IW>
+__device__ __forceinline__ float dot_vec_p(const SlotPtrs<FMT, IW>& sp, const float* __restrict__ xsp, uint32_t zc,
+                                           uint32_t kb, uint32_t ke, uint32_t li, uint32_t iters) {
+    using T = typename Fmt<FMT>::T;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int len = (int)(ke - kb);
+    const uint32_t kb4 = kb & ~3u;
+    int off = (int)(4 * li) - (int)(kb & 3u);
+    uint32_t k4 = kb4 + 4 * li;
+    for (uint32_t it = 0; it < iters; ++it, off += 4 * L, k4 += 4 * L) {
+        const uint32_t kg = off < len ? k4 : kb4;
+        uint32_t c[4];
+        if (IW == 4) {
+            const uint4 cc = *reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(sp.col) + kg);
+            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+        } else {
+            const uint2 cc = *reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(sp.col) + kg);
+            c[0] = cc.x & 0xFFFFu; c[1] = cc.x >> 16; c[2] = cc.y & 0xFFFFu; c[3] = cc.y >> 16;
+        }
+        float a[4];
+        if (sizeof(T) == 2) {
+            const uint2 qv = *reinterpret_cast<const uint2*>(sp.val + kg);
+            Fmt<FMT>::dec4(qv.x, qv.y, a);
+        } else {
+            Fmt<FMT>::dec4(*reinterpret_cast<const uint32_t*>(sp.val + kg), 0u, a);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool m = (uint32_t)(off + u) < (uint32_t)len;
+            acc[u] = __fmaf_rn(m ? a[u] : 0.f, xsp[m ? c[u] : zc], acc[u]);
+        }
     }
-    return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
+    return __fadd_rn(__fadd_rn(acc[0], acc[1]), __fadd_rn(acc[2], acc[3]));
 }
 
 // Same with a run-time stride (the whole-CTA reduction of long rows).
-template <int FMT>
+template <int FMT, uint32_t IW = 4>
 __device__ __forceinline__ float dot_strided(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke,
                                              uint32_t step) {
     constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
@@ -520,8 +550,8 @@ __device__ __forceinline__ float dot_strided(const SlotView& v, uint32_t xs, uin
     uint32_t k = kb;
     for (; k + 3 * step < ke; k += 4 * step) {
         const uint32_t k1 = k + step, k2 = k + 2 * step, k3 = k + 3 * step;
-        const uint32_t c0 = dev::lds_u32(v.col + 4 * k), c1 = dev::lds_u32(v.col + 4 * k1);
-        const uint32_t c2 = dev::lds_u32(v.col + 4 * k2), c3 = dev::lds_u32(v.col + 4 * k3);
+        const uint32_t c0 = col_at<IW>(v, k), c1 = col_at<IW>(v, k1);
+        const uint32_t c2 = col_at<IW>(v, k2), c3 = col_at<IW>(v, k3);
         const float w0 = Fmt<FMT>::lds(v.val + ES * k), w1 = Fmt<FMT>::lds(v.val + ES * k1);
         const float w2 = Fmt<FMT>::lds(v.val + ES * k2), w3 = Fmt<FMT>::lds(v.val + ES * k3);
         a0 = __fmaf_rn(w0, dev::lds_f32(xs + 4 * c0), a0);
@@ -529,24 +559,24 @@ __device__ __forceinline__ float dot_strided(const SlotView& v, uint32_t xs, uin
         a2 = __fmaf_rn(w2, dev::lds_f32(xs + 4 * c2), a2);
         a3 = __fmaf_rn(w3, dev::lds_f32(xs + 4 * c3), a3);
     }
-    if (k < ke) a0 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * dev::lds_u32(v.col + 4 * k)), a0);
+    if (k < ke) a0 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * col_at<IW>(v, k)), a0);
     k += step;
-    if (k < ke) a1 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * dev::lds_u32(v.col + 4 * k)), a1);
+    if (k < ke) a1 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * col_at<IW>(v, k)), a1);
     k += step;
-    if (k < ke) a2 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * dev::lds_u32(v.col + 4 * k)), a2);
+    if (k < ke) a2 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * col_at<IW>(v, k)), a2);
     return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
 }
 
 // Compensated version (Dot2 of Ogita, Rump and Oishi, 2005): returns (s, c)
 // with s + c the dot product to about twice the working precision.
-template <int FMT>
+template <int FMT, uint32_t IW = 4>
 __device__ __forceinline__ void dot_strided_comp(const SlotView& v, uint32_t xs, const float* __restrict__ xg,
                                                  bool xsmem, uint32_t kb, uint32_t ke, uint32_t step, float& s,
                                                  float& c) {
     constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
     for (uint32_t k = kb; k < ke; k += step) {
         const float a = Fmt<FMT>::lds(v.val + ES * k);
-        const uint32_t j = dev::lds_u32(v.col + 4 * k);
+        const uint32_t j = col_at<IW>(v, k);
         const float xv = xsmem ? dev::lds_f32(xs + 4 * j) : __ldg(xg + j);
         float pr, ep, t, es;
         dev::two_prod(a, xv, pr, ep);
@@ -557,7 +587,7 @@ __device__ __forceinline__ void dot_strided_comp(const SlotView& v, uint32_t xs,
 }
 
 // Plain sum with x read from global memory (x too large for shared memory).
-template <int FMT>
+template <int FMT, uint32_t IW = 4>
 __device__ __forceinline__ float dot_strided_gx(const SlotView& v, const float* __restrict__ xg, uint32_t kb,
                                                 uint32_t ke, uint32_t step) {
     constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
@@ -565,12 +595,12 @@ __device__ __forceinline__ float dot_strided_gx(const SlotView& v, const float* 
     uint32_t k = kb;
     for (; k + step < ke; k += 2 * step) {
         const uint32_t k1 = k + step;
-        const uint32_t c0 = dev::lds_u32(v.col + 4 * k), c1 = dev::lds_u32(v.col + 4 * k1);
+        const uint32_t c0 = col_at<IW>(v, k), c1 = col_at<IW>(v, k1);
         const float w0 = Fmt<FMT>::lds(v.val + ES * k), w1 = Fmt<FMT>::lds(v.val + ES * k1);
         a0 = __fmaf_rn(w0, __ldg(xg + c0), a0);
         a1 = __fmaf_rn(w1, __ldg(xg + c1), a1);
     }
-    if (k < ke) a0 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), __ldg(xg + dev::lds_u32(v.col + 4 * k)), a0);
+    if (k < ke) a0 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), __ldg(xg + col_at<IW>(v, k)), a0);
     return __fadd_rn(a0, a1);
 }
 

@@ -106,6 +106,11 @@ def test_create_rejects_invalid_csr_on_host(lib):
     assert lib.dose_create_matrix(ctypes.byref(d), 0, None, None, ctypes.byref(out)) == 1
     assert lib.dose_create_matrix(None, 0, None, None, ctypes.byref(out)) == 1
     assert lib.dose_create_matrix(ctypes.byref(d), 0x80, None, None, ctypes.byref(out)) == 1
+    # 16-bit column indices need ncols <= 65536
+    d = _desc(nrows=1, ncols=70000, nnz=3, row_ptr=arr([0, 3], np.uint32), col_idx=arr([0, 1, 69999], np.uint32),
+              fmt=0, values_f64=arr([0.5, 1.0, 0.2], np.float64))
+    assert lib.dose_create_matrix(ctypes.byref(d), dose.CREATE_U16_INDEX, None, None, ctypes.byref(out)) == 1
+    assert "65536" in lib.dose_last_error().decode()
     assert lib.dose_destroy(None) == 0
     assert lib.dose_spmv(None, None, None, None) == 1
     assert lib.dose_spmv_batched(None, -1, None, None, 16, None) == 1

@@ -67,6 +67,36 @@ def test_forward_edge_cases(name, fmt):
         A.device_status()
 
 
+@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8"])
+@pytest.mark.parametrize("compensated", [False, True])
+def test_forward_16bit_column_indices(tiny, fmt, compensated):
+    """DOSE_CREATE_U16_INDEX: dose_spmv reads 16-bit column indices; results
+    equal the 32-bit path bitwise (same schedule, same order), the byte model
+    counts 2-byte indices, and the other kernels keep working on the handle."""
+    A32, enc = make(tiny, fmt, compensated=compensated)
+    A16, _ = make(tiny, fmt, compensated=compensated, index16=True)
+    x = _x(tiny.ncols)
+    d16 = A16.spmv(_to(x)).cpu().numpy()
+    fwd_check(d16, oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x))
+    assert np.array_equal(d16.view(np.uint32), A32.spmv(_to(x)).cpu().numpy().view(np.uint32))
+    i16, i32 = A16.info(), A32.info()
+    assert i32["spmv_bytes"] - i16["spmv_bytes"] == 2 * tiny.nnz
+    r = np.random.default_rng(4).normal(size=tiny.nrows).astype(np.float32)
+    assert np.array_equal(A16.adjoint(_to(r)).cpu().numpy(), A32.adjoint(_to(r)).cpu().numpy())
+    A16.device_status()
+
+
+@pytest.mark.parametrize("name", list(edge_case_matrices().keys()))
+def test_forward_16bit_column_indices_edge_cases(name):
+    csr = edge_case_matrices()[name]
+    for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4),
+                   dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16)):
+        A, enc = make(csr, "u16", tuning=tuning, index16=True)
+        x = _x(csr.ncols, seed=5)
+        fwd_check(A.spmv(_to(x)).cpu().numpy(), oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x))
+        A.device_status()
+
+
 @pytest.mark.parametrize("fmt", ["u16", "fp8", "bf16"])
 def test_unit_vectors_reproduce_stored_columns_bit_exact(tiny, fmt):
     A, enc = make(tiny, fmt)
