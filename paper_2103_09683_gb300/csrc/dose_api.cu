@@ -869,7 +869,7 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
     AdjTuning best_a = orig_a;
     if (result == DOSE_OK) {
         float best_a_ms = 1e30f;
-        const uint32_t anz[] = {2048, 4096, 8192};
+        const uint32_t anz[] = {2048, 4096, 5120, 6144, 8192};
         const uint32_t arows[] = {512, 1024, 2048};
         const uint32_t adepth[] = {2, 3, 4, 6};
         const uint32_t afw[] = {4, 8};

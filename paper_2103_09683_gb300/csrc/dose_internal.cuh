@@ -97,9 +97,9 @@ struct ScheduleView {
 
 // Shape of the adjoint / fused kernels (warp specialisation and pipeline).
 struct AdjTuning {
-    uint32_t tile_nnz = 4096;
-    uint32_t tile_rows = 512;
-    uint32_t stages = 4;
+    uint32_t tile_nnz = 5120;
+    uint32_t tile_rows = 1024;
+    uint32_t stages = 3;
     uint32_t forward_warps = 8;   // fused pass: warps computing d, f and r
     uint32_t scatter_warps = 0;   // warps owning gradient accumulators (0 = as many as fit, up to the cap)
     uint32_t l2_prefetch = 8;     // stages prefetched into L2 ahead of the shared-memory ring

@@ -386,7 +386,7 @@ def test_autotune_keeps_parity(tiny, objective_inputs):
     p, w, x = objective_inputs
     A, enc = make(tiny, "u16")
     best = A.autotune(_to(x))
-    assert best["tile_nnz"] in (2048, 4096, 8192) and best["adj_tile_nnz"] in (2048, 4096, 8192)
+    assert best["tile_nnz"] in (2048, 4096, 8192) and best["adj_tile_nnz"] in (2048, 4096, 5120, 6144, 8192)
     assert A.info()["tuning"] == best
     d = A.spmv(_to(x)).cpu().numpy()
     fwd_check(d, oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x))
