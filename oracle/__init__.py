@@ -13,7 +13,8 @@ Paper passages followed:
     arrays (Sec. II-C).
   * Memory-traffic model 6*nnz + 12*nr + 8*nc bytes and 2*nnz flops for the
     half-value / double-vector kernel, giving OI 0.332 for liver beam 1 (Sec. V).
-  * 16-bit stored values with FP32/FP64 vectors (Sec. II-D).
+  * 16-bit stored values with FP32/FP64 vectors (Sec. II-D); IEEE half values
+    with double vectors and double accumulation, the paper's own kernel (Sec. IV).
 The objective, its gradient and the projected-gradient step are the quadratic
 dose objective of the optimisation the paper motivates (Sec. I, Sec. II-A).
 
@@ -36,8 +37,8 @@ _SRC = os.path.join(_HERE, "dose_oracle.c")
 _lock = threading.Lock()
 _lib = None
 
-U16_SCALE, BF16, FP8E4M3_ROWSCALE = 0, 1, 2
-FORMAT_NAMES = {U16_SCALE: "u16", BF16: "bf16", FP8E4M3_ROWSCALE: "fp8"}
+U16_SCALE, BF16, FP8E4M3_ROWSCALE, F16 = 0, 1, 2, 3
+FORMAT_NAMES = {U16_SCALE: "u16", BF16: "bf16", FP8E4M3_ROWSCALE: "fp8", F16: "f16"}
 
 
 def build(force: bool = False) -> str:
@@ -68,6 +69,10 @@ def _load():
                 "oracle_bf16_value": (_F64, [_U16]),
                 "oracle_fp8_e4m3_nearest": (_U8, [_F64]),
                 "oracle_bf16_round": (_U16, [_F64]),
+                "oracle_f16_value": (_F64, [_U16]),
+                "oracle_f16_round": (_U16, [_F64]),
+                "oracle_encode_f16": (ctypes.c_int, [_U64, _P, _P]),
+                "oracle_decode_f16": (None, [_U64, _P, _P]),
                 "oracle_encode_u16": (ctypes.c_int, [_U64, _P, _P, _P]),
                 "oracle_encode_bf16": (ctypes.c_int, [_U64, _P, _P]),
                 "oracle_encode_fp8_rowscale": (ctypes.c_int, [_U32, _P, _P, _P, _P]),
@@ -119,14 +124,22 @@ def bf16_round(v: float) -> int:
     return int(_load().oracle_bf16_round(float(v)))
 
 
+def f16_value(bits: int) -> float:
+    return _load().oracle_f16_value(int(bits))
+
+
+def f16_round(v: float) -> int:
+    return int(_load().oracle_f16_round(float(v)))
+
+
 class Encoded:
     """A CSR matrix in one stored format, plus its FP64 decoded values."""
 
     def __init__(self, fmt, nrows, ncols, row_ptr, col, values, scales, decoded):
         self.fmt, self.nrows, self.ncols = fmt, nrows, ncols
         self.row_ptr, self.col = row_ptr, col
-        self.values = values      # uint16 (u16 codes or bf16 bits) or uint8 (e4m3 codes)
-        self.scales = scales      # float32[1] (u16), float32[nrows] (fp8) or None (bf16)
+        self.values = values      # uint16 (u16 codes, bf16 or f16 bits) or uint8 (e4m3 codes)
+        self.scales = scales      # float32[1] (u16), float32[nrows] (fp8) or None (bf16, f16)
         self.decoded = decoded    # float64[nnz], exact value of each stored entry
 
     @property
@@ -154,6 +167,11 @@ def encode(csr, fmt: int) -> Encoded:
         lib.oracle_encode_bf16(nnz, _ptr(v), _ptr(q))
         lib.oracle_decode_bf16(nnz, _ptr(q), _ptr(dec))
         return Encoded(fmt, csr.nrows, csr.ncols, rp, col, q, None, dec)
+    if fmt == F16:
+        q = np.empty(nnz, dtype=np.uint16)
+        lib.oracle_encode_f16(nnz, _ptr(v), _ptr(q))
+        lib.oracle_decode_f16(nnz, _ptr(q), _ptr(dec))
+        return Encoded(fmt, csr.nrows, csr.ncols, rp, col, q, None, dec)
     if fmt == FP8E4M3_ROWSCALE:
         q = np.empty(nnz, dtype=np.uint8)
         s = np.empty(csr.nrows, dtype=np.float32)
@@ -176,6 +194,9 @@ def decode(fmt, nrows, row_ptr, values, scales) -> np.ndarray:
     elif fmt == BF16:
         q = _c(values, np.uint16)
         lib.oracle_decode_bf16(nnz, _ptr(q), _ptr(dec))
+    elif fmt == F16:
+        q = _c(values, np.uint16)
+        lib.oracle_decode_f16(nnz, _ptr(q), _ptr(dec))
     elif fmt == FP8E4M3_ROWSCALE:
         q = _c(values, np.uint8)
         s = _c(scales, np.float32)

@@ -23,6 +23,9 @@
  *   BF16      : bfloat16 (1 sign, 8 exponent, 7 fraction bits), a = bf16 value
  *   FP8E4M3   : OCP FP8 E4M3 (bias 7, no infinities, S.1111.111 = NaN,
  *               subnormals m/8 * 2^-6) with one FP32 scale per row, a = s_r*e4m3(q)
+ *   F16       : IEEE 754 binary16 (1 sign, 5 exponent with bias 15, 10 fraction
+ *               bits, subnormals m/1024 * 2^-14), a = half value (the paper's
+ *               "Half" storage, Sec. IV)
  * Encoders follow the readings: u16 s = fl32(max v / 65535), q = RNE(v/s)
  * clamped to [0,65535]; BF16 = round-to-nearest-even of the FP64 value; FP8
  * s_r = fl32(row max / 448) (1 for empty or all-zero rows), q = nearest E4M3
@@ -55,6 +58,45 @@ double oracle_bf16_value(uint16_t bits) {
     float f;
     memcpy(&f, &u, sizeof f);
     return (double)f;
+}
+
+/* Value of an IEEE binary16 bit pattern from its fields. */
+double oracle_f16_value(uint16_t bits) {
+    int sign = (bits >> 15) & 1;
+    int e = (bits >> 10) & 0x1F;
+    int m = bits & 0x3FF;
+    double v;
+    if (e == 0x1F) return m ? NAN : (sign ? -INFINITY : INFINITY);
+    if (e == 0)
+        v = ldexp((double)m / 1024.0, -14);          /* subnormal */
+    else
+        v = ldexp(1.0 + (double)m / 1024.0, e - 15); /* normal */
+    return sign ? -v : v;
+}
+
+/* Round-to-nearest-even of v to binary16 (11 significant bits; quantum 2^-24
+ * below 2^-14; magnitudes from 65520 up round to infinity). */
+uint16_t oracle_f16_round(double v) {
+    if (v != v) return 0x7E00;
+    double a = fabs(v);
+    uint16_t sign = (v < 0 || (v == 0 && signbit(v))) ? 0x8000 : 0;
+    double q;
+    if (a == 0) {
+        q = 0;
+    } else if (a < ldexp(1.0, -14)) {
+        q = nearbyint(ldexp(a, 24)) * ldexp(1.0, -24);   /* subnormal quantum 2^-24 */
+    } else {
+        int ex;
+        double m = frexp(a, &ex);                         /* a = m 2^ex, m in [0.5,1) */
+        q = ldexp(nearbyint(ldexp(m, 11)), ex - 11);       /* 11 significant bits */
+    }
+    if (q >= 65536.0) return sign | 0x7C00;                /* overflow: infinity */
+    if (q < ldexp(1.0, -14)) return sign | (uint16_t)(q * 16777216.0); /* subnormal or zero */
+    int ex;
+    double m = frexp(q, &ex);                              /* q = m 2^ex, m in [0.5,1) */
+    uint16_t e = (uint16_t)(ex - 1 + 15);
+    uint16_t f = (uint16_t)((m * 2.0 - 1.0) * 1024.0);
+    return sign | (uint16_t)(e << 10) | f;
 }
 
 /* Nearest E4M3 code to a non-negative finite t, searched over every finite
@@ -119,6 +161,11 @@ int oracle_encode_bf16(uint64_t nnz, const double* v, uint16_t* out) {
     return 0;
 }
 
+int oracle_encode_f16(uint64_t nnz, const double* v, uint16_t* out) {
+    for (uint64_t k = 0; k < nnz; ++k) out[k] = oracle_f16_round(v[k]);
+    return 0;
+}
+
 /* FP8 E4M3 with one FP32 scale per row: returns 0, or -1 for a negative/NaN value. */
 int oracle_encode_fp8_rowscale(uint32_t nrows, const uint32_t* row_ptr, const double* v,
                                float* row_scale, uint8_t* q) {
@@ -143,6 +190,10 @@ void oracle_decode_u16(uint64_t nnz, const uint16_t* q, float scale, double* a) 
 
 void oracle_decode_bf16(uint64_t nnz, const uint16_t* bits, double* a) {
     for (uint64_t k = 0; k < nnz; ++k) a[k] = oracle_bf16_value(bits[k]);
+}
+
+void oracle_decode_f16(uint64_t nnz, const uint16_t* bits, double* a) {
+    for (uint64_t k = 0; k < nnz; ++k) a[k] = oracle_f16_value(bits[k]);
 }
 
 void oracle_decode_fp8_rowscale(uint32_t nrows, const uint32_t* row_ptr, const uint8_t* q,

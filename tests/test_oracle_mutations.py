@@ -34,6 +34,9 @@ MUTATIONS = {
     "fp8_ties_not_even": ("if (dd < bestd || (dd == bestd && (c & 1) == 0 && (best & 1) == 1)) {",
                           "if (dd < bestd) {"),
     "bf16_truncates": ("q = ldexp(nearbyint(ldexp(m, 8)), ex - 8);", "q = ldexp(floor(ldexp(m, 8)), ex - 8);"),
+    "f16_truncates": ("q = ldexp(nearbyint(ldexp(m, 11)), ex - 11);", "q = ldexp(floor(ldexp(m, 11)), ex - 11);"),
+    "f16_wrong_bias": ("v = ldexp(1.0 + (double)m / 1024.0, e - 15);", "v = ldexp(1.0 + (double)m / 1024.0, e - 14);"),
+    "f16_subnormal_quantum": ("v = ldexp((double)m / 1024.0, -14);", "v = ldexp((double)m / 1024.0, -15);"),
     "u16_round_half_up": ("double t = nearbyint(v[k] / (double)s);", "double t = floor(v[k] / (double)s + 0.5);"),
     "u16_scale_off_by_one": ("float s = vmax > 0.0 ? (float)(vmax / 65535.0) : 1.0f;",
                              "float s = vmax > 0.0 ? (float)(vmax / 65536.0) : 1.0f;"),

@@ -232,6 +232,46 @@ def test_bf16_round_matches_torch_and_neighbour_search():
             assert err < e2 or (err == e2 and c % 2 == 0)
 
 
+def test_f16_code_table_matches_numpy():
+    """Every binary16 bit pattern decodes to numpy's float16 value."""
+    vals = np.array([oracle.f16_value(c) for c in range(65536)])
+    ref = np.arange(65536, dtype=np.uint32).astype(np.uint16).view(np.float16).astype(np.float64)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(vals), nan) and np.array_equal(vals[~nan], ref[~nan])
+    assert np.signbit(vals[0x8000]) and not np.signbit(vals[0])
+    assert vals[0x3C00] == 1.0 and vals[0x7BFF] == 65504.0 and vals[0x0001] == 2.0 ** -24
+    assert vals[0x0400] == 2.0 ** -14 and vals[0x03FF] == 1023 * 2.0 ** -24
+
+
+def test_f16_round_matches_numpy_rne():
+    rng = np.random.default_rng(17)
+    mids = []   # exact halfway points between neighbouring finite halves: ties
+    for c in list(range(0, 0x7BFF, 97)) + [0x03FF, 0x0400, 0x3BFF, 0x3C00, 0x7BFE]:
+        a = np.uint16(c).view(np.float16).astype(np.float64)
+        b = np.uint16(c + 1).view(np.float16).astype(np.float64)
+        mids.append((a + b) / 2)
+    v = np.concatenate([rng.uniform(0, 1, 3000), rng.uniform(0, 1e-4, 1000), rng.uniform(0, 7e4, 500),
+                        -rng.uniform(0, 10, 200), mids,
+                        [0.0, -0.0, 65504.0, 65519.99, 65520.0, 1e9, 2.0 ** -25, 3 * 2.0 ** -26,
+                         2.0 ** -26, 2.0 ** -14 - 2.0 ** -25]])
+    ours = np.array([oracle.f16_round(float(t)) for t in v], dtype=np.uint16)
+    with np.errstate(over="ignore"):
+        ref = v.astype(np.float16).view(np.uint16)   # numpy rounds FP64 to half directly, ties to even
+    assert np.array_equal(ours, ref)
+    assert oracle.f16_round(65520.0) == 0x7C00 and oracle.f16_round(-1e9) == 0xFC00
+
+
+def test_f16_encoding_error_bound():
+    A = dosegen.random_csr(60, 30, seed=18, density=0.3)
+    enc = oracle.encode(A, oracle.F16)
+    assert enc.scales is None and enc.values.dtype == np.uint16
+    assert np.array_equal(enc.values, A.val.astype(np.float16).view(np.uint16))
+    normal = A.val >= 2.0 ** -14
+    # 11 significant bits: unit roundoff 2^-11 for normal values, 2^-25 absolute below
+    assert np.all(np.abs(enc.decoded - A.val)[normal] <= 2.0 ** -11 * A.val[normal])
+    assert np.all(np.abs(enc.decoded - A.val)[~normal] <= 2.0 ** -25)
+
+
 def test_u16_encoding_nearest_code():
     A = dosegen.random_csr(100, 50, seed=14, density=0.3)
     enc = oracle.encode(A, oracle.U16_SCALE)
