@@ -24,7 +24,8 @@ from . import _build
 __all__ = ["build", "load", "DoseMatrix", "DoseError", "FORMATS", "spmv_batched", "adjoint_noalloc", "dose_spmv",
            "QuadraticDoseObjective", "pg_solve", "PGSolver", "encode_host", "library_path", "selftest_bounded_wait"]
 
-FORMATS = {"u16": 0, "bf16": 1, "fp8": 2}
+FORMATS = {"u16": 0, "bf16": 1, "fp8": 2, "f16": 3}
+_NO_SCALES = ("bf16", "f16")
 CREATE_COMPENSATED = 0x1
 CREATE_U16_INDEX = 0x2
 _STATUS = {0: "DOSE_OK", 1: "DOSE_ERR_INVALID_ARG", 2: "DOSE_ERR_OOM", 3: "DOSE_ERR_CUDA",
@@ -171,7 +172,7 @@ def encode_host(fmt: str, row_ptr: np.ndarray, values_f64: np.ndarray):
     scales = np.empty(nrows if fmt == "fp8" else 1, dtype=np.float32)
     _check(lib.dose_encode_host(f, nrows, rp.ctypes.data, v.size, v.ctypes.data if v.size else None,
                                 codes.ctypes.data if codes.size else None, scales.ctypes.data))
-    return codes, (None if fmt == "bf16" else scales)
+    return codes, (None if fmt in _NO_SCALES else scales)
 
 
 class DoseMatrix:
@@ -222,14 +223,14 @@ class DoseMatrix:
                 raise ValueError("device CSR needs encoded values")
             vt = torch.uint8 if fmt == "fp8" else torch.int16
             d.values = dev(values if values.dtype == vt else values.view(vt), vt, "values")
-            if fmt != "bf16":
+            if fmt not in _NO_SCALES:
                 d.scales = dev(scales, torch.float32, "scales")
         else:
             d.row_ptr = host(row_ptr, np.uint32)
             d.col_idx = host(col, np.uint32)
             if values is not None:
                 d.values = host(values, vdt_np)
-                if fmt != "bf16":
+                if fmt not in _NO_SCALES:
                     d.scales = host(np.asarray(scales, dtype=np.float32).reshape(-1), np.float32)
             elif values_f64 is not None:
                 d.values_f64 = host(values_f64, np.float64)

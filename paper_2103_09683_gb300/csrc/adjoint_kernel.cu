@@ -514,6 +514,10 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
                 e = quad ? launch_adj_t<DOSE_FMT_BF16, ADJ_MODE_QUADRATIC>(A, prm, smem, s)
                          : launch_adj_t<DOSE_FMT_BF16, ADJ_MODE_ADJOINT>(A, prm, smem, s);
                 break;
+            case DOSE_FMT_F16:
+                e = quad ? launch_adj_t<DOSE_FMT_F16, ADJ_MODE_QUADRATIC>(A, prm, smem, s)
+                         : launch_adj_t<DOSE_FMT_F16, ADJ_MODE_ADJOINT>(A, prm, smem, s);
+                break;
             case DOSE_FMT_FP8E4M3_ROWSCALE:
                 e = quad ? launch_adj_t<DOSE_FMT_FP8E4M3_ROWSCALE, ADJ_MODE_QUADRATIC>(A, prm, smem, s)
                          : launch_adj_t<DOSE_FMT_FP8E4M3_ROWSCALE, ADJ_MODE_ADJOINT>(A, prm, smem, s);

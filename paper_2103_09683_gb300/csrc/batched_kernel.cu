@@ -292,6 +292,10 @@ __global__ void __launch_bounds__(32 * (kSpmmConsumerWarps + 1), 1) spmm_staged_
                         produce_stages<DOSE_FMT_BF16>(R, it.sched, sb, se, it.row_ptr, it.col, it.val, vecs, slot_base,
                                                       SL, p.slot_stride, full, empty, S, dwin, dbar, p.l2pf, p.err);
                         break;
+                    case DOSE_FMT_F16:  // same bytes as BF16: only the decode differs
+                        produce_stages<DOSE_FMT_BF16>(R, it.sched, sb, se, it.row_ptr, it.col, it.val, vecs, slot_base,
+                                                      SL, p.slot_stride, full, empty, S, dwin, dbar, p.l2pf, p.err);
+                        break;
                     default:
                         produce_stages<DOSE_FMT_FP8E4M3_ROWSCALE>(R, it.sched, sb, se, it.row_ptr, it.col, it.val,
                                                                   vecs, slot_base, SL, p.slot_stride, full, empty, S,
@@ -340,6 +344,10 @@ __global__ void __launch_bounds__(32 * (kSpmmConsumerWarps + 1), 1) spmm_staged_
                 case DOSE_FMT_BF16:
                     spmm_stage<DOSE_FMT_BF16, NQ>(it, SL, slotp, slot, xw4, xw0, wlo, p.nvec, p.vec4 != 0, ctid, lane,
                                                   cw, nct, r);
+                    break;
+                case DOSE_FMT_F16:
+                    spmm_stage<DOSE_FMT_F16, NQ>(it, SL, slotp, slot, xw4, xw0, wlo, p.nvec, p.vec4 != 0, ctid, lane,
+                                                 cw, nct, r);
                     break;
                 default:
                     spmm_stage<DOSE_FMT_FP8E4M3_ROWSCALE, NQ>(it, SL, slotp, slot, xw4, xw0, wlo, p.nvec,
@@ -395,7 +403,7 @@ __device__ __forceinline__ void spmm_row(const BatchItem& it, uint32_t row, uint
         float s = 1.0f;
         if (FMT == DOSE_FMT_U16_SCALE) s = it.scale;
         if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) s = __ldg(it.row_scale + row);
-        it.D[(size_t)row * nvec + v] = FMT == DOSE_FMT_BF16 ? acc : __fmul_rn(s, acc);
+        it.D[(size_t)row * nvec + v] = (FMT == DOSE_FMT_BF16 || FMT == DOSE_FMT_F16) ? acc : __fmul_rn(s, acc);
     }
 }
 
@@ -425,6 +433,7 @@ __global__ void __launch_bounds__(256) spmm_global_kernel(const __grid_constant_
             switch (it.fmt) {
                 case DOSE_FMT_U16_SCALE: spmm_row<DOSE_FMT_U16_SCALE>(it, row, v, p.nvec); break;
                 case DOSE_FMT_BF16: spmm_row<DOSE_FMT_BF16>(it, row, v, p.nvec); break;
+                case DOSE_FMT_F16: spmm_row<DOSE_FMT_F16>(it, row, v, p.nvec); break;
                 default: spmm_row<DOSE_FMT_FP8E4M3_ROWSCALE>(it, row, v, p.nvec); break;
             }
         }

@@ -80,6 +80,33 @@ static uint8_t encode_e4m3(double t) {
     return code > 0x7E ? (uint8_t)0x7E : (uint8_t)code;
 }
 
+// IEEE binary16 bits of v, rounded to nearest with ties to even, from the
+// binary64 fields of v: the 53-bit significand is shifted down to the half's
+// quantum (2^(E-10) for normal halves, 2^-24 below 2^-14) and the dropped bits
+// decide the rounding; a carry out of the significand moves to the next
+// exponent, and past the largest finite half (65504) to infinity.
+static uint16_t encode_f16(double v) {
+    uint64_t b;
+    std::memcpy(&b, &v, 8);
+    const uint16_t sign = (uint16_t)((b >> 48) & 0x8000u);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const uint64_t frac = b & ((1ull << 52) - 1);
+    if (e == 0x7FF) return sign | (frac ? 0x7E00 : 0x7C00);
+    if (e == 0) return sign;  // below 2^-1022: far under half the smallest half
+    const int E = e - 1023;
+    if (E > 15) return sign | 0x7C00;
+    const uint64_t sig = frac | (1ull << 52);                 // v = sig * 2^(E - 52)
+    const int qexp = E >= -14 ? E - 10 : -24;                  // exponent of the half's quantum
+    const int shift = qexp - (E - 52);                         // 42 for normal halves
+    if (shift > 63) return sign;
+    uint64_t keep = sig >> shift;
+    const uint64_t rem = sig & ((1ull << shift) - 1), halfway = 1ull << (shift - 1);
+    if (rem > halfway || (rem == halfway && (keep & 1))) ++keep;
+    if (E < -14) return sign | (uint16_t)keep;                 // subnormal (1024 = smallest normal)
+    const uint32_t bits = ((uint32_t)(E + 15) << 10) + (uint32_t)(keep - 1024);  // carry moves the exponent
+    return sign | (uint16_t)(bits >= 0x7C00u ? 0x7C00u : bits);
+}
+
 static dose_status encode(dose_format fmt, uint32_t nrows, const uint32_t* row_ptr, uint64_t nnz,
                           const double* v, void* codes, float* scales) {
     for (uint64_t k = 0; k < nnz; ++k)
@@ -101,6 +128,11 @@ static dose_status encode(dose_format fmt, uint32_t nrows, const uint32_t* row_p
     if (fmt == DOSE_FMT_BF16) {
         uint16_t* q = static_cast<uint16_t*>(codes);
         for (uint64_t k = 0; k < nnz; ++k) q[k] = encode_bf16(v[k]);
+        return DOSE_OK;
+    }
+    if (fmt == DOSE_FMT_F16) {
+        uint16_t* q = static_cast<uint16_t*>(codes);
+        for (uint64_t k = 0; k < nnz; ++k) q[k] = encode_f16(v[k]);
         return DOSE_OK;
     }
     if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {
@@ -483,7 +515,8 @@ const char* dose_version(void) { return "libdose 0.1 (sm_103a)"; }
 dose_status dose_encode_host(dose_format fmt, uint32_t nrows, const uint32_t* row_ptr, uint64_t nnz,
                              const double* values_f64, void* codes, float* scales) {
     if ((nnz && (!values_f64 || !codes)) || !row_ptr) return invalid("dose_encode_host: null pointer");
-    if (fmt != DOSE_FMT_BF16 && !scales) return invalid("dose_encode_host: scales needed for this format");
+    if (fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_F16 && !scales)
+        return invalid("dose_encode_host: scales needed for this format");
     return encode(fmt, nrows, row_ptr, nnz, values_f64, codes, scales);
 }
 
@@ -495,7 +528,8 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if ((flags & DOSE_CREATE_U16_INDEX) && desc->ncols > 65536u)
         return invalid("DOSE_CREATE_U16_INDEX needs ncols <= 65536 (16-bit column indices)");
     const dose_format fmt = desc->fmt;
-    if (fmt != DOSE_FMT_U16_SCALE && fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_FP8E4M3_ROWSCALE)
+    if (fmt != DOSE_FMT_U16_SCALE && fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_FP8E4M3_ROWSCALE &&
+        fmt != DOSE_FMT_F16)
         return invalid("dose_create_matrix: unknown format");
     if (desc->nnz >= (1ull << 32)) return invalid("nnz must be < 2^32 (uint32 row pointers)");
     if (desc->nrows == 0xFFFFFFFFu) return invalid("nrows must be < 2^32 - 1");
@@ -503,7 +537,8 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if (desc->nnz && !desc->col_idx) return invalid("col_idx is NULL");
     if (desc->on_device && desc->values_f64) return invalid("values_f64 must be host memory (on_device=0)");
     if (!desc->values && !desc->values_f64 && desc->nnz) return invalid("neither values nor values_f64 given");
-    if (desc->values && fmt != DOSE_FMT_BF16 && !desc->scales) return invalid("scales are NULL for this format");
+    if (desc->values && fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_F16 && !desc->scales)
+        return invalid("scales are NULL for this format");
     const uint32_t nrows = desc->nrows, ncols = desc->ncols;
     const uint64_t nnz = desc->nnz;
     const size_t esize = fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
@@ -577,6 +612,12 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
         if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE)
             for (uint64_t k = 0; k < nnz; ++k)
                 if ((vals[k] & 0x7F) == 0x7F) return invalid("FP8 code is NaN at entry " + std::to_string(k));
+        if (fmt == DOSE_FMT_F16)
+            for (uint64_t k = 0; k < nnz; ++k) {
+                uint16_t h;
+                std::memcpy(&h, vals.data() + 2 * k, 2);
+                if ((h & 0x7C00u) == 0x7C00u) return invalid("F16 value is infinite or NaN at entry " + std::to_string(k));
+            }
     }
     if (fmt == DOSE_FMT_U16_SCALE) scale = scl.empty() ? 1.0f : scl[0];
 

@@ -13,7 +13,7 @@
 //     its non-empty rows evenly: groups of L lanes per row, L chosen per stage
 //     from its mean row length (row-length binning); rows longer than coop_nnz
 //     are reduced by the whole CTA;
-//   * values are decoded in registers (u16 -> f32, bf16 -> f32, e4m3 -> f32),
+//   * values are decoded in registers (u16, bf16, f16, e4m3 -> f32),
 //     x sits in shared memory, accumulation is FP32 (optionally compensated),
 //     and the U16/FP8 scale is applied once per row.
 // Every reduction has a fixed shape, so results are bitwise reproducible.
@@ -303,6 +303,7 @@ cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStre
     switch (A->fmt) {
         case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, smem, comp, xsmem, idx16, s);
         case DOSE_FMT_BF16: return launch_fmt<DOSE_FMT_BF16>(A, p, smem, comp, xsmem, idx16, s);
+        case DOSE_FMT_F16: return launch_fmt<DOSE_FMT_F16>(A, p, smem, comp, xsmem, idx16, s);
         case DOSE_FMT_FP8E4M3_ROWSCALE:
             return launch_fmt<DOSE_FMT_FP8E4M3_ROWSCALE>(A, p, smem, comp, xsmem, idx16, s);
     }

@@ -91,6 +91,34 @@ struct Fmt<DOSE_FMT_FP8E4M3_ROWSCALE> {
 #endif
 };
 
+template <>
+struct Fmt<DOSE_FMT_F16> {
+    using T = uint16_t;
+    static constexpr uint32_t kAlign = 8;
+#ifdef __CUDACC__
+    __device__ static float dec(T v) { return dev::f16_to_f32(v); }
+    __device__ static float lds(uint32_t a) { return dev::f16_to_f32((uint16_t)dev::lds_u16(a)); }
+    __device__ static float lds_lt(uint32_t k, uint32_t ke, uint32_t a) {
+        return dev::f16_to_f32((uint16_t)dev::lds_u16_lt(k, ke, a));
+    }
+    __device__ static void lds4(bool p, uint32_t a, float* w) {
+        const uint2 q = dev::lds_v2_if(p, a);
+        float v[4];
+        dec4(q.x, q.y, v);
+        w[0] = v[0];
+        w[1] = v[1];
+        w[2] = v[2];
+        w[3] = v[3];
+    }
+    __device__ static void dec4(uint32_t q0, uint32_t q1, float (&w)[4]) {
+        w[0] = dev::f16_to_f32(static_cast<uint16_t>(q0 & 0xFFFFu));
+        w[1] = dev::f16_to_f32(static_cast<uint16_t>(q0 >> 16));
+        w[2] = dev::f16_to_f32(static_cast<uint16_t>(q1 & 0xFFFFu));
+        w[3] = dev::f16_to_f32(static_cast<uint16_t>(q1 >> 16));
+    }
+#endif
+};
+
 __host__ __device__ constexpr uint32_t round_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 
 constexpr uint32_t kMaxVec = 3;  // per-row float vectors staged with a slot

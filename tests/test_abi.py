@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 @pytest.mark.parametrize("fmt,ofmt", [("u16", oracle.U16_SCALE), ("bf16", oracle.BF16),
-                                      ("fp8", oracle.FP8E4M3_ROWSCALE)])
+                                      ("fp8", oracle.FP8E4M3_ROWSCALE), ("f16", oracle.F16)])
 def test_library_encoder_matches_oracle_bit_exact(lib, fmt, ofmt):
     A = dosegen.generate(dosegen.TINY)
     rng = np.random.default_rng(1)
@@ -47,8 +47,22 @@ def test_library_encoder_matches_oracle_bit_exact(lib, fmt, ofmt):
     codes, scales = dose.encode_host(fmt, A.row_ptr, val)
     ref = oracle.encode(dosegen.CSR(A.nrows, A.ncols, A.row_ptr, A.col, val), ofmt)
     assert np.array_equal(codes, ref.values)
-    if fmt != "bf16":
+    if fmt not in ("bf16", "f16"):
         assert np.array_equal(scales, ref.scales)
+
+
+def test_f16_encoder_on_ties_subnormals_and_overflow(lib):
+    """Every halfway point between neighbouring finite halves, the subnormal
+    range and the overflow threshold, against the oracle's encoder."""
+    codes = np.arange(0, 0x7BFF, dtype=np.uint32).astype(np.uint16)
+    lo = codes.view(np.float16).astype(np.float64)
+    hi = (codes + 1).view(np.float16).astype(np.float64)
+    v = np.concatenate([lo, 0.5 * (lo + hi), [65504.0, 65519.99, 65520.0, 1e6, 2.0 ** -25, 2.0 ** -26, 1e-300]])
+    rp = np.array([0, v.size], dtype=np.uint32)
+    got, scales = dose.encode_host("f16", rp, v)
+    assert scales is None
+    ref = np.array([oracle.f16_round(float(t)) for t in v], dtype=np.uint16)
+    assert np.array_equal(got, ref)
 
 
 def test_fp8_encoder_on_exact_ties(lib):
