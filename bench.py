@@ -10,7 +10,8 @@ HBM.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
     python bench.py --workload batched [--steps K]   # 27 scenario matrices x 16 vectors
-    python bench.py --workload precision             # u16 / BF16 / FP8, plain and compensated
+    python bench.py --workload precision             # u16 / BF16 / FP8 / F16, plain and compensated
+    python bench.py --workload halfdouble            # the paper's Half/double: F16 values, FP64 x and d
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on the same workload and metric.  Under torchrun (N > 1) every rank
@@ -516,8 +517,9 @@ def run_precision(args):
     peak, _ = _peaks()
     K = max(3, min(args.steps, 200))
     variants = []
-    for fmt in ("u16", "bf16", "fp8"):
-        enc = oracle.encode(csr, {"u16": oracle.U16_SCALE, "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE}[fmt])
+    ofmt = {"u16": oracle.U16_SCALE, "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE, "f16": oracle.F16}
+    for fmt in ("u16", "bf16", "fp8", "f16"):
+        enc = oracle.encode(csr, ofmt[fmt])
         same = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
         for comp, idx16 in ((False, False), (True, False), (False, True)):
             A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt=fmt, values=enc.values,
@@ -558,6 +560,76 @@ def run_precision(args):
     print(json.dumps(out), flush=True)
 
 
+HD_METRIC = ("Half/double dose SpMV (F16 values, FP64 x and d): effective HBM GB/s of the 6 nnz + 12 nr + 8 nc "
+             "traffic model, GFLOP/s, and the max relative dose error vs the FP64 oracle")
+
+
+def run_halfdouble(args):
+    """The paper's own configuration (Sec. IV, "Half/double") at the clinical
+    size: IEEE half values, FP64 spot weights and dose, with 32-bit indices (the
+    paper's byte model) and 16-bit indices; double-float accumulation (default)
+    and FP64-FMA accumulation (the paper's arithmetic).  A step is one
+    dose_spmv_f64 call (the x split and the SpMV kernel)."""
+    import torch
+
+    import oracle
+    import paper_2103_09683_gb300 as dose
+
+    dose.build()
+    torch.cuda.set_device(0)
+    beam = dosegen.CLINICAL
+    csr = dosegen.generate(beam)
+    x = dosegen.spot_weights_f64(csr.ncols, dosegen.weight_seed(beam))
+    xd = torch.from_numpy(x).cuda()
+    rng = np.random.default_rng(7)
+    lens = np.diff(csr.row_ptr.astype(np.int64))
+    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 20000, replace=False))
+    enc = oracle.encode(csr, oracle.F16)
+    same = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
+    absref = oracle.spmv_rows(rows, enc.row_ptr, enc.col, np.abs(enc.decoded), np.abs(x))
+    peak, _ = _peaks()
+    K = max(3, min(args.steps, 200))
+    clocks = ClockSampler(0)
+    variants = []
+    clocks.start()
+    for idx16 in (False, True):
+        A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt="f16", values=enc.values,
+                                     index16=idx16)
+        nbytes = A.info()["spmv_f64_bytes"]
+        for native in (False, True):
+            d = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+            for _ in range(args.warmup):
+                A.spmv_f64(xd, d, native=native)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(K):
+                A.spmv_f64(xd, d, native=native)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            A.device_status()
+            err = np.abs(d.cpu().numpy()[rows] - same) / absref
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            variants.append({"accumulation": "fp64_fma" if native else "double_float", "index_bytes": 2 if idx16 else 4,
+                             "ms": round(ms, 5), "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                             "gflops": round(2 * csr.nnz / (ms * 1e-3) / 1e9, 1), "bytes": nbytes,
+                             "err_over_sum_abs": {"max": float(err.max()), "mean": float(err.mean())}})
+            del d
+        del A
+    clk = clocks.stop()
+    base = variants[0]
+    out = {"metric": HD_METRIC, "value": base["achieved_gbs"], "unit": "GB/s", "n_gpus": 1, "steps": K,
+           "warmup": args.warmup, "ms_per_step": base["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f16 values, f64 vectors", "data": "synthetic",
+           "config": {"workload": "clinical pencil beam 256x256x160 voxels x 4000 spots, ~1.5e8 entries; "
+                                  "F16 values; step = one dose_spmv_f64 (x split + SpMV)",
+                      "sampled_rows": int(len(rows)), "l2": "A (~0.9 GB) > L2: streamed from HBM every step",
+                      "peak_gbs": peak},
+           "clocks": clk, "variants": variants}
+    print(json.dumps(out), flush=True)
+
+
 def batched_cpu_baseline(csr, X, budget_s=10.0):
     """The oracle's FP64 SpMM on row blocks of one scenario matrix (about
     budget_s of single-core work), as GB/s of the same byte model."""
@@ -589,9 +661,10 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="time candidate schedules first (dose_autotune)")
     ap.add_argument("--tuning", default="", help="schedule knobs, e.g. tile_nnz=8192,adj_scatter_warps=4")
     ap.add_argument("--matrices", default="", help="batched: subset of the 27 scenario matrices, e.g. 4,13,22")
-    ap.add_argument("--workload", default="clinical", choices=["clinical", "batched", "precision"],
+    ap.add_argument("--workload", default="clinical", choices=["clinical", "batched", "precision", "halfdouble"],
                     help="clinical: the dose + dose-gradient step (default); batched: 27 matrices x 16 vectors; "
-                         "precision: dose eval per stored format with its error vs the FP64 oracle")
+                         "precision: dose eval per stored format with its error vs the FP64 oracle; "
+                         "halfdouble: F16 values with FP64 x and d")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -601,6 +674,8 @@ def main():
         run_batched(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "halfdouble":
+        run_halfdouble(args)
     else:
         run_gpu(args)
 

@@ -59,6 +59,8 @@ def _load():
                                     ctypes.c_void_p]
             lib.pb_uniform_f32.restype = None
             lib.pb_uniform_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]
+            lib.pb_uniform_f64.restype = None
+            lib.pb_uniform_f64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]
             lib.pb_splitmix64_at.restype = ctypes.c_uint64
             lib.pb_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             _lib = lib
@@ -175,6 +177,14 @@ def spot_weights(n: int, seed: int, nvec: int = 1) -> np.ndarray:
     out = np.empty(n * nvec, dtype=np.float32)
     lib.pb_uniform_f32(int(seed) & 0xFFFFFFFFFFFFFFFF, n * nvec, out.ctypes.data)
     return out if nvec == 1 else out.reshape(n, nvec)
+
+
+def spot_weights_f64(n: int, seed: int) -> np.ndarray:
+    """Seeded FP64 spot weights uniform in [0,1) with all 53 bits random: shape (n,)."""
+    lib = _load()
+    out = np.empty(n, dtype=np.float64)
+    lib.pb_uniform_f64(int(seed) & 0xFFFFFFFFFFFFFFFF, n, out.ctypes.data)
+    return out
 
 
 def weight_seed(beam: Beam, k: int = 0) -> int:

@@ -57,6 +57,12 @@ void pb_uniform_f32(uint64_t seed, uint64_t n, float* out) {
         out[k] = (float)(pb_splitmix64_at(seed, k) >> 40) * (1.0f / 16777216.0f);
 }
 
+/* n uniform FP64 values in [0,1): top 53 bits of the stream, exact in FP64. */
+void pb_uniform_f64(uint64_t seed, uint64_t n, double* out) {
+    for (uint64_t k = 0; k < n; ++k)
+        out[k] = (double)(pb_splitmix64_at(seed, k) >> 11) * (1.0 / 9007199254740992.0);
+}
+
 static double bragg_depth(const pb_params* p, int32_t j) {
     double u = (double)(pb_splitmix64_at(p->seed, (uint64_t)j) >> 11) * (1.0 / 9007199254740992.0);
     return (double)p->nz * (0.4 + 0.4 * u);

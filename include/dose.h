@@ -139,6 +139,7 @@ typedef struct {
     uint64_t spmv_bytes;        /* algorithmic HBM bytes of one dose_spmv */
     uint64_t adjoint_bytes;     /* ... of one dose_adjoint */
     uint64_t fused_bytes;       /* ... of one dose_fwd_adj_quadratic with d == NULL */
+    uint64_t spmv_f64_bytes;    /* ... of one dose_spmv_f64 (x read once, d written once) */
     float scale;                /* U16: the matrix scale s; else 0 */
     dose_tuning tuning;         /* the knobs in effect */
 } dose_info;
@@ -155,6 +156,28 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
  * x: device, ncols floats.  d: device, nrows floats, every row written (empty
  * rows get 0).  FP32 accumulation; U16 and FP8 scales applied once per row. */
 dose_status dose_spmv(const dose_matrix* A, const float* x, float* d, void* stream);
+
+/* dose_spmv_f64 flags */
+#define DOSE_SPMV_F64_NATIVE 0x1u /* accumulate with FP64 FMAs (the paper's arithmetic) instead of
+                                     double-float FP32 pairs */
+
+/* d = A x with double-precision vectors (Sec. II-D: the optimiser needs the spot
+ * weights and the dose in double precision; Sec. IV "Half/double": 16-bit matrix
+ * values with double vectors -- DOSE_FMT_F16 is the paper's configuration, any
+ * stored format is accepted).
+ * x: device, ncols doubles, 8-byte aligned, finite with |x_j| < 3.4e38 (the
+ * FP32 range of the split below).  d: device, nrows doubles, 8-byte aligned,
+ * every row written (empty rows get +0.0).
+ * Arithmetic (flags = 0): x_j is split into FP32 hi + lo (2^-48 relative), each
+ * product is formed to ~2^-47 relative with FMAs, and sums are double-float pairs
+ * (TwoSum); row results are rounded once to FP64.  A row of n entries then has
+ * |d_i - sum_k a_ik x_k| <= (2^-45 + g(m)^2) sum_k |a_ik x_k| + 2^-53 |d_i|, where
+ * m <= n is the most terms any one accumulator of the row adds (a handful on the
+ * default schedule) and g(m) = m 2^-24 / (1 - m 2^-24).  DOSE_SPMV_F64_NATIVE
+ * accumulates with FP64 FMAs: |error| <= (n + 2) 2^-53 sum_k |a_ik x_k|.
+ * Uses a handle-owned scratch copy of x (ncols + 1 doubles) and two launches on
+ * `stream`; the same-stream rule for calls on one handle applies. */
+dose_status dose_spmv_f64(const dose_matrix* A, const double* x, double* d, unsigned flags, void* stream);
 
 /* D_m = A_m X_m for m < count, all in one persistent launch (one dose evaluation
  * of many beams and uncertainty scenarios, Sec. I).  X[m]: device, ncols_m x nvec

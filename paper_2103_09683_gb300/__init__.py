@@ -28,6 +28,7 @@ FORMATS = {"u16": 0, "bf16": 1, "fp8": 2, "f16": 3}
 _NO_SCALES = ("bf16", "f16")
 CREATE_COMPENSATED = 0x1
 CREATE_U16_INDEX = 0x2
+SPMV_F64_NATIVE = 0x1
 _STATUS = {0: "DOSE_OK", 1: "DOSE_ERR_INVALID_ARG", 2: "DOSE_ERR_OOM", 3: "DOSE_ERR_CUDA",
            4: "DOSE_ERR_UNSUPPORTED", 5: "DOSE_ERR_TIMEOUT"}
 
@@ -70,7 +71,7 @@ class _Info(ctypes.Structure):
                 ("adj_block_fused", ctypes.c_uint32), ("adj_block_adjoint", ctypes.c_uint32),
                 ("max_row_len", ctypes.c_uint32), ("adj_window", ctypes.c_uint32),
                 ("reserved0", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("spmv_bytes", ctypes.c_uint64),
-                ("adjoint_bytes", ctypes.c_uint64), ("fused_bytes", ctypes.c_uint64),
+                ("adjoint_bytes", ctypes.c_uint64), ("fused_bytes", ctypes.c_uint64), ("spmv_f64_bytes", ctypes.c_uint64),
                 ("scale", ctypes.c_float), ("tuning", Tuning)]
 
 
@@ -80,6 +81,7 @@ _P = ctypes.c_void_p
 EXPORTS = {
     "dose_create_matrix": (ctypes.c_int, [_P, ctypes.c_uint, _P, _P, _P]),
     "dose_spmv": (ctypes.c_int, [_P, _P, _P, _P]),
+    "dose_spmv_f64": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint, _P]),
     "dose_spmv_batched": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "dose_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
     "dose_fwd_adj_quadratic": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
@@ -276,6 +278,18 @@ class DoseMatrix:
             d = torch.empty(self.nrows, dtype=torch.float32, device=x.device)
         _check(load().dose_spmv(self._h, _dptr(x, torch.float32, self.ncols, "x"),
                                 _dptr(d, torch.float32, self.nrows, "d"), _stream_handle(stream)))
+        return d
+
+    def spmv_f64(self, x, d=None, native: bool = False, stream=None):
+        """d = A x with FP64 vectors (the paper's Half/double interface).
+        x: CUDA float64 [ncols]; d (optional): CUDA float64 [nrows].  `native`:
+        FP64 FMA accumulation instead of double-float pairs."""
+        torch = _torch()
+        if d is None:
+            d = torch.empty(self.nrows, dtype=torch.float64, device=x.device)
+        _check(load().dose_spmv_f64(self._h, _dptr(x, torch.float64, self.ncols, "x"),
+                                    _dptr(d, torch.float64, self.nrows, "d"),
+                                    SPMV_F64_NATIVE if native else 0, _stream_handle(stream)))
         return d
 
     def adjoint(self, r, g=None, stream=None):

@@ -328,6 +328,7 @@ static void free_all(dose_matrix* A) {
     cudaFree(A->col16);
     cudaFree(A->val);
     cudaFree(A->row_scale);
+    cudaFree(A->x64);
     cudaFree(A->g_part);
     cudaFree(A->f_part);
     cudaFree(A->err);
@@ -670,6 +671,8 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE &&
         (e = upload(&A->row_scale, scl.data(), (size_t)nrows, (size_t)nrows + 16)) != cudaSuccess)
         return fail(e, "row scales");
+    const size_t x64_alloc = ((size_t)ncols + 2) / 2 * 2;  // ncols + 1 elements, even count (16 B multiple)
+    if ((e = cudaMalloc(&A->x64, x64_alloc * 8)) != cudaSuccess) return fail(e, "FP64 vector scratch");
     const size_t ncols_pad = ((size_t)ncols + 31) / 32 * 32;  // a CTA's window is at most this wide
     if ((e = cudaMalloc(&A->g_part, std::max<size_t>((size_t)A->adj.grid * ncols_pad, 1) * 4)) != cudaSuccess)
         return fail(e, "adjoint partials");
@@ -685,7 +688,7 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
         }
     }
     A->device_bytes = rp_alloc * 4 + col_alloc * 4 + ((flags & DOSE_CREATE_U16_INDEX) ? col16_alloc * 2 : 0) + val_alloc +
-                      (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) +
+                      (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) + x64_alloc * 8 +
                       (size_t)A->adj.grid * ncols_pad * 4 + (size_t)A->adj.grid * 8 + 4 + schedule_bytes(A->fwd) +
                       schedule_bytes(A->adj);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "create");
@@ -707,6 +710,17 @@ dose_status dose_spmv(const dose_matrix* A, const float* x, float* d, void* stre
     if (A->ncols && !x) return invalid("dose_spmv: x is NULL");
     cudaError_t e = launch_spmv(A, x, d, as_stream(stream));
     return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_spmv launch");
+}
+
+dose_status dose_spmv_f64(const dose_matrix* A, const double* x, double* d, unsigned flags, void* stream) {
+    if (!A) return invalid("dose_spmv_f64: null matrix");
+    if (flags & ~DOSE_SPMV_F64_NATIVE) return invalid("dose_spmv_f64: unknown flags");
+    if (A->nrows && !d) return invalid("dose_spmv_f64: d is NULL");
+    if (A->ncols && !x) return invalid("dose_spmv_f64: x is NULL");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(d)) & 7u)
+        return invalid("dose_spmv_f64: x and d must be 8-byte aligned");
+    cudaError_t e = launch_spmv_f64(A, x, d, (flags & DOSE_SPMV_F64_NATIVE) != 0, as_stream(stream));
+    return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_spmv_f64 launch");
 }
 
 static dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* const* vecs, int nvec) {
@@ -811,6 +825,9 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     out->spmv_bytes = (vb + ib) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
     out->adjoint_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
     out->fused_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 8 * nr + 4 * nc + 4 * nc + 8;
+    // FP64 vectors: 8-byte x read once, 8-byte d written once (for F16 values and
+    // 32-bit indices this is 6 nnz + 12 nr + 8 nc + 4, the traffic model of Sec. V)
+    out->spmv_f64_bytes = (vb + ib) * nz + 4 * (nr + 1) + rs + 8 * nr + 8 * nc;
     out->scale = A->fmt == DOSE_FMT_U16_SCALE ? A->scale : 0.f;
     export_tuning(A->fwd.tuning, A->adj_tuning, &out->tuning);
     return DOSE_OK;

@@ -128,6 +128,9 @@ struct dose_matrix {
     dose::DevSchedule adj;      // schedule of the adjoint / fused kernels
     dose::AdjTuning adj_tuning;
 
+    // dose_spmv_f64 scratch: x as the kernel reads it (ncols + 1 elements of 8 bytes)
+    uint2* x64 = nullptr;
+
     // adjoint scratch: per-CTA partial gradients and objective values
     float* g_part = nullptr;     // adj.grid * ncols
     double* f_part = nullptr;    // adj.grid
@@ -145,10 +148,13 @@ namespace dose {
 void set_error(const std::string& msg);
 dose_status cuda_fail(cudaError_t e, const char* what);
 
-// Launchers (spmv_kernel.cu, adjoint_kernel.cu, batched_kernel.cu)
+// Launchers (spmv_kernel.cu, spmv_f64_kernel.cu, adjoint_kernel.cu, batched_kernel.cu)
 size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem);
 bool spmv_x_in_smem(const dose_matrix* A);
 cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s);
+size_t spmv_f64_smem_bytes(const dose_matrix* A, bool x_in_smem);
+bool spmv_f64_x_in_smem(const dose_matrix* A);
+cudaError_t launch_spmv_f64(const dose_matrix* A, const double* x, double* d, bool native, cudaStream_t s);
 // Adjoint shape that fits in shared memory: fills forward/scatter warp counts; false if none.
 bool adjoint_shape(const dose_matrix* A, const AdjTuning& in, bool quad, AdjTuning* out, size_t* smem);
 cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const float* p,

@@ -1,0 +1,408 @@
+// Dose SpMV with double-precision vectors, d = A x with x and d in FP64
+// (Sec. II-D: the optimiser needs the spot weights and the dose in double
+// precision while the matrix is stored in 16 bits; Sec. IV: the "Half/double"
+// kernel, half-precision values with double vectors).
+//
+// GB300 design.  The pipeline is the FP32 forward kernel's: persistent CTAs on
+// the forward schedule, a producer warp streaming each row block's row_ptr /
+// non-empty-row list / value / column slices into a shared-memory ring with
+// bulk async copies, consumer groups of L lanes per row, and a whole-CTA
+// reduction of long rows.  What changes is the arithmetic.  GB300 executes FP64
+// at a small fraction of its FP32 rate, so an FP64 FMA per entry (the paper's
+// arithmetic) would make this memory-bound kernel compute-bound.  The default
+// therefore accumulates in double-float, on FP32 instructions only:
+//   * x is split once per call into FP32 pairs (hi, lo), hi = fl32(x_j),
+//     lo = fl32(x_j - hi), so hi + lo equals x_j to 2^-48 relative;
+//   * a decoded value a (at most 24 significant bits, exactly an FP32 number)
+//     times x_j is p + e with p = fl(a*hi) and e = fma(a, lo, fma(a, hi, -p)):
+//     the inner FMA is the exact error of the product, so p + e equals a*x_j to
+//     about 2^-47 relative;
+//   * each accumulator is a pair (s, c): s takes p through TwoSum (Knuth), whose
+//     exact rounding error goes into c together with e (Dot2 of Ogita, Rump and
+//     Oishi); pairs are combined the same way;
+//   * the row result is one FP64 addition, d_i = s + c (after the U16 / FP8
+//     scale is applied to the pair exactly in the same manner).
+// DOSE_SPMV_F64_NATIVE instead converts each decoded value to FP64 and
+// accumulates with FP64 FMAs (the paper's arithmetic), to compare the two.
+// Every reduction has a fixed shape, so results are bitwise reproducible.
+#include "stage_common.cuh"
+
+namespace dose {
+namespace {
+
+constexpr int F64_DF = 0;  // double-float accumulation (FP32 pairs)
+constexpr int F64_DP = 1;  // native FP64 FMA accumulation
+
+struct Spmv64Params {
+    const uint32_t* row_ptr;
+    const void* col;  // column indices of IW bytes
+    const void* val;
+    float scale;
+    const uint2* x;   // ncols + 1 elements of 8 bytes, the last one zero: DF (hi, lo) pairs, DP doubles
+    double* d;
+    uint32_t nrows, ncols;
+    ScheduleView sched;
+    VecSet vecs;  // FP8: the row scales
+    uint32_t tile_nnz, tile_rows, depth, cwarps, l2pf;
+    int* err;
+};
+
+constexpr uint32_t kHeaderBytes = 3072;  // mbarriers, CTA reduction scratch, 2 KB of stage descriptors
+
+// x as the kernels read it: ncols pairs (or doubles) and a zero element at
+// index ncols, which masked entries of a group read.
+template <int MODE>
+__global__ void prepare_x_kernel(const double* __restrict__ x, uint2* __restrict__ out, uint32_t n) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > n) return;
+    const double v = j < n ? x[j] : 0.0;
+    if (MODE == F64_DF) {
+        const float hi = __double2float_rn(v);
+        const float lo = __double2float_rn(v - (double)hi);  // v - hi is exact in FP64
+        out[j] = make_uint2(__float_as_uint(hi), __float_as_uint(lo));
+    } else {
+        out[j] = make_uint2((uint32_t)__double2loint(v), (uint32_t)__double2hiint(v));
+    }
+}
+
+// (s, c) += a * (hi + lo)
+__device__ __forceinline__ void df_mac(float a, float2 x, float& s, float& c) {
+    const float p = __fmul_rn(a, x.x);
+    const float e = __fmaf_rn(a, x.y, __fmaf_rn(a, x.x, -p));
+    float t, err;
+    dev::two_sum(s, p, t, err);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// (s, c) += (s2, c2)
+__device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
+    float t, e;
+    dev::two_sum(s, s2, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(c2, e));
+}
+
+// Accumulator of one lane: a double-float pair or a double.
+template <int MODE>
+struct Acc;
+template <>
+struct Acc<F64_DF> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void mac(float a, const uint2* xsp, uint32_t j) {
+        const uint2 q = xsp[j];
+        df_mac(a, make_float2(__uint_as_float(q.x), __uint_as_float(q.y)), s, c);
+    }
+    __device__ __forceinline__ void add(const Acc& o) { df_add(s, c, o.s, o.c); }
+    __device__ __forceinline__ Acc shfl_xor(uint32_t off) const {
+        Acc o;
+        o.s = __shfl_xor_sync(0xffffffffu, s, off);
+        o.c = __shfl_xor_sync(0xffffffffu, c, off);
+        return o;
+    }
+    // d = sc * (s + c) in FP64 (sc = 1: no scale)
+    __device__ __forceinline__ double result(bool scaled, float sc) const {
+        if (!scaled) return __dadd_rn((double)s, (double)c);
+        const float p = __fmul_rn(sc, s);
+        const float e = __fmaf_rn(sc, c, __fmaf_rn(sc, s, -p));
+        return __dadd_rn((double)p, (double)e);
+    }
+    __device__ __forceinline__ uint2 pack() const { return make_uint2(__float_as_uint(s), __float_as_uint(c)); }
+    __device__ __forceinline__ static Acc unpack(uint2 q) {
+        Acc a;
+        a.s = __uint_as_float(q.x);
+        a.c = __uint_as_float(q.y);
+        return a;
+    }
+};
+template <>
+struct Acc<F64_DP> {
+    double v = 0.0;
+    __device__ __forceinline__ void mac(float a, const uint2* xsp, uint32_t j) {
+        const uint2 q = xsp[j];
+        v = __fma_rn((double)a, __hiloint2double((int)q.y, (int)q.x), v);
+    }
+    __device__ __forceinline__ void add(const Acc& o) { v = __dadd_rn(v, o.v); }
+    __device__ __forceinline__ Acc shfl_xor(uint32_t off) const {
+        Acc o;
+        o.v = __shfl_xor_sync(0xffffffffu, v, off);
+        return o;
+    }
+    __device__ __forceinline__ double result(bool scaled, float sc) const {
+        return scaled ? __dmul_rn((double)sc, v) : v;
+    }
+    __device__ __forceinline__ uint2 pack() const {
+        return make_uint2((uint32_t)__double2loint(v), (uint32_t)__double2hiint(v));
+    }
+    __device__ __forceinline__ static Acc unpack(uint2 q) {
+        Acc a;
+        a.v = __hiloint2double((int)q.y, (int)q.x);
+        return a;
+    }
+};
+
+// Lane li of an L-lane group takes the groups of four consecutive entries at
+// (kb & ~3) + 4 li + 4 L s for `iters` steps (the same for the whole warp),
+// exactly as the FP32 kernel does: a group past the row's end reloads the row's
+// first group, and every entry outside [kb, ke) gets weight 0 and reads x at the
+// zero element zc.  Four accumulators, combined as (0 + 1) + (2 + 3).
+template <int FMT, int MODE, uint32_t L, uint32_t IW>
+__device__ __forceinline__ Acc<MODE> dot_vec64(const SlotPtrs<FMT, IW>& sp, const uint2* __restrict__ xsp, uint32_t zc,
+                                               uint32_t kb, uint32_t ke, uint32_t li, uint32_t iters) {
+    using T = typename Fmt<FMT>::T;
+    Acc<MODE> acc[4];
+    const int len = (int)(ke - kb);
+    const uint32_t kb4 = kb & ~3u;
+    int off = (int)(4 * li) - (int)(kb & 3u);
+    uint32_t k4 = kb4 + 4 * li;
+    for (uint32_t it = 0; it < iters; ++it, off += 4 * L, k4 += 4 * L) {
+        const uint32_t kg = off < len ? k4 : kb4;
+        uint32_t c[4];
+        if (IW == 4) {
+            const uint4 cc = *reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(sp.col) + kg);
+            c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+        } else {
+            const uint2 cc = *reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(sp.col) + kg);
+            c[0] = cc.x & 0xFFFFu; c[1] = cc.x >> 16; c[2] = cc.y & 0xFFFFu; c[3] = cc.y >> 16;
+        }
+        float a[4];
+        if (sizeof(T) == 2) {
+            const uint2 qv = *reinterpret_cast<const uint2*>(sp.val + kg);
+            Fmt<FMT>::dec4(qv.x, qv.y, a);
+        } else {
+            Fmt<FMT>::dec4(*reinterpret_cast<const uint32_t*>(sp.val + kg), 0u, a);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool m = (uint32_t)(off + u) < (uint32_t)len;
+            acc[u].mac(m ? a[u] : 0.f, xsp, m ? c[u] : zc);
+        }
+    }
+    acc[0].add(acc[1]);
+    acc[2].add(acc[3]);
+    acc[0].add(acc[2]);
+    return acc[0];
+}
+
+template <int FMT>
+__device__ __forceinline__ float row_scale(const Spmv64Params& p, uint32_t slot, const SlotLayout& SL, uint32_t row0,
+                                           uint32_t row) {
+    if (FMT == DOSE_FMT_U16_SCALE) return p.scale;
+    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) return slot_vec(slot, SL, p.vecs, 0, row0, row);
+    return 1.0f;
+}
+
+constexpr bool fmt_scaled(int fmt) { return fmt == DOSE_FMT_U16_SCALE || fmt == DOSE_FMT_FP8E4M3_ROWSCALE; }
+
+// The non-empty rows of a NORMAL stage, 2^LG lanes per row (dealt as in the
+// FP32 kernel).
+template <int FMT, int MODE, uint32_t IW, uint32_t LG>
+__device__ __forceinline__ void normal_rows64(const Spmv64Params& p, const StageDesc& D, const SlotView& v,
+                                              uint32_t slot, const SlotLayout& SL, const SlotPtrs<FMT, IW>& sp,
+                                              const uint2* xsp, uint32_t ctid, uint32_t lane, uint32_t nct,
+                                              uint32_t rotw) {
+    constexpr uint32_t L = 1u << LG;
+    const uint32_t gid = ctid >> LG, li = lane & (L - 1), G = nct >> LG;
+    const uint32_t j0 = (gid + G - ((rotw << (5 - LG)) & (G - 1))) & (G - 1);
+    const uint32_t n_ne = D.ne1 - D.ne0;
+    for (uint32_t base = 0; base < n_ne; base += G) {
+        const uint32_t i = base + j0;
+        const bool has = i < n_ne;
+        uint32_t row = 0, rs = D.nz0, re = D.nz0;  // groups without a row read masked entries
+        if (has) {
+            row = D.row0 + dev::lds_u16(v.ne + 2 * i);
+            rs = dev::lds_u32(v.rp + 4 * row);
+            re = dev::lds_u32(v.rp + 4 * row + 4);
+        }
+        const uint32_t span = re > rs ? re - (rs & ~3u) : 0;
+        const uint32_t iters = __reduce_max_sync(0xffffffffu, (span + 4 * L - 1) / (4 * L));
+        Acc<MODE> a = dot_vec64<FMT, MODE, L, IW>(sp, xsp, p.ncols, rs, re, li, iters);
+        for (uint32_t o = L >> 1; o > 0; o >>= 1) a.add(a.shfl_xor(o));
+        if (has && li == 0) p.d[row] = a.result(fmt_scaled(FMT), row_scale<FMT>(p, slot, SL, D.row0, row));
+    }
+}
+
+template <int FMT, int MODE, bool XSMEM, uint32_t IW>
+__global__ void __launch_bounds__(544, 1) spmv_f64_kernel(const Spmv64Params p) {
+    using T = typename Fmt<FMT>::T;
+    constexpr uint32_t ES = (uint32_t)sizeof(T);
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t S = p.depth, W = p.cwarps;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + S;
+    uint64_t* dbar = full + 16;                        // 2 descriptor-window barriers
+    uint2* red = reinterpret_cast<uint2*>(smem + 256);  // 32 x 8 bytes: CTA reduction
+    StageDesc* dwin = reinterpret_cast<StageDesc*>(smem + 1024);
+    uint2* xs = reinterpret_cast<uint2*>(smem + kHeaderBytes);
+    const uint32_t x_bytes = XSMEM ? round_up((p.ncols + 1) * 8, 128) : 0;
+    unsigned char* slot_base = smem + kHeaderBytes + x_bytes;
+    const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, ES, p.vecs.n, false, IW);
+
+    const uint32_t s_begin = p.sched.cta_begin[blockIdx.x];
+    const uint32_t s_end = p.sched.cta_begin[blockIdx.x + 1];
+
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < S; ++i) {
+            dev::mbar_init(&full[i], 1);
+            dev::mbar_init(&empty[i], W);
+        }
+        dev::mbar_init(&dbar[0], 1);
+        dev::mbar_init(&dbar[1], 1);
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    if (s_begin >= s_end) return;
+
+    if (warp == 0) {
+        if (lane == 0)
+            run_producer<FMT, IW>(p.sched, s_begin, s_end, p.row_ptr, p.col, p.val, p.vecs, slot_base, SL, full,
+                                  empty, S, dwin, dbar, p.l2pf, p.err);
+        return;
+    }
+
+    // -------------------- consumers
+    const uint32_t cw = warp - 1;
+    const uint32_t ctid = threadIdx.x - 32;
+    const uint32_t nct = W * 32;
+    if (XSMEM) {
+        for (uint32_t j = ctid; j <= p.ncols; j += nct) xs[j] = __ldg(p.x + j);
+        dev::named_barrier(1, nct);
+    }
+    const uint2* xsp = XSMEM ? xs : p.x;
+    const uint32_t slot0 = dev::smem_u32(slot_base);
+    Acc<MODE> coop;
+
+    uint32_t st = 0, ph = 0;
+    for (uint32_t s = s_begin; s < s_end; ++s) {
+        if (!dev::mbar_wait_bounded(&full[st], ph)) {
+            atomicExch(p.err, kErrTimeoutFull);
+            return;
+        }
+        const uint32_t slot = slot0 + st * SL.bytes;
+        const StageDesc D = slot_desc(slot);
+        const SlotView v = slot_view<FMT, IW>(slot, SL, D);
+        const SlotPtrs<FMT, IW> sp = slot_ptrs<FMT, IW>(slot_base + st * SL.bytes, SL, D);
+
+        if (!(D.meta & STAGE_COOP)) {
+            for (uint32_t r = D.row0 + ctid; r < D.row1; r += nct)
+                if (dev::lds_u32(v.rp + 4 * r) == dev::lds_u32(v.rp + 4 * r + 4)) p.d[r] = 0.0;
+            const uint32_t rotw = s & (W - 1);
+            switch (D.meta & STAGE_LANES_MASK) {
+                case 0: normal_rows64<FMT, MODE, IW, 0>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
+                case 1: normal_rows64<FMT, MODE, IW, 1>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
+                case 2: normal_rows64<FMT, MODE, IW, 2>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
+                case 3: normal_rows64<FMT, MODE, IW, 3>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
+                case 4: normal_rows64<FMT, MODE, IW, 4>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
+                default: normal_rows64<FMT, MODE, IW, 5>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
+            }
+        } else {
+            // one chunk of a long row: every consumer thread takes entries
+            // nz0 + ctid, + nct, ...; the partials are combined at its last chunk
+            if (D.meta & STAGE_FIRST) coop = Acc<MODE>();
+            for (uint32_t k = D.nz0 + ctid; k < D.nz1; k += nct)
+                coop.mac(Fmt<FMT>::lds(v.val + ES * k), xsp, col_at<IW>(v, k));
+            if (D.meta & STAGE_LAST) {
+                Acc<MODE> a = coop;
+                for (uint32_t o = 16; o > 0; o >>= 1) a.add(a.shfl_xor(o));
+                if (lane == 0) red[cw] = a.pack();
+                dev::named_barrier(1, nct);
+                if (ctid == 0) {
+                    Acc<MODE> tot = Acc<MODE>::unpack(red[0]);
+                    for (uint32_t w2 = 1; w2 < W; ++w2) tot.add(Acc<MODE>::unpack(red[w2]));
+                    p.d[D.row0] = tot.result(fmt_scaled(FMT), row_scale<FMT>(p, slot, SL, D.row0, D.row0));
+                }
+                dev::named_barrier(1, nct);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) dev::mbar_arrive(&empty[st]);
+        if (++st == S) {
+            st = 0;
+            ph ^= 1;
+        }
+    }
+}
+
+template <int FMT, int MODE, bool XSMEM, uint32_t IW>
+cudaError_t launch_t(const dose_matrix* A, const Spmv64Params& p, size_t smem, cudaStream_t s) {
+    auto k = spmv_f64_kernel<FMT, MODE, XSMEM, IW>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<A->fwd.grid, 32 * (p.cwarps + 1), smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int FMT, int MODE>
+cudaError_t launch_mode(const dose_matrix* A, const Spmv64Params& p, size_t smem, bool xsmem, bool idx16,
+                        cudaStream_t s) {
+    if (idx16) return xsmem ? launch_t<FMT, MODE, true, 2>(A, p, smem, s) : launch_t<FMT, MODE, false, 2>(A, p, smem, s);
+    return xsmem ? launch_t<FMT, MODE, true, 4>(A, p, smem, s) : launch_t<FMT, MODE, false, 4>(A, p, smem, s);
+}
+
+template <int FMT>
+cudaError_t launch_fmt(const dose_matrix* A, const Spmv64Params& p, size_t smem, bool native, bool xsmem, bool idx16,
+                       cudaStream_t s) {
+    return native ? launch_mode<FMT, F64_DP>(A, p, smem, xsmem, idx16, s)
+                  : launch_mode<FMT, F64_DF>(A, p, smem, xsmem, idx16, s);
+}
+
+}  // namespace
+
+size_t spmv_f64_smem_bytes(const dose_matrix* A, bool x_in_smem) {
+    const Tuning& t = A->fwd.tuning;
+    const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const uint32_t nvec = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
+    const uint32_t iw = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;
+    const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, false, iw);
+    return kHeaderBytes + (x_in_smem ? round_up((A->ncols + 1) * 8, 128) : 0) + (size_t)t.stages * SL.bytes;
+}
+
+bool spmv_f64_x_in_smem(const dose_matrix* A) { return spmv_f64_smem_bytes(A, true) <= kMaxSmemPerBlock; }
+
+cudaError_t launch_spmv_f64(const dose_matrix* A, const double* x, double* d, bool native, cudaStream_t s) {
+    if (A->nrows == 0) return cudaSuccess;
+    const uint32_t nx = A->ncols + 1;
+    if (native)
+        prepare_x_kernel<F64_DP><<<(nx + 255) / 256, 256, 0, s>>>(x, A->x64, A->ncols);
+    else
+        prepare_x_kernel<F64_DF><<<(nx + 255) / 256, 256, 0, s>>>(x, A->x64, A->ncols);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    Spmv64Params p;
+    const bool idx16 = (A->flags & DOSE_CREATE_U16_INDEX) != 0;
+    p.row_ptr = A->row_ptr;
+    p.col = idx16 ? static_cast<const void*>(A->col16) : static_cast<const void*>(A->col);
+    p.val = A->val;
+    p.scale = A->scale;
+    p.x = A->x64;
+    p.d = d;
+    p.nrows = A->nrows;
+    p.ncols = A->ncols;
+    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin, nullptr};
+    p.vecs.n = 0;
+    if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {
+        p.vecs.n = 1;
+        p.vecs.ptr[0] = A->row_scale;
+        p.vecs.lim[0] = round_up(A->nrows, 4);
+    }
+    p.tile_nnz = A->fwd.tuning.tile_nnz;
+    p.tile_rows = A->fwd.tuning.tile_rows;
+    p.depth = A->fwd.tuning.stages;
+    p.cwarps = A->fwd.tuning.consumer_warps;
+    p.l2pf = A->fwd.tuning.l2_prefetch;
+    p.err = A->err;
+    const bool xsmem = spmv_f64_x_in_smem(A);
+    const size_t smem = spmv_f64_smem_bytes(A, xsmem);
+    switch (A->fmt) {
+        case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, smem, native, xsmem, idx16, s);
+        case DOSE_FMT_BF16: return launch_fmt<DOSE_FMT_BF16>(A, p, smem, native, xsmem, idx16, s);
+        case DOSE_FMT_F16: return launch_fmt<DOSE_FMT_F16>(A, p, smem, native, xsmem, idx16, s);
+        case DOSE_FMT_FP8E4M3_ROWSCALE:
+            return launch_fmt<DOSE_FMT_FP8E4M3_ROWSCALE>(A, p, smem, native, xsmem, idx16, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dose

@@ -78,6 +78,36 @@ def test_clinical_fused_objective_and_gradient(clinical):
     A.device_status()
 
 
+@pytest.mark.parametrize("native", [False, True])
+def test_clinical_half_double_sampled_rows(native):
+    """The paper's Half/double configuration at the clinical size: F16 values,
+    16-bit column indices, FP64 spot weights and dose (bench.py --workload
+    halfdouble), sampled rows against the oracle under the bounds of the FP64
+    parity tests."""
+    beam = dosegen.CLINICAL
+    csr = dosegen.generate(beam)
+    A, enc = make(csr, "f16", index16=True)
+    x = dosegen.spot_weights_f64(csr.ncols, dosegen.weight_seed(beam))
+    d = A.spmv_f64(_to(x), native=native).cpu().numpy()
+    rows = _sample_rows(csr.nrows, enc.row_ptr, 6000, 3)
+    ref = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
+    absref = oracle.spmv_rows(rows, enc.row_ptr, enc.col, np.abs(enc.decoded), np.abs(x))
+    n = np.diff(enc.row_ptr.astype(np.int64))[rows].astype(np.float64)
+    u = 2.0 ** -53
+    if native:
+        bound = 2 * (n + 2) * u * absref
+    else:
+        g = n * 2.0 ** -24 / (1 - n * 2.0 ** -24)
+        bound = (2.0 ** -45 + g * g) * absref + u * np.abs(d[rows]) + (n + 2) * u * absref
+    err = np.abs(d[rows] - ref)
+    assert np.all(err <= bound)
+    nz = absref > 0
+    assert np.all(d[rows][~nz] == 0.0)
+    assert np.max(err[nz] / absref[nz]) <= 2.0 ** -40
+    assert np.all(d[np.diff(enc.row_ptr.astype(np.int64)) == 0] == 0.0)
+    A.device_status()
+
+
 def test_batched_27_scenarios_16_vectors_sampled_rows():
     """All 27 scenario matrices in one launch (bench.py --workload batched),
     64 sampled rows x 16 vectors per matrix against the oracle."""
