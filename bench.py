@@ -147,6 +147,11 @@ def _traffic(kernel: str):
     return None
 
 
+def _tuning_kv(args) -> dict:
+    """--tuning "k=v,k=v" as a dict of schedule knobs."""
+    return {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))} if args.tuning else {}
+
+
 def setup_workload(device):
     """Clinical beam on the device: handle, x, p, w and the PG step size."""
     import torch
@@ -183,7 +188,7 @@ def run_gpu(args):
         td.init_process_group("nccl", device_id=device)
     csr, A, x, p, w, eta = setup_workload(device)
     if args.tuning:
-        A.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
+        A.set_tuning(**_tuning_kv(args))
     tuned = A.autotune(x) if args.autotune else None
     info = A.info()
     stream = torch.cuda.current_stream()
@@ -595,6 +600,8 @@ def run_halfdouble(args):
     for idx16 in (False, True):
         A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt="f16", values=enc.values,
                                      index16=idx16)
+        if args.tuning:
+            A.set_tuning(**_tuning_kv(args))
         nbytes = A.info()["spmv_f64_bytes"]
         for native in (False, True):
             d = torch.empty(A.nrows, dtype=torch.float64, device="cuda")

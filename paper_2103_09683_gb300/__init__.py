@@ -56,7 +56,8 @@ class Tuning(ctypes.Structure):
                 ("l2_prefetch", ctypes.c_uint32),
                 ("adj_tile_nnz", ctypes.c_uint32), ("adj_tile_rows", ctypes.c_uint32),
                 ("adj_stages", ctypes.c_uint32), ("adj_forward_warps", ctypes.c_uint32),
-                ("adj_scatter_warps", ctypes.c_uint32), ("adj_l2_prefetch", ctypes.c_uint32)]
+                ("adj_scatter_warps", ctypes.c_uint32), ("adj_l2_prefetch", ctypes.c_uint32),
+                ("row_order", ctypes.c_uint32), ("adj_row_order", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -200,6 +200,14 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
         D.row1 = r;
         D.nz1 = rp[r];
         D.ne1 = (uint32_t)S.ne.size();
+        if (t.row_order == 2) {
+            // Longest rows first (counted in the 4-entry groups a lane loads), so the
+            // rows that one warp reduces together have similar trip counts.
+            const uint32_t row0 = D.row0;
+            auto groups = [&](uint16_t o) { return (rp[row0 + o + 1] - (rp[row0 + o] & ~3u) + 3) / 4; };
+            std::stable_sort(S.ne.begin() + D.ne0, S.ne.end(),
+                             [&](uint16_t a, uint16_t b) { return groups(a) > groups(b); });
+        }
         const uint32_t nonempty = D.ne1 - D.ne0;
         const double mean = nonempty ? (double)nz / nonempty : 0.0;
         const uint32_t lg = nonempty ? nearest_pow2_log2(mean / t.lane_target) : 5;
@@ -342,6 +350,7 @@ static dose_status check_tuning(const dose_matrix* A, Tuning& t) {
     if (t.stages < 2 || t.stages > 8) return invalid("tuning.stages must be in [2, 8]");
     if (t.consumer_warps != 4 && t.consumer_warps != 8 && t.consumer_warps != 16)
         return invalid("tuning.consumer_warps must be 4, 8 or 16");
+    if (t.row_order < 1 || t.row_order > 2) return invalid("tuning.row_order must be 1 or 2");
     if (spmv_smem_bytes(A, t, spmv_x_in_smem(A)) > kMaxSmemPerBlock)
         return invalid("tuning needs more shared memory than a CTA has");
     return DOSE_OK;
@@ -368,6 +377,7 @@ static dose_status check_adj_tuning(const AdjTuning& t) {
     if (t.tile_rows < 32 || t.tile_rows > 8192) return invalid("tuning.adj_tile_rows must be in [32, 8192]");
     if (t.stages < 2 || t.stages > 8) return invalid("tuning.adj_stages must be in [2, 8]");
     if (t.forward_warps < 1 || t.forward_warps > 15) return invalid("tuning.adj_forward_warps must be in [1, 15]");
+    if (t.row_order < 1 || t.row_order > 2) return invalid("tuning.adj_row_order must be 1 or 2");
     if (t.scatter_warps > kMaxAdjWarps - 2)
         return invalid("tuning.adj_scatter_warps must be in [0, " + std::to_string(kMaxAdjWarps - 2) + "]");
     return DOSE_OK;
@@ -388,6 +398,8 @@ static void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
     if (in->adj_forward_warps) a.forward_warps = in->adj_forward_warps;
     if (in->adj_scatter_warps) a.scatter_warps = in->adj_scatter_warps;
     if (in->adj_l2_prefetch) a.l2_prefetch = in->adj_l2_prefetch >= 32 ? 0 : in->adj_l2_prefetch;
+    if (in->row_order) t.row_order = in->row_order;
+    if (in->adj_row_order) a.row_order = in->adj_row_order;
 }
 
 static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out) {
@@ -404,6 +416,8 @@ static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out)
     out->adj_forward_warps = a.forward_warps;
     out->adj_scatter_warps = a.scatter_warps;
     out->adj_l2_prefetch = a.l2_prefetch ? a.l2_prefetch : 32;
+    out->row_order = t.row_order;
+    out->adj_row_order = a.row_order;
 }
 
 template <class T>
@@ -445,6 +459,7 @@ static Tuning adj_schedule_tuning(const Tuning& fwd, const AdjTuning& a) {
     t.tile_rows = a.tile_rows;
     t.coop_nnz = std::min(fwd.coop_nnz, a.tile_nnz);
     t.stages = a.stages;
+    t.row_order = a.row_order;
     return t;
 }
 
