@@ -631,6 +631,7 @@ def run_halfdouble(args):
            "vs_baseline": None, "dtype": "f16 values, f64 vectors", "data": "synthetic",
            "config": {"workload": "clinical pencil beam 256x256x160 voxels x 4000 spots, ~1.5e8 entries; "
                                   "F16 values; step = one dose_spmv_f64 (x split + SpMV)",
+                      "tuning": _tuning_kv(args),
                       "sampled_rows": int(len(rows)), "l2": "A (~0.9 GB) > L2: streamed from HBM every step",
                       "peak_gbs": peak},
            "clocks": clk, "variants": variants}
