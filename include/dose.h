@@ -120,7 +120,9 @@ typedef struct {
                                    never more than 19 - forward warps) */
     uint32_t adj_l2_prefetch;   /* as l2_prefetch, for these passes (32 = off) */
     /* order of a row block's non-empty rows among the consumer groups */
-    uint32_t row_order;         /* forward: 1 = matrix order, 2 = rows with the most 4-entry groups first */
+    uint32_t row_order;         /* forward: 1 = matrix order, 2 = rows with the most 4-entry groups first
+                                   (default: the rows one warp reduces together then have similar trip
+                                   counts) */
     uint32_t adj_row_order;     /* the same for the adjoint schedule */
 } dose_tuning;
 

@@ -61,7 +61,7 @@ struct Tuning {
     uint32_t stages = 3;
     uint32_t consumer_warps = 16;
     uint32_t l2_prefetch = 2;   // stages prefetched into L2 ahead of the shared-memory ring
-    uint32_t row_order = 1;     // non-empty rows of a stage: 1 = matrix order, 2 = most 4-entry groups first
+    uint32_t row_order = 2;     // non-empty rows of a stage: 1 = matrix order, 2 = most 4-entry groups first
 };
 
 struct Schedule {
@@ -104,7 +104,7 @@ struct AdjTuning {
     uint32_t forward_warps = 8;   // fused pass: warps computing d, f and r
     uint32_t scatter_warps = 0;   // warps owning gradient accumulators (0 = as many as fit, up to the cap)
     uint32_t l2_prefetch = 8;     // stages prefetched into L2 ahead of the shared-memory ring
-    uint32_t row_order = 1;       // as Tuning::row_order, for the adjoint schedule
+    uint32_t row_order = 2;       // as Tuning::row_order, for the adjoint schedule
 };
 
 }  // namespace dose

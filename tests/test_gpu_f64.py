@@ -112,7 +112,7 @@ def test_spmv_f64_edge_cases(name, native):
     csr = edge_case_matrices()[name]
     for fmt in ("f16", "fp8"):
         for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4),
-                       dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16, row_order=2)):
+                       dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16, row_order=1)):
             for index16 in (False, True):
                 if index16 and csr.ncols > 65536:
                     continue

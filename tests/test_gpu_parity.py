@@ -56,7 +56,7 @@ def test_forward_tiny_beam(tiny, fmt, compensated):
 def test_forward_edge_cases(name, fmt):
     csr = edge_case_matrices()[name]
     for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4),
-                   dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16, row_order=2)):
+                   dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16, row_order=1)):
         A, enc = make(csr, fmt, tuning=tuning)
         x = _x(csr.ncols, seed=3)
         d = A.spmv(_to(x)).cpu().numpy()
@@ -90,7 +90,7 @@ def test_forward_16bit_column_indices(tiny, fmt, compensated):
 def test_forward_16bit_column_indices_edge_cases(name):
     csr = edge_case_matrices()[name]
     for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4),
-                   dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16, row_order=2)):
+                   dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16, row_order=1)):
         A, enc = make(csr, "u16", tuning=tuning, index16=True)
         x = _x(csr.ncols, seed=5)
         fwd_check(A.spmv(_to(x)).cpu().numpy(), oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x))
@@ -154,7 +154,7 @@ def test_adjoint_edge_cases(name):
                                  lengths=np.minimum(csr.row_lengths(), 9000))
     for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4,
                               adj_tile_nnz=256, adj_tile_rows=32, adj_stages=2, adj_forward_warps=2,
-                              adj_scatter_warps=3, adj_row_order=2)):
+                              adj_scatter_warps=3, adj_row_order=1)):
         A, enc = make(csr, "u16", tuning=tuning)
         r = np.random.default_rng(9).normal(size=csr.nrows).astype(np.float32)
         g = A.adjoint(_to(r)).cpu().numpy()
