@@ -10,7 +10,7 @@ HBM.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
     python bench.py --workload batched [--steps K]   # 27 scenario matrices x 16 vectors
-    python bench.py --workload precision             # u16 / BF16 / FP8 / F16, plain and compensated
+    python bench.py --workload precision             # u16 / BF16 / FP8 / F16 / F32, plain and compensated
     python bench.py --workload halfdouble            # the paper's Half/double: F16 values, FP64 x and d
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
@@ -522,8 +522,9 @@ def run_precision(args):
     peak, _ = _peaks()
     K = max(3, min(args.steps, 200))
     variants = []
-    ofmt = {"u16": oracle.U16_SCALE, "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE, "f16": oracle.F16}
-    for fmt in ("u16", "bf16", "fp8", "f16"):
+    ofmt = {"u16": oracle.U16_SCALE, "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE, "f16": oracle.F16,
+            "f32": oracle.F32}
+    for fmt in ("u16", "bf16", "fp8", "f16", "f32"):
         enc = oracle.encode(csr, ofmt[fmt])
         same = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
         for comp, idx16 in ((False, False), (True, False), (False, True)):

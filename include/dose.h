@@ -52,12 +52,15 @@ typedef enum {
  *   U16_SCALE        : uint16 code q, one FP32 scale s per matrix, a = s * q
  *   BF16             : bfloat16 bits, a = value
  *   FP8E4M3_ROWSCALE : OCP FP8 E4M3 code q, one FP32 scale s_r per row, a = s_r * e4m3(q)
- *   F16              : IEEE 754 binary16 bits, a = value (finite codes only) */
+ *   F16              : IEEE 754 binary16 bits, a = value (finite codes only)
+ *   F32              : IEEE 754 binary32 bits, a = value (finite only; the paper's "Single"
+ *                      configuration, Sec. IV, 8 bytes per entry with 32-bit indices) */
 typedef enum {
     DOSE_FMT_U16_SCALE = 0,
     DOSE_FMT_BF16 = 1,
     DOSE_FMT_FP8E4M3_ROWSCALE = 2,
-    DOSE_FMT_F16 = 3
+    DOSE_FMT_F16 = 3,
+    DOSE_FMT_F32 = 4
 } dose_format;
 
 /* A CSR matrix (Sec. II-C: values, column indices, row starts).
@@ -65,9 +68,10 @@ typedef enum {
  *   row_ptr      : nrows+1 entries, row_ptr[0] = 0, non-decreasing, row_ptr[nrows] = nnz.
  *   col_idx      : nnz entries, each < ncols, unique within a row (any order).
  *   fmt          : stored format of `values`.
- *   values       : nnz encoded values (uint16 for U16/BF16/F16, uint8 for FP8), or NULL
+ *   values       : nnz encoded values (uint16 for U16/BF16/F16, uint8 for FP8, 32-bit
+ *                  for F32), or NULL
  *                  to have the library encode `values_f64`.
- *   scales       : U16: 1 float (s); FP8: nrows floats (s_r); BF16, F16: NULL.  Ignored
+ *   scales       : U16: 1 float (s); FP8: nrows floats (s_r); BF16, F16, F32: NULL.  Ignored
  *                  when the library encodes.
  *   values_f64   : nnz non-negative FP64 values, used when values == NULL.
  *   on_device    : 0 = all pointers are host memory; 1 = row_ptr, col_idx, values,
@@ -245,8 +249,8 @@ dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning);
 dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tuning* best);
 
 /* Host-only encoder of the library's stored formats (no GPU needed):
- * values_f64 (nnz, non-negative) -> codes (uint16 or uint8, nnz) and scales
- * (U16: 1 float; FP8: nrows floats; BF16, F16: untouched, may be NULL; F16 rounds
+ * values_f64 (nnz, non-negative) -> codes (uint16, uint8 or 32-bit, nnz) and scales
+ * (U16: 1 float; FP8: nrows floats; BF16, F16, F32: untouched, may be NULL; F16 rounds
  * to nearest, ties to even, and gives infinity above the half range).  Uses
  * row_ptr (host, nrows+1) for FP8 row scales. */
 dose_status dose_encode_host(dose_format fmt, uint32_t nrows, const uint32_t* row_ptr,

@@ -37,8 +37,8 @@ _SRC = os.path.join(_HERE, "dose_oracle.c")
 _lock = threading.Lock()
 _lib = None
 
-U16_SCALE, BF16, FP8E4M3_ROWSCALE, F16 = 0, 1, 2, 3
-FORMAT_NAMES = {U16_SCALE: "u16", BF16: "bf16", FP8E4M3_ROWSCALE: "fp8", F16: "f16"}
+U16_SCALE, BF16, FP8E4M3_ROWSCALE, F16, F32 = 0, 1, 2, 3, 4
+FORMAT_NAMES = {U16_SCALE: "u16", BF16: "bf16", FP8E4M3_ROWSCALE: "fp8", F16: "f16", F32: "f32"}
 
 
 def build(force: bool = False) -> str:
@@ -72,6 +72,8 @@ def _load():
                 "oracle_f16_value": (_F64, [_U16]),
                 "oracle_f16_round": (_U16, [_F64]),
                 "oracle_encode_f16": (ctypes.c_int, [_U64, _P, _P]),
+                "oracle_encode_f32": (ctypes.c_int, [_U64, _P, _P]),
+                "oracle_decode_f32": (None, [_U64, _P, _P]),
                 "oracle_decode_f16": (None, [_U64, _P, _P]),
                 "oracle_encode_u16": (ctypes.c_int, [_U64, _P, _P, _P]),
                 "oracle_encode_bf16": (ctypes.c_int, [_U64, _P, _P]),
@@ -138,8 +140,8 @@ class Encoded:
     def __init__(self, fmt, nrows, ncols, row_ptr, col, values, scales, decoded):
         self.fmt, self.nrows, self.ncols = fmt, nrows, ncols
         self.row_ptr, self.col = row_ptr, col
-        self.values = values      # uint16 (u16 codes, bf16 or f16 bits) or uint8 (e4m3 codes)
-        self.scales = scales      # float32[1] (u16), float32[nrows] (fp8) or None (bf16, f16)
+        self.values = values      # uint16 (u16 codes, bf16 or f16 bits), uint8 (e4m3 codes), uint32 (f32 bits)
+        self.scales = scales      # float32[1] (u16), float32[nrows] (fp8) or None (bf16, f16, f32)
         self.decoded = decoded    # float64[nnz], exact value of each stored entry
 
     @property
@@ -172,6 +174,11 @@ def encode(csr, fmt: int) -> Encoded:
         lib.oracle_encode_f16(nnz, _ptr(v), _ptr(q))
         lib.oracle_decode_f16(nnz, _ptr(q), _ptr(dec))
         return Encoded(fmt, csr.nrows, csr.ncols, rp, col, q, None, dec)
+    if fmt == F32:
+        q = np.empty(nnz, dtype=np.uint32)
+        lib.oracle_encode_f32(nnz, _ptr(v), _ptr(q))
+        lib.oracle_decode_f32(nnz, _ptr(q), _ptr(dec))
+        return Encoded(fmt, csr.nrows, csr.ncols, rp, col, q, None, dec)
     if fmt == FP8E4M3_ROWSCALE:
         q = np.empty(nnz, dtype=np.uint8)
         s = np.empty(csr.nrows, dtype=np.float32)
@@ -197,6 +204,9 @@ def decode(fmt, nrows, row_ptr, values, scales) -> np.ndarray:
     elif fmt == F16:
         q = _c(values, np.uint16)
         lib.oracle_decode_f16(nnz, _ptr(q), _ptr(dec))
+    elif fmt == F32:
+        q = _c(values, np.uint32)
+        lib.oracle_decode_f32(nnz, _ptr(q), _ptr(dec))
     elif fmt == FP8E4M3_ROWSCALE:
         q = _c(values, np.uint8)
         s = _c(scales, np.float32)

@@ -26,6 +26,9 @@
  *   F16       : IEEE 754 binary16 (1 sign, 5 exponent with bias 15, 10 fraction
  *               bits, subnormals m/1024 * 2^-14), a = half value (the paper's
  *               "Half" storage, Sec. IV)
+ *   F32       : IEEE 754 binary32, a = float value (the paper's "Single"
+ *               configuration, Sec. IV); encoded by C's double-to-float
+ *               conversion (round to nearest, ties to even)
  * Encoders follow the readings: u16 s = fl32(max v / 65535), q = RNE(v/s)
  * clamped to [0,65535]; BF16 = round-to-nearest-even of the FP64 value; FP8
  * s_r = fl32(row max / 448) (1 for empty or all-zero rows), q = nearest E4M3
@@ -159,6 +162,15 @@ int oracle_encode_u16(uint64_t nnz, const double* v, float* scale, uint16_t* q) 
 int oracle_encode_bf16(uint64_t nnz, const double* v, uint16_t* out) {
     for (uint64_t k = 0; k < nnz; ++k) out[k] = oracle_bf16_round(v[k]);
     return 0;
+}
+
+int oracle_encode_f32(uint64_t nnz, const double* v, float* out) {
+    for (uint64_t k = 0; k < nnz; ++k) out[k] = (float)v[k];
+    return 0;
+}
+
+void oracle_decode_f32(uint64_t nnz, const float* bits, double* a) {
+    for (uint64_t k = 0; k < nnz; ++k) a[k] = (double)bits[k];
 }
 
 int oracle_encode_f16(uint64_t nnz, const double* v, uint16_t* out) {

@@ -24,8 +24,9 @@ from . import _build
 __all__ = ["build", "load", "DoseMatrix", "DoseError", "FORMATS", "spmv_batched", "adjoint_noalloc", "dose_spmv",
            "QuadraticDoseObjective", "pg_solve", "PGSolver", "encode_host", "library_path", "selftest_bounded_wait"]
 
-FORMATS = {"u16": 0, "bf16": 1, "fp8": 2, "f16": 3}
-_NO_SCALES = ("bf16", "f16")
+FORMATS = {"u16": 0, "bf16": 1, "fp8": 2, "f16": 3, "f32": 4}
+_NO_SCALES = ("bf16", "f16", "f32")
+_VAL_NP = {"fp8": np.uint8, "f32": np.uint32}      # stored value dtype (default uint16)
 CREATE_COMPENSATED = 0x1
 CREATE_U16_INDEX = 0x2
 SPMV_F64_NATIVE = 0x1
@@ -127,6 +128,12 @@ def load():
     return _lib
 
 
+def _val_torch(fmt):
+    """torch dtype carrying the stored values' bits."""
+    torch = _torch()
+    return {"fp8": torch.uint8, "f32": torch.int32}.get(fmt, torch.int16)
+
+
 def _check(status: int):
     if status != 0:
         msg = load().dose_last_error().decode(errors="replace")
@@ -171,7 +178,7 @@ def encode_host(fmt: str, row_ptr: np.ndarray, values_f64: np.ndarray):
     v = np.ascontiguousarray(values_f64, dtype=np.float64)
     nrows = rp.size - 1
     f = FORMATS[fmt]
-    codes = np.empty(v.size, dtype=np.uint8 if fmt == "fp8" else np.uint16)
+    codes = np.empty(v.size, dtype=_VAL_NP.get(fmt, np.uint16))
     scales = np.empty(nrows if fmt == "fp8" else 1, dtype=np.float32)
     _check(lib.dose_encode_host(f, nrows, rp.ctypes.data, v.size, v.ctypes.data if v.size else None,
                                 codes.ctypes.data if codes.size else None, scales.ctypes.data))
@@ -217,14 +224,14 @@ class DoseMatrix:
         d = _Desc()
         d.nrows, d.ncols, d.nnz, d.fmt = nrows, int(ncols), nnz, FORMATS[fmt]
         d.on_device = 1 if on_dev else 0
-        vdt_np = np.uint8 if fmt == "fp8" else np.uint16
+        vdt_np = _VAL_NP.get(fmt, np.uint16)
         if on_dev:
             d.row_ptr = dev(row_ptr, torch.int32, "row_ptr") if row_ptr.dtype == torch.int32 else \
                 dev(row_ptr.view(torch.int32), torch.int32, "row_ptr")
             d.col_idx = dev(col if col.dtype == torch.int32 else col.view(torch.int32), torch.int32, "col")
             if values is None:
                 raise ValueError("device CSR needs encoded values")
-            vt = torch.uint8 if fmt == "fp8" else torch.int16
+            vt = _val_torch(fmt)
             d.values = dev(values if values.dtype == vt else values.view(vt), vt, "values")
             if fmt not in _NO_SCALES:
                 d.scales = dev(scales, torch.float32, "scales")
@@ -360,14 +367,14 @@ def adjoint_noalloc(row_ptr, col, values, r, *, ncols: int, fmt: str = "u16", sc
                     row_scales=None, g=None, stream=None):
     """g = A^T r from caller-held device CSR arrays, allocating no device memory
     in the library (dose_adjoint_noalloc).  All arrays are CUDA tensors: row_ptr
-    and col int32 (bit patterns of uint32), values int16 (u16/bf16 codes) or
+    and col int32 (bit patterns of uint32), values int16 (u16/bf16/f16 codes), int32 (f32 bits) or
     uint8 (fp8), r float32; g (optional) float32 [ncols]."""
     torch = _torch()
     nrows = int(row_ptr.numel()) - 1
     nnz = int(col.numel())
     if g is None:
         g = torch.empty(ncols, dtype=torch.float32, device=r.device)
-    vt = torch.uint8 if fmt == "fp8" else torch.int16
+    vt = _val_torch(fmt)
     rs = _dptr(row_scales, torch.float32, nrows, "row_scales") if fmt == "fp8" else None
     _check(load().dose_adjoint_noalloc(
         nrows, int(ncols), nnz, _dptr(row_ptr, torch.int32, nrows + 1, "row_ptr"), _dptr(col, torch.int32, nnz, "col"),

@@ -425,7 +425,7 @@ cudaError_t launch_adj_t(const dose_matrix* A, const AdjParams& p, size_t smem, 
 }
 
 size_t adj_smem(const dose_matrix* A, const AdjTuning& t, bool quad, uint32_t ws) {
-    const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const uint32_t esize = value_bytes(A->fmt);
     const uint32_t nvec = (quad ? 2 : 1) + (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, quad);
     const size_t col_bytes = round_up(A->adj.wwidth * 4, 128);
@@ -517,6 +517,10 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
             case DOSE_FMT_F16:
                 e = quad ? launch_adj_t<DOSE_FMT_F16, ADJ_MODE_QUADRATIC>(A, prm, smem, s)
                          : launch_adj_t<DOSE_FMT_F16, ADJ_MODE_ADJOINT>(A, prm, smem, s);
+                break;
+            case DOSE_FMT_F32:
+                e = quad ? launch_adj_t<DOSE_FMT_F32, ADJ_MODE_QUADRATIC>(A, prm, smem, s)
+                         : launch_adj_t<DOSE_FMT_F32, ADJ_MODE_ADJOINT>(A, prm, smem, s);
                 break;
             case DOSE_FMT_FP8E4M3_ROWSCALE:
                 e = quad ? launch_adj_t<DOSE_FMT_FP8E4M3_ROWSCALE, ADJ_MODE_QUADRATIC>(A, prm, smem, s)

@@ -54,7 +54,7 @@ struct StagedParams {
     int* err;
 };
 
-__device__ __forceinline__ uint32_t esize_of(int fmt) { return fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1u : 2u; }
+__device__ __forceinline__ uint32_t esize_of(int fmt) { return value_bytes(fmt); }
 
 __device__ __forceinline__ VecSet item_vecs(const StagedItem& it) {
     VecSet v;
@@ -123,12 +123,7 @@ __device__ __forceinline__ void spmm_rows(const StagedItem& it, const StageDesc&
             const uint32_t kg = off < len ? k4 : kb4;
             const uint4 cc = *reinterpret_cast<const uint4*>(colp + kg);
             float av[4];
-            if (sizeof(T) == 2) {
-                const uint2 qv = *reinterpret_cast<const uint2*>(valp + kg);
-                Fmt<FMT>::dec4(qv.x, qv.y, av);
-            } else {
-                Fmt<FMT>::dec4(*reinterpret_cast<const uint32_t*>(valp + kg), 0u, av);
-            }
+            load_vals4<FMT>(valp + kg, av);
             const uint32_t cu[4] = {cc.x, cc.y, cc.z, cc.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -296,6 +291,10 @@ __global__ void __launch_bounds__(32 * (kSpmmConsumerWarps + 1), 1) spmm_staged_
                         produce_stages<DOSE_FMT_BF16>(R, it.sched, sb, se, it.row_ptr, it.col, it.val, vecs, slot_base,
                                                       SL, p.slot_stride, full, empty, S, dwin, dbar, p.l2pf, p.err);
                         break;
+                    case DOSE_FMT_F32:
+                        produce_stages<DOSE_FMT_F32>(R, it.sched, sb, se, it.row_ptr, it.col, it.val, vecs, slot_base,
+                                                     SL, p.slot_stride, full, empty, S, dwin, dbar, p.l2pf, p.err);
+                        break;
                     default:
                         produce_stages<DOSE_FMT_FP8E4M3_ROWSCALE>(R, it.sched, sb, se, it.row_ptr, it.col, it.val,
                                                                   vecs, slot_base, SL, p.slot_stride, full, empty, S,
@@ -347,6 +346,10 @@ __global__ void __launch_bounds__(32 * (kSpmmConsumerWarps + 1), 1) spmm_staged_
                     break;
                 case DOSE_FMT_F16:
                     spmm_stage<DOSE_FMT_F16, NQ>(it, SL, slotp, slot, xw4, xw0, wlo, p.nvec, p.vec4 != 0, ctid, lane,
+                                                 cw, nct, r);
+                    break;
+                case DOSE_FMT_F32:
+                    spmm_stage<DOSE_FMT_F32, NQ>(it, SL, slotp, slot, xw4, xw0, wlo, p.nvec, p.vec4 != 0, ctid, lane,
                                                  cw, nct, r);
                     break;
                 default:
@@ -403,7 +406,8 @@ __device__ __forceinline__ void spmm_row(const BatchItem& it, uint32_t row, uint
         float s = 1.0f;
         if (FMT == DOSE_FMT_U16_SCALE) s = it.scale;
         if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) s = __ldg(it.row_scale + row);
-        it.D[(size_t)row * nvec + v] = (FMT == DOSE_FMT_BF16 || FMT == DOSE_FMT_F16) ? acc : __fmul_rn(s, acc);
+        it.D[(size_t)row * nvec + v] =
+            (FMT == DOSE_FMT_U16_SCALE || FMT == DOSE_FMT_FP8E4M3_ROWSCALE) ? __fmul_rn(s, acc) : acc;
     }
 }
 
@@ -434,6 +438,7 @@ __global__ void __launch_bounds__(256) spmm_global_kernel(const __grid_constant_
                 case DOSE_FMT_U16_SCALE: spmm_row<DOSE_FMT_U16_SCALE>(it, row, v, p.nvec); break;
                 case DOSE_FMT_BF16: spmm_row<DOSE_FMT_BF16>(it, row, v, p.nvec); break;
                 case DOSE_FMT_F16: spmm_row<DOSE_FMT_F16>(it, row, v, p.nvec); break;
+                case DOSE_FMT_F32: spmm_row<DOSE_FMT_F32>(it, row, v, p.nvec); break;
                 default: spmm_row<DOSE_FMT_FP8E4M3_ROWSCALE>(it, row, v, p.nvec); break;
             }
         }
@@ -441,7 +446,7 @@ __global__ void __launch_bounds__(256) spmm_global_kernel(const __grid_constant_
 }
 
 uint32_t staged_slot_bytes(const dose_matrix* M) {
-    const uint32_t es = M->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const uint32_t es = value_bytes(M->fmt);
     const uint32_t nv = M->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
     return slot_layout(M->adj.tuning.tile_nnz, M->adj.tuning.tile_rows, es, nv, false).bytes;
 }

@@ -135,6 +135,14 @@ static dose_status encode(dose_format fmt, uint32_t nrows, const uint32_t* row_p
         for (uint64_t k = 0; k < nnz; ++k) q[k] = encode_f16(v[k]);
         return DOSE_OK;
     }
+    if (fmt == DOSE_FMT_F32) {
+        float* q = static_cast<float*>(codes);
+        for (uint64_t k = 0; k < nnz; ++k) {
+            q[k] = (float)v[k];  // IEEE conversion: round to nearest, ties to even
+            if (std::isinf(q[k])) return invalid("values_f64 exceed the FP32 range");
+        }
+        return DOSE_OK;
+    }
     if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {
         uint8_t* q = static_cast<uint8_t*>(codes);
         for (uint32_t i = 0; i < nrows; ++i) {
@@ -434,7 +442,7 @@ static cudaError_t upload(T** dst, const T* src, size_t n, size_t alloc_n) {
 // adjoint schedule (`windowed`) gets per-CTA column windows.
 static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& t, bool windowed = false) {
     const bool win = windowed && !A->host_row_cmin.empty();
-    const uint32_t vbytes = (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2) + 4;
+    const uint32_t vbytes = value_bytes(A->fmt) + 4;
     Schedule S = build_schedule(A->host_row_ptr, A->nrows, t, D.grid, win ? A->host_row_cmin.data() : nullptr,
                                 win ? A->host_row_cmax.data() : nullptr, A->ncols, vbytes);
     free_dev_schedule(D);
@@ -531,7 +539,7 @@ const char* dose_version(void) { return "libdose 0.1 (sm_103a)"; }
 dose_status dose_encode_host(dose_format fmt, uint32_t nrows, const uint32_t* row_ptr, uint64_t nnz,
                              const double* values_f64, void* codes, float* scales) {
     if ((nnz && (!values_f64 || !codes)) || !row_ptr) return invalid("dose_encode_host: null pointer");
-    if (fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_F16 && !scales)
+    if ((fmt == DOSE_FMT_U16_SCALE || fmt == DOSE_FMT_FP8E4M3_ROWSCALE) && !scales)
         return invalid("dose_encode_host: scales needed for this format");
     return encode(fmt, nrows, row_ptr, nnz, values_f64, codes, scales);
 }
@@ -545,7 +553,7 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
         return invalid("DOSE_CREATE_U16_INDEX needs ncols <= 65536 (16-bit column indices)");
     const dose_format fmt = desc->fmt;
     if (fmt != DOSE_FMT_U16_SCALE && fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_FP8E4M3_ROWSCALE &&
-        fmt != DOSE_FMT_F16)
+        fmt != DOSE_FMT_F16 && fmt != DOSE_FMT_F32)
         return invalid("dose_create_matrix: unknown format");
     if (desc->nnz >= (1ull << 32)) return invalid("nnz must be < 2^32 (uint32 row pointers)");
     if (desc->nrows == 0xFFFFFFFFu) return invalid("nrows must be < 2^32 - 1");
@@ -553,11 +561,11 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if (desc->nnz && !desc->col_idx) return invalid("col_idx is NULL");
     if (desc->on_device && desc->values_f64) return invalid("values_f64 must be host memory (on_device=0)");
     if (!desc->values && !desc->values_f64 && desc->nnz) return invalid("neither values nor values_f64 given");
-    if (desc->values && fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_F16 && !desc->scales)
+    if (desc->values && (fmt == DOSE_FMT_U16_SCALE || fmt == DOSE_FMT_FP8E4M3_ROWSCALE) && !desc->scales)
         return invalid("scales are NULL for this format");
     const uint32_t nrows = desc->nrows, ncols = desc->ncols;
     const uint64_t nnz = desc->nnz;
-    const size_t esize = fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const size_t esize = value_bytes(fmt);
     cudaStream_t s = as_stream(stream);
 
     // Bring the structure to the host (validation and scheduling need it).
@@ -633,6 +641,13 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
                 uint16_t h;
                 std::memcpy(&h, vals.data() + 2 * k, 2);
                 if ((h & 0x7C00u) == 0x7C00u) return invalid("F16 value is infinite or NaN at entry " + std::to_string(k));
+            }
+        if (fmt == DOSE_FMT_F32)
+            for (uint64_t k = 0; k < nnz; ++k) {
+                uint32_t w;
+                std::memcpy(&w, vals.data() + 4 * k, 4);
+                if ((w & 0x7F800000u) == 0x7F800000u)
+                    return invalid("F32 value is infinite or NaN at entry " + std::to_string(k));
             }
     }
     if (fmt == DOSE_FMT_U16_SCALE) scale = scl.empty() ? 1.0f : scl[0];
@@ -832,7 +847,7 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     out->adj_window = A->adj.wwidth;
     out->max_row_len = A->max_row_len;
     out->device_bytes = A->device_bytes;
-    const uint64_t vb = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const uint64_t vb = value_bytes(A->fmt);
     const uint64_t nz = A->nnz, nr = A->nrows, nc = A->ncols;
     const uint64_t rs = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 4 * nr : 0;  // row scales
     // Algorithmic bytes: every stored byte of A once, the vectors once.

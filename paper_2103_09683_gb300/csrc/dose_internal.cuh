@@ -166,6 +166,11 @@ cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const fl
                                 float* const* D, int nvec, cudaStream_t s, std::string* why);
 
 constexpr uint32_t kMaxSmemPerBlock = 227 * 1024;
+
+// Stored bytes per value of a format.
+__host__ __device__ constexpr uint32_t value_bytes(int fmt) {
+    return fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1u : (fmt == DOSE_FMT_F32 ? 4u : 2u);
+}
 constexpr uint32_t kMaxAdjWarps = 20;      // producer + forward + scatter warps of the adjoint kernels
 constexpr uint32_t kAdjColumnGroups = 16;  // column groups of the adjoint schedule (CTAs per group: grid / 16)
 constexpr uint32_t kXSmemMaxCols = 16384;  // x staged in shared memory up to 64 KB

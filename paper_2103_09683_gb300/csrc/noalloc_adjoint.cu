@@ -44,6 +44,7 @@ std::mutex scratch_mu;
 
 __device__ __forceinline__ float dec_value(int fmt, const void* values, uint32_t k) {
     if (fmt == DOSE_FMT_FP8E4M3_ROWSCALE) return dev::dec_e4m3(static_cast<const uint8_t*>(values)[k]);
+    if (fmt == DOSE_FMT_F32) return static_cast<const float*>(values)[k];
     const uint16_t q = static_cast<const uint16_t*>(values)[k];
     if (fmt == DOSE_FMT_F16) return dev::f16_to_f32(q);
     return fmt == DOSE_FMT_BF16 ? dev::dec_bf16(q) : dev::dec_u16(q);
@@ -125,7 +126,7 @@ extern "C" dose_status dose_adjoint_noalloc(uint32_t nrows, uint32_t ncols, uint
                                             const float* row_scales, float scale, const float* r, float* g,
                                             void* stream) {
     if (fmt != DOSE_FMT_U16_SCALE && fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_FP8E4M3_ROWSCALE &&
-        fmt != DOSE_FMT_F16) {
+        fmt != DOSE_FMT_F16 && fmt != DOSE_FMT_F32) {
         set_error("dose_adjoint_noalloc: unknown format");
         return DOSE_ERR_INVALID_ARG;
     }

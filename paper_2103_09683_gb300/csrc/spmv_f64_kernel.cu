@@ -149,7 +149,6 @@ struct Acc<F64_DP> {
 template <int FMT, int MODE, uint32_t L, uint32_t IW>
 __device__ __forceinline__ Acc<MODE> dot_vec64(const SlotPtrs<FMT, IW>& sp, const uint2* __restrict__ xsp, uint32_t zc,
                                                uint32_t kb, uint32_t ke, uint32_t li, uint32_t iters) {
-    using T = typename Fmt<FMT>::T;
     Acc<MODE> acc[4];
     const int len = (int)(ke - kb);
     const uint32_t kb4 = kb & ~3u;
@@ -166,12 +165,7 @@ __device__ __forceinline__ Acc<MODE> dot_vec64(const SlotPtrs<FMT, IW>& sp, cons
             c[0] = cc.x & 0xFFFFu; c[1] = cc.x >> 16; c[2] = cc.y & 0xFFFFu; c[3] = cc.y >> 16;
         }
         float a[4];
-        if (sizeof(T) == 2) {
-            const uint2 qv = *reinterpret_cast<const uint2*>(sp.val + kg);
-            Fmt<FMT>::dec4(qv.x, qv.y, a);
-        } else {
-            Fmt<FMT>::dec4(*reinterpret_cast<const uint32_t*>(sp.val + kg), 0u, a);
-        }
+        load_vals4<FMT>(sp.val + kg, a);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const bool m = (uint32_t)(off + u) < (uint32_t)len;
@@ -352,7 +346,7 @@ cudaError_t launch_fmt(const dose_matrix* A, const Spmv64Params& p, size_t smem,
 
 size_t spmv_f64_smem_bytes(const dose_matrix* A, bool x_in_smem) {
     const Tuning& t = A->fwd.tuning;
-    const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const uint32_t esize = value_bytes(A->fmt);
     const uint32_t nvec = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
     const uint32_t iw = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, false, iw);
@@ -399,6 +393,7 @@ cudaError_t launch_spmv_f64(const dose_matrix* A, const double* x, double* d, bo
         case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, smem, native, xsmem, idx16, s);
         case DOSE_FMT_BF16: return launch_fmt<DOSE_FMT_BF16>(A, p, smem, native, xsmem, idx16, s);
         case DOSE_FMT_F16: return launch_fmt<DOSE_FMT_F16>(A, p, smem, native, xsmem, idx16, s);
+        case DOSE_FMT_F32: return launch_fmt<DOSE_FMT_F32>(A, p, smem, native, xsmem, idx16, s);
         case DOSE_FMT_FP8E4M3_ROWSCALE:
             return launch_fmt<DOSE_FMT_FP8E4M3_ROWSCALE>(A, p, smem, native, xsmem, idx16, s);
     }

@@ -13,7 +13,7 @@
 //     its non-empty rows evenly: groups of L lanes per row, L chosen per stage
 //     from its mean row length (row-length binning); rows longer than coop_nnz
 //     are reduced by the whole CTA;
-//   * values are decoded in registers (u16, bf16, f16, e4m3 -> f32),
+//   * values are decoded in registers (u16, bf16, f16, e4m3 -> f32; f32 as is),
 //     x sits in shared memory, accumulation is FP32 (optionally compensated),
 //     and the U16/FP8 scale is applied once per row.
 // Every reduction has a fixed shape, so results are bitwise reproducible.
@@ -265,7 +265,7 @@ cudaError_t launch_fmt(const dose_matrix* A, const SpmvParams& p, size_t smem, b
 bool spmv_x_in_smem(const dose_matrix* A) { return A->ncols <= kXSmemMaxCols; }
 
 size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem) {
-    const uint32_t esize = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 2;
+    const uint32_t esize = value_bytes(A->fmt);
     const uint32_t nvec = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
     const uint32_t iw = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, false, iw);
@@ -304,6 +304,7 @@ cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStre
         case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, smem, comp, xsmem, idx16, s);
         case DOSE_FMT_BF16: return launch_fmt<DOSE_FMT_BF16>(A, p, smem, comp, xsmem, idx16, s);
         case DOSE_FMT_F16: return launch_fmt<DOSE_FMT_F16>(A, p, smem, comp, xsmem, idx16, s);
+        case DOSE_FMT_F32: return launch_fmt<DOSE_FMT_F32>(A, p, smem, comp, xsmem, idx16, s);
         case DOSE_FMT_FP8E4M3_ROWSCALE:
             return launch_fmt<DOSE_FMT_FP8E4M3_ROWSCALE>(A, p, smem, comp, xsmem, idx16, s);
     }

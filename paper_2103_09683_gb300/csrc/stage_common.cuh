@@ -119,6 +119,45 @@ struct Fmt<DOSE_FMT_F16> {
 #endif
 };
 
+template <>
+struct Fmt<DOSE_FMT_F32> {
+    using T = uint32_t;
+    static constexpr uint32_t kAlign = 4;
+#ifdef __CUDACC__
+    __device__ static float dec(T v) { return __uint_as_float(v); }
+    __device__ static float lds(uint32_t a) { return dev::lds_f32(a); }
+    __device__ static float lds_lt(uint32_t k, uint32_t ke, uint32_t a) { return dev::lds_f32_lt(k, ke, a); }
+    __device__ static void lds4(bool p, uint32_t a, float* w) {
+        const uint4 q = dev::lds_v4_if(p, a);
+        w[0] = __uint_as_float(q.x);
+        w[1] = __uint_as_float(q.y);
+        w[2] = __uint_as_float(q.z);
+        w[3] = __uint_as_float(q.w);
+    }
+#endif
+};
+
+#ifdef __CUDACC__
+// The four stored values at p (a group of four consecutive entries, 4-aligned),
+// decoded to FP32: one 16-, 8- or 4-byte load.
+template <int FMT>
+__device__ __forceinline__ void load_vals4(const typename Fmt<FMT>::T* p, float (&a)[4]) {
+    using T = typename Fmt<FMT>::T;
+    if constexpr (sizeof(T) == 4) {
+        const uint4 q = *reinterpret_cast<const uint4*>(p);
+        a[0] = __uint_as_float(q.x);
+        a[1] = __uint_as_float(q.y);
+        a[2] = __uint_as_float(q.z);
+        a[3] = __uint_as_float(q.w);
+    } else if constexpr (sizeof(T) == 2) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        Fmt<FMT>::dec4(q.x, q.y, a);
+    } else {
+        Fmt<FMT>::dec4(*reinterpret_cast<const uint32_t*>(p), 0u, a);
+    }
+}
+#endif
+
 __host__ __device__ constexpr uint32_t round_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 
 constexpr uint32_t kMaxVec = 3;  // per-row float vectors staged with a slot
@@ -434,13 +473,24 @@ __device__ __forceinline__ float dot_fixed(const SlotView& v, uint32_t xs, uint3
 // that predicate guards its gather, its FMA and (scatter) its store, so no
 // loaded value needs a default and masked entries cost no select.
 
-// Column indices (one 16-byte load) and stored values (8 bytes, or 4 for FP8)
+// Column indices (one 16-byte load) and stored values (8 bytes; 4 for FP8, 16 for F32)
 // of the group at shared addresses ca / va, loaded only if the group reaches
 // into the row (off < len), decoded to FP32.  Registers of a group that is not
 // loaded hold unspecified values that no guarded access ever uses.
 template <int FMT>
 __device__ __forceinline__ void load_group(int off, int len, uint32_t ca, uint32_t va, uint32_t (&c)[4],
                                            float (&a)[4]) {
+    if constexpr (sizeof(typename Fmt<FMT>::T) == 4) {
+        uint32_t q[4];
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.lt.s32 p, %8, %9;\n\t"
+            "@p ld.shared.v4.u32 {%0, %1, %2, %3}, [%10];\n\t"
+            "@p ld.shared.v4.u32 {%4, %5, %6, %7}, [%11];\n\t}"
+            : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3])
+            : "r"(off), "r"(len), "r"(ca), "r"(va));
+        for (int u = 0; u < 4; ++u) a[u] = __uint_as_float(q[u]);
+        return;
+    } else {
     uint32_t q0, q1 = 0;
     if (sizeof(typename Fmt<FMT>::T) == 2) {
         asm volatile(
@@ -458,6 +508,7 @@ __device__ __forceinline__ void load_group(int off, int len, uint32_t ca, uint32
             : "r"(off), "r"(len), "r"(ca), "r"(va));
     }
     Fmt<FMT>::dec4(q0, q1, a);
+    }
 }
 
 // acc[u] += a[u] * x[c[u]] for the group's entries inside the row; x at shared
@@ -554,12 +605,7 @@ __device__ __forceinline__ float dot_vec_p(const SlotPtrs<FMT, IW>& sp, const fl
             c[0] = cc.x & 0xFFFFu; c[1] = cc.x >> 16; c[2] = cc.y & 0xFFFFu; c[3] = cc.y >> 16;
         }
         float a[4];
-        if (sizeof(T) == 2) {
-            const uint2 qv = *reinterpret_cast<const uint2*>(sp.val + kg);
-            Fmt<FMT>::dec4(qv.x, qv.y, a);
-        } else {
-            Fmt<FMT>::dec4(*reinterpret_cast<const uint32_t*>(sp.val + kg), 0u, a);
-        }
+        load_vals4<FMT>(sp.val + kg, a);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const bool m = (uint32_t)(off + u) < (uint32_t)len;

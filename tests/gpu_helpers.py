@@ -6,7 +6,8 @@ import dosegen
 import oracle
 import paper_2103_09683_gb300 as dose
 
-OFMT = {"u16": oracle.U16_SCALE, "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE, "f16": oracle.F16}
+OFMT = {"u16": oracle.U16_SCALE, "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE, "f16": oracle.F16,
+        "f32": oracle.F32}
 
 # Max relative error of an FP32-accumulated row sum of non-negative terms
 # against the FP64 oracle on the same decoded matrix.

@@ -22,7 +22,7 @@ from gpu_helpers import edge_case_matrices, make
 
 pytestmark = pytest.mark.gpu
 
-FMTS = ["f16", "u16", "bf16", "fp8"]
+FMTS = ["f16", "u16", "bf16", "fp8", "f32"]
 
 
 @pytest.fixture(scope="module", autouse=True)

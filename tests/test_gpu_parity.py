@@ -38,7 +38,7 @@ def tiny():
 
 # ---------------------------------------------------------------- forward
 
-@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8", "f16"])
+@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8", "f16", "f32"])
 @pytest.mark.parametrize("compensated", [False, True])
 def test_forward_tiny_beam(tiny, fmt, compensated):
     A, enc = make(tiny, fmt, compensated=compensated)
@@ -67,7 +67,7 @@ def test_forward_edge_cases(name, fmt):
         A.device_status()
 
 
-@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8", "f16"])
+@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8", "f16", "f32"])
 @pytest.mark.parametrize("compensated", [False, True])
 def test_forward_16bit_column_indices(tiny, fmt, compensated):
     """DOSE_CREATE_U16_INDEX: dose_spmv reads 16-bit column indices; results
@@ -97,7 +97,7 @@ def test_forward_16bit_column_indices_edge_cases(name):
         A.device_status()
 
 
-@pytest.mark.parametrize("fmt", ["u16", "fp8", "bf16", "f16"])
+@pytest.mark.parametrize("fmt", ["u16", "fp8", "bf16", "f16", "f32"])
 def test_unit_vectors_reproduce_stored_columns_bit_exact(tiny, fmt):
     A, enc = make(tiny, fmt)
     rng = np.random.default_rng(0)
@@ -133,7 +133,7 @@ def test_compensated_long_rows_adversarial():
 
 # ---------------------------------------------------------------- adjoint
 
-@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8", "f16"])
+@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8", "f16", "f32"])
 def test_adjoint_tiny_beam(tiny, fmt):
     A, enc = make(tiny, fmt)
     r = np.random.default_rng(4).normal(size=tiny.nrows).astype(np.float32)
@@ -320,7 +320,7 @@ def test_batched_spmm_small(nvec):
     mats.append(dosegen.random_csr(40, 3000, seed=30, lengths=[0, 2500] + [7] * 38))
     handles, encs, Xs = [], [], []
     for i, m in enumerate(mats):
-        A, enc = make(m, ("u16", "fp8", "bf16", "f16")[i % 4])
+        A, enc = make(m, ("u16", "fp8", "bf16", "f16", "f32")[i % 5])
         handles.append(A)
         encs.append(enc)
         Xs.append(_to(dosegen.spot_weights(m.ncols, 100 + i, nvec=nvec).reshape(m.ncols, nvec)))
@@ -350,7 +350,7 @@ def test_batched_spmm_pencil_beams_staged_and_graph():
     the staged form (each CTA's window of X in shared memory), checked against the
     oracle, bitwise repeatable, and identical when replayed from a CUDA graph."""
     mats = _small_beam_batch()
-    fmts = ["u16", "bf16", "fp8", "f16", "fp8", "bf16"]
+    fmts = ["u16", "bf16", "fp8", "f16", "f32", "bf16"]
     handles, encs, Xs = [], [], []
     for i, (m, f) in enumerate(zip(mats, fmts)):
         A, enc = make(m, f)

@@ -272,6 +272,23 @@ def test_f16_encoding_error_bound():
     assert np.all(np.abs(enc.decoded - A.val)[~normal] <= 2.0 ** -25)
 
 
+def test_f32_encoding_matches_numpy_rne():
+    """FP32 storage (the paper's Single): numpy's FP64 -> FP32 rounding, including
+    exact halfway points between neighbouring floats."""
+    rng = np.random.default_rng(19)
+    f = rng.uniform(0, 1, 200).astype(np.float32)
+    mids = (f.astype(np.float64) + np.nextafter(f, np.float32(2)).astype(np.float64)) / 2
+    v = np.concatenate([rng.uniform(0, 1, 3000), rng.uniform(0, 1e-30, 200), mids, [0.0, 1e-45, 3.4e38]])
+    A = dosegen.CSR(1, v.size, np.array([0, v.size], dtype=np.uint32), np.arange(v.size, dtype=np.uint32), v)
+    enc = oracle.encode(A, oracle.F32)
+    assert enc.scales is None and enc.values.dtype == np.uint32
+    assert np.array_equal(enc.values, v.astype(np.float32).view(np.uint32))
+    assert np.array_equal(enc.decoded, v.astype(np.float32).astype(np.float64))
+    # ties went to the even neighbour
+    even = np.where(f.view(np.uint32) % 2 == 0, f, np.nextafter(f, np.float32(2)))
+    assert np.array_equal(enc.values[3200:3400], even.view(np.uint32))
+
+
 def test_u16_encoding_nearest_code():
     A = dosegen.random_csr(100, 50, seed=14, density=0.3)
     enc = oracle.encode(A, oracle.U16_SCALE)
