@@ -171,6 +171,61 @@ def generate(beam: Beam) -> CSR:
     return CSR(beam.nrows, beam.ncols, row_ptr, col, val)
 
 
+def generate_along(beam: Beam, axis: str) -> CSR:
+    """The beam entering the patient grid `beam.grid` = (nx, ny, nz) along +z
+    (the generator's own direction), +x or +y.  The matrix is generated on the
+    permuted grid whose depth axis is the entry axis, then its rows are put in
+    patient voxel order (row (z*ny + y)*nx + x); the lattice lies in the plane
+    across the entry axis, with the generator's lateral axes in cyclic order."""
+    nx, ny, nz = beam.grid
+    if axis == "z":
+        return generate(beam)
+    if axis == "x":      # generator (gx, gy, gz) = patient (y, z, x)
+        g = replace(beam, grid=(ny, nz, nx))
+    elif axis == "y":    # generator (gx, gy, gz) = patient (z, x, y)
+        g = replace(beam, grid=(nz, nx, ny))
+    else:
+        raise ValueError("axis must be 'x', 'y' or 'z'")
+    csr = generate(g)
+    gnx, gny, gnz = g.grid
+    gz, gy, gx = np.meshgrid(np.arange(gnz), np.arange(gny), np.arange(gnx), indexing="ij")
+    if axis == "x":
+        x, y, z = gz, gx, gy
+    else:
+        x, y, z = gy, gz, gx
+    patient_row = ((z * ny + y) * nx + x).reshape(-1)          # generator row -> patient row
+    src = np.empty(csr.nrows, dtype=np.int64)
+    src[patient_row] = np.arange(csr.nrows)                    # patient row -> generator row
+    rp = csr.row_ptr.astype(np.int64)
+    lens = (rp[1:] - rp[:-1])[src]
+    row_ptr = np.zeros(csr.nrows + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    take = np.repeat(rp[src] - row_ptr[:-1], lens) + np.arange(int(row_ptr[-1]))
+    return CSR(csr.nrows, csr.ncols, row_ptr.astype(np.uint32), csr.col[take], csr.val[take])
+
+
+# A three-beam plan on one patient grid (entry along +z, +x, +y), each beam under
+# the nine lateral setup shifts: scenario s holds the three beams under shift s.
+ROBUST_GRID = (160, 160, 100)
+ROBUST_AXES = ("z", "x", "y")
+
+
+def robust_plan(grid=ROBUST_GRID, lattice=(40, 25), base: Beam = None) -> list:
+    """Scenarios x beams: out[s][b] = (Beam, axis) for the 9 setup shifts and the
+    three entry axes.  Beam b's lattice spans its lateral plane with the
+    clinical beam's spacing, sigma and tau unless `base` gives others."""
+    base = base or CLINICAL
+    out = []
+    for sh in _SCENARIO_SHIFTS:
+        row = []
+        for b, axis in enumerate(ROBUST_AXES):
+            beam = replace(base, grid=tuple(grid), lattice=tuple(lattice), seed=SEED0 + 7 + 100 * (b + 1),
+                           shift=sh)
+            row.append((beam, axis))
+        out.append(row)
+    return out
+
+
 def spot_weights(n: int, seed: int, nvec: int = 1) -> np.ndarray:
     """Seeded FP32 spot weights uniform in [0,1): shape (n,) or (n, nvec) row-major."""
     lib = _load()

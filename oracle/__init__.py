@@ -90,6 +90,7 @@ def _load():
                 "oracle_fgrad": (_F64, [_U32, _U32, _P, _P, _P, _P, _P, _P, _P, _P]),
                 "oracle_pg": (ctypes.c_int, [_U32, _U32, _P, _P, _P, _P, _P, _F64, _U32, _P, _P]),
                 "oracle_norm2_sq": (_F64, [_U32, _U32, _P, _P, _P, _U32]),
+                "oracle_robust_combine": (_F64, [_U32, _U32, ctypes.c_int, _P, _P, _P, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -285,6 +286,41 @@ def fgrad(nrows, ncols, row_ptr, col, a, x, p, w):
     f = lib.oracle_fgrad(nrows, ncols, _ptr(rp), _ptr(cl), _ptr(av), _ptr(xv), _ptr(pv), _ptr(wv),
                          _ptr(g), _ptr(work))
     return f, g
+
+
+def multibeam_spmv(beams, xs) -> np.ndarray:
+    """Total dose of a plan, d = sum_b A_b x_b over its beams on one voxel grid
+    (Sec. I: the doses of multiple beams): each beam's FP64 product (spmv),
+    added in beam order.  beams: list of (nrows, row_ptr, col, a)."""
+    d = None
+    for (nrows, rp, col, a), x in zip(beams, xs):
+        db = spmv(nrows, rp, col, a, x)
+        d = db if d is None else d + db
+    return d
+
+
+EXPECTED, WORST_CASE = 0, 1
+
+
+def robust_quadratic(scenarios, x, p, w, mode, prob=None):
+    """Robust quadratic dose objective over scenarios (Sec. I: uncertainty
+    realisations), each scenario a matrix (nrows, ncols, row_ptr, col, a) of the
+    same shape: f_s, g_s of every scenario (fgrad), combined by
+    oracle_robust_combine (expected value with probabilities `prob`, default
+    uniform; or worst case).  Returns (F, G, f_s, s*)."""
+    lib = _load()
+    S = len(scenarios)
+    ncols = scenarios[0][1]
+    fs = np.empty(S, dtype=np.float64)
+    gs = np.empty((S, ncols), dtype=np.float64)
+    for s, (nr, nc, rp, col, a) in enumerate(scenarios):
+        fs[s], gs[s] = fgrad(nr, nc, rp, col, a, x, p, w)
+    pr = _c(np.full(S, 1.0 / S) if prob is None else prob, np.float64)
+    G = np.empty(ncols, dtype=np.float64)
+    arg = ctypes.c_int32(0)
+    F = lib.oracle_robust_combine(S, ncols, int(mode), _ptr(pr), _ptr(fs), gs.ctypes.data, _ptr(G),
+                                  ctypes.addressof(arg))
+    return F, G, fs, int(arg.value)
 
 
 def pg(nrows, ncols, row_ptr, col, a, x0, p, w, eta, iters):

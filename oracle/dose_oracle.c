@@ -308,6 +308,35 @@ int oracle_pg(uint32_t nrows, uint32_t ncols, const uint32_t* row_ptr, const uin
     return 0;
 }
 
+/* Robust quadratic objective over S dose scenarios (Sec. I: doses under several
+ * realisations of the uncertainties in every optimisation iteration), from the
+ * per-scenario values f_s = f(A_s x) and gradients g_s = grad f(A_s x) (g row s
+ * of an S x ncols array):
+ *   mode 0, expected:   F = sum_s prob_s f_s,  G = sum_s prob_s g_s;
+ *   mode 1, worst case: s* = the first s with the largest f_s, F = f_s*, G = g_s*
+ *                       (a subgradient of max_s f_s).
+ * Returns F and writes G; returns s* through *arg (mode 0: -1). */
+double oracle_robust_combine(uint32_t S, uint32_t ncols, int mode, const double* prob, const double* f_s,
+                             const double* g_s, double* G, int32_t* arg) {
+    if (mode == 0) {
+        double F = 0.0;
+        for (uint32_t s = 0; s < S; ++s) F += prob[s] * f_s[s];
+        for (uint32_t j = 0; j < ncols; ++j) {
+            double t = 0.0;
+            for (uint32_t s = 0; s < S; ++s) t += prob[s] * g_s[(size_t)s * ncols + j];
+            G[j] = t;
+        }
+        *arg = -1;
+        return F;
+    }
+    uint32_t best = 0;
+    for (uint32_t s = 1; s < S; ++s)
+        if (f_s[s] > f_s[best]) best = s;
+    for (uint32_t j = 0; j < ncols; ++j) G[j] = g_s[(size_t)best * ncols + j];
+    *arg = (int32_t)best;
+    return f_s[best];
+}
+
 /* Largest eigenvalue of A^T A by `iters` power iterations from the all-ones vector. */
 double oracle_norm2_sq(uint32_t nrows, uint32_t ncols, const uint32_t* row_ptr,
                        const uint32_t* col, const double* a, uint32_t iters) {

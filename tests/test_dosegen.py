@@ -5,6 +5,7 @@ most rows are empty (about 70 % in Fig. 2) and row lengths are very uneven;
 the non-zero ratio of the paper's matrices is 0.6-2 %.
 """
 import numpy as np
+import pytest
 
 import dosegen
 
@@ -60,3 +61,39 @@ def test_ellipsoid_target():
     assert inside.sum() > 0 and np.all(w[inside] == 10.0) and np.all(w[~inside] == 1.0)
     # semi-axes (8, 8, 4): volume ~ 4/3 pi 256 voxels
     assert abs(inside.sum() - 4.0 / 3.0 * np.pi * 256) < 0.15 * 4.0 / 3.0 * np.pi * 256
+
+
+@pytest.mark.parametrize("axis", ["x", "y", "z"])
+def test_generate_along_permutes_rows_to_patient_order(axis):
+    """Row (z*ny + y)*nx + x of a beam entering along `axis` is the generator's
+    row at the permuted coordinates (depth axis = entry axis)."""
+    from dataclasses import replace
+    beam = replace(dosegen.TINY, grid=(12, 10, 8), lattice=(6, 5), spacing=(2.0, 2.0))
+    nx, ny, nz = beam.grid
+    pat = dosegen.generate_along(beam, axis)
+    if axis == "z":
+        g, gcoord = beam, lambda x, y, z: (x, y, z)
+    elif axis == "x":
+        g, gcoord = replace(beam, grid=(ny, nz, nx)), lambda x, y, z: (y, z, x)
+    else:
+        g, gcoord = replace(beam, grid=(nz, nx, ny)), lambda x, y, z: (z, x, y)
+    gen = dosegen.generate(g)
+    gnx, gny, _ = g.grid
+    assert pat.nnz == gen.nnz and pat.nrows == gen.nrows
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                r = (z * ny + y) * nx + x
+                gx, gy, gz = gcoord(x, y, z)
+                q = (gz * gny + gy) * gnx + gx
+                a = slice(pat.row_ptr[r], pat.row_ptr[r + 1])
+                b = slice(gen.row_ptr[q], gen.row_ptr[q + 1])
+                assert np.array_equal(pat.col[a], gen.col[b]) and np.array_equal(pat.val[a], gen.val[b])
+
+
+def test_robust_plan_shapes():
+    plan = dosegen.robust_plan()
+    assert len(plan) == 9 and all(len(s) == 3 for s in plan)
+    assert {ax for _, ax in plan[0]} == {"x", "y", "z"}
+    assert len({b.shift for b, _ in (s[0] for s in plan)}) == 9
+    assert all(b.grid == dosegen.ROBUST_GRID for s in plan for b, _ in s)

@@ -37,6 +37,9 @@ MUTATIONS = {
     "f16_truncates": ("q = ldexp(nearbyint(ldexp(m, 11)), ex - 11);", "q = ldexp(floor(ldexp(m, 11)), ex - 11);"),
     "f16_wrong_bias": ("v = ldexp(1.0 + (double)m / 1024.0, e - 15);", "v = ldexp(1.0 + (double)m / 1024.0, e - 14);"),
     "f16_subnormal_quantum": ("v = ldexp((double)m / 1024.0, -14);", "v = ldexp((double)m / 1024.0, -15);"),
+    "robust_expected_drops_probability": ("for (uint32_t s = 0; s < S; ++s) F += prob[s] * f_s[s];",
+                                          "for (uint32_t s = 0; s < S; ++s) F += f_s[s] / S;"),
+    "robust_worst_takes_the_smallest": ("if (f_s[s] > f_s[best]) best = s;", "if (f_s[s] < f_s[best]) best = s;"),
     "u16_round_half_up": ("double t = nearbyint(v[k] / (double)s);", "double t = floor(v[k] / (double)s + 0.5);"),
     "u16_scale_off_by_one": ("float s = vmax > 0.0 ? (float)(vmax / 65535.0) : 1.0f;",
                              "float s = vmax > 0.0 ? (float)(vmax / 65536.0) : 1.0f;"),

@@ -188,6 +188,110 @@ def test_pg_closed_form_on_diagonal_and_monotone_on_beam():
     assert fh[-1] < fh[0]
 
 
+# ------------------------------------------------- multi-beam and robust objective
+
+def _merge_beams(beams):
+    """Horizontal concatenation [A_1 A_2 ...] of CSR matrices with one row count."""
+    nrows = beams[0].nrows
+    offs = np.cumsum([0] + [b.ncols for b in beams])
+    lens = sum(b.row_lengths() for b in beams)
+    rp = np.zeros(nrows + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    col = np.empty(int(rp[-1]), dtype=np.uint32)
+    val = np.empty(int(rp[-1]))
+    for i in range(nrows):
+        k = rp[i]
+        for b, o in zip(beams, offs):
+            a, e = b.row_ptr[i], b.row_ptr[i + 1]
+            col[k:k + e - a] = b.col[a:e] + o
+            val[k:k + e - a] = b.val[a:e]
+            k += e - a
+    return dosegen.CSR(nrows, int(offs[-1]), rp.astype(np.uint32), col, val)
+
+
+def test_multibeam_dose_is_the_concatenated_product():
+    """sum_b A_b x_b = [A_1 A_2 A_3][x_1; x_2; x_3], checked against the dense sum."""
+    from dataclasses import replace
+    beam = replace(dosegen.TINY, grid=(16, 14, 10), lattice=(8, 6), spacing=(2.0, 2.0))
+    beams = [dosegen.generate_along(replace(beam, seed=beam.seed + k), ax) for k, ax in enumerate("zxy")]
+    xs = [dosegen.spot_weights_f64(b.ncols, 30 + k) for k, b in enumerate(beams)]
+    d = oracle.multibeam_spmv([(b.nrows, b.row_ptr, b.col, b.val) for b in beams], xs)
+    dense = sum(sp.csr_matrix((b.val, b.col, b.row_ptr), shape=(b.nrows, b.ncols)).toarray() @ x
+                for b, x in zip(beams, xs))
+    assert np.allclose(d, dense, rtol=1e-14, atol=0)
+    m = _merge_beams(beams)
+    dm = oracle.spmv(m.nrows, m.row_ptr, m.col, m.val, np.concatenate(xs))
+    assert np.allclose(d, dm, rtol=1e-14, atol=0)
+
+
+def _scenarios(n=4):
+    from dataclasses import replace
+    base = replace(dosegen.TINY, grid=(16, 14, 10), lattice=(8, 6), spacing=(2.0, 2.0))
+    out = []
+    for k in range(n):
+        m = dosegen.generate(replace(base, shift=(float(k % 3) - 1.0, float(k // 3) - 1.0)))
+        out.append(m)
+    return out
+
+
+def test_robust_single_scenario_is_the_quadratic():
+    m = _scenarios(1)[0]
+    x = dosegen.spot_weights_f64(m.ncols, 5)
+    p = np.where(np.arange(m.nrows) % 7 == 0, 60.0, 0.0)
+    w = np.where(p > 0, 10.0, 1.0)
+    f, g = oracle.fgrad(m.nrows, m.ncols, m.row_ptr, m.col, m.val, x, p, w)
+    for mode in (oracle.EXPECTED, oracle.WORST_CASE):
+        F, G, fs, arg = oracle.robust_quadratic([(m.nrows, m.ncols, m.row_ptr, m.col, m.val)], x, p, w, mode)
+        assert F == f and np.array_equal(G, g)
+
+
+def test_robust_expected_is_the_stacked_quadratic():
+    """sum_s pi_s f(A_s x) is one quadratic over the row-stacked matrix with
+    voxel weights pi_s w: an independent construction of the same value."""
+    ms = _scenarios(4)
+    prob = np.array([0.1, 0.2, 0.3, 0.4])
+    x = dosegen.spot_weights_f64(ms[0].ncols, 6)
+    p = np.where(np.arange(ms[0].nrows) % 5 == 0, 60.0, 0.0)
+    w = np.where(p > 0, 10.0, 1.0)
+    F, G, fs, arg = oracle.robust_quadratic([(m.nrows, m.ncols, m.row_ptr, m.col, m.val) for m in ms],
+                                            x, p, w, oracle.EXPECTED, prob)
+    st = sp.vstack([sp.csr_matrix((m.val, m.col, m.row_ptr), shape=(m.nrows, m.ncols)) for m in ms]).tocsr()
+    st.sort_indices()
+    P = np.tile(p, 4)
+    W = np.concatenate([pr * w for pr in prob])
+    f2, g2 = oracle.fgrad(st.shape[0], st.shape[1], st.indptr.astype(np.uint32), st.indices.astype(np.uint32),
+                          st.data, x, P, W)
+    assert abs(F - f2) <= 1e-13 * f2 and np.allclose(G, g2, rtol=1e-12, atol=1e-12 * np.abs(g2).max())
+    assert arg == -1
+
+
+def test_robust_worst_case_picks_the_largest_and_its_gradient():
+    """Scaled copies A_s = c_s A: the worst case is the scenario with the largest
+    f_s (first on ties), its gradient is c_s* A^T r_s*, and away from ties the
+    max is locally that quadratic, so central differences are exact."""
+    m = _scenarios(1)[0]
+    x = dosegen.spot_weights_f64(m.ncols, 7)
+    p = np.where(np.arange(m.nrows) % 7 == 0, 60.0, 0.0)
+    w = np.where(p > 0, 10.0, 1.0)
+    cs = [1.0, 3.0, 0.5, 3.0]     # f grows with c here (doses far above p): scenario 1 wins, 3 ties it
+    scen = [(m.nrows, m.ncols, m.row_ptr, m.col, c * m.val) for c in cs]
+    F, G, fs, arg = oracle.robust_quadratic(scen, x * 50, p, w, oracle.WORST_CASE)
+    assert arg == 1 and fs[1] == fs[3] and F == fs[1] == fs.max()
+    f1, g1 = oracle.fgrad(m.nrows, m.ncols, m.row_ptr, m.col, 3.0 * m.val, x * 50, p, w)
+    assert F == f1 and np.array_equal(G, g1)
+    cs = [1.0, 3.0, 0.5]
+    scen = [(m.nrows, m.ncols, m.row_ptr, m.col, c * m.val) for c in cs]
+    xs = x * 50
+    F, G, fs, arg = oracle.robust_quadratic(scen, xs, p, w, oracle.WORST_CASE)
+    h = 1e-3
+    for j in (0, 7, m.ncols - 1):
+        e = np.zeros(m.ncols)
+        e[j] = h
+        Fp = oracle.robust_quadratic(scen, xs + e, p, w, oracle.WORST_CASE)[0]
+        Fm = oracle.robust_quadratic(scen, xs - e, p, w, oracle.WORST_CASE)[0]
+        assert abs((Fp - Fm) / (2 * h) - G[j]) <= 1e-6 * max(1.0, abs(G[j]))
+
+
 # ------------------------------------------------------------------ formats
 
 def test_fp8_e4m3_code_table():
