@@ -12,6 +12,7 @@ HBM.  Prints one JSON line.
     python bench.py --workload batched [--steps K]   # 27 scenario matrices x 16 vectors
     python bench.py --workload precision             # u16 / BF16 / FP8 / F16 / F32, plain and compensated
     python bench.py --workload halfdouble            # the paper's Half/double: F16 values, FP64 x and d
+    python bench.py --workload robust                # 3-beam plan x 9 setup shifts: robust objective + PG step
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on the same workload and metric.  Under torchrun (N > 1) every rank
@@ -639,6 +640,98 @@ def run_halfdouble(args):
     print(json.dumps(out), flush=True)
 
 
+ROBUST_METRIC = ("robust dose+gradient evaluation over 9 setup-shift scenarios of a 3-beam plan: ms per "
+                 "evaluation and effective HBM GB/s of its algorithmic bytes")
+
+
+def run_robust(args):
+    """A three-beam plan on a 160x160x100 grid (beams entering along +z, +x, +y,
+    1000 spots each) under the nine lateral setup shifts: nine merged scenario
+    handles (u16 + scale), one projected-gradient step of the expected and of
+    the worst-case robust quadratic objective per timed step (nine fused passes
+    and one combine kernel each), captured in a CUDA graph."""
+    import torch
+
+    import paper_2103_09683_gb300 as dose
+
+    dose.build()
+    torch.cuda.set_device(0)
+    plan = dosegen.robust_plan()
+    mats, abs_row, abs_col, nnz = [], None, None, 0
+    for s, beams in enumerate(plan):
+        csrs = [dosegen.generate_along(b, ax) for b, ax in beams]
+        mats.append(dose.DoseMatrix.from_multibeam([(c.row_ptr, c.col, c.ncols, c.val) for c in csrs], fmt="u16"))
+        # ||A_s||_1 ||A_s||_inf bounds ||A_s||_2^2, hence the Lipschitz constant of every scenario's gradient
+        rs = sum(np.add.reduceat(np.concatenate([c.val, [0.0]]), c.row_ptr.astype(np.int64)[:-1])
+                 * (np.diff(c.row_ptr.astype(np.int64)) > 0) for c in csrs)
+        cs = np.concatenate([np.bincount(c.col, weights=c.val, minlength=c.ncols) for c in csrs])
+        abs_row = rs.max() if abs_row is None else max(abs_row, rs.max())
+        abs_col = cs.max() if abs_col is None else max(abs_col, cs.max())
+        nnz += sum(c.nnz for c in csrs)
+        del csrs
+    nrows, ncols = mats[0].nrows, mats[0].ncols
+    grid_beam = plan[0][0][0]
+    p, w = dosegen.ellipsoid_target(grid_beam, semi_axes=(20.0, 16.0, 12.0), depth_frac=0.5)
+    eta = 1.0 / (2.0 * float(w.max()) * float(abs_row) * float(abs_col))
+    x0 = np.concatenate([dosegen.spot_weights(1000, dosegen.weight_seed(b) & 0xFFFF) for b, _ in plan[4]])
+    dev = torch.device("cuda", 0)
+    pt, wt, x0t = (torch.from_numpy(a).to(dev) for a in (p, w, x0))
+    S = dose.ScenarioSet(mats)
+    step_bytes = sum(A.info()["fused_bytes"] for A in mats) + 9 * (ncols * 4) + ncols * 12 + 9 * 8
+    peak, _ = _peaks()
+    K = max(3, min(args.steps, 100))
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(0)
+    variants = []
+    clocks.start()
+    for mode in ("expected", "worst"):
+        x = x0t.clone()
+        f = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty(ncols, dtype=torch.float32, device=dev)
+        stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                S.pg_step(x, pt, wt, eta, mode=mode, f=f, g=g, stream=stream)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            S.pg_step(x, pt, wt, eta, mode=mode, f=f, g=g, stream=stream)
+        x.copy_(x0t)
+        torch.cuda.synchronize()
+        f_first = None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            graph.replay()
+            stream.synchronize()
+            f_first = float(f.item())
+            e0.record(stream)
+            for _ in range(K):
+                graph.replay()
+            e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        f_last = float(f.item())
+        for A in mats:
+            A.device_status()
+        gbs = step_bytes / (ms * 1e-3) / 1e9
+        variants.append({"mode": mode, "ms": round(ms, 4), "ms_per_scenario": round(ms / 9, 4),
+                         "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                         "f_first": f_first, "f_after": f_last, "launches_per_step": 2 * 9 + 1})
+    clk = clocks.stop()
+    S.close()
+    base = variants[0]
+    out = {"metric": ROBUST_METRIC, "value": base["achieved_gbs"], "unit": "GB/s", "n_gpus": 1, "steps": K,
+           "warmup": args.warmup, "ms_per_step": base["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"3-beam plan on 160x160x100 voxels (beams along +z, +x, +y, 1000 spots each) "
+                                  f"x 9 setup shifts; {nnz} entries in all, u16 + scale; step = one robust PG step "
+                                  f"(9 fused passes + combine) in a CUDA graph",
+                      "nrows": nrows, "ncols": ncols, "step_bytes": step_bytes,
+                      "l2": "9 scenario matrices (~5 GB) > L2: streamed from HBM every step", "peak_gbs": peak},
+           "clocks": clk, "gpu_launches": 19 * K, "variants": variants}
+    print(json.dumps(out), flush=True)
+
+
 def batched_cpu_baseline(csr, X, budget_s=10.0):
     """The oracle's FP64 SpMM on row blocks of one scenario matrix (about
     budget_s of single-core work), as GB/s of the same byte model."""
@@ -670,10 +763,11 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="time candidate schedules first (dose_autotune)")
     ap.add_argument("--tuning", default="", help="schedule knobs, e.g. tile_nnz=8192,adj_scatter_warps=4")
     ap.add_argument("--matrices", default="", help="batched: subset of the 27 scenario matrices, e.g. 4,13,22")
-    ap.add_argument("--workload", default="clinical", choices=["clinical", "batched", "precision", "halfdouble"],
+    ap.add_argument("--workload", default="clinical",
+                    choices=["clinical", "batched", "precision", "halfdouble", "robust"],
                     help="clinical: the dose + dose-gradient step (default); batched: 27 matrices x 16 vectors; "
                          "precision: dose eval per stored format with its error vs the FP64 oracle; "
-                         "halfdouble: F16 values with FP64 x and d")
+                         "halfdouble: F16 values with FP64 x and d; robust: 3-beam plan x 9 scenarios")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -685,6 +779,8 @@ def main():
         run_precision(args)
     elif args.workload == "halfdouble":
         run_halfdouble(args)
+    elif args.workload == "robust":
+        run_robust(args)
     else:
         run_gpu(args)
 

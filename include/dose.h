@@ -234,6 +234,46 @@ dose_status dose_adjoint_noalloc(uint32_t nrows, uint32_t ncols, uint64_t nnz, c
                                  const float* row_scales, float scale, const float* r, float* g,
                                  void* stream);
 
+/* A plan of several beams on one voxel grid (Sec. I: the dose of a plan comes from
+ * multiple beams): one handle whose columns are the beams' spots in beam order, so
+ * that with x = [x_1; ...; x_B] every call above computes the plan's total dose
+ * d = sum_b A_b x_b (and A^T r gives every beam's gradient).  beams: nbeams (1..64)
+ * host CSR descriptors (on_device = 0) with the same nrows and format; either all
+ * give values_f64 (encoded once, after merging) or all give codes (BF16, F16,
+ * F32; U16 only if every beam has the same scale; not FP8, whose row scales
+ * would differ within a merged row).  flags, tuning, stream: as for
+ * dose_create_matrix, which validates the merged matrix. */
+dose_status dose_create_multibeam(const dose_csr_desc* beams, int nbeams, unsigned flags, const dose_tuning* tuning,
+                                  void* stream, dose_matrix** out);
+
+/* Robust optimisation over uncertainty scenarios (Sec. I: doses under several
+ * realisations of the uncertainties in every iteration).  A scenario set groups
+ * count (1..64) matrices of one shape -- the same plan under different setup
+ * shifts -- with probabilities prob (host, count values >= 0 summing to 1; NULL =
+ * uniform).  The set owns scratch of count x ncols floats; the matrices must
+ * outlive it; calls on one set must be ordered on one stream.  Objective of the
+ * quadratic dose term f_s(x) = sum_i w_i ((A_s x)_i - p_i)^2 of each scenario:
+ *   DOSE_ROBUST_EXPECTED:   F = sum_s prob_s f_s,  g = sum_s prob_s grad f_s
+ *   DOSE_ROBUST_WORST_CASE: F = max_s f_s, g = grad f_s* for the first s* with the
+ *                           largest f_s (a subgradient of the maximum). */
+typedef struct dose_scenarios dose_scenarios; /* opaque, library-owned */
+#define DOSE_ROBUST_EXPECTED 0
+#define DOSE_ROBUST_WORST_CASE 1
+dose_status dose_create_scenarios(const dose_matrix* const* A, int count, const double* prob, dose_scenarios** out);
+dose_status dose_destroy_scenarios(dose_scenarios* S); /* synchronises the device; NULL -> DOSE_OK */
+
+/* F and g of the robust objective: one fused pass per scenario (as
+ * dose_fwd_adj_quadratic) and one combine kernel, sums in scenario order.
+ * x: device ncols floats; p, w: device nrows floats, 16-byte aligned; f: device
+ * double; f_scen: device count doubles (each f_s) or NULL; g: device ncols floats. */
+dose_status dose_robust_quadratic(const dose_scenarios* S, int mode, const float* x, const float* p, const float* w,
+                                  double* f, double* f_scen, float* g, void* stream);
+
+/* One projected-gradient step of the robust objective: F and g at x, then
+ * x <- max(0, x - eta g) in place.  g may be NULL. */
+dose_status dose_robust_pg_step(const dose_scenarios* S, int mode, float* x, const float* p, const float* w,
+                                float eta, double* f, float* g, void* stream);
+
 /* Free the handle and its device memory (synchronises the device first).  NULL -> DOSE_OK. */
 dose_status dose_destroy(dose_matrix* A);
 

@@ -22,7 +22,8 @@ import numpy as np
 from . import _build
 
 __all__ = ["build", "load", "DoseMatrix", "DoseError", "FORMATS", "spmv_batched", "adjoint_noalloc", "dose_spmv",
-           "QuadraticDoseObjective", "pg_solve", "PGSolver", "encode_host", "library_path", "selftest_bounded_wait"]
+           "QuadraticDoseObjective", "pg_solve", "PGSolver", "encode_host", "library_path", "selftest_bounded_wait",
+           "ScenarioSet"]
 
 FORMATS = {"u16": 0, "bf16": 1, "fp8": 2, "f16": 3, "f32": 4}
 _NO_SCALES = ("bf16", "f16", "f32")
@@ -30,6 +31,7 @@ _VAL_NP = {"fp8": np.uint8, "f32": np.uint32}      # stored value dtype (default
 CREATE_COMPENSATED = 0x1
 CREATE_U16_INDEX = 0x2
 SPMV_F64_NATIVE = 0x1
+ROBUST_MODES = {"expected": 0, "worst": 1}
 _STATUS = {0: "DOSE_OK", 1: "DOSE_ERR_INVALID_ARG", 2: "DOSE_ERR_OOM", 3: "DOSE_ERR_CUDA",
            4: "DOSE_ERR_UNSUPPORTED", 5: "DOSE_ERR_TIMEOUT"}
 
@@ -89,6 +91,11 @@ EXPORTS = {
     "dose_fwd_adj_quadratic": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "dose_pg_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
     "dose_destroy": (ctypes.c_int, [_P]),
+    "dose_create_multibeam": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint, _P, _P, _P]),
+    "dose_create_scenarios": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "dose_destroy_scenarios": (ctypes.c_int, [_P]),
+    "dose_robust_quadratic": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "dose_robust_pg_step": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
     "dose_matrix_info": (ctypes.c_int, [_P, _P]),
     "dose_set_tuning": (ctypes.c_int, [_P, _P]),
     "dose_autotune": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -257,6 +264,45 @@ class DoseMatrix:
                                       ctypes.byref(out)))
         return cls(out.value, nrows, int(ncols), nnz, fmt)
 
+    @classmethod
+    def from_multibeam(cls, beams, *, fmt: str = "u16", compensated: bool = False, index16: bool = False,
+                       tuning: dict | None = None, stream=None):
+        """One handle for a plan of several beams on one voxel grid
+        (dose_create_multibeam): columns are the beams' spots in beam order, so
+        spmv([x_1; ...; x_B]) is the total dose sum_b A_b x_b.  beams: host
+        (numpy) tuples (row_ptr, col, ncols, values_f64) or, for BF16/F16/F32
+        (U16 with one scale), (row_ptr, col, ncols, values, scales)."""
+        torch = _torch()
+        lib = load()
+        keep = []
+
+        def host(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data if a.size else None
+
+        descs = (_Desc * len(beams))()
+        nrows = None
+        for d, bm in zip(descs, beams):
+            rp, col, nc = bm[0], bm[1], int(bm[2])
+            d.nrows, d.ncols, d.nnz, d.fmt = len(rp) - 1, nc, len(col), FORMATS[fmt]
+            nrows = d.nrows
+            d.row_ptr, d.col_idx = host(rp, np.uint32), host(col, np.uint32)
+            if len(bm) == 4:
+                d.values_f64 = host(bm[3], np.float64)
+            else:
+                d.values = host(bm[3], _VAL_NP.get(fmt, np.uint16))
+                if fmt not in _NO_SCALES:
+                    d.scales = host(np.asarray(bm[4], dtype=np.float32).reshape(-1), np.float32)
+            d.on_device = 0
+        t = Tuning(**{k: int(v) for k, v in tuning.items()}) if tuning else None
+        out = ctypes.c_void_p()
+        stream_h = _stream_handle(stream) if torch.cuda.is_available() else ctypes.c_void_p(0)
+        flags = (CREATE_COMPENSATED if compensated else 0) | (CREATE_U16_INDEX if index16 else 0)
+        _check(lib.dose_create_multibeam(descs, len(beams), flags, ctypes.byref(t) if t is not None else None,
+                                         stream_h, ctypes.byref(out)))
+        return cls(out.value, nrows, sum(int(b[2]) for b in beams), sum(len(b[1]) for b in beams), fmt)
+
     def close(self):
         if self._h and self._h.value:
             load().dose_destroy(self._h)
@@ -399,6 +445,58 @@ def spmv_batched(mats, Xs, Ds=None, stream=None):
                                  for A, D in zip(mats, Ds)])
     _check(load().dose_spmv_batched(hs, n, xp, dp, nvec, _stream_handle(stream)))
     return Ds
+
+
+class ScenarioSet:
+    """Matrices of one shape under several uncertainty scenarios, with their
+    probabilities (dose_create_scenarios); robust objective and PG step."""
+
+    def __init__(self, mats, prob=None):
+        lib = load()
+        self.mats = list(mats)   # the handles must outlive the set
+        self.nrows, self.ncols = self.mats[0].nrows, self.mats[0].ncols
+        n = len(self.mats)
+        hs = (ctypes.c_void_p * n)(*[A.handle.value for A in self.mats])
+        pr = None if prob is None else np.ascontiguousarray(prob, dtype=np.float64)
+        out = ctypes.c_void_p()
+        _check(lib.dose_create_scenarios(hs, n, pr.ctypes.data if pr is not None else None, ctypes.byref(out)))
+        self._h = out
+
+    def robust_quadratic(self, x, p, w, mode: str = "expected", f=None, g=None, f_scen=None, stream=None):
+        """(F, g[, f_s]) of the robust quadratic objective (device tensors)."""
+        torch = _torch()
+        dev = x.device
+        f = torch.empty(1, dtype=torch.float64, device=dev) if f is None else f
+        g = torch.empty(self.ncols, dtype=torch.float32, device=dev) if g is None else g
+        _check(load().dose_robust_quadratic(
+            self._h, ROBUST_MODES[mode], _dptr(x, torch.float32, self.ncols, "x"),
+            _dptr(p, torch.float32, self.nrows, "p"), _dptr(w, torch.float32, self.nrows, "w"),
+            _dptr(f, torch.float64, 1, "f"),
+            _dptr(f_scen, torch.float64, len(self.mats), "f_scen") if f_scen is not None else None,
+            _dptr(g, torch.float32, self.ncols, "g"), _stream_handle(stream)))
+        return (f, g, f_scen) if f_scen is not None else (f, g)
+
+    def pg_step(self, x, p, w, eta: float, mode: str = "expected", f=None, g=None, stream=None):
+        """F at x, then x <- max(0, x - eta g) in place; returns F (device double)."""
+        torch = _torch()
+        f = torch.empty(1, dtype=torch.float64, device=x.device) if f is None else f
+        _check(load().dose_robust_pg_step(
+            self._h, ROBUST_MODES[mode], _dptr(x, torch.float32, self.ncols, "x"),
+            _dptr(p, torch.float32, self.nrows, "p"), _dptr(w, torch.float32, self.nrows, "w"),
+            ctypes.c_float(eta), _dptr(f, torch.float64, 1, "f"),
+            _dptr(g, torch.float32, self.ncols, "g") if g is not None else None, _stream_handle(stream)))
+        return f
+
+    def close(self):
+        if self._h and self._h.value:
+            load().dose_destroy_scenarios(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ autograd

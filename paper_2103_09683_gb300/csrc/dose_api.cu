@@ -726,6 +726,79 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     return DOSE_OK;
 }
 
+dose_status dose_create_multibeam(const dose_csr_desc* beams, int nbeams, unsigned flags, const dose_tuning* tuning,
+                                  void* stream, dose_matrix** out) {
+    if (!out) return invalid("dose_create_multibeam: out is NULL");
+    *out = nullptr;
+    if (!beams || nbeams < 1 || nbeams > 64) return invalid("dose_create_multibeam: nbeams must be in [1, 64]");
+    const dose_csr_desc& b0 = beams[0];
+    const bool f64 = b0.values == nullptr;
+    uint64_t ncols = 0, nnz = 0;
+    for (int b = 0; b < nbeams; ++b) {
+        const dose_csr_desc& d = beams[b];
+        const std::string tag = "dose_create_multibeam: beam " + std::to_string(b) + ": ";
+        if (d.on_device) return invalid(tag + "beams must be host CSR arrays (on_device = 0)");
+        if (d.nrows != b0.nrows) return invalid(tag + "every beam needs the same voxel grid (nrows)");
+        if (d.fmt != b0.fmt) return invalid(tag + "every beam needs the same format");
+        if ((d.values == nullptr) != f64) return invalid(tag + "give values_f64 for every beam, or codes for every beam");
+        if (!d.row_ptr || (d.nnz && !d.col_idx) || (d.nnz && f64 && !d.values_f64))
+            return invalid(tag + "null array");
+        if (d.row_ptr[0] != 0 || d.row_ptr[d.nrows] != d.nnz) return invalid(tag + "row_ptr must run from 0 to nnz");
+        for (uint32_t i = 0; i < d.nrows; ++i)
+            if (d.row_ptr[i + 1] < d.row_ptr[i]) return invalid(tag + "row_ptr must be non-decreasing");
+        for (uint64_t k = 0; k < d.nnz; ++k)
+            if (d.col_idx[k] >= d.ncols) return invalid(tag + "col_idx out of range");
+        if (!f64) {
+            if (d.fmt == DOSE_FMT_FP8E4M3_ROWSCALE)
+                return invalid(tag + "FP8 row scales of different beams cannot share a row: give values_f64");
+            if (d.fmt == DOSE_FMT_U16_SCALE && (!d.scales || !b0.scales || d.scales[0] != b0.scales[0]))
+                return invalid(tag + "U16 codes of beams with different scales cannot be merged: give values_f64");
+        }
+        ncols += d.ncols;
+        nnz += d.nnz;
+    }
+    if (ncols > 0xFFFFFFFFull || nnz >= (1ull << 32)) return invalid("dose_create_multibeam: merged matrix too large");
+    // Row i of the plan = row i of beam 0, then of beam 1, ... with beam b's
+    // columns moved up by the spots of the beams before it.
+    const uint32_t nrows = b0.nrows;
+    const size_t es = f64 ? 8 : value_bytes(b0.fmt);
+    std::vector<uint32_t> rp(nrows + 1, 0), col(nnz), off(nbeams, 0);
+    std::vector<unsigned char> val(nnz * es);
+    for (int b = 1; b < nbeams; ++b) off[b] = off[b - 1] + beams[b - 1].ncols;
+    for (uint32_t i = 0; i < nrows; ++i) {
+        uint32_t len = 0;
+        for (int b = 0; b < nbeams; ++b) len += beams[b].row_ptr[i + 1] - beams[b].row_ptr[i];
+        rp[i + 1] = rp[i] + len;
+    }
+    for (uint32_t i = 0; i < nrows; ++i) {
+        uint32_t k = rp[i];
+        for (int b = 0; b < nbeams; ++b) {
+            const dose_csr_desc& d = beams[b];
+            for (uint32_t q = d.row_ptr[i]; q < d.row_ptr[i + 1]; ++q, ++k) {
+                col[k] = d.col_idx[q] + off[b];
+                const unsigned char* src = f64 ? reinterpret_cast<const unsigned char*>(d.values_f64)
+                                               : static_cast<const unsigned char*>(d.values);
+                std::memcpy(val.data() + (size_t)k * es, src + (size_t)q * es, es);
+            }
+        }
+    }
+    dose_csr_desc m{};
+    m.nrows = nrows;
+    m.ncols = (uint32_t)ncols;
+    m.nnz = nnz;
+    m.row_ptr = rp.data();
+    m.col_idx = col.data();
+    m.fmt = b0.fmt;
+    m.on_device = 0;
+    if (f64) {
+        m.values_f64 = reinterpret_cast<const double*>(val.data());
+    } else {
+        m.values = val.data();
+        m.scales = b0.scales;
+    }
+    return dose_create_matrix(&m, flags, tuning, stream, out);
+}
+
 dose_status dose_destroy(dose_matrix* A) {
     if (!A) return DOSE_OK;
     cudaDeviceSynchronize();
@@ -753,7 +826,10 @@ dose_status dose_spmv_f64(const dose_matrix* A, const double* x, double* d, unsi
     return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_spmv_f64 launch");
 }
 
-static dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* const* vecs, int nvec) {
+}  // extern "C"
+
+namespace dose {
+dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* const* vecs, int nvec) {
     if (quad && A->adj.wwidth > kXSmemMaxCols) {
         set_error("the fused objective pass keeps each CTA's window of x in shared memory: the column window (" +
                   std::to_string(A->adj.wwidth) + ") must be <= 16384");
@@ -769,6 +845,9 @@ static dose_status adjoint_supported(const dose_matrix* A, bool quad, const floa
             return invalid("per-row vectors (p, w, r) must be 16-byte aligned");
     return DOSE_OK;
 }
+}  // namespace dose
+
+extern "C" {
 
 dose_status dose_adjoint(const dose_matrix* A, const float* r, float* g, void* stream) {
     if (!A) return invalid("dose_adjoint: null matrix");

@@ -162,6 +162,9 @@ bool adjoint_shape(const dose_matrix* A, const AdjTuning& in, bool quad, AdjTuni
 cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const float* p,
                            const float* w, const float* r, float* d, double* f, float* g,
                            float* x_update, float eta, cudaStream_t s);
+// Whether the adjoint / fused kernels can run on A (window and accumulators fit;
+// per-row vectors 16-byte aligned); sets the error message if not.
+dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* const* vecs, int nvec);
 cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const float* const* X,
                                 float* const* D, int nvec, cudaStream_t s, std::string* why);
 

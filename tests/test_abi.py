@@ -129,3 +129,34 @@ def test_create_rejects_invalid_csr_on_host(lib):
     assert lib.dose_destroy(None) == 0
     assert lib.dose_spmv(None, None, None, None) == 1
     assert lib.dose_spmv_batched(None, -1, None, None, 16, None) == 1
+
+
+def test_multibeam_and_scenarios_reject_bad_arguments_on_host(lib):
+    """dose_create_multibeam validates every beam on the host before merging;
+    dose_create_scenarios rejects empty sets before touching a device."""
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    out = ctypes.c_void_p()
+    ok = dict(nrows=2, ncols=3, nnz=3, row_ptr=arr([0, 2, 3], np.uint32), col_idx=arr([0, 1, 2], np.uint32),
+              fmt=0, values_f64=arr([0.5, 0.25, 1.0], np.float64))
+    cases = {
+        "same voxel grid": [ok, dict(ok, nrows=1, row_ptr=arr([0, 3], np.uint32))],
+        "same format": [ok, dict(ok, fmt=1)],
+        "col_idx out of range": [ok, dict(ok, col_idx=arr([0, 3, 2], np.uint32))],
+        "row_ptr must run from 0 to nnz": [ok, dict(ok, row_ptr=arr([0, 2, 2], np.uint32))],
+        "host CSR arrays": [ok, dict(ok, on_device=1)],
+    }
+    for needle, beams in cases.items():
+        descs = (dose._Desc * len(beams))(*[_desc(**b) for b in beams])
+        st = lib.dose_create_multibeam(descs, len(beams), 0, None, None, ctypes.byref(out))
+        assert st == 1, needle
+        assert needle in lib.dose_last_error().decode(), (needle, lib.dose_last_error())
+    assert lib.dose_create_multibeam(None, 0, 0, None, None, ctypes.byref(out)) == 1
+    assert lib.dose_create_scenarios(None, 0, None, ctypes.byref(out)) == 1
+    assert lib.dose_robust_quadratic(None, 0, None, None, None, None, None, None, None) == 1
+    assert lib.dose_robust_pg_step(None, 0, None, None, None, ctypes.c_float(-1.0), None, None, None) == 1
