@@ -660,7 +660,8 @@ def run_robust(args):
     mats, abs_row, abs_col, nnz = [], None, None, 0
     for s, beams in enumerate(plan):
         csrs = [dosegen.generate_along(b, ax) for b, ax in beams]
-        mats.append(dose.DoseMatrix.from_multibeam([(c.row_ptr, c.col, c.ncols, c.val) for c in csrs], fmt="u16"))
+        mats.append(dose.DoseMatrix.from_multibeam([(c.row_ptr, c.col, c.ncols, c.val) for c in csrs], fmt="u16",
+                                                   tuning=_tuning_kv(args) or None))
         # ||A_s||_1 ||A_s||_inf bounds ||A_s||_2^2, hence the Lipschitz constant of every scenario's gradient
         rs = sum(np.add.reduceat(np.concatenate([c.val, [0.0]]), c.row_ptr.astype(np.int64)[:-1])
                  * (np.diff(c.row_ptr.astype(np.int64)) > 0) for c in csrs)
@@ -726,7 +727,9 @@ def run_robust(args):
            "config": {"workload": f"3-beam plan on 160x160x100 voxels (beams along +z, +x, +y, 1000 spots each) "
                                   f"x 9 setup shifts; {nnz} entries in all, u16 + scale; step = one robust PG step "
                                   f"(9 fused passes + combine) in a CUDA graph",
-                      "nrows": nrows, "ncols": ncols, "step_bytes": step_bytes,
+                      "nrows": nrows, "ncols": ncols, "step_bytes": step_bytes, "tuning": _tuning_kv(args),
+                      "adj_window": max(A.info()["adj_window"] for A in mats),
+                      "adj_block_fused": mats[0].info()["adj_block_fused"],
                       "l2": "9 scenario matrices (~5 GB) > L2: streamed from HBM every step", "peak_gbs": peak},
            "clocks": clk, "gpu_launches": 19 * K, "variants": variants}
     print(json.dumps(out), flush=True)
