@@ -13,6 +13,7 @@ HBM.  Prints one JSON line.
     python bench.py --workload precision             # u16 / BF16 / FP8 / F16 / F32, plain and compensated
     python bench.py --workload halfdouble            # the paper's Half/double: F16 values, FP64 x and d
     python bench.py --workload robust                # 3-beam plan x 9 setup shifts: robust objective + PG step
+    python bench.py --workload sell                  # dose eval on SELL-32-sigma copies, sigma sweep, vs CSR
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on the same workload and metric.  Under torchrun (N > 1) every rank
@@ -735,6 +736,74 @@ def run_robust(args):
     print(json.dumps(out), flush=True)
 
 
+SELL_METRIC = ("dose SpMV on SELL-32-sigma storage (the paper's future-work format) against the CSR kernel: "
+               "effective HBM GB/s of each layout's own bytes, ms per dose eval, padding")
+
+
+def run_sell(args):
+    """The clinical beam (u16 + scale) stored as SELL-32-sigma for several sigma,
+    with 32- and 16-bit indices, next to the CSR kernel on the same matrix; a
+    step is one dose_spmv."""
+    import torch
+
+    import oracle
+    import paper_2103_09683_gb300 as dose
+
+    dose.build()
+    torch.cuda.set_device(0)
+    beam = dosegen.CLINICAL
+    csr = dosegen.generate(beam)
+    enc = oracle.encode(csr, oracle.U16_SCALE)
+    x = dosegen.spot_weights(csr.ncols, dosegen.weight_seed(beam))
+    xd = torch.from_numpy(x).cuda()
+    rng = np.random.default_rng(7)
+    lens = np.diff(csr.row_ptr.astype(np.int64))
+    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 20000, replace=False))
+    same = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
+    peak, _ = _peaks()
+    K = max(3, min(args.steps, 200))
+    clocks = ClockSampler(0)
+    variants = []
+    clocks.start()
+    for idx16 in (False, True):
+        for sigma in (0, 1, 32, 256, 1024, 8192, 1 << 20):   # 0: the CSR kernel
+            A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt="u16", values=enc.values,
+                                         scales=enc.scales, index16=idx16, sell=sigma > 0,
+                                         tuning=dict(sell_sigma=sigma) if sigma else None)
+            inf = A.info()
+            d = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
+            for _ in range(args.warmup):
+                A.spmv(xd, d)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(K):
+                A.spmv(xd, d)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            A.device_status()
+            dv = d.cpu().numpy()[rows].astype(np.float64)
+            rel = float(np.max(np.abs(dv - same) / same))
+            gbs = inf["spmv_bytes"] / (ms * 1e-3) / 1e9
+            variants.append({"layout": f"sell-32-{sigma}" if sigma else "csr", "index_bytes": 2 if idx16 else 4,
+                             "ms": round(ms, 5), "bytes": inf["spmv_bytes"], "achieved_gbs": round(gbs, 1),
+                             "frac": round(gbs / peak, 4),
+                             "stored_entries": inf["sell_entries"] if sigma else csr.nnz,
+                             "padding": round(inf["sell_entries"] / csr.nnz - 1, 4) if sigma else 0.0,
+                             "max_rel_err_vs_same_decoded": rel})
+            del A, d
+    clk = clocks.stop()
+    base = next(v for v in variants if v["layout"] == "sell-32-1024" and v["index_bytes"] == 4)
+    out = {"metric": SELL_METRIC, "value": base["achieved_gbs"], "unit": "GB/s", "n_gpus": 1, "steps": K,
+           "warmup": args.warmup, "ms_per_step": base["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "clinical pencil beam 256x256x160 voxels x 4000 spots, ~1.5e8 entries; u16 + scale; "
+                                  "step = one dose_spmv", "sampled_rows": int(len(rows)), "peak_gbs": peak},
+           "clocks": clk, "variants": variants}
+    print(json.dumps(out), flush=True)
+
+
 def batched_cpu_baseline(csr, X, budget_s=10.0):
     """The oracle's FP64 SpMM on row blocks of one scenario matrix (about
     budget_s of single-core work), as GB/s of the same byte model."""
@@ -767,7 +836,7 @@ def main():
     ap.add_argument("--tuning", default="", help="schedule knobs, e.g. tile_nnz=8192,adj_scatter_warps=4")
     ap.add_argument("--matrices", default="", help="batched: subset of the 27 scenario matrices, e.g. 4,13,22")
     ap.add_argument("--workload", default="clinical",
-                    choices=["clinical", "batched", "precision", "halfdouble", "robust"],
+                    choices=["clinical", "batched", "precision", "halfdouble", "robust", "sell"],
                     help="clinical: the dose + dose-gradient step (default); batched: 27 matrices x 16 vectors; "
                          "precision: dose eval per stored format with its error vs the FP64 oracle; "
                          "halfdouble: F16 values with FP64 x and d; robust: 3-beam plan x 9 scenarios")
@@ -784,6 +853,8 @@ def main():
         run_halfdouble(args)
     elif args.workload == "robust":
         run_robust(args)
+    elif args.workload == "sell":
+        run_sell(args)
     else:
         run_gpu(args)
 

@@ -100,6 +100,13 @@ typedef struct {
                                         The handle keeps a 16-bit copy of the indices beside the
                                         32-bit ones (the other kernels use those): +2 B per entry of
                                         device memory. */
+#define DOSE_CREATE_SELL 0x4u        /* dose_spmv runs on a SELL-32-sigma copy of the matrix (the
+                                        SIMT-oriented format the paper names as future work, Sec. III):
+                                        rows ordered by length inside windows of sigma rows
+                                        (dose_tuning.sell_sigma), chunks of 32 rows padded to their longest
+                                        row, one row per lane.  The other calls keep using the CSR
+                                        arrays; the copy costs its padded size in device memory
+                                        (dose_info.sell_entries). */
 
 /* Schedule knobs of a matrix (row-length binning and pipeline shape).  All
  * fields 0 = library default.  Changing them never changes which rows an
@@ -128,6 +135,8 @@ typedef struct {
                                    (default: the rows one warp reduces together then have similar trip
                                    counts) */
     uint32_t adj_row_order;     /* the same for the adjoint schedule */
+    uint32_t sell_sigma;        /* DOSE_CREATE_SELL: rows per sorting window (1 = no sorting;
+                                   default 1024); read at create only */
 } dose_tuning;
 
 typedef struct {
@@ -149,6 +158,9 @@ typedef struct {
     uint64_t adjoint_bytes;     /* ... of one dose_adjoint */
     uint64_t fused_bytes;       /* ... of one dose_fwd_adj_quadratic with d == NULL */
     uint64_t spmv_f64_bytes;    /* ... of one dose_spmv_f64 (x read once, d written once) */
+    uint64_t sell_entries;      /* DOSE_CREATE_SELL: stored entries of the SELL copy, padding
+                                   included (0 without the flag); spmv_bytes then counts the SELL
+                                   arrays */
     float scale;                /* U16: the matrix scale s; else 0 */
     dose_tuning tuning;         /* the knobs in effect */
 } dose_info;

@@ -30,6 +30,7 @@ _NO_SCALES = ("bf16", "f16", "f32")
 _VAL_NP = {"fp8": np.uint8, "f32": np.uint32}      # stored value dtype (default uint16)
 CREATE_COMPENSATED = 0x1
 CREATE_U16_INDEX = 0x2
+CREATE_SELL = 0x4
 SPMV_F64_NATIVE = 0x1
 ROBUST_MODES = {"expected": 0, "worst": 1}
 _STATUS = {0: "DOSE_OK", 1: "DOSE_ERR_INVALID_ARG", 2: "DOSE_ERR_OOM", 3: "DOSE_ERR_CUDA",
@@ -60,7 +61,8 @@ class Tuning(ctypes.Structure):
                 ("adj_tile_nnz", ctypes.c_uint32), ("adj_tile_rows", ctypes.c_uint32),
                 ("adj_stages", ctypes.c_uint32), ("adj_forward_warps", ctypes.c_uint32),
                 ("adj_scatter_warps", ctypes.c_uint32), ("adj_l2_prefetch", ctypes.c_uint32),
-                ("row_order", ctypes.c_uint32), ("adj_row_order", ctypes.c_uint32)]
+                ("row_order", ctypes.c_uint32), ("adj_row_order", ctypes.c_uint32),
+                ("sell_sigma", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -76,6 +78,7 @@ class _Info(ctypes.Structure):
                 ("max_row_len", ctypes.c_uint32), ("adj_window", ctypes.c_uint32),
                 ("reserved0", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("spmv_bytes", ctypes.c_uint64),
                 ("adjoint_bytes", ctypes.c_uint64), ("fused_bytes", ctypes.c_uint64), ("spmv_f64_bytes", ctypes.c_uint64),
+                ("sell_entries", ctypes.c_uint64),
                 ("scale", ctypes.c_float), ("tuning", Tuning)]
 
 
@@ -202,14 +205,15 @@ class DoseMatrix:
     # ---- construction
     @classmethod
     def from_csr(cls, row_ptr, col, *, ncols: int, fmt: str = "u16", values=None, scales=None,
-                 values_f64=None, compensated: bool = False, index16: bool = False, tuning: dict | None = None,
-                 stream=None):
+                 values_f64=None, compensated: bool = False, index16: bool = False, sell: bool = False,
+                 tuning: dict | None = None, stream=None):
         """Create from host (numpy) or device (torch CUDA) CSR arrays.
 
         Pass either encoded `values` (+ `scales`) in the stored format, or
         `values_f64` (host) to let the library encode.  `compensated`: Dot2
         accumulation on rows longer than 128 entries; `index16`: the dose SpMV
-        reads 16-bit column indices (ncols <= 65536).
+        reads 16-bit column indices (ncols <= 65536); `sell`: dose_spmv runs on a
+        SELL-32-sigma copy (tuning sell_sigma).
         """
         torch = _torch()
         lib = load()
@@ -258,7 +262,8 @@ class DoseMatrix:
             t = Tuning(**{k: int(v) for k, v in tuning.items()})
         out = ctypes.c_void_p()
         stream_h = _stream_handle(stream) if torch.cuda.is_available() else ctypes.c_void_p(0)
-        flags = (CREATE_COMPENSATED if compensated else 0) | (CREATE_U16_INDEX if index16 else 0)
+        flags = ((CREATE_COMPENSATED if compensated else 0) | (CREATE_U16_INDEX if index16 else 0) |
+                 (CREATE_SELL if sell else 0))
         _check(lib.dose_create_matrix(ctypes.byref(d), flags,
                                       ctypes.byref(t) if t is not None else None, stream_h,
                                       ctypes.byref(out)))

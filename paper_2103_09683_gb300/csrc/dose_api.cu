@@ -345,6 +345,7 @@ static void free_all(dose_matrix* A) {
     cudaFree(A->val);
     cudaFree(A->row_scale);
     cudaFree(A->x64);
+    free_sell(A);
     cudaFree(A->g_part);
     cudaFree(A->f_part);
     cudaFree(A->err);
@@ -548,7 +549,11 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
                                dose_matrix** out) {
     if (!desc || !out) return invalid("dose_create_matrix: null desc or out");
     *out = nullptr;
-    if (flags & ~(DOSE_CREATE_COMPENSATED | DOSE_CREATE_U16_INDEX)) return invalid("dose_create_matrix: unknown flags");
+    if (flags & ~(DOSE_CREATE_COMPENSATED | DOSE_CREATE_U16_INDEX | DOSE_CREATE_SELL))
+        return invalid("dose_create_matrix: unknown flags");
+    const uint32_t sell_sigma = (tuning && tuning->sell_sigma) ? tuning->sell_sigma : kSellDefaultSigma;
+    if ((flags & DOSE_CREATE_SELL) && sell_sigma > (1u << 24))
+        return invalid("tuning.sell_sigma must be in [1, 2^24]");
     if ((flags & DOSE_CREATE_U16_INDEX) && desc->ncols > 65536u)
         return invalid("DOSE_CREATE_U16_INDEX needs ncols <= 65536 (16-bit column indices)");
     const dose_format fmt = desc->fmt;
@@ -728,7 +733,17 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
             return st;
         }
     }
-    A->device_bytes = rp_alloc * 4 + col_alloc * 4 + ((flags & DOSE_CREATE_U16_INDEX) ? col16_alloc * 2 : 0) + val_alloc +
+    if (flags & DOSE_CREATE_SELL) {
+        std::string why;
+        if ((e = build_sell(A.get(), col, vals.data(), sell_sigma, &why)) != cudaSuccess) {
+            if (!why.empty()) {
+                free_all(A.get());
+                return invalid(why);
+            }
+            return fail(e, "SELL copy");
+        }
+    }
+    A->device_bytes = A->sell.bytes + rp_alloc * 4 + col_alloc * 4 + ((flags & DOSE_CREATE_U16_INDEX) ? col16_alloc * 2 : 0) + val_alloc +
                       (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) + x64_alloc * 8 +
                       (size_t)A->adj.grid * ncols_pad * 4 + (size_t)A->adj.grid * 8 + 4 + schedule_bytes(A->fwd) +
                       schedule_bytes(A->adj);
@@ -822,7 +837,8 @@ dose_status dose_spmv(const dose_matrix* A, const float* x, float* d, void* stre
     if (!A) return invalid("dose_spmv: null matrix");
     if (A->nrows && !d) return invalid("dose_spmv: d is NULL");
     if (A->ncols && !x) return invalid("dose_spmv: x is NULL");
-    cudaError_t e = launch_spmv(A, x, d, as_stream(stream));
+    cudaError_t e = (A->flags & DOSE_CREATE_SELL) ? launch_spmv_sell(A, x, d, as_stream(stream))
+                                                  : launch_spmv(A, x, d, as_stream(stream));
     return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_spmv launch");
 }
 
@@ -943,6 +959,12 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     // Algorithmic bytes: every stored byte of A once, the vectors once.
     const uint64_t ib = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;  // column index bytes read by dose_spmv
     out->spmv_bytes = (vb + ib) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
+    if (A->flags & DOSE_CREATE_SELL) {
+        // padded entries, one perm word per chunk slot, 8 bytes per chunk descriptor
+        out->sell_entries = A->sell.entries;
+        out->spmv_bytes = (vb + ib) * A->sell.entries + 4ull * 32 * A->sell.nchunks + 8ull * A->sell.nchunks + rs +
+                          4 * nr + 4 * nc;
+    }
     out->adjoint_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;
     out->fused_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 8 * nr + 4 * nc + 4 * nc + 8;
     // FP64 vectors: 8-byte x read once, 8-byte d written once (for F16 values and
@@ -950,6 +972,7 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     out->spmv_f64_bytes = (vb + ib) * nz + 4 * (nr + 1) + rs + 8 * nr + 8 * nc;
     out->scale = A->fmt == DOSE_FMT_U16_SCALE ? A->scale : 0.f;
     export_tuning(A->fwd.tuning, A->adj_tuning, &out->tuning);
+    out->tuning.sell_sigma = A->sell.sigma;
     return DOSE_OK;
 }
 

@@ -64,6 +64,17 @@ struct Tuning {
     uint32_t row_order = 2;     // non-empty rows of a stage: 1 = matrix order, 2 = most 4-entry groups first
 };
 
+// SELL-32-sigma copy of a matrix for the forward SpMV (DOSE_CREATE_SELL).
+struct SellArrays {
+    void* val = nullptr;      // stored values in SELL order
+    void* col = nullptr;      // column indices (4 or 2 bytes) in SELL order
+    uint2* chunk = nullptr;   // per chunk: first entry / 128, groups of four entries
+    uint32_t* perm = nullptr; // original row of each chunk slot (~0: none)
+    uint32_t nchunks = 0, sigma = 0;
+    uint64_t entries = 0;     // stored entries including padding
+    uint64_t bytes = 0;       // device bytes of the arrays above
+};
+
 struct Schedule {
     std::vector<StageDesc> desc;      // n_stages, stored CTA by CTA
     std::vector<uint16_t> ne;         // non-empty rows of NORMAL stages (offset from row0)
@@ -133,6 +144,8 @@ struct dose_matrix {
     // dose_spmv_f64 scratch: x as the kernel reads it (ncols + 1 elements of 8 bytes)
     uint2* x64 = nullptr;
 
+    dose::SellArrays sell;  // DOSE_CREATE_SELL only
+
     // adjoint scratch: per-CTA partial gradients and objective values
     float* g_part = nullptr;     // adj.grid * ncols
     double* f_part = nullptr;    // adj.grid
@@ -155,6 +168,11 @@ size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem);
 bool spmv_x_in_smem(const dose_matrix* A);
 cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s);
 size_t spmv_f64_smem_bytes(const dose_matrix* A, bool x_in_smem);
+// SELL-32-sigma (sell_kernel.cu): build from host CSR columns and encoded values, free, launch.
+cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const unsigned char* vals, uint32_t sigma,
+                       std::string* why);
+void free_sell(dose_matrix* A);
+cudaError_t launch_spmv_sell(const dose_matrix* A, const float* x, float* d, cudaStream_t s);
 bool spmv_f64_x_in_smem(const dose_matrix* A);
 cudaError_t launch_spmv_f64(const dose_matrix* A, const double* x, double* d, bool native, cudaStream_t s);
 // Adjoint shape that fits in shared memory: fills forward/scatter warp counts; false if none.
@@ -175,6 +193,7 @@ __host__ __device__ constexpr uint32_t value_bytes(int fmt) {
     return fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1u : (fmt == DOSE_FMT_F32 ? 4u : 2u);
 }
 constexpr uint32_t kMaxAdjWarps = 20;      // producer + forward + scatter warps of the adjoint kernels
+constexpr uint32_t kSellDefaultSigma = 1024;  // rows per sorting window of the SELL copy
 constexpr uint32_t kAdjMinScatterWarps = 8;  // below this the default adjoint tile shrinks to 4096 entries
 constexpr uint32_t kAdjColumnGroups = 16;  // column groups of the adjoint schedule (CTAs per group: grid / 16)
 constexpr uint32_t kXSmemMaxCols = 16384;  // x staged in shared memory up to 64 KB

@@ -78,6 +78,19 @@ def test_clinical_fused_objective_and_gradient(clinical):
     A.device_status()
 
 
+def test_clinical_sell_dose_sampled_rows(clinical):
+    """The SELL-32-1024 copy of the clinical beam (bench.py --workload sell)."""
+    csr, _, enc, p, w, x = clinical
+    A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt="u16", values=enc.values,
+                                 scales=enc.scales, sell=True)
+    d = A.spmv(_to(x)).cpu().numpy()
+    rows = _sample_rows(csr.nrows, enc.row_ptr, 6000, 4)
+    fwd_check(d[rows], oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x))
+    assert np.all(d[np.diff(enc.row_ptr.astype(np.int64)) == 0] == 0)
+    A.device_status()
+    A.close()
+
+
 @pytest.mark.parametrize("native", [False, True])
 def test_clinical_half_double_sampled_rows(native):
     """The paper's Half/double configuration at the clinical size: F16 values,

@@ -115,6 +115,54 @@ def test_unit_vectors_reproduce_stored_columns_bit_exact(tiny, fmt):
         assert np.array_equal(d.view(np.uint32), expect.view(np.uint32)), j
 
 
+@pytest.mark.parametrize("fmt", ["u16", "bf16", "fp8", "f16", "f32"])
+@pytest.mark.parametrize("sigma", [1, 32, 1024, 1 << 20])
+@pytest.mark.parametrize("index16", [False, True])
+def test_forward_sell_storage(tiny, fmt, sigma, index16):
+    """DOSE_CREATE_SELL: dose_spmv on the SELL-32-sigma copy (one row per lane)
+    against the oracle; padding counted in sell_entries; bitwise repeatable;
+    unit vectors give the stored values bit-exactly."""
+    A, enc = make(tiny, fmt, sell=True, index16=index16, tuning=dict(sell_sigma=sigma))
+    x = _x(tiny.ncols)
+    d = A.spmv(_to(x)).cpu().numpy()
+    fwd_check(d, oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x))
+    assert np.array_equal(d.view(np.uint32), A.spmv(_to(x)).cpu().numpy().view(np.uint32))
+    # padding: every chunk of 32 consecutive rows (after sorting inside windows of
+    # sigma rows) is padded to its longest row, rounded up to 4
+    lens = np.diff(enc.row_ptr.astype(np.int64))
+    order = np.concatenate([w[np.argsort(-lens[w], kind="stable")] for w in
+                            np.array_split(np.arange(tiny.nrows), np.arange(sigma, tiny.nrows, sigma))]) \
+        if sigma > 1 else np.arange(tiny.nrows)
+    chunks = [lens[order[c:c + 32]].max() for c in range(0, tiny.nrows, 32)]
+    assert A.info()["sell_entries"] == sum(128 * ((m + 3) // 4) for m in chunks)
+    rows_of = np.repeat(np.arange(tiny.nrows), lens)
+    for j in np.random.default_rng(1).choice(tiny.ncols, 4, replace=False):
+        e = np.zeros(tiny.ncols, dtype=np.float32)
+        e[j] = 1.0
+        expect = np.zeros(tiny.nrows, dtype=np.float32)
+        sel = enc.col == j
+        expect[rows_of[sel]] = enc.decoded[sel].astype(np.float32)
+        assert np.array_equal(A.spmv(_to(e)).cpu().numpy().view(np.uint32), expect.view(np.uint32))
+    # the other calls still use the CSR arrays
+    r = np.random.default_rng(4).normal(size=tiny.nrows).astype(np.float32)
+    g = A.adjoint(_to(r)).cpu().numpy()
+    adj_check(g, oracle.spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r),
+              oracle.abs_spmv_t(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, r))
+    A.device_status()
+
+
+@pytest.mark.parametrize("name", list(edge_case_matrices().keys()))
+def test_forward_sell_edge_cases(name):
+    csr = edge_case_matrices()[name]
+    for sigma in (1, 64, 4096):
+        for fmt in ("u16", "fp8"):
+            A, enc = make(csr, fmt, sell=True, tuning=dict(sell_sigma=sigma))
+            x = _x(csr.ncols, seed=3)
+            fwd_check(A.spmv(_to(x)).cpu().numpy(), oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x),
+                      rtol=3e-5 if csr.row_lengths().max() > 4096 else 1e-5)
+            A.device_status()
+
+
 def test_compensated_long_rows_adversarial():
     # descending magnitudes over 16000 entries: plain FP32 loses digits
     n = 16000
