@@ -70,8 +70,7 @@ struct SellArrays {
     void* col = nullptr;      // column indices (4 or 2 bytes) in SELL order
     uint2* chunk = nullptr;   // per chunk: first entry / 128, groups of four entries
     uint32_t* perm = nullptr; // original row of each chunk slot (~0: none)
-    uint32_t* cta_begin = nullptr;  // grid + 1 chunk indices: CTA b's contiguous range
-    uint32_t nchunks = 0, sigma = 0, grid = 0;
+    uint32_t nchunks = 0, sigma = 0;
     uint64_t entries = 0;     // stored entries including padding
     uint64_t bytes = 0;       // device bytes of the arrays above
 };

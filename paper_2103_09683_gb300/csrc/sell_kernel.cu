@@ -19,9 +19,8 @@
 // the whole matrix) would pad every one of the 10.5 M rows of the clinical beam
 // to its longest row and is not offered.
 //
-// Kernel: CTA b takes a contiguous range of chunks holding about 1/grid of the
-// bytes (fixed at create) and its warps deal them round-robin, so each CTA
-// streams one region of HBM; lane l
+// Kernel: CTA b takes a contiguous range of chunks and its warps deal them
+// round-robin (each CTA streams one region of HBM); lane l
 // sums its row over the chunk's groups with four accumulators (combined as
 // (0 + 1) + (2 + 3)), x in shared memory; the row's dose is written to
 // d[perm].  A row is summed by one lane in storage order, so the result does
@@ -46,7 +45,6 @@ struct SellParams {
     const void* val;       // stored values, SELL order
     const uint2* chunk;    // {first entry / 128, groups} per chunk
     const uint32_t* perm;  // 32 per chunk
-    const uint32_t* cta_begin;  // grid + 1: CTA b runs chunks [cta_begin[b], cta_begin[b + 1])
     const float* row_scale;
     float scale;
     const float* x;
@@ -64,9 +62,10 @@ __global__ void __launch_bounds__(kSellWarps * 32) sell_spmv_kernel(const SellPa
     }
     const float* xs = XSMEM ? xs_smem : p.x;
     const uint32_t lane = threadIdx.x & 31;
-    // CTA b owns the contiguous chunks [c0, c1) of about equal bytes (one region
-    // of HBM streamed per CTA); its warps take them round-robin
-    const uint32_t c0 = __ldg(p.cta_begin + blockIdx.x), c1 = __ldg(p.cta_begin + blockIdx.x + 1);
+    // CTA b owns the contiguous chunks [c0, c1) (one region of HBM streamed per
+    // CTA); its warps take them round-robin
+    const uint32_t c0 = (uint32_t)(((uint64_t)p.nchunks * blockIdx.x) / gridDim.x);
+    const uint32_t c1 = (uint32_t)(((uint64_t)p.nchunks * (blockIdx.x + 1)) / gridDim.x);
     for (uint32_t c = c0 + (threadIdx.x >> 5); c < c1; c += kSellWarps) {
         const uint2 ch = __ldg(p.chunk + c);
         const size_t base = (size_t)ch.x * 128 + 4 * lane;
@@ -114,7 +113,9 @@ cudaError_t launch_t(const dose_matrix* A, const SellParams& p, cudaStream_t s) 
     auto k = xsmem ? sell_spmv_kernel<FMT, IW, true> : sell_spmv_kernel<FMT, IW, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<A->sell.grid, kSellWarps * 32, smem, s>>>(p);
+    const uint32_t grid = std::max(1u, std::min<uint32_t>((uint32_t)A->sm_count * kSellCtasPerSm,
+                                                          (A->sell.nchunks + kSellWarps - 1) / kSellWarps));
+    k<<<grid, kSellWarps * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -158,21 +159,6 @@ cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const u
         for (uint32_t k = c0; k < c0 + kSellC; ++k) perm.push_back(k < c1 ? order[k] : 0xFFFFFFFFu);
     }
     const size_t entries = (size_t)groups * 128;
-    // contiguous chunk ranges of about equal bytes, one per CTA
-    const uint32_t grid = std::max(1, A->sm_count) * kSellCtasPerSm;
-    std::vector<uint32_t> cta_begin(grid + 1, (uint32_t)chunk.size());
-    {
-        const uint64_t per_group = 128ull * (esize + iw), per_chunk = 32ull * 8 + 8;
-        const uint64_t total = groups * per_group + chunk.size() * per_chunk;
-        uint64_t acc = 0;
-        uint32_t b = 0;
-        cta_begin[0] = 0;
-        for (uint32_t c = 0; c < chunk.size(); ++c) {
-            while (b + 1 < grid && acc * grid >= total * (b + 1)) cta_begin[++b] = c;
-            acc += chunk[c].y * per_group + per_chunk;
-        }
-        while (b + 1 < grid) cta_begin[++b] = (uint32_t)chunk.size();
-    }
     std::vector<unsigned char> sval(entries * esize + 64, 0), scol(entries * iw + 64, 0);
     for (size_t c = 0; c < chunk.size(); ++c)
         for (uint32_t l = 0; l < kSellC; ++l) {
@@ -196,9 +182,6 @@ cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const u
     if ((e = cudaMalloc(&S.col, scol.size())) != cudaSuccess) return e;
     if ((e = cudaMalloc(&S.chunk, std::max<size_t>(chunk.size(), 1) * sizeof(uint2))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&S.perm, std::max<size_t>(perm.size(), 1) * 4)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&S.cta_begin, cta_begin.size() * 4)) != cudaSuccess) return e;
-    if ((e = cudaMemcpy(S.cta_begin, cta_begin.data(), cta_begin.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
-        return e;
     if ((e = cudaMemcpy(S.val, sval.data(), sval.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(S.col, scol.data(), scol.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if (!chunk.empty() &&
@@ -207,10 +190,9 @@ cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const u
     if (!perm.empty() && (e = cudaMemcpy(S.perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
     S.nchunks = (uint32_t)chunk.size();
-    S.grid = grid;
     S.entries = entries;
     S.sigma = sigma;
-    S.bytes = sval.size() + scol.size() + chunk.size() * sizeof(uint2) + perm.size() * 4 + cta_begin.size() * 4;
+    S.bytes = sval.size() + scol.size() + chunk.size() * sizeof(uint2) + perm.size() * 4;
     return cudaSuccess;
 }
 
@@ -219,7 +201,6 @@ void free_sell(dose_matrix* A) {
     cudaFree(A->sell.col);
     cudaFree(A->sell.chunk);
     cudaFree(A->sell.perm);
-    cudaFree(A->sell.cta_begin);
     A->sell = SellArrays();
 }
 
@@ -230,7 +211,6 @@ cudaError_t launch_spmv_sell(const dose_matrix* A, const float* x, float* d, cud
     p.val = A->sell.val;
     p.chunk = A->sell.chunk;
     p.perm = A->sell.perm;
-    p.cta_begin = A->sell.cta_begin;
     p.row_scale = A->row_scale;
     p.scale = A->scale;
     p.x = x;
