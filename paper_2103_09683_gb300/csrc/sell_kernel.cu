@@ -19,8 +19,7 @@
 // the whole matrix) would pad every one of the 10.5 M rows of the clinical beam
 // to its longest row and is not offered.
 //
-// Kernel: CTA b takes a contiguous range of chunks and its warps deal them
-// round-robin (each CTA streams one region of HBM); lane l
+// Kernel: every warp takes chunks c = warp id, + number of warps, ...; lane l
 // sums its row over the chunk's groups with four accumulators (combined as
 // (0 + 1) + (2 + 3)), x in shared memory; the row's dose is written to
 // d[perm].  A row is summed by one lane in storage order, so the result does
@@ -62,11 +61,8 @@ __global__ void __launch_bounds__(kSellWarps * 32) sell_spmv_kernel(const SellPa
     }
     const float* xs = XSMEM ? xs_smem : p.x;
     const uint32_t lane = threadIdx.x & 31;
-    // CTA b owns the contiguous chunks [c0, c1) (one region of HBM streamed per
-    // CTA); its warps take them round-robin
-    const uint32_t c0 = (uint32_t)(((uint64_t)p.nchunks * blockIdx.x) / gridDim.x);
-    const uint32_t c1 = (uint32_t)(((uint64_t)p.nchunks * (blockIdx.x + 1)) / gridDim.x);
-    for (uint32_t c = c0 + (threadIdx.x >> 5); c < c1; c += kSellWarps) {
+    const uint32_t nwarps = gridDim.x * kSellWarps;
+    for (uint32_t c = blockIdx.x * kSellWarps + (threadIdx.x >> 5); c < p.nchunks; c += nwarps) {
         const uint2 ch = __ldg(p.chunk + c);
         const size_t base = (size_t)ch.x * 128 + 4 * lane;
         const T* vp = static_cast<const T*>(p.val) + base;
