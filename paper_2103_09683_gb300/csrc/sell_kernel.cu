@@ -68,29 +68,52 @@ __global__ void __launch_bounds__(kSellWarps * 32) sell_spmv_kernel(const SellPa
         const T* vp = static_cast<const T*>(p.val) + base;
         const unsigned char* cp = static_cast<const unsigned char*>(p.col) + base * IW;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-        for (uint32_t g = 0; g < ch.y; ++g) {
-            uint32_t cc[4];
+        // raw words of one group: four column indices (16 or 8 bytes) and four values (16, 8 or 4 bytes)
+        struct Raw {
+            uint4 c, v;
+        };
+        auto load = [&](uint32_t g) {
+            Raw r;
             if (IW == 4) {
-                const uint4 q = __ldg(reinterpret_cast<const uint4*>(cp + (size_t)g * 128 * IW));
-                cc[0] = q.x; cc[1] = q.y; cc[2] = q.z; cc[3] = q.w;
+                r.c = __ldg(reinterpret_cast<const uint4*>(cp + (size_t)g * 128 * IW));
             } else {
                 const uint2 q = __ldg(reinterpret_cast<const uint2*>(cp + (size_t)g * 128 * IW));
-                cc[0] = q.x & 0xFFFFu; cc[1] = q.x >> 16; cc[2] = q.y & 0xFFFFu; cc[3] = q.y >> 16;
+                r.c = make_uint4(q.x, q.y, 0u, 0u);
+            }
+            if constexpr (sizeof(T) == 4) {
+                r.v = __ldg(reinterpret_cast<const uint4*>(vp + (size_t)g * 128));
+            } else if constexpr (sizeof(T) == 2) {
+                const uint2 q = __ldg(reinterpret_cast<const uint2*>(vp + (size_t)g * 128));
+                r.v = make_uint4(q.x, q.y, 0u, 0u);
+            } else {
+                r.v = make_uint4(__ldg(reinterpret_cast<const uint32_t*>(vp + (size_t)g * 128)), 0u, 0u, 0u);
+            }
+            return r;
+        };
+        auto use = [&](const Raw& r) {
+            uint32_t cc[4];
+            if (IW == 4) {
+                cc[0] = r.c.x; cc[1] = r.c.y; cc[2] = r.c.z; cc[3] = r.c.w;
+            } else {
+                cc[0] = r.c.x & 0xFFFFu; cc[1] = r.c.x >> 16; cc[2] = r.c.y & 0xFFFFu; cc[3] = r.c.y >> 16;
             }
             float a[4];
             if constexpr (sizeof(T) == 4) {
-                const uint4 q = __ldg(reinterpret_cast<const uint4*>(vp + (size_t)g * 128));
-                a[0] = __uint_as_float(q.x); a[1] = __uint_as_float(q.y);
-                a[2] = __uint_as_float(q.z); a[3] = __uint_as_float(q.w);
-            } else if constexpr (sizeof(T) == 2) {
-                const uint2 q = __ldg(reinterpret_cast<const uint2*>(vp + (size_t)g * 128));
-                Fmt<FMT>::dec4(q.x, q.y, a);
+                a[0] = __uint_as_float(r.v.x); a[1] = __uint_as_float(r.v.y);
+                a[2] = __uint_as_float(r.v.z); a[3] = __uint_as_float(r.v.w);
             } else {
-                Fmt<FMT>::dec4(__ldg(reinterpret_cast<const uint32_t*>(vp + (size_t)g * 128)), 0u, a);
+                Fmt<FMT>::dec4(r.v.x, r.v.y, a);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc[u] = __fmaf_rn(a[u], XSMEM ? xs[cc[u]] : __ldg(xs + cc[u]), acc[u]);
+        };
+        // two groups in flight ahead of the one being summed
+        Raw r0 = ch.y > 0 ? load(0) : Raw{}, r1 = ch.y > 1 ? load(1) : Raw{};
+        for (uint32_t g = 0; g < ch.y; ++g) {
+            const Raw cur = r0;
+            r0 = r1;
+            if (g + 2 < ch.y) r1 = load(g + 2);
+            use(cur);
         }
         const uint32_t row = __ldg(p.perm + (size_t)c * kSellC + lane);
         if (row != 0xFFFFFFFFu) {
