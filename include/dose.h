@@ -136,7 +136,7 @@ typedef struct {
                                    counts) */
     uint32_t adj_row_order;     /* the same for the adjoint schedule */
     uint32_t sell_sigma;        /* DOSE_CREATE_SELL: rows per sorting window (1 = no sorting;
-                                   default 1024); read at create only */
+                                   default 2^20); read at create only */
 } dose_tuning;
 
 typedef struct {

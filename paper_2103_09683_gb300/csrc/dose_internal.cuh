@@ -193,7 +193,7 @@ __host__ __device__ constexpr uint32_t value_bytes(int fmt) {
     return fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1u : (fmt == DOSE_FMT_F32 ? 4u : 2u);
 }
 constexpr uint32_t kMaxAdjWarps = 20;      // producer + forward + scatter warps of the adjoint kernels
-constexpr uint32_t kSellDefaultSigma = 1024;  // rows per sorting window of the SELL copy
+constexpr uint32_t kSellDefaultSigma = 1u << 20;  // rows per sorting window of the SELL copy
 constexpr uint32_t kAdjMinScatterWarps = 8;  // below this the default adjoint tile shrinks to 4096 entries
 constexpr uint32_t kAdjColumnGroups = 16;  // column groups of the adjoint schedule (CTAs per group: grid / 16)
 constexpr uint32_t kXSmemMaxCols = 16384;  // x staged in shared memory up to 64 KB

@@ -79,7 +79,7 @@ def test_clinical_fused_objective_and_gradient(clinical):
 
 
 def test_clinical_sell_dose_sampled_rows(clinical):
-    """The SELL-32-1024 copy of the clinical beam (bench.py --workload sell)."""
+    """The default SELL-32-2^20 copy of the clinical beam (bench.py --workload sell)."""
     csr, _, enc, p, w, x = clinical
     A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt="u16", values=enc.values,
                                  scales=enc.scales, sell=True)
