@@ -232,24 +232,43 @@ def run_gpu(args):
     total_ms = max_over_ranks(total_ms, device)
     A.device_status()
 
-    # end to end through the public API with host buffers: H2D x, both calls, D2H d and f
+    # End to end through the public API with host buffers: every step copies x in
+    # from pinned host memory, runs both calls, and copies its dose d and
+    # objective f out to pinned host memory.  The read-back of step k runs on a
+    # copy stream while step k + 1 computes (d and f double-buffered; a buffer
+    # is reused only after its copy has landed); the timed region ends when the
+    # last copy has landed.
     xh = x0.cpu().pin_memory()
-    dh = torch.empty(A.nrows, dtype=torch.float32).pin_memory()
-    fh = torch.empty(1, dtype=torch.float64).pin_memory()
+    d_dev = [d, torch.empty_like(d)]
+    f_dev = [f, torch.empty_like(f)]
+    dh = [torch.empty(A.nrows, dtype=torch.float32).pin_memory() for _ in range(2)]
+    fh = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    copy_stream = torch.cuda.Stream(device=device)
+    ready = [torch.cuda.Event() for _ in range(2)]
+    landed = [torch.cuda.Event() for _ in range(2)]
     ke = max(3, min(K, 50))
-    for _ in range(2):
-        x.copy_(xh, non_blocking=True)
-        step()
-        dh.copy_(d, non_blocking=True)
-        fh.copy_(f, non_blocking=True)
+
+    def e2e_steps(n):
+        for k in range(n):
+            b = k & 1
+            if k >= 2:
+                stream.wait_event(landed[b])
+            x.copy_(xh, non_blocking=True)
+            A.spmv(x, d_dev[b])
+            A.pg_step(x, p, w, eta, f=f_dev[b])
+            ready[b].record(stream)
+            copy_stream.wait_event(ready[b])
+            with torch.cuda.stream(copy_stream):
+                dh[b].copy_(d_dev[b], non_blocking=True)
+                fh[b].copy_(f_dev[b], non_blocking=True)
+            landed[b].record(copy_stream)
+        stream.wait_stream(copy_stream)
+
+    e2e_steps(4)
     torch.cuda.synchronize()
     e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     e2[0].record(stream)
-    for _ in range(ke):
-        x.copy_(xh, non_blocking=True)
-        step()
-        dh.copy_(d, non_blocking=True)
-        fh.copy_(f, non_blocking=True)
+    e2e_steps(ke)
     e2[1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = e2[0].elapsed_time(e2[1]) / ke
@@ -287,7 +306,8 @@ def run_gpu(args):
         "roofline": roof,
         "e2e": {"value": round(step_bytes / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
                 "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": 4 * A.ncols,
-                "d2h_bytes_per_step": 4 * A.nrows + 8},
+                "d2h_bytes_per_step": 4 * A.nrows + 8,
+                "note": "pinned host buffers; step k's d and f copied out while step k+1 computes"},
         "gpu_launches": 3 * K,
         "clocks": clk,
         "tuning": info["tuning"],
