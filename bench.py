@@ -227,8 +227,9 @@ def run_gpu(args):
     time.sleep(0.2)
     clk = clocks.stop()
     total_ms = e_start.elapsed_time(e_end)
-    spmv_ms = sum(ev[k][0].elapsed_time(ev[k][1]) for k in range(K)) / K
-    grad_ms = sum(ev[k][1].elapsed_time(ev[k][2]) for k in range(K)) / K
+    spmv_all = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    grad_all = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    spmv_ms, grad_ms = sum(spmv_all) / K, sum(grad_all) / K
     total_ms = max_over_ranks(total_ms, device)
     A.device_status()
 
@@ -301,6 +302,10 @@ def run_gpu(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "ms_per_dose_eval": round(spmv_ms, 5),
         "ms_per_dose_grad_eval": round(grad_ms, 5),
+        "ms_stats": {"dose_eval": {"mean": round(spmv_ms, 5), "median": round(statistics.median(spmv_all), 5),
+                                   "min": round(min(spmv_all), 5)},
+                     "dose_grad_eval": {"mean": round(grad_ms, 5), "median": round(statistics.median(grad_all), 5),
+                                        "min": round(min(grad_all), 5)}},
         "pct_of_nominal_8tbs": round(100 * spmv_gbs / 8000.0, 1),
         "kernels": kernels,
         "roofline": roof,
