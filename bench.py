@@ -14,6 +14,7 @@ HBM.  Prints one JSON line.
     python bench.py --workload halfdouble            # the paper's Half/double: F16 values, FP64 x and d
     python bench.py --workload robust                # 3-beam plan x 9 setup shifts: robust objective + PG step
     python bench.py --workload sell                  # dose eval on SELL-32-sigma copies, sigma sweep, vs CSR
+    python bench.py --workload liver1                # the paper's Liver 1 shape (2.97e6 x 6.8e4, 1.48e9 entries)
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on the same workload and metric.  Under torchrun (N > 1) every rank
@@ -829,6 +830,106 @@ def run_sell(args):
     print(json.dumps(out), flush=True)
 
 
+LIVER_METRIC = ("dose SpMV on a matrix shaped like the paper's liver beam 1 (Table I): effective HBM GB/s "
+                "of each call's algorithmic bytes and GFLOP/s, Half/double and FP32 forms")
+
+
+def run_liver1(args):
+    """The paper's own headline matrix shape: 2.97e6 voxels x 6.8e4 spots,
+    1.48e9 entries, ~75 % empty rows, most non-empty rows longer than 1024
+    entries (whole-CTA reduction), x too large for shared memory (gathered from
+    L2).  Variants: the paper's Half/double (F16 values, FP64 x and d; the
+    paper's 6 nnz + 12 nr + 8 nc bytes) with double-float and FP64-FMA
+    accumulation, and the FP32-vector dose_spmv on u16 + scale.  Sampled rows
+    are checked against the FP64 oracle."""
+    import torch
+
+    import oracle
+    import paper_2103_09683_gb300 as dose
+
+    dose.build()
+    torch.cuda.set_device(0)
+    beam = dosegen.LIVER1_SHAPED
+    csr = dosegen.generate(beam)
+    rng = np.random.default_rng(11)
+    rp = csr.row_ptr.astype(np.int64)
+    lens = rp[1:] - rp[:-1]
+    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 4000, replace=False))
+    sub_lens = lens[rows]
+    sub_rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(sub_lens, out=sub_rp[1:])
+    take = np.repeat(rp[rows] - sub_rp[:-1], sub_lens) + np.arange(int(sub_rp[-1]))
+    sub = dosegen.CSR(len(rows), csr.ncols, sub_rp.astype(np.uint32), csr.col[take], csr.val[take])
+    vmax = float(csr.val.max())
+    A16 = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="f16", values_f64=csr.val)
+    Au = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="u16", values_f64=csr.val)
+    nrows, ncols, nnz = csr.nrows, csr.ncols, csr.nnz
+    del csr, take
+    enc16 = oracle.encode(sub, oracle.F16)
+    encu = oracle.encode(sub, oracle.U16_SCALE)
+    # the u16 scale of the whole matrix, applied to the sampled entries
+    s = float(np.float32(vmax / 65535.0))
+    qu = np.minimum(np.rint(sub.val / s), 65535.0)
+    assert float(Au.info()["scale"]) == s
+    x64 = dosegen.spot_weights_f64(ncols, dosegen.weight_seed(beam))
+    x32 = dosegen.spot_weights(ncols, dosegen.weight_seed(beam))
+    xd64, xd32 = torch.from_numpy(x64).cuda(), torch.from_numpy(x32).cuda()
+    ref64 = oracle.spmv(len(rows), enc16.row_ptr, enc16.col, enc16.decoded, x64)
+    abs64 = oracle.spmv(len(rows), enc16.row_ptr, enc16.col, np.abs(enc16.decoded), np.abs(x64))
+    ref32 = oracle.spmv(len(rows), encu.row_ptr, encu.col, s * qu, x32)
+    peak, _ = _peaks()
+    K = max(3, min(args.steps, 50))
+    rows_t = torch.from_numpy(rows).cuda()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    variants = []
+    d64 = torch.empty(nrows, dtype=torch.float64, device="cuda")
+    b64 = A16.info()["spmv_f64_bytes"]
+    for native in (False, True):
+        ms = timed(lambda: A16.spmv_f64(xd64, d64, native=native))
+        err = np.abs(d64[rows_t].cpu().numpy() - ref64) / abs64
+        gbs = b64 / (ms * 1e-3) / 1e9
+        variants.append({"form": "half_double", "accumulation": "fp64_fma" if native else "double_float",
+                         "ms": round(ms, 4), "bytes": b64, "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                         "gflops": round(2 * nnz / (ms * 1e-3) / 1e9, 1),
+                         "err_over_sum_abs": {"max": float(err.max()), "mean": float(err.mean())}})
+    del d64
+    d32 = torch.empty(nrows, dtype=torch.float32, device="cuda")
+    bu = Au.info()["spmv_bytes"]
+    ms = timed(lambda: Au.spmv(xd32, d32))
+    rel = np.abs(d32[rows_t].cpu().numpy().astype(np.float64) - ref32) / ref32
+    gbs = bu / (ms * 1e-3) / 1e9
+    variants.append({"form": "u16+scale, FP32 vectors", "accumulation": "fp32", "ms": round(ms, 4), "bytes": bu,
+                     "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                     "gflops": round(2 * nnz / (ms * 1e-3) / 1e9, 1), "max_rel_err": float(rel.max())})
+    clk = clocks.stop()
+    A16.device_status()
+    Au.device_status()
+    base = variants[0]
+    out = {"metric": LIVER_METRIC, "value": base["achieved_gbs"], "unit": "GB/s", "n_gpus": 1, "steps": K,
+           "warmup": args.warmup, "ms_per_step": base["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f16 values, f64 vectors", "data": "synthetic",
+           "config": {"workload": f"liver-beam-1-shaped pencil beam: {nrows} voxels x {ncols} spots, {nnz} entries "
+                                  f"(Table I: 2.97e6 x 6.80e4, 1.48e9); step = one dose evaluation",
+                      "sampled_rows": int(len(rows)), "x_in_shared_memory": False, "peak_gbs": peak,
+                      "paper_a100_half_double": "1250-1350 GB/s, up to 420 GFLOP/s on the liver beams (context)"},
+           "clocks": clk, "variants": variants}
+    print(json.dumps(out), flush=True)
+
+
 def batched_cpu_baseline(csr, X, budget_s=10.0):
     """The oracle's FP64 SpMM on row blocks of one scenario matrix (about
     budget_s of single-core work), as GB/s of the same byte model."""
@@ -861,7 +962,7 @@ def main():
     ap.add_argument("--tuning", default="", help="schedule knobs, e.g. tile_nnz=8192,adj_scatter_warps=4")
     ap.add_argument("--matrices", default="", help="batched: subset of the 27 scenario matrices, e.g. 4,13,22")
     ap.add_argument("--workload", default="clinical",
-                    choices=["clinical", "batched", "precision", "halfdouble", "robust", "sell"],
+                    choices=["clinical", "batched", "precision", "halfdouble", "robust", "sell", "liver1"],
                     help="clinical: the dose + dose-gradient step (default); batched: 27 matrices x 16 vectors; "
                          "precision: dose eval per stored format with its error vs the FP64 oracle; "
                          "halfdouble: F16 values with FP64 x and d; robust: 3-beam plan x 9 scenarios")
@@ -880,6 +981,8 @@ def main():
         run_robust(args)
     elif args.workload == "sell":
         run_sell(args)
+    elif args.workload == "liver1":
+        run_liver1(args)
     else:
         run_gpu(args)
 

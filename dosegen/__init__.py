@@ -119,7 +119,14 @@ TINY = Beam(grid=(32, 32, 20), lattice=(25, 20), spacing=(32 / 25, 32 / 20), sig
 CLINICAL = Beam(grid=(256, 256, 160), lattice=(80, 50), spacing=(1.25, 1.25), sigma=4.0,
                 tau=0.009134, seed=SEED0 + 1)
 
-NNZ_TARGETS = {"tiny": 2.0e5, "clinical": 1.5e8}
+# Shaped like liver beam 1 of Table I (2.97e6 rows, 6.80e4 columns, 1.48e9
+# entries, ~70 % empty rows, Fig. 2): 150x150x132 voxels, 272x250 spots a
+# quarter voxel apart (dense enough that the central voxels see thousands of
+# spots, as the energy layers of a real beam do).
+LIVER1_SHAPED = Beam(grid=(150, 150, 132), lattice=(272, 250), spacing=(0.25, 0.25), sigma=4.0,
+                     tau=0.028798, seed=SEED0 + 9)
+
+NNZ_TARGETS = {"tiny": 2.0e5, "clinical": 1.5e8, "liver1": 1.48e9}
 
 _SCENARIO_SHIFTS = [(sx, sy) for sy in (-3.0, 0.0, 3.0) for sx in (-3.0, 0.0, 3.0)]
 

@@ -34,6 +34,17 @@ def test_clinical_beam_counts_and_row_length_profile():
     assert rl.size / dosegen.CLINICAL.ncols > 40                # rows >> columns
 
 
+def test_liver1_shaped_beam_counts():
+    """The paper-shaped matrix: Table I's liver beam 1 dimensions and nnz within
+    1 %, about 70 % empty rows (Fig. 2), rows of thousands of entries."""
+    b = dosegen.LIVER1_SHAPED
+    n, rl = dosegen.count_nnz(b, row_lengths=True)
+    assert b.nrows == 2_970_000 and b.ncols == 68_000
+    assert abs(n - dosegen.NNZ_TARGETS["liver1"]) <= 0.01 * dosegen.NNZ_TARGETS["liver1"]
+    assert 0.65 <= np.mean(rl == 0) <= 0.8
+    assert rl.max() > 4000 and np.mean(rl[rl > 0] > 1024) > 0.5
+
+
 def test_generation_is_deterministic():
     a = dosegen.generate(dosegen.TINY)
     b = dosegen.generate(dosegen.TINY)
