@@ -861,8 +861,9 @@ def run_liver1(args):
     take = np.repeat(rp[rows] - sub_rp[:-1], sub_lens) + np.arange(int(sub_rp[-1]))
     sub = dosegen.CSR(len(rows), csr.ncols, sub_rp.astype(np.uint32), csr.col[take], csr.val[take])
     vmax = float(csr.val.max())
-    A16 = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="f16", values_f64=csr.val)
-    Au = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="u16", values_f64=csr.val)
+    tun = _tuning_kv(args) or None
+    A16 = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="f16", values_f64=csr.val, tuning=tun)
+    Au = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="u16", values_f64=csr.val, tuning=tun)
     nrows, ncols, nnz = csr.nrows, csr.ncols, csr.nnz
     del csr, take
     enc16 = oracle.encode(sub, oracle.F16)
@@ -924,7 +925,8 @@ def run_liver1(args):
            "vs_baseline": None, "dtype": "f16 values, f64 vectors", "data": "synthetic",
            "config": {"workload": f"liver-beam-1-shaped pencil beam: {nrows} voxels x {ncols} spots, {nnz} entries "
                                   f"(Table I: 2.97e6 x 6.80e4, 1.48e9); step = one dose evaluation",
-                      "sampled_rows": int(len(rows)), "x_in_shared_memory": False, "peak_gbs": peak,
+                      "sampled_rows": int(len(rows)), "peak_gbs": peak, "tuning": _tuning_kv(args),
+                      "info": {k: Au.info()[k] for k in ("n_stages", "n_coop_rows", "lanes_hist", "adj_window")},
                       "paper_a100_half_double": "1250-1350 GB/s, up to 420 GFLOP/s on the liver beams (context)"},
            "clocks": clk, "variants": variants}
     print(json.dumps(out), flush=True)
