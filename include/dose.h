@@ -115,7 +115,8 @@ typedef struct {
     /* forward SpMV (dose_spmv, dose_spmv_batched) */
     uint32_t tile_nnz;       /* max entries staged per pipeline stage (256..16384) */
     uint32_t tile_rows;      /* max rows per stage (32..8192) */
-    uint32_t coop_nnz;       /* rows longer than this are reduced by the whole CTA */
+    uint32_t coop_nnz;       /* rows longer than this are reduced by the whole CTA (default: the tile;
+                                the adjoint schedule uses at most 1024) */
     uint32_t lane_target;    /* lanes per row = power of two nearest mean row length / lane_target */
     uint32_t stages;         /* pipeline depth (2..8) */
     uint32_t consumer_warps; /* 4, 8 or 16 */
@@ -152,7 +153,8 @@ typedef struct {
     uint32_t adj_block_adjoint; /* threads per CTA of the adjoint (0 if it does not fit) */
     uint32_t max_row_len;
     uint32_t adj_window;        /* columns of each CTA's gradient window in the adjoint schedule */
-    uint32_t reserved0;
+    uint32_t fwd_window;        /* ncols > 16384: columns of each forward CTA's window of x (staged in
+                                   shared memory when it fits beside the ring); else 0 */
     uint64_t device_bytes;      /* device memory held by the handle */
     uint64_t spmv_bytes;        /* algorithmic HBM bytes of one dose_spmv */
     uint64_t adjoint_bytes;     /* ... of one dose_adjoint */

@@ -76,7 +76,7 @@ class _Info(ctypes.Structure):
                 ("block", ctypes.c_uint32), ("adj_n_stages", ctypes.c_uint32),
                 ("adj_block_fused", ctypes.c_uint32), ("adj_block_adjoint", ctypes.c_uint32),
                 ("max_row_len", ctypes.c_uint32), ("adj_window", ctypes.c_uint32),
-                ("reserved0", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("spmv_bytes", ctypes.c_uint64),
+                ("fwd_window", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("spmv_bytes", ctypes.c_uint64),
                 ("adjoint_bytes", ctypes.c_uint64), ("fused_bytes", ctypes.c_uint64), ("spmv_f64_bytes", ctypes.c_uint64),
                 ("sell_entries", ctypes.c_uint64),
                 ("scale", ctypes.c_float), ("tuning", Tuning)]
@@ -393,7 +393,7 @@ class DoseMatrix:
     def info(self) -> dict:
         inf = _Info()
         _check(load().dose_matrix_info(self._h, ctypes.byref(inf)))
-        out = {k: getattr(inf, k) for k, _ in _Info._fields_ if k not in ("lanes_hist", "tuning", "reserved0")}
+        out = {k: getattr(inf, k) for k, _ in _Info._fields_ if k not in ("lanes_hist", "tuning")}
         out["lanes_hist"] = list(inf.lanes_hist)
         out["tuning"] = inf.tuning.as_dict()
         return out

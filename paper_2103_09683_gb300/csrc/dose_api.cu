@@ -360,7 +360,7 @@ static dose_status check_tuning(const dose_matrix* A, Tuning& t) {
     if (t.consumer_warps != 4 && t.consumer_warps != 8 && t.consumer_warps != 16)
         return invalid("tuning.consumer_warps must be 4, 8 or 16");
     if (t.row_order < 1 || t.row_order > 2) return invalid("tuning.row_order must be 1 or 2");
-    if (spmv_smem_bytes(A, t, spmv_x_in_smem(A)) > kMaxSmemPerBlock)
+    if (spmv_smem_bytes(A, t, spmv_x_in_smem(A, t)) > kMaxSmemPerBlock)
         return invalid("tuning needs more shared memory than a CTA has");
     return DOSE_OK;
 }
@@ -369,7 +369,7 @@ static dose_status check_tuning(const dose_matrix* A, Tuning& t) {
 // first the tile (down to 1024 entries), then the depth (down to 2).
 static void fit_default_tuning(const dose_matrix* A, Tuning& t, const dose_tuning* in) {
     const bool user_tile = in && in->tile_nnz, user_stages = in && in->stages;
-    while (spmv_smem_bytes(A, t, spmv_x_in_smem(A)) > kMaxSmemPerBlock) {
+    while (spmv_smem_bytes(A, t, spmv_x_in_smem(A, t)) > kMaxSmemPerBlock) {
         if (!user_tile && t.tile_nnz > 1024) {
             t.tile_nnz /= 2;
             if (!(in && in->coop_nnz)) t.coop_nnz = std::min(t.coop_nnz, t.tile_nnz);
@@ -466,7 +466,7 @@ static Tuning adj_schedule_tuning(const Tuning& fwd, const AdjTuning& a) {
     Tuning t = fwd;
     t.tile_nnz = a.tile_nnz;
     t.tile_rows = a.tile_rows;
-    t.coop_nnz = std::min(fwd.coop_nnz, a.tile_nnz);
+    t.coop_nnz = std::min({fwd.coop_nnz, a.tile_nnz, kAdjCoopNnz});
     t.stages = a.stages;
     t.row_order = a.row_order;
     return t;
@@ -672,6 +672,10 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     A->host_row_ptr = std::move(rp);
     A->host_row_cmin = std::move(rcmin);
     A->host_row_cmax = std::move(rcmax);
+    // Too many columns for all of x in shared memory: the forward schedule gets
+    // column windows (a row block of a pencil beam touches a narrow band of
+    // spots) and the kernels stage each CTA's window of x.
+    A->fwd_windowed = ncols > kXSmemMaxCols;
     Tuning t;
     AdjTuning at;
     merge_tuning(t, at, tuning);
@@ -715,7 +719,15 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if ((e = cudaMalloc(&A->err, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     if ((e = cudaMemset(A->err, 0, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     {
-        dose_status st = apply_schedule(A.get(), A->fwd, t);
+        dose_status st = apply_schedule(A.get(), A->fwd, t, A->fwd_windowed);
+        // Default tiles shrink (down to 1024 entries) until the window of x fits
+        // beside the ring; past that the kernels gather x from global memory.
+        while (st == DOSE_OK && A->fwd_windowed && !(tuning && tuning->tile_nnz) && !spmv_x_in_smem(A.get(), t) &&
+               t.tile_nnz > 1024) {
+            t.tile_nnz /= 2;
+            if (!(tuning && tuning->coop_nnz)) t.coop_nnz = std::min(t.coop_nnz, t.tile_nnz);
+            st = apply_schedule(A.get(), A->fwd, t, A->fwd_windowed);
+        }
         if (st == DOSE_OK) st = apply_schedule(A.get(), A->adj, adj_schedule_tuning(t, at), true);
         // A wide column window (e.g. a multi-beam plan, whose rows span every
         // beam's spots) leaves few scatter warps beside 5120-entry tiles; the
@@ -951,6 +963,7 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
         out->adj_block_fused = 32 * (1 + sh.forward_warps + sh.scatter_warps);
     if (adjoint_shape(A, A->adj_tuning, false, &sh, nullptr)) out->adj_block_adjoint = 32 * (1 + sh.scatter_warps);
     out->adj_window = A->adj.wwidth;
+    out->fwd_window = A->fwd_windowed ? A->fwd.wwidth : 0;
     out->max_row_len = A->max_row_len;
     out->device_bytes = A->device_bytes;
     const uint64_t vb = value_bytes(A->fmt);
@@ -986,7 +999,7 @@ dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning) {
     if (st != DOSE_OK) return st;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "dose_set_tuning");
-    st = apply_schedule(A, A->fwd, t);
+    st = apply_schedule(A, A->fwd, t, A->fwd_windowed);
     if (st != DOSE_OK) return st;
     A->adj_tuning = at;
     return apply_schedule(A, A->adj, adj_schedule_tuning(t, at), true);
@@ -1052,7 +1065,7 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
                     t.lane_target = lt;
                     t.stages = sd;
                     if (check_tuning(A, t) != DOSE_OK) continue;
-                    if (apply_schedule(A, A->fwd, t) != DOSE_OK) continue;
+                    if (apply_schedule(A, A->fwd, t, A->fwd_windowed) != DOSE_OK) continue;
                     const float ms = time_launches(s, e0, e1, reps, [&] { return launch_spmv(A, x, d, s); });
                     if (ms < 0.f) {
                         result = cuda_fail(cudaGetLastError(), "dose_autotune forward timing");
@@ -1063,7 +1076,7 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
                         best_t = t;
                     }
                 }
-    if (result == DOSE_OK) result = apply_schedule(A, A->fwd, best_t);
+    if (result == DOSE_OK) result = apply_schedule(A, A->fwd, best_t, A->fwd_windowed);
 
     // 2. fused objective pass: adjoint tile sizes, depth, forward warps (scatter warps: all that fit)
     const AdjTuning orig_a = A->adj_tuning;

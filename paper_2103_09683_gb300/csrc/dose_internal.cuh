@@ -56,7 +56,7 @@ struct StageDesc {
 struct Tuning {
     uint32_t tile_nnz = 8192;
     uint32_t tile_rows = 2048;
-    uint32_t coop_nnz = 1024;
+    uint32_t coop_nnz = 8192;   // rows longer than this (longer than a tile) are reduced by the whole CTA
     uint32_t lane_target = 24;  // entries per lane: 4 per unrolled step, about 6 steps
     uint32_t stages = 3;
     uint32_t consumer_warps = 16;
@@ -138,6 +138,8 @@ struct dose_matrix {
     float* row_scale = nullptr;  // FP8 only
 
     dose::DevSchedule fwd;      // schedule of dose_spmv (and the batched SpMM)
+    bool fwd_windowed = false;  // ncols too many for all of x in shared memory: the forward schedule
+                                // has column windows and the kernels stage each CTA's window
     dose::DevSchedule adj;      // schedule of the adjoint / fused kernels
     dose::AdjTuning adj_tuning;
 
@@ -165,7 +167,10 @@ dose_status cuda_fail(cudaError_t e, const char* what);
 
 // Launchers (spmv_kernel.cu, spmv_f64_kernel.cu, adjoint_kernel.cu, batched_kernel.cu)
 size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem);
-bool spmv_x_in_smem(const dose_matrix* A);
+// Columns of x a forward CTA stages (all of x, or the schedule's window width).
+uint32_t spmv_x_cols(const dose_matrix* A);
+// Whether the forward kernel can stage its x (or window of x) beside the ring of tuning t.
+bool spmv_x_in_smem(const dose_matrix* A, const Tuning& t);
 cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s);
 size_t spmv_f64_smem_bytes(const dose_matrix* A, bool x_in_smem);
 // SELL-32-sigma (sell_kernel.cu): build from host CSR columns and encoded values, free, launch.
@@ -194,7 +199,8 @@ __host__ __device__ constexpr uint32_t value_bytes(int fmt) {
 }
 constexpr uint32_t kMaxAdjWarps = 20;      // producer + forward + scatter warps of the adjoint kernels
 constexpr uint32_t kSellDefaultSigma = 1u << 20;  // rows per sorting window of the SELL copy
-constexpr uint32_t kAdjMinScatterWarps = 8;  // below this the default adjoint tile shrinks to 4096 entries
+constexpr uint32_t kAdjMinScatterWarps = 8;
+constexpr uint32_t kAdjCoopNnz = 1024;  // the adjoint schedule reduces rows longer than this with the whole CTA  // below this the default adjoint tile shrinks to 4096 entries
 constexpr uint32_t kAdjColumnGroups = 16;  // column groups of the adjoint schedule (CTAs per group: grid / 16)
 constexpr uint32_t kXSmemMaxCols = 16384;  // x staged in shared memory up to 64 KB
 constexpr uint32_t kCompThreshold = 128;   // compensated accumulation above this row length

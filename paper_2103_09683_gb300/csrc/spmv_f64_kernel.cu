@@ -41,6 +41,7 @@ struct Spmv64Params {
     const uint2* x;   // ncols + 1 elements of 8 bytes, the last one zero: DF (hi, lo) pairs, DP doubles
     double* d;
     uint32_t nrows, ncols;
+    uint32_t xcols;  // columns of x staged per CTA (ncols, or the window width)
     ScheduleView sched;
     VecSet vecs;  // FP8: the row scales
     uint32_t tile_nnz, tile_rows, depth, cwarps, l2pf;
@@ -193,8 +194,8 @@ constexpr bool fmt_scaled(int fmt) { return fmt == DOSE_FMT_U16_SCALE || fmt == 
 template <int FMT, int MODE, uint32_t IW, uint32_t LG>
 __device__ __forceinline__ void normal_rows64(const Spmv64Params& p, const StageDesc& D, const SlotView& v,
                                               uint32_t slot, const SlotLayout& SL, const SlotPtrs<FMT, IW>& sp,
-                                              const uint2* xsp, uint32_t ctid, uint32_t lane, uint32_t nct,
-                                              uint32_t rotw) {
+                                              const uint2* xsp, uint32_t zc, uint32_t ctid, uint32_t lane,
+                                              uint32_t nct, uint32_t rotw) {
     constexpr uint32_t L = 1u << LG;
     const uint32_t gid = ctid >> LG, li = lane & (L - 1), G = nct >> LG;
     const uint32_t j0 = (gid + G - ((rotw << (5 - LG)) & (G - 1))) & (G - 1);
@@ -210,7 +211,7 @@ __device__ __forceinline__ void normal_rows64(const Spmv64Params& p, const Stage
         }
         const uint32_t span = re > rs ? re - (rs & ~3u) : 0;
         const uint32_t iters = __reduce_max_sync(0xffffffffu, (span + 4 * L - 1) / (4 * L));
-        Acc<MODE> a = dot_vec64<FMT, MODE, L, IW>(sp, xsp, p.ncols, rs, re, li, iters);
+        Acc<MODE> a = dot_vec64<FMT, MODE, L, IW>(sp, xsp, zc, rs, re, li, iters);
         for (uint32_t o = L >> 1; o > 0; o >>= 1) a.add(a.shfl_xor(o));
         if (has && li == 0) p.d[row] = a.result(fmt_scaled(FMT), row_scale<FMT>(p, slot, SL, D.row0, row));
     }
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(544, 1) spmv_f64_kernel(const Spmv64Params p) 
     uint2* red = reinterpret_cast<uint2*>(smem + 256);  // 32 x 8 bytes: CTA reduction
     StageDesc* dwin = reinterpret_cast<StageDesc*>(smem + 1024);
     uint2* xs = reinterpret_cast<uint2*>(smem + kHeaderBytes);
-    const uint32_t x_bytes = XSMEM ? round_up((p.ncols + 1) * 8, 128) : 0;
+    const uint32_t x_bytes = XSMEM ? round_up((p.xcols + 1) * 8, 128) : 0;
     unsigned char* slot_base = smem + kHeaderBytes + x_bytes;
     const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, ES, p.vecs.n, false, IW);
 
@@ -260,11 +261,16 @@ __global__ void __launch_bounds__(544, 1) spmv_f64_kernel(const Spmv64Params p) 
     const uint32_t cw = warp - 1;
     const uint32_t ctid = threadIdx.x - 32;
     const uint32_t nct = W * 32;
+    // x, or this CTA's window [wlo, wlo + xcols) of it, then a zero element,
+    // addressed by column through a pointer moved down by wlo elements
+    const uint32_t wlo = p.sched.wlo ? p.sched.wlo[blockIdx.x] : 0u;
     if (XSMEM) {
-        for (uint32_t j = ctid; j <= p.ncols; j += nct) xs[j] = __ldg(p.x + j);
+        for (uint32_t j = ctid; j <= p.xcols; j += nct)
+            xs[j] = (j < p.xcols && wlo + j < p.ncols) ? __ldg(p.x + wlo + j) : make_uint2(0u, 0u);
         dev::named_barrier(1, nct);
     }
-    const uint2* xsp = XSMEM ? xs : p.x;
+    const uint2* xsp = XSMEM ? xs - wlo : p.x;
+    const uint32_t zc = XSMEM ? wlo + p.xcols : p.ncols;  // the zero element's column
     const uint32_t slot0 = dev::smem_u32(slot_base);
     Acc<MODE> coop;
 
@@ -284,12 +290,12 @@ __global__ void __launch_bounds__(544, 1) spmv_f64_kernel(const Spmv64Params p) 
                 if (dev::lds_u32(v.rp + 4 * r) == dev::lds_u32(v.rp + 4 * r + 4)) p.d[r] = 0.0;
             const uint32_t rotw = s & (W - 1);
             switch (D.meta & STAGE_LANES_MASK) {
-                case 0: normal_rows64<FMT, MODE, IW, 0>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
-                case 1: normal_rows64<FMT, MODE, IW, 1>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
-                case 2: normal_rows64<FMT, MODE, IW, 2>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
-                case 3: normal_rows64<FMT, MODE, IW, 3>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
-                case 4: normal_rows64<FMT, MODE, IW, 4>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
-                default: normal_rows64<FMT, MODE, IW, 5>(p, D, v, slot, SL, sp, xsp, ctid, lane, nct, rotw); break;
+                case 0: normal_rows64<FMT, MODE, IW, 0>(p, D, v, slot, SL, sp, xsp, zc, ctid, lane, nct, rotw); break;
+                case 1: normal_rows64<FMT, MODE, IW, 1>(p, D, v, slot, SL, sp, xsp, zc, ctid, lane, nct, rotw); break;
+                case 2: normal_rows64<FMT, MODE, IW, 2>(p, D, v, slot, SL, sp, xsp, zc, ctid, lane, nct, rotw); break;
+                case 3: normal_rows64<FMT, MODE, IW, 3>(p, D, v, slot, SL, sp, xsp, zc, ctid, lane, nct, rotw); break;
+                case 4: normal_rows64<FMT, MODE, IW, 4>(p, D, v, slot, SL, sp, xsp, zc, ctid, lane, nct, rotw); break;
+                default: normal_rows64<FMT, MODE, IW, 5>(p, D, v, slot, SL, sp, xsp, zc, ctid, lane, nct, rotw); break;
             }
         } else {
             // one chunk of a long row: every consumer thread takes entries
@@ -350,10 +356,12 @@ size_t spmv_f64_smem_bytes(const dose_matrix* A, bool x_in_smem) {
     const uint32_t nvec = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
     const uint32_t iw = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, false, iw);
-    return kHeaderBytes + (x_in_smem ? round_up((A->ncols + 1) * 8, 128) : 0) + (size_t)t.stages * SL.bytes;
+    return kHeaderBytes + (x_in_smem ? round_up((spmv_x_cols(A) + 1) * 8, 128) : 0) + (size_t)t.stages * SL.bytes;
 }
 
-bool spmv_f64_x_in_smem(const dose_matrix* A) { return spmv_f64_smem_bytes(A, true) <= kMaxSmemPerBlock; }
+bool spmv_f64_x_in_smem(const dose_matrix* A) {
+    return spmv_x_cols(A) > 0 && spmv_f64_smem_bytes(A, true) <= kMaxSmemPerBlock;
+}
 
 cudaError_t launch_spmv_f64(const dose_matrix* A, const double* x, double* d, bool native, cudaStream_t s) {
     if (A->nrows == 0) return cudaSuccess;
@@ -374,7 +382,8 @@ cudaError_t launch_spmv_f64(const dose_matrix* A, const double* x, double* d, bo
     p.d = d;
     p.nrows = A->nrows;
     p.ncols = A->ncols;
-    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin, nullptr};
+    p.xcols = spmv_x_cols(A);
+    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin, A->fwd_windowed ? A->fwd.wlo : nullptr};
     p.vecs.n = 0;
     if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {
         p.vecs.n = 1;

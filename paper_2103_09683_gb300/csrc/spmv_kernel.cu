@@ -30,6 +30,7 @@ struct SpmvParams {
     const float* x;
     float* d;
     uint32_t nrows, ncols;
+    uint32_t xcols;  // columns of x staged per CTA (ncols, or the window width)
     ScheduleView sched;
     VecSet vecs;  // FP8: the row scales
     uint32_t tile_nnz, tile_rows, depth, cwarps, l2pf;
@@ -87,8 +88,8 @@ __device__ __forceinline__ void row_dot(const SlotView& v, uint32_t xs, const fl
 template <int FMT, bool COMP, bool XSMEM, uint32_t IW, uint32_t LG>
 __device__ __forceinline__ void normal_rows(const SpmvParams& p, const StageDesc& D, const SlotView& v,
                                             uint32_t slot, const SlotLayout& SL, uint32_t xs_a,
-                                            const SlotPtrs<FMT, IW>& sp, const float* xsp, uint32_t ctid,
-                                            uint32_t lane, uint32_t nct, uint32_t rotw) {
+                                            const SlotPtrs<FMT, IW>& sp, const float* xsp, uint32_t zc,
+                                            uint32_t ctid, uint32_t lane, uint32_t nct, uint32_t rotw) {
     constexpr uint32_t L = 1u << LG;
     const uint32_t gid = ctid >> LG, li = lane & (L - 1), G = nct >> LG;
     const uint32_t j0 = (gid + G - ((rotw << (5 - LG)) & (G - 1))) & (G - 1);
@@ -108,7 +109,7 @@ __device__ __forceinline__ void normal_rows(const SpmvParams& p, const StageDesc
             // one trip count for the whole warp: no divergent loop tails
             const uint32_t span = re > rs ? re - (rs & ~3u) : 0;
             const uint32_t iters = __reduce_max_sync(0xffffffffu, (span + 4 * L - 1) / (4 * L));
-            sum = dot_vec_p<FMT, L, IW>(sp, xsp, p.ncols, rs, re, li, iters);
+            sum = dot_vec_p<FMT, L, IW>(sp, xsp, zc, rs, re, li, iters);
         } else if (has) {
             if (COMP && re - rs > kCompThreshold)
                 dot_strided_comp<FMT, IW>(v, xs_a, p.x, XSMEM, rs + li, re, L, sum, comp);
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     float* red = reinterpret_cast<float*>(smem + 256);  // 64 floats: CTA reduction
     StageDesc* dwin = reinterpret_cast<StageDesc*>(smem + 1024);  // 2 x kDescWin descriptors
     float* xs = reinterpret_cast<float*>(smem + kHeaderBytes);
-    const uint32_t x_bytes = XSMEM ? round_up((p.ncols + 1) * 4, 128) : 0;  // x and one zero element
+    const uint32_t x_bytes = XSMEM ? round_up((p.xcols + 1) * 4, 128) : 0;  // x (window) and one zero element
     unsigned char* slot_base = smem + kHeaderBytes + x_bytes;
     const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, sizeof(T), p.vecs.n, false, IW);
 
@@ -163,11 +164,18 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
     const uint32_t cw = warp - 1;
     const uint32_t ctid = threadIdx.x - 32;
     const uint32_t nct = W * 32;
+    // x, or this CTA's window [wlo, wlo + xcols) of it, then a zero element; the
+    // base is moved down by wlo words, so shifted_base + column lands in place
+    // (shared addresses wrap mod 2^32; the generic pointer is only offset)
+    const uint32_t wlo = p.sched.wlo ? p.sched.wlo[blockIdx.x] : 0u;
     if (XSMEM) {
-        for (uint32_t j = ctid; j <= p.ncols; j += nct) xs[j] = j < p.ncols ? __ldg(p.x + j) : 0.f;
+        for (uint32_t j = ctid; j <= p.xcols; j += nct)
+            xs[j] = (j < p.xcols && wlo + j < p.ncols) ? __ldg(p.x + wlo + j) : 0.f;
         dev::named_barrier(1, nct);
     }
-    const uint32_t xs_a = dev::smem_u32(xs);
+    const uint32_t xs_a = dev::smem_u32(xs) - 4u * wlo;
+    const float* xsw = xs - wlo;
+    const uint32_t zc = wlo + p.xcols;  // the zero element's column
     const uint32_t slot0 = dev::smem_u32(slot_base);
     float coop_s = 0.f, coop_c = 0.f;
 
@@ -189,12 +197,12 @@ __global__ void __launch_bounds__(544, 1) spmv_kernel(const SpmvParams p) {
             // non-empty rows: groups of L lanes (L chosen per stage)
             const uint32_t rotw = s & (W - 1);
             switch (D.meta & STAGE_LANES_MASK) {
-                case 0: normal_rows<FMT, COMP, XSMEM, IW, 0>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
-                case 1: normal_rows<FMT, COMP, XSMEM, IW, 1>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
-                case 2: normal_rows<FMT, COMP, XSMEM, IW, 2>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
-                case 3: normal_rows<FMT, COMP, XSMEM, IW, 3>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
-                case 4: normal_rows<FMT, COMP, XSMEM, IW, 4>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
-                default: normal_rows<FMT, COMP, XSMEM, IW, 5>(p, D, v, slot, SL, xs_a, sp, xs, ctid, lane, nct, rotw); break;
+                case 0: normal_rows<FMT, COMP, XSMEM, IW, 0>(p, D, v, slot, SL, xs_a, sp, xsw, zc, ctid, lane, nct, rotw); break;
+                case 1: normal_rows<FMT, COMP, XSMEM, IW, 1>(p, D, v, slot, SL, xs_a, sp, xsw, zc, ctid, lane, nct, rotw); break;
+                case 2: normal_rows<FMT, COMP, XSMEM, IW, 2>(p, D, v, slot, SL, xs_a, sp, xsw, zc, ctid, lane, nct, rotw); break;
+                case 3: normal_rows<FMT, COMP, XSMEM, IW, 3>(p, D, v, slot, SL, xs_a, sp, xsw, zc, ctid, lane, nct, rotw); break;
+                case 4: normal_rows<FMT, COMP, XSMEM, IW, 4>(p, D, v, slot, SL, xs_a, sp, xsw, zc, ctid, lane, nct, rotw); break;
+                default: normal_rows<FMT, COMP, XSMEM, IW, 5>(p, D, v, slot, SL, xs_a, sp, xsw, zc, ctid, lane, nct, rotw); break;
             }
         } else {
             // one chunk of a long row, reduced by every consumer thread
@@ -262,14 +270,19 @@ cudaError_t launch_fmt(const dose_matrix* A, const SpmvParams& p, size_t smem, b
 
 }  // namespace
 
-bool spmv_x_in_smem(const dose_matrix* A) { return A->ncols <= kXSmemMaxCols; }
+uint32_t spmv_x_cols(const dose_matrix* A) { return A->fwd_windowed ? A->fwd.wwidth : A->ncols; }
+
+bool spmv_x_in_smem(const dose_matrix* A, const Tuning& t) {
+    if (!A->fwd_windowed) return A->ncols <= kXSmemMaxCols;
+    return A->fwd.wwidth > 0 && spmv_smem_bytes(A, t, true) <= kMaxSmemPerBlock;
+}
 
 size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem) {
     const uint32_t esize = value_bytes(A->fmt);
     const uint32_t nvec = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
     const uint32_t iw = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, false, iw);
-    return kHeaderBytes + (x_in_smem ? round_up((A->ncols + 1) * 4, 128) : 0) + (size_t)t.stages * SL.bytes;
+    return kHeaderBytes + (x_in_smem ? round_up((spmv_x_cols(A) + 1) * 4, 128) : 0) + (size_t)t.stages * SL.bytes;
 }
 
 cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s) {
@@ -284,7 +297,8 @@ cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStre
     p.d = d;
     p.nrows = A->nrows;
     p.ncols = A->ncols;
-    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin, nullptr};
+    p.xcols = spmv_x_cols(A);
+    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin, A->fwd_windowed ? A->fwd.wlo : nullptr};
     p.vecs.n = 0;
     if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {  // library-owned, padded: every row can be copied
         p.vecs.n = 1;
@@ -297,7 +311,7 @@ cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStre
     p.cwarps = A->fwd.tuning.consumer_warps;
     p.l2pf = A->fwd.tuning.l2_prefetch;
     p.err = A->err;
-    const bool xsmem = spmv_x_in_smem(A);
+    const bool xsmem = spmv_x_in_smem(A, A->fwd.tuning);
     const size_t smem = spmv_smem_bytes(A, A->fwd.tuning, xsmem);
     const bool comp = (A->flags & DOSE_CREATE_COMPENSATED) != 0;
     switch (A->fmt) {

@@ -163,6 +163,30 @@ def test_forward_sell_edge_cases(name):
             A.device_status()
 
 
+@pytest.mark.parametrize("fmt", ["u16", "f16"])
+def test_forward_column_windows_for_wide_matrices(fmt):
+    """20000 spots (more than shared memory holds as one x): the forward schedule
+    gets column windows and each CTA stages its window of x; FP32 and FP64
+    vectors against the oracle, and the same with a window too wide to stage."""
+    from dataclasses import replace
+    beam = replace(dosegen.TINY, grid=(24, 40, 8), lattice=(100, 200), spacing=(0.24, 0.2), sigma=2.0, tau=0.3)
+    csr = dosegen.generate(beam)
+    assert csr.ncols == 20000
+    for tuning in (None, dict(tile_nnz=1024, tile_rows=256, stages=2)):
+        A, enc = make(csr, fmt, tuning=tuning)
+        inf = A.info()
+        assert 0 < inf["fwd_window"] < csr.ncols
+        x = _x(csr.ncols, seed=12)
+        fwd_check(A.spmv(_to(x)).cpu().numpy(), oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x))
+        x64 = dosegen.spot_weights_f64(csr.ncols, 13)
+        d64 = A.spmv_f64(_to(x64)).cpu().numpy()
+        ref = oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x64)
+        absref = oracle.spmv(csr.nrows, enc.row_ptr, enc.col, np.abs(enc.decoded), x64)
+        nz = absref > 0
+        assert np.all(d64[~nz] == 0) and np.max(np.abs(d64[nz] - ref[nz]) / absref[nz]) <= 2.0 ** -40
+        A.device_status()
+
+
 def test_compensated_long_rows_adversarial():
     # descending magnitudes over 16000 entries: plain FP32 loses digits
     n = 16000
