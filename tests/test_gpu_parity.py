@@ -172,10 +172,14 @@ def test_forward_column_windows_for_wide_matrices(fmt):
     beam = replace(dosegen.TINY, grid=(24, 40, 8), lattice=(100, 200), spacing=(0.24, 0.2), sigma=2.0, tau=0.3)
     csr = dosegen.generate(beam)
     assert csr.ncols == 20000
-    for tuning in (None, dict(tile_nnz=1024, tile_rows=256, stages=2)):
+    # row blocks of 64 or 32 rows span ~3 voxel rows of y, so their windows are
+    # narrow; the default 2048-row blocks span the whole 40-voxel grid
+    for tuning in (None, dict(tile_nnz=2048, tile_rows=64), dict(tile_nnz=1024, tile_rows=32, stages=2)):
         A, enc = make(csr, fmt, tuning=tuning)
         inf = A.info()
-        assert 0 < inf["fwd_window"] < csr.ncols
+        assert 0 < inf["fwd_window"] <= csr.ncols
+        if tuning:
+            assert inf["fwd_window"] < csr.ncols // 2
         x = _x(csr.ncols, seed=12)
         fwd_check(A.spmv(_to(x)).cpu().numpy(), oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x))
         x64 = dosegen.spot_weights_f64(csr.ncols, 13)
