@@ -409,6 +409,7 @@ static void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
     if (in->adj_l2_prefetch) a.l2_prefetch = in->adj_l2_prefetch >= 32 ? 0 : in->adj_l2_prefetch;
     if (in->row_order) t.row_order = in->row_order;
     if (in->adj_row_order) a.row_order = in->adj_row_order;
+    if (!in->coop_nnz) t.coop_nnz = std::min(t.coop_nnz, t.tile_nnz);  // the default follows a smaller tile
 }
 
 static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out) {
