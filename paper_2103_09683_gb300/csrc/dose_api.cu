@@ -168,7 +168,7 @@ static uint32_t nearest_pow2_log2(double v) {
 }
 
 // Column windows: rcmin / rcmax give each row's lowest and highest column (null
-// for the forward schedule, which deals round-robin).  vbytes: stored bytes per
+// for a schedule without windows, which deals round-robin).  vbytes: stored bytes per
 // entry (value + column index), used to balance the CTAs' HBM traffic.
 static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, const Tuning& t, uint32_t grid,
                                const uint32_t* rcmin, const uint32_t* rcmax, uint32_t ncols, uint32_t vbytes) {
@@ -198,9 +198,19 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
         D.nz0 = rp[r];
         D.ne0 = (uint32_t)S.ne.size();
         uint64_t nz = 0;
+        uint32_t slo = 0xFFFFFFFFu, shi = 0;  // columns of the block's rows so far (windowed schedules)
         while (r < nrows && r - D.row0 < t.tile_rows) {
             const uint32_t l = rp[r + 1] - rp[r];
             if (l > t.coop_nnz || nz + l > t.tile_nnz) break;
+            if (rcmin && l) {
+                // A block whose column range would more than double with this row
+                // (the voxel order wrapping to the far side of the beam) ends
+                // here: one wide block would widen every CTA's window.
+                const uint32_t nlo = std::min(slo, rcmin[r]), nhi = std::max(shi, rcmax[r]);
+                if (slo <= shi && nhi - nlo > 2 * std::max(shi - slo, rcmax[r] - rcmin[r]) + 64) break;
+                slo = nlo;
+                shi = nhi;
+            }
             nz += l;
             if (l) S.ne.push_back((uint16_t)(r - D.row0));
             ++r;
