@@ -348,6 +348,7 @@ static void free_dev_schedule(DevSchedule& D) {
 
 static void free_all(dose_matrix* A) {
     free_dev_schedule(A->fwd);
+    free_dev_schedule(A->fwd64);
     free_dev_schedule(A->adj);
     cudaFree(A->row_ptr);
     cudaFree(A->col);
@@ -730,6 +731,7 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if ((e = cudaMalloc(&A->err, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     if ((e = cudaMemset(A->err, 0, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     {
+        const Tuning t_full = t;
         dose_status st = apply_schedule(A.get(), A->fwd, t, A->fwd_windowed);
         // Default tiles shrink (down to 1024 entries) until the window of x fits
         // beside the ring; past that the kernels gather x from global memory.
@@ -740,6 +742,13 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
             st = apply_schedule(A.get(), A->fwd, t, A->fwd_windowed);
         }
         if (st == DOSE_OK) st = apply_schedule(A.get(), A->adj, adj_schedule_tuning(t, at), true);
+        // dose_spmv_f64 stages 8 bytes per column: if even that window does not
+        // fit, it reads x from L2 and gets its own schedule with the full tiles.
+        if (st == DOSE_OK && A->fwd_windowed && !spmv_f64_x_in_smem(A.get())) {
+            A->fwd64.grid = A->fwd.grid;
+            A->fwd64_own = true;
+            st = apply_schedule(A.get(), A->fwd64, t_full, false);
+        }
         // A wide column window (e.g. a multi-beam plan, whose rows span every
         // beam's spots) leaves few scatter warps beside 5120-entry tiles; the
         // default then takes 4096-entry tiles (measured on a three-beam plan with
@@ -769,7 +778,7 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     A->device_bytes = A->sell.bytes + rp_alloc * 4 + col_alloc * 4 + ((flags & DOSE_CREATE_U16_INDEX) ? col16_alloc * 2 : 0) + val_alloc +
                       (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) + x64_alloc * 8 +
                       (size_t)A->adj.grid * ncols_pad * 4 + (size_t)A->adj.grid * 8 + 4 + schedule_bytes(A->fwd) +
-                      schedule_bytes(A->adj);
+                      schedule_bytes(A->adj) + (A->fwd64_own ? schedule_bytes(A->fwd64) : 0);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "create");
     *out = A.release();
     return DOSE_OK;
@@ -1011,6 +1020,7 @@ dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "dose_set_tuning");
     st = apply_schedule(A, A->fwd, t, A->fwd_windowed);
+    if (st == DOSE_OK && A->fwd64_own) st = apply_schedule(A, A->fwd64, t, false);
     if (st != DOSE_OK) return st;
     A->adj_tuning = at;
     return apply_schedule(A, A->adj, adj_schedule_tuning(t, at), true);

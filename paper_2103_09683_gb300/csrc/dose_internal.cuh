@@ -140,6 +140,8 @@ struct dose_matrix {
     dose::DevSchedule fwd;      // schedule of dose_spmv (and the batched SpMM)
     bool fwd_windowed = false;  // ncols too many for all of x in shared memory: the forward schedule
                                 // has column windows and the kernels stage each CTA's window
+    dose::DevSchedule fwd64;    // dose_spmv_f64's own schedule when its 8-byte window of x would not
+    bool fwd64_own = false;     // fit (x then comes from L2 and full tiles pay more than windows)
     dose::DevSchedule adj;      // schedule of the adjoint / fused kernels
     dose::AdjTuning adj_tuning;
 

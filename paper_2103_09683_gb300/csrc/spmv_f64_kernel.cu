@@ -330,7 +330,7 @@ cudaError_t launch_t(const dose_matrix* A, const Spmv64Params& p, size_t smem, c
     auto k = spmv_f64_kernel<FMT, MODE, XSMEM, IW>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<A->fwd.grid, 32 * (p.cwarps + 1), smem, s>>>(p);
+    k<<<(A->fwd64_own ? A->fwd64 : A->fwd).grid, 32 * (p.cwarps + 1), smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -350,16 +350,21 @@ cudaError_t launch_fmt(const dose_matrix* A, const Spmv64Params& p, size_t smem,
 
 }  // namespace
 
+// The schedule dose_spmv_f64 runs on.
+static const DevSchedule& f64_schedule(const dose_matrix* A) { return A->fwd64_own ? A->fwd64 : A->fwd; }
+
 size_t spmv_f64_smem_bytes(const dose_matrix* A, bool x_in_smem) {
-    const Tuning& t = A->fwd.tuning;
+    const Tuning& t = f64_schedule(A).tuning;
     const uint32_t esize = value_bytes(A->fmt);
     const uint32_t nvec = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
     const uint32_t iw = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, false, iw);
-    return kHeaderBytes + (x_in_smem ? round_up((spmv_x_cols(A) + 1) * 8, 128) : 0) + (size_t)t.stages * SL.bytes;
+    const uint32_t xcols = A->fwd64_own ? A->ncols : spmv_x_cols(A);
+    return kHeaderBytes + (x_in_smem ? round_up((xcols + 1) * 8, 128) : 0) + (size_t)t.stages * SL.bytes;
 }
 
 bool spmv_f64_x_in_smem(const dose_matrix* A) {
+    if (A->fwd64_own) return false;
     return spmv_x_cols(A) > 0 && spmv_f64_smem_bytes(A, true) <= kMaxSmemPerBlock;
 }
 
@@ -382,19 +387,21 @@ cudaError_t launch_spmv_f64(const dose_matrix* A, const double* x, double* d, bo
     p.d = d;
     p.nrows = A->nrows;
     p.ncols = A->ncols;
-    p.xcols = spmv_x_cols(A);
-    p.sched = ScheduleView{A->fwd.desc, A->fwd.ne, A->fwd.cta_begin, A->fwd_windowed ? A->fwd.wlo : nullptr};
+    const DevSchedule& F = f64_schedule(A);
+    const bool win = A->fwd_windowed && !A->fwd64_own;
+    p.xcols = win ? A->fwd.wwidth : A->ncols;
+    p.sched = ScheduleView{F.desc, F.ne, F.cta_begin, win ? F.wlo : nullptr};
     p.vecs.n = 0;
     if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {
         p.vecs.n = 1;
         p.vecs.ptr[0] = A->row_scale;
         p.vecs.lim[0] = round_up(A->nrows, 4);
     }
-    p.tile_nnz = A->fwd.tuning.tile_nnz;
-    p.tile_rows = A->fwd.tuning.tile_rows;
-    p.depth = A->fwd.tuning.stages;
-    p.cwarps = A->fwd.tuning.consumer_warps;
-    p.l2pf = A->fwd.tuning.l2_prefetch;
+    p.tile_nnz = F.tuning.tile_nnz;
+    p.tile_rows = F.tuning.tile_rows;
+    p.depth = F.tuning.stages;
+    p.cwarps = F.tuning.consumer_warps;
+    p.l2pf = F.tuning.l2_prefetch;
     p.err = A->err;
     const bool xsmem = spmv_f64_x_in_smem(A);
     const size_t smem = spmv_f64_smem_bytes(A, xsmem);
