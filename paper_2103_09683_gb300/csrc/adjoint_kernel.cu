@@ -53,8 +53,7 @@ __device__ __forceinline__ float finish_dot(const AdjParams& p, float rs, float 
 }
 
 // gw[col_k] += a_k * rj for the entries k = kb, kb + step, ... < ke of one row
-// (gw: shared address of a warp's accumulator, column c at gw + 4 pad_col(c)).
-// The columns of a row are
+// (gw: shared address of a warp's accumulator).  The columns of a row are
 // distinct, so the four loads may precede the four stores.
 template <int FMT>
 __device__ __forceinline__ void scatter_entries(uint32_t gw, const SlotView& v, uint32_t kb, uint32_t ke,
@@ -68,7 +67,7 @@ __device__ __forceinline__ void scatter_entries(uint32_t gw, const SlotView& v, 
         for (int u = 0; u < 4; ++u) {
             const uint32_t k = k0 + step * u;
             ok[u] = k < ke;
-            ga[u] = gw + 4 * pad_col(ok[u] ? dev::lds_u32(v.col + 4 * k) : 0u);
+            ga[u] = gw + 4 * (ok[u] ? dev::lds_u32(v.col + 4 * k) : 0u);
             a[u] = ok[u] ? Fmt<FMT>::lds(v.val + ES * k) : 0.f;
         }
 #pragma unroll
@@ -161,7 +160,7 @@ __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D,
         }
         const uint32_t span = re > rs ? re - (rs & ~3u) : 0;
         const uint32_t iters = __reduce_max_sync(0xffffffffu, (span + 4 * L - 1) / (4 * L));
-        float sum = dot_vec_p<FMT, L, 4, true>(sp, xsp, zc, rs, re, li, iters);
+        float sum = dot_vec_p<FMT, L, 4>(sp, xsp, zc, rs, re, li, iters);
 #pragma unroll
         for (uint32_t off = L >> 1; off > 0; off >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, off));
         if (has && li == 0) {
@@ -192,18 +191,14 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
     StageDesc* dwin = reinterpret_cast<StageDesc*>(smem + 1024);  // 2 x kDescWin descriptors
     float* red = reinterpret_cast<float*>(smem + 256);      // 32 floats: long-row partials
     double* fred = reinterpret_cast<double*>(smem + 512);   // 32 doubles: per-warp objective
-    // This CTA's entries have columns in [wlo, wlo + wwidth) (wlo and wwidth
-    // multiples of 32): the accumulators and x hold that window with one pad
-    // word per 32 columns (pad_col: column c at word pad_col(c - wlo), which is
-    // pad_col(c) - pad_col(wlo)), addressed through a base moved down by
-    // pad_col(wlo) words (shared addresses wrap mod 2^32, so base + 4 pad_col(c)
-    // lands in place).
+    // This CTA's entries have columns in [wlo, wlo + wwidth): the accumulators
+    // and x hold that window, addressed by column through a base moved down by
+    // wlo words (shared addresses wrap mod 2^32, so base + 4 c lands in place).
     const uint32_t wlo = p.sched.wlo[blockIdx.x];
-    const uint32_t wpad = pad_col(p.wwidth), plo = pad_col(wlo);  // padded window width, shift
-    const uint32_t gw_floats = round_up(wpad * 4, 128) / 4;
+    const uint32_t gw_floats = round_up(p.wwidth * 4, 128) / 4;
     float* gacc = reinterpret_cast<float*>(smem + kAdjHeader);  // Ws x gw_floats
     float* xs = gacc + Ws * gw_floats;
-    const uint32_t x_bytes = QUAD ? round_up((wpad + 1) * 4, 128) : 0;  // the window of x and a zero
+    const uint32_t x_bytes = QUAD ? round_up((p.wwidth + 1) * 4, 128) : 0;  // the window of x and a zero
     unsigned char* slot_base = reinterpret_cast<unsigned char*>(xs) + x_bytes;
     const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, sizeof(T), p.vecs.n, QUAD);
 
@@ -232,12 +227,12 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
 
     const uint32_t ctid = threadIdx.x - 32;
     for (uint32_t j = ctid; j < Ws * gw_floats; j += ncons) gacc[j] = 0.f;
-    if (QUAD)  // column wlo + j at word pad_col(j); j = wwidth is the zero element (word wpad)
+    if (QUAD)
         for (uint32_t j = ctid; j <= p.wwidth; j += ncons)
-            xs[pad_col(j)] = j < p.wwidth && wlo + j < p.ncols ? __ldg(p.x + wlo + j) : 0.f;
+            xs[j] = j < p.wwidth && wlo + j < p.ncols ? __ldg(p.x + wlo + j) : 0.f;
     dev::named_barrier(1, ncons);
 
-    const uint32_t xs_a = dev::smem_u32(xs) - 4 * plo;
+    const uint32_t xs_a = dev::smem_u32(xs) - 4 * wlo;
     const uint32_t slot0 = dev::smem_u32(slot_base);
     const bool is_fwd = QUAD && warp <= Wf;
     bool failed = false;
@@ -246,8 +241,8 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
     if (is_fwd) {
         // ------------------------------------------------ forward warps
         const uint32_t fw = warp - 1, ftid = fw * 32 + lane, nft = Wf * 32;  // Wf is a power of two
-        const float* xsp = xs - plo;               // x of column c at xsp[pad_col(c)]
-        const uint32_t zc = pad_col(wlo + p.wwidth);  // the zero element after the window
+        const float* xsp = xs - wlo;         // x of column c at xsp[c] (c in this CTA's window)
+        const uint32_t zc = wlo + p.wwidth;  // the zero element after the window
         float coop_s = 0.f;
         uint32_t st = 0, ph = 0;
         for (uint32_t s = s_begin; s < s_end; ++s) {
@@ -282,7 +277,7 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
             } else {
                 // one chunk of a long row: every forward thread takes part
                 if (D.meta & STAGE_FIRST) coop_s = 0.f;
-                coop_s = __fadd_rn(coop_s, dot_strided<FMT, 4, true>(v, xs_a, D.nz0 + ftid, D.nz1, nft));
+                coop_s = __fadd_rn(coop_s, dot_strided<FMT>(v, xs_a, D.nz0 + ftid, D.nz1, nft));
                 if (D.meta & STAGE_LAST) {
                     float sum = coop_s;
                     for (uint32_t off = 16; off > 0; off >>= 1)
@@ -315,7 +310,7 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
     } else {
         // ------------------------------------------------ scatter warps
         const uint32_t sw = warp - 1 - Wf;
-        const uint32_t gw = dev::smem_u32(gacc + sw * gw_floats) - 4 * plo;
+        const uint32_t gw = dev::smem_u32(gacc + sw * gw_floats) - 4 * wlo;
         uint32_t st = 0, ph = 0, first = sw;  // first list entry of this warp, rotating per stage
         for (uint32_t s = s_begin; s < s_end; ++s, first = first + 1 == Ws ? 0 : first + 1) {
             if (!dev::mbar_wait_bounded(&full[st], ph) || (QUAD && !dev::mbar_wait_bounded(&fwd_done[st], ph))) {
@@ -335,7 +330,7 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
                     const uint32_t kb = __ldg(p.row_ptr + D.row0), ke = __ldg(p.row_ptr + D.row0 + 1);
                     const T* vg = static_cast<const T*>(p.val);
                     for (uint32_t k = kb + sw * 32 + lane; k < ke; k += Ws * 32) {
-                        const uint32_t ga = gw + 4 * pad_col(__ldg(p.col + k));
+                        const uint32_t ga = gw + 4 * __ldg(p.col + k);
                         dev::sts_f32(ga, __fmaf_rn(Fmt<FMT>::dec(vg[k]), rj, dev::lds_f32(ga)));
                     }
                 }
@@ -365,9 +360,8 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
     }
     dev::named_barrier(1, ncons);
     for (uint32_t j = ctid; j < p.wwidth; j += ncons) {
-        const uint32_t q = pad_col(j);
-        float t = gacc[q];
-        for (uint32_t w2 = 1; w2 < Ws; ++w2) t = __fadd_rn(t, gacc[w2 * gw_floats + q]);
+        float t = gacc[j];
+        for (uint32_t w2 = 1; w2 < Ws; ++w2) t = __fadd_rn(t, gacc[w2 * gw_floats + j]);
         p.g_part[(size_t)blockIdx.x * p.wwidth + j] = t;
     }
     if (ctid == 0) {
@@ -434,9 +428,8 @@ size_t adj_smem(const dose_matrix* A, const AdjTuning& t, bool quad, uint32_t ws
     const uint32_t esize = value_bytes(A->fmt);
     const uint32_t nvec = (quad ? 2 : 1) + (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, quad);
-    const uint32_t wpad = A->adj.wwidth + A->adj.wwidth / 32;  // one pad word per 32 columns
-    const size_t col_bytes = round_up(wpad * 4, 128);
-    const size_t x_bytes = quad ? round_up((wpad + 1) * 4, 128) : 0;  // the window of x and a zero
+    const size_t col_bytes = round_up(A->adj.wwidth * 4, 128);
+    const size_t x_bytes = quad ? round_up((A->adj.wwidth + 1) * 4, 128) : 0;  // the window of x and a zero
     return kAdjHeader + ws * col_bytes + x_bytes + (size_t)t.stages * SL.bytes;
 }
 

@@ -312,13 +312,11 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
             for (uint32_t i : mine[k])
                 for (uint32_t d = items[i].s; d < items[i].e; ++d) per[k].push_back(d);
         }
-        // windows start on a multiple of 32 columns (the kernels pad their
-        // windows with one word per 32 columns, relative to the start)
         uint32_t width = 0;
         for (uint32_t k = 0; k < grid; ++k)
-            if (lo[k] <= hi[k]) width = std::max(width, hi[k] - (lo[k] & ~31u) + 1);
+            if (lo[k] <= hi[k]) width = std::max(width, hi[k] - lo[k] + 1);
         S.wwidth = std::max<uint32_t>(32, std::min(ncols_pad, (width + 31) / 32 * 32));
-        for (uint32_t k = 0; k < grid; ++k) S.wlo[k] = lo[k] <= hi[k] ? (lo[k] & ~31u) : 0;
+        for (uint32_t k = 0; k < grid; ++k) S.wlo[k] = lo[k] <= hi[k] ? lo[k] : 0;
     }
     // Store the descriptors CTA by CTA, so each CTA reads one contiguous range.
     std::vector<StageDesc> sorted;

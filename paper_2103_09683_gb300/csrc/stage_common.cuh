@@ -533,24 +533,21 @@ __device__ __forceinline__ void dot_group(int off, int len, uint32_t xs, const u
           "f"(a[2]), "f"(a[3]));
 }
 
-// g[c[u]] += a[u] * r for the group's entries inside the row; g of column c
-// at shared address gw + 4 * pad_col(c).  The columns of a row are distinct, so
-// the four loads may precede the four stores, and no two lanes of the warp
-// touch one word.
+// g[c[u]] += a[u] * r for the group's entries inside the row; g at shared
+// address gw + 4 * column.  The columns of a row are distinct, so the four
+// loads may precede the four stores, and no two lanes of the warp touch one
+// word.
 __device__ __forceinline__ void scatter_group(int off, int len, uint32_t gw, const uint32_t (&c)[4],
                                               const float (&a)[4], float r) {
     asm volatile(
-        "{\n\t.reg .pred p0, p1, p2, p3;\n\t.reg .b32 t1, t2, t3, g0, g1, g2, g3, h0, h1, h2, h3;\n\t"
+        "{\n\t.reg .pred p0, p1, p2, p3;\n\t.reg .b32 t1, t2, t3, g0, g1, g2, g3;\n\t"
         ".reg .f32 v0, v1, v2, v3;\n\t"
         "setp.lt.u32 p0, %0, %1;\n\t"
         "add.s32 t1, %0, 1;\n\tsetp.lt.u32 p1, t1, %1;\n\t"
         "add.s32 t2, %0, 2;\n\tsetp.lt.u32 p2, t2, %1;\n\t"
         "add.s32 t3, %0, 3;\n\tsetp.lt.u32 p3, t3, %1;\n\t"
-        // padded positions c + (c >> 5) (pad_col)
-        "shr.u32 h0, %3, 5;\n\tshr.u32 h1, %4, 5;\n\tshr.u32 h2, %5, 5;\n\tshr.u32 h3, %6, 5;\n\t"
-        "add.u32 h0, h0, %3;\n\tadd.u32 h1, h1, %4;\n\tadd.u32 h2, h2, %5;\n\tadd.u32 h3, h3, %6;\n\t"
-        "mad.lo.u32 g0, h0, 4, %2;\n\tmad.lo.u32 g1, h1, 4, %2;\n\t"
-        "mad.lo.u32 g2, h2, 4, %2;\n\tmad.lo.u32 g3, h3, 4, %2;\n\t"
+        "mad.lo.u32 g0, %3, 4, %2;\n\tmad.lo.u32 g1, %4, 4, %2;\n\t"
+        "mad.lo.u32 g2, %5, 4, %2;\n\tmad.lo.u32 g3, %6, 4, %2;\n\t"
         "@p0 ld.shared.f32 v0, [g0];\n\t@p1 ld.shared.f32 v1, [g1];\n\t"
         "@p2 ld.shared.f32 v2, [g2];\n\t@p3 ld.shared.f32 v3, [g3];\n\t"
         "@p0 fma.rn.f32 v0, %7, %11, v0;\n\t@p1 fma.rn.f32 v1, %8, %11, v1;\n\t"
@@ -561,12 +558,6 @@ __device__ __forceinline__ void scatter_group(int off, int len, uint32_t gw, con
           "f"(a[2]), "f"(a[3]), "f"(r)
         : "memory");
 }
-
-// Padded position of column c in a column window whose first column is a
-// multiple of 32: one unused word after every 32 columns, so the 32 lanes of a
-// warp reading columns 4 apart (a row's consecutive spots, four entries per
-// lane) fall in 32 different shared-memory banks instead of 8.
-__device__ __forceinline__ uint32_t pad_col(uint32_t c) { return c + (c >> 5); }
 
 // Plain typed pointers to a slot's column indices and values, indexed by the
 // global entry index (the slot holds [nz0 & ~(16/IW - 1), ...) and
@@ -594,7 +585,7 @@ __device__ __forceinline__ SlotPtrs<FMT, IW> slot_ptrs(const unsigned char* slot
 // with weight 0, so it adds exactly nothing.  Plain typed shared-memory loads
 // (the slot's data were released by an mbarrier wait, a compiler barrier), so
 // the compiler may overlap steps.
-template <int FMT, uint32_t L, uint32_t IW, bool PADX = false>
+template <int FMT, uint32_t L, uint32_t IW>
 __device__ __forceinline__ float dot_vec_p(const SlotPtrs<FMT, IW>& sp, const float* __restrict__ xsp, uint32_t zc,
                                            uint32_t kb, uint32_t ke, uint32_t li, uint32_t iters) {
     using T = typename Fmt<FMT>::T;
@@ -618,18 +609,16 @@ __device__ __forceinline__ float dot_vec_p(const SlotPtrs<FMT, IW>& sp, const fl
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const bool m = (uint32_t)(off + u) < (uint32_t)len;
-            acc[u] = __fmaf_rn(m ? a[u] : 0.f, xsp[m ? (PADX ? pad_col(c[u]) : c[u]) : zc], acc[u]);
+            acc[u] = __fmaf_rn(m ? a[u] : 0.f, xsp[m ? c[u] : zc], acc[u]);
         }
     }
     return __fadd_rn(__fadd_rn(acc[0], acc[1]), __fadd_rn(acc[2], acc[3]));
 }
 
-// Same with a run-time stride (the whole-CTA reduction of long rows); PADX:
-// x of column c at xs + 4 * pad_col(c).
-template <int FMT, uint32_t IW = 4, bool PADX = false>
+// Same with a run-time stride (the whole-CTA reduction of long rows).
+template <int FMT, uint32_t IW = 4>
 __device__ __forceinline__ float dot_strided(const SlotView& v, uint32_t xs, uint32_t kb, uint32_t ke,
                                              uint32_t step) {
-    auto xi = [](uint32_t c) { return PADX ? c + (c >> 5) : c; };
     constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     uint32_t k = kb;
@@ -639,16 +628,16 @@ __device__ __forceinline__ float dot_strided(const SlotView& v, uint32_t xs, uin
         const uint32_t c2 = col_at<IW>(v, k2), c3 = col_at<IW>(v, k3);
         const float w0 = Fmt<FMT>::lds(v.val + ES * k), w1 = Fmt<FMT>::lds(v.val + ES * k1);
         const float w2 = Fmt<FMT>::lds(v.val + ES * k2), w3 = Fmt<FMT>::lds(v.val + ES * k3);
-        a0 = __fmaf_rn(w0, dev::lds_f32(xs + 4 * xi(c0)), a0);
-        a1 = __fmaf_rn(w1, dev::lds_f32(xs + 4 * xi(c1)), a1);
-        a2 = __fmaf_rn(w2, dev::lds_f32(xs + 4 * xi(c2)), a2);
-        a3 = __fmaf_rn(w3, dev::lds_f32(xs + 4 * xi(c3)), a3);
+        a0 = __fmaf_rn(w0, dev::lds_f32(xs + 4 * c0), a0);
+        a1 = __fmaf_rn(w1, dev::lds_f32(xs + 4 * c1), a1);
+        a2 = __fmaf_rn(w2, dev::lds_f32(xs + 4 * c2), a2);
+        a3 = __fmaf_rn(w3, dev::lds_f32(xs + 4 * c3), a3);
     }
-    if (k < ke) a0 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * xi(col_at<IW>(v, k))), a0);
+    if (k < ke) a0 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * col_at<IW>(v, k)), a0);
     k += step;
-    if (k < ke) a1 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * xi(col_at<IW>(v, k))), a1);
+    if (k < ke) a1 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * col_at<IW>(v, k)), a1);
     k += step;
-    if (k < ke) a2 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * xi(col_at<IW>(v, k))), a2);
+    if (k < ke) a2 = __fmaf_rn(Fmt<FMT>::lds(v.val + ES * k), dev::lds_f32(xs + 4 * col_at<IW>(v, k)), a2);
     return __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
 }
 
