@@ -142,3 +142,38 @@ def test_batched_27_scenarios_16_vectors_sampled_rows():
         fwd_check(D[torch.from_numpy(rows).cuda()].cpu().numpy().reshape(-1), ref.reshape(-1))
     for A in handles:
         A.device_status()
+
+
+def test_liver1_shaped_dose_sampled_rows():
+    """The paper's own matrix shape (Table I, liver beam 1: 2.97e6 x 6.8e4,
+    1.48e9 entries; bench.py --workload liver1): x does not fit in shared memory,
+    so the forward kernels stage column windows (FP32) or read x from L2
+    (Half/double).  FP32 dose and the Half/double dose on sampled rows against
+    the oracle."""
+    beam = dosegen.LIVER1_SHAPED
+    csr = dosegen.generate(beam)
+    rp = csr.row_ptr.astype(np.int64)
+    rows = _sample_rows(csr.nrows, csr.row_ptr, 2000, 5)
+    lens = rp[rows + 1] - rp[rows]
+    sub_rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=sub_rp[1:])
+    take = np.repeat(rp[rows] - sub_rp[:-1], lens) + np.arange(int(sub_rp[-1]))
+    sub = dosegen.CSR(len(rows), csr.ncols, sub_rp.astype(np.uint32), csr.col[take], csr.val[take])
+    A = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="f16", values_f64=csr.val)
+    nrows, ncols = csr.nrows, csr.ncols
+    empty = np.nonzero(np.diff(rp) == 0)[0]
+    del csr, take
+    assert 0 < A.info()["fwd_window"] < ncols
+    enc = oracle.encode(sub, oracle.F16)   # elementwise: the same codes the library stores
+    x = dosegen.spot_weights(ncols, dosegen.weight_seed(beam))
+    d = A.spmv(_to(x)).cpu().numpy()
+    fwd_check(d[rows], oracle.spmv(len(rows), enc.row_ptr, enc.col, enc.decoded, x))
+    assert np.all(d[empty] == 0)
+    x64 = dosegen.spot_weights_f64(ncols, dosegen.weight_seed(beam))
+    d64 = A.spmv_f64(_to(x64)).cpu().numpy()[rows]
+    ref = oracle.spmv(len(rows), enc.row_ptr, enc.col, enc.decoded, x64)
+    absref = oracle.spmv(len(rows), enc.row_ptr, enc.col, np.abs(enc.decoded), x64)
+    nz = absref > 0
+    assert np.all(d64[~nz] == 0) and np.max(np.abs(d64[nz] - ref[nz]) / absref[nz]) <= 2.0 ** -40
+    A.device_status()
+    A.close()
