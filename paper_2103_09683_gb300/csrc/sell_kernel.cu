@@ -64,16 +64,6 @@ __global__ void __launch_bounds__(kSellWarps * 32) sell_spmv_kernel(const SellPa
     const uint32_t nwarps = gridDim.x * kSellWarps;
     for (uint32_t c = blockIdx.x * kSellWarps + (threadIdx.x >> 5); c < p.nchunks; c += nwarps) {
         const uint2 ch = __ldg(p.chunk + c);
-        // ask L2 for this warp's next chunk (contiguous values and indices)
-        // while this one is summed: the plain loads then wait on L2, not HBM
-        if (lane == 0 && c + nwarps < p.nchunks) {
-            const uint2 nx = __ldg(p.chunk + c + nwarps);
-            if (nx.y) {  // at most the first 512 groups (64 KB of a chunk of 32-bit indices)
-                const uint32_t ngp = min(nx.y, 512u);
-                dev::bulk_prefetch_l2(static_cast<const T*>(p.val) + (size_t)nx.x * 128, ngp * 128 * (uint32_t)sizeof(T));
-                dev::bulk_prefetch_l2(static_cast<const unsigned char*>(p.col) + (size_t)nx.x * 128 * IW, ngp * 128 * IW);
-            }
-        }
         const size_t base = (size_t)ch.x * 128 + 4 * lane;
         const T* vp = static_cast<const T*>(p.val) + base;
         const unsigned char* cp = static_cast<const unsigned char*>(p.col) + base * IW;
