@@ -765,14 +765,9 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
             return st;
         }
     }
-    if ((flags & DOSE_CREATE_SELL) && !sell_fits(A.get())) {
-        free_all(A.get());
-        return invalid("DOSE_CREATE_SELL: the SELL ring of this tuning does not fit in shared memory");
-    }
     if (flags & DOSE_CREATE_SELL) {
         std::string why;
-        if ((e = build_sell(A.get(), col, vals.data(), scl.empty() ? nullptr : scl.data(), sell_sigma, &why)) !=
-            cudaSuccess) {
+        if ((e = build_sell(A.get(), col, vals.data(), sell_sigma, &why)) != cudaSuccess) {
             if (!why.empty()) {
                 free_all(A.get());
                 return invalid(why);
@@ -1000,7 +995,7 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     if (A->flags & DOSE_CREATE_SELL) {
         // padded entries, one perm word per chunk slot, 8 bytes per chunk descriptor
         out->sell_entries = A->sell.entries;
-        out->spmv_bytes = (vb + ib) * A->sell.entries + 4ull * 32 * A->sell.nchunks + 2ull * A->sell.nchunks + rs +
+        out->spmv_bytes = (vb + ib) * A->sell.entries + 4ull * 32 * A->sell.nchunks + 8ull * A->sell.nchunks + rs +
                           4 * nr + 4 * nc;
     }
     out->adjoint_bytes = (vb + 4) * nz + 4 * (nr + 1) + rs + 4 * nr + 4 * nc;

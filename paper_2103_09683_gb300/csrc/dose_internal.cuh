@@ -64,19 +64,15 @@ struct Tuning {
     uint32_t row_order = 2;     // non-empty rows of a stage: 1 = matrix order, 2 = most 4-entry groups first
 };
 
-// SELL-32-sigma copy of a matrix for the forward SpMV (DOSE_CREATE_SELL), with
-// its stage schedule (consecutive chunks per stage, dealt round-robin).
+// SELL-32-sigma copy of a matrix for the forward SpMV (DOSE_CREATE_SELL).
 struct SellArrays {
-    void* val = nullptr;           // stored values in SELL order
-    void* col = nullptr;           // column indices (4 or 2 bytes) in SELL order
-    uint32_t* perm = nullptr;      // original row of each chunk slot (~0: none), padded
-    uint16_t* choff = nullptr;     // per chunk: first group relative to its stage's first entry
-    StageDesc* desc = nullptr;     // stages, CTA by CTA
-    uint32_t* cta_begin = nullptr; // grid + 1
-    float* scale_perm = nullptr;   // FP8: row scale of each slot
-    uint32_t nchunks = 0, nslots = 0, n_stages = 0, grid = 0, sigma = 0;
-    uint64_t entries = 0;          // stored entries including padding
-    uint64_t bytes = 0;            // device bytes of the arrays above
+    void* val = nullptr;      // stored values in SELL order
+    void* col = nullptr;      // column indices (4 or 2 bytes) in SELL order
+    uint2* chunk = nullptr;   // per chunk: first entry / 128, groups of four entries
+    uint32_t* perm = nullptr; // original row of each chunk slot (~0: none)
+    uint32_t nchunks = 0, sigma = 0;
+    uint64_t entries = 0;     // stored entries including padding
+    uint64_t bytes = 0;       // device bytes of the arrays above
 };
 
 struct Schedule {
@@ -180,10 +176,8 @@ bool spmv_x_in_smem(const dose_matrix* A, const Tuning& t);
 cudaError_t launch_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s);
 size_t spmv_f64_smem_bytes(const dose_matrix* A, bool x_in_smem);
 // SELL-32-sigma (sell_kernel.cu): build from host CSR columns and encoded values, free, launch.
-cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const unsigned char* vals,
-                       const float* row_scale, uint32_t sigma, std::string* why);
-// Whether the SELL ring fits in shared memory with the forward tuning (x from L2 if need be).
-bool sell_fits(const dose_matrix* A);
+cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const unsigned char* vals, uint32_t sigma,
+                       std::string* why);
 void free_sell(dose_matrix* A);
 cudaError_t launch_spmv_sell(const dose_matrix* A, const float* x, float* d, cudaStream_t s);
 bool spmv_f64_x_in_smem(const dose_matrix* A);

@@ -19,16 +19,11 @@
 // the whole matrix) would pad every one of the 10.5 M rows of the clinical beam
 // to its longest row and is not offered.
 //
-// Kernel: the forward kernel's pipeline.  Consecutive chunks form stages (at
-// most tile_nnz entries and tile_rows / 32 chunks), dealt round-robin to
-// persistent CTAs; a producer warp bulk-copies each stage's perm slots (in the
-// row-pointer slice of the ring slot), chunk offsets (in the row-list slice),
-// values and columns -- one contiguous range each -- into a shared-memory ring.
-// Consumer warps take the stage's chunks round-robin; lane l sums its row over
-// the chunk's groups with four accumulators, x in shared memory, and writes
-// d[perm].  A chunk longer than a tile spans several stages of its own, summed
-// by the first consumer warp.  A row is summed by one lane in storage order:
-// bitwise reproducible.
+// Kernel: every warp takes chunks c = warp id, + number of warps, ...; lane l
+// sums its row over the chunk's groups with four accumulators (combined as
+// (0 + 1) + (2 + 3)), x in shared memory; the row's dose is written to
+// d[perm].  A row is summed by one lane in storage order, so the result does
+// not depend on the chunk-to-warp assignment: bitwise reproducible.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -41,179 +36,125 @@ namespace dose {
 namespace {
 
 constexpr uint32_t kSellC = 32;
-constexpr uint32_t kSellPart = STAGE_COOP;  // a stage holding part of one long chunk
+constexpr uint32_t kSellWarps = 16;  // warps per CTA
+constexpr uint32_t kSellCtasPerSm = 4;
 
 struct SellParams {
-    const uint32_t* perm;  // 32 per chunk (+ padding), the ring's "row pointer" slice
     const void* col;       // IW-byte column indices, SELL order
     const void* val;       // stored values, SELL order
+    const uint2* chunk;    // {first entry / 128, groups} per chunk
+    const uint32_t* perm;  // 32 per chunk
+    const float* row_scale;
     float scale;
     const float* x;
     float* d;
-    uint32_t ncols;
-    ScheduleView sched;    // stages; sched.ne = chunk offsets (groups from the stage's first entry)
-    VecSet vecs;           // FP8: row scales in slot order
-    uint32_t tile_nnz, tile_rows, depth, cwarps, l2pf;
-    int* err;
+    uint32_t ncols, nchunks;
 };
 
-constexpr uint32_t kHeaderBytes = 3072;
-
 template <int FMT, uint32_t IW, bool XSMEM>
-__device__ __forceinline__ void sum_groups(const SlotPtrs<FMT, IW>& sp, const float* __restrict__ xs, uint32_t base,
-                                           uint32_t ng, float (&acc)[4]) {
-    for (uint32_t g = 0; g < ng; ++g) {
-        const uint32_t k = base + 128 * g;
-        uint32_t cc[4];
-        if (IW == 4) {
-            const uint4 q = *reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(sp.col) + k);
-            cc[0] = q.x; cc[1] = q.y; cc[2] = q.z; cc[3] = q.w;
-        } else {
-            const uint2 q = *reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(sp.col) + k);
-            cc[0] = q.x & 0xFFFFu; cc[1] = q.x >> 16; cc[2] = q.y & 0xFFFFu; cc[3] = q.y >> 16;
-        }
-        float a[4];
-        load_vals4<FMT>(sp.val + k, a);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = __fmaf_rn(a[u], XSMEM ? xs[cc[u]] : __ldg(xs + cc[u]), acc[u]);
-    }
-}
-
-template <int FMT>
-__device__ __forceinline__ float row_out(const SellParams& p, uint32_t slot, const SlotLayout& SL, uint32_t s_row0,
-                                         uint32_t slot_idx, const float (&acc)[4]) {
-    float v = __fadd_rn(__fadd_rn(acc[0], acc[1]), __fadd_rn(acc[2], acc[3]));
-    if (FMT == DOSE_FMT_U16_SCALE) v = __fmul_rn(p.scale, v);
-    if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) v = __fmul_rn(slot_vec(slot, SL, p.vecs, 0, s_row0, slot_idx), v);
-    return v;
-}
-
-template <int FMT, uint32_t IW, bool XSMEM>
-__global__ void __launch_bounds__(544, 1) sell_spmv_kernel(const SellParams p) {
+__global__ void __launch_bounds__(kSellWarps * 32) sell_spmv_kernel(const SellParams p) {
     using T = typename Fmt<FMT>::T;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t S = p.depth, W = p.cwarps;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* empty = full + S;
-    uint64_t* dbar = full + 16;
-    StageDesc* dwin = reinterpret_cast<StageDesc*>(smem + 1024);
-    float* xs = reinterpret_cast<float*>(smem + kHeaderBytes);
-    const uint32_t x_bytes = XSMEM ? round_up(p.ncols * 4, 128) : 0;
-    unsigned char* slot_base = smem + kHeaderBytes + x_bytes;
-    const SlotLayout SL = slot_layout(p.tile_nnz, p.tile_rows, sizeof(T), p.vecs.n, false, IW);
-    const uint32_t s_begin = p.sched.cta_begin[blockIdx.x], s_end = p.sched.cta_begin[blockIdx.x + 1];
-
-    if (threadIdx.x == 0) {
-        for (uint32_t i = 0; i < S; ++i) {
-            dev::mbar_init(&full[i], 1);
-            dev::mbar_init(&empty[i], W);
-        }
-        dev::mbar_init(&dbar[0], 1);
-        dev::mbar_init(&dbar[1], 1);
-        dev::fence_mbar_init();
-    }
-    __syncthreads();
-    if (s_begin >= s_end) return;
-    if (warp == 0) {
-        if (lane == 0)
-            run_producer<FMT, IW>(p.sched, s_begin, s_end, p.perm, p.col, p.val, p.vecs, slot_base, SL, full, empty, S,
-                                  dwin, dbar, p.l2pf, p.err);
-        return;
-    }
-    const uint32_t cw = warp - 1, ctid = threadIdx.x - 32, nct = W * 32;
+    extern __shared__ __align__(16) float xs_smem[];
     if (XSMEM) {
-        for (uint32_t j = ctid; j < p.ncols; j += nct) xs[j] = __ldg(p.x + j);
-        dev::named_barrier(1, nct);
+        for (uint32_t j = threadIdx.x; j < p.ncols; j += blockDim.x) xs_smem[j] = __ldg(p.x + j);
+        __syncthreads();
     }
-    const float* xsrc = XSMEM ? xs : p.x;
-    const uint32_t slot0 = dev::smem_u32(slot_base);
-    float part[4] = {0.f, 0.f, 0.f, 0.f};  // a long chunk's sums across its stages (first consumer warp)
-    uint32_t st = 0, ph = 0;
-    for (uint32_t s = s_begin; s < s_end; ++s) {
-        if (!dev::mbar_wait_bounded(&full[st], ph)) {
-            atomicExch(p.err, kErrTimeoutFull);
-            return;
-        }
-        const uint32_t slot = slot0 + st * SL.bytes;
-        const StageDesc D = slot_desc(slot);
-        const SlotView v = slot_view<FMT, IW>(slot, SL, D);
-        const SlotPtrs<FMT, IW> sp = slot_ptrs<FMT, IW>(slot_base + st * SL.bytes, SL, D);
-        if (!(D.meta & kSellPart)) {
-            const uint32_t nch = D.ne1 - D.ne0, total = (D.nz1 - D.nz0) / 128;
-            for (uint32_t k = cw; k < nch; k += W) {
-                const uint32_t g0 = dev::lds_u16(v.ne + 2 * k);
-                const uint32_t g1 = k + 1 < nch ? dev::lds_u16(v.ne + 2 * (k + 1)) : total;
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                sum_groups<FMT, IW, XSMEM>(sp, xsrc, D.nz0 + 128 * g0 + 4 * lane, g1 - g0, acc);
-                const uint32_t si = D.row0 + 32 * k + lane;  // this lane's slot
-                const uint32_t row = dev::lds_u32(v.rp + 4 * si);
-                if (row != 0xFFFFFFFFu) p.d[row] = row_out<FMT>(p, slot, SL, D.row0, si, acc);
+    const float* xs = XSMEM ? xs_smem : p.x;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * kSellWarps;
+    for (uint32_t c = blockIdx.x * kSellWarps + (threadIdx.x >> 5); c < p.nchunks; c += nwarps) {
+        const uint2 ch = __ldg(p.chunk + c);
+        const size_t base = (size_t)ch.x * 128 + 4 * lane;
+        const T* vp = static_cast<const T*>(p.val) + base;
+        const unsigned char* cp = static_cast<const unsigned char*>(p.col) + base * IW;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        // raw words of one group: four column indices (16 or 8 bytes) and four values (16, 8 or 4 bytes)
+        struct Raw {
+            uint4 c, v;
+        };
+        auto load = [&](uint32_t g) {
+            Raw r;
+            if (IW == 4) {
+                r.c = __ldg(reinterpret_cast<const uint4*>(cp + (size_t)g * 128 * IW));
+            } else {
+                const uint2 q = __ldg(reinterpret_cast<const uint2*>(cp + (size_t)g * 128 * IW));
+                r.c = make_uint4(q.x, q.y, 0u, 0u);
             }
-        } else if (cw == 0) {
-            if (D.meta & STAGE_FIRST) part[0] = part[1] = part[2] = part[3] = 0.f;
-            sum_groups<FMT, IW, XSMEM>(sp, xsrc, D.nz0 + 4 * lane, (D.nz1 - D.nz0) / 128, part);
-            if (D.meta & STAGE_LAST) {
-                // (the ring stages no perm slice for these stages: read it from global memory)
-                const uint32_t si = D.row0 + lane;
-                const uint32_t row = __ldg(p.perm + si);
-                if (row != 0xFFFFFFFFu) p.d[row] = row_out<FMT>(p, slot, SL, D.row0, si, part);
+            if constexpr (sizeof(T) == 4) {
+                r.v = __ldg(reinterpret_cast<const uint4*>(vp + (size_t)g * 128));
+            } else if constexpr (sizeof(T) == 2) {
+                const uint2 q = __ldg(reinterpret_cast<const uint2*>(vp + (size_t)g * 128));
+                r.v = make_uint4(q.x, q.y, 0u, 0u);
+            } else {
+                r.v = make_uint4(__ldg(reinterpret_cast<const uint32_t*>(vp + (size_t)g * 128)), 0u, 0u, 0u);
             }
+            return r;
+        };
+        auto use = [&](const Raw& r) {
+            uint32_t cc[4];
+            if (IW == 4) {
+                cc[0] = r.c.x; cc[1] = r.c.y; cc[2] = r.c.z; cc[3] = r.c.w;
+            } else {
+                cc[0] = r.c.x & 0xFFFFu; cc[1] = r.c.x >> 16; cc[2] = r.c.y & 0xFFFFu; cc[3] = r.c.y >> 16;
+            }
+            float a[4];
+            if constexpr (sizeof(T) == 4) {
+                a[0] = __uint_as_float(r.v.x); a[1] = __uint_as_float(r.v.y);
+                a[2] = __uint_as_float(r.v.z); a[3] = __uint_as_float(r.v.w);
+            } else {
+                Fmt<FMT>::dec4(r.v.x, r.v.y, a);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = __fmaf_rn(a[u], XSMEM ? xs[cc[u]] : __ldg(xs + cc[u]), acc[u]);
+        };
+        // two groups in flight ahead of the one being summed
+        Raw r0 = ch.y > 0 ? load(0) : Raw{}, r1 = ch.y > 1 ? load(1) : Raw{};
+        for (uint32_t g = 0; g < ch.y; ++g) {
+            const Raw cur = r0;
+            r0 = r1;
+            if (g + 2 < ch.y) r1 = load(g + 2);
+            use(cur);
         }
-        __syncwarp();
-        if (lane == 0) dev::mbar_arrive(&empty[st]);
-        if (++st == S) {
-            st = 0;
-            ph ^= 1;
+        const uint32_t row = __ldg(p.perm + (size_t)c * kSellC + lane);
+        if (row != 0xFFFFFFFFu) {
+            float v = __fadd_rn(__fadd_rn(acc[0], acc[1]), __fadd_rn(acc[2], acc[3]));
+            if (FMT == DOSE_FMT_U16_SCALE) v = __fmul_rn(p.scale, v);
+            if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) v = __fmul_rn(__ldg(p.row_scale + row), v);
+            p.d[row] = v;
         }
     }
 }
 
-uint32_t sell_tile_rows(const Tuning& t) { return std::max(32u, t.tile_rows / 32 * 32); }
-
-size_t sell_smem(const dose_matrix* A, const Tuning& t, bool xsmem) {
-    const uint32_t esize = value_bytes(A->fmt), iw = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;
-    const uint32_t nvec = A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0;
-    const SlotLayout SL = slot_layout(t.tile_nnz, sell_tile_rows(t), esize, nvec, false, iw);
-    return kHeaderBytes + (xsmem ? round_up(A->ncols * 4, 128) : 0) + (size_t)t.stages * SL.bytes;
-}
-
-template <int FMT, uint32_t IW, bool XSMEM>
-cudaError_t launch_t(const dose_matrix* A, const SellParams& p, size_t smem, cudaStream_t s) {
-    auto k = sell_spmv_kernel<FMT, IW, XSMEM>;
+template <int FMT, uint32_t IW>
+cudaError_t launch_t(const dose_matrix* A, const SellParams& p, cudaStream_t s) {
+    const bool xsmem = A->ncols <= kXSmemMaxCols;
+    const size_t smem = xsmem ? (size_t)A->ncols * 4 : 0;
+    auto k = xsmem ? sell_spmv_kernel<FMT, IW, true> : sell_spmv_kernel<FMT, IW, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<A->sell.grid, 32 * (p.cwarps + 1), smem, s>>>(p);
+    const uint32_t grid = std::max(1u, std::min<uint32_t>((uint32_t)A->sm_count * kSellCtasPerSm,
+                                                          (A->sell.nchunks + kSellWarps - 1) / kSellWarps));
+    k<<<grid, kSellWarps * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <int FMT>
-cudaError_t launch_fmt(const dose_matrix* A, const SellParams& p, size_t smem, bool xsmem, cudaStream_t s) {
-    if (A->flags & DOSE_CREATE_U16_INDEX)
-        return xsmem ? launch_t<FMT, 2, true>(A, p, smem, s) : launch_t<FMT, 2, false>(A, p, smem, s);
-    return xsmem ? launch_t<FMT, 4, true>(A, p, smem, s) : launch_t<FMT, 4, false>(A, p, smem, s);
-}
-
-template <class V>
-cudaError_t upload_vec(V** dst, const std::vector<V>& src, size_t pad) {
-    cudaError_t e = cudaMalloc(dst, (src.size() + pad) * sizeof(V));
-    if (e == cudaSuccess) e = cudaMemset(*dst, 0, (src.size() + pad) * sizeof(V));
-    if (e == cudaSuccess && !src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice);
-    return e;
+cudaError_t launch_fmt(const dose_matrix* A, const SellParams& p, cudaStream_t s) {
+    return (A->flags & DOSE_CREATE_U16_INDEX) ? launch_t<FMT, 2>(A, p, s) : launch_t<FMT, 4>(A, p, s);
 }
 
 }  // namespace
 
 // Host: SELL-32-sigma arrays of A from its host CSR (values and indices given
-// in CSR order; esize / iw bytes each) and their stage schedule.
-cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const unsigned char* vals,
-                       const float* row_scale, uint32_t sigma, std::string* why) {
+// in CSR order; esize / iw bytes each).  Returns the device arrays in A->sell.
+cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const unsigned char* vals, uint32_t sigma,
+                       std::string* why) {
     const std::vector<uint32_t>& rp = A->host_row_ptr;
     const uint32_t nrows = A->nrows, esize = value_bytes(A->fmt);
     const uint32_t iw = (A->flags & DOSE_CREATE_U16_INDEX) ? 2 : 4;
     std::vector<uint32_t> order(nrows);
     std::iota(order.begin(), order.end(), 0u);
-    std::vector<uint2> chunk;  // first group, groups
+    std::vector<uint2> chunk;
     std::vector<uint32_t> perm;
     uint64_t groups = 0;  // 128-entry blocks
     if (sigma > 1)
@@ -228,16 +169,16 @@ cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const u
         uint32_t longest = 0;
         for (uint32_t k = c0; k < c1; ++k) longest = std::max(longest, rp[order[k] + 1] - rp[order[k]]);
         const uint32_t ng = (longest + 3) / 4;
+        if (groups > 0xFFFFFFFFull) {
+            *why = "SELL storage needs more than 2^32 blocks of 128 entries";
+            return cudaErrorInvalidValue;
+        }
         chunk.push_back(make_uint2((uint32_t)groups, ng));
         groups += ng;
         for (uint32_t k = c0; k < c0 + kSellC; ++k) perm.push_back(k < c1 ? order[k] : 0xFFFFFFFFu);
     }
-    if (groups * 128 >= (1ull << 32)) {
-        *why = "SELL storage needs 2^32 or more entries (padding included)";
-        return cudaErrorInvalidValue;
-    }
     const size_t entries = (size_t)groups * 128;
-    std::vector<unsigned char> sval(entries * esize, 0), scol(entries * iw, 0);
+    std::vector<unsigned char> sval(entries * esize + 64, 0), scol(entries * iw + 64, 0);
     for (size_t c = 0; c < chunk.size(); ++c)
         for (uint32_t l = 0; l < kSellC; ++l) {
             const uint32_t r = perm[c * kSellC + l];
@@ -254,131 +195,53 @@ cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const u
                 }
             }
         }
-    // Stages: consecutive chunks with at most tile_nnz entries and tile_rows / 32
-    // chunks; a chunk longer than a tile gets stages of its own (FIRST .. LAST).
-    const Tuning& t = A->fwd.tuning;
-    const uint32_t gmax = std::max(1u, t.tile_nnz / 128), cmax = sell_tile_rows(t) / kSellC;
-    std::vector<StageDesc> desc;
-    std::vector<uint16_t> choff(chunk.size(), 0);
-    std::vector<std::pair<uint32_t, uint32_t>> items;  // stage ranges, dealt whole
-    for (uint32_t c = 0; c < chunk.size();) {
-        if (chunk[c].y > gmax) {
-            const uint32_t s0 = (uint32_t)desc.size();
-            for (uint32_t g = 0; g < chunk[c].y; g += gmax) {
-                StageDesc D{};
-                D.row0 = kSellC * c;
-                D.row1 = kSellC * (c + 1);
-                D.nz0 = (chunk[c].x + g) * 128;
-                D.nz1 = (chunk[c].x + std::min(chunk[c].y, g + gmax)) * 128;
-                D.ne0 = c;
-                D.ne1 = c + 1;
-                D.meta = kSellPart | (g == 0 ? STAGE_FIRST : 0u) | (g + gmax >= chunk[c].y ? STAGE_LAST : 0u);
-                desc.push_back(D);
-            }
-            items.push_back({s0, (uint32_t)desc.size()});
-            ++c;
-            continue;
-        }
-        StageDesc D{};
-        D.row0 = kSellC * c;
-        D.ne0 = c;
-        D.nz0 = chunk[c].x * 128;
-        uint32_t g = 0, c1 = c;
-        while (c1 < chunk.size() && c1 - c < cmax && chunk[c1].y <= gmax && g + chunk[c1].y <= gmax) {
-            choff[c1] = (uint16_t)g;
-            g += chunk[c1].y;
-            ++c1;
-        }
-        D.row1 = kSellC * c1;
-        D.ne1 = c1;
-        D.nz1 = D.nz0 + g * 128;
-        items.push_back({(uint32_t)desc.size(), (uint32_t)desc.size() + 1});
-        desc.push_back(D);
-        c = c1;
-    }
-    const uint32_t grid = (uint32_t)std::max(1, A->sm_count);
-    std::vector<std::vector<uint32_t>> per(grid);
-    for (size_t i = 0; i < items.size(); ++i)
-        for (uint32_t k = items[i].first; k < items[i].second; ++k) per[i % grid].push_back(k);
-    std::vector<StageDesc> sorted;
-    std::vector<uint32_t> cta_begin(grid + 1, 0);
-    for (uint32_t b = 0; b < grid; ++b) {
-        cta_begin[b] = (uint32_t)sorted.size();
-        for (uint32_t k : per[b]) sorted.push_back(desc[k]);
-    }
-    cta_begin[grid] = (uint32_t)sorted.size();
-    // FP8 row scales in slot order (the ring stages them like the perm slots)
-    std::vector<float> sscale;
-    if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {
-        sscale.assign(perm.size(), 1.0f);
-        for (size_t i = 0; i < perm.size(); ++i)
-            if (perm[i] != 0xFFFFFFFFu) sscale[i] = row_scale[perm[i]];
-    }
     SellArrays& S = A->sell;
     cudaError_t e;
-    if ((e = upload_vec(reinterpret_cast<unsigned char**>(&S.val), sval, 64)) != cudaSuccess) return e;
-    if ((e = upload_vec(reinterpret_cast<unsigned char**>(&S.col), scol, 64)) != cudaSuccess) return e;
-    if ((e = upload_vec(&S.perm, perm, 32)) != cudaSuccess) return e;
-    if ((e = upload_vec(&S.choff, choff, 32)) != cudaSuccess) return e;
-    if ((e = upload_vec(&S.desc, sorted, 1)) != cudaSuccess) return e;
-    if ((e = upload_vec(&S.cta_begin, cta_begin, 0)) != cudaSuccess) return e;
-    if (!sscale.empty() && (e = upload_vec(&S.scale_perm, sscale, 32)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&S.val, sval.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&S.col, scol.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&S.chunk, std::max<size_t>(chunk.size(), 1) * sizeof(uint2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&S.perm, std::max<size_t>(perm.size(), 1) * 4)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(S.val, sval.data(), sval.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(S.col, scol.data(), scol.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if (!chunk.empty() &&
+        (e = cudaMemcpy(S.chunk, chunk.data(), chunk.size() * sizeof(uint2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if (!perm.empty() && (e = cudaMemcpy(S.perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
     S.nchunks = (uint32_t)chunk.size();
-    S.nslots = (uint32_t)perm.size();
-    S.n_stages = (uint32_t)sorted.size();
-    S.grid = grid;
     S.entries = entries;
     S.sigma = sigma;
-    S.bytes = sval.size() + scol.size() + (perm.size() + 32) * 4 + (choff.size() + 32) * 2 +
-              (sorted.size() + 1) * sizeof(StageDesc) + cta_begin.size() * 4 + (sscale.size() + 32) * 4;
+    S.bytes = sval.size() + scol.size() + chunk.size() * sizeof(uint2) + perm.size() * 4;
     return cudaSuccess;
 }
 
 void free_sell(dose_matrix* A) {
     cudaFree(A->sell.val);
     cudaFree(A->sell.col);
+    cudaFree(A->sell.chunk);
     cudaFree(A->sell.perm);
-    cudaFree(A->sell.choff);
-    cudaFree(A->sell.desc);
-    cudaFree(A->sell.cta_begin);
-    cudaFree(A->sell.scale_perm);
     A->sell = SellArrays();
 }
 
-bool sell_fits(const dose_matrix* A) { return sell_smem(A, A->fwd.tuning, false) <= kMaxSmemPerBlock; }
-
 cudaError_t launch_spmv_sell(const dose_matrix* A, const float* x, float* d, cudaStream_t s) {
-    if (A->nrows == 0 || A->sell.n_stages == 0) return cudaSuccess;
-    const Tuning& t = A->fwd.tuning;
+    if (A->nrows == 0 || A->sell.nchunks == 0) return cudaSuccess;
     SellParams p;
-    p.perm = A->sell.perm;
     p.col = A->sell.col;
     p.val = A->sell.val;
+    p.chunk = A->sell.chunk;
+    p.perm = A->sell.perm;
+    p.row_scale = A->row_scale;
     p.scale = A->scale;
     p.x = x;
     p.d = d;
     p.ncols = A->ncols;
-    p.sched = ScheduleView{A->sell.desc, A->sell.choff, A->sell.cta_begin, nullptr};
-    p.vecs.n = 0;
-    if (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE) {
-        p.vecs.n = 1;
-        p.vecs.ptr[0] = A->sell.scale_perm;
-        p.vecs.lim[0] = A->sell.nslots;
-    }
-    p.tile_nnz = t.tile_nnz;
-    p.tile_rows = sell_tile_rows(t);
-    p.depth = t.stages;
-    p.cwarps = t.consumer_warps;
-    p.l2pf = t.l2_prefetch;
-    p.err = A->err;
-    const bool xsmem = A->ncols <= kXSmemMaxCols && sell_smem(A, t, true) <= kMaxSmemPerBlock;
-    const size_t smem = sell_smem(A, t, xsmem);
+    p.nchunks = A->sell.nchunks;
     switch (A->fmt) {
-        case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, smem, xsmem, s);
-        case DOSE_FMT_BF16: return launch_fmt<DOSE_FMT_BF16>(A, p, smem, xsmem, s);
-        case DOSE_FMT_F16: return launch_fmt<DOSE_FMT_F16>(A, p, smem, xsmem, s);
-        case DOSE_FMT_F32: return launch_fmt<DOSE_FMT_F32>(A, p, smem, xsmem, s);
-        case DOSE_FMT_FP8E4M3_ROWSCALE: return launch_fmt<DOSE_FMT_FP8E4M3_ROWSCALE>(A, p, smem, xsmem, s);
+        case DOSE_FMT_U16_SCALE: return launch_fmt<DOSE_FMT_U16_SCALE>(A, p, s);
+        case DOSE_FMT_BF16: return launch_fmt<DOSE_FMT_BF16>(A, p, s);
+        case DOSE_FMT_F16: return launch_fmt<DOSE_FMT_F16>(A, p, s);
+        case DOSE_FMT_F32: return launch_fmt<DOSE_FMT_F32>(A, p, s);
+        case DOSE_FMT_FP8E4M3_ROWSCALE: return launch_fmt<DOSE_FMT_FP8E4M3_ROWSCALE>(A, p, s);
     }
     return cudaErrorInvalidValue;
 }
