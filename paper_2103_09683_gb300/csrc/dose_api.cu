@@ -169,13 +169,18 @@ static uint32_t nearest_pow2_log2(double v) {
 
 // Column windows: rcmin / rcmax give each row's lowest and highest column (null
 // for a schedule without windows, which deals round-robin).  vbytes: stored bytes per
-// entry (value + column index), used to balance the CTAs' HBM traffic.  cut_jumps:
-// end a row block where its column range would more than double.
+// entry (value + column index), used to balance the CTAs' HBM traffic.
 static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, const Tuning& t, uint32_t grid,
-                               const uint32_t* rcmin, const uint32_t* rcmax, uint32_t ncols, uint32_t vbytes,
-                               bool cut_jumps) {
+                               const uint32_t* rcmin, const uint32_t* rcmax, uint32_t ncols, uint32_t vbytes) {
     Schedule S;
     uint32_t r = 0;
+    // Widest single row: a block wider than 1.5 times it can only come from rows
+    // far apart in the spot numbering (see the cut below).
+    uint32_t row_span_max = 0;
+    if (rcmin)
+        for (uint32_t i = 0; i < nrows; ++i)
+            if (rcmin[i] <= rcmax[i]) row_span_max = std::max(row_span_max, rcmax[i] - rcmin[i]);
+    const uint64_t span_cap = (uint64_t)row_span_max * 3 / 2;
     while (r < nrows) {
         const uint32_t len = rp[r + 1] - rp[r];
         if (len > t.coop_nnz) {
@@ -204,15 +209,16 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
         while (r < nrows && r - D.row0 < t.tile_rows) {
             const uint32_t l = rp[r + 1] - rp[r];
             if (l > t.coop_nnz || nz + l > t.tile_nnz) break;
-            if (cut_jumps && rcmin && l) {
-                // A block whose column range would more than double with this row
-                // (the voxel order wrapping to the far side of the beam) ends
-                // here: one wide block would widen every CTA's window.  Only the
-                // forward schedule of a wide matrix does this: its window must fit
-                // in shared memory, while the adjoint's rows of a multi-beam plan
-                // span several beams' columns and would be cut into many blocks.
+            if (rcmin && l) {
+                // A block whose column range would more than double with this row,
+                // and grow wider than 1.5 times any single row (the voxel order
+                // wrapping to the far side of the beam), ends here: one wide block
+                // would widen every CTA's window.  Rows of a multi-beam plan
+                // already span all beams' spots, so their blocks are never cut.
                 const uint32_t nlo = std::min(slo, rcmin[r]), nhi = std::max(shi, rcmax[r]);
-                if (slo <= shi && nhi - nlo > 2 * std::max(shi - slo, rcmax[r] - rcmin[r]) + 64) break;
+                if (slo <= shi && nhi - nlo > 2 * std::max(shi - slo, rcmax[r] - rcmin[r]) + 64 &&
+                    nhi - nlo > span_cap)
+                    break;
                 slo = nlo;
                 shi = nhi;
             }
@@ -462,7 +468,7 @@ static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& 
     const bool win = windowed && !A->host_row_cmin.empty();
     const uint32_t vbytes = value_bytes(A->fmt) + 4;
     Schedule S = build_schedule(A->host_row_ptr, A->nrows, t, D.grid, win ? A->host_row_cmin.data() : nullptr,
-                                win ? A->host_row_cmax.data() : nullptr, A->ncols, vbytes, win && &D == &A->fwd);
+                                win ? A->host_row_cmax.data() : nullptr, A->ncols, vbytes);
     free_dev_schedule(D);
     cudaError_t e;
     if ((e = upload(&D.desc, S.desc.data(), S.desc.size(), S.desc.size() + 1)) != cudaSuccess ||
