@@ -169,9 +169,12 @@ static uint32_t nearest_pow2_log2(double v) {
 
 // Column windows: rcmin / rcmax give each row's lowest and highest column (null
 // for a schedule without windows, which deals round-robin).  vbytes: stored bytes per
-// entry (value + column index), used to balance the CTAs' HBM traffic.
+// entry (value + column index), used to balance the CTAs' HBM traffic.  tight:
+// also end a block where its column range would more than double below the cap
+// (narrower windows; more blocks).
 static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, const Tuning& t, uint32_t grid,
-                               const uint32_t* rcmin, const uint32_t* rcmax, uint32_t ncols, uint32_t vbytes) {
+                               const uint32_t* rcmin, const uint32_t* rcmax, uint32_t ncols, uint32_t vbytes,
+                               bool tight = false) {
     Schedule S;
     uint32_t r = 0;
     // Widest single row: a block wider than 1.5 times it can only come from rows
@@ -217,7 +220,7 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
                 // already span all beams' spots, so their blocks are never cut.
                 const uint32_t nlo = std::min(slo, rcmin[r]), nhi = std::max(shi, rcmax[r]);
                 if (slo <= shi && nhi - nlo > 2 * std::max(shi - slo, rcmax[r] - rcmin[r]) + 64 &&
-                    nhi - nlo > span_cap)
+                    (tight || nhi - nlo > span_cap))
                     break;
                 slo = nlo;
                 shi = nhi;
@@ -469,6 +472,15 @@ static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& 
     const uint32_t vbytes = value_bytes(A->fmt) + 4;
     Schedule S = build_schedule(A->host_row_ptr, A->nrows, t, D.grid, win ? A->host_row_cmin.data() : nullptr,
                                 win ? A->host_row_cmax.data() : nullptr, A->ncols, vbytes);
+    if (win) {
+        // Cutting blocks at every doubling of their column range narrows the
+        // windows of a single beam (one more scatter warp fits on the clinical
+        // beam) but only fragments a multi-beam plan, whose rows already span
+        // every beam: keep it where it narrows the window.
+        Schedule T = build_schedule(A->host_row_ptr, A->nrows, t, D.grid, A->host_row_cmin.data(),
+                                    A->host_row_cmax.data(), A->ncols, vbytes, true);
+        if (T.wwidth < S.wwidth) S = std::move(T);
+    }
     free_dev_schedule(D);
     cudaError_t e;
     if ((e = upload(&D.desc, S.desc.data(), S.desc.size(), S.desc.size() + 1)) != cudaSuccess ||
