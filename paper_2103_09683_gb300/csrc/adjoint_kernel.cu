@@ -37,10 +37,8 @@ struct AdjParams {
     double* f_part;   // grid
     uint32_t nrows, ncols;
     uint32_t wwidth;  // columns of each CTA's window [wlo, wlo + wwidth), wlo = sched.wlo[cta]
-    const float* pg;  // QUADRATIC: p and w, read by the forward warps from global memory
-    const float* wg;
     ScheduleView sched;
-    VecSet vecs;      // QUADRATIC: [row scale]; ADJOINT: r [, row scale]
+    VecSet vecs;      // QUADRATIC: p, w [, row scale]; ADJOINT: r [, row scale]
     uint32_t tile_nnz, tile_rows, depth, fwarps, swarps, l2pf;
     int* err;
 };
@@ -170,8 +168,8 @@ __device__ __forceinline__ void fwd_rows(const AdjParams& p, const StageDesc& D,
                 FMT == DOSE_FMT_FP8E4M3_ROWSCALE ? slot_vec(slot, SL, p.vecs, kRowScaleVec, D.row0, row) : 1.f;
             const float dv = finish_dot<FMT>(p, rsc, sum);
             if (p.d) p.d[row] = dv;
-            const float wv = __ldg(p.wg + row);
-            const float e = dev::df_add_wsq(f_hi, f_lo, wv, dv, __ldg(p.pg + row));
+            const float wv = slot_vec(slot, SL, p.vecs, 1, D.row0, row);
+            const float e = dev::df_add_wsq(f_hi, f_lo, wv, dv, slot_vec(slot, SL, p.vecs, 0, D.row0, row));
             dev::sts_f32(rl + 4 * i, __fmul_rn(__fmul_rn(__fmul_rn(2.0f, wv), e), rsc));
         }
     }
@@ -181,7 +179,7 @@ template <int FMT, int MODE>
 __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const AdjParams p) {
     using T = typename Fmt<FMT>::T;
     constexpr bool QUAD = MODE == ADJ_MODE_QUADRATIC;
-    constexpr uint32_t kRowScaleVec = QUAD ? 0 : 1;  // index of the FP8 row scales in vecs
+    constexpr uint32_t kRowScaleVec = QUAD ? 2 : 1;  // index of the FP8 row scales in vecs
     extern __shared__ __align__(128) unsigned char smem[];
 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -263,8 +261,8 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
                     if (dev::lds_u32(v.rp + 4 * r) == dev::lds_u32(v.rp + 4 * r + 4)) {
                         if (p.d) p.d[r] = 0.0f;
                         // an empty row with p = 0 adds exactly nothing (d = 0), unless w is not finite
-                        const float pv = __ldg(p.pg + r);
-                        const float wv = __ldg(p.wg + r);
+                        const float pv = slot_vec(slot, SL, p.vecs, 0, D.row0, r);
+                        const float wv = slot_vec(slot, SL, p.vecs, 1, D.row0, r);
                         if (pv != 0.0f || !(fabsf(wv) < INFINITY)) dev::df_add_wsq(f_hi, f_lo, wv, 0.0f, pv);
                     }
                 }
@@ -294,8 +292,9 @@ __global__ void __launch_bounds__(kMaxAdjWarps * 32, 1) adjoint_kernel(const Adj
                                               : 1.f;
                         const float dv = finish_dot<FMT>(p, rsc, tot);
                         if (p.d) p.d[D.row0] = dv;
-                        const float wv = __ldg(p.wg + D.row0);
-                        const float e = dev::df_add_wsq(f_hi, f_lo, wv, dv, __ldg(p.pg + D.row0));
+                        const float wv = slot_vec(slot, SL, p.vecs, 1, D.row0, D.row0);
+                        const float e =
+                            dev::df_add_wsq(f_hi, f_lo, wv, dv, slot_vec(slot, SL, p.vecs, 0, D.row0, D.row0));
                         dev::sts_f32(slot + SL.hdr_off + 32, __fmul_rn(__fmul_rn(__fmul_rn(2.0f, wv), e), rsc));
                     }
                     dev::named_barrier(2, nft);
@@ -427,7 +426,7 @@ cudaError_t launch_adj_t(const dose_matrix* A, const AdjParams& p, size_t smem, 
 
 size_t adj_smem(const dose_matrix* A, const AdjTuning& t, bool quad, uint32_t ws) {
     const uint32_t esize = value_bytes(A->fmt);
-    const uint32_t nvec = (quad ? 0 : 1) + (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
+    const uint32_t nvec = (quad ? 2 : 1) + (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
     const SlotLayout SL = slot_layout(t.tile_nnz, t.tile_rows, esize, nvec, quad);
     const size_t col_bytes = round_up(A->adj.wwidth * 4, 128);
     const size_t x_bytes = quad ? round_up((A->adj.wwidth + 1) * 4, 128) : 0;  // the window of x and a zero
@@ -482,9 +481,13 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
         prm.sched = ScheduleView{A->adj.desc, A->adj.ne, A->adj.cta_begin, A->adj.wlo};
         const uint32_t user_lim = A->nrows & ~3u;  // caller arrays: whole 16-byte pieces only
         prm.vecs.n = 0;
-        prm.pg = p;
-        prm.wg = w;
-        if (!quad) {
+        if (quad) {
+            prm.vecs.ptr[0] = p;
+            prm.vecs.lim[0] = user_lim;
+            prm.vecs.ptr[1] = w;
+            prm.vecs.lim[1] = user_lim;
+            prm.vecs.n = 2;
+        } else {
             prm.vecs.ptr[0] = r;
             prm.vecs.lim[0] = user_lim;
             prm.vecs.n = 1;
