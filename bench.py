@@ -137,13 +137,14 @@ def whole_job_gbs(bytes_per_step: int, steps: int, world_size: int, max_ms: floa
 
 
 def _traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this build."""
+    """DRAM bytes per launch from the committed ncu summary, if the sources the
+    kernel depends on are the ones it was captured from."""
     try:
         import paper_2103_09683_gb300._build as b
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tab = json.load(f)
         ent = tab.get(kernel)
-        if ent and ent.get("inputs_sha256") == b._inputs_digest():
+        if ent and ent.get("inputs_sha256") == b._inputs_digest(ent.get("sources")):
             return float(ent["dram_bytes_per_launch"])
     except Exception:
         pass

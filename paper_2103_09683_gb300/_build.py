@@ -31,11 +31,13 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the dose library needs the CUDA toolkit to build")
 
 
-def _inputs_digest() -> str:
+def _inputs_digest(names=None) -> str:
+    """SHA-256 of the library sources and compile flags; with `names`, of those
+    source files only (the ones one kernel's code and launch depend on)."""
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):
         for name in sorted(os.listdir(d)):
-            if name.endswith((".cu", ".cuh", ".h")):
+            if name.endswith((".cu", ".cuh", ".h")) and (names is None or name in names):
                 with open(os.path.join(d, name), "rb") as f:
                     h.update(name.encode() + f.read())
     h.update(" ".join(ARCH + NVCC_FLAGS).encode())

@@ -152,7 +152,8 @@ __device__ __forceinline__ void spmm_rows(const StagedItem& it, const StageDesc&
                                  __fmul_rn(sc, acc.w)};
             float* dst = it.D + (size_t)row * nvec;
             if (vec4) {
-                *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+                // nvec = 12 runs four quads: the fourth lies past the row
+                if (4 * q < nvec) *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(r4[0], r4[1], r4[2], r4[3]);
             } else {
 #pragma unroll
                 for (uint32_t u = 0; u < 4; ++u)

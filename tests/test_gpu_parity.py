@@ -390,10 +390,14 @@ def test_autograd_function_uses_adjoint(tiny, objective_inputs):
 
 # ----------------------------------------------------------------- batched
 
-@pytest.mark.parametrize("nvec", [1, 5, 16])
+@pytest.mark.parametrize("nvec", [1, 5, 8, 12, 16])
 def test_batched_spmm_small(nvec):
+    """Mixed formats and row lengths: rows of ~6 to 700 entries take 1 to 32
+    lanes per row, and a 2500-entry row the long-row path."""
     mats = [dosegen.random_csr(500 + 97 * i, 60 + 13 * i, seed=20 + i, density=0.1) for i in range(5)]
     mats.append(dosegen.random_csr(40, 3000, seed=30, lengths=[0, 2500] + [7] * 38))
+    for k, n in enumerate((40, 100, 150, 700)):
+        mats.append(dosegen.random_csr(48 + k, 1200, seed=40 + k, lengths=[n] * (48 + k)))
     handles, encs, Xs = [], [], []
     for i, m in enumerate(mats):
         A, enc = make(m, ("u16", "fp8", "bf16", "f16", "f32")[i % 5])
@@ -454,6 +458,31 @@ def test_batched_spmm_pencil_beams_staged_and_graph():
     torch.cuda.synchronize()
     for D, F in zip(Ds, first):
         assert torch.equal(D, F)
+    for A in handles:
+        A.device_status()
+
+
+@pytest.mark.parametrize("nvec", [4, 8, 12, 16])
+def test_batched_spmm_staged_writes_stay_inside_d(nvec):
+    """The staged form with every vector count that stores whole quads (nvec a
+    multiple of 4): each D is the head of a larger buffer whose tail must come
+    back untouched (nvec = 12 runs four quads of vectors, the fourth past the
+    row)."""
+    mats = _small_beam_batch()[:3]
+    handles, encs, Xs, bufs, Ds = [], [], [], [], []
+    for i, m in enumerate(mats):
+        A, enc = make(m, ("u16", "bf16", "fp8")[i])
+        handles.append(A)
+        encs.append(enc)
+        Xs.append(_to(dosegen.spot_weights(m.ncols, 300 + i, nvec=nvec).reshape(m.ncols, nvec)))
+        buf = torch.full((m.nrows * nvec + 64,), 7.0, dtype=torch.float32, device="cuda")
+        bufs.append(buf)
+        Ds.append(buf[:m.nrows * nvec].view(m.nrows, nvec))
+    dose.spmv_batched(handles, Xs, Ds)
+    for m, enc, X, D, buf in zip(mats, encs, Xs, Ds, bufs):
+        ref = oracle.spmm(m.nrows, enc.row_ptr, enc.col, enc.decoded, X.cpu().numpy().astype(np.float64))
+        fwd_check(D.cpu().numpy().reshape(-1), ref.reshape(-1))
+        assert torch.all(buf[m.nrows * nvec:] == 7.0)
     for A in handles:
         A.device_status()
 
