@@ -191,6 +191,61 @@ def test_forward_column_windows_for_wide_matrices(fmt):
         A.device_status()
 
 
+def _banded_65536():
+    """65536 spots, the most 16-bit column indices can address: 4096 rows of 48
+    entries inside a 160-column band that slides across all the columns, so
+    row 0 holds column 0 and the last row column 65535 (narrow column windows
+    for both schedules)."""
+    nrows, ncols, n, band = 4096, 65536, 48, 160
+    rng = np.random.default_rng(65536)
+    rp = np.arange(nrows + 1, dtype=np.uint32) * n
+    cols = []
+    for i in range(nrows):
+        lo = (i * (ncols - band)) // (nrows - 1)
+        c = np.sort(rng.choice(band, n, replace=False)) + lo
+        if i == 0:
+            c[0] = 0
+        if i == nrows - 1:
+            c[-1] = ncols - 1
+        cols.append(c)
+    col = np.concatenate(cols).astype(np.uint32)
+    return dosegen.CSR(nrows, ncols, rp, col, rng.uniform(1e-3, 1.0, col.size))
+
+
+@pytest.mark.parametrize("fmt", ["u16", "f16"])
+@pytest.mark.parametrize("index16", [False, True])
+def test_largest_16bit_column_range(fmt, index16):
+    """Column 65535 through every path that reads column indices: the dose
+    (FP32 and FP64 vectors, CSR and SELL), the adjoint and the fused pass."""
+    csr = _banded_65536()
+    assert csr.col.max() == 65535 and csr.col.min() == 0
+    x = _x(csr.ncols, seed=14)
+    x64 = dosegen.spot_weights_f64(csr.ncols, 15)
+    for sell in (False, True):
+        A, enc = make(csr, fmt, index16=index16, sell=sell)
+        ref = oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x)
+        fwd_check(A.spmv(_to(x)).cpu().numpy(), ref)
+        if sell:
+            continue
+        d64 = A.spmv_f64(_to(x64)).cpu().numpy()
+        ref64 = oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x64)
+        absref = oracle.spmv(csr.nrows, enc.row_ptr, enc.col, np.abs(enc.decoded), x64)
+        assert np.max(np.abs(d64 - ref64) / absref) <= 2.0 ** -40
+        r = np.random.default_rng(16).normal(size=csr.nrows).astype(np.float32)
+        g_ref = oracle.spmv_t(csr.nrows, csr.ncols, enc.row_ptr, enc.col, enc.decoded, r)
+        g_abs = oracle.abs_spmv_t(csr.nrows, csr.ncols, enc.row_ptr, enc.col, enc.decoded, r)
+        adj_check(A.adjoint(_to(r)).cpu().numpy(), g_ref, g_abs)
+        p = np.where(np.arange(csr.nrows) % 3 == 0, 1.0, 0.0).astype(np.float32)
+        w = np.ones(csr.nrows, dtype=np.float32)
+        f, g = A.fwd_adj_quadratic(_to(x), _to(p), _to(w))
+        f_ref, g2_ref = oracle.fgrad(csr.nrows, csr.ncols, enc.row_ptr, enc.col, enc.decoded, x, p, w)
+        assert abs(float(f.item()) - f_ref) <= 1e-4 * f_ref
+        _, r2 = oracle.objective(ref, p, w)
+        g2_abs = oracle.abs_spmv_t(csr.nrows, csr.ncols, enc.row_ptr, enc.col, enc.decoded, r2)
+        adj_check(g.cpu().numpy(), g2_ref, g2_abs, rtol=1e-4)
+        A.device_status()
+
+
 def test_compensated_long_rows_adversarial():
     # descending magnitudes over 16000 entries: plain FP32 loses digits
     n = 16000
