@@ -41,7 +41,9 @@ typedef struct dose_matrix dose_matrix; /* opaque, library-owned */
 typedef enum {
     DOSE_OK = 0,
     DOSE_ERR_INVALID_ARG = 1, /* bad pointer, size, structure or value */
-    DOSE_ERR_OOM = 2,         /* host or device allocation failed */
+    DOSE_ERR_OOM = 2,         /* host or device allocation failed (for tests: with
+                                 DOSE_TEST_ALLOC_LIMIT=<bytes> in the environment,
+                                 every device allocation larger than that fails so) */
     DOSE_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
     DOSE_ERR_UNSUPPORTED = 4, /* valid request outside what this build implements */
     DOSE_ERR_TIMEOUT = 5      /* a kernel's bounded wait ran out (dose_device_status) */

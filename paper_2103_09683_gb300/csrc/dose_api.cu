@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -23,8 +24,21 @@ static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 dose_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        set_error(std::string(what) + ": out of device memory");
+        return DOSE_ERR_OOM;
+    }
     set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
     return DOSE_ERR_CUDA;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (const char* lim = std::getenv("DOSE_TEST_ALLOC_LIMIT")) {
+        const unsigned long long n = std::strtoull(lim, nullptr, 10);
+        if (n && bytes > n) return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
 }
 
 static dose_status invalid(const std::string& msg) {
@@ -457,7 +471,7 @@ static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out)
 
 template <class T>
 static cudaError_t upload(T** dst, const T* src, size_t n, size_t alloc_n) {
-    cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(alloc_n, 1) * sizeof(T));
+    cudaError_t e = dev_malloc(dst, std::max<size_t>(alloc_n, 1) * sizeof(T));
     if (e != cudaSuccess) return e;
     e = cudaMemset(*dst, 0, std::max<size_t>(alloc_n, 1) * sizeof(T));
     if (e != cudaSuccess) return e;
@@ -746,12 +760,12 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
         (e = upload(&A->row_scale, scl.data(), (size_t)nrows, (size_t)nrows + 16)) != cudaSuccess)
         return fail(e, "row scales");
     const size_t x64_alloc = ((size_t)ncols + 2) / 2 * 2;  // ncols + 1 elements, even count (16 B multiple)
-    if ((e = cudaMalloc(&A->x64, x64_alloc * 8)) != cudaSuccess) return fail(e, "FP64 vector scratch");
+    if ((e = dev_malloc(&A->x64, x64_alloc * 8)) != cudaSuccess) return fail(e, "FP64 vector scratch");
     const size_t ncols_pad = ((size_t)ncols + 31) / 32 * 32;  // a CTA's window is at most this wide
-    if ((e = cudaMalloc(&A->g_part, std::max<size_t>((size_t)A->adj.grid * ncols_pad, 1) * 4)) != cudaSuccess)
+    if ((e = dev_malloc(&A->g_part, std::max<size_t>((size_t)A->adj.grid * ncols_pad, 1) * 4)) != cudaSuccess)
         return fail(e, "adjoint partials");
-    if ((e = cudaMalloc(&A->f_part, (size_t)A->adj.grid * 8)) != cudaSuccess) return fail(e, "objective partials");
-    if ((e = cudaMalloc(&A->err, sizeof(int))) != cudaSuccess) return fail(e, "error word");
+    if ((e = dev_malloc(&A->f_part, (size_t)A->adj.grid * 8)) != cudaSuccess) return fail(e, "objective partials");
+    if ((e = dev_malloc(&A->err, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     if ((e = cudaMemset(A->err, 0, sizeof(int))) != cudaSuccess) return fail(e, "error word");
     {
         const Tuning t_full = t;
@@ -1072,10 +1086,10 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
     float *d = nullptr, *pw = nullptr, *g = nullptr;
     double* f = nullptr;
     const size_t nr = std::max<size_t>(A->nrows, 1), nrp = (nr + 3) / 4 * 4;
-    cudaError_t e = cudaMalloc(&d, nr * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&pw, 2 * nrp * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&g, std::max<size_t>(A->ncols, 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&f, 8);
+    cudaError_t e = dev_malloc(&d, nr * 4);
+    if (e == cudaSuccess) e = dev_malloc(&pw, 2 * nrp * 4);
+    if (e == cudaSuccess) e = dev_malloc(&g, std::max<size_t>(A->ncols, 1) * 4);
+    if (e == cudaSuccess) e = dev_malloc(&f, 8);
     if (e == cudaSuccess) e = cudaMemset(pw, 0, 2 * nrp * 4);  // p = 0, w = 0: timing only
     if (e != cudaSuccess) {
         cudaFree(d);

@@ -166,6 +166,15 @@ namespace dose {
 // Host helpers (dose_api.cu)
 void set_error(const std::string& msg);
 dose_status cuda_fail(cudaError_t e, const char* what);
+// Every device allocation of the library goes through here.  A test hook:
+// with DOSE_TEST_ALLOC_LIMIT=<bytes> in the environment, a request for more
+// than that many bytes fails as out of memory without reaching the driver, so
+// the out-of-memory paths run without exhausting the device.
+cudaError_t dev_malloc(void** p, size_t bytes);
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
 
 // Launchers (spmv_kernel.cu, spmv_f64_kernel.cu, adjoint_kernel.cu, batched_kernel.cu)
 size_t spmv_smem_bytes(const dose_matrix* A, const Tuning& t, bool x_in_smem);

@@ -138,9 +138,9 @@ dose_status dose_create_scenarios(const dose_matrix* const* A, int count, const 
     int dev_prev = 0;
     cudaGetDevice(&dev_prev);
     cudaSetDevice(A[0]->device);
-    cudaError_t e = cudaMalloc(&S->prob, count * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&S->f_s, count * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&S->g_s, std::max<size_t>((size_t)count * S->ncols, 1) * sizeof(float));
+    cudaError_t e = dev_malloc(&S->prob, count * sizeof(double));
+    if (e == cudaSuccess) e = dev_malloc(&S->f_s, count * sizeof(double));
+    if (e == cudaSuccess) e = dev_malloc(&S->g_s, std::max<size_t>((size_t)count * S->ncols, 1) * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(S->prob, pr.data(), count * sizeof(double), cudaMemcpyHostToDevice);
     cudaSetDevice(dev_prev);
     if (e != cudaSuccess) {

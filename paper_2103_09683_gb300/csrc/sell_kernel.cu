@@ -197,10 +197,10 @@ cudaError_t build_sell(dose_matrix* A, const std::vector<uint32_t>& col, const u
         }
     SellArrays& S = A->sell;
     cudaError_t e;
-    if ((e = cudaMalloc(&S.val, sval.size())) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&S.col, scol.size())) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&S.chunk, std::max<size_t>(chunk.size(), 1) * sizeof(uint2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&S.perm, std::max<size_t>(perm.size(), 1) * 4)) != cudaSuccess) return e;
+    if ((e = dev_malloc(&S.val, sval.size())) != cudaSuccess) return e;
+    if ((e = dev_malloc(&S.col, scol.size())) != cudaSuccess) return e;
+    if ((e = dev_malloc(&S.chunk, std::max<size_t>(chunk.size(), 1) * sizeof(uint2))) != cudaSuccess) return e;
+    if ((e = dev_malloc(&S.perm, std::max<size_t>(perm.size(), 1) * 4)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(S.val, sval.data(), sval.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(S.col, scol.data(), scol.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if (!chunk.empty() &&
