@@ -40,6 +40,22 @@ MUTATIONS = {
     "robust_expected_drops_probability": ("for (uint32_t s = 0; s < S; ++s) F += prob[s] * f_s[s];",
                                           "for (uint32_t s = 0; s < S; ++s) F += f_s[s] / S;"),
     "robust_worst_takes_the_smallest": ("if (f_s[s] > f_s[best]) best = s;", "if (f_s[s] < f_s[best]) best = s;"),
+    "spmm_wrong_vector_stride": ("s += a[k] * X[(uint64_t)col[k] * nvec + v];", "s += a[k] * X[(uint64_t)col[k] + v];"),
+    "spmv_rows_ignores_selection": ("        uint32_t i = rows[t];", "        uint32_t i = (uint32_t)t;"),
+    "abs_adjoint_keeps_sign_of_r": ("g[col[k]] += fabs(a[k]) * fabs(r[i]);", "g[col[k]] += fabs(a[k]) * r[i];"),
+    "gradient_swaps_target_and_weight": ("double f = oracle_objective(nrows, d, p, w, r);",
+                                         "double f = oracle_objective(nrows, d, w, p, r);"),
+    "pg_ascends": ("double t = x[j] - eta * grad[j];", "double t = x[j] + eta * grad[j];"),
+    "power_iteration_unnormalised": ("for (uint32_t j = 0; j < ncols; ++j) v[j] /= nv;",
+                                     "for (uint32_t j = 0; j < ncols; ++j) v[j] /= 1.0;"),
+    "fp8_search_skips_largest_code": ("for (int c = 0; c < 0x7F; ++c) { /* 0x7F is NaN */",
+                                      "for (int c = 0; c < 0x7E; ++c) { /* 0x7F is NaN */"),
+    "fp8_rowscale_wrong_divisor": ("float s = rmax > 0.0 ? (float)(rmax / 448.0) : 1.0f;",
+                                   "float s = rmax > 0.0 ? (float)(rmax / 480.0) : 1.0f;"),
+    "robust_expected_gradient_of_first_scenario": ("for (uint32_t s = 0; s < S; ++s) t += prob[s] * g_s[(size_t)s * ncols + j];",
+                                                   "for (uint32_t s = 0; s < S; ++s) t += prob[s] * g_s[j];"),
+    "u16_decode_in_fp32": ("for (uint64_t k = 0; k < nnz; ++k) a[k] = (double)scale * (double)q[k];",
+                           "for (uint64_t k = 0; k < nnz; ++k) a[k] = (double)(scale * (float)q[k]);"),
     "u16_round_half_up": ("double t = nearbyint(v[k] / (double)s);", "double t = floor(v[k] / (double)s + 0.5);"),
     "u16_scale_off_by_one": ("float s = vmax > 0.0 ? (float)(vmax / 65535.0) : 1.0f;",
                              "float s = vmax > 0.0 ? (float)(vmax / 65536.0) : 1.0f;"),
