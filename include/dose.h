@@ -52,7 +52,7 @@ typedef enum {
 /* Stored value formats.  The paper stores 16-bit values (Sec. II-D), IEEE half
  * precision in its own kernel (Sec. III, Sec. IV "Half/double"):
  *   U16_SCALE        : uint16 code q, one FP32 scale s per matrix, a = s * q
- *   BF16             : bfloat16 bits, a = value
+ *   BF16             : bfloat16 bits, a = value (finite codes only)
  *   FP8E4M3_ROWSCALE : OCP FP8 E4M3 code q, one FP32 scale s_r per row, a = s_r * e4m3(q)
  *   F16              : IEEE 754 binary16 bits, a = value (finite codes only)
  *   F32              : IEEE 754 binary32 bits, a = value (finite only; the paper's "Single"

@@ -696,6 +696,13 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
                 std::memcpy(&h, vals.data() + 2 * k, 2);
                 if ((h & 0x7C00u) == 0x7C00u) return invalid("F16 value is infinite or NaN at entry " + std::to_string(k));
             }
+        if (fmt == DOSE_FMT_BF16)
+            for (uint64_t k = 0; k < nnz; ++k) {
+                uint16_t b;
+                std::memcpy(&b, vals.data() + 2 * k, 2);
+                if ((b & 0x7F80u) == 0x7F80u)
+                    return invalid("BF16 value is infinite or NaN at entry " + std::to_string(k));
+            }
         if (fmt == DOSE_FMT_F32)
             for (uint64_t k = 0; k < nnz; ++k) {
                 uint32_t w;

@@ -131,6 +131,56 @@ def test_create_rejects_invalid_csr_on_host(lib):
     assert lib.dose_spmv_batched(None, -1, None, None, 16, None) == 1
 
 
+def test_create_rejects_bad_descriptors_and_codes_on_host(lib):
+    """Every create-time check that needs no device: sizes, missing arrays,
+    flags, and non-finite codes or scales in each stored format."""
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    out = ctypes.c_void_p()
+    rp, col = arr([0, 2, 3], np.uint32), arr([0, 2, 1], np.uint32)
+    v64 = arr([0.5, 0.25, 1.0], np.float64)
+    base = dict(nrows=2, ncols=3, nnz=3, row_ptr=rp, col_idx=col)
+
+    def rejects(needle, flags=0, tuning=None, **kw):
+        d = _desc(**{**base, **kw})
+        st = lib.dose_create_matrix(ctypes.byref(d), flags, ctypes.byref(tuning) if tuning else None, None,
+                                    ctypes.byref(out))
+        msg = lib.dose_last_error().decode()
+        assert st == 1 and needle in msg, (needle, st, msg)
+        assert out.value is None
+
+    rejects("nnz must be < 2^32", nnz=1 << 32, fmt=0, values_f64=v64)
+    rejects("nrows must be < 2^32 - 1", nrows=0xFFFFFFFF, fmt=0, values_f64=v64)
+    rejects("row_ptr is NULL", row_ptr=None, fmt=0, values_f64=v64)
+    rejects("col_idx is NULL", col_idx=None, fmt=0, values_f64=v64)
+    rejects("values_f64 must be host memory", on_device=1, fmt=0, values_f64=v64)
+    rejects("neither values nor values_f64", fmt=0)
+    rejects("unknown format", fmt=9, values_f64=v64)
+    rejects("scales are NULL", fmt=0, values=arr([1, 2, 3], np.uint16))
+    rejects("scales are NULL", fmt=2, values=arr([1, 2, 3], np.uint8))
+    t = dose.Tuning(sell_sigma=(1 << 24) + 1)
+    rejects("sell_sigma", flags=dose.CREATE_SELL, tuning=t, fmt=0, values_f64=v64)
+    for bad in (0.0, -1.0, np.inf, np.nan):
+        rejects("scales must be finite and positive", fmt=0, values=arr([1, 2, 3], np.uint16),
+                scales=arr([bad], np.float32))
+        rejects("scales must be finite and positive", fmt=2, values=arr([1, 2, 3], np.uint8),
+                scales=arr([1.0, bad], np.float32))
+    rejects("FP8 code is NaN at entry 1", fmt=2, values=arr([0x38, 0xFF, 0x10], np.uint8),
+            scales=arr([1.0, 1.0], np.float32))
+    rejects("F16 value is infinite or NaN at entry 2", fmt=3, values=arr([0x3C00, 0x3800, 0x7C00], np.uint16))
+    rejects("BF16 value is infinite or NaN at entry 0", fmt=1, values=arr([0x7FC0, 0x3F80, 0x3F00], np.uint16))
+    rejects("BF16 value is infinite or NaN at entry 1", fmt=1, values=arr([0x3F80, 0xFF80, 0x3F00], np.uint16))
+    rejects("F32 value is infinite or NaN at entry 1", fmt=4,
+            values=arr(np.array([1.0, np.inf, 0.5], np.float32).view(np.uint32), np.uint32))
+    # the FP64-value path rejects what its encoders cannot represent
+    rejects("", fmt=0, values_f64=arr([0.5, np.nan, 1.0], np.float64))
+
+
 def test_multibeam_and_scenarios_reject_bad_arguments_on_host(lib):
     """dose_create_multibeam validates every beam on the host before merging;
     dose_create_scenarios rejects empty sets before touching a device."""
