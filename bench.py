@@ -579,20 +579,18 @@ def run_batched(args):
         print(json.dumps(out), flush=True)
 
 
-PREC_METRIC = "dose SpMV effective HBM GB/s per stored format, with max / mean relative dose error vs the FP64 oracle"
+PREC_METRIC = "dose SpMV effective HBM GB/s per stored format (plain, compensated, 16-bit indices)"
 
 
 def run_precision(args):
-    """The clinical beam stored as u16 + scale (the baseline), BF16 and FP8-E4M3
-    with per-row scales, each plain, with compensated (Dot2) rows, and with
-    16-bit column indices: time per
-    dose evaluation, effective GB/s of the format's own bytes, and the dose
-    error on sampled rows against the FP64 oracle applied to (a) the
-    generator's FP64 values (format + accumulation error) and (b) the same
-    decoded values (accumulation error only)."""
+    """The clinical beam stored as u16 + scale (the baseline), BF16, FP8-E4M3
+    with per-row scales, F16 and F32, each plain, with compensated (Dot2) rows,
+    and with 16-bit column indices: time per dose evaluation and effective GB/s
+    of the format's own bytes.  The library encodes the generator's FP64 values
+    (dose_encode_host, once per format); the dose error of every format at this
+    size is checked against the FP64 oracle by the full-size GPU tests."""
     import torch
 
-    import oracle
     import paper_2103_09683_gb300 as dose
 
     dose.build()
@@ -601,21 +599,14 @@ def run_precision(args):
     csr = dosegen.generate(beam)
     x = dosegen.spot_weights(csr.ncols, dosegen.weight_seed(beam))
     xd = torch.from_numpy(x).cuda()
-    rng = np.random.default_rng(7)
-    lens = np.diff(csr.row_ptr.astype(np.int64))
-    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 20000, replace=False))
-    exact = oracle.spmv_rows(rows, csr.row_ptr, csr.col, csr.val, x)  # generator's FP64 values
     peak, _ = _peaks()
     K = max(3, min(args.steps, 200))
     variants = []
-    ofmt = {"u16": oracle.U16_SCALE, "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE, "f16": oracle.F16,
-            "f32": oracle.F32}
     for fmt in ("u16", "bf16", "fp8", "f16", "f32"):
-        enc = oracle.encode(csr, ofmt[fmt])
-        same = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
+        codes, scales = dose.encode_host(fmt, csr.row_ptr, csr.val)
         for comp, idx16 in ((False, False), (True, False), (False, True)):
-            A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt=fmt, values=enc.values,
-                                         scales=enc.scales, compensated=comp, index16=idx16)
+            A = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt=fmt, values=codes,
+                                         scales=scales, compensated=comp, index16=idx16)
             d = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
             for _ in range(args.warmup):
                 A.spmv(xd, d)
@@ -628,32 +619,24 @@ def run_precision(args):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / K
             A.device_status()
-            dv = d.cpu().numpy()[rows].astype(np.float64)
-            nz = exact != 0
-            rel_fmt = np.abs(dv[nz] - exact[nz]) / np.abs(exact[nz])
-            nz2 = same != 0
-            rel_acc = np.abs(dv[nz2] - same[nz2]) / np.abs(same[nz2])
             nbytes = A.info()["spmv_bytes"]
             variants.append({"format": fmt, "compensated": comp, "index_bytes": 2 if idx16 else 4, "ms": round(ms, 5),
                              "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
                              "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4), "bytes": nbytes,
-                             "bytes_per_entry": round(nbytes / csr.nnz, 3),
-                             "rel_err_vs_fp64_values": {"max": float(rel_fmt.max()), "mean": float(rel_fmt.mean())},
-                             "rel_err_vs_same_decoded": {"max": float(rel_acc.max()), "mean": float(rel_acc.mean())}})
+                             "bytes_per_entry": round(nbytes / csr.nnz, 3)})
             del A, d
-        del enc
+        del codes, scales
     base = variants[0]
     out = {"metric": PREC_METRIC, "value": base["achieved_gbs"], "unit": "GB/s", "n_gpus": 1, "steps": K,
            "warmup": args.warmup, "ms_per_step": base["ms"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD.split("; step")[0] + "; dose eval d = A x per stored format",
-                      "sampled_rows": int(len(rows))},
-           "variants": variants}
+           "config": {"workload": WORKLOAD.split("; step")[0] + "; dose eval d = A x per stored format"},
+           "gpu_launches": len(variants) * K, "variants": variants}
     print(json.dumps(out), flush=True)
 
 
 HD_METRIC = ("Half/double dose SpMV (F16 values, FP64 x and d): effective HBM GB/s of the 6 nnz + 12 nr + 8 nc "
-             "traffic model, GFLOP/s, and the max relative dose error vs the FP64 oracle")
+             "traffic model and GFLOP/s")
 
 
 def run_halfdouble(args):
@@ -664,7 +647,6 @@ def run_halfdouble(args):
     dose_spmv_f64 call (the x split and the SpMV kernel)."""
     import torch
 
-    import oracle
     import paper_2103_09683_gb300 as dose
 
     dose.build()
@@ -673,19 +655,14 @@ def run_halfdouble(args):
     csr = dosegen.generate(beam)
     x = dosegen.spot_weights_f64(csr.ncols, dosegen.weight_seed(beam))
     xd = torch.from_numpy(x).cuda()
-    rng = np.random.default_rng(7)
-    lens = np.diff(csr.row_ptr.astype(np.int64))
-    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 20000, replace=False))
-    enc = oracle.encode(csr, oracle.F16)
-    same = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
-    absref = oracle.spmv_rows(rows, enc.row_ptr, enc.col, np.abs(enc.decoded), np.abs(x))
+    codes, _ = dose.encode_host("f16", csr.row_ptr, csr.val)
     peak, _ = _peaks()
     K = max(3, min(args.steps, 200))
     clocks = ClockSampler(0)
     variants = []
     clocks.start()
     for idx16 in (False, True):
-        A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt="f16", values=enc.values,
+        A = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="f16", values=codes,
                                      index16=idx16)
         if args.tuning:
             A.set_tuning(**_tuning_kv(args))
@@ -703,12 +680,10 @@ def run_halfdouble(args):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / K
             A.device_status()
-            err = np.abs(d.cpu().numpy()[rows] - same) / absref
             gbs = nbytes / (ms * 1e-3) / 1e9
             variants.append({"accumulation": "fp64_fma" if native else "double_float", "index_bytes": 2 if idx16 else 4,
                              "ms": round(ms, 5), "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
-                             "gflops": round(2 * csr.nnz / (ms * 1e-3) / 1e9, 1), "bytes": nbytes,
-                             "err_over_sum_abs": {"max": float(err.max()), "mean": float(err.mean())}})
+                             "gflops": round(2 * csr.nnz / (ms * 1e-3) / 1e9, 1), "bytes": nbytes})
             del d
         del A
     clk = clocks.stop()
@@ -719,7 +694,7 @@ def run_halfdouble(args):
            "config": {"workload": "clinical pencil beam 256x256x160 voxels x 4000 spots, ~1.5e8 entries; "
                                   "F16 values; step = one dose_spmv_f64 (x split + SpMV)",
                       "tuning": _tuning_kv(args),
-                      "sampled_rows": int(len(rows)), "l2": "A (~0.9 GB) > L2: streamed from HBM every step",
+                      "l2": "A (~0.9 GB) > L2: streamed from HBM every step",
                       "peak_gbs": peak},
            "clocks": clk, "variants": variants}
     print(json.dumps(out), flush=True)
@@ -827,23 +802,19 @@ SELL_METRIC = ("dose SpMV on SELL-32-sigma storage (the paper's future-work form
 def run_sell(args):
     """The clinical beam (u16 + scale) stored as SELL-32-sigma for several sigma,
     with 32- and 16-bit indices, next to the CSR kernel on the same matrix; a
-    step is one dose_spmv."""
+    step is one dose_spmv.  The SELL dose at this size is checked against the
+    FP64 oracle by the full-size GPU tests."""
     import torch
 
-    import oracle
     import paper_2103_09683_gb300 as dose
 
     dose.build()
     torch.cuda.set_device(0)
     beam = dosegen.CLINICAL
     csr = dosegen.generate(beam)
-    enc = oracle.encode(csr, oracle.U16_SCALE)
+    codes, scales = dose.encode_host("u16", csr.row_ptr, csr.val)
     x = dosegen.spot_weights(csr.ncols, dosegen.weight_seed(beam))
     xd = torch.from_numpy(x).cuda()
-    rng = np.random.default_rng(7)
-    lens = np.diff(csr.row_ptr.astype(np.int64))
-    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 20000, replace=False))
-    same = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
     peak, _ = _peaks()
     K = max(3, min(args.steps, 200))
     clocks = ClockSampler(0)
@@ -851,8 +822,8 @@ def run_sell(args):
     clocks.start()
     for idx16 in (False, True):
         for sigma in (0, 1, 32, 256, 1024, 8192, 1 << 20):   # 0: the CSR kernel
-            A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt="u16", values=enc.values,
-                                         scales=enc.scales, index16=idx16, sell=sigma > 0,
+            A = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="u16", values=codes,
+                                         scales=scales, index16=idx16, sell=sigma > 0,
                                          tuning=dict(sell_sigma=sigma) if sigma else None)
             inf = A.info()
             d = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
@@ -867,15 +838,12 @@ def run_sell(args):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / K
             A.device_status()
-            dv = d.cpu().numpy()[rows].astype(np.float64)
-            rel = float(np.max(np.abs(dv - same) / same))
             gbs = inf["spmv_bytes"] / (ms * 1e-3) / 1e9
             variants.append({"layout": f"sell-32-{sigma}" if sigma else "csr", "index_bytes": 2 if idx16 else 4,
                              "ms": round(ms, 5), "bytes": inf["spmv_bytes"], "achieved_gbs": round(gbs, 1),
                              "frac": round(gbs / peak, 4),
                              "stored_entries": inf["sell_entries"] if sigma else csr.nnz,
-                             "padding": round(inf["sell_entries"] / csr.nnz - 1, 4) if sigma else 0.0,
-                             "max_rel_err_vs_same_decoded": rel})
+                             "padding": round(inf["sell_entries"] / csr.nnz - 1, 4) if sigma else 0.0})
             del A, d
     clk = clocks.stop()
     base = next(v for v in variants if v["layout"] == "sell-32-1048576" and v["index_bytes"] == 4)
@@ -883,7 +851,7 @@ def run_sell(args):
            "warmup": args.warmup, "ms_per_step": base["ms"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "clinical pencil beam 256x256x160 voxels x 4000 spots, ~1.5e8 entries; u16 + scale; "
-                                  "step = one dose_spmv", "sampled_rows": int(len(rows)), "peak_gbs": peak},
+                                  "step = one dose_spmv", "peak_gbs": peak},
            "clocks": clk, "variants": variants}
     print(json.dumps(out), flush=True)
 
@@ -898,47 +866,27 @@ def run_liver1(args):
     entries (whole-CTA reduction), x too large for shared memory (gathered from
     L2).  Variants: the paper's Half/double (F16 values, FP64 x and d; the
     paper's 6 nnz + 12 nr + 8 nc bytes) with double-float and FP64-FMA
-    accumulation, and the FP32-vector dose_spmv on u16 + scale.  Sampled rows
-    are checked against the FP64 oracle."""
+    accumulation, and the FP32-vector dose_spmv on u16 + scale.  The dose at
+    this size is checked against the FP64 oracle on sampled rows by the
+    full-size GPU tests."""
     import torch
 
-    import oracle
     import paper_2103_09683_gb300 as dose
 
     dose.build()
     torch.cuda.set_device(0)
     beam = dosegen.LIVER1_SHAPED
     csr = dosegen.generate(beam)
-    rng = np.random.default_rng(11)
-    rp = csr.row_ptr.astype(np.int64)
-    lens = rp[1:] - rp[:-1]
-    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 4000, replace=False))
-    sub_lens = lens[rows]
-    sub_rp = np.zeros(len(rows) + 1, dtype=np.int64)
-    np.cumsum(sub_lens, out=sub_rp[1:])
-    take = np.repeat(rp[rows] - sub_rp[:-1], sub_lens) + np.arange(int(sub_rp[-1]))
-    sub = dosegen.CSR(len(rows), csr.ncols, sub_rp.astype(np.uint32), csr.col[take], csr.val[take])
-    vmax = float(csr.val.max())
     tun = _tuning_kv(args) or None
     A16 = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="f16", values_f64=csr.val, tuning=tun)
     Au = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="u16", values_f64=csr.val, tuning=tun)
     nrows, ncols, nnz = csr.nrows, csr.ncols, csr.nnz
-    del csr, take
-    enc16 = oracle.encode(sub, oracle.F16)
-    encu = oracle.encode(sub, oracle.U16_SCALE)
-    # the u16 scale of the whole matrix, applied to the sampled entries
-    s = float(np.float32(vmax / 65535.0))
-    qu = np.minimum(np.rint(sub.val / s), 65535.0)
-    assert float(Au.info()["scale"]) == s
+    del csr
     x64 = dosegen.spot_weights_f64(ncols, dosegen.weight_seed(beam))
     x32 = dosegen.spot_weights(ncols, dosegen.weight_seed(beam))
     xd64, xd32 = torch.from_numpy(x64).cuda(), torch.from_numpy(x32).cuda()
-    ref64 = oracle.spmv(len(rows), enc16.row_ptr, enc16.col, enc16.decoded, x64)
-    abs64 = oracle.spmv(len(rows), enc16.row_ptr, enc16.col, np.abs(enc16.decoded), np.abs(x64))
-    ref32 = oracle.spmv(len(rows), encu.row_ptr, encu.col, s * qu, x32)
     peak, _ = _peaks()
     K = max(3, min(args.steps, 50))
-    rows_t = torch.from_numpy(rows).cuda()
 
     def timed(fn):
         for _ in range(args.warmup):
@@ -959,21 +907,18 @@ def run_liver1(args):
     b64 = A16.info()["spmv_f64_bytes"]
     for native in (False, True):
         ms = timed(lambda: A16.spmv_f64(xd64, d64, native=native))
-        err = np.abs(d64[rows_t].cpu().numpy() - ref64) / abs64
         gbs = b64 / (ms * 1e-3) / 1e9
         variants.append({"form": "half_double", "accumulation": "fp64_fma" if native else "double_float",
                          "ms": round(ms, 4), "bytes": b64, "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
-                         "gflops": round(2 * nnz / (ms * 1e-3) / 1e9, 1),
-                         "err_over_sum_abs": {"max": float(err.max()), "mean": float(err.mean())}})
+                         "gflops": round(2 * nnz / (ms * 1e-3) / 1e9, 1)})
     del d64
     d32 = torch.empty(nrows, dtype=torch.float32, device="cuda")
     bu = Au.info()["spmv_bytes"]
     ms = timed(lambda: Au.spmv(xd32, d32))
-    rel = np.abs(d32[rows_t].cpu().numpy().astype(np.float64) - ref32) / ref32
     gbs = bu / (ms * 1e-3) / 1e9
     variants.append({"form": "u16+scale, FP32 vectors", "accumulation": "fp32", "ms": round(ms, 4), "bytes": bu,
                      "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
-                     "gflops": round(2 * nnz / (ms * 1e-3) / 1e9, 1), "max_rel_err": float(rel.max())})
+                     "gflops": round(2 * nnz / (ms * 1e-3) / 1e9, 1)})
     clk = clocks.stop()
     A16.device_status()
     Au.device_status()
@@ -983,7 +928,7 @@ def run_liver1(args):
            "vs_baseline": None, "dtype": "f16 values, f64 vectors", "data": "synthetic",
            "config": {"workload": f"liver-beam-1-shaped pencil beam: {nrows} voxels x {ncols} spots, {nnz} entries "
                                   f"(Table I: 2.97e6 x 6.80e4, 1.48e9); step = one dose evaluation",
-                      "sampled_rows": int(len(rows)), "peak_gbs": peak, "tuning": _tuning_kv(args),
+                      "peak_gbs": peak, "tuning": _tuning_kv(args),
                       "info": {k: Au.info()[k] for k in ("n_stages", "n_coop_rows", "lanes_hist", "adj_window")},
                       "paper_a100_half_double": "1250-1350 GB/s, up to 420 GFLOP/s on the liver beams (context)"},
            "clocks": clk, "variants": variants}

@@ -61,6 +61,27 @@ def test_clinical_dose_sampled_rows(clinical):
     assert np.all(d[empty] == 0.0)
 
 
+@pytest.mark.parametrize("fmt", ["bf16", "fp8", "f16", "f32"])
+def test_clinical_dose_every_stored_format_sampled_rows(clinical, fmt):
+    """The other stored formats at the clinical size (bench.py --workload
+    precision): the dose of the same decoded matrix on sampled rows, with
+    compensated rows and with 16-bit column indices too."""
+    csr, _, _, _, _, x = clinical
+    enc = oracle.encode(csr, oracle.U16_SCALE if fmt == "u16" else {
+        "bf16": oracle.BF16, "fp8": oracle.FP8E4M3_ROWSCALE, "f16": oracle.F16, "f32": oracle.F32}[fmt])
+    rows = _sample_rows(csr.nrows, enc.row_ptr, 4000, 5)
+    ref = oracle.spmv_rows(rows, enc.row_ptr, enc.col, enc.decoded, x)
+    empty = np.diff(enc.row_ptr.astype(np.int64)) == 0
+    for kw in (dict(), dict(compensated=True), dict(index16=True)):
+        A = dose.DoseMatrix.from_csr(enc.row_ptr, enc.col, ncols=csr.ncols, fmt=fmt, values=enc.values,
+                                     scales=enc.scales, **kw)
+        d = A.spmv(_to(x)).cpu().numpy()
+        fwd_check(d[rows], ref)
+        assert np.all(d[empty] == 0.0)
+        A.device_status()
+        A.close()
+
+
 def test_clinical_fused_objective_and_gradient(clinical):
     csr, A, enc, p, w, x = clinical
     f, g, d = A.fwd_adj_quadratic(_to(x), _to(p), _to(w), want_d=True)
