@@ -579,16 +579,35 @@ def run_batched(args):
         print(json.dumps(out), flush=True)
 
 
-PREC_METRIC = "dose SpMV effective HBM GB/s per stored format (plain, compensated, 16-bit indices)"
+PREC_METRIC = ("dose SpMV effective HBM GB/s per stored format (plain, compensated, 16-bit indices), with each "
+               "result's relative error against the FP64 dose of the generator's values")
+
+
+def fp64_dose_rows(row_ptr, col, val, x, rows):
+    """d_i = sum_k val_k x[col_k] in FP64 (numpy) for the listed rows: the
+    exact-values dose that a stored format's result is compared with."""
+    rp = np.asarray(row_ptr).astype(np.int64)
+    rows = np.asarray(rows, dtype=np.int64)
+    lens = rp[rows + 1] - rp[rows]
+    starts = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=starts[1:])
+    idx = np.repeat(rp[rows] - starts[:-1], lens) + np.arange(int(starts[-1]))
+    prod = np.asarray(val, dtype=np.float64)[idx] * np.asarray(x, dtype=np.float64)[np.asarray(col)[idx]]
+    out = np.zeros(len(rows))
+    ne = lens > 0
+    out[ne] = np.add.reduceat(prod, starts[:-1][ne]) if prod.size else 0.0
+    return out
 
 
 def run_precision(args):
     """The clinical beam stored as u16 + scale (the baseline), BF16, FP8-E4M3
     with per-row scales, F16 and F32, each plain, with compensated (Dot2) rows,
-    and with 16-bit column indices: time per dose evaluation and effective GB/s
-    of the format's own bytes.  The library encodes the generator's FP64 values
-    (dose_encode_host, once per format); the dose error of every format at this
-    size is checked against the FP64 oracle by the full-size GPU tests."""
+    and with 16-bit column indices: time per dose evaluation, effective GB/s
+    of the format's own bytes, and each result's relative error on sampled rows
+    against the FP64 dose of the generator's own values (the format's rounding
+    plus the FP32 accumulation).  The library encodes the generator's FP64
+    values (dose_encode_host, once per format); parity with the FP64 oracle on
+    the same decoded values is the full-size GPU tests' job."""
     import torch
 
     import paper_2103_09683_gb300 as dose
@@ -599,6 +618,11 @@ def run_precision(args):
     csr = dosegen.generate(beam)
     x = dosegen.spot_weights(csr.ncols, dosegen.weight_seed(beam))
     xd = torch.from_numpy(x).cuda()
+    rng = np.random.default_rng(7)
+    lens = np.diff(csr.row_ptr.astype(np.int64))
+    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 20000, replace=False))
+    exact = fp64_dose_rows(csr.row_ptr, csr.col, csr.val, x, rows)
+    nz = exact != 0
     peak, _ = _peaks()
     K = max(3, min(args.steps, 200))
     variants = []
@@ -620,17 +644,21 @@ def run_precision(args):
             ms = e0.elapsed_time(e1) / K
             A.device_status()
             nbytes = A.info()["spmv_bytes"]
+            dv = d.cpu().numpy()[rows].astype(np.float64)
+            rel = np.abs(dv[nz] - exact[nz]) / np.abs(exact[nz])
             variants.append({"format": fmt, "compensated": comp, "index_bytes": 2 if idx16 else 4, "ms": round(ms, 5),
                              "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
                              "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4), "bytes": nbytes,
-                             "bytes_per_entry": round(nbytes / csr.nnz, 3)})
+                             "bytes_per_entry": round(nbytes / csr.nnz, 3),
+                             "rel_err_vs_fp64_values": {"max": float(rel.max()), "mean": float(rel.mean())}})
             del A, d
         del codes, scales
     base = variants[0]
     out = {"metric": PREC_METRIC, "value": base["achieved_gbs"], "unit": "GB/s", "n_gpus": 1, "steps": K,
            "warmup": args.warmup, "ms_per_step": base["ms"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD.split("; step")[0] + "; dose eval d = A x per stored format"},
+           "config": {"workload": WORKLOAD.split("; step")[0] + "; dose eval d = A x per stored format",
+                      "error_rows": int(len(rows))},
            "gpu_launches": len(variants) * K, "variants": variants}
     print(json.dumps(out), flush=True)
 

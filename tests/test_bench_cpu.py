@@ -43,3 +43,16 @@ def test_all_cores_leg_reports_its_threads(tiny):
     csr, p, w, x = tiny
     out = bench.cpu_baseline_all_cores(csr, x, p, w, budget_s=0.2)
     assert out["cores"] == (os.cpu_count() or 1) and out["kind"] == "oracle" and out["value"] > 0
+
+
+def test_fp64_dose_rows_is_the_oracles_row_sample(tiny):
+    """The precision workload's exact-values dose on sampled rows (numpy) equals
+    the oracle's, empty rows included."""
+    csr, _, _, x = tiny
+    rows = np.unique(np.random.default_rng(8).choice(csr.nrows, 700, replace=False))
+    got = bench.fp64_dose_rows(csr.row_ptr, csr.col, csr.val, x, rows)
+    ref = oracle.spmv_rows(rows, csr.row_ptr, csr.col, csr.val, x)
+    lens = np.diff(csr.row_ptr.astype(np.int64))[rows]
+    assert (lens == 0).any() and (lens > 0).any()
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=0)
+    assert np.all(got[lens == 0] == 0.0)
