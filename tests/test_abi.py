@@ -210,3 +210,23 @@ def test_multibeam_and_scenarios_reject_bad_arguments_on_host(lib):
     assert lib.dose_create_scenarios(None, 0, None, ctypes.byref(out)) == 1
     assert lib.dose_robust_quadratic(None, 0, None, None, None, None, None, None, None) == 1
     assert lib.dose_robust_pg_step(None, 0, None, None, None, ctypes.c_float(-1.0), None, None, None) == 1
+
+
+def test_binding_has_no_cpu_path(lib, monkeypatch):
+    """Host tensors are refused before any library call, and a missing
+    libdose.so is an error: nothing computes on the CPU."""
+    import torch
+
+    A = dose.DoseMatrix(0, 8, 4, 0, "u16")  # a null handle: no call may reach the library
+    x, v8 = torch.zeros(4), torch.zeros(8)
+    calls = [lambda: A.spmv(x), lambda: A.spmv_f64(x.double()), lambda: A.adjoint(v8),
+             lambda: A.fwd_adj_quadratic(x, v8, v8), lambda: A.pg_step(x, v8, v8, 0.1),
+             lambda: dose.spmv_batched([A], [x.reshape(4, 1)])]
+    for call in calls:
+        with pytest.raises(TypeError, match="CUDA tensor"):
+            call()
+    A.close()
+    monkeypatch.setattr(dose, "_lib", None)
+    monkeypatch.setattr(dose._build, "LIB", "/nonexistent/libdose.so")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        dose.load()
