@@ -566,6 +566,7 @@ class PGSolver:
         torch = _torch()
         self.A, self.x, self.p, self.w, self.eta, self.iters = A, x, p, w, float(eta), int(iters)
         self.f_hist = torch.zeros(self.iters, dtype=torch.float64, device=x.device)
+        self.steps_done = 0
         self.graph = None
         if use_graph:
             s = torch.cuda.Stream()
@@ -585,7 +586,41 @@ class PGSolver:
             self.graph.replay()
         else:
             self._enqueue(None)
+        self.steps_done += self.iters
         return self.f_hist
+
+    def checkpoint(self, path: str):
+        """Save the optimiser state (x, steps done, eta, the last run's f) to an .npz."""
+        save_pg_state(path, self.x, self.steps_done, self.eta, self.f_hist)
+
+    def resume(self, path: str):
+        """Load a checkpoint into this solver: x is overwritten in place (the
+        captured graph keeps pointing at it); returns the steps done."""
+        self.steps_done, _ = load_pg_state(path, self.x, self.eta)
+        return self.steps_done
+
+
+def save_pg_state(path: str, x, steps_done: int, eta: float, f_hist=None):
+    """Projected-gradient state as an .npz: x (float32), the number of steps
+    done, the step size and the f values of the last run (float64)."""
+    xs = x.detach().to("cpu").numpy().astype(np.float32, copy=True)
+    fh = (f_hist.detach().to("cpu").numpy().astype(np.float64, copy=True) if f_hist is not None
+          else np.zeros(0, dtype=np.float64))
+    np.savez(path, x=xs, steps_done=np.int64(steps_done), eta=np.float64(eta), f_hist=fh)
+
+
+def load_pg_state(path: str, x, eta: float | None = None):
+    """Copy a saved x into the tensor x (same length, in place) and return
+    (steps done, f history).  With eta given, the saved step size must match."""
+    with np.load(path) as z:
+        xs, steps, eta0, fh = z["x"], int(z["steps_done"]), float(z["eta"]), z["f_hist"]
+    if xs.size != x.numel():
+        raise ValueError(f"checkpoint has {xs.size} spot weights, x has {x.numel()}")
+    if eta is not None and float(eta) != eta0:
+        raise ValueError(f"checkpoint was taken with eta = {eta0}, not {eta}")
+    torch = _torch()
+    x.copy_(torch.from_numpy(xs).to(x.device, x.dtype).reshape(x.shape))
+    return steps, fh
 
 
 def pg_solve(A: DoseMatrix, x, p, w, eta: float, iters: int = 100, use_graph: bool = True):
