@@ -140,6 +140,23 @@ typedef struct {
     uint32_t adj_row_order;     /* the same for the adjoint schedule */
     uint32_t sell_sigma;        /* DOSE_CREATE_SELL: rows per sorting window (1 = no sorting;
                                    default 2^20); read at create only */
+    /* layout of the adjoint and fused objective passes (read at create; later calls may
+       switch between the layouts that were built):
+         0 = row groups where they apply, else CSR (default);
+         1 = CSR (per-row scatter; the row-group layout is not built);
+         2 = row groups (create fails with DOSE_ERR_UNSUPPORTED if they do not apply).
+       Row groups: up to four consecutive non-empty rows share one list of the union of
+       their columns, with the four rows' values stored side by side (stored zeros where
+       a row has no entry); built when no row has more than 4096 entries.  The union
+       order is chosen per group (shared-memory banks), so these passes sum a row's terms
+       in another order than dose_spmv.  A non-finite x_j or residual reaches every row
+       of a group whose union holds column j (0 * inf), not only the rows that store j. */
+    uint32_t adj_layout;
+    uint32_t rg_tile_union;     /* row groups: union columns per pipeline stage (512..8192; default
+                                   by format, about 24 KB of columns and values) */
+    uint32_t rg_tile_rows;      /* row groups: rows per stage (256..8192) */
+    uint32_t rg_stages;         /* row groups: pipeline depth (2..8) */
+    uint32_t rg_warps;          /* row groups: worker warps (1..16; 0 = as many as fit) */
 } dose_tuning;
 
 typedef struct {
@@ -167,6 +184,14 @@ typedef struct {
                                    arrays */
     float scale;                /* U16: the matrix scale s; else 0 */
     dose_tuning tuning;         /* the knobs in effect */
+    uint32_t adj_layout_fused;  /* layout the fused pass runs on: 1 = CSR, 2 = row groups, 0 = none fits */
+    uint32_t adj_layout_adjoint;/* ... dose_adjoint */
+    uint64_t rg_groups;         /* row groups built (0: the layout was not built) */
+    uint64_t rg_union_entries;  /* union columns of all groups (values stored: 4 per union column) */
+    uint32_t rg_window;         /* columns of each CTA's gradient window on the row-group layout */
+    uint32_t rg_warps_fused;    /* worker warps of the row-group fused pass (0 if it does not fit) */
+    uint32_t rg_index_bytes;    /* bytes per union column index (2 when ncols <= 65536, else 4) */
+    uint32_t rg_pad;
 } dose_info;
 
 /* Build a matrix handle: validate the CSR on the host (or on the device for
@@ -214,7 +239,8 @@ dose_status dose_spmv_batched(const dose_matrix* const* A, int count, const floa
 
 /* g = A^T r, the adjoint (gradient of any dose objective with dD/dd = r).
  * r: device, nrows floats, 16-byte aligned.  g: device, ncols floats.  Deterministic: per-warp
- * private accumulators combined in a fixed order, no atomics on values. */
+ * private accumulators combined in a fixed order, no atomics on values.  Runs on the
+ * row-group layout when the handle has it (dose_tuning.adj_layout), else on the CSR arrays. */
 dose_status dose_adjoint(const dose_matrix* A, const float* r, float* g, void* stream);
 
 /* One pass over A of the quadratic dose objective

@@ -62,7 +62,9 @@ class Tuning(ctypes.Structure):
                 ("adj_stages", ctypes.c_uint32), ("adj_forward_warps", ctypes.c_uint32),
                 ("adj_scatter_warps", ctypes.c_uint32), ("adj_l2_prefetch", ctypes.c_uint32),
                 ("row_order", ctypes.c_uint32), ("adj_row_order", ctypes.c_uint32),
-                ("sell_sigma", ctypes.c_uint32)]
+                ("sell_sigma", ctypes.c_uint32),
+                ("adj_layout", ctypes.c_uint32), ("rg_tile_union", ctypes.c_uint32),
+                ("rg_tile_rows", ctypes.c_uint32), ("rg_stages", ctypes.c_uint32), ("rg_warps", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -79,7 +81,11 @@ class _Info(ctypes.Structure):
                 ("fwd_window", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("spmv_bytes", ctypes.c_uint64),
                 ("adjoint_bytes", ctypes.c_uint64), ("fused_bytes", ctypes.c_uint64), ("spmv_f64_bytes", ctypes.c_uint64),
                 ("sell_entries", ctypes.c_uint64),
-                ("scale", ctypes.c_float), ("tuning", Tuning)]
+                ("scale", ctypes.c_float), ("tuning", Tuning),
+                ("adj_layout_fused", ctypes.c_uint32), ("adj_layout_adjoint", ctypes.c_uint32),
+                ("rg_groups", ctypes.c_uint64), ("rg_union_entries", ctypes.c_uint64),
+                ("rg_window", ctypes.c_uint32), ("rg_warps_fused", ctypes.c_uint32),
+                ("rg_index_bytes", ctypes.c_uint32), ("rg_pad", ctypes.c_uint32)]
 
 
 _lib = None

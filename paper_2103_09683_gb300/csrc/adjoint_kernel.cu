@@ -462,6 +462,7 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
                            const float* r, float* d, double* f, float* g, float* x_update, float eta,
                            cudaStream_t s) {
     const bool quad = mode == ADJ_MODE_QUADRATIC;
+    if (rg_active(A, quad)) return launch_rg(A, mode, x, p, w, r, d, f, g, x_update, eta, s);
     AdjTuning t;
     size_t smem = 0;
     if (!adjoint_shape(A, A->adj_tuning, quad, &t, &smem)) return cudaErrorInvalidConfiguration;
@@ -529,11 +530,17 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
         }
         if (e != cudaSuccess) return e;
     }
-    const uint32_t nparts = A->nrows > 0 ? A->adj.grid : 0;
+    return launch_adjoint_finalize(A, A->g_part, A->adj.wlo, A->adj.wwidth, A->nrows > 0 ? A->adj.grid : 0, quad, g,
+                                   f, x_update, eta, s);
+}
+
+cudaError_t launch_adjoint_finalize(const dose_matrix* A, const float* g_part, const uint32_t* wlo, uint32_t wwidth,
+                                    uint32_t nparts, bool quad, float* g, double* f, float* x_update, float eta,
+                                    cudaStream_t s) {
     const float scale = A->fmt == DOSE_FMT_U16_SCALE ? A->scale : 1.0f;
     const uint32_t blocks = A->ncols ? (A->ncols + 31) / 32 : 1;
-    adjoint_finalize<<<blocks, 256, 0, s>>>(A->g_part, A->adj.wlo, A->adj.wwidth, A->f_part, nparts, A->ncols,
-                                            scale, g, quad ? f : nullptr, x_update, eta);
+    adjoint_finalize<<<blocks, 256, 0, s>>>(g_part, wlo, wwidth, A->f_part, nparts, A->ncols, scale, g,
+                                            quad ? f : nullptr, x_update, eta);
     return cudaGetLastError();
 }
 

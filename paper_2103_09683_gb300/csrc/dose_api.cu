@@ -181,6 +181,82 @@ static uint32_t nearest_pow2_log2(double v) {
     return (uint32_t)std::min(5, std::max(0, lg));
 }
 
+// Deal work items (ranges of S.desc) to the grid's CTAs and store the
+// descriptors CTA by CTA.  Without windows: round-robin in matrix order.  With
+// windows: items with entries are sorted by lowest column and cut into G groups
+// of equal estimated cost; group g is dealt round-robin, in matrix order, to
+// its own grid/G CTAs.  A CTA's window then spans one group's columns (for a
+// pencil beam: one lateral band plus the spot footprint), while round-robin
+// inside the group mixes long and short rows as evenly as dealing over the
+// whole matrix does.  Items without entries (blocks of empty rows: cheap in
+// bytes, but each costs a ring round trip) are dealt round-robin over all CTAs.
+// Each CTA runs its items in matrix order, so the blocks in flight at any time
+// lie close together in HBM.  align_wlo: windows start on a multiple of 32
+// columns (a column then falls in shared-memory bank c mod 32 in every CTA).
+void deal_items(Schedule& S, const std::vector<DealItem>& items, uint32_t grid, uint32_t ncols, bool windowed,
+                bool align_wlo) {
+    const uint32_t n = (uint32_t)S.desc.size();
+    std::vector<std::vector<uint32_t>> per(grid);
+    S.wlo.assign(grid, 0);
+    const uint32_t ncols_pad = (ncols + 31) / 32 * 32;
+    S.wwidth = ncols_pad;
+    if (!windowed) {
+        for (size_t i = 0; i < items.size(); ++i)
+            for (uint32_t k = items[i].s; k < items[i].e; ++k) per[i % grid].push_back(k);
+    } else {
+        std::vector<uint32_t> order, empties;
+        for (uint32_t i = 0; i < items.size(); ++i) (items[i].lo <= items[i].hi ? order : empties).push_back(i);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](uint32_t a, uint32_t b) { return items[a].lo < items[b].lo; });
+        uint64_t total = 0;
+        for (uint32_t i : order) total += items[i].cost;
+        const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(kAdjColumnGroups, grid));
+        std::vector<std::vector<uint32_t>> group(G);
+        uint64_t acc = 0;
+        uint32_t gi = 0;
+        for (uint32_t i : order) {
+            while (gi + 1 < G && acc * G >= total * (gi + 1)) ++gi;  // group gi holds its share
+            group[gi].push_back(i);
+            acc += items[i].cost;
+        }
+        std::vector<uint32_t> lo(grid, 0xFFFFFFFFu), hi(grid, 0);
+        std::vector<std::vector<uint32_t>> mine(grid);
+        for (uint32_t g = 0; g < G; ++g) {
+            const uint32_t c0 = (uint32_t)((uint64_t)grid * g / G), c1 = (uint32_t)((uint64_t)grid * (g + 1) / G);
+            std::sort(group[g].begin(), group[g].end());
+            for (size_t k = 0; k < group[g].size(); ++k) {
+                const uint32_t c = c0 + (uint32_t)(k % (c1 - c0)), i = group[g][k];
+                mine[c].push_back(i);
+                lo[c] = std::min(lo[c], items[i].lo);
+                hi[c] = std::max(hi[c], items[i].hi);
+            }
+        }
+        for (size_t k = 0; k < empties.size(); ++k) mine[k % grid].push_back(empties[k]);
+        if (align_wlo)
+            for (uint32_t k = 0; k < grid; ++k)
+                if (lo[k] <= hi[k]) lo[k] &= ~31u;
+        uint32_t width = 0;
+        for (uint32_t k = 0; k < grid; ++k) {
+            std::sort(mine[k].begin(), mine[k].end());
+            for (uint32_t i : mine[k])
+                for (uint32_t d = items[i].s; d < items[i].e; ++d) per[k].push_back(d);
+            if (lo[k] <= hi[k]) width = std::max(width, hi[k] - lo[k] + 1);
+        }
+        S.wwidth = std::max<uint32_t>(32, std::min(ncols_pad, (width + 31) / 32 * 32));
+        for (uint32_t k = 0; k < grid; ++k) S.wlo[k] = lo[k] <= hi[k] ? lo[k] : 0;
+    }
+    // Store the descriptors CTA by CTA, so each CTA reads one contiguous range.
+    std::vector<StageDesc> sorted;
+    sorted.reserve(n);
+    S.cta_begin.assign(grid + 1, 0);
+    for (uint32_t c = 0; c < grid; ++c) {
+        S.cta_begin[c] = (uint32_t)sorted.size();
+        for (uint32_t k : per[c]) sorted.push_back(S.desc[k]);
+    }
+    S.cta_begin[grid] = (uint32_t)sorted.size();
+    S.desc.swap(sorted);
+}
+
 // Column windows: rcmin / rcmax give each row's lowest and highest column (null
 // for a schedule without windows, which deals round-robin).  vbytes: stored bytes per
 // entry (value + column index), used to balance the CTAs' HBM traffic.  tight:
@@ -264,19 +340,15 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
 
     // Work items: a NORMAL stage, or the consecutive chunks of one long row.
     const uint32_t n = (uint32_t)S.desc.size();
-    struct Item {
-        uint32_t s, e;       // descriptors [s, e)
-        uint32_t lo, hi;     // column range (lo > hi: no entries)
-        uint64_t cost;       // HBM bytes (entries, row pointers, two per-row vectors)
-                             // + for the adjoint, a share per 128-entry step of each row
-    };
-    std::vector<Item> items;
+    std::vector<DealItem> items;
     for (uint32_t s = 0; s < n;) {
         uint32_t e = s + 1;
         if (S.desc[s].meta & STAGE_COOP)
             while (e < n && (S.desc[e].meta & STAGE_COOP) && !(S.desc[e].meta & STAGE_FIRST)) ++e;
-        Item it{s, e, 0xFFFFFFFFu, 0u, 0};
+        DealItem it{s, e, 0xFFFFFFFFu, 0u, 0};
         const uint32_t r0 = S.desc[s].row0, r1 = S.desc[e - 1].row1;
+        // HBM bytes (entries, row pointers, two per-row vectors) + for the
+        // adjoint, a share per 128-entry step of each row
         it.cost = (uint64_t)vbytes * (rp[r1] - rp[r0]) + 12ull * (r1 - r0);
         if (rcmin)
             for (uint32_t r = r0; r < r1; ++r)
@@ -289,73 +361,7 @@ static Schedule build_schedule(const std::vector<uint32_t>& rp, uint32_t nrows, 
         items.push_back(it);
         s = e;
     }
-    std::vector<std::vector<uint32_t>> per(grid);
-    S.wlo.assign(grid, 0);
-    const uint32_t ncols_pad = (ncols + 31) / 32 * 32;
-    S.wwidth = ncols_pad;
-    if (!rcmin) {
-        // round-robin, in matrix order
-        for (size_t i = 0; i < items.size(); ++i)
-            for (uint32_t k = items[i].s; k < items[i].e; ++k) per[i % grid].push_back(k);
-    } else {
-        // Items with entries are sorted by lowest column and cut into G groups of
-        // equal estimated cost; group g is dealt round-robin, in matrix order, to
-        // its own grid/G CTAs.  A CTA's window then spans one group's columns
-        // (for a pencil beam: one lateral band plus the spot footprint), while
-        // round-robin inside the group mixes long and short rows as evenly as
-        // dealing over the whole matrix does.  Items without entries (blocks of
-        // empty rows: cheap in bytes, but each costs a ring round trip) are
-        // dealt round-robin over all CTAs.  Each CTA runs its items in matrix
-        // order, so the blocks in flight at any time lie close together in HBM.
-        std::vector<uint32_t> order, empties;
-        for (uint32_t i = 0; i < items.size(); ++i) (items[i].lo <= items[i].hi ? order : empties).push_back(i);
-        std::stable_sort(order.begin(), order.end(),
-                         [&](uint32_t a, uint32_t b) { return items[a].lo < items[b].lo; });
-        uint64_t total = 0;
-        for (uint32_t i : order) total += items[i].cost;
-        const uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(kAdjColumnGroups, grid));
-        std::vector<std::vector<uint32_t>> group(G);
-        uint64_t acc = 0;
-        uint32_t gi = 0;
-        for (uint32_t i : order) {
-            while (gi + 1 < G && acc * G >= total * (gi + 1)) ++gi;  // group gi holds its share
-            group[gi].push_back(i);
-            acc += items[i].cost;
-        }
-        std::vector<uint32_t> lo(grid, 0xFFFFFFFFu), hi(grid, 0);
-        std::vector<std::vector<uint32_t>> mine(grid);
-        for (uint32_t g = 0; g < G; ++g) {
-            const uint32_t c0 = (uint32_t)((uint64_t)grid * g / G), c1 = (uint32_t)((uint64_t)grid * (g + 1) / G);
-            std::sort(group[g].begin(), group[g].end());
-            for (size_t k = 0; k < group[g].size(); ++k) {
-                const uint32_t c = c0 + (uint32_t)(k % (c1 - c0)), i = group[g][k];
-                mine[c].push_back(i);
-                lo[c] = std::min(lo[c], items[i].lo);
-                hi[c] = std::max(hi[c], items[i].hi);
-            }
-        }
-        for (size_t k = 0; k < empties.size(); ++k) mine[k % grid].push_back(empties[k]);
-        for (uint32_t k = 0; k < grid; ++k) {
-            std::sort(mine[k].begin(), mine[k].end());
-            for (uint32_t i : mine[k])
-                for (uint32_t d = items[i].s; d < items[i].e; ++d) per[k].push_back(d);
-        }
-        uint32_t width = 0;
-        for (uint32_t k = 0; k < grid; ++k)
-            if (lo[k] <= hi[k]) width = std::max(width, hi[k] - lo[k] + 1);
-        S.wwidth = std::max<uint32_t>(32, std::min(ncols_pad, (width + 31) / 32 * 32));
-        for (uint32_t k = 0; k < grid; ++k) S.wlo[k] = lo[k] <= hi[k] ? lo[k] : 0;
-    }
-    // Store the descriptors CTA by CTA, so each CTA reads one contiguous range.
-    std::vector<StageDesc> sorted;
-    sorted.reserve(n);
-    S.cta_begin.assign(grid + 1, 0);
-    for (uint32_t c = 0; c < grid; ++c) {
-        S.cta_begin[c] = (uint32_t)sorted.size();
-        for (uint32_t k : per[c]) sorted.push_back(S.desc[k]);
-    }
-    S.cta_begin[grid] = (uint32_t)sorted.size();
-    S.desc.swap(sorted);
+    deal_items(S, items, grid, ncols, rcmin != nullptr, false);
     return S;
 }
 
@@ -375,6 +381,7 @@ static void free_dev_schedule(DevSchedule& D) {
 }
 
 static void free_all(dose_matrix* A) {
+    free_row_groups(A);
     free_dev_schedule(A->fwd);
     free_dev_schedule(A->fwd64);
     free_dev_schedule(A->adj);
@@ -428,6 +435,12 @@ static dose_status check_adj_tuning(const AdjTuning& t) {
     if (t.row_order < 1 || t.row_order > 2) return invalid("tuning.adj_row_order must be 1 or 2");
     if (t.scatter_warps > kMaxAdjWarps - 2)
         return invalid("tuning.adj_scatter_warps must be in [0, " + std::to_string(kMaxAdjWarps - 2) + "]");
+    if (t.layout > 2) return invalid("tuning.adj_layout must be 0, 1 or 2");
+    if (t.rg_tile_u && (t.rg_tile_u < 256 || t.rg_tile_u > 8192))
+        return invalid("tuning.rg_tile_union must be in [256, 8192]");
+    if (t.rg_tile_rows < 256 || t.rg_tile_rows > 8192) return invalid("tuning.rg_tile_rows must be in [256, 8192]");
+    if (t.rg_stages < 2 || t.rg_stages > 8) return invalid("tuning.rg_stages must be in [2, 8]");
+    if (t.rg_warps > kRgMaxWarps) return invalid("tuning.rg_warps must be in [0, " + std::to_string(kRgMaxWarps) + "]");
     return DOSE_OK;
 }
 
@@ -448,6 +461,11 @@ static void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
     if (in->adj_l2_prefetch) a.l2_prefetch = in->adj_l2_prefetch >= 32 ? 0 : in->adj_l2_prefetch;
     if (in->row_order) t.row_order = in->row_order;
     if (in->adj_row_order) a.row_order = in->adj_row_order;
+    if (in->adj_layout) a.layout = in->adj_layout;
+    if (in->rg_tile_union) a.rg_tile_u = in->rg_tile_union;
+    if (in->rg_tile_rows) a.rg_tile_rows = in->rg_tile_rows;
+    if (in->rg_stages) a.rg_stages = in->rg_stages;
+    if (in->rg_warps) a.rg_warps = in->rg_warps;
     if (!in->coop_nnz) t.coop_nnz = std::min(t.coop_nnz, t.tile_nnz);  // the default follows a smaller tile
 }
 
@@ -467,6 +485,11 @@ static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out)
     out->adj_l2_prefetch = a.l2_prefetch ? a.l2_prefetch : 32;
     out->row_order = t.row_order;
     out->adj_row_order = a.row_order;
+    out->adj_layout = a.layout;
+    out->rg_tile_union = a.rg_tile_u;
+    out->rg_tile_rows = a.rg_tile_rows;
+    out->rg_stages = a.rg_stages;
+    out->rg_warps = a.rg_warps;
 }
 
 template <class T>
@@ -819,7 +842,34 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
             return fail(e, "SELL copy");
         }
     }
-    A->device_bytes = A->sell.bytes + rp_alloc * 4 + col_alloc * 4 + ((flags & DOSE_CREATE_U16_INDEX) ? col16_alloc * 2 : 0) + val_alloc +
+    // Row-group layout of the adjoint and fused passes (unless the caller asked for CSR).
+    if (A->adj_tuning.layout != 1) {
+        std::string why;
+        A->rg.sched.grid = A->adj.grid;
+        bool ok = build_row_groups(A.get(), A->host_row_ptr.data(), col.data(), vals.data(), &why, &e);
+        if (!ok && e != cudaSuccess) return fail(e, "row-group layout");
+        if (ok) {
+            e = rg_schedule(A.get(), A->adj_tuning);
+            if (e == cudaErrorInvalidValue) {
+                why = "tuning.rg_tile_union is smaller than a group's union of columns";
+                free_row_groups(A.get());
+                ok = false;
+                if (A->adj_tuning.layout == 2) {
+                    free_all(A.get());
+                    return invalid(why);
+                }
+            } else if (e != cudaSuccess) {
+                return fail(e, "row-group schedule");
+            }
+        }
+        if (A->adj_tuning.layout == 2 && !(ok && rg_active(A.get(), false))) {
+            free_all(A.get());
+            set_error("adj_layout = 2: the row-group layout does not apply" + (why.empty() ? std::string() : ": " + why));
+            return DOSE_ERR_UNSUPPORTED;
+        }
+    }
+    A->device_bytes = A->rg.bytes + (A->rg.built ? (A->rg.host.size() + 1) * 16 + schedule_bytes(A->rg.sched) : 0) +
+                      A->sell.bytes + rp_alloc * 4 + col_alloc * 4 + ((flags & DOSE_CREATE_U16_INDEX) ? col16_alloc * 2 : 0) + val_alloc +
                       (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) + x64_alloc * 8 +
                       (size_t)A->adj.grid * ncols_pad * 4 + (size_t)A->adj.grid * 8 + 4 + schedule_bytes(A->fwd) +
                       schedule_bytes(A->adj) + (A->fwd64_own ? schedule_bytes(A->fwd64) : 0);
@@ -933,6 +983,10 @@ dose_status dose_spmv_f64(const dose_matrix* A, const double* x, double* d, unsi
 
 namespace dose {
 dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* const* vecs, int nvec) {
+    for (int k = 0; k < nvec; ++k)
+        if (vecs[k] && (reinterpret_cast<uintptr_t>(vecs[k]) & 15u))
+            return invalid("per-row vectors (p, w, r) must be 16-byte aligned");
+    if (rg_active(A, quad)) return DOSE_OK;
     if (quad && A->adj.wwidth > kXSmemMaxCols) {
         set_error("the fused objective pass keeps each CTA's window of x in shared memory: the column window (" +
                   std::to_string(A->adj.wwidth) + ") must be <= 16384");
@@ -1050,6 +1104,27 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     out->scale = A->fmt == DOSE_FMT_U16_SCALE ? A->scale : 0.f;
     export_tuning(A->fwd.tuning, A->adj_tuning, &out->tuning);
     out->tuning.sell_sigma = A->sell.sigma;
+    out->adj_layout_fused = out->adj_block_fused ? 1 : 0;
+    out->adj_layout_adjoint = out->adj_block_adjoint ? 1 : 0;
+    if (A->rg.built) {
+        out->rg_groups = A->rg.host.size();
+        out->rg_union_entries = A->rg.n_union;
+        out->rg_window = A->rg.sched.wwidth;
+        out->rg_index_bytes = A->rg.iw;
+        out->tuning.rg_tile_union = A->rg.tile_u;
+        size_t smem = 0;
+        out->rg_warps_fused = rg_shape(A, A->adj_tuning, true, &smem);
+        if (rg_active(A, true)) {
+            out->adj_layout_fused = 2;
+            out->adj_block_fused = 32 * (1 + out->rg_warps_fused);
+            out->fused_bytes = rg_fused_bytes(A, false);
+        }
+        if (rg_active(A, false)) {
+            out->adj_layout_adjoint = 2;
+            out->adj_block_adjoint = 32 * (1 + rg_shape(A, A->adj_tuning, false, &smem));
+            out->adjoint_bytes = rg_adjoint_bytes(A);
+        }
+    }
     return DOSE_OK;
 }
 
@@ -1066,7 +1141,18 @@ dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning) {
     st = apply_schedule(A, A->fwd, t, A->fwd_windowed);
     if (st == DOSE_OK && A->fwd64_own) st = apply_schedule(A, A->fwd64, t, false);
     if (st != DOSE_OK) return st;
+    if (at.layout == 2 && !A->rg.built) return invalid("adj_layout = 2: the handle has no row-group layout");
+    const AdjTuning old_at = A->adj_tuning;
     A->adj_tuning = at;
+    if (A->rg.built && (at.rg_tile_u != old_at.rg_tile_u || at.rg_tile_rows != old_at.rg_tile_rows)) {
+        e = rg_schedule(A, at);
+        if (e == cudaErrorInvalidValue) {
+            A->adj_tuning = old_at;
+            rg_schedule(A, old_at);
+            return invalid("tuning.rg_tile_union is smaller than a group's union of columns");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "row-group schedule");
+    }
     return apply_schedule(A, A->adj, adj_schedule_tuning(t, at), true);
 }
 
@@ -1195,7 +1281,11 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
     cudaFree(g);
     cudaFree(f);
     if (result != DOSE_OK) return result;
-    if (best) export_tuning(A->fwd.tuning, A->adj_tuning, best);
+    if (best) {
+        dose_info inf;
+        dose_matrix_info(A, &inf);
+        *best = inf.tuning;  // the knobs in effect, as dose_matrix_info reports them
+    }
     return DOSE_OK;
 }
 

@@ -107,6 +107,50 @@ struct ScheduleView {
     const uint32_t* wlo;  // adjoint schedule only (else null)
 };
 
+// A work item for dealing stages to CTAs: descriptors [s, e), the columns its
+// entries touch [lo, hi] (lo > hi: none) and its estimated cost.
+struct DealItem {
+    uint32_t s, e;
+    uint32_t lo, hi;
+    uint64_t cost;
+};
+
+// Row-group layout of a matrix, built at create for the adjoint and the fused
+// objective pass.  The non-empty rows, in matrix order, are cut into groups of
+// up to four consecutive ones whose columns mostly coincide (neighbouring voxels
+// see the same spots).  A group stores the union of its rows' columns once and,
+// for each union column, the four rows' stored values side by side (the stored
+// zero where a row has no entry).  One warp then takes a whole group: per union
+// column one gather of x feeds four rows' dot products, and after the four
+// residuals are known one read-modify-write of the gradient accumulator adds
+// all four rows' contributions.
+//   stage (StageDesc reused): rows [row0, row1), union entries [nz0, nz1),
+//   groups [ne0, ne1); meta unused.
+//   group record (uint4): x = first union entry, y = union size, z / w = the
+//   rows' offsets from the stage's row0 as u16 pairs (0xFFFF: no row).
+struct RgHostGroup {
+    uint32_t row[4];   // absolute rows (~0u: none)
+    uint32_t uoff, nu; // union entries [uoff, uoff + nu)
+    uint32_t lo, hi;   // lowest / highest union column
+};
+
+struct RowGroups {
+    bool built = false;
+    uint32_t iw = 4;                // bytes per union column index (2 when ncols <= 65536)
+    uint64_t n_union = 0;           // union entries of all groups
+    void* ucol = nullptr;           // union column indices
+    void* uval = nullptr;           // four stored values per union entry
+    uint4* grp = nullptr;           // group records (depend on the stage cut)
+    uint32_t* mask = nullptr;       // one bit per row: the row has entries
+    double* f_rows = nullptr;       // objective sums of the finalize's row blocks
+    uint32_t* ticket = nullptr;     // finalize: row blocks done (reset by the last one)
+    uint32_t nblk_rows = 0;         // finalize row blocks (256 rows per warp, 8 warps)
+    DevSchedule sched;              // stages of groups, dealt to CTAs with column windows
+    uint32_t tile_u = 0, tile_g = 0, tile_rows = 0;  // stage limits of the schedule in effect
+    uint64_t bytes = 0;             // device bytes of the arrays above
+    std::vector<RgHostGroup> host; // kept for re-cutting the stages
+};
+
 // Shape of the adjoint / fused kernels (warp specialisation and pipeline).
 struct AdjTuning {
     uint32_t tile_nnz = 5120;
@@ -116,6 +160,13 @@ struct AdjTuning {
     uint32_t scatter_warps = 0;   // warps owning gradient accumulators (0 = as many as fit, up to the cap)
     uint32_t l2_prefetch = 8;     // stages prefetched into L2 ahead of the shared-memory ring
     uint32_t row_order = 2;       // as Tuning::row_order, for the adjoint schedule
+    // layout of the adjoint / fused passes: 0 = row groups where they apply, else
+    // CSR; 1 = CSR; 2 = row groups (create fails if they do not apply)
+    uint32_t layout = 0;
+    uint32_t rg_tile_u = 0;        // row groups: union entries per stage (0 = by format)
+    uint32_t rg_tile_rows = 512;   // row groups: rows a stage may span
+    uint32_t rg_stages = 2;        // row groups: pipeline depth
+    uint32_t rg_warps = 0;         // row groups: worker warps (0 = as many as fit, up to kRgMaxWarps)
 };
 
 }  // namespace dose
@@ -149,6 +200,8 @@ struct dose_matrix {
     uint2* x64 = nullptr;
 
     dose::SellArrays sell;  // DOSE_CREATE_SELL only
+
+    dose::RowGroups rg;     // row-group layout of the adjoint / fused passes (when it applies)
 
     // adjoint scratch: per-CTA partial gradients and objective values
     float* g_part = nullptr;     // adj.grid * ncols
@@ -199,6 +252,29 @@ cudaError_t launch_adjoint(const dose_matrix* A, int mode, const float* x, const
 // Whether the adjoint / fused kernels can run on A (window and accumulators fit;
 // per-row vectors 16-byte aligned); sets the error message if not.
 dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* const* vecs, int nvec);
+// Row-group layout (rg_layout.cu, rg_kernel.cu).  build_row_groups forms the
+// groups from the host CSR and the stored values; false (with *why) if some row
+// does not fit one stage.  rg_schedule cuts the stages and deals them
+// (re-run when the tuning changes).
+bool build_row_groups(dose_matrix* A, const uint32_t* rp, const uint32_t* col, const unsigned char* vals,
+                      std::string* why, cudaError_t* err);
+cudaError_t rg_schedule(dose_matrix* A, const AdjTuning& t);
+void free_row_groups(dose_matrix* A);
+// Worker warps that fit for tuning t (0: none); *smem the dynamic shared memory.
+uint32_t rg_shape(const dose_matrix* A, const AdjTuning& t, bool quad, size_t* smem);
+// Whether the adjoint (quad = false) / fused pass of A runs on the row-group layout.
+bool rg_active(const dose_matrix* A, bool quad);
+cudaError_t launch_rg(const dose_matrix* A, int mode, const float* x, const float* p, const float* w,
+                      const float* r, float* d, double* f, float* g, float* x_update, float eta, cudaStream_t s);
+uint64_t rg_fused_bytes(const dose_matrix* A, bool with_d);
+uint64_t rg_adjoint_bytes(const dose_matrix* A);
+// Sum of the per-CTA partials (g, f) in a fixed order; optional projected-gradient step.
+cudaError_t launch_adjoint_finalize(const dose_matrix* A, const float* g_part, const uint32_t* wlo, uint32_t wwidth,
+                                    uint32_t nparts, bool quad, float* g, double* f, float* x_update, float eta,
+                                    cudaStream_t s);
+void deal_items(Schedule& S, const std::vector<DealItem>& items, uint32_t grid, uint32_t ncols, bool windowed,
+                bool align_wlo);
+
 cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const float* const* X,
                                 float* const* D, int nvec, cudaStream_t s, std::string* why);
 
@@ -208,6 +284,10 @@ constexpr uint32_t kMaxSmemPerBlock = 227 * 1024;
 __host__ __device__ constexpr uint32_t value_bytes(int fmt) {
     return fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1u : (fmt == DOSE_FMT_F32 ? 4u : 2u);
 }
+// Worker warps of the row-group kernel (plus one producer): 16 warps in all, so
+// that each of the SM's four register files holds four warps of up to 128 registers.
+constexpr uint32_t kRgMaxWarps = 15;
+constexpr uint32_t kRgMaxUnionReg = 320;  // union columns a group may hold to stay in registers
 constexpr uint32_t kMaxAdjWarps = 20;      // producer + forward + scatter warps of the adjoint kernels
 constexpr uint32_t kSellDefaultSigma = 1u << 20;  // rows per sorting window of the SELL copy
 constexpr uint32_t kAdjMinScatterWarps = 8;
@@ -303,6 +383,19 @@ __device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, uint32_t parity, 
 // The waits of the pipelined kernels: ~4 s (the kernels run for milliseconds).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
     return mbar_wait_limit(bar, parity, 4000000000ull);
+}
+
+// The same bound with plain try_wait polls (each poll blocks for a short,
+// hardware-chosen time and returns as soon as the phase completes); the
+// global timer is read once per 64 polls.
+__device__ __forceinline__ bool mbar_wait_poll(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > 4000000000ull) return false;
+    }
 }
 
 // Bulk async copy global -> shared (no tensor map), completion counted on `bar`.
