@@ -156,7 +156,9 @@ typedef struct {
                                    by format, about 24 KB of columns and values) */
     uint32_t rg_tile_rows;      /* row groups: rows per stage (256..8192) */
     uint32_t rg_stages;         /* row groups: pipeline depth (2..8) */
-    uint32_t rg_warps;          /* row groups: worker warps (1..16; 0 = as many as fit) */
+    uint32_t rg_warps;          /* row groups: worker warps (1..15; 0 = as many as fit) */
+    uint32_t rg_l2_prefetch;    /* row groups: stages prefetched into L2 ahead of the ring (1..31;
+                                   0 = default, off; 32 = off) */
 } dose_tuning;
 
 typedef struct {

@@ -64,7 +64,8 @@ class Tuning(ctypes.Structure):
                 ("row_order", ctypes.c_uint32), ("adj_row_order", ctypes.c_uint32),
                 ("sell_sigma", ctypes.c_uint32),
                 ("adj_layout", ctypes.c_uint32), ("rg_tile_union", ctypes.c_uint32),
-                ("rg_tile_rows", ctypes.c_uint32), ("rg_stages", ctypes.c_uint32), ("rg_warps", ctypes.c_uint32)]
+                ("rg_tile_rows", ctypes.c_uint32), ("rg_stages", ctypes.c_uint32), ("rg_warps", ctypes.c_uint32),
+                ("rg_l2_prefetch", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

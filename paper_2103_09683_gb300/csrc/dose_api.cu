@@ -466,6 +466,7 @@ static void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
     if (in->rg_tile_rows) a.rg_tile_rows = in->rg_tile_rows;
     if (in->rg_stages) a.rg_stages = in->rg_stages;
     if (in->rg_warps) a.rg_warps = in->rg_warps;
+    if (in->rg_l2_prefetch) a.rg_l2_prefetch = in->rg_l2_prefetch >= 32 ? 0 : in->rg_l2_prefetch;
     if (!in->coop_nnz) t.coop_nnz = std::min(t.coop_nnz, t.tile_nnz);  // the default follows a smaller tile
 }
 
@@ -490,6 +491,7 @@ static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out)
     out->rg_tile_rows = a.rg_tile_rows;
     out->rg_stages = a.rg_stages;
     out->rg_warps = a.rg_warps;
+    out->rg_l2_prefetch = a.rg_l2_prefetch ? a.rg_l2_prefetch : 32;
 }
 
 template <class T>

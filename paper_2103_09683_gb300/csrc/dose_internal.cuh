@@ -167,6 +167,7 @@ struct AdjTuning {
     uint32_t rg_tile_rows = 512;   // row groups: rows a stage may span
     uint32_t rg_stages = 2;        // row groups: pipeline depth
     uint32_t rg_warps = 0;         // row groups: worker warps (0 = as many as fit, up to kRgMaxWarps)
+    uint32_t rg_l2_prefetch = 0;   // row groups: stages prefetched into L2 ahead of the ring (0 = off)
 };
 
 }  // namespace dose

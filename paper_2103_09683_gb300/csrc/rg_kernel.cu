@@ -288,12 +288,13 @@ struct RgStage {
     uint32_t row0, r_a;
 };
 
-// One group whose union takes exactly K steps of 32 columns (K = 0: any number
-// of steps, union re-read for the scatter).  Steps 0 .. K-2 are full; only the
-// last step's lanes are masked.  Fused pass: row sums, d, objective terms,
+// One group whose union takes more than KF and at most K steps of 32 columns
+// (K = 0: any number of steps, union re-read for the scatter).  Steps
+// 0 .. KF-1 are full; only the lanes of the later steps are masked (a fully
+// masked step reads x at the zero element and adds nothing).  Fused pass: row sums, d, objective terms,
 // residuals and the accumulator updates; adjoint: the updates with the staged
 // residuals.
-template <int FMT, int MODE, uint32_t IW, int K>
+template <int FMT, int MODE, uint32_t IW, int K, int KF>
 __device__ __forceinline__ void rg_group(const RgParams& p, const RgStage& C, const uint4 G, uint32_t xs_a,
                                          uint32_t gw_a, uint32_t zc, uint32_t lane, float& f_hi, float& f_lo) {
     constexpr bool QUAD = MODE == ADJ_MODE_QUADRATIC;
@@ -332,13 +333,16 @@ __device__ __forceinline__ void rg_group(const RgParams& p, const RgStage& C, co
     float v[KV][4];
     if (K) {
 #pragma unroll
-        for (int it = 0; it < KR - 1; ++it) {
-            c[it] = rg_ldcol<IW>(ca + IW * 32 * it);
-            raw[it] = rg_ldval<FMT>(va + RV * 32 * it);
+        for (int it = 0; it < KR; ++it) {
+            if (it < KF) {
+                c[it] = rg_ldcol<IW>(ca + IW * 32 * it);
+                raw[it] = rg_ldval<FMT>(va + RV * 32 * it);
+            } else {
+                // masked lanes read x at the zero element and values 0
+                c[it] = rg_ldcol_lt<IW>(32 * it + lane, nU, ca + IW * 32 * it, zc);
+                raw[it] = rg_ldval_lt<FMT>(32 * it + lane, nU, va + RV * 32 * it);
+            }
         }
-        // the last step: masked lanes read x at the zero element and values 0
-        c[KR - 1] = rg_ldcol_lt<IW>(32 * (KR - 1) + lane, nU, ca + IW * 32 * (KR - 1), zc);
-        raw[KR - 1] = rg_ldval_lt<FMT>(32 * (KR - 1) + lane, nU, va + RV * 32 * (KR - 1));
     }
     if (QUAD) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -392,8 +396,8 @@ __device__ __forceinline__ void rg_group(const RgParams& p, const RgStage& C, co
         // all loads of the accumulator before its stores (the union columns are distinct)
         float gv[KR];
 #pragma unroll
-        for (int it = 0; it < KR - 1; ++it) gv[it] = dev::lds_f32(gw_a + 4 * c[it]);
-        gv[KR - 1] = dev::lds_f32_lt(32 * (KR - 1) + lane, nU, gw_a + 4 * c[KR - 1]);
+        for (int it = 0; it < KR; ++it)
+            gv[it] = it < KF ? dev::lds_f32(gw_a + 4 * c[it]) : dev::lds_f32_lt(32 * it + lane, nU, gw_a + 4 * c[it]);
 #pragma unroll
         for (int it = 0; it < KR; ++it) {
             float q[4];
@@ -406,10 +410,10 @@ __device__ __forceinline__ void rg_group(const RgParams& p, const RgStage& C, co
             t = __fmaf_rn(q[1], r1, t);
             t = __fmaf_rn(q[2], r2, t);
             t = __fmaf_rn(q[3], r3, t);
-            if (it < KR - 1)
+            if (it < KF)
                 dev::sts_f32(gw_a + 4 * c[it], __fadd_rn(gv[it], t));
             else
-                dev::sts_f32_lt(32 * (KR - 1) + lane, nU, gw_a + 4 * c[it], __fadd_rn(gv[it], t));
+                dev::sts_f32_lt(32 * it + lane, nU, gw_a + 4 * c[it], __fadd_rn(gv[it], t));
         }
     } else {
         const uint32_t nit = (nU + 31) >> 5;
@@ -467,6 +471,9 @@ __global__ void __launch_bounds__((kRgMaxWarps + 1) * 32, 1) rg_kernel(const RgP
     }
     __syncthreads();
 
+    // every CTA is resident: the finalize kernel may be scheduled onto SMs as
+    // their CTAs finish (it waits for this grid before reading its results)
+    asm volatile("griddepcontrol.launch_dependents;");
     if (warp == 0) {
         if (lane == 0) rg_produce<FMT, IW, QUAD>(p, s_begin, s_end, slot_base, full, empty, dwin, dbar);
         return;
@@ -506,19 +513,19 @@ __global__ void __launch_bounds__((kRgMaxWarps + 1) * 32, 1) rg_kernel(const RgP
         const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
         for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
             const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
-            switch ((G.y + 31) >> 5) {
-                case 0:
-                case 1: rg_group<FMT, MODE, IW, 1>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-                case 2: rg_group<FMT, MODE, IW, 2>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-                case 3: rg_group<FMT, MODE, IW, 3>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-                case 4: rg_group<FMT, MODE, IW, 4>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-                case 5: rg_group<FMT, MODE, IW, 5>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-                case 6: rg_group<FMT, MODE, IW, 6>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-                case 7: rg_group<FMT, MODE, IW, 7>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-                case 8: rg_group<FMT, MODE, IW, 8>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-                case 9: rg_group<FMT, MODE, IW, 9>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-                default: rg_group<FMT, MODE, IW, 0>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo); break;
-            }
+            // four code paths (each unrolled for its step count) keep the
+            // kernel's instructions within the instruction cache
+            const uint32_t nit = (G.y + 31) >> 5;
+            if (nit <= 2)
+                rg_group<FMT, MODE, IW, 2, 0>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo);
+            else if (nit <= 4)
+                rg_group<FMT, MODE, IW, 4, 2>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo);
+            else if (nit <= 6)
+                rg_group<FMT, MODE, IW, 6, 4>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo);
+            else if (nit <= 9)
+                rg_group<FMT, MODE, IW, 9, 6>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo);
+            else
+                rg_group<FMT, MODE, IW, 0, 0>(p, C, G, xs_a, gw_a, zc, lane, f_hi, f_lo);
             __syncwarp();  // this group's updates precede the next group's loads in every lane
         }
         rot = rot + 1 == NW ? 0 : rot + 1;
@@ -549,15 +556,18 @@ __global__ void __launch_bounds__((kRgMaxWarps + 1) * 32, 1) rg_kernel(const RgP
     }
 }
 
-// Second kernel of the row-group passes.
-//   blocks [0, nblk_g): g_j = s * (sum of the partials of the CTAs whose window
-//     holds j, in CTA order), and the optional projected-gradient step on x;
-//   blocks [nblk_g, nblk_g + nblk_r) (fused pass only): the rows without
-//     entries, four consecutive rows per thread and step (16-byte loads of p
-//     and w, grid-stride): d = 0 and the objective term w p^2.  Each block's
-//     sum goes to f_rows, and the last row block to finish (integer ticket)
-//     writes f = the CTAs' objective partials and the row blocks' sums, added
-//     in one fixed order, then resets the ticket.
+// Second kernel of the row-group passes, one wave of blocks, launched as a
+// programmatic dependent of the main kernel so that it starts on SMs whose
+// main CTA has finished:
+//   fused pass only, first: the rows without entries (they do not depend on
+//     the main kernel), four consecutive rows per thread and step (16-byte
+//     loads of p and w, grid-stride): d = 0 and the objective term w p^2;
+//   then, after the main kernel has completed: column blocks cb = block,
+//     block + grid, ... : g_j = s * (sum of the partials of the CTAs whose
+//     window holds j, in CTA order), and the optional projected-gradient step
+//     on x; each block's objective sum goes to f_rows, and the last block to
+//     finish (integer ticket) writes f = the CTAs' objective partials and the
+//     blocks' sums, added in one fixed order, then resets the ticket.
 struct RgFin {
     const float* g_part;
     const uint32_t* wlo;
@@ -575,10 +585,10 @@ struct RgFin {
     uint32_t nrows;
     double* f_rows;
     uint32_t* ticket;
-    uint32_t nblk_g, nblk_r;
+    uint32_t nblk_g;
 };
 
-constexpr uint32_t kFinMaxParts = 1024;  // CTA partials whose window bases the g blocks keep in shared memory
+constexpr uint32_t kFinMaxParts = 1024;  // CTA partials whose window bases a block keeps in shared memory
 
 __global__ void __launch_bounds__(256) rg_finalize(const RgFin q) {
     __shared__ float part[8][33];
@@ -586,10 +596,58 @@ __global__ void __launch_bounds__(256) rg_finalize(const RgFin q) {
     __shared__ uint32_t swlo[kFinMaxParts];
     __shared__ uint32_t last;
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float hi = 0.f, lo = 0.f;
+    if (q.f) {
+        // rows without entries: thread takes rows 4i .. 4i+3 for i = tid, tid + T, ...
+        // (four such steps' loads issued together)
+        constexpr uint32_t U = 4;
+        const uint32_t nq = (q.nrows + 3) / 4, T = gridDim.x * 256;
+        const uint32_t full_q = q.nrows / 4;  // quads inside p and w (16-byte loads)
+        const float4* __restrict__ p4 = reinterpret_cast<const float4*>(q.p);
+        const float4* __restrict__ w4 = reinterpret_cast<const float4*>(q.w);
+        for (uint32_t i0 = blockIdx.x * 256 + threadIdx.x; i0 < nq; i0 += U * T) {
+            uint32_t m[U];
+            float4 a[U], b[U];
+#pragma unroll
+            for (uint32_t k = 0; k < U; ++k) {
+                const uint32_t i = i0 + k * T, r = 4 * i;
+                m[k] = i < nq ? (__ldg(q.mask + (r >> 5)) >> (r & 31)) & 0xFu : 0xFu;
+                if (i < nq && r + 4 > q.nrows) m[k] |= (0xFu << (q.nrows - r)) & 0xFu;  // rows past the end
+                if (i < full_q) {
+                    a[k] = __ldg(p4 + i);
+                    b[k] = __ldg(w4 + i);
+                } else {
+                    float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    for (uint32_t u = 0; u < 4; ++u)
+                        if (i < nq && r + u < q.nrows) {
+                            t[u] = __ldg(q.p + r + u);
+                            t[4 + u] = __ldg(q.w + r + u);
+                        }
+                    a[k] = make_float4(t[0], t[1], t[2], t[3]);
+                    b[k] = make_float4(t[4], t[5], t[6], t[7]);
+                }
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < U; ++k) {
+                const uint32_t r = 4 * (i0 + k * T);
+                const float pv[4] = {a[k].x, a[k].y, a[k].z, a[k].w}, wv[4] = {b[k].x, b[k].y, b[k].z, b[k].w};
+#pragma unroll
+                for (uint32_t u = 0; u < 4; ++u) {
+                    if ((m[k] >> u) & 1u) continue;  // a row with entries, or past the end
+                    if (q.d) q.d[r + u] = 0.0f;
+                    if (pv[u] != 0.0f || !(fabsf(wv[u]) < INFINITY)) dev::df_add_wsq(hi, lo, wv[u], 0.0f, pv[u]);
+                }
+            }
+        }
+    }
+    // the rest reads the main kernel's partials (and may update x, which it reads)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (blockIdx.x < q.nblk_g) {
         for (uint32_t c = threadIdx.x; c < q.nparts && c < kFinMaxParts; c += 256) swlo[c] = __ldg(q.wlo + c);
         __syncthreads();
-        const uint32_t j = blockIdx.x * 32 + lane;
+    }
+    for (uint32_t cb = blockIdx.x; cb < q.nblk_g; cb += gridDim.x) {
+        const uint32_t j = cb * 32 + lane;
         float t = 0.f;
         if (j < q.ncols) {
             // warp w adds the partials c = w, w + 8, ... in order; eight loads in flight
@@ -622,49 +680,9 @@ __global__ void __launch_bounds__(256) rg_finalize(const RgFin q) {
                 q.x_update[j] = xn > 0.f ? xn : 0.f;
             }
         }
-        return;
+        __syncthreads();
     }
-    // rows without entries: thread takes rows 4i .. 4i+3 for i = tid, tid + T, ...
-    // (four such steps' loads issued together)
-    float hi = 0.f, lo = 0.f;
-    const uint32_t nq = (q.nrows + 3) / 4, T = q.nblk_r * 256;
-    const uint32_t full_q = q.nrows / 4;  // quads inside p and w (16-byte loads)
-    const float4* __restrict__ p4 = reinterpret_cast<const float4*>(q.p);
-    const float4* __restrict__ w4 = reinterpret_cast<const float4*>(q.w);
-    for (uint32_t i0 = (blockIdx.x - q.nblk_g) * 256 + threadIdx.x; i0 < nq; i0 += 4 * T) {
-        uint32_t m[4];
-        float4 a[4], b[4];
-#pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t i = i0 + k * T, r = 4 * i;
-            m[k] = i < nq ? (__ldg(q.mask + (r >> 5)) >> (r & 31)) & 0xFu : 0xFu;
-            if (i < nq && r + 4 > q.nrows) m[k] |= (0xFu << (q.nrows - r)) & 0xFu;  // rows past the end
-            if (i < full_q) {
-                a[k] = __ldg(p4 + i);
-                b[k] = __ldg(w4 + i);
-            } else {
-                float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                for (uint32_t u = 0; u < 4; ++u)
-                    if (i < nq && r + u < q.nrows) {
-                        t[u] = __ldg(q.p + r + u);
-                        t[4 + u] = __ldg(q.w + r + u);
-                    }
-                a[k] = make_float4(t[0], t[1], t[2], t[3]);
-                b[k] = make_float4(t[4], t[5], t[6], t[7]);
-            }
-        }
-#pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t r = 4 * (i0 + k * T);
-            const float pv[4] = {a[k].x, a[k].y, a[k].z, a[k].w}, wv[4] = {b[k].x, b[k].y, b[k].z, b[k].w};
-#pragma unroll
-            for (uint32_t u = 0; u < 4; ++u) {
-                if ((m[k] >> u) & 1u) continue;  // a row with entries, or past the end
-                if (q.d) q.d[r + u] = 0.0f;
-                if (pv[u] != 0.0f || !(fabsf(wv[u]) < INFINITY)) dev::df_add_wsq(hi, lo, wv[u], 0.0f, pv[u]);
-            }
-        }
-    }
+    if (!q.f) return;
     double fl = (double)hi + (double)lo;
     for (uint32_t o = 16; o > 0; o >>= 1) fl += __shfl_xor_sync(0xffffffffu, fl, o);
     if (lane == 0) red[w] = fl;
@@ -672,15 +690,15 @@ __global__ void __launch_bounds__(256) rg_finalize(const RgFin q) {
     if (threadIdx.x == 0) {
         double b = 0.0;
         for (uint32_t k = 0; k < 8; ++k) b += red[k];
-        q.f_rows[blockIdx.x - q.nblk_g] = b;
+        q.f_rows[blockIdx.x] = b;
         __threadfence();
-        last = atomicAdd(q.ticket, 1u) == q.nblk_r - 1;
+        last = atomicAdd(q.ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     double acc = 0.0;
-    const uint32_t n = q.nparts + q.nblk_r;
+    const uint32_t n = q.nparts + gridDim.x;
     for (uint32_t i = threadIdx.x; i < n; i += 256)
         acc += i < q.nparts ? __ldcg(q.f_part + i) : __ldcg(q.f_rows + (i - q.nparts));
     red[threadIdx.x] = acc;
@@ -808,7 +826,7 @@ cudaError_t launch_rg(const dose_matrix* A, int mode, const float* x, const floa
         prm.SL = rg_slot(R.tile_u, R.tile_g, R.tile_rows, es, R.iw, prm.vecs.n);
         prm.depth = A->adj_tuning.rg_stages;
         prm.nw = nw;
-        prm.l2pf = A->adj_tuning.l2_prefetch;
+        prm.l2pf = A->adj_tuning.rg_l2_prefetch;
         prm.err = A->err;
         cudaError_t e;
         if (R.iw == 2)
@@ -837,9 +855,20 @@ cudaError_t launch_rg(const dose_matrix* A, int mode, const float* x, const floa
     q.f_rows = R.f_rows;
     q.ticket = R.ticket;
     q.nblk_g = A->ncols ? (A->ncols + 31) / 32 : 1;
-    q.nblk_r = quad ? R.nblk_rows : 0;
-    rg_finalize<<<q.nblk_g + q.nblk_r, 256, 0, s>>>(q);
-    return cudaGetLastError();
+    // one wave: the blocks that fit on every SM at once take the columns, then
+    // (fused pass) the rows without entries
+    const uint32_t nblk = quad ? R.nblk_rows : q.nblk_g;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblk);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = A->nrows > 0 ? 1 : 0;  // without a main kernel, an ordinary launch
+    return cudaLaunchKernelEx(&cfg, rg_finalize, q);
 }
 
 }  // namespace dose

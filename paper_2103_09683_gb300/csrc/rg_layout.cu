@@ -225,9 +225,8 @@ bool build_row_groups(dose_matrix* A, const uint32_t* rp, const uint32_t* col, c
         if (rp[r + 1] > rp[r]) mask[r >> 5] |= 1u << (r & 31);
     if (e == cudaSuccess)
         e = rg_upload(reinterpret_cast<void**>(&R.mask), mask.data(), mask.size() * 4, mask.size() * 4);
-    // finalize row blocks: four per SM, each thread a 4-row step at a time
-    const uint64_t quads = ((uint64_t)nrows + 3) / 4;
-    R.nblk_rows = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((quads + 255) / 256, 4ull * R.sched.grid));
+    // finalize blocks of the fused pass: four 256-thread blocks per SM (one wave)
+    R.nblk_rows = 4 * std::max<uint32_t>(R.sched.grid, 1);
     if (e == cudaSuccess)
         e = rg_upload(reinterpret_cast<void**>(&R.f_rows), nullptr, 0, (size_t)R.nblk_rows * 8);
     if (e == cudaSuccess) e = rg_upload(reinterpret_cast<void**>(&R.ticket), nullptr, 0, 16);
