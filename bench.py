@@ -41,10 +41,10 @@ sys.path.insert(0, ROOT)
 import dosegen  # noqa: E402
 
 METRIC = "dose SpMV effective HBM GB/s (% of GB300 peak) and ms per dose+gradient eval"
-WORKLOAD = ("clinical pencil beam: 256x256x160 voxels (10,485,760 rows) x 4000 spots, "
-            "sigma 4 voxels, ~1.5e8 entries; u16 values + FP32 scale, u32 indices, FP32 x/d; "
-            "step = dose eval (d = A x) + dose+gradient eval (fused d, FP64 f, A^T[2w(d-p)], "
-            "projected-gradient update)")
+WORKLOAD = "clinical pencil beam 256x256x160 voxels x 4000 spots, 1.5e8 entries, u16+scale, u32 indices"
+GPU_STEP = ("dose eval d = A x, then dose+gradient eval: d, FP64 f = sum w (d-p)^2, g = A^T[2w(d-p)] and the "
+            "projected-gradient update x <- max(0, x - eta g)")
+REF_STEP = "FP64 d = A x, then FP64 f and g = A^T[2w(d-p)] on a row block (no projected-gradient update)"
 
 
 def _peaks():
@@ -276,30 +276,45 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = e2[0].elapsed_time(e2[1]) / ke
 
-    step_bytes = info["spmv_bytes"] + info["fused_bytes"]
+    # Algorithmic bytes of the fused pass: the CSR byte model of the measurement
+    # plan (stored values and 32-bit indices once, row pointers, p and w, x in,
+    # g out, the CTA partials written and read once).  On the row-group layout
+    # the kernel moves fewer bytes (its own model is reported beside it).
+    fused_csr = csr_fused_bytes(info)
+    step_bytes = info["spmv_bytes"] + fused_csr
     value = whole_job_gbs(step_bytes, K, ws, total_ms)
     peak, peak_kind = _peaks()
     spmv_gbs = info["spmv_bytes"] / (spmv_ms * 1e-3) / 1e9
-    grad_gbs = info["fused_bytes"] / (grad_ms * 1e-3) / 1e9
+    grad_gbs = fused_csr / (grad_ms * 1e-3) / 1e9
+    rg = info["adj_layout_fused"] == 2
+    fused_name = "rg_kernel+rg_finalize" if rg else "adjoint_kernel+finalize"
     kernels = {
         "spmv_kernel": {"ms": round(spmv_ms, 5), "bytes": info["spmv_bytes"],
                         "achieved_gbs": round(spmv_gbs, 1), "frac": round(spmv_gbs / peak, 4),
                         "traffic": _traffic("spmv_kernel")},
-        "adjoint_kernel+finalize": {"ms": round(grad_ms, 5), "bytes": info["fused_bytes"],
-                                    "achieved_gbs": round(grad_gbs, 1), "frac": round(grad_gbs / peak, 4),
-                                    "traffic": _traffic("adjoint_kernel")},
+        fused_name: {"ms": round(grad_ms, 5), "bytes": fused_csr, "achieved_gbs": round(grad_gbs, 1),
+                     "frac": round(grad_gbs / peak, 4),
+                     "layout": "row groups" if rg else "CSR",
+                     "own_bytes": info["fused_bytes"],
+                     "own_gbs": round(info["fused_bytes"] / (grad_ms * 1e-3) / 1e9, 1),
+                     "own_frac": round(info["fused_bytes"] / (grad_ms * 1e-3) / 1e9 / peak, 4),
+                     "traffic": _traffic("rg_kernel" if rg else "adjoint_kernel")},
     }
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     roof = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": peak,
             "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
             else "fallback 6.8 TB/s", "unit": "GB/s", "frac": kernels[dom]["frac"],
             "traffic": kernels[dom]["traffic"]}
+    if "own_bytes" in kernels[dom]:
+        roof.update({"note": "achieved = the CSR byte model of the pass / its time; the row-group layout reads "
+                             "own_bytes, of which own_frac is the fraction of the measured peak",
+                     "own_bytes": kernels[dom]["own_bytes"], "own_frac": kernels[dom]["own_frac"]})
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(total_ms / K, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nrows": A.nrows, "ncols": A.ncols, "nnz": A.nnz,
-                   "format": "u16+scale", "bytes_per_step": step_bytes,
+                   "format": "u16+scale", "bytes_per_step": step_bytes, "step": GPU_STEP,
                    "l2": "inputs larger than L2 (A streams ~1 GB per call; L2 129 MB)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "ms_per_dose_eval": round(spmv_ms, 5),
@@ -319,7 +334,17 @@ def run_gpu(args):
         "clocks": clk,
         "tuning": info["tuning"],
         "autotuned": bool(tuned),
+        "fused_layout": {"name": "row groups" if rg else "CSR", "groups": info["rg_groups"],
+                         "union_entries": info["rg_union_entries"], "window": info["rg_window"],
+                         "workers": info["rg_warps_fused"], "index_bytes": info["rg_index_bytes"],
+                         "bytes_per_entry": round(info["fused_bytes"] / A.nnz, 3),
+                         "csr_bytes_per_entry": round(fused_csr / A.nnz, 3)},
     }
+    if rank == 0 and not args.no_extras:
+        # other forms of the same evaluation on this GPU (outside the timed region)
+        del d
+        out["precision_variants"] = precision_variants(csr, A, x0, p, w, eta, min(K, 100), args.warmup)
+        out["batched_subset"] = batched_subset(min(K, 20), args.warmup)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         hx, hp, hw = x0.cpu().numpy(), p.cpu().numpy(), w.cpu().numpy()
         out["cpu_baseline"] = cpu_baseline(csr, hx, hp, hw)
@@ -356,8 +381,14 @@ def oracle_step(csr, enc, x, p, w, frac):
     oracle.spmv(nr, rp, col, a, x)
     oracle.fgrad(nr, nc, rp, col, a, x, p[r0:r1], w[r0:r1])
     dt = time.perf_counter() - t0
-    bytes_ = (6 * nz + 4 * (nr + 1) + 4 * nr + 4 * nc) + (6 * nz + 4 * (nr + 1) + 8 * nr + 8 * nc + 8)
-    return bytes_, dt
+    return oracle_step_bytes(nr, nc, nz), dt
+
+
+def oracle_step_bytes(nr, nc, nz) -> int:
+    """Bytes of one oracle step's arrays: the SpMV (values and indices, row
+    pointers, x, d) and the f and A^T r pass (the same matrix again, p and w, x,
+    g, f)."""
+    return (6 * nz + 4 * (nr + 1) + 4 * nr + 4 * nc) + (6 * nz + 4 * (nr + 1) + 8 * nr + 8 * nc + 8)
 
 
 def cpu_baseline(csr, x, p, w, budget_s=10.0):
@@ -411,8 +442,7 @@ def cpu_baseline_all_cores(csr, x, p, w, budget_s=10.0):
         oracle.spmv(nr, brp, bcol, ba, x)
         return oracle.fgrad(nr, nc, brp, bcol, ba, x, bp, bw)
 
-    nr, nnz = csr.nrows, csr.nnz
-    step_bytes = (6 * nnz + 4 * (nr + 1) + 4 * nr + 4 * nc) + (6 * nnz + 4 * (nr + 1) + 8 * nr + 8 * nc + 8)
+    step_bytes = oracle_step_bytes(csr.nrows, nc, csr.nnz)
     tot_t, reps = 0.0, 0
     with ThreadPoolExecutor(max_workers=n) as pool:
         list(pool.map(block_step, blocks))  # threads started, pages touched
@@ -429,6 +459,119 @@ def cpu_baseline_all_cores(csr, x, p, w, budget_s=10.0):
             "ms_per_step": round(1e3 * tot_t / reps, 1), "cpu": f"{os.uname().machine}, {n} threads",
             "sample": f"{reps} full-matrix step(s) of the clinical beam ({csr.nnz} entries): FP64 SpMV + f "
                       f"and A^T r, rows in {n} equal-entry blocks, one thread each, partials added in block order"}
+
+
+def csr_fused_bytes(info) -> int:
+    """Byte model of one fused dose+gradient pass over the CSR arrays: stored
+    values and 32-bit column indices once, row pointers, p and w, x in and g
+    out, and the per-CTA gradient partials written and read once."""
+    vb = {0: 2, 1: 2, 2: 1, 3: 2, 4: 4}[info["fmt"]]
+    nz, nr, nc, P = info["nnz"], info["nrows"], info["ncols"], info["grid"]
+    rs = 4 * nr if info["fmt"] == 2 else 0
+    return (vb + 4) * nz + 4 * (nr + 1) + rs + 8 * nr + 8 * nc + 2 * P * nc * 4 + 8
+
+
+def _time_calls(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def precision_variants(csr, A_u16, x, p, w, eta, steps, warmup):
+    """The clinical beam in the other stored forms on the same GPU: FP8-E4M3
+    with row scales, BF16, and u16 with 16-bit column indices for the dose
+    SpMV; per form the dose eval and the dose+gradient eval times and the dose's
+    relative error on 20000 sampled rows against the FP64 dose of the
+    generator's values (fp64_dose_rows), next to the u16 baseline."""
+    import torch
+
+    import paper_2103_09683_gb300 as dose
+
+    xh = x.cpu().numpy()
+    rng = np.random.default_rng(7)
+    lens = np.diff(csr.row_ptr.astype(np.int64))
+    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 20000, replace=False))
+    exact = fp64_dose_rows(csr.row_ptr, csr.col, csr.val, xh, rows)
+    nz = exact != 0
+    f = torch.empty(1, dtype=torch.float64, device=x.device)
+    g = torch.empty(csr.ncols, dtype=torch.float32, device=x.device)
+    out = []
+    for fmt, idx16 in (("u16", False), ("u16", True), ("bf16", False), ("fp8", False)):
+        if fmt == "u16" and not idx16:
+            A = A_u16
+        else:
+            codes, scales = dose.encode_host(fmt, csr.row_ptr, csr.val)
+            A = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt=fmt, values=codes,
+                                         scales=scales, index16=idx16)
+            del codes, scales
+        inf = A.info()
+        d = torch.empty(A.nrows, dtype=torch.float32, device=x.device)
+        ms_d = _time_calls(lambda: A.spmv(x, d), steps, warmup)
+        dv = d.cpu().numpy()[rows].astype(np.float64)
+        rel = np.abs(dv[nz] - exact[nz]) / np.abs(exact[nz])
+        ms_g = _time_calls(lambda: A.fwd_adj_quadratic(x, p, w, f=f, g=g), steps, warmup)
+        A.device_status()
+        out.append({"format": fmt, "spmv_index_bytes": 2 if idx16 else 4,
+                    "ms_per_dose_eval": round(ms_d, 5),
+                    "dose_eval_gbs": round(inf["spmv_bytes"] / (ms_d * 1e-3) / 1e9, 1),
+                    "ms_per_dose_grad_eval": round(ms_g, 5),
+                    "dose_grad_eval_gbs_csr_model": round(csr_fused_bytes(inf) / (ms_g * 1e-3) / 1e9, 1),
+                    "dose_grad_eval_own_bytes": inf["fused_bytes"],
+                    "rel_err_vs_fp64_values": {"max": float(rel.max()), "mean": float(rel.mean())}})
+        del d
+        if A is not A_u16:
+            A.close()
+    return {"rows_sampled": int(len(rows)), "steps": steps, "variants": out}
+
+
+def batched_subset(steps, warmup, pick=(4, 13, 22)):
+    """Three of the 27 scenario matrices (one per beam shape, unshifted) x 16
+    spot-weight vectors in one graph-captured dose_spmv_batched launch, against
+    the same three as single-vector dose evaluations 16 times over."""
+    import torch
+
+    import paper_2103_09683_gb300 as dose
+
+    nvec = 16
+    mats, Xs, nbytes, nnz = [], [], 0, 0
+    beams = dosegen.batched_beams()
+    for i in pick:
+        csr = dosegen.generate(beams[i])
+        mats.append(dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="u16", values_f64=csr.val))
+        Xs.append(torch.from_numpy(dosegen.spot_weights(csr.ncols, 300 + i, nvec=nvec).reshape(csr.ncols, nvec))
+                  .cuda())
+        nbytes += 6 * csr.nnz + 4 * (csr.nrows + 1) + 4 * nvec * (csr.nrows + csr.ncols)
+        nnz += csr.nnz
+        del csr
+    Ds = [torch.empty((A.nrows, nvec), dtype=torch.float32, device="cuda") for A in mats]
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            dose.spmv_batched(mats, Xs, Ds, stream=stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            dose.spmv_batched(mats, Xs, Ds, stream=stream)
+        ms = _time_calls(graph.replay, steps, warmup)
+    torch.cuda.synchronize()
+    x1 = [X[:, 0].contiguous() for X in Xs]
+    d1 = [torch.empty(A.nrows, dtype=torch.float32, device="cuda") for A in mats]
+    ms_single = _time_calls(lambda: [A.spmv(x, d) for A, x, d in zip(mats, x1, d1)], steps, warmup)
+    for A in mats:
+        A.device_status()
+    peak, _ = _peaks()
+    return {"matrices": list(pick), "nvec": nvec, "nnz": nnz, "ms_per_step": round(ms, 4),
+            "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+            "bytes_per_step": nbytes, "ms_three_single_vector_evals": round(ms_single, 4),
+            "ms_per_vector_batched": round(ms / nvec, 4)}
 
 
 def run_reference(args):
@@ -458,7 +601,11 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot_t / args.steps, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOAD, "nrows": csr.nrows, "ncols": csr.ncols,
-                                           "nnz": csr.nnz},
+                                           "nnz": csr.nnz, "format": "u16+scale",
+                                           "bytes_per_step": oracle_step_bytes(csr.nrows, csr.ncols, csr.nnz),
+                                           "step": REF_STEP, "sample_fraction": round(frac, 6),
+                                           "l2": "host memory (the oracle on the CPU)",
+                                           "parallelism": "single CPU thread"},
            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -991,6 +1138,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the precision variants and the batched subset of the default line")
     ap.add_argument("--autotune", action="store_true", help="time candidate schedules first (dose_autotune)")
     ap.add_argument("--tuning", default="", help="schedule knobs, e.g. tile_nnz=8192,adj_scatter_warps=4")
     ap.add_argument("--matrices", default="", help="batched: subset of the 27 scenario matrices, e.g. 4,13,22")
