@@ -95,7 +95,8 @@ typedef struct {
 
 /* dose_create_matrix flags */
 #define DOSE_CREATE_COMPENSATED 0x1u /* compensated (TwoSum/TwoProduct) accumulation on rows
-                                        longer than 128 entries */
+                                        longer than 128 entries (with DOSE_CREATE_SELL: in the
+                                        chunks whose longest row is longer than 128 entries) */
 #define DOSE_CREATE_U16_INDEX 0x2u   /* dose_spmv reads 16-bit column indices: 2 + value bytes per
                                         entry instead of 4 + value bytes (the reduced index width the
                                         paper's Sec. V proposes as future work); needs ncols <= 65536.
@@ -142,7 +143,8 @@ typedef struct {
                                    default 2^20); read at create only */
     /* layout of the adjoint and fused objective passes (read at create; later calls may
        switch between the layouts that were built):
-         0 = row groups where they apply, else CSR (default);
+         0 = row groups where they apply (and their arrays fit in device memory), else CSR
+             (default);
          1 = CSR (per-row scatter; the row-group layout is not built);
          2 = row groups (create fails with DOSE_ERR_UNSUPPORTED if they do not apply).
        Row groups: up to four consecutive non-empty rows share one list of the union of
@@ -264,15 +266,24 @@ dose_status dose_pg_step(const dose_matrix* A, float* x, const float* p, const f
  * callers cannot create a handle, so A is passed as device CSR arrays.  The
  * paper has no counterpart: this is a deployment variant of dose_adjoint.
  *   row_ptr (nrows+1), col_idx (nnz), values (nnz, fmt-encoded): device memory,
- *   a valid CSR (malformed rows are skipped, never read out of bounds);
+ *   a valid CSR (rows whose pointers run backwards or past nnz, and columns
+ *   >= ncols, are skipped, never read or written out of bounds).  The columns
+ *   of a row must be distinct: nothing checks it on the device, and a row that
+ *   repeats a column makes two lanes update one accumulator word in the same
+ *   instruction, so one of the two updates is lost and g is wrong and may
+ *   differ from run to run (dose_create_matrix rejects such rows);
  *   row_scales: FP8 only, device nrows floats; scale: U16 matrix scale;
  *   r: device nrows floats; g: device ncols floats (written).
  * Scratch is a 4 MiB static __device__ array that every GPU loading the
  * library holds until exit; all calls on a device share it, so calls that
  * overlap on the GPU race -- order them.  The first call on a device looks up
- * the array's address; make it before any stream capture.  ncols beyond the
- * scratch (2^20 floats) or beyond one shared-memory accumulator is rejected with
- * DOSE_ERR_INVALID_ARG.  Deterministic, asynchronous on `stream`. */
+ * the array's address; make it before any stream capture.  That address is
+ * kept for the life of the process: it assumes the device's primary context
+ * lives as long (after cudaDeviceReset, or anything else that tears the context
+ * down, this entry point must not be called again in the same process).
+ * ncols beyond the scratch (2^20 floats) or beyond one shared-memory
+ * accumulator is rejected with DOSE_ERR_INVALID_ARG.  Deterministic,
+ * asynchronous on `stream`. */
 dose_status dose_adjoint_noalloc(uint32_t nrows, uint32_t ncols, uint64_t nnz, const uint32_t* row_ptr,
                                  const uint32_t* col_idx, dose_format fmt, const void* values,
                                  const float* row_scales, float scale, const float* r, float* g,
@@ -299,7 +310,8 @@ dose_status dose_create_multibeam(const dose_csr_desc* beams, int nbeams, unsign
  * quadratic dose term f_s(x) = sum_i w_i ((A_s x)_i - p_i)^2 of each scenario:
  *   DOSE_ROBUST_EXPECTED:   F = sum_s prob_s f_s,  g = sum_s prob_s grad f_s
  *   DOSE_ROBUST_WORST_CASE: F = max_s f_s, g = grad f_s* for the first s* with the
- *                           largest f_s (a subgradient of the maximum). */
+ *                           largest f_s (a subgradient of the maximum); a NaN f_s
+ *                           counts as the largest, so a diverged scenario shows in F. */
 typedef struct dose_scenarios dose_scenarios; /* opaque, library-owned */
 #define DOSE_ROBUST_EXPECTED 0
 #define DOSE_ROBUST_WORST_CASE 1

@@ -397,6 +397,19 @@ static void free_all(dose_matrix* A) {
     cudaFree(A->err);
 }
 
+// Ranges of the forward knobs (no handle needed).
+static dose_status check_tuning_ranges(const Tuning& t) {
+    if (t.tile_nnz < 256 || t.tile_nnz > 16384) return invalid("tuning.tile_nnz must be in [256, 16384]");
+    if (t.tile_rows < 32 || t.tile_rows > 8192) return invalid("tuning.tile_rows must be in [32, 8192]");
+    if (t.coop_nnz < 32 || t.coop_nnz > t.tile_nnz) return invalid("tuning.coop_nnz must be in [32, tile_nnz]");
+    if (t.lane_target < 1 || t.lane_target > 64) return invalid("tuning.lane_target must be in [1, 64]");
+    if (t.stages < 2 || t.stages > 8) return invalid("tuning.stages must be in [2, 8]");
+    if (t.consumer_warps != 4 && t.consumer_warps != 8 && t.consumer_warps != 16)
+        return invalid("tuning.consumer_warps must be 4, 8 or 16");
+    if (t.row_order < 1 || t.row_order > 2) return invalid("tuning.row_order must be 1 or 2");
+    return DOSE_OK;
+}
+
 static dose_status check_tuning(const dose_matrix* A, Tuning& t) {
     if (t.tile_nnz < 256 || t.tile_nnz > 16384) return invalid("tuning.tile_nnz must be in [256, 16384]");
     if (t.tile_rows < 32 || t.tile_rows > 8192) return invalid("tuning.tile_rows must be in [32, 8192]");
@@ -642,6 +655,15 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
     if (!desc->values && !desc->values_f64 && desc->nnz) return invalid("neither values nor values_f64 given");
     if (desc->values && (fmt == DOSE_FMT_U16_SCALE || fmt == DOSE_FMT_FP8E4M3_ROWSCALE) && !desc->scales)
         return invalid("scales are NULL for this format");
+    {
+        // knob ranges first: a bad tuning is refused before any CUDA call
+        Tuning t0;
+        AdjTuning a0;
+        merge_tuning(t0, a0, tuning);
+        dose_status st = check_tuning_ranges(t0);
+        if (st == DOSE_OK) st = check_adj_tuning(a0);
+        if (st != DOSE_OK) return st;
+    }
     const uint32_t nrows = desc->nrows, ncols = desc->ncols;
     const uint64_t nnz = desc->nnz;
     const size_t esize = value_bytes(fmt);
@@ -849,10 +871,20 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
         std::string why;
         A->rg.sched.grid = A->adj.grid;
         bool ok = build_row_groups(A.get(), A->host_row_ptr.data(), col.data(), vals.data(), &why, &e);
-        if (!ok && e != cudaSuccess) return fail(e, "row-group layout");
+        if (!ok && e != cudaSuccess) {
+            // the layout is optional by default: without the memory for it the
+            // handle keeps the CSR passes (asked for explicitly, it is an error)
+            if (e != cudaErrorMemoryAllocation || A->adj_tuning.layout == 2) return fail(e, "row-group layout");
+            cudaGetLastError();
+            why = "its arrays do not fit in device memory";
+        }
         if (ok) {
             e = rg_schedule(A.get(), A->adj_tuning);
-            if (e == cudaErrorInvalidValue) {
+            if (e == cudaErrorMemoryAllocation && A->adj_tuning.layout != 2) {
+                cudaGetLastError();
+                free_row_groups(A.get());
+                ok = false;
+            } else if (e == cudaErrorInvalidValue) {
                 why = "tuning.rg_tile_union is smaller than a group's union of columns";
                 free_row_groups(A.get());
                 ok = false;

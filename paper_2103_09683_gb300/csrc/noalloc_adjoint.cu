@@ -15,7 +15,13 @@
 // each call overwrites the part it uses, so calls that overlap on the GPU (two
 // streams, or two host threads) race on it; order them.  The first call on a
 // device looks up the array's device address (cudaGetSymbolAddress) and caches
-// it; make that first call before any stream capture.
+// it for the rest of the process, which assumes that the device's primary
+// context lives as long; make that first call before any stream capture.
+//
+// The columns of a row must be distinct (dose_create_matrix rejects rows that
+// repeat one; this entry point takes the caller's arrays unchecked): the lanes
+// of a warp update their accumulator words with plain read-modify-writes, so a
+// repeated column loses one of its updates.
 //
 // The reduction order is fixed (per-warp shared accumulators in row order, warp
 // order, then CTA order), so results are bitwise reproducible for the same

@@ -39,7 +39,9 @@ namespace {
 constexpr int kMaxScenarios = 64;
 
 // F and G (and optionally the projected-gradient update of x) from the
-// per-scenario f_s, g_s.  Every thread finds s* itself (S <= 64 values).
+// per-scenario f_s, g_s.  Every thread finds s* itself (S <= 64 values): the
+// first scenario with the largest f_s, a NaN counting as larger than every
+// number (a diverged scenario is reported, whatever its position).
 __global__ void __launch_bounds__(256) robust_combine(uint32_t S, uint32_t ncols, int mode,
                                                       const double* __restrict__ prob,
                                                       const double* __restrict__ f_s, const float* __restrict__ g_s,
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(256) robust_combine(uint32_t S, uint32_t ncols
     uint32_t best = 0;
     if (mode == DOSE_ROBUST_WORST_CASE)
         for (uint32_t s = 1; s < S; ++s)
-            if (f_s[s] > f_s[best]) best = s;
+            if (!isnan(f_s[best]) && (isnan(f_s[s]) || f_s[s] > f_s[best])) best = s;
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j == 0) {
         double t = 0.0;

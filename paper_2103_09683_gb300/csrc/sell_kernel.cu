@@ -22,8 +22,12 @@
 // Kernel: every warp takes chunks c = warp id, + number of warps, ...; lane l
 // sums its row over the chunk's groups with four accumulators (combined as
 // (0 + 1) + (2 + 3)), x in shared memory; the row's dose is written to
-// d[perm].  A row is summed by one lane in storage order, so the result does
-// not depend on the chunk-to-warp assignment: bitwise reproducible.
+// d[perm].  With DOSE_CREATE_COMPENSATED, the lanes of a chunk whose longest
+// row has more than 128 entries accumulate compensated sums instead (Dot2 of
+// Ogita, Rump and Oishi per accumulator: TwoProduct by FMA, TwoSum; the four
+// (sum, error) pairs combined by TwoSum).  A row is summed by one lane in
+// storage order, so the result does not depend on the chunk-to-warp
+// assignment: bitwise reproducible.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -51,7 +55,7 @@ struct SellParams {
     uint32_t ncols, nchunks;
 };
 
-template <int FMT, uint32_t IW, bool XSMEM>
+template <int FMT, uint32_t IW, bool XSMEM, bool COMP>
 __global__ void __launch_bounds__(kSellWarps * 32) sell_spmv_kernel(const SellParams p) {
     using T = typename Fmt<FMT>::T;
     extern __shared__ __align__(16) float xs_smem[];
@@ -68,6 +72,8 @@ __global__ void __launch_bounds__(kSellWarps * 32) sell_spmv_kernel(const SellPa
         const T* vp = static_cast<const T*>(p.val) + base;
         const unsigned char* cp = static_cast<const unsigned char*>(p.col) + base * IW;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float err[4] = {0.f, 0.f, 0.f, 0.f};  // compensated chunks: the running error terms
+        const bool comp = COMP && ch.y * 4 > kCompThreshold;
         // raw words of one group: four column indices (16 or 8 bytes) and four values (16, 8 or 4 bytes)
         struct Raw {
             uint4 c, v;
@@ -104,8 +110,19 @@ __global__ void __launch_bounds__(kSellWarps * 32) sell_spmv_kernel(const SellPa
             } else {
                 Fmt<FMT>::dec4(r.v.x, r.v.y, a);
             }
+            if (COMP && comp) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] = __fmaf_rn(a[u], XSMEM ? xs[cc[u]] : __ldg(xs + cc[u]), acc[u]);
+                for (int u = 0; u < 4; ++u) {
+                    float pr, ep, t, es;
+                    dev::two_prod(a[u], XSMEM ? xs[cc[u]] : __ldg(xs + cc[u]), pr, ep);
+                    dev::two_sum(acc[u], pr, t, es);
+                    acc[u] = t;
+                    err[u] = __fadd_rn(err[u], __fadd_rn(es, ep));
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = __fmaf_rn(a[u], XSMEM ? xs[cc[u]] : __ldg(xs + cc[u]), acc[u]);
+            }
         };
         // two groups in flight ahead of the one being summed
         Raw r0 = ch.y > 0 ? load(0) : Raw{}, r1 = ch.y > 1 ? load(1) : Raw{};
@@ -117,7 +134,19 @@ __global__ void __launch_bounds__(kSellWarps * 32) sell_spmv_kernel(const SellPa
         }
         const uint32_t row = __ldg(p.perm + (size_t)c * kSellC + lane);
         if (row != 0xFFFFFFFFu) {
-            float v = __fadd_rn(__fadd_rn(acc[0], acc[1]), __fadd_rn(acc[2], acc[3]));
+            float v;
+            if (COMP && comp) {
+                float sum = acc[0], e = err[0];
+                for (int u = 1; u < 4; ++u) {
+                    float t, es;
+                    dev::two_sum(sum, acc[u], t, es);
+                    sum = t;
+                    e = __fadd_rn(e, __fadd_rn(err[u], es));
+                }
+                v = __fadd_rn(sum, e);
+            } else {
+                v = __fadd_rn(__fadd_rn(acc[0], acc[1]), __fadd_rn(acc[2], acc[3]));
+            }
             if (FMT == DOSE_FMT_U16_SCALE) v = __fmul_rn(p.scale, v);
             if (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) v = __fmul_rn(__ldg(p.row_scale + row), v);
             p.d[row] = v;
@@ -129,7 +158,9 @@ template <int FMT, uint32_t IW>
 cudaError_t launch_t(const dose_matrix* A, const SellParams& p, cudaStream_t s) {
     const bool xsmem = A->ncols <= kXSmemMaxCols;
     const size_t smem = xsmem ? (size_t)A->ncols * 4 : 0;
-    auto k = xsmem ? sell_spmv_kernel<FMT, IW, true> : sell_spmv_kernel<FMT, IW, false>;
+    const bool comp = (A->flags & DOSE_CREATE_COMPENSATED) != 0;
+    auto k = xsmem ? (comp ? sell_spmv_kernel<FMT, IW, true, true> : sell_spmv_kernel<FMT, IW, true, false>)
+                   : (comp ? sell_spmv_kernel<FMT, IW, false, true> : sell_spmv_kernel<FMT, IW, false, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint32_t grid = std::max(1u, std::min<uint32_t>((uint32_t)A->sm_count * kSellCtasPerSm,

@@ -97,3 +97,28 @@ def test_sell_copy_and_scenario_set_report_oom(monkeypatch):
     S = dose.ScenarioSet([A, A])
     S.close()
     A.device_status()
+
+
+def test_row_group_layout_past_the_limit_falls_back_to_csr(monkeypatch):
+    """The row-group arrays (union values: 4 stored values per union column) are
+    larger than the CSR column indices; with the limit between the two, the
+    default layout keeps the CSR passes and still matches the oracle, while an
+    explicit adj_layout = 2 reports the out-of-memory failure."""
+    lens = np.random.default_rng(81).integers(1, 200, 4096)
+    csr = dosegen.random_csr(4096, 600, seed=81, lengths=lens)
+    enc = oracle.encode(csr, oracle.U16_SCALE)
+    col_bytes = 4 * ((csr.nnz + 3) // 4 * 4 + 16)
+    monkeypatch.setenv("DOSE_TEST_ALLOC_LIMIT", str(col_bytes))
+    with pytest.raises(dose.DoseError) as ei:
+        make(csr, "u16", tuning=dict(adj_layout=2))
+    assert ei.value.status == OOM and "row-group layout" in str(ei.value)
+    A, enc = make(csr, "u16")
+    monkeypatch.delenv("DOSE_TEST_ALLOC_LIMIT")
+    inf = A.info()
+    assert inf["rg_groups"] == 0 and inf["adj_layout_fused"] == 1
+    r = np.random.default_rng(82).normal(size=csr.nrows).astype(np.float32)
+    g = A.adjoint(torch.from_numpy(r).cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle.spmv_t(csr.nrows, csr.ncols, enc.row_ptr, enc.col, enc.decoded, r)
+    gabs = oracle.abs_spmv_t(csr.nrows, csr.ncols, enc.row_ptr, enc.col, enc.decoded, r)
+    assert np.all(np.abs(g - ref) <= 1e-5 * gabs + 1e-30)
+    A.device_status()

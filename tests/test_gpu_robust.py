@@ -198,3 +198,44 @@ def test_scenario_set_rejects_mismatched_shapes(scenarios, plan):
         dose.ScenarioSet([scen[0][0], other])
     with pytest.raises(dose.DoseError):
         dose.ScenarioSet([scen[0][0], scen[1][0]], prob=[0.7, 0.7])
+
+
+@pytest.mark.parametrize("nan_at", [0, 1, 2])
+def test_worst_case_reports_a_diverged_scenario(nan_at):
+    """Three scenarios of one shape; in scenario nan_at one row reaches spot 0 with
+    weight 0, and x_0 = 1e30 makes that row's dose overflow in (d - p)^2, so
+    w (d - p)^2 = 0 * inf is NaN there: the worst case must be that scenario
+    (F NaN, its g copied) wherever it sits among the scenarios."""
+    nrows, ncols = 64, 32
+    rng = np.random.default_rng(51)
+    mats = []
+    for s in range(3):
+        # columns 1 .. ncols-1 only; the NaN scenario's row 5 also reaches column 0
+        base = dosegen.random_csr(nrows, ncols - 1, seed=60 + s, lengths=rng.integers(1, 6, nrows))
+        rp, cols, vals = [0], [], []
+        brp = base.row_ptr.astype(np.int64)
+        for i in range(nrows):
+            c = list(base.col[brp[i]:brp[i + 1]] + 1)
+            v = list(base.val[brp[i]:brp[i + 1]])
+            if s == nan_at and i == 5:
+                c, v = [0] + c, [0.5] + v
+            cols += c
+            vals += v
+            rp.append(len(cols))
+        mats.append(dose.DoseMatrix.from_csr(np.asarray(rp, dtype=np.uint32), np.asarray(cols, dtype=np.uint32),
+                                             ncols=ncols, fmt="f32",
+                                             values=np.asarray(vals, dtype=np.float32).view(np.uint32)))
+    x = np.full(ncols, 0.5, dtype=np.float32)
+    x[0] = 1e30
+    p = np.zeros(nrows, dtype=np.float32)
+    w = np.ones(nrows, dtype=np.float32)
+    w[5] = 0.0
+    S = dose.ScenarioSet(mats)
+    f_scen = torch.empty(3, dtype=torch.float64, device="cuda")
+    F, G, fs = S.robust_quadratic(_to(x), _to(p), _to(w), mode="worst", f_scen=f_scen)
+    fs = fs.cpu().numpy()
+    assert np.isnan(fs[nan_at]) and np.all(np.isfinite(np.delete(fs, nan_at)))
+    assert np.isnan(float(F.item()))
+    _, g_alone = mats[nan_at].fwd_adj_quadratic(_to(x), _to(p), _to(w))
+    assert np.array_equal(G.cpu().numpy().view(np.uint32), g_alone.cpu().numpy().view(np.uint32))
+    S.close()

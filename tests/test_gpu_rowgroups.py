@@ -201,3 +201,31 @@ def test_row_groups_pg_graph_matches_eager(tiny):
     fe = dose.PGSolver(A, xe, _to(p), _to(w), eta, 100, use_graph=False).run().cpu().numpy()
     assert np.array_equal(fe.view(np.uint64), fh.view(np.uint64))
     assert np.array_equal(xe.cpu().numpy().view(np.uint32), xg.cpu().numpy().view(np.uint32))
+
+
+def test_pg_solver_resumes_from_a_checkpoint(tiny, tmp_path):
+    """Run 50 graph-captured projected-gradient steps, checkpoint, then resume in
+    a new solver (its own graph, x overwritten in place under the captured
+    pointer) for 50 more: the final x and the f history of the second half are
+    bitwise those of 100 uninterrupted steps."""
+    p, w = dosegen.ellipsoid_target(dosegen.TINY)
+    x0 = dosegen.spot_weights(tiny.ncols, dosegen.weight_seed(dosegen.TINY))
+    A, enc = make(tiny, "u16")
+    eta = oracle.pg_step_size(tiny.nrows, tiny.ncols, enc.row_ptr, enc.col, enc.decoded, w)
+    pt, wt = _to(p), _to(w)
+    x_full = _to(x0.copy())
+    full = dose.PGSolver(A, x_full, pt, wt, eta, 50, use_graph=True)
+    f_first = full.run().cpu().numpy().copy()
+    f_second = full.run().cpu().numpy().copy()
+    x_a = _to(x0.copy())
+    first = dose.PGSolver(A, x_a, pt, wt, eta, 50, use_graph=True)
+    assert np.array_equal(first.run().cpu().numpy().view(np.uint64), f_first.view(np.uint64))
+    path = str(tmp_path / "pg50.npz")
+    first.checkpoint(path)
+    x_b = _to(np.zeros_like(x0))
+    second = dose.PGSolver(A, x_b, pt, wt, eta, 50, use_graph=True)  # captured before the state is loaded
+    assert second.resume(path) == 50
+    f_b = second.run().cpu().numpy()
+    assert np.array_equal(f_b.view(np.uint64), f_second.view(np.uint64))
+    assert np.array_equal(x_b.cpu().numpy().view(np.uint32), x_full.cpu().numpy().view(np.uint32))
+    assert second.steps_done == 100
