@@ -571,7 +571,8 @@ def batched_subset(steps, warmup, pick=(4, 13, 22)):
     return {"matrices": list(pick), "nvec": nvec, "nnz": nnz, "ms_per_step": round(ms, 4),
             "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
             "bytes_per_step": nbytes, "ms_three_single_vector_evals": round(ms_single, 4),
-            "ms_per_vector_batched": round(ms / nvec, 4)}
+            "ms_per_vector_batched": round(ms / nvec, 4),
+            "layout": "row groups" if dose.spmv_batched_plan(mats, nvec)[0] == 2 else "CSR"}
 
 
 def run_reference(args):
@@ -649,6 +650,8 @@ def run_batched(args):
             sample = (csr, Xs[-1].cpu().numpy())
         del csr
     Ds = [torch.empty((A.nrows, nvec), dtype=torch.float32, device=device) for A in mats]
+    layout, launches = dose.spmv_batched_plan(mats, nvec)
+    kname = "rg_spmm_kernel" if layout == 2 else "spmm_staged_kernel"
     stream = torch.cuda.Stream(device)
     stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):
@@ -709,13 +712,15 @@ def run_batched(args):
                    "matrices": len(mats), "nvec": nvec, "nnz": nnz, "nrows": nrows,
                    "bytes_per_step": nbytes, "l2": "inputs larger than L2 (A streams ~11 GB per step)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "spmm_staged_kernel", "achieved": round(gbs, 1), "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": kname + (" + rg_spmm_zero" if layout == 2 else ""),
+                     "achieved": round(gbs, 1), "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "unit": "GB/s", "frac": round(gbs / peak, 4), "traffic": _traffic("spmm_staged_kernel")},
+                     "unit": "GB/s", "frac": round(gbs / peak, 4), "traffic": _traffic(kname)},
+        "layout": "row groups" if layout == 2 else "CSR",
         "e2e": {"value": round(nbytes / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s", "ms_per_step": round(e2e_ms, 3),
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": K,
+        "gpu_launches": K * launches,
         "clocks": clk,
     }
     if sample is not None:

@@ -241,6 +241,14 @@ dose_status dose_spmv_f64(const dose_matrix* A, const double* x, double* d, unsi
 dose_status dose_spmv_batched(const dose_matrix* const* A, int count, const float* const* X,
                               float* const* D, int nvec, void* stream);
 
+/* The form dose_spmv_batched takes for these matrices, without launching
+ * anything: *layout = 2 when every matrix is run on its row-group layout (one
+ * launch for rows without entries, one for the rest, per 32 matrices), 1 for
+ * the CSR forms (one launch per 64 matrices), 0 for count = 0; *launches = the
+ * kernels one call launches.  Host only; the same arguments as dose_spmv_batched
+ * (layout and launches must not be NULL; nvec in [1, 16]). */
+dose_status dose_spmv_batched_plan(const dose_matrix* const* A, int count, int nvec, int* layout, int* launches);
+
 /* g = A^T r, the adjoint (gradient of any dose objective with dD/dd = r).
  * r: device, nrows floats, 16-byte aligned.  g: device, ncols floats.  Deterministic: per-warp
  * private accumulators combined in a fixed order, no atomics on values.  Runs on the

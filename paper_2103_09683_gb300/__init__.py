@@ -97,6 +97,7 @@ EXPORTS = {
     "dose_spmv": (ctypes.c_int, [_P, _P, _P, _P]),
     "dose_spmv_f64": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint, _P]),
     "dose_spmv_batched": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "dose_spmv_batched_plan": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "dose_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
     "dose_fwd_adj_quadratic": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "dose_pg_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
@@ -457,6 +458,16 @@ def spmv_batched(mats, Xs, Ds=None, stream=None):
                                  for A, D in zip(mats, Ds)])
     _check(load().dose_spmv_batched(hs, n, xp, dp, nvec, _stream_handle(stream)))
     return Ds
+
+
+def spmv_batched_plan(mats, nvec):
+    """(layout, launches) of dose_spmv_batched for these matrices: layout 2 = row
+    groups, 1 = CSR; launches = kernels per call."""
+    n = len(mats)
+    hs = (ctypes.c_void_p * max(n, 1))(*[A.handle.value for A in mats])
+    lay, nl = ctypes.c_int(), ctypes.c_int()
+    _check(load().dose_spmv_batched_plan(hs, n, int(nvec), ctypes.byref(lay), ctypes.byref(nl)))
+    return lay.value, nl.value
 
 
 class ScenarioSet:

@@ -493,6 +493,21 @@ cudaError_t launch_staged(const dose_matrix* const* A, const float* const* X, fl
 
 }  // namespace
 
+void spmm_batched_plan(const dose_matrix* const* A, int count, int* layout, int* launches) {
+    bool rg = count > 0;
+    for (int base = 0; base < count && rg; base += (int)kRgSpmmMaxPerLaunch)
+        rg = rg_spmm_applies(A + base, std::min<int>(count - base, (int)kRgSpmmMaxPerLaunch), nullptr, nullptr);
+    const int per = rg ? (int)kRgSpmmMaxPerLaunch : kMaxBatchPerLaunch;
+    int n = 0;
+    for (int base = 0; base < count; base += per) {
+        uint64_t rows = 0;
+        for (int i = base; i < std::min(count, base + per); ++i) rows += A[i]->nrows;
+        if (rows) n += rg ? 2 : 1;
+    }
+    *layout = rg ? 2 : 1;
+    *launches = n;
+}
+
 cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const float* const* X, float* const* D,
                                 int nvec, cudaStream_t s, std::string* why) {
     int dev = A[0]->device;
@@ -501,6 +516,11 @@ cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const fl
             *why = "dose_spmv_batched: all matrices must live on one device";
             return cudaSuccess;
         }
+    // the row-group form where every matrix has that layout (rg_spmm.cu)
+    bool rg = true;
+    for (int base = 0; base < count && rg; base += (int)kRgSpmmMaxPerLaunch)
+        rg = rg_spmm_applies(A + base, std::min<int>(count - base, (int)kRgSpmmMaxPerLaunch), nullptr, nullptr);
+    if (rg) return launch_rg_spmm(A, count, X, D, nvec, s);
     const uint32_t nq = nvec <= 4 ? 1 : nvec <= 8 ? 2 : 4;
     for (int base = 0; base < count; base += kMaxBatchPerLaunch) {
         const int n = count - base < kMaxBatchPerLaunch ? count - base : kMaxBatchPerLaunch;

@@ -1096,6 +1096,19 @@ dose_status dose_spmv_batched(const dose_matrix* const* A, int count, const floa
     return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_spmv_batched launch");
 }
 
+dose_status dose_spmv_batched_plan(const dose_matrix* const* A, int count, int nvec, int* layout, int* launches) {
+    if (!layout || !launches) return invalid("dose_spmv_batched_plan: null output");
+    if (count < 0 || count > 4096) return invalid("dose_spmv_batched_plan: count must be in [0, 4096]");
+    if (nvec < 1 || nvec > 16) return invalid("dose_spmv_batched_plan: nvec must be in [1, 16]");
+    if (count && !A) return invalid("dose_spmv_batched_plan: null array");
+    for (int m = 0; m < count; ++m)
+        if (!A[m]) return invalid("dose_spmv_batched_plan: null matrix " + std::to_string(m));
+    *layout = 0;
+    *launches = 0;
+    if (count) spmm_batched_plan(A, count, layout, launches);
+    return DOSE_OK;
+}
+
 dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     if (!A || !out) return invalid("dose_matrix_info: null argument");
     std::memset(out, 0, sizeof(*out));

@@ -268,6 +268,15 @@ bool rg_active(const dose_matrix* A, bool quad);
 cudaError_t launch_rg(const dose_matrix* A, int mode, const float* x, const float* p, const float* w,
                       const float* r, float* d, double* f, float* g, float* x_update, float eta, cudaStream_t s);
 uint64_t rg_fused_bytes(const dose_matrix* A, bool with_d);
+// Batched SpMM on the row-group layout (rg_spmm.cu): whether it applies to the
+// matrices A[0 .. count) (count <= kRgSpmmMaxPerLaunch), and the launches.
+constexpr uint32_t kRgSpmmMaxPerLaunch = 32;
+bool rg_spmm_applies(const dose_matrix* const* A, int count, size_t* smem, uint32_t* depth);
+// Which form dose_spmv_batched takes for these matrices (2 row groups, 1 CSR)
+// and how many kernels one call launches.
+void spmm_batched_plan(const dose_matrix* const* A, int count, int* layout, int* launches);
+cudaError_t launch_rg_spmm(const dose_matrix* const* A, int count, const float* const* X, float* const* D, int nvec,
+                           cudaStream_t s);
 uint64_t rg_adjoint_bytes(const dose_matrix* A);
 // Sum of the per-CTA partials (g, f) in a fixed order; optional projected-gradient step.
 cudaError_t launch_adjoint_finalize(const dose_matrix* A, const float* g_part, const uint32_t* wlo, uint32_t wwidth,

@@ -129,6 +129,12 @@ def test_create_rejects_invalid_csr_on_host(lib):
     assert lib.dose_destroy(None) == 0
     assert lib.dose_spmv(None, None, None, None) == 1
     assert lib.dose_spmv_batched(None, -1, None, None, 16, None) == 1
+    lay, nl = ctypes.c_int(7), ctypes.c_int(7)
+    assert lib.dose_spmv_batched_plan(None, 0, 16, ctypes.byref(lay), ctypes.byref(nl)) == 0
+    assert (lay.value, nl.value) == (0, 0)
+    assert lib.dose_spmv_batched_plan(None, 0, 17, ctypes.byref(lay), ctypes.byref(nl)) == 1
+    assert lib.dose_spmv_batched_plan(None, 1, 16, ctypes.byref(lay), ctypes.byref(nl)) == 1
+    assert lib.dose_spmv_batched_plan(None, 0, 16, None, ctypes.byref(nl)) == 1
 
 
 def test_create_rejects_bad_descriptors_and_codes_on_host(lib):

@@ -229,3 +229,82 @@ def test_pg_solver_resumes_from_a_checkpoint(tiny, tmp_path):
     assert np.array_equal(f_b.view(np.uint64), f_second.view(np.uint64))
     assert np.array_equal(x_b.cpu().numpy().view(np.uint32), x_full.cpu().numpy().view(np.uint32))
     assert second.steps_done == 100
+
+
+def _beam_batch(n=4):
+    from dataclasses import replace
+    b2 = replace(dosegen.TINY, grid=(40, 36, 24), lattice=(30, 24), spacing=(40 / 30, 36 / 24),
+                 seed=dosegen.SEED0 + 50)
+    out = []
+    for base in (dosegen.TINY, b2):
+        for sh in ((-3.0, 0.0), (3.0, 3.0)):
+            out.append(dosegen.generate(replace(base, shift=sh)))
+    return out[:n]
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("nvec", [1, 3, 8, 13, 16])
+def test_row_group_batched_spmm(fmt, nvec):
+    """dose_spmv_batched on matrices of one format that all have the row-group
+    layout: each D against the oracle's SpMM (per element, FP32 bound), rows
+    without entries exactly 0 although D held garbage, the tail past each D
+    untouched, bitwise repeatable, and within the bound of the same batch on
+    CSR-layout handles."""
+    mats = _beam_batch()
+    handles, csr_handles, encs, Xs, bufs, Ds = [], [], [], [], [], []
+    for i, m in enumerate(mats):
+        A, enc = make(m, fmt)
+        assert A.info()["rg_groups"] > 0
+        C, _ = make(m, fmt, tuning=dict(adj_layout=1))
+        handles.append(A)
+        csr_handles.append(C)
+        encs.append(enc)
+        Xs.append(_to(dosegen.spot_weights(m.ncols, 400 + i, nvec=nvec).reshape(m.ncols, nvec)))
+        buf = torch.full((m.nrows * nvec + 37,), -7.0, dtype=torch.float32, device="cuda")
+        bufs.append(buf)
+        Ds.append(buf[:m.nrows * nvec].view(m.nrows, nvec))
+    assert dose.spmv_batched_plan(handles, nvec) == (2, 2)
+    assert dose.spmv_batched_plan(csr_handles, nvec) == (1, 1)
+    dose.spmv_batched(handles, Xs, Ds)
+    first = [D.clone() for D in Ds]
+    for m, enc, X, D, buf in zip(mats, encs, Xs, Ds, bufs):
+        ref = oracle.spmm(m.nrows, enc.row_ptr, enc.col, enc.decoded, X.cpu().numpy().astype(np.float64))
+        fwd_check(D.cpu().numpy().reshape(-1), ref.reshape(-1))
+        assert torch.all(buf[m.nrows * nvec:] == -7.0)
+    dose.spmv_batched(handles, Xs, Ds)
+    for D, F in zip(Ds, first):
+        assert torch.equal(D, F)
+    Dc = dose.spmv_batched(csr_handles, Xs)
+    for m, enc, X, D, C in zip(mats, encs, Xs, Ds, Dc):
+        ref = oracle.spmm(m.nrows, enc.row_ptr, enc.col, enc.decoded, X.cpu().numpy().astype(np.float64))
+        fwd_check(C.cpu().numpy().reshape(-1), ref.reshape(-1))
+
+
+def test_row_group_batched_spmm_in_a_graph():
+    """The row-group batch captured in a CUDA graph: the replay gives the same
+    bits as the eager call; small stage tiles spread each matrix over many
+    stages and the ring runs on across the matrices."""
+    mats = _beam_batch()
+    handles, Xs = [], []
+    for i, m in enumerate(mats):
+        A, _ = make(m, "u16", tuning=dict(rg_tile_union=320, rg_tile_rows=256))
+        handles.append(A)
+        Xs.append(_to(dosegen.spot_weights(m.ncols, 500 + i, nvec=16).reshape(m.ncols, 16)))
+    eager = [D.clone() for D in dose.spmv_batched(handles, Xs)]
+    Ds = [torch.empty_like(D) for D in eager]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        dose.spmv_batched(handles, Xs, Ds, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        dose.spmv_batched(handles, Xs, Ds, stream=s)
+    for D in Ds:
+        D.fill_(3.0)
+    graph.replay()
+    torch.cuda.synchronize()
+    for D, E in zip(Ds, eager):
+        assert torch.equal(D, E)
+    for A in handles:
+        A.device_status()
