@@ -243,7 +243,7 @@ dose_status dose_spmv_batched(const dose_matrix* const* A, int count, const floa
 
 /* The form dose_spmv_batched takes for these matrices, without launching
  * anything: *layout = 2 when every matrix is run on its row-group layout (one
- * launch for rows without entries, one for the rest, per 32 matrices), 1 for
+ * launch per 32 matrices), 1 for
  * the CSR forms (one launch per 64 matrices), 0 for count = 0; *launches = the
  * kernels one call launches.  Host only; the same arguments as dose_spmv_batched
  * (layout and launches must not be NULL; nvec in [1, 16]). */

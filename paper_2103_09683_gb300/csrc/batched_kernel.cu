@@ -502,7 +502,7 @@ void spmm_batched_plan(const dose_matrix* const* A, int count, int* layout, int*
     for (int base = 0; base < count; base += per) {
         uint64_t rows = 0;
         for (int i = base; i < std::min(count, base + per); ++i) rows += A[i]->nrows;
-        if (rows) n += rg ? 2 : 1;
+        if (rows) ++n;
     }
     *layout = rg ? 2 : 1;
     *launches = n;

@@ -6,13 +6,16 @@
 // matrix's row-group stages (the column-windowed schedule of rg_layout.cu),
 // streamed by a producer thread through a shared-memory ring that runs on from
 // matrix to matrix.  The workers hold the CTA's window of X_m in shared memory
-// (16 floats per column, zero past nvec, and a zero column after the window).
-// A warp takes a whole group: lane l = 8 q + t computes row t / 2 of the group
-// for vectors 8 (t % 2) .. 8 (t % 2) + 7 over the union positions u = q, q + 4,
-// ... (one X-row gather serves the four rows of the group), then the four
-// lane slices q are added by a fixed butterfly and every lane stores two of its
-// row's results.  Rows without entries get D = 0 from a separate pass that
-// runs beside it (the SpMM kernel is its programmatic dependent).
+// (16 floats per column, zero past nvec, and a zero column after the window),
+// laid out so that one 16-byte load of 8 columns that differ mod 8 is one
+// shared-memory wavefront.  A warp takes a whole group: lane l = 4 q + g
+// computes row g of the group for all 16 vectors over the union positions
+// u = q, q + 8, ... (one X-row gather serves the four rows of the group; the
+// union order of rg_layout.cu sorts each 32 positions by column, so 8
+// consecutive positions mostly differ mod 8), then the eight lane slices q are
+// added by a fixed transposed butterfly that leaves every lane two of its row's
+// results to store.  Two more warps write D = 0 for the CTA's share of the rows
+// without entries while the workers compute.
 // Deterministic: static assignment of groups to warps, fixed per-lane order,
 // fixed butterfly.
 #include "rg_common.cuh"
@@ -24,9 +27,15 @@ namespace dose {
 namespace {
 
 constexpr uint32_t kMmMaxPerLaunch = kRgSpmmMaxPerLaunch;
-constexpr uint32_t kMmWorkers = 16;      // worker warps (plus one producer)
+constexpr uint32_t kMmWorkers = 16;      // worker warps (plus one producer and the zero warps)
+constexpr uint32_t kMmZeroWarps = 2;     // warps writing the rows without entries
 constexpr uint32_t kMmHeader = 1024;     // mbarriers
-constexpr uint32_t kMmXStride = 16;      // floats per column of the staged window of X
+constexpr uint32_t kMmSmemBudget = kMaxSmemPerBlock;
+constexpr uint32_t kMmXStride = 16;      // floats per column of the staged window of X (vectors <= 16)
+
+// Shared bytes of a window of W columns of X and the zero column after it
+// (whole blocks of 8 columns x 16 floats).
+__host__ __device__ constexpr uint32_t mm_xs_bytes(uint32_t W) { return ((W + 1 + 7) / 8 * 8 * 64 + 127) / 128 * 128; }
 
 struct MmItem {
     const uint4* grp;
@@ -36,6 +45,7 @@ struct MmItem {
     const uint32_t* cta_begin;
     const uint32_t* wlo;
     const float* row_scale;  // FP8 (padded to whole 16-byte pieces)
+    const uint32_t* mask;    // rows with entries, one bit each
     const float* X;          // ncols x nvec, row-major
     float* D;                // nrows x nvec, row-major
     float scale;             // U16
@@ -49,37 +59,34 @@ struct MmParams {
     int* err;
 };
 
-// Rows without entries: D = 0 (every matrix of the launch, grid-stride over
-// 16-byte pieces of D when nvec is a multiple of 4, else over floats).
-struct MmZero {
-    const uint32_t* mask[kMmMaxPerLaunch];
-    float* D[kMmMaxPerLaunch];
-    uint32_t nrows[kMmMaxPerLaunch];
-    uint32_t count, nvec;
-};
-
-__global__ void __launch_bounds__(256) rg_spmm_zero(const __grid_constant__ MmZero z) {
-    // the SpMM kernel (launched next, as a programmatic dependent) writes the
-    // other rows and may run beside this one
-    asm volatile("griddepcontrol.launch_dependents;");
-    const uint32_t T = gridDim.x * blockDim.x;
-    for (uint32_t m = 0; m < z.count; ++m) {
-        float* D = z.D[m];
-        const uint32_t* mask = z.mask[m];
-        if ((z.nvec & 3u) == 0 && (reinterpret_cast<uintptr_t>(D) & 15u) == 0) {
-            // 16-byte pieces, consecutive threads on consecutive pieces
-            const uint32_t per = z.nvec / 4;  // 1 .. 4
-            const uint64_t n = (uint64_t)z.nrows[m] * per;
-            for (uint64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += T) {
-                const uint32_t r = per == 4 ? (uint32_t)(i >> 2) : (uint32_t)(i / per);
-                if (!((__ldg(mask + (r >> 5)) >> (r & 31)) & 1u))
-                    reinterpret_cast<float4*>(D)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        } else {
-            const uint64_t n = (uint64_t)z.nrows[m] * z.nvec;
-            for (uint64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += T) {
-                const uint32_t r = (uint32_t)(i / z.nvec);
-                if (!((__ldg(mask + (r >> 5)) >> (r & 31)) & 1u)) D[i] = 0.0f;
+// Rows without entries: D = 0.  Zero warp z of NZ takes the CTA's share of the
+// matrix's row-mask words (32 rows each) 32 words at a time and writes the
+// rows without entries, consecutive lanes on consecutive 16-byte pieces
+// (4-byte pieces unless nvec is a multiple of 4 and D 16-byte aligned).
+__device__ void mm_zero_rows(const uint32_t* mask, float* D, uint32_t nrows, uint32_t nv, uint32_t z, uint32_t NZ,
+                             uint32_t lane) {
+    const uint32_t nword = (nrows + 31) / 32;
+    const uint32_t wb = (uint32_t)((uint64_t)nword * blockIdx.x / gridDim.x);
+    const uint32_t we = (uint32_t)((uint64_t)nword * (blockIdx.x + 1) / gridDim.x);
+    const bool vec = (nv & 3u) == 0 && (reinterpret_cast<uintptr_t>(D) & 15u) == 0;
+    const uint32_t per = vec ? nv / 4 : nv;  // pieces per row
+    for (uint32_t w0 = wb + 32 * z; w0 < we; w0 += 32 * NZ) {
+        const uint32_t mine = w0 + lane < we ? __ldg(mask + w0 + lane) : 0xFFFFFFFFu;
+        for (uint32_t i = 0; i < 32 && w0 + i < we; ++i) {
+            uint32_t word = __shfl_sync(0xffffffffu, mine, i);
+            const uint32_t r0 = 32 * (w0 + i);
+            if (r0 + 32 > nrows) word |= ~0u << (nrows - r0);  // rows past the end: nothing to write
+            if (word == 0xFFFFFFFFu) continue;
+            if (vec) {
+                float4* d4 = reinterpret_cast<float4*>(D + (size_t)r0 * nv);
+                for (uint32_t k = lane; k < 32 * per; k += 32) {
+                    const uint32_t r = per == 4 ? k >> 2 : k / per;
+                    if (!((word >> r) & 1u)) d4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            } else {
+                float* d = D + (size_t)r0 * nv;
+                for (uint32_t k = lane; k < 32 * per; k += 32)
+                    if (!((word >> (k / per)) & 1u)) d[k] = 0.f;
             }
         }
     }
@@ -181,7 +188,7 @@ __device__ void mm_produce(const MmParams& p, unsigned char* slot_base, uint64_t
 }
 
 template <int FMT, uint32_t IW>
-__global__ void __launch_bounds__((kMmWorkers + 1) * 32, 1) rg_spmm_kernel(const __grid_constant__ MmParams p) {
+__global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_spmm_kernel(const __grid_constant__ MmParams p) {
     constexpr uint32_t RV = 4 * (uint32_t)sizeof(typename Fmt<FMT>::T);
     constexpr uint32_t ES = (uint32_t)sizeof(typename Fmt<FMT>::T);
     constexpr uint32_t VA = RV >= 16 ? 1 : 16 / RV;
@@ -192,10 +199,13 @@ __global__ void __launch_bounds__((kMmWorkers + 1) * 32, 1) rg_spmm_kernel(const
     const uint32_t S = p.depth, NW = p.nw;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + 8;
-    float* xs = reinterpret_cast<float*>(smem + kMmHeader);  // (W + 1) x 16 floats: the window of X and a zero column
+    // the window of X: blocks of 8 columns, each 4 rows of 128 bytes (4 floats of
+    // all 8 columns per row), so that 8 lanes reading the same 4 floats of 8
+    // columns that differ mod 8 touch 8 distinct bank quads
+    float* xs = reinterpret_cast<float*>(smem + kMmHeader);
     uint32_t wmax = 0;
     for (uint32_t m = 0; m < p.count; ++m) wmax = max(wmax, p.item[m].W);
-    unsigned char* slot_base = smem + kMmHeader + round_up((wmax + 1) * kMmXStride * 4, 128);
+    unsigned char* slot_base = smem + kMmHeader + mm_xs_bytes(wmax);
     const RgSlot SL = p.SL;
     if (threadIdx.x == 0) {
         for (uint32_t i = 0; i < S; ++i) {
@@ -209,22 +219,29 @@ __global__ void __launch_bounds__((kMmWorkers + 1) * 32, 1) rg_spmm_kernel(const
         if (lane == 0) mm_produce<FMT, IW>(p, slot_base, full, empty);
         return;
     }
+    if (warp > NW) {
+        for (uint32_t m = 0; m < p.count; ++m)
+            mm_zero_rows(p.item[m].mask, p.item[m].D, p.item[m].nrows, p.nvec, warp - NW - 1, kMmZeroWarps, lane);
+        return;
+    }
     const uint32_t wi = warp - 1, ctid = threadIdx.x - 32, nct = NW * 32;
-    // lane = 8 q + t: union positions u = q (mod 4), row g = t / 2, vectors 8 h .. 8 h + 7
-    const uint32_t q = lane >> 3, g = (lane >> 1) & 3u, h = lane & 1u;
+    // lane = 4 q + g: union positions u = q (mod 8), row g of the group, all 16 vectors
+    const uint32_t q = lane >> 2, g = lane & 3u;
     const uint32_t slot0 = dev::smem_u32(slot_base);
     uint32_t st = 0, ph = 0, rot = 0;
     for (uint32_t m = 0; m < p.count; ++m) {
         const MmItem& it = p.item[m];
         const uint32_t W = it.W, wlo = it.wlo[blockIdx.x];
         dev::named_barrier(1, nct);  // every worker is done with the previous window of X
-        for (uint32_t j = ctid; j < (W + 1) * kMmXStride; j += nct) {
-            const uint32_t c = j / kMmXStride, v = j % kMmXStride;
+        const uint32_t nx = round_up(W + 1, 8) * kMmXStride;
+        for (uint32_t j = ctid; j < nx; j += nct) {
+            const uint32_t c = 8 * (j >> 7) + ((j >> 2) & 7u), v = 4 * ((j >> 5) & 3u) + (j & 3u);
             xs[j] = c < W && wlo + c < it.ncols && v < p.nvec ? __ldg(it.X + (size_t)(wlo + c) * p.nvec + v) : 0.f;
         }
         dev::named_barrier(1, nct);
-        const uint32_t xs_a = dev::smem_u32(xs) - 4 * kMmXStride * wlo + 32 * h;  // + 64 c: x[c][8h ..]
-        const uint32_t zc = wlo + W;                                             // the zero column
+        // column c's 4 floats j at xs_a + 64 (c & ~7) + 16 (c & 7) + 128 j (wlo is a multiple of 32)
+        const uint32_t xs_a = dev::smem_u32(xs) - 64 * wlo;
+        const uint32_t zc = wlo + W;  // the zero column
         const uint32_t sb = it.cta_begin[blockIdx.x], se = it.cta_begin[blockIdx.x + 1];
         for (uint32_t s = sb; s < se; ++s) {
             if (!dev::mbar_wait_poll(&full[st], ph)) {
@@ -239,50 +256,65 @@ __global__ void __launch_bounds__((kMmWorkers + 1) * 32, 1) rg_spmm_kernel(const
             const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
             for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
                 const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
-                const uint32_t nU = G.y, u0 = G.x, nfull = nU >> 2;
-                float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const uint32_t nU = G.y, u0 = G.x, nfull = nU >> 3;
+                float acc[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[i] = 0.f;
                 auto mac = [&](float a, uint32_t c) {
-                    const float4 x0 = mm_ld4(xs_a + 64 * c), x1 = mm_ld4(xs_a + 64 * c + 16);
-                    acc[0] = __fmaf_rn(a, x0.x, acc[0]);
-                    acc[1] = __fmaf_rn(a, x0.y, acc[1]);
-                    acc[2] = __fmaf_rn(a, x0.z, acc[2]);
-                    acc[3] = __fmaf_rn(a, x0.w, acc[3]);
-                    acc[4] = __fmaf_rn(a, x1.x, acc[4]);
-                    acc[5] = __fmaf_rn(a, x1.y, acc[5]);
-                    acc[6] = __fmaf_rn(a, x1.z, acc[6]);
-                    acc[7] = __fmaf_rn(a, x1.w, acc[7]);
+                    const uint32_t xa = xs_a + 64 * (c & ~7u) + 16 * (c & 7u);
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const float4 x = mm_ld4(xa + 128 * jj);
+                        acc[4 * jj + 0] = __fmaf_rn(a, x.x, acc[4 * jj + 0]);
+                        acc[4 * jj + 1] = __fmaf_rn(a, x.y, acc[4 * jj + 1]);
+                        acc[4 * jj + 2] = __fmaf_rn(a, x.z, acc[4 * jj + 2]);
+                        acc[4 * jj + 3] = __fmaf_rn(a, x.w, acc[4 * jj + 3]);
+                    }
                 };
-                // this lane's union positions u = q, q + 4, ...: steps where all four
-                // slices have a position need no mask
+                // this lane's union positions u = q, q + 8, ...: steps where all
+                // eight slices have a position need no mask
                 const uint32_t ca = col_a + IW * (u0 + q), va = val_a + RV * (u0 + q);
-#pragma unroll 4
+#pragma unroll 2
                 for (uint32_t k = 0; k < nfull; ++k) {
-                    const uint32_t c = rg_ldcol<IW>(ca + 4 * IW * k);
-                    mac(mm_val_lt<FMT>(0u, 1u, va + 4 * RV * k), c);
+                    const uint32_t c = rg_ldcol<IW>(ca + 8 * IW * k);
+                    mac(mm_val_lt<FMT>(0u, 1u, va + 8 * RV * k), c);
                 }
-                if (nU & 3u) {
-                    const uint32_t u = 4 * nfull + q;
-                    const uint32_t c = rg_ldcol_lt<IW>(u, nU, ca + 4 * IW * nfull, zc);
-                    mac(mm_val_lt<FMT>(u, nU, va + 4 * RV * nfull), c);
+                if (nU & 7u) {
+                    const uint32_t u = 8 * nfull + q;
+                    const uint32_t c = rg_ldcol_lt<IW>(u, nU, ca + 8 * IW * nfull, zc);
+                    mac(mm_val_lt<FMT>(u, nU, va + 8 * RV * nfull), c);
                 }
-                // the four slices of the union: a fixed butterfly over q
+                // the eight slices: a transposed butterfly over q (lane bits 4, 3, 2);
+                // each level keeps the half of the vectors that the lane's bit selects
+                // and adds the partner's copy of it, so that lane 4 q + g ends with
+                // vectors v0, v0 + 1 of row g, v0 = 8 b4 + 4 b3 + 2 b2
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    acc[i] = __fadd_rn(acc[i], __shfl_xor_sync(0xffffffffu, acc[i], 8));
-                    acc[i] = __fadd_rn(acc[i], __shfl_xor_sync(0xffffffffu, acc[i], 16));
+                    const bool b = lane & 16u;
+                    const float snd = b ? acc[i] : acc[i + 8], kp = b ? acc[i + 8] : acc[i];
+                    acc[i] = __fadd_rn(kp, __shfl_xor_sync(0xffffffffu, snd, 16));
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool b = lane & 8u;
+                    const float snd = b ? acc[i] : acc[i + 4], kp = b ? acc[i + 4] : acc[i];
+                    acc[i] = __fadd_rn(kp, __shfl_xor_sync(0xffffffffu, snd, 8));
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const bool b = lane & 4u;
+                    const float snd = b ? acc[i] : acc[i + 2], kp = b ? acc[i + 2] : acc[i];
+                    acc[i] = __fadd_rn(kp, __shfl_xor_sync(0xffffffffu, snd, 4));
                 }
                 const uint32_t off = rg_row_off(G, g);
                 if (off != 0xFFFFu) {
                     const uint32_t row = D.row0 + off;
                     const float sc = FP8 ? dev::lds_f32(vrs + 4 * row) : (FMT == DOSE_FMT_U16_SCALE ? it.scale : 1.f);
-                    // lane slice q stores vectors 8 h + 2 q and 8 h + 2 q + 1
-                    const float r0 = q == 0 ? acc[0] : q == 1 ? acc[2] : q == 2 ? acc[4] : acc[6];
-                    const float r1 = q == 0 ? acc[1] : q == 1 ? acc[3] : q == 2 ? acc[5] : acc[7];
-                    const uint32_t v = 8 * h + 2 * q;
                     const bool scaled = FP8 || FMT == DOSE_FMT_U16_SCALE;
+                    const uint32_t v = 8 * ((lane >> 4) & 1u) + 4 * ((lane >> 3) & 1u) + 2 * ((lane >> 2) & 1u);
                     float* dr = it.D + (size_t)row * p.nvec;
-                    if (v < p.nvec) dr[v] = scaled ? __fmul_rn(sc, r0) : r0;
-                    if (v + 1 < p.nvec) dr[v + 1] = scaled ? __fmul_rn(sc, r1) : r1;
+                    if (v < p.nvec) dr[v] = scaled ? __fmul_rn(sc, acc[0]) : acc[0];
+                    if (v + 1 < p.nvec) dr[v + 1] = scaled ? __fmul_rn(sc, acc[1]) : acc[1];
                 }
             }
             rot = rot + 1 == NW ? 0 : rot + 1;
@@ -294,8 +326,6 @@ __global__ void __launch_bounds__((kMmWorkers + 1) * 32, 1) rg_spmm_kernel(const
             }
         }
     }
-    // the zero pass this launch depends on has finished before this grid does
-    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 template <int FMT, uint32_t IW>
@@ -303,17 +333,8 @@ cudaError_t mm_launch_t(const MmParams& p, uint32_t grid, size_t smem, cudaStrea
     auto k = rg_spmm_kernel<FMT, IW>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(32 * (1 + p.nw));
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, p);
+    k<<<grid, 32 * (1 + p.nw + kMmZeroWarps), smem, s>>>(p);
+    return cudaGetLastError();
 }
 
 template <uint32_t IW>
@@ -348,9 +369,9 @@ bool rg_spmm_applies(const dose_matrix* const* A, int count, size_t* smem_out, u
     }
     const RgSlot SL = rg_slot(tu, tg, tr, value_bytes(A[0]->fmt), A[0]->rg.iw,
                               A[0]->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
-    const size_t fixed = kMmHeader + round_up((wmax + 1) * kMmXStride * 4, 128);
-    if (fixed + 2ull * SL.bytes > kMaxSmemPerBlock) return false;
-    const uint32_t depth = (uint32_t)std::min<size_t>(4, (kMaxSmemPerBlock - fixed) / SL.bytes);
+    const size_t fixed = kMmHeader + mm_xs_bytes(wmax);
+    if (fixed + 2ull * SL.bytes > kMmSmemBudget) return false;
+    const uint32_t depth = (uint32_t)std::min<size_t>(4, (kMmSmemBudget - fixed) / SL.bytes);
     if (smem_out) *smem_out = fixed + (size_t)depth * SL.bytes;
     if (depth_out) *depth_out = depth;
     return true;
@@ -363,10 +384,9 @@ cudaError_t launch_rg_spmm(const dose_matrix* const* A, int count, const float* 
         size_t smem = 0;
         uint32_t depth = 0;
         if (!rg_spmm_applies(A + base, n, &smem, &depth)) return cudaErrorInvalidConfiguration;
-        MmZero z;
         MmParams p;
-        p.count = z.count = (uint32_t)n;
-        p.nvec = z.nvec = (uint32_t)nvec;
+        p.count = (uint32_t)n;
+        p.nvec = (uint32_t)nvec;
         p.depth = depth;
         p.nw = kMmWorkers;
         p.err = A[base]->err;
@@ -389,9 +409,7 @@ cudaError_t launch_rg_spmm(const dose_matrix* const* A, int count, const float* 
             it.nrows = M->nrows;
             it.ncols = M->ncols;
             it.W = R.sched.wwidth;
-            z.mask[i] = R.mask;
-            z.D[i] = D[base + i];
-            z.nrows[i] = M->nrows;
+            it.mask = R.mask;
             tu = std::max(tu, R.tile_u);
             tg = std::max(tg, R.tile_g);
             tr = std::max(tr, R.tile_rows);
@@ -400,15 +418,8 @@ cudaError_t launch_rg_spmm(const dose_matrix* const* A, int count, const float* 
         if (rows == 0) continue;
         p.SL = rg_slot(tu, tg, tr, value_bytes(A[base]->fmt), A[base]->rg.iw,
                        A[base]->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
-        const uint32_t sms = (uint32_t)std::max(1, A[base]->sm_count);
-        // the zero pass keeps the shared-memory carveout of the SpMM kernel so
-        // that both can share an SM while they overlap
-        cudaFuncSetAttribute(rg_spmm_zero, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        rg_spmm_zero<<<4 * sms, 256, 0, s>>>(z);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
         const uint32_t grid = A[base]->rg.sched.grid;
-        e = A[base]->rg.iw == 2 ? mm_launch_iw<2>(A[base]->fmt, p, grid, smem, s)
+        const cudaError_t e = A[base]->rg.iw == 2 ? mm_launch_iw<2>(A[base]->fmt, p, grid, smem, s)
                                 : mm_launch_iw<4>(A[base]->fmt, p, grid, smem, s);
         if (e != cudaSuccess) return e;
     }

@@ -263,7 +263,7 @@ def test_row_group_batched_spmm(fmt, nvec):
         buf = torch.full((m.nrows * nvec + 37,), -7.0, dtype=torch.float32, device="cuda")
         bufs.append(buf)
         Ds.append(buf[:m.nrows * nvec].view(m.nrows, nvec))
-    assert dose.spmv_batched_plan(handles, nvec) == (2, 2)
+    assert dose.spmv_batched_plan(handles, nvec) == (2, 1)
     assert dose.spmv_batched_plan(csr_handles, nvec) == (1, 1)
     dose.spmv_batched(handles, Xs, Ds)
     first = [D.clone() for D in Ds]
