@@ -46,7 +46,8 @@ typedef enum {
                                  every device allocation larger than that fails so) */
     DOSE_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
     DOSE_ERR_UNSUPPORTED = 4, /* valid request outside what this build implements */
-    DOSE_ERR_TIMEOUT = 5      /* a kernel's bounded wait ran out (dose_device_status) */
+    DOSE_ERR_TIMEOUT = 5,     /* a kernel's bounded wait ran out (dose_device_status) */
+    DOSE_ERR_IO = 6           /* the autotune cache file could not be read, parsed or written */
 } dose_status;
 
 /* Stored value formats.  The paper stores 16-bit values (Sec. II-D), IEEE half
@@ -196,6 +197,7 @@ typedef struct {
     uint32_t rg_warps_fused;    /* worker warps of the row-group fused pass (0 if it does not fit) */
     uint32_t rg_index_bytes;    /* bytes per union column index (2 when ncols <= 65536, else 4) */
     uint32_t rg_pad;
+    uint64_t fingerprint;       /* FNV-1a of the structure (dose_fingerprint_host): the autotune cache key */
 } dose_info;
 
 /* Build a matrix handle: validate the CSR on the host (or on the device for
@@ -347,10 +349,65 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out);
 /* Re-schedule a handle with new knobs (synchronous; not during capture). */
 dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning);
 
-/* Time candidate schedules of dose_spmv on this GPU with x (device, ncols
- * floats) and keep the fastest; the chosen knobs are returned in *best (may be
- * NULL).  Synchronous; uses `stream`; not during capture. */
+/* Autotuner (the execution-configuration sweep of Sec. V-A, Fig. 4, for this
+ * library's knobs).  Purposes: which calls the knobs are chosen for. */
+#define DOSE_TUNE_FORWARD 1u /* dose_spmv: stage tiles, lanes-per-row target, pipeline depth */
+#define DOSE_TUNE_FUSED 2u   /* dose_fwd_adj_quadratic / dose_pg_step with p = w = 1: adjoint layout
+                                (row groups or CSR) and its tiles and warps */
+#define DOSE_TUNE_BATCHED 4u /* dose_spmv_batched of this matrix with 16 vectors (same knobs as
+                                DOSE_TUNE_FUSED; with both, their summed time is minimised) */
+enum {
+    DOSE_AUTOTUNE_ENV = -1,   /* read $DOSE_AUTOTUNE: off | cached | full (unset: off) */
+    DOSE_AUTOTUNE_OFF = 0,    /* change nothing */
+    DOSE_AUTOTUNE_CACHED = 1, /* apply the cache's knobs for this matrix and GPU; on a miss, sweep and store */
+    DOSE_AUTOTUNE_FULL = 2    /* sweep and store (replacing the entry) */
+};
+typedef struct {
+    int32_t source;       /* 0 = nothing done (off), 1 = knobs from the cache, 2 = swept (and stored) */
+    uint32_t purposes;    /* the purposes the knobs were chosen for */
+    uint64_t fingerprint; /* the matrix's cache key (dose_info.fingerprint) */
+    double ms[3];         /* times of dose_spmv, the fused pass, the 16-vector batched call with
+                             the chosen knobs (0 = not a purpose; from the sweep that chose them) */
+} dose_autotune_report;
+
+/* Time candidate schedules of dose_spmv and of the fused objective pass on this
+ * GPU with x (device, ncols floats; NULL = all ones) and keep the fastest; the
+ * chosen knobs are returned in *best (may be NULL).  No cache.  Synchronous;
+ * uses `stream`; not during capture. */
 dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tuning* best);
+
+/* The autotuner with its cache.  The cache is a JSON file (format
+ * "dose-autotune-1": a list of entries, each the GPU name as dose_gpu_name gives
+ * it, the matrix fingerprint in 16 hex digits, the purposes, every dose_tuning
+ * field by name and the sweep's times).  path: the file; NULL = $DOSE_AUTOTUNE_CACHE,
+ * else $XDG_CACHE_HOME/dose/autotune.json, else $HOME/.cache/dose/autotune.json.
+ * mode: DOSE_AUTOTUNE_*.  purposes: DOSE_TUNE_* (0 = FORWARD | FUSED).  A hit
+ * applies the entry with dose_set_tuning; a miss (or mode FULL) sweeps, applies
+ * the fastest knobs and rewrites the file (a temporary file renamed over it; a
+ * concurrent writer's entry may be lost, never half written).  A file that is
+ * not such a cache is refused (DOSE_ERR_IO), not overwritten; if the write
+ * fails the swept knobs stay applied.  x as for dose_autotune.  Synchronous.
+ * With DOSE_AUTOTUNE=cached|full in the environment, dose_create_matrix calls
+ * this (x = NULL, purposes 0, path NULL) on handles created with tuning = NULL. */
+dose_status dose_autotune_cached(dose_matrix* A, const float* x, int mode, unsigned purposes, const char* path,
+                                 void* stream, dose_tuning* best, dose_autotune_report* report);
+
+/* Host only.  The fingerprint dose_create_matrix gives this CSR with these
+ * creation flags (host arrays; the values do not enter). */
+dose_status dose_fingerprint_host(const dose_csr_desc* desc, unsigned flags, uint64_t* out);
+
+/* Host only.  Read or write one entry of a cache file (key: gpu, fingerprint,
+ * purposes).  lookup: *found = 1 and *out, ms[3] (each may be NULL) when the
+ * entry exists, *found = 0 otherwise or when the file does not exist.  store:
+ * adds or replaces the entry (ms may be NULL). */
+dose_status dose_autotune_cache_lookup(const char* path, const char* gpu, uint64_t fingerprint, unsigned purposes,
+                                       dose_tuning* out, double* ms, int* found);
+dose_status dose_autotune_cache_store(const char* path, const char* gpu, uint64_t fingerprint, unsigned purposes,
+                                      const dose_tuning* tuning, const double* ms);
+
+/* The GPU name the cache keys on ("<name> (<SMs> SMs, sm_<cc>)") for a CUDA
+ * device, written to buf (len bytes, truncated); returns buf, or NULL if buf is NULL. */
+const char* dose_gpu_name(int device, char* buf, int len);
 
 /* Host-only encoder of the library's stored formats (no GPU needed):
  * values_f64 (nnz, non-negative) -> codes (uint16, uint8 or 32-bit, nnz) and scales

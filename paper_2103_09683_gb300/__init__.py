@@ -34,7 +34,7 @@ CREATE_SELL = 0x4
 SPMV_F64_NATIVE = 0x1
 ROBUST_MODES = {"expected": 0, "worst": 1}
 _STATUS = {0: "DOSE_OK", 1: "DOSE_ERR_INVALID_ARG", 2: "DOSE_ERR_OOM", 3: "DOSE_ERR_CUDA",
-           4: "DOSE_ERR_UNSUPPORTED", 5: "DOSE_ERR_TIMEOUT"}
+           4: "DOSE_ERR_UNSUPPORTED", 5: "DOSE_ERR_TIMEOUT", 6: "DOSE_ERR_IO"}
 
 
 class DoseError(RuntimeError):
@@ -86,7 +86,7 @@ class _Info(ctypes.Structure):
                 ("adj_layout_fused", ctypes.c_uint32), ("adj_layout_adjoint", ctypes.c_uint32),
                 ("rg_groups", ctypes.c_uint64), ("rg_union_entries", ctypes.c_uint64),
                 ("rg_window", ctypes.c_uint32), ("rg_warps_fused", ctypes.c_uint32),
-                ("rg_index_bytes", ctypes.c_uint32), ("rg_pad", ctypes.c_uint32)]
+                ("rg_index_bytes", ctypes.c_uint32), ("rg_pad", ctypes.c_uint32), ("fingerprint", ctypes.c_uint64)]
 
 
 _lib = None
@@ -110,6 +110,13 @@ EXPORTS = {
     "dose_matrix_info": (ctypes.c_int, [_P, _P]),
     "dose_set_tuning": (ctypes.c_int, [_P, _P]),
     "dose_autotune": (ctypes.c_int, [_P, _P, _P, _P]),
+    "dose_autotune_cached": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_uint, ctypes.c_char_p, _P, _P, _P]),
+    "dose_fingerprint_host": (ctypes.c_int, [_P, ctypes.c_uint, _P]),
+    "dose_autotune_cache_lookup": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint,
+                                                  _P, _P, _P]),
+    "dose_autotune_cache_store": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint,
+                                                 _P, _P]),
+    "dose_gpu_name": (ctypes.c_char_p, [ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
     "dose_encode_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, _P, ctypes.c_uint64, _P, _P, _P]),
     "dose_device_status": (ctypes.c_int, [_P, _P]),
     "dose_adjoint_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, _P, _P, ctypes.c_int,
@@ -118,6 +125,48 @@ EXPORTS = {
     "dose_last_error": (ctypes.c_char_p, []),
     "dose_version": (ctypes.c_char_p, []),
 }
+
+
+TUNE_FORWARD, TUNE_FUSED, TUNE_BATCHED = 1, 2, 4
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("source", ctypes.c_int32), ("purposes", ctypes.c_uint32), ("fingerprint", ctypes.c_uint64),
+                ("ms", ctypes.c_double * 3)]
+
+
+def fingerprint_host(row_ptr, col, *, ncols: int, fmt: str = "u16", flags: int = 0) -> int:
+    """dose_fingerprint_host: the autotune cache key dose_create_matrix gives
+    this structure (host arrays; no GPU)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.uint32)
+    ci = np.ascontiguousarray(col, dtype=np.uint32)
+    d = _Desc(nrows=len(rp) - 1, ncols=int(ncols), nnz=len(ci), row_ptr=rp.ctypes.data, col_idx=ci.ctypes.data,
+              fmt=FORMATS[fmt], on_device=0)
+    out = ctypes.c_uint64()
+    _check(load().dose_fingerprint_host(ctypes.byref(d), int(flags), ctypes.byref(out)))
+    return out.value
+
+
+def autotune_cache_lookup(path, gpu: str, fingerprint: int, purposes: int):
+    """(tuning dict, [ms x3]) of a cache entry, or None (host only)."""
+    t, ms, found = Tuning(), (ctypes.c_double * 3)(), ctypes.c_int()
+    _check(load().dose_autotune_cache_lookup(os.fsencode(path), gpu.encode(), int(fingerprint), int(purposes),
+                                             ctypes.byref(t), ms, ctypes.byref(found)))
+    return (t.as_dict(), list(ms)) if found.value else None
+
+
+def autotune_cache_store(path, gpu: str, fingerprint: int, purposes: int, tuning: dict, ms=(0.0, 0.0, 0.0)):
+    """Add or replace a cache entry (host only)."""
+    t = Tuning(**{k: int(v) for k, v in tuning.items()})
+    m = (ctypes.c_double * 3)(*ms)
+    _check(load().dose_autotune_cache_store(os.fsencode(path), gpu.encode(), int(fingerprint), int(purposes),
+                                            ctypes.byref(t), m))
+
+
+def gpu_name(device: int = 0) -> str:
+    """The GPU name the autotune cache keys on."""
+    buf = ctypes.create_string_buffer(256)
+    return load().dose_gpu_name(int(device), buf, 256).decode()
 
 
 def build(force: bool = False) -> str:
@@ -410,12 +459,28 @@ class DoseMatrix:
         t = Tuning(**{k: int(v) for k, v in knobs.items()})
         _check(load().dose_set_tuning(self._h, ctypes.byref(t)))
 
-    def autotune(self, x, stream=None) -> dict:
+    def autotune(self, x=None, stream=None, *, mode=None, purposes=("forward", "fused"), cache=None) -> dict:
+        """Choose the schedule knobs by timing candidates on this GPU.  mode=None:
+        dose_autotune (sweep, no cache); "off" | "cached" | "full" | "env":
+        dose_autotune_cached with the JSON cache at `cache` (None = the library's
+        default path).  Returns the knobs in effect; with a mode, also
+        "source" ("off", "cache" or "sweep") and the sweep's times in ms."""
         torch = _torch()
         t = Tuning()
-        _check(load().dose_autotune(self._h, _dptr(x, torch.float32, self.ncols, "x"),
-                                    _stream_handle(stream), ctypes.byref(t)))
-        return t.as_dict()
+        xp = None if x is None else _dptr(x, torch.float32, self.ncols, "x")
+        if mode is None:
+            _check(load().dose_autotune(self._h, xp, _stream_handle(stream), ctypes.byref(t)))
+            return t.as_dict()
+        modes = {"env": -1, "off": 0, "cached": 1, "full": 2}
+        bits = {"forward": TUNE_FORWARD, "fused": TUNE_FUSED, "batched": TUNE_BATCHED}
+        rep = _Report()
+        _check(load().dose_autotune_cached(self._h, xp, modes[mode], sum(bits[p] for p in purposes),
+                                           None if cache is None else os.fsencode(cache), _stream_handle(stream),
+                                           ctypes.byref(t), ctypes.byref(rep)))
+        out = t.as_dict()
+        out.update(source=("off", "cache", "sweep")[rep.source], fingerprint=rep.fingerprint,
+                   ms_forward=rep.ms[0], ms_fused=rep.ms[1], ms_batched=rep.ms[2])
+        return out
 
     def device_status(self, stream=None):
         """Synchronise and raise DoseError if a kernel recorded a failure."""

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdose.so")
 SOURCES = ["dose_api.cu", "spmv_kernel.cu", "spmv_f64_kernel.cu", "adjoint_kernel.cu", "batched_kernel.cu",
-           "noalloc_adjoint.cu", "robust.cu", "sell_kernel.cu", "rg_layout.cu", "rg_kernel.cu", "rg_spmm.cu"]
+           "noalloc_adjoint.cu", "robust.cu", "sell_kernel.cu", "rg_layout.cu", "rg_kernel.cu", "rg_spmm.cu", "autotune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

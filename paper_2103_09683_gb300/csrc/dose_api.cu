@@ -410,7 +410,7 @@ static dose_status check_tuning_ranges(const Tuning& t) {
     return DOSE_OK;
 }
 
-static dose_status check_tuning(const dose_matrix* A, Tuning& t) {
+dose_status check_tuning(const dose_matrix* A, Tuning& t) {
     if (t.tile_nnz < 256 || t.tile_nnz > 16384) return invalid("tuning.tile_nnz must be in [256, 16384]");
     if (t.tile_rows < 32 || t.tile_rows > 8192) return invalid("tuning.tile_rows must be in [32, 8192]");
     if (t.coop_nnz < 32 || t.coop_nnz > t.tile_nnz) return invalid("tuning.coop_nnz must be in [32, tile_nnz]");
@@ -440,7 +440,7 @@ static void fit_default_tuning(const dose_matrix* A, Tuning& t, const dose_tunin
     }
 }
 
-static dose_status check_adj_tuning(const AdjTuning& t) {
+dose_status check_adj_tuning(const AdjTuning& t) {
     if (t.tile_nnz < 256 || t.tile_nnz > 16384) return invalid("tuning.adj_tile_nnz must be in [256, 16384]");
     if (t.tile_rows < 32 || t.tile_rows > 8192) return invalid("tuning.adj_tile_rows must be in [32, 8192]");
     if (t.stages < 2 || t.stages > 8) return invalid("tuning.adj_stages must be in [2, 8]");
@@ -457,7 +457,7 @@ static dose_status check_adj_tuning(const AdjTuning& t) {
     return DOSE_OK;
 }
 
-static void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
+void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
     if (!in) return;
     if (in->tile_nnz) t.tile_nnz = in->tile_nnz;
     if (in->tile_rows) t.tile_rows = in->tile_rows;
@@ -483,7 +483,7 @@ static void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
     if (!in->coop_nnz) t.coop_nnz = std::min(t.coop_nnz, t.tile_nnz);  // the default follows a smaller tile
 }
 
-static void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out) {
+void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out) {
     out->tile_nnz = t.tile_nnz;
     out->tile_rows = t.tile_rows;
     out->coop_nnz = t.coop_nnz;
@@ -519,7 +519,7 @@ static cudaError_t upload(T** dst, const T* src, size_t n, size_t alloc_n) {
 
 // Build one schedule on the host and replace `D` with its device copy.  The
 // adjoint schedule (`windowed`) gets per-CTA column windows.
-static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& t, bool windowed = false) {
+dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& t, bool windowed) {
     const bool win = windowed && !A->host_row_cmin.empty();
     const uint32_t vbytes = value_bytes(A->fmt) + 4;
     Schedule S = build_schedule(A->host_row_ptr, A->nrows, t, D.grid, win ? A->host_row_cmin.data() : nullptr,
@@ -549,7 +549,7 @@ static dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& 
 }
 
 // The adjoint schedule: its own tile sizes, the forward's lane binning.
-static Tuning adj_schedule_tuning(const Tuning& fwd, const AdjTuning& a) {
+Tuning adj_schedule_tuning(const Tuning& fwd, const AdjTuning& a) {
     Tuning t = fwd;
     t.tile_nnz = a.tile_nnz;
     t.tile_rows = a.tile_rows;
@@ -572,19 +572,6 @@ using namespace dose;
 namespace {
 // Time `reps` launches of fn after 3 warm-up launches; returns ms per launch or
 // a negative value on error.
-template <class F>
-static float time_launches(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& fn) {
-    for (int i = 0; i < 3; ++i)
-        if (fn() != cudaSuccess) return -1.f;
-    cudaEventRecord(e0, s);
-    for (int i = 0; i < reps; ++i)
-        if (fn() != cudaSuccess) return -1.f;
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    return ms / reps;
-}
 
 // Self-test of the bounded waits: one thread waits on a phase of an mbarrier
 // that nothing arrives at; the wait gives up after limit_ns and the kernel
@@ -907,8 +894,22 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
                       (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) + x64_alloc * 8 +
                       (size_t)A->adj.grid * ncols_pad * 4 + (size_t)A->adj.grid * 8 + 4 + schedule_bytes(A->fwd) +
                       schedule_bytes(A->adj) + (A->fwd64_own ? schedule_bytes(A->fwd64) : 0);
+    A->fingerprint = matrix_fingerprint(A.get());
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "create");
-    *out = A.release();
+    dose_matrix* H = A.release();
+    // DOSE_AUTOTUNE=cached|full in the environment tunes a handle created with
+    // default knobs (dose_autotune_cached with its environment defaults)
+    const char* env = std::getenv("DOSE_AUTOTUNE");
+    if (!tuning && env && *env && std::strcmp(env, "off") && std::strcmp(env, "0")) {
+        const dose_status st = dose_autotune_cached(H, nullptr, DOSE_AUTOTUNE_ENV, 0, nullptr, stream, nullptr, nullptr);
+        if (st != DOSE_OK) {
+            cudaDeviceSynchronize();
+            free_all(H);
+            delete H;
+            return st;
+        }
+    }
+    *out = H;
     return DOSE_OK;
 }
 
@@ -1117,6 +1118,7 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     out->nnz = A->nnz;
     out->fmt = A->fmt;
     out->flags = A->flags;
+    out->fingerprint = A->fingerprint;
     out->n_stages = A->fwd.n_stages;
     out->n_coop_rows = A->fwd.n_coop_rows;
     std::memcpy(out->lanes_hist, A->fwd.lanes_hist, sizeof(out->lanes_hist));
@@ -1219,121 +1221,5 @@ dose_status dose_device_status(const dose_matrix* A, void* stream) {
     return DOSE_OK;
 }
 
-dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tuning* best) {
-    if (!A) return invalid("dose_autotune: null matrix");
-    if (A->ncols && !x) return invalid("dose_autotune: x is NULL");
-    cudaStream_t s = as_stream(stream);
-    float *d = nullptr, *pw = nullptr, *g = nullptr;
-    double* f = nullptr;
-    const size_t nr = std::max<size_t>(A->nrows, 1), nrp = (nr + 3) / 4 * 4;
-    cudaError_t e = dev_malloc(&d, nr * 4);
-    if (e == cudaSuccess) e = dev_malloc(&pw, 2 * nrp * 4);
-    if (e == cudaSuccess) e = dev_malloc(&g, std::max<size_t>(A->ncols, 1) * 4);
-    if (e == cudaSuccess) e = dev_malloc(&f, 8);
-    if (e == cudaSuccess) e = cudaMemset(pw, 0, 2 * nrp * 4);  // p = 0, w = 0: timing only
-    if (e != cudaSuccess) {
-        cudaFree(d);
-        cudaFree(pw);
-        cudaFree(g);
-        cudaFree(f);
-        return cuda_fail(e, "dose_autotune scratch");
-    }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    const int reps = 10;
-    dose_status result = DOSE_OK;
-
-    // 1. forward: tile sizes, lanes-per-row target, pipeline depth
-    const Tuning orig = A->fwd.tuning;
-    Tuning best_t = orig;
-    float best_ms = 1e30f;
-    const uint32_t nnzs[] = {2048, 4096, 8192};
-    const uint32_t rows[] = {1024, 2048, 4096};
-    const uint32_t targets[] = {4, 8, 12, 16, 24};
-    const uint32_t depths[] = {3, 4, 6};
-    for (uint32_t tn : nnzs)
-        for (uint32_t tr : rows)
-            for (uint32_t lt : targets)
-                for (uint32_t sd : depths) {
-                    Tuning t = orig;
-                    t.tile_nnz = tn;
-                    t.tile_rows = tr;
-                    t.coop_nnz = std::min(t.coop_nnz, tn);
-                    t.lane_target = lt;
-                    t.stages = sd;
-                    if (check_tuning(A, t) != DOSE_OK) continue;
-                    if (apply_schedule(A, A->fwd, t, A->fwd_windowed) != DOSE_OK) continue;
-                    const float ms = time_launches(s, e0, e1, reps, [&] { return launch_spmv(A, x, d, s); });
-                    if (ms < 0.f) {
-                        result = cuda_fail(cudaGetLastError(), "dose_autotune forward timing");
-                        break;
-                    }
-                    if (ms < best_ms) {
-                        best_ms = ms;
-                        best_t = t;
-                    }
-                }
-    if (result == DOSE_OK) result = apply_schedule(A, A->fwd, best_t, A->fwd_windowed);
-
-    // 2. fused objective pass: adjoint tile sizes, depth, forward warps (scatter warps: all that fit)
-    const AdjTuning orig_a = A->adj_tuning;
-    AdjTuning best_a = orig_a;
-    if (result == DOSE_OK) {
-        float best_a_ms = 1e30f;
-        const uint32_t anz[] = {2048, 4096, 5120, 6144, 8192};
-        const uint32_t arows[] = {512, 1024, 2048};
-        const uint32_t adepth[] = {2, 3, 4, 6};
-        const uint32_t afw[] = {4, 8};
-        const uint32_t asw[] = {4, 8, 12, 0};
-        for (uint32_t tn : anz)
-            for (uint32_t tr : arows) {
-                // the schedule (and so the column window) depends on the tile sizes only
-                AdjTuning a = orig_a;
-                a.tile_nnz = tn;
-                a.tile_rows = tr;
-                A->adj_tuning = a;
-                if (apply_schedule(A, A->adj, adj_schedule_tuning(A->fwd.tuning, a), true) != DOSE_OK) continue;
-                if (A->adj.wwidth > kXSmemMaxCols) continue;
-                for (uint32_t sd : adepth)
-                    for (uint32_t fw : afw)
-                        for (uint32_t sw : asw) {
-                            a.stages = sd;
-                            a.forward_warps = fw;
-                            a.scatter_warps = sw;
-                            if (!adjoint_shape(A, a, true, nullptr, nullptr)) continue;
-                            A->adj_tuning = a;
-                            const float ms = time_launches(s, e0, e1, reps, [&] {
-                                return launch_adjoint(A, ADJ_MODE_QUADRATIC, x, pw, pw + nrp, nullptr, nullptr, f, g,
-                                                      nullptr, 0.f, s);
-                            });
-                            if (ms < 0.f) {
-                                result = cuda_fail(cudaGetLastError(), "dose_autotune fused timing");
-                                break;
-                            }
-                            if (ms < best_a_ms) {
-                                best_a_ms = ms;
-                                best_a = a;
-                            }
-                        }
-            }
-        A->adj_tuning = best_a;
-        dose_status st = apply_schedule(A, A->adj, adj_schedule_tuning(A->fwd.tuning, best_a), true);
-        if (result == DOSE_OK) result = st;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(d);
-    cudaFree(pw);
-    cudaFree(g);
-    cudaFree(f);
-    if (result != DOSE_OK) return result;
-    if (best) {
-        dose_info inf;
-        dose_matrix_info(A, &inf);
-        *best = inf.tuning;  // the knobs in effect, as dose_matrix_info reports them
-    }
-    return DOSE_OK;
-}
 
 }  // extern "C"

@@ -210,6 +210,7 @@ struct dose_matrix {
 
     int* err = nullptr;  // device error word (0 = ok)
     uint64_t device_bytes = 0;
+    uint64_t fingerprint = 0;  // of the structure (autotune cache key; autotune.cu)
     std::vector<uint32_t> host_row_ptr;  // kept for re-scheduling
     std::vector<uint32_t> host_row_cmin;  // lowest / highest column of each row (empty rows:
     std::vector<uint32_t> host_row_cmax;  // cmin > cmax), for the adjoint's column windows
@@ -287,6 +288,18 @@ void deal_items(Schedule& S, const std::vector<DealItem>& items, uint32_t grid, 
 
 cudaError_t launch_spmm_batched(const dose_matrix* const* A, int count, const float* const* X,
                                 float* const* D, int nvec, cudaStream_t s, std::string* why);
+
+// Knobs and schedules (dose_api.cu): range checks, the merge of a caller's
+// dose_tuning into the internal knobs and back, and the re-cut of a schedule.
+dose_status check_tuning(const dose_matrix* A, Tuning& t);
+dose_status check_adj_tuning(const AdjTuning& t);
+void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in);
+void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out);
+dose_status apply_schedule(dose_matrix* A, DevSchedule& D, const Tuning& t, bool windowed = false);
+Tuning adj_schedule_tuning(const Tuning& fwd, const AdjTuning& a);
+// FNV-1a of the matrix's shape, format, creation flags, row pointers and the
+// column extent of each non-empty row (autotune.cu).
+uint64_t matrix_fingerprint(const dose_matrix* A);
 
 constexpr uint32_t kMaxSmemPerBlock = 227 * 1024;
 
