@@ -162,6 +162,12 @@ typedef struct {
     uint32_t rg_warps;          /* row groups: worker warps (1..15; 0 = as many as fit) */
     uint32_t rg_l2_prefetch;    /* row groups: stages prefetched into L2 ahead of the ring (1..31;
                                    0 = default, off; 32 = off) */
+    uint32_t fwd_layout;        /* layout dose_spmv runs on: 0 = row groups where the handle has them
+                                   (and not DOSE_CREATE_COMPENSATED, whose long-row sums run on CSR),
+                                   else CSR (default); 1 = CSR; 2 = row groups (create and
+                                   dose_set_tuning fail if dose_spmv cannot take them).  On row groups
+                                   a row's terms are added in its group's union order (see adj_layout),
+                                   so the last bits may differ from the CSR form's. */
 } dose_tuning;
 
 typedef struct {
@@ -198,6 +204,10 @@ typedef struct {
     uint32_t rg_index_bytes;    /* bytes per union column index (2 when ncols <= 65536, else 4) */
     uint32_t rg_pad;
     uint64_t fingerprint;       /* FNV-1a of the structure (dose_fingerprint_host): the autotune cache key */
+    uint32_t spmv_layout;       /* layout dose_spmv runs on: 1 = CSR, 2 = row groups, 3 = SELL */
+    uint32_t pad2;
+    uint64_t rg_spmv_bytes;     /* algorithmic HBM bytes of one dose_spmv on the row-group layout (0 when
+                                   it runs on another layout; spmv_bytes stays the CSR byte model) */
 } dose_info;
 
 /* Build a matrix handle: validate the CSR on the host (or on the device for

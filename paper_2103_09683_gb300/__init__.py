@@ -65,7 +65,7 @@ class Tuning(ctypes.Structure):
                 ("sell_sigma", ctypes.c_uint32),
                 ("adj_layout", ctypes.c_uint32), ("rg_tile_union", ctypes.c_uint32),
                 ("rg_tile_rows", ctypes.c_uint32), ("rg_stages", ctypes.c_uint32), ("rg_warps", ctypes.c_uint32),
-                ("rg_l2_prefetch", ctypes.c_uint32)]
+                ("rg_l2_prefetch", ctypes.c_uint32), ("fwd_layout", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -86,7 +86,8 @@ class _Info(ctypes.Structure):
                 ("adj_layout_fused", ctypes.c_uint32), ("adj_layout_adjoint", ctypes.c_uint32),
                 ("rg_groups", ctypes.c_uint64), ("rg_union_entries", ctypes.c_uint64),
                 ("rg_window", ctypes.c_uint32), ("rg_warps_fused", ctypes.c_uint32),
-                ("rg_index_bytes", ctypes.c_uint32), ("rg_pad", ctypes.c_uint32), ("fingerprint", ctypes.c_uint64)]
+                ("rg_index_bytes", ctypes.c_uint32), ("rg_pad", ctypes.c_uint32), ("fingerprint", ctypes.c_uint64),
+                ("spmv_layout", ctypes.c_uint32), ("pad2", ctypes.c_uint32), ("rg_spmv_bytes", ctypes.c_uint64)]
 
 
 _lib = None

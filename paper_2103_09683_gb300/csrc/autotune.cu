@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "dose_internal.cuh"
+#include "nvtx_range.cuh"
 
 namespace dose {
 namespace {
@@ -260,7 +261,7 @@ constexpr const char* kTuneNames[] = {
     "consumer_warps", "l2_prefetch",      "adj_tile_nnz",      "adj_tile_rows",   "adj_stages",
     "adj_forward_warps", "adj_scatter_warps", "adj_l2_prefetch", "row_order",     "adj_row_order",
     "sell_sigma",    "adj_layout",        "rg_tile_union",     "rg_tile_rows",    "rg_stages",
-    "rg_warps",      "rg_l2_prefetch"};
+    "rg_warps",      "rg_l2_prefetch",    "fwd_layout"};
 constexpr size_t kTuneFields = sizeof(kTuneNames) / sizeof(kTuneNames[0]);
 static_assert(sizeof(dose_tuning) == kTuneFields * sizeof(uint32_t), "dose_tuning is a list of uint32_t knobs");
 
@@ -476,23 +477,27 @@ dose_status sweep(dose_matrix* A, const float* x, unsigned purposes, cudaStream_
     float* D1[1] = {S.D16};
     auto batched = [&] { return dose_spmv_batched(one, 1, X1, D1, 16, s); };
 
-    // 1. dose_spmv: stage tiles, lanes-per-row target, pipeline depth
+    // 1. dose_spmv: the CSR form's stage tiles, lanes-per-row target and
+    //    pipeline depth, then the row-group form against the best of them
     if ((purposes & DOSE_TUNE_FORWARD) && !(A->flags & DOSE_CREATE_SELL)) {
         const Tuning orig = A->fwd.tuning;
-        Tuning best = orig;
+        Tuning base = orig;
+        base.layout = 1;  // time the CSR form
+        if ((st = apply_schedule(A, A->fwd, base, A->fwd_windowed)) != DOSE_OK) return st;
+        Tuning best = base;
         float best_ms = time_calls(s, S.e0, S.e1, 10, &st, spmv);
         if (best_ms < 0.f) return st;
         for (uint32_t tn : {4096u, 8192u})
             for (uint32_t tr : {1024u, 2048u, 4096u})
                 for (uint32_t lt : {8u, 16u, 24u})
                     for (uint32_t sd : {3u, 4u}) {
-                        Tuning t = orig;
+                        Tuning t = base;
                         t.tile_nnz = tn;
                         t.tile_rows = tr;
-                        t.coop_nnz = std::min(orig.coop_nnz, tn);
+                        t.coop_nnz = std::min(base.coop_nnz, tn);
                         t.lane_target = lt;
                         t.stages = sd;
-                        if (!std::memcmp(&t, &orig, sizeof(t)) || check_tuning(A, t) != DOSE_OK) continue;
+                        if (!std::memcmp(&t, &base, sizeof(t)) || check_tuning(A, t) != DOSE_OK) continue;
                         if ((st = apply_schedule(A, A->fwd, t, A->fwd_windowed)) != DOSE_OK) return st;
                         const float m = time_calls(s, S.e0, S.e1, 10, &st, spmv);
                         if (m < 0.f) return st;
@@ -502,6 +507,18 @@ dose_status sweep(dose_matrix* A, const float* x, unsigned purposes, cudaStream_
                         }
                     }
         if ((st = apply_schedule(A, A->fwd, best, A->fwd_windowed)) != DOSE_OK) return st;
+        if (orig.layout != 1) {
+            A->fwd.tuning.layout = orig.layout;
+            if (spmv_on_row_groups(A)) {
+                const float m = time_calls(s, S.e0, S.e1, 10, &st, spmv);
+                if (m < 0.f) return st;
+                if (m < best_ms || orig.layout == 2) {
+                    best_ms = m;
+                    best.layout = orig.layout;
+                }
+            }
+            A->fwd.tuning.layout = best.layout;
+        }
         if (A->fwd64_own && (st = apply_schedule(A, A->fwd64, best, false)) != DOSE_OK) return st;
         // the adjoint schedule takes the forward's lane binning
         if ((st = apply_schedule(A, A->adj, adj_schedule_tuning(best, A->adj_tuning), true)) != DOSE_OK) return st;
@@ -517,6 +534,9 @@ dose_status sweep(dose_matrix* A, const float* x, unsigned purposes, cudaStream_
     //    the adjoint layout and its knobs, scored by the sum of their times
     if (purposes & (DOSE_TUNE_FUSED | DOSE_TUNE_BATCHED)) {
         const bool time_b = (purposes & DOSE_TUNE_BATCHED) && S.X16;
+        // a row-group dose_spmv shares the layout's stages: its time joins the score
+        const bool time_v = (purposes & DOSE_TUNE_FORWARD) && !(A->flags & DOSE_CREATE_SELL) && A->rg.built &&
+                            A->fwd.tuning.layout != 1;
         const AdjTuning base = A->adj_tuning;
         AdjTuning rg_cut = base, csr_cut = base;  // knobs the two adjoint schedules are cut with
         std::vector<AdjTuning> cands{base};
@@ -574,12 +594,12 @@ dose_status sweep(dose_matrix* A, const float* x, unsigned purposes, cudaStream_
         };
         float best = 3e38f;
         AdjTuning best_a = base;
-        double bf = 0, bb = 0;
+        double bf = 0, bb = 0, bv = ms[0];
         for (const AdjTuning& a : cands) {
             bool usable = true;
             if ((st = cut(a, &usable)) != DOSE_OK) return st;
             if (!usable) continue;
-            float tf = 0.f, tb = 0.f;
+            float tf = 0.f, tb = 0.f, tv = 0.f;
             if (purposes & DOSE_TUNE_FUSED) {
                 tf = time_calls(s, S.e0, S.e1, 10, &st, fused);
                 if (tf < 0.f) {
@@ -594,15 +614,21 @@ dose_status sweep(dose_matrix* A, const float* x, unsigned purposes, cudaStream_
                     return st;
                 }
             }
-            if (tf + tb < best) {
-                best = tf + tb;
+            if (time_v && spmv_on_row_groups(A)) {
+                tv = time_calls(s, S.e0, S.e1, 10, &st, spmv);
+                if (tv < 0.f) return st;
+            }
+            if (tf + tb + tv < best) {
+                best = tf + tb + tv;
                 best_a = a;
                 bf = tf;
                 bb = tb;
+                if (tv > 0.f) bv = tv;
             }
         }
         bool usable = true;
         if ((st = cut(best_a, &usable)) != DOSE_OK) return st;
+        ms[0] = bv;
         ms[1] = bf;
         ms[2] = bb;
     }
@@ -624,6 +650,7 @@ using namespace dose;
 extern "C" {
 
 dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tuning* best) {
+    NvtxRange nvtx_range("dose_autotune");
     if (!A) return bad("dose_autotune: null matrix");
     double ms[3];
     const dose_status st = sweep(A, x, DOSE_TUNE_FORWARD | DOSE_TUNE_FUSED, static_cast<cudaStream_t>(stream), ms);
@@ -638,6 +665,7 @@ dose_status dose_autotune(dose_matrix* A, const float* x, void* stream, dose_tun
 
 dose_status dose_autotune_cached(dose_matrix* A, const float* x, int mode, unsigned purposes, const char* path,
                                  void* stream, dose_tuning* best, dose_autotune_report* report) {
+    NvtxRange nvtx_range("dose_autotune_cached");
     if (!A) return bad("dose_autotune_cached: null matrix");
     if (purposes & ~(unsigned)(DOSE_TUNE_FORWARD | DOSE_TUNE_FUSED | DOSE_TUNE_BATCHED))
         return bad("dose_autotune_cached: unknown purposes");

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "dose_internal.cuh"
+#include "nvtx_range.cuh"
 
 namespace dose {
 
@@ -407,6 +408,7 @@ static dose_status check_tuning_ranges(const Tuning& t) {
     if (t.consumer_warps != 4 && t.consumer_warps != 8 && t.consumer_warps != 16)
         return invalid("tuning.consumer_warps must be 4, 8 or 16");
     if (t.row_order < 1 || t.row_order > 2) return invalid("tuning.row_order must be 1 or 2");
+    if (t.layout > 2) return invalid("tuning.fwd_layout must be 0, 1 or 2");
     return DOSE_OK;
 }
 
@@ -419,6 +421,7 @@ dose_status check_tuning(const dose_matrix* A, Tuning& t) {
     if (t.consumer_warps != 4 && t.consumer_warps != 8 && t.consumer_warps != 16)
         return invalid("tuning.consumer_warps must be 4, 8 or 16");
     if (t.row_order < 1 || t.row_order > 2) return invalid("tuning.row_order must be 1 or 2");
+    if (t.layout > 2) return invalid("tuning.fwd_layout must be 0, 1 or 2");
     if (spmv_smem_bytes(A, t, spmv_x_in_smem(A, t)) > kMaxSmemPerBlock)
         return invalid("tuning needs more shared memory than a CTA has");
     return DOSE_OK;
@@ -480,6 +483,7 @@ void merge_tuning(Tuning& t, AdjTuning& a, const dose_tuning* in) {
     if (in->rg_stages) a.rg_stages = in->rg_stages;
     if (in->rg_warps) a.rg_warps = in->rg_warps;
     if (in->rg_l2_prefetch) a.rg_l2_prefetch = in->rg_l2_prefetch >= 32 ? 0 : in->rg_l2_prefetch;
+    if (in->fwd_layout) t.layout = in->fwd_layout;
     if (!in->coop_nnz) t.coop_nnz = std::min(t.coop_nnz, t.tile_nnz);  // the default follows a smaller tile
 }
 
@@ -505,6 +509,7 @@ void export_tuning(const Tuning& t, const AdjTuning& a, dose_tuning* out) {
     out->rg_stages = a.rg_stages;
     out->rg_warps = a.rg_warps;
     out->rg_l2_prefetch = a.rg_l2_prefetch ? a.rg_l2_prefetch : 32;
+    out->fwd_layout = t.layout;
 }
 
 template <class T>
@@ -621,6 +626,7 @@ dose_status dose_encode_host(dose_format fmt, uint32_t nrows, const uint32_t* ro
 
 dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const dose_tuning* tuning, void* stream,
                                dose_matrix** out) {
+    NvtxRange nvtx_range("dose_create_matrix");
     if (!desc || !out) return invalid("dose_create_matrix: null desc or out");
     *out = nullptr;
     if (flags & ~(DOSE_CREATE_COMPENSATED | DOSE_CREATE_U16_INDEX | DOSE_CREATE_SELL))
@@ -889,6 +895,12 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
             return DOSE_ERR_UNSUPPORTED;
         }
     }
+    if (A->fwd.tuning.layout == 2 && !spmv_on_row_groups(A.get())) {
+        free_all(A.get());
+        set_error("fwd_layout = 2: dose_spmv cannot run on the row-group layout of this handle" +
+                  std::string((flags & DOSE_CREATE_COMPENSATED) ? " (DOSE_CREATE_COMPENSATED sums on CSR)" : ""));
+        return DOSE_ERR_UNSUPPORTED;
+    }
     A->device_bytes = A->rg.bytes + (A->rg.built ? (A->rg.host.size() + 1) * 16 + schedule_bytes(A->rg.sched) : 0) +
                       A->sell.bytes + rp_alloc * 4 + col_alloc * 4 + ((flags & DOSE_CREATE_U16_INDEX) ? col16_alloc * 2 : 0) + val_alloc +
                       (fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? ((size_t)nrows + 16) * 4 : 0) + x64_alloc * 8 +
@@ -915,6 +927,7 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
 
 dose_status dose_create_multibeam(const dose_csr_desc* beams, int nbeams, unsigned flags, const dose_tuning* tuning,
                                   void* stream, dose_matrix** out) {
+    NvtxRange nvtx_range("dose_create_multibeam");
     if (!out) return invalid("dose_create_multibeam: out is NULL");
     *out = nullptr;
     if (!beams || nbeams < 1 || nbeams > 64) return invalid("dose_create_multibeam: nbeams must be in [1, 64]");
@@ -995,15 +1008,18 @@ dose_status dose_destroy(dose_matrix* A) {
 }
 
 dose_status dose_spmv(const dose_matrix* A, const float* x, float* d, void* stream) {
+    NvtxRange nvtx_range("dose_spmv");
     if (!A) return invalid("dose_spmv: null matrix");
     if (A->nrows && !d) return invalid("dose_spmv: d is NULL");
     if (A->ncols && !x) return invalid("dose_spmv: x is NULL");
     cudaError_t e = (A->flags & DOSE_CREATE_SELL) ? launch_spmv_sell(A, x, d, as_stream(stream))
-                                                  : launch_spmv(A, x, d, as_stream(stream));
+                    : spmv_on_row_groups(A)      ? launch_rg_spmv(A, x, d, as_stream(stream))
+                                                 : launch_spmv(A, x, d, as_stream(stream));
     return e == cudaSuccess ? DOSE_OK : cuda_fail(e, "dose_spmv launch");
 }
 
 dose_status dose_spmv_f64(const dose_matrix* A, const double* x, double* d, unsigned flags, void* stream) {
+    NvtxRange nvtx_range("dose_spmv_f64");
     if (!A) return invalid("dose_spmv_f64: null matrix");
     if (flags & ~DOSE_SPMV_F64_NATIVE) return invalid("dose_spmv_f64: unknown flags");
     if (A->nrows && !d) return invalid("dose_spmv_f64: d is NULL");
@@ -1017,6 +1033,13 @@ dose_status dose_spmv_f64(const dose_matrix* A, const double* x, double* d, unsi
 }  // extern "C"
 
 namespace dose {
+// dose_spmv runs on the row-group layout unless the caller asked for CSR
+// (fwd_layout = 1), the handle sums long rows with compensation (a CSR path),
+// or the layout is missing or its ring does not fit beside the window of x.
+bool spmv_on_row_groups(const dose_matrix* A) {
+    return A->fwd.tuning.layout != 1 && !(A->flags & DOSE_CREATE_COMPENSATED) && rg_spmv_applies(A, nullptr, nullptr);
+}
+
 dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* const* vecs, int nvec) {
     for (int k = 0; k < nvec; ++k)
         if (vecs[k] && (reinterpret_cast<uintptr_t>(vecs[k]) & 15u))
@@ -1042,6 +1065,7 @@ dose_status adjoint_supported(const dose_matrix* A, bool quad, const float* cons
 extern "C" {
 
 dose_status dose_adjoint(const dose_matrix* A, const float* r, float* g, void* stream) {
+    NvtxRange nvtx_range("dose_adjoint");
     if (!A) return invalid("dose_adjoint: null matrix");
     if (A->nrows && !r) return invalid("dose_adjoint: r is NULL");
     if (A->ncols && !g) return invalid("dose_adjoint: g is NULL");
@@ -1055,6 +1079,7 @@ dose_status dose_adjoint(const dose_matrix* A, const float* r, float* g, void* s
 
 dose_status dose_fwd_adj_quadratic(const dose_matrix* A, const float* x, const float* p, const float* w, float* d,
                                    double* f, float* g, void* stream) {
+    NvtxRange nvtx_range("dose_fwd_adj_quadratic");
     if (!A) return invalid("dose_fwd_adj_quadratic: null matrix");
     if (!f || (A->ncols && (!x || !g)) || (A->nrows && (!p || !w)))
         return invalid("dose_fwd_adj_quadratic: null pointer argument");
@@ -1067,6 +1092,7 @@ dose_status dose_fwd_adj_quadratic(const dose_matrix* A, const float* x, const f
 
 dose_status dose_pg_step(const dose_matrix* A, float* x, const float* p, const float* w, float eta, double* f,
                          float* g, void* stream) {
+    NvtxRange nvtx_range("dose_pg_step");
     if (!A) return invalid("dose_pg_step: null matrix");
     if (!f || (A->ncols && !x) || (A->nrows && (!p || !w))) return invalid("dose_pg_step: null pointer argument");
     if (!(eta >= 0.0f) || std::isinf(eta)) return invalid("dose_pg_step: eta must be finite and >= 0");
@@ -1079,6 +1105,7 @@ dose_status dose_pg_step(const dose_matrix* A, float* x, const float* p, const f
 
 dose_status dose_spmv_batched(const dose_matrix* const* A, int count, const float* const* X, float* const* D,
                               int nvec, void* stream) {
+    NvtxRange nvtx_range("dose_spmv_batched");
     if (count < 0 || count > 4096) return invalid("dose_spmv_batched: count must be in [0, 4096]");
     if (count == 0) return DOSE_OK;
     if (!A || !X || !D) return invalid("dose_spmv_batched: null array");
@@ -1119,6 +1146,8 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
     out->fmt = A->fmt;
     out->flags = A->flags;
     out->fingerprint = A->fingerprint;
+    out->spmv_layout = (A->flags & DOSE_CREATE_SELL) ? 3u : spmv_on_row_groups(A) ? 2u : 1u;
+    out->rg_spmv_bytes = out->spmv_layout == 2 ? rg_spmv_bytes(A) : 0;
     out->n_stages = A->fwd.n_stages;
     out->n_coop_rows = A->fwd.n_coop_rows;
     std::memcpy(out->lanes_hist, A->fwd.lanes_hist, sizeof(out->lanes_hist));
@@ -1178,6 +1207,7 @@ dose_status dose_matrix_info(const dose_matrix* A, dose_info* out) {
 }
 
 dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning) {
+    NvtxRange nvtx_range("dose_set_tuning");
     if (!A) return invalid("dose_set_tuning: null matrix");
     Tuning t = A->fwd.tuning;
     AdjTuning at = A->adj_tuning;
@@ -1191,6 +1221,8 @@ dose_status dose_set_tuning(dose_matrix* A, const dose_tuning* tuning) {
     if (st == DOSE_OK && A->fwd64_own) st = apply_schedule(A, A->fwd64, t, false);
     if (st != DOSE_OK) return st;
     if (at.layout == 2 && !A->rg.built) return invalid("adj_layout = 2: the handle has no row-group layout");
+    if (t.layout == 2 && (!A->rg.built || (A->flags & DOSE_CREATE_COMPENSATED)))
+        return invalid("fwd_layout = 2: dose_spmv cannot run on the row-group layout of this handle");
     const AdjTuning old_at = A->adj_tuning;
     A->adj_tuning = at;
     if (A->rg.built && (at.rg_tile_u != old_at.rg_tile_u || at.rg_tile_rows != old_at.rg_tile_rows)) {

@@ -62,6 +62,7 @@ struct Tuning {
     uint32_t consumer_warps = 16;
     uint32_t l2_prefetch = 2;   // stages prefetched into L2 ahead of the shared-memory ring
     uint32_t row_order = 2;     // non-empty rows of a stage: 1 = matrix order, 2 = most 4-entry groups first
+    uint32_t layout = 0;        // dose_spmv: 0 = row groups where built, 1 = CSR, 2 = row groups
 };
 
 // SELL-32-sigma copy of a matrix for the forward SpMV (DOSE_CREATE_SELL).
@@ -273,12 +274,18 @@ uint64_t rg_fused_bytes(const dose_matrix* A, bool with_d);
 // matrices A[0 .. count) (count <= kRgSpmmMaxPerLaunch), and the launches.
 constexpr uint32_t kRgSpmmMaxPerLaunch = 32;
 bool rg_spmm_applies(const dose_matrix* const* A, int count, size_t* smem, uint32_t* depth);
+// d = A x on the row-group layout (rg_spmm.cu): whether it fits, and the launch.
+bool rg_spmv_applies(const dose_matrix* A, size_t* smem, uint32_t* depth);
+// Whether dose_spmv takes the row-group form for this handle (dose_api.cu).
+bool spmv_on_row_groups(const dose_matrix* A);
+cudaError_t launch_rg_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s);
 // Which form dose_spmv_batched takes for these matrices (2 row groups, 1 CSR)
 // and how many kernels one call launches.
 void spmm_batched_plan(const dose_matrix* const* A, int count, int* layout, int* launches);
 cudaError_t launch_rg_spmm(const dose_matrix* const* A, int count, const float* const* X, float* const* D, int nvec,
                            cudaStream_t s);
 uint64_t rg_adjoint_bytes(const dose_matrix* A);
+uint64_t rg_spmv_bytes(const dose_matrix* A);
 // Sum of the per-CTA partials (g, f) in a fixed order; optional projected-gradient step.
 cudaError_t launch_adjoint_finalize(const dose_matrix* A, const float* g_part, const uint32_t* wlo, uint32_t wwidth,
                                     uint32_t nparts, bool quad, float* g, double* f, float* x_update, float eta,

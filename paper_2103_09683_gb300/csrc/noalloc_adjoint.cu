@@ -34,6 +34,7 @@
 #include <string>
 
 #include "dose_internal.cuh"
+#include "nvtx_range.cuh"
 
 namespace dose {
 namespace {
@@ -131,6 +132,7 @@ extern "C" dose_status dose_adjoint_noalloc(uint32_t nrows, uint32_t ncols, uint
                                             const uint32_t* col_idx, dose_format fmt, const void* values,
                                             const float* row_scales, float scale, const float* r, float* g,
                                             void* stream) {
+    NvtxRange nvtx_range("dose_adjoint_noalloc");
     if (fmt != DOSE_FMT_U16_SCALE && fmt != DOSE_FMT_BF16 && fmt != DOSE_FMT_FP8E4M3_ROWSCALE &&
         fmt != DOSE_FMT_F16 && fmt != DOSE_FMT_F32) {
         set_error("dose_adjoint_noalloc: unknown format");

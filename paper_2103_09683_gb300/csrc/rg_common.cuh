@@ -98,6 +98,24 @@ __device__ __forceinline__ void rg_dec4(const uint4& q, float (&a)[4]) {
     }
 }
 
+// Sum of the four row sums over the warp; lane l returns row (l >> 3)'s total
+// (every lane of an octet the same value, in one fixed order).
+__device__ __forceinline__ float rg_reduce4(float a0, float a1, float a2, float a3, uint32_t lane) {
+    const bool hi = lane & 16;
+    float k0 = hi ? a2 : a0, k1 = hi ? a3 : a1;
+    const float s0 = hi ? a0 : a2, s1 = hi ? a1 : a3;
+    k0 = __fadd_rn(k0, __shfl_xor_sync(0xffffffffu, s0, 16));
+    k1 = __fadd_rn(k1, __shfl_xor_sync(0xffffffffu, s1, 16));
+    const bool b3 = lane & 8;
+    float k = b3 ? k1 : k0;
+    const float s = b3 ? k0 : k1;
+    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, s, 8));
+    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, k, 4));
+    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, k, 2));
+    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, k, 1));
+    return k;
+}
+
 // Offset of group row g (0..3) from the stage's first row; 0xFFFF: no row.
 __device__ __forceinline__ uint32_t rg_row_off(const uint4& G, uint32_t g) {
     const uint32_t w = g < 2 ? G.z : G.w;

@@ -48,23 +48,6 @@ struct RgParams {
     int* err;
 };
 
-// Sum of the four row sums over the warp; lane l returns row (l >> 3)'s total
-// (every lane of an octet the same value, in one fixed order).
-__device__ __forceinline__ float rg_reduce4(float a0, float a1, float a2, float a3, uint32_t lane) {
-    const bool hi = lane & 16;
-    float k0 = hi ? a2 : a0, k1 = hi ? a3 : a1;
-    const float s0 = hi ? a0 : a2, s1 = hi ? a1 : a3;
-    k0 = __fadd_rn(k0, __shfl_xor_sync(0xffffffffu, s0, 16));
-    k1 = __fadd_rn(k1, __shfl_xor_sync(0xffffffffu, s1, 16));
-    const bool b3 = lane & 8;
-    float k = b3 ? k1 : k0;
-    const float s = b3 ? k0 : k1;
-    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, s, 8));
-    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, k, 4));
-    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, k, 2));
-    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, k, 1));
-    return k;
-}
 
 // Producer (one thread): descriptors in double-buffered windows of kDescWin as
 // in the CSR pipeline, then per stage the group records, union columns, union
@@ -680,6 +663,13 @@ uint64_t rg_fused_bytes(const dose_matrix* A, bool with_d) {
     const uint64_t nr = A->nrows, nc = A->ncols, P = A->rg.sched.grid, W = A->rg.sched.wwidth;
     return rg_matrix_bytes(A) + (nr + 7) / 8 + 8 * nr + (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 4 * nr : 0) +
            (with_d ? 4 * nr : 0) + 8 * nc + 8ull * P * W + 8 * P + 8;
+}
+
+// Bytes of one dose_spmv on the layout: the layout once, the non-empty bits,
+// FP8 row scales, x in (once), d out (every row).
+uint64_t rg_spmv_bytes(const dose_matrix* A) {
+    const uint64_t nr = A->nrows, nc = A->ncols;
+    return rg_matrix_bytes(A) + (nr + 7) / 8 + (A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 4 * nr : 0) + 4 * nc + 4 * nr;
 }
 
 uint64_t rg_adjoint_bytes(const dose_matrix* A) {

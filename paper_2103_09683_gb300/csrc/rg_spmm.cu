@@ -37,6 +37,9 @@ constexpr uint32_t kMmXStride = 16;      // floats per column of the staged wind
 // (whole blocks of 8 columns x 16 floats).
 __host__ __device__ constexpr uint32_t mm_xs_bytes(uint32_t W) { return ((W + 1 + 7) / 8 * 8 * 64 + 127) / 128 * 128; }
 
+// ... of a window of W columns of x and the zero element after it (one float each).
+__host__ __device__ constexpr uint32_t mm_x1_bytes(uint32_t W) { return ((W + 1) * 4 + 127) / 128 * 128; }
+
 struct MmItem {
     const uint4* grp;
     const void* ucol;
@@ -328,6 +331,130 @@ __global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
     }
 }
 
+// Single-vector form (d = A x on the row-group layout, dose_spmv): the same
+// producer, ring and zero warps; the window of x is one float per column.  A
+// warp takes a group: lane l handles the union positions u = l, l + 32, ...
+// (one column load, the four rows' values in one load, one x gather: the 32
+// positions of a step have columns that differ mod 32, so the gather is one
+// wavefront), keeps the four rows' partial sums and reduces them with the
+// transposed butterfly of rg_reduce4; lane 8 g stores row g's dose.
+template <int FMT, uint32_t IW>
+__global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_spmv_kernel(const __grid_constant__ MmParams p) {
+    constexpr uint32_t RV = 4 * (uint32_t)sizeof(typename Fmt<FMT>::T);
+    constexpr uint32_t VA = RV >= 16 ? 1 : 16 / RV;
+    constexpr uint32_t CA = 16 / IW;
+    constexpr bool FP8 = FMT == DOSE_FMT_FP8E4M3_ROWSCALE;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t S = p.depth, NW = p.nw;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + 8;
+    float* xs = reinterpret_cast<float*>(smem + kMmHeader);  // W + 1 floats: the window of x and a zero
+    uint32_t wmax = 0;
+    for (uint32_t m = 0; m < p.count; ++m) wmax = max(wmax, p.item[m].W);
+    unsigned char* slot_base = smem + kMmHeader + mm_x1_bytes(wmax);
+    const RgSlot SL = p.SL;
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < S; ++i) {
+            dev::mbar_init(&full[i], 1);
+            dev::mbar_init(&empty[i], NW);
+        }
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        if (lane == 0) mm_produce<FMT, IW>(p, slot_base, full, empty);
+        return;
+    }
+    if (warp > NW) {
+        for (uint32_t m = 0; m < p.count; ++m)
+            mm_zero_rows(p.item[m].mask, p.item[m].D, p.item[m].nrows, 1, warp - NW - 1, kMmZeroWarps, lane);
+        return;
+    }
+    const uint32_t wi = warp - 1, ctid = threadIdx.x - 32, nct = NW * 32;
+    const uint32_t slot0 = dev::smem_u32(slot_base);
+    uint32_t st = 0, ph = 0, rot = 0;
+    for (uint32_t m = 0; m < p.count; ++m) {
+        const MmItem& it = p.item[m];
+        const uint32_t W = it.W, wlo = it.wlo[blockIdx.x];
+        dev::named_barrier(1, nct);  // every worker is done with the previous window of x
+        for (uint32_t c = ctid; c <= W; c += nct)
+            xs[c] = c < W && wlo + c < it.ncols ? __ldg(it.X + wlo + c) : 0.f;
+        dev::named_barrier(1, nct);
+        const uint32_t xs_a = dev::smem_u32(xs) - 4 * wlo;  // x_c at xs_a + 4 c
+        const uint32_t zc = wlo + W;                        // the zero element
+        const uint32_t sb = it.cta_begin[blockIdx.x], se = it.cta_begin[blockIdx.x + 1];
+        for (uint32_t s = sb; s < se; ++s) {
+            if (!dev::mbar_wait_poll(&full[st], ph)) {
+                atomicExch(p.err, kErrTimeoutFull);
+                return;  // every worker waits on the same phases, so all of them leave here
+            }
+            const uint32_t slot = slot0 + st * SL.bytes;
+            const StageDesc D = slot_desc(slot);
+            const uint32_t col_a = slot + SL.col_off - IW * (D.nz0 & ~(CA - 1));
+            const uint32_t val_a = slot + SL.val_off - RV * (D.nz0 & ~(VA - 1));
+            const uint32_t vrs = slot + SL.vec_off - 4 * (D.row0 & ~3u);
+            const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
+            for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
+                const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
+                const uint32_t nU = G.y, u0 = G.x, nfull = nU >> 5;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                auto mac = [&](const uint4& q, uint32_t c) {
+                    float v[4];
+                    rg_dec4<FMT>(q, v);
+                    const float x = dev::lds_f32(xs_a + 4 * c);
+                    a0 = __fmaf_rn(v[0], x, a0);
+                    a1 = __fmaf_rn(v[1], x, a1);
+                    a2 = __fmaf_rn(v[2], x, a2);
+                    a3 = __fmaf_rn(v[3], x, a3);
+                };
+                const uint32_t ca = col_a + IW * (u0 + lane), va = val_a + RV * (u0 + lane);
+#pragma unroll 2
+                for (uint32_t k = 0; k < nfull; ++k) mac(rg_ldval<FMT>(va + 32 * RV * k), rg_ldcol<IW>(ca + 32 * IW * k));
+                if (nU & 31u) {
+                    const uint32_t u = 32 * nfull + lane;
+                    mac(rg_ldval_lt<FMT>(u, nU, va + 32 * RV * nfull), rg_ldcol_lt<IW>(u, nU, ca + 32 * IW * nfull, zc));
+                }
+                const float sum = rg_reduce4(a0, a1, a2, a3, lane);
+                const uint32_t off = rg_row_off(G, lane >> 3);
+                if ((lane & 7u) == 0 && off != 0xFFFFu) {
+                    const uint32_t row = D.row0 + off;
+                    const float sc = FP8 ? dev::lds_f32(vrs + 4 * row) : it.scale;
+                    it.D[row] = FP8 || FMT == DOSE_FMT_U16_SCALE ? __fmul_rn(sc, sum) : sum;
+                }
+            }
+            rot = rot + 1 == NW ? 0 : rot + 1;
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&empty[st]);
+            if (++st == S) {
+                st = 0;
+                ph ^= 1;
+            }
+        }
+    }
+}
+
+template <int FMT, uint32_t IW>
+cudaError_t mv_launch_t(const MmParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
+    auto k = rg_spmv_kernel<FMT, IW>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 32 * (1 + p.nw + kMmZeroWarps), smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <uint32_t IW>
+cudaError_t mv_launch_iw(int fmt, const MmParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
+    switch (fmt) {
+        case DOSE_FMT_U16_SCALE: return mv_launch_t<DOSE_FMT_U16_SCALE, IW>(p, grid, smem, s);
+        case DOSE_FMT_BF16: return mv_launch_t<DOSE_FMT_BF16, IW>(p, grid, smem, s);
+        case DOSE_FMT_F16: return mv_launch_t<DOSE_FMT_F16, IW>(p, grid, smem, s);
+        case DOSE_FMT_F32: return mv_launch_t<DOSE_FMT_F32, IW>(p, grid, smem, s);
+        case DOSE_FMT_FP8E4M3_ROWSCALE: return mv_launch_t<DOSE_FMT_FP8E4M3_ROWSCALE, IW>(p, grid, smem, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int FMT, uint32_t IW>
 cudaError_t mm_launch_t(const MmParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
     auto k = rg_spmm_kernel<FMT, IW>;
@@ -424,6 +551,58 @@ cudaError_t launch_rg_spmm(const dose_matrix* const* A, int count, const float* 
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+}  // namespace dose
+
+namespace dose {
+
+// The row-group form of dose_spmv applies when the handle has the layout and
+// the window of x plus a ring of two slots fits in shared memory.
+bool rg_spmv_applies(const dose_matrix* A, size_t* smem_out, uint32_t* depth_out) {
+    const RowGroups& R = A->rg;
+    if (!R.built || !R.sched.desc) return false;
+    const RgSlot SL = rg_slot(R.tile_u, R.tile_g, R.tile_rows, value_bytes(A->fmt), R.iw,
+                              A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
+    const size_t fixed = kMmHeader + mm_x1_bytes(R.sched.wwidth);
+    if (fixed + 2ull * SL.bytes > kMmSmemBudget) return false;
+    const uint32_t depth = (uint32_t)std::min<size_t>(8, (kMmSmemBudget - fixed) / SL.bytes);
+    if (smem_out) *smem_out = fixed + (size_t)depth * SL.bytes;
+    if (depth_out) *depth_out = depth;
+    return true;
+}
+
+cudaError_t launch_rg_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s) {
+    size_t smem = 0;
+    uint32_t depth = 0;
+    if (!rg_spmv_applies(A, &smem, &depth)) return cudaErrorInvalidConfiguration;
+    if (A->nrows == 0) return cudaSuccess;
+    const RowGroups& R = A->rg;
+    MmParams p;
+    p.count = 1;
+    p.nvec = 1;
+    p.depth = depth;
+    p.nw = kMmWorkers;
+    p.err = A->err;
+    MmItem& it = p.item[0];
+    it.grp = R.grp;
+    it.ucol = R.ucol;
+    it.uval = R.uval;
+    it.desc = R.sched.desc;
+    it.cta_begin = R.sched.cta_begin;
+    it.wlo = R.sched.wlo;
+    it.row_scale = A->row_scale;
+    it.mask = R.mask;
+    it.X = x;
+    it.D = d;
+    it.scale = A->scale;
+    it.nrows = A->nrows;
+    it.ncols = A->ncols;
+    it.W = R.sched.wwidth;
+    p.SL = rg_slot(R.tile_u, R.tile_g, R.tile_rows, value_bytes(A->fmt), R.iw,
+                   A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
+    return R.iw == 2 ? mv_launch_iw<2>(A->fmt, p, R.sched.grid, smem, s)
+                     : mv_launch_iw<4>(A->fmt, p, R.sched.grid, smem, s);
 }
 
 }  // namespace dose

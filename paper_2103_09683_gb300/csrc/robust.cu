@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "dose_internal.cuh"
+#include "nvtx_range.cuh"
 
 using namespace dose;
 
@@ -171,12 +172,14 @@ dose_status dose_destroy_scenarios(dose_scenarios* S) {
 
 dose_status dose_robust_quadratic(const dose_scenarios* S, int mode, const float* x, const float* p, const float* w,
                                   double* f, double* f_scen, float* g, void* stream) {
+    NvtxRange nvtx_range("dose_robust_quadratic");
     if (S && S->ncols && !g) return invalid("dose_robust_quadratic: g is NULL");
     return robust_run(S, mode, x, p, w, f, f_scen, g, nullptr, 0.f, stream);
 }
 
 dose_status dose_robust_pg_step(const dose_scenarios* S, int mode, float* x, const float* p, const float* w,
                                 float eta, double* f, float* g, void* stream) {
+    NvtxRange nvtx_range("dose_robust_pg_step");
     if (!(eta >= 0.0f) || std::isinf(eta)) return invalid("dose_robust_pg_step: eta must be finite and >= 0");
     return robust_run(S, mode, x, p, w, f, nullptr, g, x, eta, stream);
 }

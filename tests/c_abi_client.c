@@ -51,6 +51,7 @@ static void print_layouts(void) {
     LAYOUT(dose_tuning, adj_layout);
     LAYOUT(dose_tuning, rg_warps);
     LAYOUT(dose_tuning, rg_l2_prefetch);
+    LAYOUT(dose_tuning, fwd_layout);
     printf("sizeof dose_info %zu\n", sizeof(dose_info));
     LAYOUT(dose_info, nnz);
     LAYOUT(dose_info, lanes_hist);
@@ -64,6 +65,9 @@ static void print_layouts(void) {
     LAYOUT(dose_info, rg_union_entries);
     LAYOUT(dose_info, rg_window);
     LAYOUT(dose_info, rg_index_bytes);
+    LAYOUT(dose_info, fingerprint);
+    LAYOUT(dose_info, spmv_layout);
+    LAYOUT(dose_info, rg_spmv_bytes);
 }
 
 /* create must refuse desc on the host: DOSE_ERR_INVALID_ARG, a message, no handle */

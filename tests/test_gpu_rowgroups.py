@@ -308,3 +308,129 @@ def test_row_group_batched_spmm_in_a_graph():
         assert torch.equal(D, E)
     for A in handles:
         A.device_status()
+
+
+# ------------------------------------------------------------ dose_spmv on row groups
+
+def _check_spmv_rg(A, enc, csr, seed=21):
+    """dose_spmv on the row-group layout: every row against the oracle (per-row
+    FP32 bound), rows without entries exactly 0 although d held garbage, the
+    tail past d untouched, bitwise repeatable; unit vectors give the stored
+    values bit-exactly."""
+    assert A.info()["spmv_layout"] == 2
+    x = np.random.default_rng(seed).uniform(0, 1, csr.ncols).astype(np.float32)
+    buf = torch.full((csr.nrows + 33,), -5.0, dtype=torch.float32, device="cuda")
+    d = buf[:csr.nrows]
+    A.spmv(_to(x), d)
+    ref = oracle.spmv(csr.nrows, enc.row_ptr, enc.col, enc.decoded, x)
+    got = d.cpu().numpy()
+    fwd_check(got, ref)
+    empty = np.diff(enc.row_ptr.astype(np.int64)) == 0
+    assert np.all(got[empty] == 0.0)
+    assert torch.all(buf[csr.nrows:] == -5.0)
+    assert np.array_equal(A.spmv(_to(x)).cpu().numpy().view(np.uint32), got.view(np.uint32))
+    if csr.ncols:
+        rows_of = np.repeat(np.arange(csr.nrows), np.diff(enc.row_ptr.astype(np.int64)))
+        for j in np.random.default_rng(seed + 1).choice(csr.ncols, min(4, csr.ncols), replace=False):
+            e = np.zeros(csr.ncols, dtype=np.float32)
+            e[j] = 1.0
+            expect = np.zeros(csr.nrows, dtype=np.float32)
+            sel = enc.col == j
+            expect[rows_of[sel]] = enc.decoded[sel].astype(np.float32)
+            assert np.array_equal(A.spmv(_to(e)).cpu().numpy().view(np.uint32), expect.view(np.uint32)), j
+    A.device_status()
+    return got
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_spmv_on_row_groups_every_format(tiny, fmt):
+    """The default dose_spmv runs on the row-group layout; the CSR form
+    (fwd_layout = 1) on the same handle meets the same bound; switching back
+    gives the same bits as before."""
+    A, enc = make(tiny, fmt)
+    d_rg = _check_spmv_rg(A, enc, tiny)
+    A.set_tuning(fwd_layout=1)
+    assert A.info()["spmv_layout"] == 1 and A.info()["rg_spmv_bytes"] == 0
+    x = np.random.default_rng(21).uniform(0, 1, tiny.ncols).astype(np.float32)
+    fwd_check(A.spmv(_to(x)).cpu().numpy(), oracle.spmv(tiny.nrows, enc.row_ptr, enc.col, enc.decoded, x))
+    A.set_tuning(fwd_layout=2)
+    assert np.array_equal(A.spmv(_to(x)).cpu().numpy().view(np.uint32), d_rg.view(np.uint32))
+    assert A.info()["rg_spmv_bytes"] > 0
+
+
+@pytest.mark.parametrize("fmt", ["u16", "fp8"])
+def test_spmv_on_row_groups_small_tiles(tiny, fmt):
+    A, enc = make(tiny, fmt, tuning=SMALL_TILES)
+    _check_spmv_rg(A, enc, tiny)
+
+
+@pytest.mark.parametrize("name", ["one_by_one", "empty_matrix", "one_row", "ragged_small_nc"])
+def test_spmv_on_row_groups_edge_cases(name):
+    csr = edge_case_matrices()[name]
+    for tuning in (dict(fwd_layout=2), dict(fwd_layout=2, **SMALL_TILES)):
+        A, enc = make(csr, "u16", tuning=tuning)
+        _check_spmv_rg(A, enc, csr)
+
+
+def test_spmv_on_row_groups_wide_and_ragged():
+    """Rows of 200-600 entries (unions past 256 columns), 32-bit union indices
+    over 70000 spots, and nrows not a multiple of 32."""
+    rng = np.random.default_rng(12)
+    lens = rng.integers(200, 600, 901)
+    lens[::7] = 0
+    csr = dosegen.random_csr(901, 3000, seed=13, lengths=lens)
+    for fmt in ("u16", "f32", "fp8"):
+        A, enc = make(csr, fmt, tuning=dict(fwd_layout=2))
+        _check_spmv_rg(A, enc, csr)
+    nrows, ncols, span = 20003, 70000, 150
+    rp, cols = [0], []
+    for i in range(nrows):
+        start = (i * (ncols - span)) // nrows
+        n = int(rng.integers(0, 40)) if i % 5 else 0
+        cols.append(start + np.sort(rng.choice(span, size=n, replace=False)))
+        rp.append(rp[-1] + n)
+    col = np.concatenate(cols).astype(np.uint32)
+    csr = dosegen.CSR(nrows, ncols, np.asarray(rp, dtype=np.uint32), col, rng.uniform(0.01, 1.0, col.size))
+    A, enc = make(csr, "u16")
+    assert A.info()["rg_index_bytes"] == 4
+    _check_spmv_rg(A, enc, csr)
+
+
+def test_spmv_layout_fallbacks_and_refusals():
+    """Compensated handles and rows past 4096 entries keep dose_spmv on CSR;
+    fwd_layout = 2 is refused where the row-group form cannot run."""
+    csr = dosegen.generate(dosegen.TINY)
+    A, enc = make(csr, "u16", compensated=True)
+    assert A.info()["spmv_layout"] == 1
+    with pytest.raises(dose.DoseError) as ei:
+        make(csr, "u16", compensated=True, tuning=dict(fwd_layout=2))
+    assert ei.value.status == 4
+    with pytest.raises(dose.DoseError):
+        A.set_tuning(fwd_layout=2)
+    long = dosegen.random_csr(4, 6000, seed=17, lengths=[3, 5000, 7, 0])
+    B, encb = make(long, "u16")
+    assert B.info()["spmv_layout"] == 1
+    x = np.random.default_rng(3).uniform(0, 1, long.ncols).astype(np.float32)
+    fwd_check(B.spmv(_to(x)).cpu().numpy(), oracle.spmv(4, encb.row_ptr, encb.col, encb.decoded, x))
+    S, _ = make(csr, "u16", sell=True)
+    assert S.info()["spmv_layout"] == 3
+
+
+def test_spmv_on_row_groups_in_a_graph(tiny):
+    """Captured in a CUDA graph: the replay gives the eager bits."""
+    A, enc = make(tiny, "u16", tuning=SMALL_TILES)
+    x = _to(np.random.default_rng(8).uniform(0, 1, tiny.ncols).astype(np.float32))
+    eager = A.spmv(x).clone()
+    d = torch.empty_like(eager)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        A.spmv(x, d, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        A.spmv(x, d, stream=s)
+    d.fill_(7.0)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(d, eager)
