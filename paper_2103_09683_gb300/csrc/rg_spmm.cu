@@ -29,6 +29,7 @@ namespace {
 constexpr uint32_t kMmMaxPerLaunch = kRgSpmmMaxPerLaunch;
 constexpr uint32_t kMmWorkers = 16;      // worker warps (plus one producer and the zero warps)
 constexpr uint32_t kMmZeroWarps = 2;     // warps writing the rows without entries
+constexpr uint32_t kMvWorkers = 28;      // worker warps of the single-vector form (about 50 registers each)
 constexpr uint32_t kMmHeader = 1024;     // mbarriers
 constexpr uint32_t kMmSmemBudget = kMaxSmemPerBlock;
 constexpr uint32_t kMmXStride = 16;      // floats per column of the staged window of X (vectors <= 16)
@@ -331,6 +332,46 @@ __global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
     }
 }
 
+// K steps of 32 union positions of one group for lane `lane` (K = 0: any
+// number, in a loop): the four rows' values times x_c, added to a0..a3 in
+// step order.  Positions past nU read nothing and add 0 * x of the zero element.
+template <int FMT, uint32_t IW, int K>
+__device__ __forceinline__ void mv_steps(uint32_t ca, uint32_t va, uint32_t nU, uint32_t lane, uint32_t zc,
+                                         uint32_t xs_a, float& a0, float& a1, float& a2, float& a3) {
+    constexpr uint32_t RV = 4 * (uint32_t)sizeof(typename Fmt<FMT>::T);
+    auto mac = [&](const uint4& q, uint32_t c) {
+        float v[4];
+        rg_dec4<FMT>(q, v);
+        const float x = dev::lds_f32(xs_a + 4 * c);
+        a0 = __fmaf_rn(v[0], x, a0);
+        a1 = __fmaf_rn(v[1], x, a1);
+        a2 = __fmaf_rn(v[2], x, a2);
+        a3 = __fmaf_rn(v[3], x, a3);
+    };
+    if constexpr (K == 0) {
+        const uint32_t nfull = nU >> 5;
+#pragma unroll 2
+        for (uint32_t k = 0; k < nfull; ++k) mac(rg_ldval<FMT>(va + 32 * RV * k), rg_ldcol<IW>(ca + 32 * IW * k));
+        if (nU & 31u) {
+            const uint32_t u = 32 * nfull + lane;
+            mac(rg_ldval_lt<FMT>(u, nU, va + 32 * RV * nfull), rg_ldcol_lt<IW>(u, nU, ca + 32 * IW * nfull, zc));
+        }
+    } else {
+        uint4 q[K];
+        uint32_t c[K];
+#pragma unroll
+        for (int k = 0; k < K - 1; ++k) {
+            q[k] = rg_ldval<FMT>(va + 32 * RV * k);
+            c[k] = rg_ldcol<IW>(ca + 32 * IW * k);
+        }
+        const uint32_t u = 32 * (K - 1) + lane;
+        q[K - 1] = rg_ldval_lt<FMT>(u, nU, va + 32 * RV * (K - 1));
+        c[K - 1] = rg_ldcol_lt<IW>(u, nU, ca + 32 * IW * (K - 1), zc);
+#pragma unroll
+        for (int k = 0; k < K; ++k) mac(q[k], c[k]);
+    }
+}
+
 // Single-vector form (d = A x on the row-group layout, dose_spmv): the same
 // producer, ring and zero warps; the window of x is one float per column.  A
 // warp takes a group: lane l handles the union positions u = l, l + 32, ...
@@ -339,7 +380,7 @@ __global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
 // wavefront), keeps the four rows' partial sums and reduces them with the
 // transposed butterfly of rg_reduce4; lane 8 g stores row g's dose.
 template <int FMT, uint32_t IW>
-__global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_spmv_kernel(const __grid_constant__ MmParams p) {
+__global__ void __launch_bounds__((kMvWorkers + 1 + kMmZeroWarps) * 32, 1) rg_spmv_kernel(const __grid_constant__ MmParams p) {
     constexpr uint32_t RV = 4 * (uint32_t)sizeof(typename Fmt<FMT>::T);
     constexpr uint32_t VA = RV >= 16 ? 1 : 16 / RV;
     constexpr uint32_t CA = 16 / IW;
@@ -397,23 +438,23 @@ __global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
             const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
             for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
                 const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
-                const uint32_t nU = G.y, u0 = G.x, nfull = nU >> 5;
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-                auto mac = [&](const uint4& q, uint32_t c) {
-                    float v[4];
-                    rg_dec4<FMT>(q, v);
-                    const float x = dev::lds_f32(xs_a + 4 * c);
-                    a0 = __fmaf_rn(v[0], x, a0);
-                    a1 = __fmaf_rn(v[1], x, a1);
-                    a2 = __fmaf_rn(v[2], x, a2);
-                    a3 = __fmaf_rn(v[3], x, a3);
-                };
+                const uint32_t nU = G.y, u0 = G.x;
                 const uint32_t ca = col_a + IW * (u0 + lane), va = val_a + RV * (u0 + lane);
-#pragma unroll 2
-                for (uint32_t k = 0; k < nfull; ++k) mac(rg_ldval<FMT>(va + 32 * RV * k), rg_ldcol<IW>(ca + 32 * IW * k));
-                if (nU & 31u) {
-                    const uint32_t u = 32 * nfull + lane;
-                    mac(rg_ldval_lt<FMT>(u, nU, va + 32 * RV * nfull), rg_ldcol_lt<IW>(u, nU, ca + 32 * IW * nfull, zc));
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                // groups of up to 320 union columns: every step's loads issued up
+                // front, only the last step masked; longer single rows: a loop
+                switch ((nU + 31) >> 5) {
+                    case 1: mv_steps<FMT, IW, 1>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    case 2: mv_steps<FMT, IW, 2>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    case 3: mv_steps<FMT, IW, 3>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    case 4: mv_steps<FMT, IW, 4>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    case 5: mv_steps<FMT, IW, 5>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    case 6: mv_steps<FMT, IW, 6>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    case 7: mv_steps<FMT, IW, 7>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    case 8: mv_steps<FMT, IW, 8>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    case 9: mv_steps<FMT, IW, 9>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    case 10: mv_steps<FMT, IW, 10>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
+                    default: mv_steps<FMT, IW, 0>(ca, va, nU, lane, zc, xs_a, a0, a1, a2, a3); break;
                 }
                 const float sum = rg_reduce4(a0, a1, a2, a3, lane);
                 const uint32_t off = rg_row_off(G, lane >> 3);
@@ -582,7 +623,7 @@ cudaError_t launch_rg_spmv(const dose_matrix* A, const float* x, float* d, cudaS
     p.count = 1;
     p.nvec = 1;
     p.depth = depth;
-    p.nw = kMmWorkers;
+    p.nw = kMvWorkers;
     p.err = A->err;
     MmItem& it = p.item[0];
     it.grp = R.grp;
