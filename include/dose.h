@@ -47,7 +47,9 @@ typedef enum {
     DOSE_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
     DOSE_ERR_UNSUPPORTED = 4, /* valid request outside what this build implements */
     DOSE_ERR_TIMEOUT = 5,     /* a kernel's bounded wait ran out (dose_device_status) */
-    DOSE_ERR_IO = 6           /* the autotune cache file could not be read, parsed or written */
+    DOSE_ERR_IO = 6,          /* the autotune cache file could not be read, parsed or written */
+    DOSE_ERR_BOUNDS = 7       /* debug-checked build (libdose_debug.so, DOSE_DEBUG_CHECKS): a kernel met an
+                                 index outside its buffer and skipped that work (dose_device_status) */
 } dose_status;
 
 /* Stored value formats.  The paper stores 16-bit values (Sec. II-D), IEEE half
@@ -428,8 +430,12 @@ dose_status dose_encode_host(dose_format fmt, uint32_t nrows, const uint32_t* ro
                              uint64_t nnz, const double* values_f64, void* codes, float* scales);
 
 /* Synchronise `stream` and report a kernel-side failure recorded on the
- * handle since the last call (DOSE_ERR_TIMEOUT if a bounded wait ran out), then
- * clear it. */
+ * handle since the last call (DOSE_ERR_TIMEOUT if a bounded wait ran out;
+ * DOSE_ERR_BOUNDS in the debug-checked build if a row-group kernel met a group
+ * record or union column outside its stage, window or matrix and skipped that
+ * group), then clear it.  The debug-checked build is libdose_debug.so, compiled
+ * with DOSE_DEBUG_CHECKS; its results are bitwise those of the release build
+ * when nothing is out of bounds. */
 dose_status dose_device_status(const dose_matrix* A, void* stream);
 
 /* Self-test of the bounded waits that guard every pipelined kernel: one GPU

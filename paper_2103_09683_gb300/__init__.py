@@ -34,7 +34,7 @@ CREATE_SELL = 0x4
 SPMV_F64_NATIVE = 0x1
 ROBUST_MODES = {"expected": 0, "worst": 1}
 _STATUS = {0: "DOSE_OK", 1: "DOSE_ERR_INVALID_ARG", 2: "DOSE_ERR_OOM", 3: "DOSE_ERR_CUDA",
-           4: "DOSE_ERR_UNSUPPORTED", 5: "DOSE_ERR_TIMEOUT", 6: "DOSE_ERR_IO"}
+           4: "DOSE_ERR_UNSUPPORTED", 5: "DOSE_ERR_TIMEOUT", 6: "DOSE_ERR_IO", 7: "DOSE_ERR_BOUNDS"}
 
 
 class DoseError(RuntimeError):
@@ -170,24 +170,34 @@ def gpu_name(device: int = 0) -> str:
     return load().dose_gpu_name(int(device), buf, 256).decode()
 
 
-def build(force: bool = False) -> str:
-    """Compile libdose.so for sm_103a (nvcc) and return its path."""
-    return _build.build(force=force)
+def build(force: bool = False, debug: bool | None = None) -> str:
+    """Compile libdose.so for sm_103a (nvcc) and return its path; debug (default:
+    DOSE_DEBUG_CHECKS in the environment) builds libdose_debug.so instead."""
+    return _build.build(force=force, debug=debug_checks() if debug is None else debug)
 
 
 def library_path() -> str:
     return _build.LIB
 
 
+def debug_checks() -> bool:
+    """DOSE_DEBUG_CHECKS=1 in the environment selects the debug-checked library
+    (kernels test their indices and record DOSE_ERR_BOUNDS instead of an
+    out-of-bounds access)."""
+    return os.environ.get("DOSE_DEBUG_CHECKS", "") not in ("", "0")
+
+
 def load():
-    """Load libdose.so (built by build()); raise if it is missing."""
+    """Load libdose.so (built by build()), or libdose_debug.so under
+    DOSE_DEBUG_CHECKS=1; raise if it is missing."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(_build.LIB):
-                raise RuntimeError("libdose.so is not built: call paper_2103_09683_gb300.build() first "
-                                   "(there is no CPU fallback)")
-            lib = ctypes.CDLL(_build.LIB)
+            path = _build.LIB_DEBUG if debug_checks() else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"{os.path.basename(path)} is not built: call paper_2103_09683_gb300.build() "
+                                   "first (there is no CPU fallback)")
+            lib = ctypes.CDLL(path)
             for name, (res, args) in EXPORTS.items():
                 fn = getattr(lib, name)
                 fn.restype = res

@@ -1246,6 +1246,10 @@ dose_status dose_device_status(const dose_matrix* A, void* stream) {
     if (h != 0) {
         cudaMemsetAsync(A->err, 0, sizeof(int), as_stream(stream));
         cudaStreamSynchronize(as_stream(stream));
+        if (h == kErrBounds) {
+            set_error("a kernel met an index outside its buffer and skipped that work (debug-checked build)");
+            return DOSE_ERR_BOUNDS;
+        }
         set_error(h == kErrTimeoutFull ? "a consumer warp timed out waiting for staged data"
                                        : "the producer timed out waiting for a free stage slot");
         return DOSE_ERR_TIMEOUT;

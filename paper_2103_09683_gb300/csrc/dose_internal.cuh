@@ -331,6 +331,7 @@ constexpr int ADJ_MODE_QUADRATIC = 1; // d, f, g of the quadratic objective
 // Error codes written into the device error word.
 constexpr int kErrTimeoutFull = 1;
 constexpr int kErrTimeoutEmpty = 2;
+constexpr int kErrBounds = 3;  // debug-checked build: an index outside its buffer (the work was skipped)
 
 }  // namespace dose
 
@@ -502,6 +503,20 @@ __device__ __forceinline__ void sts_f32_if(bool p, uint32_t a, float v) {
                  ::"r"((uint32_t)p), "r"(a), "f"(v) : "memory");
 }
 // Vector loads (a 16- resp. 8- resp. 4-byte aligned), only when p; zeros otherwise.
+// Index check of the debug-checked build (DOSE_DEBUG_CHECKS): records
+// kErrBounds in the error word (the first failure wins) and returns whether
+// the work may go ahead.  Release builds compile it to `true`.
+__device__ __forceinline__ bool in_bounds(bool ok, int* err) {
+#ifdef DOSE_DEBUG_CHECKS
+    if (!ok) atomicCAS(err, 0, kErrBounds);
+    return ok;
+#else
+    (void)ok;
+    (void)err;
+    return true;
+#endif
+}
+
 __device__ __forceinline__ uint4 lds_v4_if(bool p, uint32_t a) {
     uint4 v = make_uint4(0, 0, 0, 0);
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t@q ld.shared.v4.u32 {%0, %1, %2, %3}, [%5];\n\t}"

@@ -116,6 +116,32 @@ __device__ __forceinline__ float rg_reduce4(float a0, float a1, float a2, float 
     return k;
 }
 
+// Debug-checked builds (DOSE_DEBUG_CHECKS): whether group record G fits its
+// stage (its union inside the stage's staged union, its rows inside the
+// stage's rows and the matrix) and every union column of it inside the CTA's
+// window [zc - W, zc] (zc: the zero element); a group that does not is
+// recorded (kErrBounds) and skipped by the whole warp.  Release builds: true.
+template <uint32_t IW>
+__device__ __forceinline__ bool rg_group_ok(const uint4& G, const StageDesc& D, uint32_t col_a, uint32_t nrows,
+                                            uint32_t zc, uint32_t W, uint32_t lane, int* err) {
+#ifdef DOSE_DEBUG_CHECKS
+    bool ok = G.x >= D.nz0 && G.x + G.y <= D.nz1 && G.x + G.y >= G.x;
+    for (uint32_t g = 0; g < 4; ++g) {
+        const uint32_t w = g < 2 ? G.z : G.w, off = (g & 1) ? (w >> 16) : (w & 0xFFFFu);
+        ok = ok && (off == 0xFFFFu || (D.row0 + off < D.row1 && D.row0 + off < nrows));
+    }
+    if (ok)
+        for (uint32_t k = lane; k < G.y; k += 32) {
+            const uint32_t c = IW == 2 ? dev::lds_u16(col_a + IW * (G.x + k)) : dev::lds_u32(col_a + IW * (G.x + k));
+            ok = ok && c - (zc - W) <= W;
+        }
+    return dev::in_bounds(__all_sync(0xffffffffu, ok), err);
+#else
+    (void)G, (void)D, (void)col_a, (void)nrows, (void)zc, (void)W, (void)lane, (void)err;
+    return true;
+#endif
+}
+
 // Offset of group row g (0..3) from the stage's first row; 0xFFFF: no row.
 __device__ __forceinline__ uint32_t rg_row_off(const uint4& G, uint32_t g) {
     const uint32_t w = g < 2 ? G.z : G.w;

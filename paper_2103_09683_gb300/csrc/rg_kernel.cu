@@ -17,8 +17,8 @@
 //      and forms r = 2 w (d - p); four shuffles give every lane the four r;
 //   4. for each of its union columns a lane adds sum_g a_gc r_g into the
 //      accumulator with one read-modify-write.
-// Rows without entries get d = 0 and their objective term in a strided pass
-// over the stage's rows.
+// Rows without entries get d = 0 and their objective term from the finalize
+// kernel (rg_finalize), which runs them while the main kernel drains.
 // Determinism (Sec. II-D: no float atomics, fixed reduction order): the union
 // columns of a group are distinct, so no two lanes of a warp update one word
 // in one instruction; each warp takes its groups in a fixed order; the CTA sums
@@ -401,6 +401,7 @@ __global__ void __launch_bounds__((kRgMaxWarps + 1) * 32, 1) rg_kernel(const RgP
         const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
         for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
             const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
+            if (!rg_group_ok<IW>(G, D, C.col, p.nrows, zc, W, lane, p.err)) continue;
             // four code paths (each unrolled for its step count) keep the
             // kernel's instructions within the instruction cache
             const uint32_t nit = (G.y + 31) >> 5;

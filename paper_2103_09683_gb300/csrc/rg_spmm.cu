@@ -260,6 +260,7 @@ __global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
             const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
             for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
                 const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
+                if (!rg_group_ok<IW>(G, D, col_a, it.nrows, zc, W, lane, p.err)) continue;
                 const uint32_t nU = G.y, u0 = G.x, nfull = nU >> 3;
                 float acc[16];
 #pragma unroll
@@ -438,6 +439,7 @@ __global__ void __launch_bounds__((kMvWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
             const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
             for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
                 const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
+                if (!rg_group_ok<IW>(G, D, col_a, it.nrows, zc, W, lane, p.err)) continue;
                 const uint32_t nU = G.y, u0 = G.x;
                 const uint32_t ca = col_a + IW * (u0 + lane), va = val_a + RV * (u0 + lane);
                 float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
