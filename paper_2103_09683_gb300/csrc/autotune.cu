@@ -543,14 +543,16 @@ dose_status sweep(dose_matrix* A, const float* x, unsigned purposes, cudaStream_
         if (A->rg.built) {
             for (uint32_t tu : {0u, 2048u, 3072u, 4096u, 6144u})
                 for (uint32_t tr : {512u, 1024u})
-                    for (uint32_t wn : {0u, 12u}) {
-                        AdjTuning a = base;
-                        a.layout = 0;
-                        a.rg_tile_u = tu;
-                        a.rg_tile_rows = tr;
-                        a.rg_warps = wn;
-                        cands.push_back(a);
-                    }
+                    for (uint32_t wn : {0u, 12u})
+                        for (uint32_t sd : {2u, 3u}) {
+                            AdjTuning a = base;
+                            a.layout = 0;
+                            a.rg_tile_u = tu;
+                            a.rg_tile_rows = tr;
+                            a.rg_warps = wn;
+                            a.rg_stages = sd;
+                            cands.push_back(a);
+                        }
             AdjTuning a = base;
             a.layout = 1;  // the CSR layout, for comparison
             cands.push_back(a);
