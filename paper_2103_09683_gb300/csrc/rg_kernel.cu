@@ -399,7 +399,7 @@ __global__ void __launch_bounds__((kRgMaxWarps + 1) * 32, 1) rg_kernel(const RgP
         C.col = slot + SL.col_off - IW * (D.nz0 & ~(CA - 1));
         C.val = slot + SL.val_off - RV * (D.nz0 & ~(VA - 1));
         const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
-        for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
+        for (uint32_t j = D.ne0 + (wi >= rot ? wi - rot : wi + NW - rot); j < D.ne1; j += NW) {
             const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
             if (!rg_group_ok<IW>(G, D, C.col, p.nrows, zc, W, lane, p.err)) continue;
             // four code paths (each unrolled for its step count) keep the

@@ -89,8 +89,12 @@ __device__ void mm_zero_rows(const uint32_t* mask, float* D, uint32_t nrows, uin
                 }
             } else {
                 float* d = D + (size_t)r0 * nv;
-                for (uint32_t k = lane; k < 32 * per; k += 32)
-                    if (!((word >> (k / per)) & 1u)) d[k] = 0.f;
+                if (per == 1) {  // one vector: lane l writes row r0 + l
+                    if (!((word >> lane) & 1u)) d[lane] = 0.f;
+                } else {
+                    for (uint32_t k = lane; k < 32 * per; k += 32)
+                        if (!((word >> (k / per)) & 1u)) d[k] = 0.f;
+                }
             }
         }
     }
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
             const uint32_t val_a = slot + SL.val_off - RV * (D.nz0 & ~(VA - 1)) + ES * g;
             const uint32_t vrs = slot + SL.vec_off - 4 * (D.row0 & ~3u);
             const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
-            for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
+            for (uint32_t j = D.ne0 + (wi >= rot ? wi - rot : wi + NW - rot); j < D.ne1; j += NW) {
                 const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
                 if (!rg_group_ok<IW>(G, D, col_a, it.nrows, zc, W, lane, p.err)) continue;
                 const uint32_t nU = G.y, u0 = G.x, nfull = nU >> 3;
@@ -437,7 +441,7 @@ __global__ void __launch_bounds__((kMvWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
             const uint32_t val_a = slot + SL.val_off - RV * (D.nz0 & ~(VA - 1));
             const uint32_t vrs = slot + SL.vec_off - 4 * (D.row0 & ~3u);
             const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
-            for (uint32_t j = D.ne0 + (wi + NW - rot) % NW; j < D.ne1; j += NW) {
+            for (uint32_t j = D.ne0 + (wi >= rot ? wi - rot : wi + NW - rot); j < D.ne1; j += NW) {
                 const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
                 if (!rg_group_ok<IW>(G, D, col_a, it.nrows, zc, W, lane, p.err)) continue;
                 const uint32_t nU = G.y, u0 = G.x;
