@@ -379,6 +379,7 @@ def run_gpu(args):
         del d
         out["precision_variants"] = precision_variants(csr, A, x0, p, w, eta, min(K, 100), args.warmup)
         out["batched_subset"] = batched_subset(min(K, 20), args.warmup, args)
+        out["half_double"] = half_double_extra(csr, x0, min(K, 100), args.warmup)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         hx, hp, hw = x0.cpu().numpy(), p.cpu().numpy(), w.cpu().numpy()
         out["cpu_baseline"] = cpu_baseline(csr, hx, hp, hw)
@@ -576,6 +577,44 @@ def precision_variants(csr, A_u16, x, p, w, eta, steps, warmup):
         if A is not A_u16:
             A.close()
     return {"rows_sampled": int(len(rows)), "steps": steps, "variants": out}
+
+
+def half_double_extra(csr, x, steps, warmup):
+    """The paper's own configuration (Sec. IV, Half/double) on the clinical beam
+    beside the plain form: IEEE half values, FP64 spot weights (the same weights
+    as the plain form's) and FP64 dose through dose_spmv_f64, both
+    accumulations; time, GB/s of the paper's byte model, and the dose's relative
+    error on 20000 sampled rows against the FP64 dose of the generator's values."""
+    import torch
+
+    import paper_2103_09683_gb300 as dose
+
+    xd = x.to(torch.float64)
+    xh = xd.cpu().numpy()
+    rng = np.random.default_rng(7)
+    lens = np.diff(csr.row_ptr.astype(np.int64))
+    rows = np.unique(rng.choice(np.nonzero(lens > 0)[0], 20000, replace=False))
+    exact = fp64_dose_rows(csr.row_ptr, csr.col, csr.val, xh, rows)
+    nz = exact != 0
+    codes, _ = dose.encode_host("f16", csr.row_ptr, csr.val)
+    A = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="f16", values=codes)
+    del codes
+    nbytes = A.info()["spmv_f64_bytes"]
+    d = torch.empty(A.nrows, dtype=torch.float64, device=x.device)
+    peak, _ = _peaks()
+    out = []
+    for native in (False, True):
+        ms = _time_calls(lambda: A.spmv_f64(xd, d, native=native), steps, warmup)
+        dv = d.cpu().numpy()[rows]
+        rel = np.abs(dv[nz] - exact[nz]) / np.abs(exact[nz])
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out.append({"accumulation": "fp64_fma" if native else "double_float", "ms_per_dose_eval": round(ms, 5),
+                    "gbs_paper_model": round(gbs, 1), "frac": round(gbs / peak, 4),
+                    "rel_err_vs_fp64_values": {"max": float(rel.max()), "mean": float(rel.mean())}})
+    A.device_status()
+    A.close()
+    return {"format": "f16 values, f64 x and d (32-bit indices, CSR)", "bytes": nbytes, "rows_sampled": int(len(rows)),
+            "variants": out}
 
 
 def batched_subset(steps, warmup, args, pick=(4, 13, 22)):

@@ -169,7 +169,9 @@ typedef struct {
                                    else CSR (default); 1 = CSR; 2 = row groups (create and
                                    dose_set_tuning fail if dose_spmv cannot take them).  On row groups
                                    a row's terms are added in its group's union order (see adj_layout),
-                                   so the last bits may differ from the CSR form's. */
+                                   so the last bits may differ from the CSR form's.  dose_spmv_f64
+                                   takes the row-group form only with fwd_layout = 2 (its arithmetic,
+                                   not its bytes, bounds it, and CSR is faster for it). */
 } dose_tuning;
 
 typedef struct {

@@ -276,6 +276,10 @@ constexpr uint32_t kRgSpmmMaxPerLaunch = 32;
 bool rg_spmm_applies(const dose_matrix* const* A, int count, size_t* smem, uint32_t* depth);
 // d = A x on the row-group layout (rg_spmm.cu): whether it fits, and the launch.
 bool rg_spmv_applies(const dose_matrix* A, size_t* smem, uint32_t* depth);
+// dose_spmv_f64 on the row-group layout (rg_spmm.cu): x64 is the handle's
+// prepared x (ncols + 1 elements of 8 bytes, the last one zero).
+bool rg_spmv64_applies(const dose_matrix* A, size_t* smem, uint32_t* depth);
+cudaError_t launch_rg_spmv64(const dose_matrix* A, const void* x64, double* d, bool native, cudaStream_t s);
 // Whether dose_spmv takes the row-group form for this handle (dose_api.cu).
 bool spmv_on_row_groups(const dose_matrix* A);
 cudaError_t launch_rg_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s);

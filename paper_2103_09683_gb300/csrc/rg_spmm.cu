@@ -18,6 +18,7 @@
 // without entries while the workers compute.
 // Deterministic: static assignment of groups to warps, fixed per-lane order,
 // fixed butterfly.
+#include "dfloat.cuh"
 #include "rg_common.cuh"
 
 #include <algorithm>
@@ -481,6 +482,156 @@ __global__ void __launch_bounds__((kMvWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
     }
 }
 
+// FP64-vector form (dose_spmv_f64 on the row-group layout): x as the 8-byte
+// elements prepare_x wrote (double-float pairs or doubles), one per column of
+// the window and a zero element; per lane four row accumulators Acc<MODE>,
+// combined by the transposed butterfly (pairs added as dfloat.cuh adds them);
+// lane 8 g stores row g's FP64 dose.  Rows without entries: the zero warps
+// write the two zero words of each double.
+__host__ __device__ constexpr uint32_t mm_x2_bytes(uint32_t W) { return ((W + 1) * 8 + 127) / 128 * 128; }
+
+template <int FMT, uint32_t IW, int MODE>
+__global__ void __launch_bounds__((kMvWorkers + 1 + kMmZeroWarps) * 32, 1) rg_spmv64_kernel(const __grid_constant__ MmParams p) {
+    constexpr uint32_t RV = 4 * (uint32_t)sizeof(typename Fmt<FMT>::T);
+    constexpr uint32_t VA = RV >= 16 ? 1 : 16 / RV;
+    constexpr uint32_t CA = 16 / IW;
+    constexpr bool FP8 = FMT == DOSE_FMT_FP8E4M3_ROWSCALE;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t S = p.depth, NW = p.nw;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + 8;
+    uint2* xs = reinterpret_cast<uint2*>(smem + kMmHeader);  // W + 1 elements: the window of x and a zero
+    uint32_t wmax = 0;
+    for (uint32_t m = 0; m < p.count; ++m) wmax = max(wmax, p.item[m].W);
+    unsigned char* slot_base = smem + kMmHeader + mm_x2_bytes(wmax);
+    const RgSlot SL = p.SL;
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < S; ++i) {
+            dev::mbar_init(&full[i], 1);
+            dev::mbar_init(&empty[i], NW);
+        }
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        if (lane == 0) mm_produce<FMT, IW>(p, slot_base, full, empty);
+        return;
+    }
+    if (warp > NW) {
+        for (uint32_t m = 0; m < p.count; ++m)  // a double row is two zero floats
+            mm_zero_rows(p.item[m].mask, p.item[m].D, p.item[m].nrows, 2, warp - NW - 1, kMmZeroWarps, lane);
+        return;
+    }
+    const uint32_t wi = warp - 1, ctid = threadIdx.x - 32, nct = NW * 32;
+    const uint32_t slot0 = dev::smem_u32(slot_base);
+    uint32_t st = 0, ph = 0, rot = 0;
+    for (uint32_t m = 0; m < p.count; ++m) {
+        const MmItem& it = p.item[m];
+        const uint2* x64 = reinterpret_cast<const uint2*>(it.X);  // ncols + 1 elements, the last one zero
+        double* d64 = reinterpret_cast<double*>(it.D);
+        const uint32_t W = it.W, wlo = it.wlo[blockIdx.x];
+        dev::named_barrier(1, nct);  // every worker is done with the previous window of x
+        for (uint32_t c = ctid; c <= W; c += nct)
+            xs[c] = c < W && wlo + c < it.ncols ? x64[wlo + c] : make_uint2(0u, 0u);
+        dev::named_barrier(1, nct);
+        const uint32_t xs_a = dev::smem_u32(xs) - 8 * wlo;  // x_c at xs_a + 8 c
+        const uint32_t zc = wlo + W;                        // the zero element
+        const uint32_t sb = it.cta_begin[blockIdx.x], se = it.cta_begin[blockIdx.x + 1];
+        for (uint32_t s = sb; s < se; ++s) {
+            if (!dev::mbar_wait_poll(&full[st], ph)) {
+                atomicExch(p.err, kErrTimeoutFull);
+                return;  // every worker waits on the same phases, so all of them leave here
+            }
+            const uint32_t slot = slot0 + st * SL.bytes;
+            const StageDesc D = slot_desc(slot);
+            const uint32_t col_a = slot + SL.col_off - IW * (D.nz0 & ~(CA - 1));
+            const uint32_t val_a = slot + SL.val_off - RV * (D.nz0 & ~(VA - 1));
+            const uint32_t vrs = slot + SL.vec_off - 4 * (D.row0 & ~3u);
+            const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
+            for (uint32_t j = D.ne0 + (wi >= rot ? wi - rot : wi + NW - rot); j < D.ne1; j += NW) {
+                const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
+                if (!rg_group_ok<IW>(G, D, col_a, it.nrows, zc, W, lane, p.err)) continue;
+                const uint32_t nU = G.y, u0 = G.x, nfull = nU >> 5;
+                Acc<MODE> a[4];
+                auto mac = [&](const uint4& q, uint32_t c) {
+                    float v[4];
+                    rg_dec4<FMT>(q, v);
+                    uint2 xq;
+                    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(xq.x), "=r"(xq.y) : "r"(xs_a + 8 * c));
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        if constexpr (MODE == F64_DF)
+                            df_mac(v[g], make_float2(__uint_as_float(xq.x), __uint_as_float(xq.y)), a[g].s, a[g].c);
+                        else
+                            a[g].v = __fma_rn((double)v[g], __hiloint2double((int)xq.y, (int)xq.x), a[g].v);
+                    }
+                };
+                const uint32_t ca = col_a + IW * (u0 + lane), va = val_a + RV * (u0 + lane);
+#pragma unroll 2
+                for (uint32_t k = 0; k < nfull; ++k) mac(rg_ldval<FMT>(va + 32 * RV * k), rg_ldcol<IW>(ca + 32 * IW * k));
+                if (nU & 31u) {
+                    const uint32_t u = 32 * nfull + lane;
+                    mac(rg_ldval_lt<FMT>(u, nU, va + 32 * RV * nfull), rg_ldcol_lt<IW>(u, nU, ca + 32 * IW * nfull, zc));
+                }
+                // the four row sums over the warp (the butterfly of rg_reduce4 on accumulator pairs):
+                // lane l ends with row l / 8's total
+                const bool b16 = lane & 16u, b8 = lane & 8u;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    Acc<MODE> k = b16 ? a[i + 2] : a[i];
+                    const Acc<MODE> snd = b16 ? a[i] : a[i + 2];
+                    k.add(snd.shfl_xor(16));
+                    a[i] = k;
+                }
+                {
+                    Acc<MODE> k = b8 ? a[1] : a[0];
+                    const Acc<MODE> snd = b8 ? a[0] : a[1];
+                    k.add(snd.shfl_xor(8));
+                    a[0] = k;
+                }
+                a[0].add(a[0].shfl_xor(4));
+                a[0].add(a[0].shfl_xor(2));
+                a[0].add(a[0].shfl_xor(1));
+                const uint32_t off = rg_row_off(G, lane >> 3);
+                if ((lane & 7u) == 0 && off != 0xFFFFu) {
+                    const uint32_t row = D.row0 + off;
+                    const float sc = FP8 ? dev::lds_f32(vrs + 4 * row) : it.scale;
+                    d64[row] = a[0].result(FP8 || FMT == DOSE_FMT_U16_SCALE, sc);
+                }
+            }
+            rot = rot + 1 == NW ? 0 : rot + 1;
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&empty[st]);
+            if (++st == S) {
+                st = 0;
+                ph ^= 1;
+            }
+        }
+    }
+}
+
+template <int FMT, uint32_t IW, int MODE>
+cudaError_t mv64_launch_t(const MmParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
+    auto k = rg_spmv64_kernel<FMT, IW, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 32 * (1 + p.nw + kMmZeroWarps), smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <uint32_t IW, int MODE>
+cudaError_t mv64_launch_iw(int fmt, const MmParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
+    switch (fmt) {
+        case DOSE_FMT_U16_SCALE: return mv64_launch_t<DOSE_FMT_U16_SCALE, IW, MODE>(p, grid, smem, s);
+        case DOSE_FMT_BF16: return mv64_launch_t<DOSE_FMT_BF16, IW, MODE>(p, grid, smem, s);
+        case DOSE_FMT_F16: return mv64_launch_t<DOSE_FMT_F16, IW, MODE>(p, grid, smem, s);
+        case DOSE_FMT_F32: return mv64_launch_t<DOSE_FMT_F32, IW, MODE>(p, grid, smem, s);
+        case DOSE_FMT_FP8E4M3_ROWSCALE: return mv64_launch_t<DOSE_FMT_FP8E4M3_ROWSCALE, IW, MODE>(p, grid, smem, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int FMT, uint32_t IW>
 cudaError_t mv_launch_t(const MmParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
     auto k = rg_spmv_kernel<FMT, IW>;
@@ -617,6 +768,63 @@ bool rg_spmv_applies(const dose_matrix* A, size_t* smem_out, uint32_t* depth_out
     if (smem_out) *smem_out = fixed + (size_t)depth * SL.bytes;
     if (depth_out) *depth_out = depth;
     return true;
+}
+
+// The one-matrix launch parameters of the single-vector forms.
+static MmParams mv_params(const dose_matrix* A, const void* x, void* d, uint32_t depth) {
+    const RowGroups& R = A->rg;
+    MmParams p;
+    p.count = 1;
+    p.nvec = 1;
+    p.depth = depth;
+    p.nw = kMvWorkers;
+    p.err = A->err;
+    MmItem& it = p.item[0];
+    it.grp = R.grp;
+    it.ucol = R.ucol;
+    it.uval = R.uval;
+    it.desc = R.sched.desc;
+    it.cta_begin = R.sched.cta_begin;
+    it.wlo = R.sched.wlo;
+    it.row_scale = A->row_scale;
+    it.mask = R.mask;
+    it.X = static_cast<const float*>(x);
+    it.D = static_cast<float*>(d);
+    it.scale = A->scale;
+    it.nrows = A->nrows;
+    it.ncols = A->ncols;
+    it.W = R.sched.wwidth;
+    p.SL = rg_slot(R.tile_u, R.tile_g, R.tile_rows, value_bytes(A->fmt), R.iw,
+                   A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
+    return p;
+}
+
+// The FP64-vector form: the window of x takes 8 bytes per column.
+bool rg_spmv64_applies(const dose_matrix* A, size_t* smem_out, uint32_t* depth_out) {
+    const RowGroups& R = A->rg;
+    if (!R.built || !R.sched.desc) return false;
+    const RgSlot SL = rg_slot(R.tile_u, R.tile_g, R.tile_rows, value_bytes(A->fmt), R.iw,
+                              A->fmt == DOSE_FMT_FP8E4M3_ROWSCALE ? 1 : 0);
+    const size_t fixed = kMmHeader + mm_x2_bytes(R.sched.wwidth);
+    if (fixed + 2ull * SL.bytes > kMmSmemBudget) return false;
+    const uint32_t depth = (uint32_t)std::min<size_t>(8, (kMmSmemBudget - fixed) / SL.bytes);
+    if (smem_out) *smem_out = fixed + (size_t)depth * SL.bytes;
+    if (depth_out) *depth_out = depth;
+    return true;
+}
+
+cudaError_t launch_rg_spmv64(const dose_matrix* A, const void* x64, double* d, bool native, cudaStream_t s) {
+    size_t smem = 0;
+    uint32_t depth = 0;
+    if (!rg_spmv64_applies(A, &smem, &depth)) return cudaErrorInvalidConfiguration;
+    if (A->nrows == 0) return cudaSuccess;
+    const MmParams p = mv_params(A, x64, d, depth);
+    const uint32_t grid = A->rg.sched.grid;
+    if (native)
+        return A->rg.iw == 2 ? mv64_launch_iw<2, F64_DP>(A->fmt, p, grid, smem, s)
+                             : mv64_launch_iw<4, F64_DP>(A->fmt, p, grid, smem, s);
+    return A->rg.iw == 2 ? mv64_launch_iw<2, F64_DF>(A->fmt, p, grid, smem, s)
+                         : mv64_launch_iw<4, F64_DF>(A->fmt, p, grid, smem, s);
 }
 
 cudaError_t launch_rg_spmv(const dose_matrix* A, const float* x, float* d, cudaStream_t s) {

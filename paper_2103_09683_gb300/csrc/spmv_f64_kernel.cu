@@ -25,13 +25,10 @@
 // DOSE_SPMV_F64_NATIVE instead converts each decoded value to FP64 and
 // accumulates with FP64 FMAs (the paper's arithmetic), to compare the two.
 // Every reduction has a fixed shape, so results are bitwise reproducible.
-#include "stage_common.cuh"
+#include "dfloat.cuh"
 
 namespace dose {
 namespace {
-
-constexpr int F64_DF = 0;  // double-float accumulation (FP32 pairs)
-constexpr int F64_DP = 1;  // native FP64 FMA accumulation
 
 struct Spmv64Params {
     const uint32_t* row_ptr;
@@ -65,82 +62,6 @@ __global__ void prepare_x_kernel(const double* __restrict__ x, uint2* __restrict
         out[j] = make_uint2((uint32_t)__double2loint(v), (uint32_t)__double2hiint(v));
     }
 }
-
-// (s, c) += a * (hi + lo)
-__device__ __forceinline__ void df_mac(float a, float2 x, float& s, float& c) {
-    const float p = __fmul_rn(a, x.x);
-    const float e = __fmaf_rn(a, x.y, __fmaf_rn(a, x.x, -p));
-    float t, err;
-    dev::two_sum(s, p, t, err);
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(err, e));
-}
-
-// (s, c) += (s2, c2)
-__device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
-    float t, e;
-    dev::two_sum(s, s2, t, e);
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(c2, e));
-}
-
-// Accumulator of one lane: a double-float pair or a double.
-template <int MODE>
-struct Acc;
-template <>
-struct Acc<F64_DF> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void mac(float a, const uint2* xsp, uint32_t j) {
-        const uint2 q = xsp[j];
-        df_mac(a, make_float2(__uint_as_float(q.x), __uint_as_float(q.y)), s, c);
-    }
-    __device__ __forceinline__ void add(const Acc& o) { df_add(s, c, o.s, o.c); }
-    __device__ __forceinline__ Acc shfl_xor(uint32_t off) const {
-        Acc o;
-        o.s = __shfl_xor_sync(0xffffffffu, s, off);
-        o.c = __shfl_xor_sync(0xffffffffu, c, off);
-        return o;
-    }
-    // d = sc * (s + c) in FP64 (sc = 1: no scale)
-    __device__ __forceinline__ double result(bool scaled, float sc) const {
-        if (!scaled) return __dadd_rn((double)s, (double)c);
-        const float p = __fmul_rn(sc, s);
-        const float e = __fmaf_rn(sc, c, __fmaf_rn(sc, s, -p));
-        return __dadd_rn((double)p, (double)e);
-    }
-    __device__ __forceinline__ uint2 pack() const { return make_uint2(__float_as_uint(s), __float_as_uint(c)); }
-    __device__ __forceinline__ static Acc unpack(uint2 q) {
-        Acc a;
-        a.s = __uint_as_float(q.x);
-        a.c = __uint_as_float(q.y);
-        return a;
-    }
-};
-template <>
-struct Acc<F64_DP> {
-    double v = 0.0;
-    __device__ __forceinline__ void mac(float a, const uint2* xsp, uint32_t j) {
-        const uint2 q = xsp[j];
-        v = __fma_rn((double)a, __hiloint2double((int)q.y, (int)q.x), v);
-    }
-    __device__ __forceinline__ void add(const Acc& o) { v = __dadd_rn(v, o.v); }
-    __device__ __forceinline__ Acc shfl_xor(uint32_t off) const {
-        Acc o;
-        o.v = __shfl_xor_sync(0xffffffffu, v, off);
-        return o;
-    }
-    __device__ __forceinline__ double result(bool scaled, float sc) const {
-        return scaled ? __dmul_rn((double)sc, v) : v;
-    }
-    __device__ __forceinline__ uint2 pack() const {
-        return make_uint2((uint32_t)__double2loint(v), (uint32_t)__double2hiint(v));
-    }
-    __device__ __forceinline__ static Acc unpack(uint2 q) {
-        Acc a;
-        a.v = __hiloint2double((int)q.y, (int)q.x);
-        return a;
-    }
-};
 
 // Lane li of an L-lane group takes the groups of four consecutive entries at
 // (kb & ~3) + 4 li + 4 L s for `iters` steps (the same for the whole warp),
@@ -377,6 +298,12 @@ cudaError_t launch_spmv_f64(const dose_matrix* A, const double* x, double* d, bo
         prepare_x_kernel<F64_DF><<<(nx + 255) / 256, 256, 0, s>>>(x, A->x64, A->ncols);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // the row-group form only when the caller asks for it (fwd_layout = 2): this
+    // kernel is bound by its arithmetic, not its bytes, and the layout's 1.17
+    // stored values per entry cost more than its fewer bytes save (clinical
+    // beam, F16: 0.228 ms on row groups against 0.221 ms on CSR)
+    if (A->fwd.tuning.layout == 2 && spmv_on_row_groups(A) && rg_spmv64_applies(A, nullptr, nullptr))
+        return launch_rg_spmv64(A, A->x64, d, native, s);
     Spmv64Params p;
     const bool idx16 = (A->flags & DOSE_CREATE_U16_INDEX) != 0;
     p.row_ptr = A->row_ptr;

@@ -67,8 +67,11 @@ def f64_check(d, enc, x, native, guard=2.0 ** -40):
 @pytest.mark.parametrize("fmt", FMTS)
 @pytest.mark.parametrize("native", [False, True])
 @pytest.mark.parametrize("index16", [False, True])
-def test_spmv_f64_tiny_beam(tiny, fmt, native, index16):
-    A, enc = make(tiny, fmt, index16=index16)
+@pytest.mark.parametrize("layout", [2, 1])
+def test_spmv_f64_tiny_beam(tiny, fmt, native, index16, layout):
+    """Row groups (fwd_layout 2) and CSR (1, also the default form of dose_spmv_f64)."""
+    A, enc = make(tiny, fmt, index16=index16, tuning=dict(fwd_layout=layout))
+    assert A.info()["spmv_layout"] == layout
     x = dosegen.spot_weights_f64(tiny.ncols, 21)
     d = A.spmv_f64(_to(x), native=native).cpu().numpy()
     f64_check(d, enc, x, native)
@@ -79,8 +82,9 @@ def test_spmv_f64_tiny_beam(tiny, fmt, native, index16):
 
 @pytest.mark.parametrize("fmt", FMTS)
 @pytest.mark.parametrize("native", [False, True])
-def test_spmv_f64_unit_vectors_give_stored_values_exactly(tiny, fmt, native):
-    A, enc = make(tiny, fmt)
+@pytest.mark.parametrize("layout", [2, 1])
+def test_spmv_f64_unit_vectors_give_stored_values_exactly(tiny, fmt, native, layout):
+    A, enc = make(tiny, fmt, tuning=dict(fwd_layout=layout))
     rng = np.random.default_rng(2)
     rows_of = np.repeat(np.arange(tiny.nrows), np.diff(enc.row_ptr.astype(np.int64)))
     for j in rng.choice(tiny.ncols, 8, replace=False):
@@ -94,9 +98,10 @@ def test_spmv_f64_unit_vectors_give_stored_values_exactly(tiny, fmt, native):
 
 
 @pytest.mark.parametrize("native", [False, True])
-def test_spmv_f64_signed_weights_across_magnitudes(tiny, native):
+@pytest.mark.parametrize("layout", [2, 1])
+def test_spmv_f64_signed_weights_across_magnitudes(tiny, native, layout):
     """x of both signs over 2^-30 .. 2^30 (cancellation inside rows)."""
-    A, enc = make(tiny, "f16")
+    A, enc = make(tiny, "f16", tuning=dict(fwd_layout=layout))
     rng = np.random.default_rng(3)
     x = (dosegen.spot_weights_f64(tiny.ncols, 22) - 0.5) * np.exp2(rng.integers(-30, 31, tiny.ncols))
     d = A.spmv_f64(_to(x), native=native).cpu().numpy()
@@ -111,8 +116,11 @@ def test_spmv_f64_edge_cases(name, native):
     default tiles, from shared memory under the small ones)."""
     csr = edge_case_matrices()[name]
     for fmt in ("f16", "fp8"):
-        for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4),
-                       dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16, row_order=1)):
+        # the default form (row groups where the matrix takes them) and the CSR
+        # form under two schedules
+        for tuning in (None, dict(tile_nnz=256, tile_rows=32, coop_nnz=64, stages=2, consumer_warps=4, fwd_layout=1),
+                       dict(tile_nnz=8192, tile_rows=4096, coop_nnz=8192, stages=2, consumer_warps=16, row_order=1,
+                            fwd_layout=1)):
             for index16 in (False, True):
                 if index16 and csr.ncols > 65536:
                     continue
