@@ -6,16 +6,16 @@
 // matrix's row-group stages (the column-windowed schedule of rg_layout.cu),
 // streamed by a producer thread through a shared-memory ring that runs on from
 // matrix to matrix.  The workers hold the CTA's window of X_m in shared memory
-// (16 floats per column, zero past nvec, and a zero column after the window),
-// laid out so that one 16-byte load of 8 columns that differ mod 8 is one
-// shared-memory wavefront.  A warp takes a whole group: lane l = 4 q + g
-// computes row g of the group for all 16 vectors over the union positions
-// u = q, q + 8, ... (one X-row gather serves the four rows of the group; the
-// union order of rg_layout.cu sorts each 32 positions by column, so 8
-// consecutive positions mostly differ mod 8), then the eight lane slices q are
-// added by a fixed transposed butterfly that leaves every lane two of its row's
-// results to store.  Two more warps write D = 0 for the CTA's share of the rows
-// without entries while the workers compute.
+// (16 floats per column, zero past nvec, and a zero column after the window)
+// in blocks of 8 columns whose 16-byte pieces j of 8 columns fill one 128-byte
+// row.  A warp takes a whole group: lane l = 2 s + r computes rows 2 r and
+// 2 r + 1 of the group for all 16 vectors over the union positions u = s,
+// s + 16, ...: per position one column load, the two rows' values in one
+// load, four 16-byte X loads (16 positions per warp-step; each X load serves
+// two rows) and 16 packed FP32 FMAs (f32x2: two IEEE FMAs each).  The sixteen
+// lane slices s are added by a fixed transposed butterfly that leaves every
+// lane two of one row's results to store.  Two more warps write D = 0 for the
+// CTA's share of the rows without entries while the workers compute.
 // Deterministic: static assignment of groups to warps, fixed per-lane order,
 // fixed butterfly.
 #include "dfloat.cuh"
@@ -101,21 +101,70 @@ __device__ void mm_zero_rows(const uint32_t* mask, float* D, uint32_t nrows, uin
     }
 }
 
-// One stored value (row g's, of a union entry) at a, decoded; 0 unless k < n.
-template <int FMT>
-__device__ __forceinline__ float mm_val_lt(uint32_t k, uint32_t n, uint32_t a) {
-    if constexpr (FMT == DOSE_FMT_F32) return dev::lds_f32_lt(k, n, a);
-    if constexpr (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) return dev::dec_e4m3((uint8_t)dev::lds_u8_lt(k, n, a));
-    const uint32_t q = dev::lds_u16_lt(k, n, a);
-    if constexpr (FMT == DOSE_FMT_BF16) return __uint_as_float(q << 16);
-    if constexpr (FMT == DOSE_FMT_F16) return dev::f16_to_f32((uint16_t)q);
-    return __fsub_rn(__uint_as_float(0x4B000000u | q), 8388608.0f);  // u16 code, exactly
+// Packed FP32 pairs (Blackwell f32x2): {lo, hi} in one 64-bit register; the
+// fused multiply-add of a pair is two IEEE FMAs, rounded as __fmaf_rn rounds.
+__device__ __forceinline__ uint64_t f2_splat(float a) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ void f2_fma(uint64_t& acc, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ void f2_split(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// 16 bytes of shared memory at a as two packed pairs.
+__device__ __forceinline__ void f2_ld4(uint32_t a, uint64_t& p0, uint64_t& p1) {
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(p0), "=l"(p1) : "r"(a));
 }
 
-__device__ __forceinline__ float4 mm_ld4(uint32_t a) {
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+// The stored values of two rows of one union entry at a (2 x the element
+// size), as raw bits in the low bytes; zeros unless k < n.
+template <int FMT>
+__device__ __forceinline__ uint2 mm_ldval2_lt(uint32_t k, uint32_t n, uint32_t a) {
+    uint2 v = make_uint2(0u, 0u);
+    if constexpr (FMT == DOSE_FMT_F32)
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %2, %3;\n\t@q ld.shared.v2.u32 {%0, %1}, [%4];\n\t}"
+                     : "+r"(v.x), "+r"(v.y) : "r"(k), "r"(n), "r"(a));
+    else if constexpr (FMT == DOSE_FMT_FP8E4M3_ROWSCALE)
+        v.x = dev::lds_u16_lt(k, n, a);
+    else
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %1, %2;\n\t@q ld.shared.u32 %0, [%3];\n\t}"
+                     : "+r"(v.x) : "r"(k), "r"(n), "r"(a));
     return v;
+}
+template <int FMT>
+__device__ __forceinline__ uint2 mm_ldval2(uint32_t a) {
+    if constexpr (FMT == DOSE_FMT_F32) {
+        uint2 v;
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+        return v;
+    } else if constexpr (FMT == DOSE_FMT_FP8E4M3_ROWSCALE) {
+        return make_uint2(dev::lds_u16(a), 0u);
+    } else {
+        return make_uint2(dev::lds_u32(a), 0u);
+    }
+}
+// Two stored values decoded to FP32 (exact).
+template <int FMT>
+__device__ __forceinline__ void mm_dec2(const uint2& q, float& a0, float& a1) {
+    if constexpr (FMT == DOSE_FMT_U16_SCALE) {
+        a0 = __fsub_rn(__uint_as_float(__byte_perm(q.x, 0x4B00u, 0x5410u)), 8388608.0f);
+        a1 = __fsub_rn(__uint_as_float(__byte_perm(q.x, 0x4B00u, 0x5432u)), 8388608.0f);
+    } else if constexpr (FMT == DOSE_FMT_F32) {
+        a0 = __uint_as_float(q.x);
+        a1 = __uint_as_float(q.y);
+    } else if constexpr (FMT == DOSE_FMT_BF16) {
+        a0 = __uint_as_float(q.x << 16);
+        a1 = __uint_as_float(q.x & 0xFFFF0000u);
+    } else if constexpr (FMT == DOSE_FMT_F16) {
+        a0 = dev::f16_to_f32((uint16_t)(q.x & 0xFFFFu));
+        a1 = dev::f16_to_f32((uint16_t)(q.x >> 16));
+    } else {
+        a0 = dev::dec_e4m3((uint8_t)(q.x & 0xFFu));
+        a1 = dev::dec_e4m3((uint8_t)((q.x >> 8) & 0xFFu));
+    }
 }
 
 __device__ __forceinline__ StageDesc mm_desc(const StageDesc* d) {
@@ -234,8 +283,9 @@ __global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
         return;
     }
     const uint32_t wi = warp - 1, ctid = threadIdx.x - 32, nct = NW * 32;
-    // lane = 4 q + g: union positions u = q (mod 8), row g of the group, all 16 vectors
-    const uint32_t q = lane >> 2, g = lane & 3u;
+    // lane = 2 s + r: union positions u = s (mod 16), rows 2 r and 2 r + 1 of the
+    // group, all 16 vectors
+    const uint32_t sl = lane >> 1, rp = lane & 1u;
     const uint32_t slot0 = dev::smem_u32(slot_base);
     uint32_t st = 0, ph = 0, rot = 0;
     for (uint32_t m = 0; m < p.count; ++m) {
@@ -248,9 +298,8 @@ __global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
             xs[j] = c < W && wlo + c < it.ncols && v < p.nvec ? __ldg(it.X + (size_t)(wlo + c) * p.nvec + v) : 0.f;
         }
         dev::named_barrier(1, nct);
-        // column c's 4 floats j at xs_a + 64 (c & ~7) + 16 (c & 7) + 128 j (wlo is a multiple of 32)
-        const uint32_t xs_a = dev::smem_u32(xs) - 64 * wlo;
-        const uint32_t zc = wlo + W;  // the zero column
+        const uint32_t xs_a = dev::smem_u32(xs) - 64 * wlo;  // + 64 (c & ~7) + 16 (c & 7) + 128 j: x[c][4 j ..]
+        const uint32_t zc = wlo + W;                        // the zero column
         const uint32_t sb = it.cta_begin[blockIdx.x], se = it.cta_begin[blockIdx.x + 1];
         for (uint32_t s = sb; s < se; ++s) {
             if (!dev::mbar_wait_poll(&full[st], ph)) {
@@ -260,68 +309,80 @@ __global__ void __launch_bounds__((kMmWorkers + 1 + kMmZeroWarps) * 32, 1) rg_sp
             const uint32_t slot = slot0 + st * SL.bytes;
             const StageDesc D = slot_desc(slot);
             const uint32_t col_a = slot + SL.col_off - IW * (D.nz0 & ~(CA - 1));
-            const uint32_t val_a = slot + SL.val_off - RV * (D.nz0 & ~(VA - 1)) + ES * g;
+            const uint32_t val_a = slot + SL.val_off - RV * (D.nz0 & ~(VA - 1)) + 2 * ES * rp;
             const uint32_t vrs = slot + SL.vec_off - 4 * (D.row0 & ~3u);
             const uint32_t grp_a = slot + SL.grp_off - 16 * D.ne0;
             for (uint32_t j = D.ne0 + (wi >= rot ? wi - rot : wi + NW - rot); j < D.ne1; j += NW) {
                 const uint4 G = dev::lds_v4_if(true, grp_a + 16 * j);
                 if (!rg_group_ok<IW>(G, D, col_a, it.nrows, zc, W, lane, p.err)) continue;
-                const uint32_t nU = G.y, u0 = G.x, nfull = nU >> 3;
-                float acc[16];
+                const uint32_t nU = G.y, u0 = G.x, nfull = nU >> 4;
+                // acc2[8 e + i]: row 2 rp + e, vectors 2 i and 2 i + 1 as a packed pair
+                uint64_t acc2[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-                auto mac = [&](float a, uint32_t c) {
+                for (int i = 0; i < 16; ++i) acc2[i] = 0ull;
+                auto mac = [&](const uint2& raw, uint32_t c) {
+                    float v0, v1;
+                    mm_dec2<FMT>(raw, v0, v1);
+                    const uint64_t w0 = f2_splat(v0), w1 = f2_splat(v1);
                     const uint32_t xa = xs_a + 64 * (c & ~7u) + 16 * (c & 7u);
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
-                        const float4 x = mm_ld4(xa + 128 * jj);
-                        acc[4 * jj + 0] = __fmaf_rn(a, x.x, acc[4 * jj + 0]);
-                        acc[4 * jj + 1] = __fmaf_rn(a, x.y, acc[4 * jj + 1]);
-                        acc[4 * jj + 2] = __fmaf_rn(a, x.z, acc[4 * jj + 2]);
-                        acc[4 * jj + 3] = __fmaf_rn(a, x.w, acc[4 * jj + 3]);
+                        uint64_t x01, x23;
+                        f2_ld4(xa + 128 * jj, x01, x23);
+                        f2_fma(acc2[2 * jj], w0, x01);
+                        f2_fma(acc2[2 * jj + 1], w0, x23);
+                        f2_fma(acc2[8 + 2 * jj], w1, x01);
+                        f2_fma(acc2[8 + 2 * jj + 1], w1, x23);
                     }
                 };
-                // this lane's union positions u = q, q + 8, ...: steps where all
-                // eight slices have a position need no mask
-                const uint32_t ca = col_a + IW * (u0 + q), va = val_a + RV * (u0 + q);
+                // this lane's union positions u = s, s + 16, ...: steps where all
+                // sixteen slices have a position need no mask
+                const uint32_t ca = col_a + IW * (u0 + sl), va = val_a + RV * (u0 + sl);
 #pragma unroll 2
-                for (uint32_t k = 0; k < nfull; ++k) {
-                    const uint32_t c = rg_ldcol<IW>(ca + 8 * IW * k);
-                    mac(mm_val_lt<FMT>(0u, 1u, va + 8 * RV * k), c);
+                for (uint32_t k = 0; k < nfull; ++k) mac(mm_ldval2<FMT>(va + 16 * RV * k), rg_ldcol<IW>(ca + 16 * IW * k));
+                if (nU & 15u) {
+                    const uint32_t u = 16 * nfull + sl;
+                    mac(mm_ldval2_lt<FMT>(u, nU, va + 16 * RV * nfull), rg_ldcol_lt<IW>(u, nU, ca + 16 * IW * nfull, zc));
                 }
-                if (nU & 7u) {
-                    const uint32_t u = 8 * nfull + q;
-                    const uint32_t c = rg_ldcol_lt<IW>(u, nU, ca + 8 * IW * nfull, zc);
-                    mac(mm_val_lt<FMT>(u, nU, va + 8 * RV * nfull), c);
-                }
-                // the eight slices: a transposed butterfly over q (lane bits 4, 3, 2);
-                // each level keeps the half of the vectors that the lane's bit selects
-                // and adds the partner's copy of it, so that lane 4 q + g ends with
-                // vectors v0, v0 + 1 of row g, v0 = 8 b4 + 4 b3 + 2 b2
+                // acc[16 e + v]: row 2 rp + e, vector v
+                float acc[32];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < 16; ++i) f2_split(acc2[i], acc[2 * i], acc[2 * i + 1]);
+                // the sixteen slices: a transposed butterfly over s (lane bits 4, 3,
+                // 2, 1); each level keeps the half that the lane's bit selects and adds
+                // the partner's copy of it, so that lane 2 s + rp ends with row
+                // g = 2 rp + b4, vectors v0 = 8 b3 + 4 b2 + 2 b1 and v0 + 1
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
                     const bool b = lane & 16u;
-                    const float snd = b ? acc[i] : acc[i + 8], kp = b ? acc[i + 8] : acc[i];
+                    const float snd = b ? acc[i] : acc[i + 16], kp = b ? acc[i + 16] : acc[i];
                     acc[i] = __fadd_rn(kp, __shfl_xor_sync(0xffffffffu, snd, 16));
                 }
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 8; ++i) {
                     const bool b = lane & 8u;
-                    const float snd = b ? acc[i] : acc[i + 4], kp = b ? acc[i + 4] : acc[i];
+                    const float snd = b ? acc[i] : acc[i + 8], kp = b ? acc[i + 8] : acc[i];
                     acc[i] = __fadd_rn(kp, __shfl_xor_sync(0xffffffffu, snd, 8));
                 }
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
+                for (int i = 0; i < 4; ++i) {
                     const bool b = lane & 4u;
-                    const float snd = b ? acc[i] : acc[i + 2], kp = b ? acc[i + 2] : acc[i];
+                    const float snd = b ? acc[i] : acc[i + 4], kp = b ? acc[i + 4] : acc[i];
                     acc[i] = __fadd_rn(kp, __shfl_xor_sync(0xffffffffu, snd, 4));
                 }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const bool b = lane & 2u;
+                    const float snd = b ? acc[i] : acc[i + 2], kp = b ? acc[i + 2] : acc[i];
+                    acc[i] = __fadd_rn(kp, __shfl_xor_sync(0xffffffffu, snd, 2));
+                }
+                const uint32_t g = 2 * rp + ((lane >> 4) & 1u);
                 const uint32_t off = rg_row_off(G, g);
                 if (off != 0xFFFFu) {
                     const uint32_t row = D.row0 + off;
                     const float sc = FP8 ? dev::lds_f32(vrs + 4 * row) : (FMT == DOSE_FMT_U16_SCALE ? it.scale : 1.f);
                     const bool scaled = FP8 || FMT == DOSE_FMT_U16_SCALE;
-                    const uint32_t v = 8 * ((lane >> 4) & 1u) + 4 * ((lane >> 3) & 1u) + 2 * ((lane >> 2) & 1u);
+                    const uint32_t v = 8 * ((lane >> 3) & 1u) + 4 * ((lane >> 2) & 1u) + 2 * ((lane >> 1) & 1u);
                     float* dr = it.D + (size_t)row * p.nvec;
                     if (v < p.nvec) dr[v] = scaled ? __fmul_rn(sc, acc[0]) : acc[0];
                     if (v + 1 < p.nvec) dr[v + 1] = scaled ? __fmul_rn(sc, acc[1]) : acc[1];
