@@ -1103,11 +1103,13 @@ def run_sell(args):
     clocks = ClockSampler(0)
     variants = []
     clocks.start()
+    # sigma 0: the CSR kernel; -1: the row-group kernel (dose_spmv's default form,
+    # whose union indices are 16-bit here whatever the CSR index width)
     for idx16 in (False, True):
-        for sigma in (0, 1, 32, 256, 1024, 8192, 1 << 20):   # 0: the CSR kernel
+        for sigma in ((-1,) if not idx16 else ()) + (0, 1, 32, 256, 1024, 8192, 1 << 20):
+            tuning = dict(sell_sigma=sigma) if sigma > 0 else (dict(fwd_layout=1) if sigma == 0 else None)
             A = dose.DoseMatrix.from_csr(csr.row_ptr, csr.col, ncols=csr.ncols, fmt="u16", values=codes,
-                                         scales=scales, index16=idx16, sell=sigma > 0,
-                                         tuning=dict(sell_sigma=sigma) if sigma else None)
+                                         scales=scales, index16=idx16, sell=sigma > 0, tuning=tuning)
             inf = A.info()
             d = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
             for _ in range(args.warmup):
@@ -1122,11 +1124,17 @@ def run_sell(args):
             ms = e0.elapsed_time(e1) / K
             A.device_status()
             gbs = inf["spmv_bytes"] / (ms * 1e-3) / 1e9
-            variants.append({"layout": f"sell-32-{sigma}" if sigma else "csr", "index_bytes": 2 if idx16 else 4,
-                             "ms": round(ms, 5), "bytes": inf["spmv_bytes"], "achieved_gbs": round(gbs, 1),
-                             "frac": round(gbs / peak, 4),
-                             "stored_entries": inf["sell_entries"] if sigma else csr.nnz,
-                             "padding": round(inf["sell_entries"] / csr.nnz - 1, 4) if sigma else 0.0})
+            name = f"sell-32-{sigma}" if sigma > 0 else ("csr" if sigma == 0 else "row-groups")
+            v = {"layout": name, "index_bytes": 2 if (idx16 or sigma < 0) else 4,
+                 "ms": round(ms, 5), "bytes": inf["spmv_bytes"], "achieved_gbs": round(gbs, 1),
+                 "frac": round(gbs / peak, 4),
+                 "stored_entries": inf["sell_entries"] if sigma > 0 else csr.nnz,
+                 "padding": round(inf["sell_entries"] / csr.nnz - 1, 4) if sigma > 0 else 0.0}
+            if sigma < 0:
+                own = inf["rg_spmv_bytes"]
+                v.update({"note": "bytes = the CSR byte model; the layout's own bytes are own_bytes",
+                          "own_bytes": own, "own_frac": round(own / (ms * 1e-3) / 1e9 / peak, 4)})
+            variants.append(v)
             del A, d
     clk = clocks.stop()
     base = next(v for v in variants if v["layout"] == "sell-32-1048576" and v["index_bytes"] == 4)
