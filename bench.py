@@ -898,13 +898,18 @@ def run_precision(args):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / K
             A.device_status()
-            nbytes = A.info()["spmv_bytes"]
+            inf = A.info()
+            nbytes = inf["spmv_bytes"]
+            rg = inf["spmv_layout"] == 2
+            own = inf["rg_spmv_bytes"] if rg else nbytes
             dv = d.cpu().numpy()[rows].astype(np.float64)
             rel = np.abs(dv[nz] - exact[nz]) / np.abs(exact[nz])
-            variants.append({"format": fmt, "compensated": comp, "index_bytes": 2 if idx16 else 4, "ms": round(ms, 5),
+            variants.append({"format": fmt, "compensated": comp, "index_bytes": 2 if idx16 else 4,
+                             "spmv_layout": "row groups" if rg else "CSR", "ms": round(ms, 5),
                              "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
                              "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4), "bytes": nbytes,
                              "bytes_per_entry": round(nbytes / csr.nnz, 3),
+                             "own_bytes": own, "own_frac": round(own / (ms * 1e-3) / 1e9 / peak, 4),
                              "rel_err_vs_fp64_values": {"max": float(rel.max()), "mean": float(rel.mean())}})
             del A, d
         del codes, scales
