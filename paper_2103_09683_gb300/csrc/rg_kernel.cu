@@ -323,7 +323,7 @@ __device__ __forceinline__ void rg_group(const RgParams& p, const RgStage& C, co
 }
 
 template <int FMT, int MODE, uint32_t IW>
-__global__ void __launch_bounds__((kRgMaxWarps + 1) * 32, 1) rg_kernel(const RgParams p) {
+__global__ void __maxnreg__(104) rg_kernel(const RgParams p) {
     constexpr bool QUAD = MODE == ADJ_MODE_QUADRATIC;
     constexpr uint32_t RV = 4 * (uint32_t)sizeof(typename Fmt<FMT>::T);
     constexpr uint32_t VA = RV >= 16 ? 1 : 16 / RV;
@@ -477,19 +477,16 @@ struct RgFin {
     uint32_t nblk_g;
 };
 
-constexpr uint32_t kFinMaxParts = 1024;  // CTA partials whose window bases a block keeps in shared memory
-
-__global__ void __launch_bounds__(256) rg_finalize(const RgFin q) {
+__global__ void __launch_bounds__(256, 8) rg_finalize(const RgFin q) {
     __shared__ float part[8][33];
     __shared__ double red[256];
-    __shared__ uint32_t swlo[kFinMaxParts];
     __shared__ uint32_t last;
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float hi = 0.f, lo = 0.f;
     if (q.f) {
         // rows without entries: thread takes rows 4i .. 4i+3 for i = tid, tid + T, ...
-        // (four such steps' loads issued together)
-        constexpr uint32_t U = 4;
+        // (two such steps' loads issued together)
+        constexpr uint32_t U = 2;
         const uint32_t nq = (q.nrows + 3) / 4, T = gridDim.x * 256;
         const uint32_t full_q = q.nrows / 4;  // quads inside p and w (16-byte loads)
         const float4* __restrict__ p4 = reinterpret_cast<const float4*>(q.p);
@@ -531,10 +528,6 @@ __global__ void __launch_bounds__(256) rg_finalize(const RgFin q) {
     }
     // the rest reads the main kernel's partials (and may update x, which it reads)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (blockIdx.x < q.nblk_g) {
-        for (uint32_t c = threadIdx.x; c < q.nparts && c < kFinMaxParts; c += 256) swlo[c] = __ldg(q.wlo + c);
-        __syncthreads();
-    }
     for (uint32_t cb = blockIdx.x; cb < q.nblk_g; cb += gridDim.x) {
         const uint32_t j = cb * 32 + lane;
         float t = 0.f;
@@ -546,14 +539,14 @@ __global__ void __launch_bounds__(256) rg_finalize(const RgFin q) {
 #pragma unroll
                 for (uint32_t u = 0; u < 8; ++u) {
                     const uint32_t cc = c + 8 * u;
-                    const uint32_t off = j - (cc < kFinMaxParts ? swlo[cc] : __ldg(q.wlo + cc));
+                    const uint32_t off = j - __ldg(q.wlo + cc);
                     v[u] = off < q.W ? __ldg(q.g_part + (size_t)cc * q.W + off) : 0.f;
                 }
 #pragma unroll
                 for (uint32_t u = 0; u < 8; ++u) t = __fadd_rn(t, v[u]);
             }
             for (; c < q.nparts; c += 8) {
-                const uint32_t off = j - (c < kFinMaxParts ? swlo[c] : __ldg(q.wlo + c));
+                const uint32_t off = j - __ldg(q.wlo + c);
                 if (off < q.W) t = __fadd_rn(t, __ldg(q.g_part + (size_t)c * q.W + off));
             }
         }
