@@ -10,10 +10,13 @@
  *     device (each must return DOSE_ERR_INVALID_ARG with a message from
  *     dose_last_error), and the NULL-tolerant calls.
  * Exit status 0 means every check passed; each failure prints a line. */
+#define _POSIX_C_SOURCE 200809L /* mkstemp, close */
 #include <stddef.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 #include "dose.h"
 
@@ -155,8 +158,44 @@ int main(void) {
     memset(&t, 0, sizeof t);
     t.rg_warps = 16;
     expect_rejected(&d, 0, &t, "rg_warps out of range");
+    memset(&t, 0, sizeof t);
+    t.fwd_layout = 3;
+    expect_rejected(&d, 0, &t, "fwd_layout out of range");
     CHECK(dose_create_matrix(NULL, 0, NULL, NULL, NULL) == DOSE_ERR_INVALID_ARG, "null desc");
 
+    {
+        /* host-only calls of the autotuner: plan of no matrices, a fingerprint, a cache round trip */
+        int layout = 7, launches = 7;
+        CHECK(dose_spmv_batched_plan(NULL, 0, 16, &layout, &launches) == DOSE_OK && layout == 0 && launches == 0,
+              "batched plan of no matrices");
+        uint64_t fp1 = 0, fp2 = 0;
+        CHECK(dose_fingerprint_host(&d, 0, &fp1) == DOSE_OK && fp1 != 0, "fingerprint");
+        CHECK(dose_fingerprint_host(&d, DOSE_CREATE_U16_INDEX, &fp2) == DOSE_OK && fp2 != fp1,
+              "fingerprint depends on the flags");
+        char path[] = "/tmp/dose_c_client_cache_XXXXXX";
+        int fd = mkstemp(path);
+        CHECK(fd >= 0, "temporary cache file");
+        if (fd >= 0) {
+            close(fd);
+            remove(path); /* a missing file reads as an empty cache */
+            dose_tuning in, out;
+            memset(&in, 0, sizeof in);
+            in.tile_nnz = 4096;
+            in.rg_tile_union = 3072;
+            in.fwd_layout = 1;
+            double ms[3] = {0.1, 0.2, 0.3}, got_ms[3] = {0, 0, 0};
+            int found = 1;
+            CHECK(dose_autotune_cache_lookup(path, "GPU", fp1, 3, &out, got_ms, &found) == DOSE_OK && !found,
+                  "lookup in a missing cache");
+            CHECK(dose_autotune_cache_store(path, "GPU", fp1, 3, &in, ms) == DOSE_OK, "cache store");
+            CHECK(dose_autotune_cache_lookup(path, "GPU", fp1, 3, &out, got_ms, &found) == DOSE_OK && found &&
+                      out.tile_nnz == 4096 && out.rg_tile_union == 3072 && out.fwd_layout == 1 && got_ms[2] == 0.3,
+                  "cache round trip");
+            CHECK(dose_autotune_cache_lookup(path, "GPU", fp2, 3, &out, got_ms, &found) == DOSE_OK && !found,
+                  "cache miss on another fingerprint");
+            remove(path);
+        }
+    }
     CHECK(dose_destroy(NULL) == DOSE_OK, "destroy NULL");
     CHECK(dose_destroy_scenarios(NULL) == DOSE_OK, "destroy_scenarios NULL");
     dose_info info;
