@@ -114,6 +114,16 @@ __device__ __forceinline__ void f2_fma(uint64_t& acc, uint64_t a, uint64_t b) {
 __device__ __forceinline__ void f2_split(uint64_t v, float& lo, float& hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
+__device__ __forceinline__ uint64_t f2_pack(uint32_t lo, uint32_t hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 // 16 bytes of shared memory at a as two packed pairs.
 __device__ __forceinline__ void f2_ld4(uint32_t a, uint64_t& p0, uint64_t& p1) {
     asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(p0), "=l"(p1) : "r"(a));
@@ -406,14 +416,35 @@ template <int FMT, uint32_t IW, int K>
 __device__ __forceinline__ void mv_steps(uint32_t ca, uint32_t va, uint32_t nU, uint32_t lane, uint32_t zc,
                                          uint32_t xs_a, float& a0, float& a1, float& a2, float& a3) {
     constexpr uint32_t RV = 4 * (uint32_t)sizeof(typename Fmt<FMT>::T);
+    // U16 and BF16: rows (0, 1) and (2, 3) as packed FP32 pairs: two codes decoded
+    // by one packed add (U16: 2^23 + q - 2^23, exact) and two rows' FMAs in one
+    // f32x2 instruction; the same IEEE operations, so the same bits as the
+    // scalar form (a0..a3 are zero on entry)
+    constexpr bool PACKED = FMT == DOSE_FMT_U16_SCALE || FMT == DOSE_FMT_BF16;
+    uint64_t a01 = 0ull, a23 = 0ull;
+    const uint64_t bias = f2_splat(-8388608.0f);
     auto mac = [&](const uint4& q, uint32_t c) {
-        float v[4];
-        rg_dec4<FMT>(q, v);
         const float x = dev::lds_f32(xs_a + 4 * c);
-        a0 = __fmaf_rn(v[0], x, a0);
-        a1 = __fmaf_rn(v[1], x, a1);
-        a2 = __fmaf_rn(v[2], x, a2);
-        a3 = __fmaf_rn(v[3], x, a3);
+        if constexpr (PACKED) {
+            uint64_t v01, v23;
+            if constexpr (FMT == DOSE_FMT_U16_SCALE) {
+                v01 = f2_add(f2_pack(__byte_perm(q.x, 0x4B00u, 0x5410u), __byte_perm(q.x, 0x4B00u, 0x5432u)), bias);
+                v23 = f2_add(f2_pack(__byte_perm(q.y, 0x4B00u, 0x5410u), __byte_perm(q.y, 0x4B00u, 0x5432u)), bias);
+            } else {
+                v01 = f2_pack(q.x << 16, q.x & 0xFFFF0000u);
+                v23 = f2_pack(q.y << 16, q.y & 0xFFFF0000u);
+            }
+            const uint64_t xx = f2_splat(x);
+            f2_fma(a01, v01, xx);
+            f2_fma(a23, v23, xx);
+        } else {
+            float v[4];
+            rg_dec4<FMT>(q, v);
+            a0 = __fmaf_rn(v[0], x, a0);
+            a1 = __fmaf_rn(v[1], x, a1);
+            a2 = __fmaf_rn(v[2], x, a2);
+            a3 = __fmaf_rn(v[3], x, a3);
+        }
     };
     if constexpr (K == 0) {
         const uint32_t nfull = nU >> 5;
@@ -436,6 +467,10 @@ __device__ __forceinline__ void mv_steps(uint32_t ca, uint32_t va, uint32_t nU, 
         c[K - 1] = rg_ldcol_lt<IW>(u, nU, ca + 32 * IW * (K - 1), zc);
 #pragma unroll
         for (int k = 0; k < K; ++k) mac(q[k], c[k]);
+    }
+    if constexpr (PACKED) {
+        f2_split(a01, a0, a1);
+        f2_split(a23, a2, a3);
     }
 }
 
