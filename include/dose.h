@@ -224,7 +224,11 @@ dose_status dose_create_matrix(const dose_csr_desc* desc, unsigned flags, const 
 
 /* d = A x (Sec. II-A; Sec. III: one output per row, the row's dot product).
  * x: device, ncols floats.  d: device, nrows floats, every row written (empty
- * rows get 0).  FP32 accumulation; U16 and FP8 scales applied once per row. */
+ * rows get 0).  FP32 accumulation; U16 and FP8 scales applied once per row.
+ * Runs on the row-group layout when the handle has it (dose_tuning.fwd_layout;
+ * dose_info.spmv_layout says which form runs), else on the CSR (or SELL)
+ * arrays; each form is deterministic, and a row is within 1e-5 relative of the
+ * FP64 sum of its terms for rows of up to 4096 entries on either. */
 dose_status dose_spmv(const dose_matrix* A, const float* x, float* d, void* stream);
 
 /* dose_spmv_f64 flags */
@@ -253,7 +257,9 @@ dose_status dose_spmv_f64(const dose_matrix* A, const double* x, double* d, unsi
  * of many beams and uncertainty scenarios, Sec. I).  X[m]: device, ncols_m x nvec
  * floats row-major (spot j's nvec weights contiguous).  D[m]: device, nrows_m x
  * nvec floats row-major.  1 <= nvec <= 16; count <= 4096.  The handles must be
- * distinct only in the sense that their outputs must not overlap. */
+ * distinct only in the sense that their outputs must not overlap.  Runs on the
+ * row-group layout when every matrix has it (one format, index width and grid;
+ * dose_spmv_batched_plan), else on the CSR arrays; deterministic either way. */
 dose_status dose_spmv_batched(const dose_matrix* const* A, int count, const float* const* X,
                               float* const* D, int nvec, void* stream);
 
